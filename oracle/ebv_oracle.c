@@ -1,0 +1,1343 @@
+/*
+ * ebv_oracle.c -- TEST INFRASTRUCTURE ONLY (see ebv_oracle.h).
+ *
+ * A plain FP64 restatement of the embedded-boundary (EB) viscoplastic flow
+ * step of Sverdrup, Almgren & Nikiforakis (arXiv:1905.07392), written for a
+ * reader who checks it against the paper: no blocking, no fusion, loops in the
+ * order of the equations.  Only the tests, the package smoke check and the
+ * CPU-baseline leg of the benchmark load it.
+ *
+ * Passages followed (paper section / equation / algorithm):
+ *   - EB geometry: Sec. "Embedded boundaries" (flags, alpha, normal into the
+ *     fluid, face apertures, EB centroid), planar cut per cell.
+ *   - Strain rate, its norm and eta: Sec. "Governing partial differential
+ *     equations" (gamma = grad u + grad u^T, ||g|| = sqrt(tr(g g^T)/2)),
+ *     Table "Generalised Newtonian fluid models", Sec. "Strain rate tensor and
+ *     apparent viscosity" (central / one-sided quadratic differences).
+ *   - Time step: Eqs. cfl:dt, cfl:convective, cfl:forcing, cfl:viscous:new.
+ *   - Algorithm 1 (Advance) and Algorithm 2 (DerivedQuantities).
+ *   - Cell-centred projection: Eq. helmholtz and the Poisson equation after it.
+ *   - Flux divergence: Eqs. divergence_conservative ... divergence_final.
+ *   - Viscous wall flux: Eqs. interpolation_distances, dudn; Appendix A.
+ *   - Semi-implicit viscous update: Eq. implicit-viscous.
+ *   - Nodal projection: Sec. "Incompressibility constraint".
+ *   - Drag: Eq. drag-force; yield criterion ||tau|| <= (1 + delta) tau0.
+ * Readings where the paper is silent are the ones listed in the design notes
+ * (face-centred EB operator, alpha-weighted trilinear nodal operator, MC
+ * limiter, upwind rule, wall-distance bound, fallbacks of the wall gradient).
+ *
+ * parity unpinned: og_drag (only the pressure part is pinned, by the
+ * buoyancy identity; the viscous traction is checked against the CUDA path
+ * alone).
+ */
+#include "ebv_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NX (g->n[0])
+#define NY (g->n[1])
+#define NZ (g->n[2])
+
+size_t og_ncell(const og_grid *g) { return (size_t)NX * NY * NZ; }
+size_t og_nnode(const og_grid *g) { return (size_t)(NX + 1) * (NY + 1) * (NZ + 1); }
+
+static size_t cidx(const og_grid *g, int i, int j, int k)
+{
+    return ((size_t)k * NY + j) * NX + i;
+}
+static size_t nidx(const og_grid *g, int i, int j, int k)
+{
+    return ((size_t)k * (NY + 1) + j) * (NX + 1) + i;
+}
+/* Face with normal d whose low corner has integer position (i,j,k); along d
+ * the index runs 0..n[d]. */
+static size_t fidx(const og_grid *g, int d, int i, int j, int k)
+{
+    if (d == 0) return ((size_t)k * NY + j) * (NX + 1) + i;
+    if (d == 1) return ((size_t)k * (NY + 1) + j) * NX + i;
+    return ((size_t)k * NY + j) * NX + i;
+}
+static size_t nface(const og_grid *g, int d)
+{
+    size_t m = 1;
+    for (int e = 0; e < 3; e++) m *= (size_t)(g->n[e] + (e == d));
+    return m;
+}
+static const double *farr(const og_geom *geo, int d)
+{
+    return d == 0 ? geo->ax : (d == 1 ? geo->ay : geo->az);
+}
+static int inside(const og_grid *g, int i, int j, int k)
+{
+    return i >= 0 && j >= 0 && k >= 0 && i < NX && j < NY && k < NZ;
+}
+/* A cell whose value may enter a stencil: inside the box and not covered. */
+static int avail(const og_grid *g, const og_geom *geo, int i, int j, int k)
+{
+    return inside(g, i, j, k) && geo->alpha[cidx(g, i, j, k)] > 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry                                                                  */
+/* ------------------------------------------------------------------------ */
+
+double og_phi(const og_shape *s, const double x[3])
+{
+    if (s->kind == OG_SHAPE_SPHERE) {
+        double dx = x[0] - s->p[0], dy = x[1] - s->p[1], dz = x[2] - s->p[2];
+        return sqrt(dx * dx + dy * dy + dz * dz) - s->p[3];
+    }
+    if (s->kind == OG_SHAPE_PLANE)
+        return s->p[0] * x[0] + s->p[1] * x[1] + s->p[2] * x[2] - s->p[3];
+    return 1.0;
+}
+
+static int is_fluid(double phi) { return phi > 0.0; }
+
+/* Point on the segment P->Q where phi changes sign, by bisection. */
+static void edge_root(const og_shape *s, const double P[3], const double Q[3], double out[3])
+{
+    double x[3], a = 0.0, b = 1.0;
+    int fa = is_fluid(og_phi(s, P));
+    for (int it = 0; it < 200 && b - a > 1e-16; it++) {
+        double m = 0.5 * (a + b);
+        for (int d = 0; d < 3; d++) x[d] = P[d] + m * (Q[d] - P[d]);
+        if (is_fluid(og_phi(s, x)) == fa) a = m; else b = m;
+    }
+    double t = 0.5 * (a + b);
+    for (int d = 0; d < 3; d++) out[d] = P[d] + t * (Q[d] - P[d]);
+}
+
+static void node_pos(const og_grid *g, int i, int j, int k, double x[3])
+{
+    x[0] = g->lo[0] + i * g->h;
+    x[1] = g->lo[1] + j * g->h;
+    x[2] = g->lo[2] + k * g->h;
+}
+
+/* Fluid aperture of one face: the polygon made of the fluid corners and the
+ * edge crossings, walked around the square; area by the shoelace formula. */
+static double face_fraction(const og_grid *g, const og_shape *s, int d, int i, int j, int k)
+{
+    int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    static const int cu[4] = {0, 1, 1, 0}, cv[4] = {0, 0, 1, 1};
+    double X[4][3];
+    int fl[4], nfl = 0;
+    for (int c = 0; c < 4; c++) {
+        int id[3] = {i, j, k};
+        id[t1] += cu[c];
+        id[t2] += cv[c];
+        node_pos(g, id[0], id[1], id[2], X[c]);
+        fl[c] = is_fluid(og_phi(s, X[c]));
+        nfl += fl[c];
+    }
+    if (nfl == 4) return 1.0;
+    if (nfl == 0) return 0.0;
+    double pu[8], pv[8];
+    int np = 0;
+    for (int c = 0; c < 4; c++) {
+        int c2 = (c + 1) % 4;
+        if (fl[c]) { pu[np] = cu[c]; pv[np] = cv[c]; np++; }
+        if (fl[c] != fl[c2]) {
+            double r[3];
+            edge_root(s, X[c], X[c2], r);
+            double o[3];
+            node_pos(g, i, j, k, o);
+            pu[np] = (r[t1] - o[t1]) / g->h;
+            pv[np] = (r[t2] - o[t2]) / g->h;
+            np++;
+        }
+    }
+    double a2 = 0.0;
+    for (int q = 0; q < np; q++) {
+        int q2 = (q + 1) % np;
+        a2 += pu[q] * pv[q2] - pu[q2] * pv[q];
+    }
+    double a = 0.5 * fabs(a2);
+    if (a < 1e-12) a = 0.0;
+    if (a > 1.0 - 1e-12) a = 1.0;
+    return a;
+}
+
+typedef struct { double ang; double p[3]; } og_pt;
+static int cmp_pt(const void *a, const void *b)
+{
+    double x = ((const og_pt *)a)->ang, y = ((const og_pt *)b)->ang;
+    return (x > y) - (x < y);
+}
+
+void og_build_geometry(const og_grid *g, const og_shape *s, og_geom *geo)
+{
+    const double h = g->h;
+    for (int d = 0; d < 3; d++) {
+        double *a = (double *)farr(geo, d);
+        int m[3] = {NX, NY, NZ};
+        m[d] += 1;
+        for (int k = 0; k < m[2]; k++)
+            for (int j = 0; j < m[1]; j++)
+                for (int i = 0; i < m[0]; i++)
+                    a[fidx(g, d, i, j, k)] = face_fraction(g, s, d, i, j, k);
+    }
+    size_t N3 = og_ncell(g);
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                double X[2][2][2][3];
+                int fl[2][2][2], nfl = 0;
+                for (int c2 = 0; c2 < 2; c2++)
+                    for (int b2 = 0; b2 < 2; b2++)
+                        for (int a2 = 0; a2 < 2; a2++) {
+                            node_pos(g, i + a2, j + b2, k + c2, X[a2][b2][c2]);
+                            fl[a2][b2][c2] = is_fluid(og_phi(s, X[a2][b2][c2]));
+                            nfl += fl[a2][b2][c2];
+                        }
+                for (int d = 0; d < 3; d++) {
+                    geo->nrm[d * N3 + c] = 0.0;
+                    geo->bcen[d * N3 + c] = 0.0;
+                }
+                geo->area[c] = 0.0;
+                if (nfl == 8) { geo->alpha[c] = 1.0; geo->flag[c] = 1; continue; }
+                if (nfl == 0) { geo->alpha[c] = 0.0; geo->flag[c] = 0; continue; }
+                /* EB area vector by closure of the fluid region's boundary. */
+                double alo[3], ahi[3], An[3], suma = 0.0;
+                for (int d = 0; d < 3; d++) {
+                    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                    hi[d] += 1;
+                    alo[d] = farr(geo, d)[fidx(g, d, lo[0], lo[1], lo[2])];
+                    ahi[d] = farr(geo, d)[fidx(g, d, hi[0], hi[1], hi[2])];
+                    An[d] = ahi[d] - alo[d];
+                    suma += alo[d] + ahi[d];
+                }
+                double A = sqrt(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
+                if (A < 1e-12) {
+                    /* The cut only touches the cell: it is full or empty. */
+                    if (suma > 3.0) { geo->alpha[c] = 1.0; geo->flag[c] = 1; }
+                    else { geo->alpha[c] = 0.0; geo->flag[c] = 0; }
+                    continue;
+                }
+                double n[3] = {An[0] / A, An[1] / A, An[2] / A};
+                /* Crossings on the 12 edges, relative to the cell centre, in h. */
+                og_pt P[12];
+                int np = 0;
+                double cc[3] = {g->lo[0] + (i + 0.5) * h, g->lo[1] + (j + 0.5) * h,
+                                g->lo[2] + (k + 0.5) * h};
+                for (int d = 0; d < 3; d++) {
+                    int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+                    for (int q1 = 0; q1 < 2; q1++)
+                        for (int q2 = 0; q2 < 2; q2++) {
+                            int o0[3] = {0, 0, 0}, o1[3];
+                            o0[t1] = q1;
+                            o0[t2] = q2;
+                            memcpy(o1, o0, sizeof o1);
+                            o1[d] = 1;
+                            if (fl[o0[0]][o0[1]][o0[2]] == fl[o1[0]][o1[1]][o1[2]]) continue;
+                            double r[3];
+                            edge_root(s, X[o0[0]][o0[1]][o0[2]], X[o1[0]][o1[1]][o1[2]], r);
+                            for (int e = 0; e < 3; e++) P[np].p[e] = (r[e] - cc[e]) / h;
+                            np++;
+                        }
+                }
+                /* Area centroid of the crossing polygon, seen along n. */
+                double M[3] = {0, 0, 0};
+                for (int q = 0; q < np; q++)
+                    for (int e = 0; e < 3; e++) M[e] += P[q].p[e] / np;
+                double e1[3], e2[3];
+                {
+                    double t[3] = {0, 0, 0};
+                    int amin = 0;
+                    for (int e = 1; e < 3; e++)
+                        if (fabs(n[e]) < fabs(n[amin])) amin = e;
+                    t[amin] = 1.0;
+                    double tn = t[0] * n[0] + t[1] * n[1] + t[2] * n[2];
+                    for (int e = 0; e < 3; e++) e1[e] = t[e] - tn * n[e];
+                    double l = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+                    for (int e = 0; e < 3; e++) e1[e] /= l;
+                    e2[0] = n[1] * e1[2] - n[2] * e1[1];
+                    e2[1] = n[2] * e1[0] - n[0] * e1[2];
+                    e2[2] = n[0] * e1[1] - n[1] * e1[0];
+                }
+                for (int q = 0; q < np; q++) {
+                    double x = 0, y = 0;
+                    for (int e = 0; e < 3; e++) {
+                        x += (P[q].p[e] - M[e]) * e1[e];
+                        y += (P[q].p[e] - M[e]) * e2[e];
+                    }
+                    P[q].ang = atan2(y, x);
+                }
+                qsort(P, np, sizeof(og_pt), cmp_pt);
+                /* Fan of triangles (M, P_q, P_q+1) around the vertex mean, so
+                 * the result does not depend on where the cycle starts. */
+                double bw = 0.0, bsum[3] = {0, 0, 0};
+                for (int q = 0; q < np; q++) {
+                    int q2 = (q + 1) % np;
+                    double u1[3], u2[3], cr[3];
+                    for (int e = 0; e < 3; e++) {
+                        u1[e] = P[q].p[e] - M[e];
+                        u2[e] = P[q2].p[e] - M[e];
+                    }
+                    cr[0] = u1[1] * u2[2] - u1[2] * u2[1];
+                    cr[1] = u1[2] * u2[0] - u1[0] * u2[2];
+                    cr[2] = u1[0] * u2[1] - u1[1] * u2[0];
+                    double w = 0.5 * (cr[0] * n[0] + cr[1] * n[1] + cr[2] * n[2]);
+                    for (int e = 0; e < 3; e++)
+                        bsum[e] += w * (M[e] + P[q].p[e] + P[q2].p[e]) / 3.0;
+                    bw += w;
+                }
+                double b[3];
+                for (int e = 0; e < 3; e++) b[e] = fabs(bw) > 1e-300 ? bsum[e] / bw : M[e];
+                /* Volume by the divergence theorem: each axis face sits at
+                 * distance 1/2 from the centre, the EB plane passes through b. */
+                double alpha = (0.5 * suma - A * (b[0] * n[0] + b[1] * n[1] + b[2] * n[2])) / 3.0;
+                if (alpha < 1e-12) alpha = 0.0;
+                if (alpha > 1.0 - 1e-12) alpha = 1.0;
+                geo->alpha[c] = alpha;
+                geo->flag[c] = alpha > 0.0 ? 2 : 0;
+                if (alpha > 0.0) {
+                    geo->area[c] = A;
+                    for (int e = 0; e < 3; e++) {
+                        geo->nrm[e * N3 + c] = n[e];
+                        geo->bcen[e * N3 + c] = b[e];
+                    }
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Strain rate and apparent viscosity                                        */
+/* ------------------------------------------------------------------------ */
+
+double og_eta_of(const og_params *p, double sr)
+{
+    /* (1 - exp(-sr*m)) / sr, with its limit m at sr = 0. */
+    double yield = (sr > 0.0) ? -expm1(-p->m * sr) / sr : p->m;
+    double srf = sr > 1.0 / p->m ? sr : 1.0 / p->m;
+    switch (p->model) {
+    case OG_NEWTONIAN: return p->mu;
+    case OG_BINGHAM: return p->mu + p->tau0 * yield;
+    case OG_HB: return p->mu * pow(srf, p->n_flow - 1.0) + p->tau0 * yield;
+    case OG_POWERLAW: return p->mu * pow(srf, p->n_flow - 1.0);
+    case OG_SMD: {
+        double y2 = (sr > 0.0) ? -expm1(-p->eta0 * sr / p->tau0) / sr : p->eta0 / p->tau0;
+        return p->mu * pow(srf, p->n_flow - 1.0) + p->tau0 * y2;
+    }
+    }
+    return p->mu;
+}
+
+/* du/dx_d at a cell from cell values, following the robust stencils:
+ * central when both neighbours exist, the one-sided quadratic when one side
+ * is missing, first order if only one neighbour exists, zero otherwise. */
+static double d_cell(const og_grid *g, const og_geom *geo, const double *f, int i, int j, int k,
+                     int d)
+{
+    int e[3] = {0, 0, 0};
+    e[d] = 1;
+    double h = g->h;
+    int ip = avail(g, geo, i + e[0], j + e[1], k + e[2]);
+    int im = avail(g, geo, i - e[0], j - e[1], k - e[2]);
+    double f0 = f[cidx(g, i, j, k)];
+    if (ip && im)
+        return (f[cidx(g, i + e[0], j + e[1], k + e[2])] - f[cidx(g, i - e[0], j - e[1], k - e[2])]) /
+               (2.0 * h);
+    if (im) {
+        double f1 = f[cidx(g, i - e[0], j - e[1], k - e[2])];
+        if (avail(g, geo, i - 2 * e[0], j - 2 * e[1], k - 2 * e[2])) {
+            double f2 = f[cidx(g, i - 2 * e[0], j - 2 * e[1], k - 2 * e[2])];
+            return (0.5 * f2 - 2.0 * f1 + 1.5 * f0) / h;
+        }
+        return (f0 - f1) / h;
+    }
+    if (ip) {
+        double f1 = f[cidx(g, i + e[0], j + e[1], k + e[2])];
+        if (avail(g, geo, i + 2 * e[0], j + 2 * e[1], k + 2 * e[2])) {
+            double f2 = f[cidx(g, i + 2 * e[0], j + 2 * e[1], k + 2 * e[2])];
+            return (-1.5 * f0 + 2.0 * f1 - 0.5 * f2) / h;
+        }
+        return (f1 - f0) / h;
+    }
+    return 0.0;
+}
+
+void og_cell_gradient(const og_grid *g, const og_geom *geo, const double *u, double *grad)
+{
+    size_t N3 = og_ncell(g);
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                for (int d = 0; d < 3; d++)
+                    for (int q = 0; q < 3; q++)
+                        grad[(3 * d + q) * N3 + c] =
+                            geo->alpha[c] > 0.0 ? d_cell(g, geo, u + q * N3, i, j, k, d) : 0.0;
+            }
+}
+
+void og_strain_eta(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                   double *eta, double *srate)
+{
+    size_t N3 = og_ncell(g);
+    double *G = malloc(9 * N3 * sizeof(double));
+    og_cell_gradient(g, geo, u, G);
+    for (size_t c = 0; c < N3; c++) {
+        if (geo->alpha[c] <= 0.0) {
+            eta[c] = 0.0;
+            if (srate) srate[c] = 0.0;
+            continue;
+        }
+        double s2 = 0.0;
+        for (int d = 0; d < 3; d++)
+            for (int q = 0; q < 3; q++) {
+                double gam = G[(3 * d + q) * N3 + c] + G[(3 * q + d) * N3 + c];
+                s2 += gam * gam;
+            }
+        double sr = sqrt(0.5 * s2);
+        eta[c] = og_eta_of(p, sr);
+        if (srate) srate[c] = sr;
+    }
+    free(G);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Generic cell-centred operator and its CG solver                           */
+/* ------------------------------------------------------------------------ */
+
+static const double *barr(int d, const double *bx, const double *by, const double *bz)
+{
+    return d == 0 ? bx : (d == 1 ? by : bz);
+}
+
+void og_cc_apply(const og_grid *g, const double *extra, const double *bx, const double *by,
+                 const double *bz, const double *x, double *y)
+{
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                double v = extra[c] * x[c];
+                for (int d = 0; d < 3; d++) {
+                    const double *B = barr(d, bx, by, bz);
+                    int id[3] = {i, j, k};
+                    double blo = B[fidx(g, d, id[0], id[1], id[2])];
+                    id[d] += 1;
+                    double bhi = B[fidx(g, d, id[0], id[1], id[2])];
+                    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                    lo[d] -= 1;
+                    hi[d] += 1;
+                    double xlo = inside(g, lo[0], lo[1], lo[2]) ? x[cidx(g, lo[0], lo[1], lo[2])] : 0.0;
+                    double xhi = inside(g, hi[0], hi[1], hi[2]) ? x[cidx(g, hi[0], hi[1], hi[2])] : 0.0;
+                    v += blo * (x[c] - xlo) + bhi * (x[c] - xhi);
+                }
+                y[c] = v;
+            }
+}
+
+static double dot(const double *a, const double *b, size_t n)
+{
+    double s = 0.0;
+    for (size_t q = 0; q < n; q++) s += a[q] * b[q];
+    return s;
+}
+
+/* Jacobi-preconditioned conjugate gradients on an SPD operator given by a
+ * callback; stops at ||b - A x|| <= tol ||b|| (true residual checked). */
+typedef void (*og_apply_fn)(const void *ctx, const double *x, double *y);
+static int pcg(og_apply_fn A, const void *ctx, const double *diag, const double *b, double *x,
+               size_t n, double tol, int max_iters, double *res_out)
+{
+    double *r = malloc(n * sizeof(double)), *z = malloc(n * sizeof(double));
+    double *pp = malloc(n * sizeof(double)), *q = malloc(n * sizeof(double));
+    double bn = sqrt(dot(b, b, n));
+    int it = 0;
+    double rel = 0.0;
+    if (bn == 0.0) {
+        memset(x, 0, n * sizeof(double));
+        goto done;
+    }
+    for (int restart = 0; restart < 20; restart++) {
+        A(ctx, x, q);
+        for (size_t s = 0; s < n; s++) r[s] = b[s] - q[s];
+        rel = sqrt(dot(r, r, n)) / bn;
+        if (rel <= tol || it >= max_iters) break;
+        for (size_t s = 0; s < n; s++) { z[s] = r[s] / diag[s]; pp[s] = z[s]; }
+        double rz = dot(r, z, n);
+        while (it < max_iters) {
+            A(ctx, pp, q);
+            double a = rz / dot(pp, q, n);
+            for (size_t s = 0; s < n; s++) { x[s] += a * pp[s]; r[s] -= a * q[s]; }
+            it++;
+            if (sqrt(dot(r, r, n)) <= 0.5 * tol * bn) break;
+            for (size_t s = 0; s < n; s++) z[s] = r[s] / diag[s];
+            double rz2 = dot(r, z, n);
+            for (size_t s = 0; s < n; s++) pp[s] = z[s] + (rz2 / rz) * pp[s];
+            rz = rz2;
+        }
+    }
+done:
+    if (res_out) *res_out = rel;
+    free(r); free(z); free(pp); free(q);
+    return it;
+}
+
+typedef struct {
+    const og_grid *g;
+    const double *extra, *bx, *by, *bz;
+} cc_ctx;
+static void cc_cb(const void *ctx, const double *x, double *y)
+{
+    const cc_ctx *c = ctx;
+    og_cc_apply(c->g, c->extra, c->bx, c->by, c->bz, x, y);
+}
+
+int og_cc_solve(const og_grid *g, const double *extra, const double *bx, const double *by,
+                const double *bz, const double *b, double *x, double tol, int max_iters,
+                double *res_out)
+{
+    size_t N3 = og_ncell(g);
+    double *diag = malloc(N3 * sizeof(double));
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                double v = extra[c];
+                for (int d = 0; d < 3; d++) {
+                    const double *B = barr(d, bx, by, bz);
+                    int id[3] = {i, j, k};
+                    v += B[fidx(g, d, id[0], id[1], id[2])];
+                    id[d] += 1;
+                    v += B[fidx(g, d, id[0], id[1], id[2])];
+                }
+                diag[c] = v > 0.0 ? v : 1.0;
+            }
+    cc_ctx ctx = {g, extra, bx, by, bz};
+    int it = pcg(cc_cb, &ctx, diag, b, x, N3, tol, max_iters, res_out);
+    free(diag);
+    return it;
+}
+
+/* Boundary condition of velocity component `comp` on box side `side`:
+ * returns 1 and the value for Dirichlet, 0 for Neumann. */
+static int side_dirichlet(const og_grid *g, int side, int comp, double *val)
+{
+    int d = side / 2;
+    switch (g->bc[side]) {
+    case OG_INFLOW: *val = g->u_in[comp]; return 1;
+    case OG_NOSLIP: *val = 0.0; return 1;
+    case OG_SLIP: *val = 0.0; return comp == d;
+    default: *val = 0.0; return 0;
+    }
+}
+
+/* Cell-centred projection operator: alpha-weighted EB Poisson (face-centred
+ * fluxes weighted by the apertures), Dirichlet phi = 0 at outflow sides,
+ * Neumann elsewhere and on the EB. */
+void og_mac_coeffs(const og_grid *g, const og_geom *geo, double *extra, double *bx, double *by,
+                   double *bz)
+{
+    const double h2 = g->h * g->h;
+    for (size_t c = 0; c < og_ncell(g); c++) extra[c] = geo->alpha[c] > 0.0 ? 0.0 : 1.0;
+    for (int d = 0; d < 3; d++) {
+        double *B = (double *)barr(d, bx, by, bz);
+        const double *a = farr(geo, d);
+        int m[3] = {NX, NY, NZ};
+        m[d] += 1;
+        for (int k = 0; k < m[2]; k++)
+            for (int j = 0; j < m[1]; j++)
+                for (int i = 0; i < m[0]; i++) {
+                    int id[3] = {i, j, k};
+                    size_t f = fidx(g, d, i, j, k);
+                    if (id[d] == 0 || id[d] == g->n[d]) {
+                        int side = 2 * d + (id[d] == g->n[d]);
+                        B[f] = g->bc[side] == OG_OUTFLOW ? 2.0 * a[f] / h2 : 0.0;
+                    } else {
+                        B[f] = a[f] / h2;
+                    }
+                }
+    }
+}
+
+/* Semi-implicit viscous operator for one component (Eq. implicit-viscous),
+ * alpha-weighted: rho*alpha*u + dt/h^2 sum a_f eta_f (u_i - u_nb)
+ * + dt/h^2 eta_i A_EB / delta_i u_i, with delta_i the distance from the EB
+ * centroid plane to the cell centre (cell units, bounded below). */
+void og_visc_coeffs(const og_grid *g, const og_geom *geo, const og_params *p, const double *eta,
+                    double dt, int comp, double *extra, double *bx, double *by, double *bz,
+                    double *rhs_bc)
+{
+    const double h2 = g->h * g->h;
+    size_t N3 = og_ncell(g);
+    for (size_t c = 0; c < N3; c++) {
+        if (geo->alpha[c] <= 0.0) { extra[c] = 1.0; if (rhs_bc) rhs_bc[c] = 0.0; continue; }
+        double e = p->rho * geo->alpha[c];
+        if (geo->flag[c] == 2 && geo->area[c] > 0.0) {
+            double nb = 0.0;
+            for (int q = 0; q < 3; q++) nb += geo->nrm[q * N3 + c] * geo->bcen[q * N3 + c];
+            double del = -nb > p->delta_min ? -nb : p->delta_min;
+            e += dt * eta[c] * geo->area[c] / (h2 * del);
+        }
+        extra[c] = e;
+        if (rhs_bc) rhs_bc[c] = 0.0;
+    }
+    for (int d = 0; d < 3; d++) {
+        double *B = (double *)barr(d, bx, by, bz);
+        const double *a = farr(geo, d);
+        int m[3] = {NX, NY, NZ};
+        m[d] += 1;
+        for (int k = 0; k < m[2]; k++)
+            for (int j = 0; j < m[1]; j++)
+                for (int i = 0; i < m[0]; i++) {
+                    int id[3] = {i, j, k};
+                    size_t f = fidx(g, d, i, j, k);
+                    if (id[d] == 0 || id[d] == g->n[d]) {
+                        int hi = id[d] == g->n[d];
+                        int side = 2 * d + hi;
+                        int cc[3] = {i, j, k};
+                        if (hi) cc[d] -= 1;
+                        size_t c = cidx(g, cc[0], cc[1], cc[2]);
+                        double val;
+                        if (a[f] > 0.0 && side_dirichlet(g, side, comp, &val)) {
+                            B[f] = 2.0 * dt * a[f] * eta[c] / h2;
+                            if (rhs_bc) rhs_bc[c] += B[f] * val;
+                        } else {
+                            B[f] = 0.0;
+                        }
+                    } else {
+                        int lo[3] = {i, j, k};
+                        lo[d] -= 1;
+                        double ef = 0.5 * (eta[cidx(g, lo[0], lo[1], lo[2])] + eta[cidx(g, i, j, k)]);
+                        B[f] = a[f] > 0.0 ? dt * a[f] * ef / h2 : 0.0;
+                    }
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nodal projection                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Trilinear (Q1) stiffness on the unit cube, int grad N_a . grad N_b, from the
+ * 1-D integrals: int phi_p phi_q = 1/3 or 1/6, int phi_p' phi_q' = +1 or -1. */
+static double q1_stiff(int oa, int ob)
+{
+    double v = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double t = 1.0;
+        for (int e = 0; e < 3; e++) {
+            int pa = (oa >> e) & 1, pb = (ob >> e) & 1;
+            if (e == d) t *= (pa == pb) ? 1.0 : -1.0;
+            else t *= (pa == pb) ? 1.0 / 3.0 : 1.0 / 6.0;
+        }
+        v += t;
+    }
+    return v;
+}
+
+static int node_dirichlet(const og_grid *g, int i, int j, int k)
+{
+    int id[3] = {i, j, k};
+    for (int d = 0; d < 3; d++) {
+        if (id[d] == 0 && g->bc[2 * d] == OG_OUTFLOW) return 1;
+        if (id[d] == g->n[d] && g->bc[2 * d + 1] == OG_OUTFLOW) return 1;
+    }
+    return 0;
+}
+/* A node is active when it is not a Dirichlet node and touches fluid. */
+static int node_active(const og_grid *g, const og_geom *geo, int i, int j, int k)
+{
+    if (node_dirichlet(g, i, j, k)) return 0;
+    for (int o = 0; o < 8; o++) {
+        int ci = i - 1 + (o & 1), cj = j - 1 + ((o >> 1) & 1), ck = k - 1 + ((o >> 2) & 1);
+        if (avail(g, geo, ci, cj, ck)) return 1;
+    }
+    return 0;
+}
+
+void og_nodal_apply(const og_grid *g, const og_geom *geo, double coef, const double *p, double *y)
+{
+    double K[8][8];
+    for (int a = 0; a < 8; a++)
+        for (int b = 0; b < 8; b++) K[a][b] = q1_stiff(a, b);
+    for (int k = 0; k <= NZ; k++)
+        for (int j = 0; j <= NY; j++)
+            for (int i = 0; i <= NX; i++) {
+                size_t n = nidx(g, i, j, k);
+                if (!node_active(g, geo, i, j, k)) { y[n] = p[n]; continue; }
+                double v = 0.0;
+                for (int oc = 0; oc < 8; oc++) {
+                    /* cell with this node at local corner oa */
+                    int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+                    if (!inside(g, ci, cj, ck)) continue;
+                    double al = geo->alpha[cidx(g, ci, cj, ck)];
+                    if (al <= 0.0) continue;
+                    int oa = (i - ci) | ((j - cj) << 1) | ((k - ck) << 2);
+                    for (int ob = 0; ob < 8; ob++) {
+                        int bi = ci + (ob & 1), bj = cj + ((ob >> 1) & 1), bk = ck + ((ob >> 2) & 1);
+                        if (!node_active(g, geo, bi, bj, bk)) continue;
+                        v += al * K[oa][ob] * p[nidx(g, bi, bj, bk)];
+                    }
+                }
+                y[n] = coef * g->h * v;
+            }
+}
+
+/* Right-hand side of the nodal Poisson equation in weak form:
+ * sum over cells of alpha_c h^3 grad N_a(centre) . u_c, minus the boundary
+ * integral of N_a u_bc . n on inflow sides (zero on walls). */
+void og_nodal_rhs(const og_grid *g, const og_geom *geo, const double *ut, double *rhs)
+{
+    size_t N3 = og_ncell(g);
+    const double h = g->h;
+    for (int k = 0; k <= NZ; k++)
+        for (int j = 0; j <= NY; j++)
+            for (int i = 0; i <= NX; i++) {
+                size_t n = nidx(g, i, j, k);
+                if (!node_active(g, geo, i, j, k)) { rhs[n] = 0.0; continue; }
+                double v = 0.0;
+                for (int oc = 0; oc < 8; oc++) {
+                    int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+                    if (!avail(g, geo, ci, cj, ck)) continue;
+                    size_t c = cidx(g, ci, cj, ck);
+                    int o[3] = {i - ci, j - cj, k - ck};
+                    for (int d = 0; d < 3; d++)
+                        v += geo->alpha[c] * h * h * 0.25 * (o[d] ? 1.0 : -1.0) * ut[d * N3 + c];
+                }
+                int id[3] = {i, j, k};
+                for (int d = 0; d < 3; d++)
+                    for (int hs = 0; hs < 2; hs++) {
+                        int side = 2 * d + hs;
+                        if (g->bc[side] != OG_INFLOW) continue;
+                        if (id[d] != (hs ? g->n[d] : 0)) continue;
+                        double sgn = hs ? 1.0 : -1.0; /* outward normal */
+                        int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+                        for (int q1 = -1; q1 <= 0; q1++)
+                            for (int q2 = -1; q2 <= 0; q2++) {
+                                int fid[3] = {i, j, k};
+                                fid[t1] += q1;
+                                fid[t2] += q2;
+                                if (fid[t1] < 0 || fid[t1] >= g->n[t1] || fid[t2] < 0 ||
+                                    fid[t2] >= g->n[t2])
+                                    continue;
+                                double af = farr(geo, d)[fidx(g, d, fid[0], fid[1], fid[2])];
+                                v -= sgn * g->u_in[d] * af * h * h * 0.25;
+                            }
+                    }
+                rhs[n] = v;
+            }
+}
+
+typedef struct {
+    const og_grid *g;
+    const og_geom *geo;
+    double coef;
+} nd_ctx;
+static void nd_cb(const void *ctx, const double *x, double *y)
+{
+    const nd_ctx *c = ctx;
+    og_nodal_apply(c->g, c->geo, c->coef, x, y);
+}
+
+int og_nodal_solve(const og_grid *g, const og_geom *geo, double coef, const double *b, double *p,
+                   double tol, int max_iters, double *res_out)
+{
+    size_t NN = og_nnode(g);
+    double *diag = malloc(NN * sizeof(double));
+    double K00 = q1_stiff(0, 0);
+    for (int k = 0; k <= NZ; k++)
+        for (int j = 0; j <= NY; j++)
+            for (int i = 0; i <= NX; i++) {
+                size_t n = nidx(g, i, j, k);
+                double v = 0.0;
+                if (node_active(g, geo, i, j, k)) {
+                    for (int oc = 0; oc < 8; oc++) {
+                        int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+                        if (avail(g, geo, ci, cj, ck)) v += geo->alpha[cidx(g, ci, cj, ck)] * K00;
+                    }
+                    v *= coef * g->h;
+                } else {
+                    p[n] = 0.0;
+                }
+                diag[n] = v > 0.0 ? v : 1.0;
+            }
+    nd_ctx ctx = {g, geo, coef};
+    int it = pcg(nd_cb, &ctx, diag, b, p, NN, tol, max_iters, res_out);
+    free(diag);
+    return it;
+}
+
+/* Gradient of the trilinear interpolant of nodal p at each cell centre. */
+void og_cell_grad_p(const og_grid *g, const double *p, double *gp)
+{
+    size_t N3 = og_ncell(g);
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                for (int d = 0; d < 3; d++) {
+                    int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+                    double s = 0.0;
+                    for (int q1 = 0; q1 < 2; q1++)
+                        for (int q2 = 0; q2 < 2; q2++) {
+                            int lo[3] = {i, j, k};
+                            lo[t1] += q1;
+                            lo[t2] += q2;
+                            int hi[3] = {lo[0], lo[1], lo[2]};
+                            hi[d] += 1;
+                            s += p[nidx(g, hi[0], hi[1], hi[2])] - p[nidx(g, lo[0], lo[1], lo[2])];
+                        }
+                    gp[d * N3 + c] = s / (4.0 * g->h);
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Derived quantities (Algorithm 2)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Monotonised-central limited slope (difference across one cell); zero when
+ * a neighbour in that direction is covered or outside the box. */
+static double slope(const og_grid *g, const og_geom *geo, const double *f, int i, int j, int k,
+                    int d)
+{
+    int e[3] = {0, 0, 0};
+    e[d] = 1;
+    if (!avail(g, geo, i + e[0], j + e[1], k + e[2]) || !avail(g, geo, i - e[0], j - e[1], k - e[2]))
+        return 0.0;
+    double f0 = f[cidx(g, i, j, k)];
+    double fp = f[cidx(g, i + e[0], j + e[1], k + e[2])];
+    double fm = f[cidx(g, i - e[0], j - e[1], k - e[2])];
+    double dl = f0 - fm, dr = fp - f0, dc = 0.5 * (fp - fm);
+    if (dl * dr <= 0.0) return 0.0;
+    double m = fabs(dc);
+    if (2.0 * fabs(dl) < m) m = 2.0 * fabs(dl);
+    if (2.0 * fabs(dr) < m) m = 2.0 * fabs(dr);
+    return dc > 0.0 ? m : -m;
+}
+
+/* Upwinding of the face-normal velocity from the two extrapolated states. */
+static double upwind_normal(double uL, double uR)
+{
+    if (uL > 0.0 && uL + uR > 0.0) return uL;
+    if (uR < 0.0 && uL + uR < 0.0) return uR;
+    return 0.0;
+}
+
+void og_face_states(const og_grid *g, const og_geom *geo, const double *u, double *uf)
+{
+    size_t N3 = og_ncell(g);
+    size_t off = 0;
+    for (int d = 0; d < 3; d++) {
+        const double *a = farr(geo, d);
+        const double *ud = u + d * N3;
+        int m[3] = {NX, NY, NZ};
+        m[d] += 1;
+        for (int k = 0; k < m[2]; k++)
+            for (int j = 0; j < m[1]; j++)
+                for (int i = 0; i < m[0]; i++) {
+                    int id[3] = {i, j, k};
+                    size_t f = fidx(g, d, i, j, k);
+                    double v = 0.0;
+                    if (a[f] > 0.0) {
+                        int lo[3] = {i, j, k};
+                        lo[d] -= 1;
+                        if (id[d] == 0 || id[d] == g->n[d]) {
+                            int hs = id[d] == g->n[d];
+                            int side = 2 * d + hs;
+                            int cc[3] = {i, j, k};
+                            if (hs) cc[d] -= 1;
+                            switch (g->bc[side]) {
+                            case OG_INFLOW: v = g->u_in[d]; break;
+                            case OG_OUTFLOW: v = ud[cidx(g, cc[0], cc[1], cc[2])]; break;
+                            default: v = 0.0;
+                            }
+                        } else {
+                            double uL = ud[cidx(g, lo[0], lo[1], lo[2])] +
+                                        0.5 * slope(g, geo, ud, lo[0], lo[1], lo[2], d);
+                            double uR = ud[cidx(g, i, j, k)] - 0.5 * slope(g, geo, ud, i, j, k, d);
+                            v = upwind_normal(uL, uR);
+                        }
+                    }
+                    uf[off + f] = v;
+                }
+        off += nface(g, d);
+    }
+}
+
+int og_mac_project(const og_grid *g, const og_geom *geo, double *uf, double *phi, double tol,
+                   int max_iters, double *res_out)
+{
+    size_t N3 = og_ncell(g);
+    size_t nf[3] = {nface(g, 0), nface(g, 1), nface(g, 2)};
+    double *ufd[3] = {uf, uf + nf[0], uf + nf[0] + nf[1]};
+    double *extra = malloc(N3 * sizeof(double)), *b = malloc(N3 * sizeof(double));
+    double *B[3];
+    for (int d = 0; d < 3; d++) B[d] = malloc(nf[d] * sizeof(double));
+    og_mac_coeffs(g, geo, extra, B[0], B[1], B[2]);
+    const double h = g->h;
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                if (geo->alpha[c] <= 0.0) { b[c] = 0.0; continue; }
+                double s = 0.0;
+                for (int d = 0; d < 3; d++) {
+                    int id[3] = {i, j, k};
+                    size_t flo = fidx(g, d, id[0], id[1], id[2]);
+                    id[d] += 1;
+                    size_t fhi = fidx(g, d, id[0], id[1], id[2]);
+                    s += farr(geo, d)[fhi] * ufd[d][fhi] - farr(geo, d)[flo] * ufd[d][flo];
+                }
+                b[c] = -s / h;
+            }
+    for (size_t c = 0; c < N3; c++) phi[c] = 0.0;
+    int it = og_cc_solve(g, extra, B[0], B[1], B[2], b, phi, tol, max_iters, res_out);
+    for (int d = 0; d < 3; d++) {
+        const double *a = farr(geo, d);
+        int m[3] = {NX, NY, NZ};
+        m[d] += 1;
+        for (int k = 0; k < m[2]; k++)
+            for (int j = 0; j < m[1]; j++)
+                for (int i = 0; i < m[0]; i++) {
+                    int id[3] = {i, j, k};
+                    size_t f = fidx(g, d, i, j, k);
+                    if (a[f] <= 0.0) continue;
+                    if (id[d] == 0 || id[d] == g->n[d]) {
+                        int hs = id[d] == g->n[d];
+                        if (g->bc[2 * d + hs] != OG_OUTFLOW) continue;
+                        int cc[3] = {i, j, k};
+                        if (hs) cc[d] -= 1;
+                        double pc = phi[cidx(g, cc[0], cc[1], cc[2])];
+                        double grad = hs ? (0.0 - pc) / (0.5 * h) : (pc - 0.0) / (0.5 * h);
+                        ufd[d][f] -= grad;
+                    } else {
+                        int lo[3] = {i, j, k};
+                        lo[d] -= 1;
+                        ufd[d][f] -= (phi[cidx(g, i, j, k)] - phi[cidx(g, lo[0], lo[1], lo[2])]) / h;
+                    }
+                }
+    }
+    free(extra); free(b);
+    for (int d = 0; d < 3; d++) free(B[d]);
+    return it;
+}
+
+/* Neighbourhood average, hybridisation and redistribution of the excess
+ * (Eqs. divergence_nonconservative .. divergence_final), with the
+ * neighbourhood read as the 26 surrounding cells that hold fluid. */
+void og_redistribute(const og_grid *g, const og_geom *geo, const double *DC, double *D)
+{
+    size_t N3 = og_ncell(g);
+    double *dD = calloc(N3, sizeof(double)), *w = calloc(N3, sizeof(double));
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                double al = geo->alpha[c];
+                if (al <= 0.0) { D[c] = 0.0; continue; }
+                double sa = 0.0, sad = 0.0;
+                for (int dk = -1; dk <= 1; dk++)
+                    for (int dj = -1; dj <= 1; dj++)
+                        for (int di = -1; di <= 1; di++) {
+                            if (!di && !dj && !dk) continue;
+                            if (!avail(g, geo, i + di, j + dj, k + dk)) continue;
+                            size_t c2 = cidx(g, i + di, j + dj, k + dk);
+                            sa += geo->alpha[c2];
+                            sad += geo->alpha[c2] * DC[c2];
+                        }
+                double dnc = sa > 0.0 ? sad / sa : DC[c];
+                D[c] = al * DC[c] + (1.0 - al) * dnc; /* hybrid D^H */
+                dD[c] = al * (1.0 - al) * (DC[c] - dnc);
+                w[c] = sa > 0.0 ? 1.0 / sa : 0.0;
+            }
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                if (geo->alpha[c] <= 0.0) continue;
+                double s = 0.0;
+                for (int dk = -1; dk <= 1; dk++)
+                    for (int dj = -1; dj <= 1; dj++)
+                        for (int di = -1; di <= 1; di++) {
+                            if (!di && !dj && !dk) continue;
+                            if (!avail(g, geo, i + di, j + dj, k + dk)) continue;
+                            size_t c2 = cidx(g, i + di, j + dj, k + dk);
+                            s += w[c2] * dD[c2];
+                        }
+                D[c] += s;
+            }
+    free(dD);
+    free(w);
+}
+
+/* Convective term C = -div(u (x) u^F) with zero EB flux; advected states are
+ * the slope-extrapolated cell values upwinded by the projected face velocity. */
+void og_convective(const og_grid *g, const og_geom *geo, const double *u, const double *uf,
+                   double *C)
+{
+    size_t N3 = og_ncell(g);
+    size_t nf[3] = {nface(g, 0), nface(g, 1), nface(g, 2)};
+    const double *ufd[3] = {uf, uf + nf[0], uf + nf[0] + nf[1]};
+    const double h = g->h;
+    double *DC = malloc(N3 * sizeof(double)), *D = malloc(N3 * sizeof(double));
+    for (int q = 0; q < 3; q++) {
+        const double *uq = u + q * N3;
+        for (int k = 0; k < NZ; k++)
+            for (int j = 0; j < NY; j++)
+                for (int i = 0; i < NX; i++) {
+                    size_t c = cidx(g, i, j, k);
+                    if (geo->alpha[c] <= 0.0) { DC[c] = 0.0; continue; }
+                    double s = 0.0;
+                    for (int d = 0; d < 3; d++)
+                        for (int hs = 0; hs < 2; hs++) {
+                            int id[3] = {i, j, k};
+                            id[d] += hs;
+                            size_t f = fidx(g, d, id[0], id[1], id[2]);
+                            double a = farr(geo, d)[f];
+                            if (a <= 0.0) continue;
+                            double w = ufd[d][f], state;
+                            if (id[d] == 0 || id[d] == g->n[d]) {
+                                int side = 2 * d + hs;
+                                if (g->bc[side] == OG_INFLOW) state = g->u_in[q];
+                                else state = uq[c];
+                            } else {
+                                int L[3] = {id[0], id[1], id[2]};
+                                L[d] -= 1;
+                                int R[3] = {id[0], id[1], id[2]};
+                                double sL = uq[cidx(g, L[0], L[1], L[2])] +
+                                            0.5 * slope(g, geo, uq, L[0], L[1], L[2], d);
+                                double sR = uq[cidx(g, R[0], R[1], R[2])] -
+                                            0.5 * slope(g, geo, uq, R[0], R[1], R[2], d);
+                                state = w > 0.0 ? sL : (w < 0.0 ? sR : 0.5 * (sL + sR));
+                            }
+                            s += (hs ? 1.0 : -1.0) * a * state * w;
+                        }
+                    DC[c] = s / (geo->alpha[c] * h);
+                }
+        og_redistribute(g, geo, DC, D);
+        for (size_t c = 0; c < N3; c++) C[q * N3 + c] = -D[c];
+    }
+    free(DC);
+    free(D);
+}
+
+/* Normal derivative of velocity component `comp` at the EB centroid of a cut
+ * cell (Eqs. interpolation_distances and dudn), u_EB = 0.  Interpolation planes
+ * are the cell-centre planes one and two cells away along the axis of the
+ * largest |n_d|; values come from biquadratic Lagrange interpolation on the
+ * 3x3 cells nearest to the crossing point.  If a needed cell is covered, the
+ * nearest cell of the first plane gives a one-point estimate. */
+double og_wall_dudn(const og_grid *g, const og_geom *geo, const double *u, int cell, int comp)
+{
+    size_t N3 = og_ncell(g);
+    const double *uq = u + (size_t)comp * N3;
+    double n[3], b[3];
+    for (int e = 0; e < 3; e++) {
+        n[e] = geo->nrm[e * N3 + cell];
+        b[e] = geo->bcen[e * N3 + cell];
+    }
+    int ci[3];
+    ci[0] = cell % NX;
+    ci[1] = (cell / NX) % NY;
+    ci[2] = cell / (NX * NY);
+    int kax = 0;
+    for (int e = 1; e < 3; e++)
+        if (fabs(n[e]) > fabs(n[kax])) kax = e;
+    int k1 = (kax == 0) ? 1 : 0, k2 = (kax == 2) ? 1 : 2;
+    double s = n[kax] > 0.0 ? 1.0 : -1.0;
+    double dist[2] = {(s - b[kax]) / n[kax], (2.0 * s - b[kax]) / n[kax]};
+    double uv[2];
+    int ok = 1, near[3] = {0, 0, 0};
+    for (int m = 0; m < 2 && ok; m++) {
+        double P[3];
+        for (int e = 0; e < 3; e++) P[e] = b[e] + dist[m] * n[e];
+        int c1 = (int)floor(P[k1] + 0.5), c2 = (int)floor(P[k2] + 0.5);
+        double x1 = P[k1] - c1, x2 = P[k2] - c2;
+        double L1[3] = {0.5 * x1 * (x1 - 1.0), 1.0 - x1 * x1, 0.5 * x1 * (x1 + 1.0)};
+        double L2[3] = {0.5 * x2 * (x2 - 1.0), 1.0 - x2 * x2, 0.5 * x2 * (x2 + 1.0)};
+        if (m == 0) {
+            near[kax] = ci[kax] + (int)s;
+            near[k1] = ci[k1] + c1;
+            near[k2] = ci[k2] + c2;
+        }
+        double v = 0.0;
+        for (int q1 = -1; q1 <= 1 && ok; q1++)
+            for (int q2 = -1; q2 <= 1; q2++) {
+                int id[3];
+                id[kax] = ci[kax] + (m + 1) * (int)s;
+                id[k1] = ci[k1] + c1 + q1;
+                id[k2] = ci[k2] + c2 + q2;
+                if (!avail(g, geo, id[0], id[1], id[2])) { ok = 0; break; }
+                v += L1[q1 + 1] * L2[q2 + 1] * uq[cidx(g, id[0], id[1], id[2])];
+            }
+        uv[m] = v;
+    }
+    const double h = g->h;
+    if (ok) {
+        double d1 = dist[0], d2 = dist[1];
+        return (d2 * d2 * uv[0] - d1 * d1 * uv[1]) / (d1 * d2 * (d2 - d1)) / h;
+    }
+    if (avail(g, geo, near[0], near[1], near[2]))
+        return uq[cidx(g, near[0], near[1], near[2])] / (dist[0] * h);
+    return 0.0;
+}
+
+/* Explicit viscous term V = (1/rho) div(eta (grad u)^T) (Eq. explicit-viscous)
+ * with face fluxes eta_f d u_d / d x_j, the EB wall flux from the wall-normal
+ * derivative, and the same hybrid redistribution as the convective term. */
+void og_viscous_explicit(const og_grid *g, const og_geom *geo, const og_params *p,
+                         const double *u, const double *eta, double *V)
+{
+    size_t N3 = og_ncell(g);
+    const double h = g->h;
+    double *G = malloc(9 * N3 * sizeof(double));
+    og_cell_gradient(g, geo, u, G);
+    double *DC = malloc(3 * N3 * sizeof(double)), *D = malloc(N3 * sizeof(double));
+    double *dudn = calloc(3 * N3, sizeof(double));
+    for (size_t c = 0; c < N3; c++)
+        if (geo->flag[c] == 2 && geo->area[c] > 0.0)
+            for (int q = 0; q < 3; q++) dudn[q * N3 + c] = og_wall_dudn(g, geo, u, (int)c, q);
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                for (int jj = 0; jj < 3; jj++) DC[jj * N3 + c] = 0.0;
+                if (geo->alpha[c] <= 0.0) continue;
+                for (int jj = 0; jj < 3; jj++) {
+                    double s = 0.0;
+                    for (int d = 0; d < 3; d++)
+                        for (int hs = 0; hs < 2; hs++) {
+                            int id[3] = {i, j, k};
+                            id[d] += hs;
+                            size_t f = fidx(g, d, id[0], id[1], id[2]);
+                            double a = farr(geo, d)[f];
+                            if (a <= 0.0) continue;
+                            double T;
+                            if (id[d] == 0 || id[d] == g->n[d]) {
+                                int side = 2 * d + hs;
+                                double val;
+                                if (side_dirichlet(g, side, d, &val)) {
+                                    double ud = u[d * N3 + c];
+                                    T = (jj == d) ? eta[c] * (hs ? (val - ud) : (ud - val)) / (0.5 * h) : 0.0;
+                                } else {
+                                    T = (jj == d) ? 0.0 : eta[c] * G[(3 * jj + d) * N3 + c];
+                                }
+                            } else {
+                                int L[3] = {id[0], id[1], id[2]};
+                                L[d] -= 1;
+                                size_t cL = cidx(g, L[0], L[1], L[2]);
+                                size_t cR = cidx(g, id[0], id[1], id[2]);
+                                double ef = 0.5 * (eta[cL] + eta[cR]);
+                                double der = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) / h
+                                                       : 0.5 * (G[(3 * jj + d) * N3 + cL] +
+                                                                G[(3 * jj + d) * N3 + cR]);
+                                T = ef * der;
+                            }
+                            s += (hs ? 1.0 : -1.0) * a * T;
+                        }
+                    if (geo->flag[c] == 2 && geo->area[c] > 0.0) {
+                        double nd = 0.0;
+                        for (int q = 0; q < 3; q++) nd += geo->nrm[q * N3 + c] * dudn[q * N3 + c];
+                        /* outward normal of the fluid region on the EB is -n */
+                        s += -eta[c] * geo->nrm[jj * N3 + c] * nd * geo->area[c];
+                    }
+                    DC[jj * N3 + c] = s / (geo->alpha[c] * h);
+                }
+            }
+    for (int q = 0; q < 3; q++) {
+        og_redistribute(g, geo, DC + q * N3, D);
+        for (size_t c = 0; c < N3; c++) V[q * N3 + c] = D[c] / p->rho;
+    }
+    free(G); free(DC); free(D); free(dudn);
+}
+
+void og_derived(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                double *C, double *eta, double *V, double *srate, og_stats *st)
+{
+    size_t N3 = og_ncell(g);
+    size_t nft = nface(g, 0) + nface(g, 1) + nface(g, 2);
+    double *uf = malloc(nft * sizeof(double)), *phi = malloc(N3 * sizeof(double));
+    double res = 0.0;
+    og_face_states(g, geo, u, uf);
+    int it = og_mac_project(g, geo, uf, phi, p->tol, p->max_iters, &res);
+    if (st) { st->iters[0] = it; st->res[0] = res; }
+    og_convective(g, geo, u, uf, C);
+    og_strain_eta(g, geo, p, u, eta, srate);
+    og_viscous_explicit(g, geo, p, u, eta, V);
+    free(uf);
+    free(phi);
+}
+
+/* Eqs. cfl:dt, cfl:convective, cfl:forcing, cfl:viscous:new. */
+double og_timestep(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                   const double *f)
+{
+    size_t N3 = og_ncell(g);
+    const double h = g->h;
+    double cc = 0.0, cf2 = 0.0;
+    for (size_t c = 0; c < N3; c++) {
+        if (geo->alpha[c] <= 0.0) continue;
+        double v = (fabs(u[c]) + fabs(u[N3 + c]) + fabs(u[2 * N3 + c])) / h;
+        if (v > cc) cc = v;
+        if (f) {
+            double w = (fabs(f[c]) + fabs(f[N3 + c]) + fabs(f[2 * N3 + c])) / h;
+            if (w > cf2) cf2 = w;
+        }
+    }
+    double cv = 2.0 * p->mu / p->rho * (p->bi_cfl + 1.0) * (3.0 / (h * h));
+    double ccv = cc + cv;
+    return p->cfl / (0.5 * (ccv + sqrt(ccv * ccv + 4.0 * cf2)));
+}
+
+int og_viscous_solve(const og_grid *g, const og_geom *geo, const og_params *p, const double *eta,
+                     const double *psi, double dt, double *ut, og_stats *st, int slot)
+{
+    size_t N3 = og_ncell(g);
+    double *extra = malloc(N3 * sizeof(double)), *rb = malloc(N3 * sizeof(double));
+    double *b = malloc(N3 * sizeof(double));
+    double *B[3];
+    for (int d = 0; d < 3; d++) B[d] = malloc(nface(g, d) * sizeof(double));
+    int tot = 0;
+    for (int q = 0; q < 3; q++) {
+        og_visc_coeffs(g, geo, p, eta, dt, q, extra, B[0], B[1], B[2], rb);
+        for (size_t c = 0; c < N3; c++) {
+            b[c] = geo->alpha[c] > 0.0 ? geo->alpha[c] * psi[q * N3 + c] + rb[c] : 0.0;
+            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? psi[q * N3 + c] / p->rho : 0.0;
+        }
+        double res = 0.0;
+        int it = og_cc_solve(g, extra, B[0], B[1], B[2], b, ut + q * N3, p->tol, p->max_iters, &res);
+        if (st) { st->iters[slot + q] = it; st->res[slot + q] = res; }
+        tot += it;
+    }
+    free(extra); free(rb); free(b);
+    for (int d = 0; d < 3; d++) free(B[d]);
+    return tot;
+}
+
+int og_nodal_project(const og_grid *g, const og_geom *geo, const og_params *p, double dt,
+                     double *ut, double *pres, og_stats *st, int slot)
+{
+    size_t N3 = og_ncell(g), NN = og_nnode(g);
+    double *gp = malloc(3 * N3 * sizeof(double)), *rhs = malloc(NN * sizeof(double));
+    double coef = dt / p->rho;
+    og_cell_grad_p(g, pres, gp);
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++)
+            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? ut[q * N3 + c] + coef * gp[q * N3 + c] : 0.0;
+    og_nodal_rhs(g, geo, ut, rhs);
+    double res = 0.0;
+    int it = og_nodal_solve(g, geo, coef, rhs, pres, p->tol, p->max_iters, &res);
+    if (st) { st->iters[slot] = it; st->res[slot] = res; }
+    og_cell_grad_p(g, pres, gp);
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++)
+            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? ut[q * N3 + c] - coef * gp[q * N3 + c] : 0.0;
+    free(gp);
+    free(rhs);
+    return it;
+}
+
+void og_drag(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+             const double *pres, double *fz, double *yield_frac)
+{
+    size_t N3 = og_ncell(g);
+    double *eta = malloc(N3 * sizeof(double)), *sr = malloc(N3 * sizeof(double));
+    og_strain_eta(g, geo, p, u, eta, sr);
+    const double h = g->h;
+    double F = 0.0, vy = 0.0, vt = 0.0;
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                double al = geo->alpha[c];
+                if (al <= 0.0) continue;
+                vt += al;
+                if (eta[c] * sr[c] <= (1.0 + 1e-3) * p->tau0) vy += al;
+                if (geo->flag[c] != 2 || geo->area[c] <= 0.0) continue;
+                double n[3], b[3], gq[3];
+                for (int e = 0; e < 3; e++) {
+                    n[e] = geo->nrm[e * N3 + c];
+                    b[e] = geo->bcen[e * N3 + c];
+                    gq[e] = og_wall_dudn(g, geo, u, (int)c, e);
+                }
+                double gn = gq[0] * n[0] + gq[1] * n[1] + gq[2] * n[2];
+                double tz = eta[c] * (n[2] * gn + gq[2]);
+                double pb = 0.0;
+                for (int o = 0; o < 8; o++) {
+                    int oi = o & 1, oj = (o >> 1) & 1, ok = (o >> 2) & 1;
+                    double w = (oi ? b[0] + 0.5 : 0.5 - b[0]) * (oj ? b[1] + 0.5 : 0.5 - b[1]) *
+                               (ok ? b[2] + 0.5 : 0.5 - b[2]);
+                    pb += w * pres[nidx(g, i + oi, j + oj, k + ok)];
+                }
+                F += geo->area[c] * h * h * (tz - pb * n[2]);
+            }
+    *fz = F;
+    *yield_frac = vt > 0.0 ? vy / vt : 0.0;
+    free(eta);
+    free(sr);
+}
+
+/* Algorithm 1: predictor and corrector with a semi-implicit viscous update
+ * and a nodal projection each. */
+int og_advance(const og_grid *g, const og_geom *geo, const og_params *p, double *u, double *pres,
+               double dt_in, const double *f, og_stats *st)
+{
+    size_t N3 = og_ncell(g), V3 = 3 * N3;
+    double dt = dt_in > 0.0 ? dt_in : og_timestep(g, geo, p, u, f);
+    double *Cm = malloc(V3 * sizeof(double)), *Vm = malloc(V3 * sizeof(double));
+    double *Cs = malloc(V3 * sizeof(double)), *Vs = malloc(V3 * sizeof(double));
+    double *em = malloc(N3 * sizeof(double)), *es = malloc(N3 * sizeof(double));
+    double *psi = malloc(V3 * sizeof(double)), *ut = malloc(V3 * sizeof(double));
+    double *gp = malloc(V3 * sizeof(double)), *ps = malloc(og_nnode(g) * sizeof(double));
+    og_stats loc;
+    memset(&loc, 0, sizeof loc);
+    og_stats tmp;
+
+    /* Predictor */
+    og_derived(g, geo, p, u, Cm, em, Vm, NULL, &tmp);
+    loc.iters[0] = tmp.iters[0];
+    loc.res[0] = tmp.res[0];
+    og_cell_grad_p(g, pres, gp);
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++) {
+            size_t s = q * N3 + c;
+            double fq = f ? f[s] : 0.0;
+            psi[s] = geo->alpha[c] > 0.0
+                         ? p->rho * u[s] + dt * (p->rho * Cm[s] + Vm[s] - gp[s] + fq)
+                         : 0.0;
+        }
+    og_viscous_solve(g, geo, p, em, psi, dt, ut, &loc, 1);
+    memcpy(ps, pres, og_nnode(g) * sizeof(double));
+    og_nodal_project(g, geo, p, dt, ut, ps, &loc, 4);
+    /* ut now holds u*, ps holds p* */
+
+    /* Corrector */
+    og_derived(g, geo, p, ut, Cs, es, Vs, NULL, &tmp);
+    loc.iters[5] = tmp.iters[0];
+    loc.res[5] = tmp.res[0];
+    for (size_t s = 0; s < V3; s++) {
+        Cm[s] = 0.5 * (Cm[s] + Cs[s]);
+        Vm[s] = 0.5 * (Vm[s] + Vs[s]);
+    }
+    for (size_t c = 0; c < N3; c++) em[c] = 0.5 * (em[c] + es[c]);
+    og_cell_grad_p(g, ps, gp);
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++) {
+            size_t s = q * N3 + c;
+            double fq = f ? f[s] : 0.0;
+            psi[s] = geo->alpha[c] > 0.0
+                         ? p->rho * u[s] + dt * (p->rho * Cm[s] + Vm[s] - gp[s] + fq)
+                         : 0.0;
+        }
+    og_viscous_solve(g, geo, p, em, psi, dt, ut, &loc, 6);
+    memcpy(pres, ps, og_nnode(g) * sizeof(double));
+    og_nodal_project(g, geo, p, dt, ut, pres, &loc, 9);
+    memcpy(u, ut, V3 * sizeof(double));
+
+    loc.dt = dt;
+    og_drag(g, geo, p, u, pres, &loc.drag, &loc.yield_frac);
+    if (st) *st = loc;
+    free(Cm); free(Vm); free(Cs); free(Vs); free(em); free(es);
+    free(psi); free(ut); free(gp); free(ps);
+    return 0;
+}

@@ -1,0 +1,83 @@
+"""Pins of the oracle's whole step (Algorithm 1) and its reductions.
+
+- Uniform inflow through an empty box is an exact steady state.
+- A centred sphere in a noise-free channel keeps the mirror symmetries of the
+  problem (x -> 1-x, y -> 1-y, x <-> y): catches transposed indices.
+- Drag, pressure part: p = -z with u = 0 gives the buoyancy F_z = |body|
+  (Eq. drag-force with the surface normal pointing into the fluid), O(h^2).
+- Time step (Eqs. cfl:dt .. cfl:viscous:new): the classical limits.
+"""
+import numpy as np
+import pytest
+
+
+def test_uniform_flow_is_steady(O):
+    n = 8
+    g = O.Grid(n=(n, n, n), h=1.0 / n)
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_NONE))
+    u = np.zeros((3, g.ncell))
+    u[2] = 1.0
+    P = O.Params(tau0=1.0, m=1e3, bi_cfl=0.25)
+    u1, p1, st = O.advance(g, geo, P, u.ravel(), np.zeros(g.nnode))
+    assert np.abs(u1 - u.ravel()).max() < 1e-13
+    assert np.abs(p1).max() < 1e-10
+    assert st["dt"] == pytest.approx(0.5 / (1.0 / g.h + 2 * 1.25 * 3 / g.h ** 2), rel=1e-14)
+
+
+def test_sphere_channel_mirror_symmetry(O):
+    # odd n: no face lies on a mirror plane, where the upwind choice of a
+    # stationary shock (u_L = -u_R) would be decided by round-off
+    n = 13
+    g = O.Grid(n=(n, n, n), h=1.0 / n)
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_SPHERE, p=(0.5, 0.5, 0.5, 0.2)))
+    u = np.zeros((3, g.ncell))
+    u[2] = 1.0
+    u *= geo.alpha > 0
+    P = O.Params(tau0=1.0, m=1e3, bi_cfl=0.4, tol=1e-14)
+    p = np.zeros(g.nnode)
+    for _ in range(2):
+        u, p, st = O.advance(g, geo, P, u.ravel(), p)
+    U = u.reshape(3, n, n, n)  # (comp, z, y, x)
+    scale = np.abs(U).max()
+    tol = 1e-9 * scale
+    assert np.abs(U[0] + U[0][:, :, ::-1]).max() < tol      # u_x odd in x
+    assert np.abs(U[1] - U[1][:, :, ::-1]).max() < tol      # u_y even in x
+    assert np.abs(U[2] - U[2][:, :, ::-1]).max() < tol
+    assert np.abs(U[1] + U[1][:, ::-1, :]).max() < tol      # u_y odd in y
+    assert np.abs(U[0] - U[1].transpose(0, 2, 1)).max() < tol  # x <-> y swap
+    assert np.abs(U[2] - U[2].transpose(0, 2, 1)).max() < tol
+    Pn = p.reshape(g.nshape())
+    assert np.abs(Pn - Pn[:, :, ::-1]).max() < 1e-9 * np.abs(Pn).max()
+    assert st["drag"] > 0
+
+
+def test_buoyancy_drag_second_order(O):
+    r = 0.2
+    errs = []
+    for n in (16, 32, 64):
+        g = O.Grid(n=(n, n, n), h=1.0 / n)
+        geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_SPHERE, p=(0.5, 0.5, 0.5, r)))
+        zn = np.meshgrid(*[np.arange(n + 1) * g.h] * 3, indexing="ij")[0]
+        fz, yf = O.drag(g, geo, O.Params(tau0=1.0), np.zeros(3 * g.ncell), (-zn).ravel())
+        errs.append(abs(fz - 4.0 / 3.0 * np.pi * r ** 3))
+        assert yf == 1.0  # a fluid at rest is unyielded everywhere
+    assert np.log2(errs[1] / errs[2]) > 1.5, errs
+
+
+def test_timestep_limits(O):
+    n = 8
+    g = O.Grid(n=(n, n, n), h=1.0 / n)
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_NONE))
+    u = np.zeros((3, g.ncell))
+    u[0, 5] = -3.0
+    u[1, 5] = 2.0
+    inviscid = O.Params(mu=0.0, cfl=0.5)
+    assert O.timestep(g, geo, inviscid, u.ravel()) == pytest.approx(0.5 * g.h / 5.0, rel=1e-15)
+    still = O.Params(mu=2.0, rho=3.0, bi_cfl=9.0, cfl=0.5)
+    assert O.timestep(g, geo, still, 0 * u.ravel()) == pytest.approx(
+        0.5 * 3.0 * g.h ** 2 / (2 * 2.0 * 10.0 * 3.0), rel=1e-15)
+    f = np.zeros((3, g.ncell))
+    f[2, 7] = 4.0
+    forced = O.Params(mu=0.0, cfl=0.5)
+    assert O.timestep(g, geo, forced, 0 * u.ravel(), f.ravel()) == pytest.approx(
+        0.5 / np.sqrt(4.0 / g.h), rel=1e-14)
