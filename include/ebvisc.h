@@ -1,0 +1,176 @@
+/*
+ * ebvisc.h -- C-ABI of the GB300 (sm_103a) embedded-boundary viscoplastic
+ * flow library.
+ *
+ * The library advances the incompressible flow of a generalised Newtonian
+ * (Bingham / Herschel-Bulkley) fluid around an embedded boundary (EB) on a
+ * single uniform grid with the two-stage Runge-Kutta projection method of
+ * Sverdrup, Almgren & Nikiforakis, "An embedded boundary approach for efficient
+ * simulations of viscoplastic fluids in three dimensions" (arXiv:1905.07392),
+ * Algorithm 1.  All arithmetic runs in CUDA kernels; the host only launches
+ * kernels and reads back convergence scalars.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Cells are cubes of side h; the box is lo + [0, n[d] h].  Cell arrays hold
+ *    n0*n1*n2 values, x fastest, no ghost cells.  Vector cell fields hold the
+ *    three components one after another (SoA, 3*n0*n1*n2).  Face arrays with
+ *    normal d hold (n[d]+1) entries along d: x-faces (n0+1)*n1*n2, y-faces
+ *    n0*(n1+1)*n2, z-faces n0*n1*(n2+1); a "face triple" is the three arrays
+ *    concatenated in that order.  Nodal arrays (pressure) hold
+ *    (n0+1)*(n1+1)*(n2+1) values, x fastest.
+ *  - Field pointers are DEVICE pointers unless a name says _host.  The caller
+ *    owns them; the library never frees or keeps them past the call.
+ *  - The library owns its context: geometry, multigrid hierarchy and work
+ *    fields, allocated by ebv_create / ebv_build_geometry only.  Stepping
+ *    calls allocate nothing.
+ *  - Work is queued on the context's CUDA stream.  Calls that return host
+ *    values (stats, drag, dt) synchronise that stream; the solvers read one
+ *    residual scalar per iteration.
+ *  - Errors: every call returns an ebv_status; ebv_last_error gives a text.
+ *    There is no CPU fallback: without a CUDA device ebv_create fails with
+ *    EBV_ERR_CUDA.  Covered cells (volume fraction 0) read as 0 on output.
+ */
+#ifndef EBVISC_H
+#define EBVISC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ebv_ctx ebv_ctx;
+
+typedef enum {
+    EBV_OK = 0,
+    EBV_ERR_INVALID = -1,        /* bad argument, size or state */
+    EBV_ERR_CUDA = -2,           /* a CUDA call failed (text in ebv_last_error) */
+    EBV_ERR_NOT_CONVERGED = -3,  /* a linear solve hit max_iters above tol */
+    EBV_ERR_NAN = -5,            /* a residual became NaN or Inf */
+    EBV_ERR_GEOMETRY = -6        /* geometry missing or unsupported */
+} ebv_status;
+
+/* Box side types, sides ordered x-, x+, y-, y+, z-, z+. */
+enum { EBV_INFLOW = 0, EBV_OUTFLOW = 1, EBV_SLIP = 2, EBV_NOSLIP = 3 };
+/* Rheology (paper Table "Generalised Newtonian fluid models"). */
+enum { EBV_NEWTONIAN = 0, EBV_BINGHAM = 1, EBV_HERSCHEL_BULKLEY = 2, EBV_POWER_LAW = 3,
+       EBV_SOUZA_MENDES_DUTRA = 4 };
+/* Precision of the multigrid smoother and transfers; the Krylov vectors,
+ * residuals, solution accumulation and geometry are always FP64. */
+enum { EBV_FP64 = 0, EBV_FP32_REFINE = 1 };
+
+typedef struct {
+    int n[3];        /* cells per direction; each even down to the multigrid bottom */
+    double lo[3];    /* low corner of the box */
+    double h;        /* cell size */
+    int bc[6];       /* EBV_INFLOW / OUTFLOW / SLIP / NOSLIP per side */
+    double u_in[3];  /* inflow velocity (used on EBV_INFLOW sides) */
+} ebv_grid;
+
+typedef struct {
+    double rho;       /* density */
+    double mu;        /* plastic viscosity (Bingham) or consistency kappa (HB, power law) */
+    double tau0;      /* yield stress */
+    double m;         /* Papanastasiou parameter 1/epsilon; also floors ||gamma|| at 1/m for n < 1 */
+    double n_flow;    /* flow index n (HB, power law, SMD) */
+    double eta0;      /* zero-shear viscosity (Souza Mendes-Dutra) */
+    int model;        /* EBV_NEWTONIAN ... */
+    double cfl;       /* C_CFL of Eq. cfl:dt */
+    double bi_cfl;    /* Bingham number in the viscous limit, Eq. cfl:viscous:new */
+    double tol;       /* relative residual of every linear solve */
+    int max_iters;    /* Krylov iterations per solve */
+    double delta_min; /* lower bound (cell units) of the wall distance in the implicit EB flux */
+    int precision;    /* EBV_FP64 or EBV_FP32_REFINE */
+} ebv_params;
+
+typedef struct {
+    double dt;          /* time step used */
+    double drag;        /* z-force on the body at the end of the step (Eq. drag-force) */
+    double yield_frac;  /* fluid volume fraction with ||tau|| <= (1 + 1e-3) tau0 */
+    int iters[10];      /* Krylov iterations: MAC, visc x3, nodal (predictor); same (corrector) */
+    double res[10];     /* final relative residuals, same order */
+} ebv_step_stats;
+
+/* Implicit function of the body: > 0 in the fluid, <= 0 in the body. */
+typedef double (*ebv_implicit_fn)(const double x[3], void *user);
+
+/* Create a context on the current CUDA device, queueing work on `stream`
+ * (a cudaStream_t, NULL for the legacy default stream).  Allocates the work
+ * fields and multigrid hierarchy.  EBV_ERR_INVALID if a size is not
+ * coarsenable (see ebv_grid.n) or a parameter is out of range. */
+ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stream,
+                      ebv_ctx **out);
+/* Replace the parameters (rheology, tolerances, precision); no allocation. */
+ebv_status ebv_set_params(ebv_ctx *ctx, const ebv_params *params);
+
+/* EB geometry from an implicit function (paper Sec. "Embedded boundaries"):
+ * planar cut per cell, face apertures, volume fraction, EB area, unit normal
+ * into the fluid and EB centroid.  Evaluated on the host (the callback is a
+ * host function), uploaded once; builds the geometry-only solver data. */
+ebv_status ebv_build_geometry(ebv_ctx *ctx, ebv_implicit_fn fn, void *user);
+/* The same for a sphere of centre c and radius r (fluid outside). */
+ebv_status ebv_build_geometry_sphere(ebv_ctx *ctx, const double c[3], double r);
+/* The same for a half-space n.x > d (tests of planar cuts). */
+ebv_status ebv_build_geometry_plane(ebv_ctx *ctx, const double nrm[3], double d);
+/* Copy the geometry out (device pointers, any may be NULL):
+ * alpha, area (cells), ax/ay/az (faces), nrm/bcen (3 x cells; bcen relative
+ * to the cell centre in units of h), flag (cells: 0 covered, 1 regular, 2 cut). */
+ebv_status ebv_get_geometry(ebv_ctx *ctx, double *alpha, double *ax, double *ay, double *az,
+                            double *area, double *nrm, double *bcen, unsigned char *flag);
+
+/* Fused strain rate and apparent viscosity (paper Sec. "Strain rate tensor and
+ * apparent viscosity", Table of rheologies): central differences, one-sided
+ * quadratic differences next to covered cells; ||gamma|| = sqrt(tr(g g^T)/2).
+ * u: 3 x cells; eta: cells; srate: cells or NULL. */
+ebv_status ebv_update_viscosity(ebv_ctx *ctx, const double *u, double *eta, double *srate);
+
+/* Derived quantities of Algorithm 2 for a velocity u: convective term C,
+ * apparent viscosity eta and explicit viscous term V (3 x cells, cells,
+ * 3 x cells).  Runs the cell-centred projection internally; iters/res of that
+ * solve are written when the pointers are not NULL (host). */
+ebv_status ebv_derived(ebv_ctx *ctx, const double *u, double *C, double *eta, double *V,
+                       int *iters, double *res);
+
+/* Slope-limited, upwinded normal face velocities of u (Algorithm 2, lines
+ * 2-3), written as a face triple. */
+ebv_status ebv_face_states(ebv_ctx *ctx, const double *u, double *uf);
+/* Cell-centred projection (Eq. helmholtz and the Poisson equation after it):
+ * uf (face triple) is made discretely divergence free in place; phi (cells)
+ * receives the potential. */
+ebv_status ebv_solve_mac(ebv_ctx *ctx, double *uf, double *phi, int *iters, double *res);
+/* Semi-implicit viscous update (Eq. implicit-viscous) for the three
+ * components: (rho - dt div(eta grad)) ut = psi with the EB no-slip wall.
+ * eta: cells; psi, ut: 3 x cells.  stats->iters[1..3], res[1..3] if stats. */
+ebv_status ebv_solve_viscous(ebv_ctx *ctx, const double *eta, const double *psi, double dt,
+                             double *ut, ebv_step_stats *stats);
+/* Nodal projection (paper Sec. "Incompressibility constraint"): adds
+ * (dt/rho) grad p to ut, solves div((dt/rho) grad p_new) = div ut for nodal
+ * p_new, and writes ut -= (dt/rho) grad p_new.  ut: 3 x cells (in/out);
+ * p: nodes (in: old pressure, out: new).  stats->iters[4], res[4] if stats. */
+ebv_status ebv_solve_projection(ebv_ctx *ctx, double *ut, double *p, double dt,
+                                ebv_step_stats *stats);
+/* Time step of Eqs. cfl:dt .. cfl:viscous:new for velocity u and force f
+ * (3 x cells or NULL); result on the host. */
+ebv_status ebv_timestep(ebv_ctx *ctx, const double *u, const double *f, double *dt_host);
+/* One step of Algorithm 1 in place: u (3 x cells), p (nodes).  dt <= 0 takes
+ * the CFL step.  f: body force 3 x cells or NULL.  stats (host) or NULL. */
+ebv_status ebv_advance(ebv_ctx *ctx, double *u, double *p, double dt, const double *f,
+                       ebv_step_stats *stats);
+/* `steps` steps from HOST buffers: copies u_host, p_host to the device, runs
+ * the steps, copies the result back.  Uses the context's own device copies. */
+ebv_status ebv_advance_host(ebv_ctx *ctx, double *u_host, double *p_host, int steps, double dt,
+                            ebv_step_stats *last);
+/* Drag F_z on the body (Eq. drag-force, surface normal into the fluid) and the
+ * unyielded fluid volume fraction (||tau|| <= (1 + 1e-3) tau0), host outputs. */
+ebv_status ebv_drag(ebv_ctx *ctx, const double *u, const double *p, double *fz_host,
+                    double *yield_frac_host);
+
+/* Counters for the measurement harness: kernel launches queued since the
+ * context was created (host counter). */
+long long ebv_launch_count(const ebv_ctx *ctx);
+const char *ebv_last_error(const ebv_ctx *ctx);
+void ebv_destroy(ebv_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,421 @@
+// C-ABI entry points (include/ebvisc.h): context life cycle, geometry, the
+// stage operations of Algorithm 2 and the step of Algorithm 1.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "ebv_internal.cuh"
+
+using namespace ebv;
+
+struct ebv_ctx : public Ctx {};
+
+namespace {
+
+ebv_status check_params(const ebv_params *p, std::string &why)
+{
+    if (!(p->rho > 0.0)) { why = "rho must be > 0"; return EBV_ERR_INVALID; }
+    if (!(p->mu >= 0.0) || !(p->tau0 >= 0.0)) { why = "mu and tau0 must be >= 0"; return EBV_ERR_INVALID; }
+    if (!(p->m > 0.0)) { why = "m (1/epsilon) must be > 0"; return EBV_ERR_INVALID; }
+    if (p->model < EBV_NEWTONIAN || p->model > EBV_SOUZA_MENDES_DUTRA) { why = "unknown model"; return EBV_ERR_INVALID; }
+    if (p->model == EBV_SOUZA_MENDES_DUTRA && !(p->tau0 > 0.0)) { why = "SMD needs tau0 > 0"; return EBV_ERR_INVALID; }
+    if (!(p->tol > 0.0) || p->max_iters < 1) { why = "tol > 0 and max_iters >= 1 required"; return EBV_ERR_INVALID; }
+    if (!(p->cfl > 0.0)) { why = "cfl must be > 0"; return EBV_ERR_INVALID; }
+    if (!(p->delta_min > 0.0)) { why = "delta_min must be > 0"; return EBV_ERR_INVALID; }
+    if (p->precision != EBV_FP64 && p->precision != EBV_FP32_REFINE) { why = "unknown precision"; return EBV_ERR_INVALID; }
+    return EBV_OK;
+}
+
+template <class T>
+bool alloc(T **p, size_t n)
+{
+    return cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(T)) == cudaSuccess;
+}
+
+double sphere_fn(const double x[3], void *user)
+{
+    const double *s = (const double *)user;
+    double dx = x[0] - s[0], dy = x[1] - s[1], dz = x[2] - s[2];
+    return sqrt(dx * dx + dy * dy + dz * dz) - s[3];
+}
+double plane_fn(const double x[3], void *user)
+{
+    const double *s = (const double *)user;
+    return s[0] * x[0] + s[1] * x[1] + s[2] * x[2] - s[3];
+}
+
+ebv_status need_geom(Ctx *c)
+{
+    if (!c->have_geom) return c->fail(EBV_ERR_GEOMETRY, "no geometry built");
+    return EBV_OK;
+}
+
+__global__ void k_set_scalar(double *dst, double v)
+{
+    if (threadIdx.x == 0) *dst = v;
+}
+
+ebv_status set_dt(Ctx *c, double dt)
+{
+    if (!(dt > 0.0)) return c->fail(EBV_ERR_INVALID, "dt must be > 0");
+    EBV_LAUNCH(c, k_set_scalar, dim3(1), dim3(32), 0, c->dt_dev, dt);
+    return EBV_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        ebv_status s_ = (x);            \
+        if (s_ != EBV_OK) return s_;    \
+    } while (0)
+
+// Algorithm 2 for velocity u: C, eta, V (and the projected face velocities in c->uf).
+ebv_status derived(Ctx *c, const double *u, double *C, double *eta, double *V, int *it, double *res)
+{
+    TRY(launch_face_states(c, u, c->uf));
+    TRY(launch_mac_rhs(c, c->uf, c->rhs_c));
+    TRY(mac_solve(c, c->rhs_c, c->phi, it, res));
+    TRY(launch_mac_correct(c, c->uf, c->phi));
+    TRY(launch_convective(c, u, c->uf, C));
+    TRY(launch_strain_eta(c, u, eta, nullptr, c->G));
+    TRY(launch_viscous_explicit(c, u, eta, c->G, V));
+    return EBV_OK;
+}
+
+__global__ void k_init_guess(int n3, const uint8_t *flag, const double *psi, double rho, double *ut)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < 3 * n3; s += gridDim.x * blockDim.x) {
+        int c = s % n3;
+        ut[s] = flag[c] ? psi[s] / rho : 0.0;
+    }
+}
+
+ebv_status viscous_update(Ctx *c, const double *eta, const double *psi, double *ut, ebv_step_stats *st, int slot)
+{
+    const int N3 = ncell(c->g);
+    EBV_LAUNCH(c, k_init_guess, dim3(kReduceBlocks), dim3(256), 0, N3, c->flag, psi, c->prm.rho, ut);
+    for (int q = 0; q < 3; q++) {
+        int it = 0;
+        double res = 0.0;
+        TRY(visc_solve(c, eta, psi + (size_t)q * N3, q, ut + (size_t)q * N3, &it, &res));
+        if (st) { st->iters[slot + q] = it; st->res[slot + q] = res; }
+    }
+    return EBV_OK;
+}
+
+// Nodal projection of ut with old pressure p (in/out), dt on the device.
+ebv_status nodal_projection(Ctx *c, double *ut, double *p, ebv_step_stats *st, int slot)
+{
+    TRY(launch_add_gradp(c, ut, p, +1.0));
+    TRY(launch_nodal_rhs(c, ut, c->rhs_n));
+    int it = 0;
+    double res = 0.0;
+    TRY(nodal_solve(c, c->rhs_n, p, &it, &res));
+    if (st) { st->iters[slot] = it; st->res[slot] = res; }
+    TRY(launch_add_gradp(c, ut, p, -1.0));
+    return EBV_OK;
+}
+
+ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f, ebv_step_stats *st)
+{
+    const GridD &g = c->g;
+    const size_t N3 = ncell(g), NN = nnode(g);
+    ebv_step_stats loc;
+    memset(&loc, 0, sizeof loc);
+    TRY(launch_timestep(c, u, f, dt));
+    // Predictor
+    TRY(derived(c, u, c->Cm, c->em, c->Vm, &loc.iters[0], &loc.res[0]));
+    TRY(launch_psi(c, u, c->Cm, c->Vm, p, f, c->psi));
+    TRY(viscous_update(c, c->em, c->psi, c->ut, &loc, 1));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ps, p, NN * 8, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(nodal_projection(c, c->ut, c->ps, &loc, 4));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->us, c->ut, 3 * N3 * 8, cudaMemcpyDeviceToDevice, c->stream));
+    // Corrector
+    TRY(derived(c, c->us, c->Cs, c->es, c->Vs, &loc.iters[5], &loc.res[5]));
+    TRY(launch_average(c, c->Cm, c->Cs, (int)(3 * N3)));
+    TRY(launch_average(c, c->Vm, c->Vs, (int)(3 * N3)));
+    TRY(launch_average(c, c->em, c->es, (int)N3));
+    TRY(launch_psi(c, u, c->Cm, c->Vm, c->ps, f, c->psi));
+    TRY(viscous_update(c, c->em, c->psi, c->ut, &loc, 6));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(p, c->ps, NN * 8, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(nodal_projection(c, c->ut, p, &loc, 9));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(u, c->ut, 3 * N3 * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (st) {
+        EBV_CUDA_TRY(c, cudaMemcpyAsync(&c->scal_host[14], c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                                        c->stream));
+        TRY(launch_drag(c, u, p, &loc.drag, &loc.yield_frac));  // synchronises
+        loc.dt = c->scal_host[14];
+        *st = loc;
+    }
+    return EBV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stream, ebv_ctx **out)
+{
+    if (!grid || !params || !out) return EBV_ERR_INVALID;
+    *out = nullptr;
+    std::string why;
+    if (check_params(params, why) != EBV_OK) return EBV_ERR_INVALID;
+    for (int d = 0; d < 3; d++)
+        if (grid->n[d] < 1) return EBV_ERR_INVALID;
+    if (!(grid->h > 0.0)) return EBV_ERR_INVALID;
+    for (int s = 0; s < 6; s++)
+        if (grid->bc[s] < EBV_INFLOW || grid->bc[s] > EBV_NOSLIP) return EBV_ERR_INVALID;
+    long long nn = (long long)(grid->n[0] + 1) * (grid->n[1] + 1) * (grid->n[2] + 1);
+    if (nn >= (1LL << 31) / 9) return EBV_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return EBV_ERR_CUDA;
+
+    ebv_ctx *c = new (std::nothrow) ebv_ctx();
+    if (!c) return EBV_ERR_INVALID;
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)stream;
+    c->prm = *params;
+    GridD &g = c->g;
+    g.nx = grid->n[0]; g.ny = grid->n[1]; g.nz = grid->n[2];
+    g.h = grid->h;
+    for (int d = 0; d < 3; d++) { g.lo[d] = grid->lo[d]; g.u_in[d] = grid->u_in[d]; }
+    for (int s = 0; s < 6; s++) g.bc[s] = grid->bc[s];
+    const size_t N3 = ncell(g), NN = nnode(g), NF = nface(g, 0) + nface(g, 1) + nface(g, 2);
+    const size_t V = std::max(N3, NN);
+    bool ok = true;
+    ok &= alloc(&c->alpha, N3) && alloc(&c->ax, nface(g, 0)) && alloc(&c->ay, nface(g, 1)) &&
+          alloc(&c->az, nface(g, 2)) && alloc(&c->area, N3) && alloc(&c->nrm, 3 * N3) &&
+          alloc(&c->bcen, 3 * N3) && alloc(&c->flag, N3);
+    ok &= alloc(&c->Cm, 3 * N3) && alloc(&c->Vm, 3 * N3) && alloc(&c->Cs, 3 * N3) && alloc(&c->Vs, 3 * N3);
+    ok &= alloc(&c->em, N3) && alloc(&c->es, N3) && alloc(&c->psi, 3 * N3) && alloc(&c->ut, 3 * N3) &&
+          alloc(&c->us, 3 * N3);
+    ok &= alloc(&c->ps, NN) && alloc(&c->uf, NF) && alloc(&c->phi, N3) && alloc(&c->G, 9 * N3) &&
+          alloc(&c->DC, 3 * N3) && alloc(&c->dD, 3 * N3) && alloc(&c->Dh, 3 * N3) && alloc(&c->wts, N3) &&
+          alloc(&c->srate, N3) && alloc(&c->rhs_c, std::max(N3, (size_t)1)) && alloc(&c->rhs_n, NN);
+    ok &= alloc(&c->dt_dev, 1) && alloc(&c->cfl_max, 2);
+    ok &= alloc(&c->u_host_dev, 3 * N3) && alloc(&c->p_host_dev, NN);
+    ok &= alloc(&c->kr, V) && alloc(&c->kz, V) && alloc(&c->kp, V) && alloc(&c->kq, V);
+    ok &= alloc(&c->part, (size_t)1 << 20) && alloc(&c->scal, 32);
+    ok &= cudaMallocHost(&c->scal_host, 32 * sizeof(double)) == cudaSuccess;
+    c->vec_len = V;
+    if (!ok) {
+        ebv_destroy(c);
+        return EBV_ERR_CUDA;
+    }
+    if (setup_solvers(c) != EBV_OK) {
+        ebv_destroy(c);
+        return EBV_ERR_INVALID;
+    }
+    cudaMemsetAsync(c->scal, 0, 32 * sizeof(double), c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        ebv_destroy(c);
+        return EBV_ERR_CUDA;
+    }
+    *out = c;
+    return EBV_OK;
+}
+
+ebv_status ebv_set_params(ebv_ctx *c, const ebv_params *params)
+{
+    if (!c || !params) return EBV_ERR_INVALID;
+    std::string why;
+    if (check_params(params, why) != EBV_OK) return c->fail(EBV_ERR_INVALID, why);
+    bool prec_changed = params->precision != c->prm.precision;
+    c->prm = *params;
+    if (prec_changed && c->have_geom) return setup_geometry_solvers(c);
+    return EBV_OK;
+}
+
+ebv_status ebv_build_geometry(ebv_ctx *c, ebv_implicit_fn fn, void *user)
+{
+    if (!c || !fn) return EBV_ERR_INVALID;
+    TRY(build_geometry_host(c, fn, user));
+    TRY(setup_geometry_solvers(c));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return EBV_OK;
+}
+
+ebv_status ebv_build_geometry_sphere(ebv_ctx *c, const double cen[3], double r)
+{
+    if (!c || !cen || !(r > 0.0)) return EBV_ERR_INVALID;
+    double s[4] = {cen[0], cen[1], cen[2], r};
+    return ebv_build_geometry(c, sphere_fn, s);
+}
+
+ebv_status ebv_build_geometry_plane(ebv_ctx *c, const double nrm[3], double d)
+{
+    if (!c || !nrm) return EBV_ERR_INVALID;
+    double s[4] = {nrm[0], nrm[1], nrm[2], d};
+    return ebv_build_geometry(c, plane_fn, s);
+}
+
+ebv_status ebv_get_geometry(ebv_ctx *c, double *alpha, double *ax, double *ay, double *az, double *area,
+                            double *nrm, double *bcen, unsigned char *flag)
+{
+    if (!c) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    const GridD &g = c->g;
+    const size_t N3 = ncell(g);
+    cudaStream_t s = c->stream;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s) : cudaSuccess;
+    };
+    EBV_CUDA_TRY(c, cp(alpha, c->alpha, N3 * 8));
+    EBV_CUDA_TRY(c, cp(ax, c->ax, nface(g, 0) * 8));
+    EBV_CUDA_TRY(c, cp(ay, c->ay, nface(g, 1) * 8));
+    EBV_CUDA_TRY(c, cp(az, c->az, nface(g, 2) * 8));
+    EBV_CUDA_TRY(c, cp(area, c->area, N3 * 8));
+    EBV_CUDA_TRY(c, cp(nrm, c->nrm, 3 * N3 * 8));
+    EBV_CUDA_TRY(c, cp(bcen, c->bcen, 3 * N3 * 8));
+    EBV_CUDA_TRY(c, cp(flag, c->flag, N3));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(s));
+    return EBV_OK;
+}
+
+ebv_status ebv_update_viscosity(ebv_ctx *c, const double *u, double *eta, double *srate)
+{
+    if (!c || !u || !eta) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(launch_strain_eta(c, u, eta, srate, nullptr));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_derived(ebv_ctx *c, const double *u, double *C, double *eta, double *V, int *iters, double *res)
+{
+    if (!c || !u || !C || !eta || !V) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(derived(c, u, C, eta, V, iters, res));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_face_states(ebv_ctx *c, const double *u, double *uf)
+{
+    if (!c || !u || !uf) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(launch_face_states(c, u, uf));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_solve_mac(ebv_ctx *c, double *uf, double *phi, int *iters, double *res)
+{
+    if (!c || !uf || !phi) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(launch_mac_rhs(c, uf, c->rhs_c));
+    TRY(mac_solve(c, c->rhs_c, phi, iters, res));
+    TRY(launch_mac_correct(c, uf, phi));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_solve_viscous(ebv_ctx *c, const double *eta, const double *psi, double dt, double *ut,
+                             ebv_step_stats *st)
+{
+    if (!c || !eta || !psi || !ut) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(set_dt(c, dt));
+    TRY(viscous_update(c, eta, psi, ut, st, 1));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_solve_projection(ebv_ctx *c, double *ut, double *p, double dt, ebv_step_stats *st)
+{
+    if (!c || !ut || !p) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(set_dt(c, dt));
+    TRY(nodal_projection(c, ut, p, st, 4));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_timestep(ebv_ctx *c, const double *u, const double *f, double *dt_host)
+{
+    if (!c || !u || !dt_host) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(launch_timestep(c, u, f, 0.0));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(&c->scal_host[14], c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    *dt_host = c->scal_host[14];
+    return EBV_OK;
+}
+
+ebv_status ebv_advance(ebv_ctx *c, double *u, double *p, double dt, const double *f, ebv_step_stats *st)
+{
+    if (!c || !u || !p) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(advance_impl(c, u, p, dt, f, st));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_advance_host(ebv_ctx *c, double *u_host, double *p_host, int steps, double dt,
+                            ebv_step_stats *last)
+{
+    if (!c || !u_host || !p_host || steps < 0) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    const size_t N3 = ncell(c->g), NN = nnode(c->g);
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->u_host_dev, u_host, 3 * N3 * 8, cudaMemcpyHostToDevice, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->p_host_dev, p_host, NN * 8, cudaMemcpyHostToDevice, c->stream));
+    for (int s = 0; s < steps; s++)
+        TRY(advance_impl(c, c->u_host_dev, c->p_host_dev, dt, nullptr, (s == steps - 1) ? last : nullptr));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(u_host, c->u_host_dev, 3 * N3 * 8, cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(p_host, c->p_host_dev, NN * 8, cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return EBV_OK;
+}
+
+ebv_status ebv_drag(ebv_ctx *c, const double *u, const double *p, double *fz, double *yf)
+{
+    if (!c || !u || !p || !fz || !yf) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(launch_drag(c, u, p, fz, yf));
+    return EBV_OK;
+}
+
+long long ebv_launch_count(const ebv_ctx *c) { return c ? c->launches : 0; }
+
+const char *ebv_last_error(const ebv_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void ebv_destroy(ebv_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    void *ptrs[] = {c->alpha, c->ax, c->ay, c->az, c->area, c->nrm, c->bcen, c->flag, c->cut, c->Cm, c->Vm,
+                    c->Cs, c->Vs, c->em, c->es, c->psi, c->ut, c->us, c->ps, c->uf, c->phi, c->G, c->DC,
+                    c->dD, c->Dh, c->wts, c->dudn, c->srate, c->rhs_c, c->rhs_n, c->u_host_dev, c->p_host_dev,
+                    c->dt_dev, c->cfl_max, c->kr, c->kz, c->kp, c->kq, c->part, c->scal};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    CcHier *hs[2] = {&c->mac, &c->visc};
+    for (int h = 0; h < 2; h++) {
+        CcHier *H = hs[h];
+        for (int l = 0; l < H->L; l++) {
+            CcLevel &L = H->lv[l];
+            cudaFree(L.extra_d); cudaFree(L.extra_f);
+            for (int d = 0; d < 3; d++) { cudaFree(L.bf_d[d]); cudaFree(L.bf_f[d]); }
+            if (h == 0) cudaFree(L.cov);
+        }
+        cudaFree(H->binv);
+        cudaFree(H->bmat);
+    }
+    for (int l = 0; l < c->nd.L; l++) {
+        NdLevel &L = c->nd.lv[l];
+        if (l) cudaFree(L.alpha_d);
+        cudaFree(L.alpha_f);
+        cudaFree(L.act);
+    }
+    cudaFree(c->nd.binv);
+    cudaFree(c->nd.bmat);
+    for (int l = 0; l < kMaxLevels; l++) {
+        cudaFree(c->lx[l]); cudaFree(c->lb[l]); cudaFree(c->lr[l]); cudaFree(c->ld[l]); cudaFree(c->lt[l]);
+    }
+    if (c->scal_host) cudaFreeHost(c->scal_host);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+// Internal declarations of the sm_103a library behind include/ebvisc.h.
+//
+// Data layout (device, all no-ghost, x fastest):
+//   cell arrays n0*n1*n2; x-faces (n0+1)*n1*n2; y-faces n0*(n1+1)*n2;
+//   z-faces n0*n1*(n2+1); nodes (n0+1)*(n1+1)*(n2+1).
+// Cell availability for stencils is "inside the box and flag != 0".
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ebvisc.h"
+
+namespace ebv {
+
+constexpr int kMaxLevels = 16;
+constexpr int kBottomMax = 512;      // largest dense bottom system (unknowns)
+constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs; fixed for determinism
+
+struct GridD {
+    int nx, ny, nz;
+    double h;
+    double lo[3];
+    int bc[6];
+    double u_in[3];
+};
+
+struct GeomD {
+    const double *alpha, *ax, *ay, *az, *area, *nrm, *bcen;
+    const uint8_t *flag;
+    const int *cut;   // linear indices of cut cells with EB area > 0
+    int ncut;
+    int ncell;
+};
+
+struct ParamsD {
+    double rho, mu, tau0, m, n_flow, eta0;
+    int model;
+    double delta_min;
+};
+
+__host__ __device__ inline int cidx(const GridD &g, int i, int j, int k)
+{
+    return (k * g.ny + j) * g.nx + i;
+}
+__host__ __device__ inline int nidx(const GridD &g, int i, int j, int k)
+{
+    return (k * (g.ny + 1) + j) * (g.nx + 1) + i;
+}
+// Face with normal d whose low corner has integer position (i,j,k).
+__host__ __device__ inline int fidx(const GridD &g, int d, int i, int j, int k)
+{
+    if (d == 0) return (k * g.ny + j) * (g.nx + 1) + i;
+    if (d == 1) return (k * (g.ny + 1) + j) * g.nx + i;
+    return (k * g.ny + j) * g.nx + i;
+}
+__host__ __device__ inline int nface(const GridD &g, int d)
+{
+    return (g.nx + (d == 0)) * (g.ny + (d == 1)) * (g.nz + (d == 2));
+}
+__host__ __device__ inline int ncell(const GridD &g) { return g.nx * g.ny * g.nz; }
+__host__ __device__ inline int nnode(const GridD &g) { return (g.nx + 1) * (g.ny + 1) * (g.nz + 1); }
+__host__ __device__ inline int dimn(const GridD &g, int d) { return d == 0 ? g.nx : (d == 1 ? g.ny : g.nz); }
+
+__device__ inline bool inbox(const GridD &g, int i, int j, int k)
+{
+    return (unsigned)i < (unsigned)g.nx && (unsigned)j < (unsigned)g.ny && (unsigned)k < (unsigned)g.nz;
+}
+__device__ inline bool avail(const GridD &g, const uint8_t *flag, int i, int j, int k)
+{
+    return inbox(g, i, j, k) && flag[cidx(g, i, j, k)] != 0;
+}
+
+// Dirichlet value of velocity component `comp` on box side `side`; false for Neumann.
+__host__ __device__ inline bool side_dirichlet(const GridD &g, int side, int comp, double *val)
+{
+    int d = side >> 1;
+    switch (g.bc[side]) {
+    case EBV_INFLOW: *val = g.u_in[comp]; return true;
+    case EBV_NOSLIP: *val = 0.0; return true;
+    case EBV_SLIP: *val = 0.0; return comp == d;
+    default: *val = 0.0; return false;
+    }
+}
+
+// Apparent viscosity of the rheology table.
+__device__ inline double eta_of(const ParamsD &p, double sr)
+{
+    double yield = (sr > 0.0) ? -expm1(-p.m * sr) / sr : p.m;
+    double srf = sr > 1.0 / p.m ? sr : 1.0 / p.m;
+    switch (p.model) {
+    case EBV_NEWTONIAN: return p.mu;
+    case EBV_BINGHAM: return p.mu + p.tau0 * yield;
+    case EBV_HERSCHEL_BULKLEY: return p.mu * pow(srf, p.n_flow - 1.0) + p.tau0 * yield;
+    case EBV_POWER_LAW: return p.mu * pow(srf, p.n_flow - 1.0);
+    case EBV_SOUZA_MENDES_DUTRA: {
+        double y2 = (sr > 0.0) ? -expm1(-p.eta0 * sr / p.tau0) / sr : p.eta0 / p.tau0;
+        return p.mu * pow(srf, p.n_flow - 1.0) + p.tau0 * y2;
+    }
+    }
+    return p.mu;
+}
+
+inline dim3 block3() { return dim3(32, 4, 2); }
+inline dim3 grid3(int nx, int ny, int nz) { return dim3((nx + 31) / 32, (ny + 3) / 4, (nz + 1) / 2); }
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+struct CcLevel {
+    GridD g;            // dims and h of this level (bc shared)
+    double *extra_d = nullptr, *bf_d[3] = {nullptr, nullptr, nullptr};
+    float *extra_f = nullptr, *bf_f[3] = {nullptr, nullptr, nullptr};
+    uint8_t *cov = nullptr;  // 1 where the cell is covered (identity row)
+};
+
+struct CcHier {
+    int L = 0;                 // number of levels (level L-1 is the bottom)
+    CcLevel lv[kMaxLevels];
+    double *binv = nullptr;    // bottom inverse, nb x nb
+    double *bmat = nullptr;    // scratch for the bottom factorisation, nb x 2nb
+    int nb = 0;
+};
+
+struct NdLevel {
+    GridD g;                     // cell dims of this level
+    double *alpha_d = nullptr;   // cell volume fractions at this level
+    float *alpha_f = nullptr;
+    uint8_t *act = nullptr;      // 1 for active nodes
+    double lam_max = 2.0;        // bound of the spectrum of D^-1 A
+};
+
+struct NdHier {
+    int L = 0;
+    NdLevel lv[kMaxLevels];
+    double *binv = nullptr;      // bottom inverse for the unit-coefficient operator
+    double *bmat = nullptr;
+    int nb = 0;
+};
+
+struct Ctx {
+    GridD g;
+    ebv_params prm;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    long long launches = 0;
+    int device = 0;
+
+    bool have_geom = false;
+    // geometry (device)
+    double *alpha = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr, *area = nullptr;
+    double *nrm = nullptr, *bcen = nullptr;
+    uint8_t *flag = nullptr;
+    int *cut = nullptr;
+    int ncut = 0;
+
+    // work fields (device)
+    double *Cm = nullptr, *Vm = nullptr, *Cs = nullptr, *Vs = nullptr;
+    double *em = nullptr, *es = nullptr, *psi = nullptr, *ut = nullptr, *us = nullptr;
+    double *ps = nullptr, *uf = nullptr, *phi = nullptr, *G = nullptr, *DC = nullptr;
+    double *dD = nullptr, *Dh = nullptr, *wts = nullptr, *dudn = nullptr, *srate = nullptr;
+    double *rhs_c = nullptr;     // cell rhs scratch
+    double *rhs_n = nullptr;     // nodal rhs scratch
+    double *u_host_dev = nullptr, *p_host_dev = nullptr;  // device copies for host-buffer steps
+    double *dt_dev = nullptr;    // device-side time step
+    unsigned long long *cfl_max = nullptr;  // [0] convective, [1] forcing (bit patterns)
+
+    // solvers
+    CcHier mac, visc;
+    NdHier nd;
+    // per-level vectors, shared by the hierarchies (sized for the larger of cells/nodes)
+    void *lx[kMaxLevels] = {}, *lb[kMaxLevels] = {}, *lr[kMaxLevels] = {}, *ld[kMaxLevels] = {};
+    void *lt[kMaxLevels] = {};
+    // Krylov vectors (FP64)
+    double *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr;
+    double *part = nullptr;      // block partial sums
+    double *scal = nullptr;      // device scalars
+    double *scal_host = nullptr; // pinned mirror
+    size_t vec_len = 0;
+
+    ebv_status fail(ebv_status s, const std::string &m)
+    {
+        err = m;
+        return s;
+    }
+};
+
+// Launch bookkeeping: every kernel launch goes through this macro.
+#define EBV_LAUNCH(ctx, kern, grid, block, smem, ...)                                   \
+    do {                                                                                \
+        kern<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                  \
+        (ctx)->launches++;                                                              \
+    } while (0)
+
+#define EBV_CUDA_TRY(ctx, call)                                                          \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return (ctx)->fail(EBV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+inline GeomD geomd(const Ctx *c)
+{
+    GeomD q;
+    q.alpha = c->alpha; q.ax = c->ax; q.ay = c->ay; q.az = c->az; q.area = c->area;
+    q.nrm = c->nrm; q.bcen = c->bcen; q.flag = c->flag; q.cut = c->cut; q.ncut = c->ncut;
+    q.ncell = ncell(c->g);
+    return q;
+}
+inline ParamsD paramsd(const ebv_params &p)
+{
+    ParamsD q;
+    q.rho = p.rho; q.mu = p.mu; q.tau0 = p.tau0; q.m = p.m; q.n_flow = p.n_flow; q.eta0 = p.eta0;
+    q.model = p.model; q.delta_min = p.delta_min;
+    return q;
+}
+
+// geometry.cu
+ebv_status build_geometry_host(Ctx *c, ebv_implicit_fn fn, void *user);
+// fields.cu
+ebv_status launch_strain_eta(Ctx *c, const double *u, double *eta, double *srate, double *G);
+ebv_status launch_face_states(Ctx *c, const double *u, double *uf);
+ebv_status launch_mac_rhs(Ctx *c, const double *uf, double *b);
+ebv_status launch_mac_correct(Ctx *c, double *uf, const double *phi);
+ebv_status launch_convective(Ctx *c, const double *u, const double *uf, double *C);
+ebv_status launch_viscous_explicit(Ctx *c, const double *u, const double *eta, const double *G,
+                                   double *V);
+ebv_status launch_redistribute_into(Ctx *c, const double *DC, double sign, double div, double *out);
+ebv_status launch_psi(Ctx *c, const double *u, const double *C, const double *V, const double *p,
+                      const double *f, double *psi);
+ebv_status launch_add_gradp(Ctx *c, double *u, const double *p, double coef_sign);
+ebv_status launch_nodal_rhs(Ctx *c, const double *ut, double *b);
+ebv_status launch_timestep(Ctx *c, const double *u, const double *f, double dt_fixed);
+ebv_status launch_average(Ctx *c, double *a, const double *b, int n);
+ebv_status launch_drag(Ctx *c, const double *u, const double *p, double *fz, double *yf);
+ebv_status launch_zero_covered(Ctx *c, double *u, int ncomp);
+// solvers.cu
+ebv_status setup_solvers(Ctx *c);
+ebv_status setup_geometry_solvers(Ctx *c);
+ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res);
+ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int comp, double *x,
+                      int *iters, double *res);
+ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *res);
+// reductions (solvers.cu)
+ebv_status reduce_sum(Ctx *c, const double *part, int nblocks, double *out_dev);
+
+}  // namespace ebv

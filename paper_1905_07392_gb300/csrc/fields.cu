@@ -1,0 +1,844 @@
+// Streaming kernels of one Runge-Kutta stage (paper Algorithm 2 and the
+// explicit parts of Algorithm 1).  One thread per cell, face or node; the
+// kernels read their stencils straight from HBM/L2 (no ghost cells) and keep
+// every value FP64.
+#include "ebv_internal.cuh"
+
+namespace ebv {
+namespace {
+
+__device__ inline int3 unit(int d) { return make_int3(d == 0, d == 1, d == 2); }
+
+// Monotonised-central slope of f at (i,j,k) along d (difference across one
+// cell); zero unless both neighbours along d hold fluid.
+__device__ inline double mc_slope(const GridD &g, const uint8_t *flag, const double *f, int i,
+                                  int j, int k, int d)
+{
+    int3 e = unit(d);
+    if (!avail(g, flag, i + e.x, j + e.y, k + e.z) || !avail(g, flag, i - e.x, j - e.y, k - e.z))
+        return 0.0;
+    double f0 = f[cidx(g, i, j, k)];
+    double fp = f[cidx(g, i + e.x, j + e.y, k + e.z)];
+    double fm = f[cidx(g, i - e.x, j - e.y, k - e.z)];
+    double dl = f0 - fm, dr = fp - f0, dc = 0.5 * (fp - fm);
+    if (dl * dr <= 0.0) return 0.0;
+    double m = fabs(dc);
+    m = fmin(m, 2.0 * fabs(dl));
+    m = fmin(m, 2.0 * fabs(dr));
+    return dc > 0.0 ? m : -m;
+}
+
+// Godunov state of Burgers' equation from the two extrapolated normal velocities.
+__device__ inline double upwind_normal(double uL, double uR)
+{
+    if (uL > 0.0 && uL + uR > 0.0) return uL;
+    if (uR < 0.0 && uL + uR < 0.0) return uR;
+    return 0.0;
+}
+
+// Robust cell-centred derivative along d (paper Sec. "Strain rate tensor and
+// apparent viscosity"): central, one-sided quadratic next to a covered cell,
+// first order with a single neighbour, zero without one.
+__device__ inline double d_robust(const GridD &g, const uint8_t *flag, const double *f, int i,
+                                  int j, int k, int d)
+{
+    int3 e = unit(d);
+    const double h = g.h;
+    bool ip = avail(g, flag, i + e.x, j + e.y, k + e.z);
+    bool im = avail(g, flag, i - e.x, j - e.y, k - e.z);
+    double f0 = f[cidx(g, i, j, k)];
+    if (ip && im)
+        return (f[cidx(g, i + e.x, j + e.y, k + e.z)] - f[cidx(g, i - e.x, j - e.y, k - e.z)]) /
+               (2.0 * h);
+    if (im) {
+        double f1 = f[cidx(g, i - e.x, j - e.y, k - e.z)];
+        if (avail(g, flag, i - 2 * e.x, j - 2 * e.y, k - 2 * e.z)) {
+            double f2 = f[cidx(g, i - 2 * e.x, j - 2 * e.y, k - 2 * e.z)];
+            return (0.5 * f2 - 2.0 * f1 + 1.5 * f0) / h;
+        }
+        return (f0 - f1) / h;
+    }
+    if (ip) {
+        double f1 = f[cidx(g, i + e.x, j + e.y, k + e.z)];
+        if (avail(g, flag, i + 2 * e.x, j + 2 * e.y, k + 2 * e.z)) {
+            double f2 = f[cidx(g, i + 2 * e.x, j + 2 * e.y, k + 2 * e.z)];
+            return (-1.5 * f0 + 2.0 * f1 - 0.5 * f2) / h;
+        }
+        return (f1 - f0) / h;
+    }
+    return 0.0;
+}
+
+#define CELL_INDEX                                         \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;   \
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;   \
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;   \
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;       \
+    const int c = cidx(g, i, j, k);
+
+// ---- fused strain rate + apparent viscosity (optionally the gradient) -----
+template <bool kWriteG>
+__global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__restrict__ flag,
+                                                    const double *__restrict__ u, ParamsD p,
+                                                    double *__restrict__ eta,
+                                                    double *__restrict__ srate,
+                                                    double *__restrict__ G)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (flag[c] == 0) {
+        eta[c] = 0.0;
+        if (srate) srate[c] = 0.0;
+        if (kWriteG)
+            for (int q = 0; q < 9; q++) G[q * N3 + c] = 0.0;
+        return;
+    }
+    double Gm[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) Gm[d][q] = d_robust(g, flag, u + q * N3, i, j, k, d);
+    double s2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            double gam = Gm[d][q] + Gm[q][d];
+            s2 += gam * gam;
+        }
+    double sr = sqrt(0.5 * s2);
+    eta[c] = eta_of(p, sr);
+    if (srate) srate[c] = sr;
+    if (kWriteG)
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+#pragma unroll
+            for (int q = 0; q < 3; q++) G[(3 * d + q) * N3 + c] = Gm[d][q];
+}
+
+// ---- normal face velocities (slopes, extrapolation, upwinding) ------------
+__global__ void k_face_states(GridD g, int d, const uint8_t *__restrict__ flag,
+                              const double *__restrict__ ap, const double *__restrict__ u,
+                              double *__restrict__ uf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    if (i >= mx || j >= my || k >= mz) return;
+    const int f = fidx(g, d, i, j, k);
+    const int N3 = ncell(g);
+    const double *ud = u + d * N3;
+    int id[3] = {i, j, k};
+    double v = 0.0;
+    if (ap[f] > 0.0) {
+        if (id[d] == 0 || id[d] == dimn(g, d)) {
+            int hs = id[d] != 0;
+            int side = 2 * d + hs;
+            int cc[3] = {i, j, k};
+            cc[d] -= hs;
+            if (g.bc[side] == EBV_INFLOW) v = g.u_in[d];
+            else if (g.bc[side] == EBV_OUTFLOW) v = ud[cidx(g, cc[0], cc[1], cc[2])];
+        } else {
+            int3 e = unit(d);
+            double uL = ud[cidx(g, i - e.x, j - e.y, k - e.z)] +
+                        0.5 * mc_slope(g, flag, ud, i - e.x, j - e.y, k - e.z, d);
+            double uR = ud[cidx(g, i, j, k)] - 0.5 * mc_slope(g, flag, ud, i, j, k, d);
+            v = upwind_normal(uL, uR);
+        }
+    }
+    uf[f] = v;
+}
+
+// ---- cell-centred projection: right-hand side and face correction ---------
+__global__ void k_mac_rhs(GridD g, const uint8_t *__restrict__ flag, const double *__restrict__ ax,
+                          const double *__restrict__ ay, const double *__restrict__ az,
+                          const double *__restrict__ ufx, const double *__restrict__ ufy,
+                          const double *__restrict__ ufz, double *__restrict__ b)
+{
+    CELL_INDEX
+    if (flag[c] == 0) { b[c] = 0.0; return; }
+    const double *A[3] = {ax, ay, az};
+    const double *U[3] = {ufx, ufy, ufz};
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        int3 e = unit(d);
+        int flo = fidx(g, d, i, j, k), fhi = fidx(g, d, i + e.x, j + e.y, k + e.z);
+        s += A[d][fhi] * U[d][fhi] - A[d][flo] * U[d][flo];
+    }
+    b[c] = -s / g.h;
+}
+
+__global__ void k_mac_correct(GridD g, int d, const double *__restrict__ ap,
+                              const double *__restrict__ phi, double *__restrict__ uf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    if (i >= mx || j >= my || k >= mz) return;
+    const int f = fidx(g, d, i, j, k);
+    if (ap[f] <= 0.0) return;
+    int id[3] = {i, j, k};
+    if (id[d] == 0 || id[d] == dimn(g, d)) {
+        int hs = id[d] != 0;
+        if (g.bc[2 * d + hs] != EBV_OUTFLOW) return;
+        int cc[3] = {i, j, k};
+        cc[d] -= hs;
+        double pc = phi[cidx(g, cc[0], cc[1], cc[2])];
+        double grad = hs ? (0.0 - pc) / (0.5 * g.h) : (pc - 0.0) / (0.5 * g.h);
+        uf[f] -= grad;
+    } else {
+        int3 e = unit(d);
+        uf[f] -= (phi[cidx(g, i, j, k)] - phi[cidx(g, i - e.x, j - e.y, k - e.z)]) / g.h;
+    }
+}
+
+// ---- convective flux divergence (conservative part D^C) -------------------
+__global__ void __launch_bounds__(256) k_convective_dc(GridD g, const uint8_t *__restrict__ flag,
+                                                       const double *__restrict__ alpha,
+                                                       const double *__restrict__ ax,
+                                                       const double *__restrict__ ay,
+                                                       const double *__restrict__ az,
+                                                       const double *__restrict__ u,
+                                                       const double *__restrict__ uf,
+                                                       double *__restrict__ DC)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (flag[c] == 0) {
+        for (int q = 0; q < 3; q++) DC[q * N3 + c] = 0.0;
+        return;
+    }
+    const double *A[3] = {ax, ay, az};
+    const double *U[3] = {uf, uf + nface(g, 0), uf + nface(g, 0) + nface(g, 1)};
+    for (int q = 0; q < 3; q++) {
+        const double *uq = u + q * N3;
+        double s = 0.0;
+        for (int d = 0; d < 3; d++) {
+            int3 e = unit(d);
+            for (int hs = 0; hs < 2; hs++) {
+                int fi = i + hs * e.x, fj = j + hs * e.y, fk = k + hs * e.z;
+                int f = fidx(g, d, fi, fj, fk);
+                double a = A[d][f];
+                if (a <= 0.0) continue;
+                int pos = d == 0 ? fi : (d == 1 ? fj : fk);
+                double w = U[d][f], state;
+                if (pos == 0 || pos == dimn(g, d)) {
+                    state = (g.bc[2 * d + hs] == EBV_INFLOW) ? g.u_in[q] : uq[c];
+                } else {
+                    int Li = fi - e.x, Lj = fj - e.y, Lk = fk - e.z;
+                    double sL = uq[cidx(g, Li, Lj, Lk)] + 0.5 * mc_slope(g, flag, uq, Li, Lj, Lk, d);
+                    double sR = uq[cidx(g, fi, fj, fk)] - 0.5 * mc_slope(g, flag, uq, fi, fj, fk, d);
+                    state = w > 0.0 ? sL : (w < 0.0 ? sR : 0.5 * (sL + sR));
+                }
+                s += (hs ? 1.0 : -1.0) * a * state * w;
+            }
+        }
+        DC[q * N3 + c] = s / (alpha[c] * g.h);
+    }
+}
+
+// ---- hybrid flux divergence and redistribution (3 components) -------------
+// Pass 1: D^H and the excess dD, with the weight w = 1 / sum of neighbour alpha.
+__global__ void __launch_bounds__(256) k_redist_a(GridD g, const uint8_t *__restrict__ flag,
+                                                  const double *__restrict__ alpha,
+                                                  const double *__restrict__ DC,
+                                                  double *__restrict__ D, double *__restrict__ dD,
+                                                  double *__restrict__ w)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (flag[c] == 0) {
+        for (int q = 0; q < 3; q++) { D[q * N3 + c] = 0.0; dD[q * N3 + c] = 0.0; }
+        w[c] = 0.0;
+        return;
+    }
+    const double al = alpha[c];
+    if (flag[c] == 1) {  // alpha = 1: D^H = D^C, no excess
+        for (int q = 0; q < 3; q++) { D[q * N3 + c] = DC[q * N3 + c]; dD[q * N3 + c] = 0.0; }
+        double sa = 0.0;
+        for (int dk = -1; dk <= 1; dk++)
+            for (int dj = -1; dj <= 1; dj++)
+                for (int di = -1; di <= 1; di++) {
+                    if (!di && !dj && !dk) continue;
+                    if (!avail(g, flag, i + di, j + dj, k + dk)) continue;
+                    sa += alpha[cidx(g, i + di, j + dj, k + dk)];
+                }
+        w[c] = sa > 0.0 ? 1.0 / sa : 0.0;
+        return;
+    }
+    double sa = 0.0, sad[3] = {0.0, 0.0, 0.0};
+    for (int dk = -1; dk <= 1; dk++)
+        for (int dj = -1; dj <= 1; dj++)
+            for (int di = -1; di <= 1; di++) {
+                if (!di && !dj && !dk) continue;
+                if (!avail(g, flag, i + di, j + dj, k + dk)) continue;
+                int c2 = cidx(g, i + di, j + dj, k + dk);
+                double a2 = alpha[c2];
+                sa += a2;
+                for (int q = 0; q < 3; q++) sad[q] += a2 * DC[q * N3 + c2];
+            }
+    for (int q = 0; q < 3; q++) {
+        double dcq = DC[q * N3 + c];
+        double dnc = sa > 0.0 ? sad[q] / sa : dcq;
+        D[q * N3 + c] = al * dcq + (1.0 - al) * dnc;
+        dD[q * N3 + c] = al * (1.0 - al) * (dcq - dnc);
+    }
+    w[c] = sa > 0.0 ? 1.0 / sa : 0.0;
+}
+
+// Pass 2: add the neighbours' weighted excess; out = sign * D / div.
+__global__ void __launch_bounds__(256) k_redist_b(GridD g, const uint8_t *__restrict__ flag,
+                                                  const double *__restrict__ D,
+                                                  const double *__restrict__ dD,
+                                                  const double *__restrict__ w, double sign,
+                                                  double div, double *__restrict__ out)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (flag[c] == 0) {
+        for (int q = 0; q < 3; q++) out[q * N3 + c] = 0.0;
+        return;
+    }
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int dk = -1; dk <= 1; dk++)
+        for (int dj = -1; dj <= 1; dj++)
+            for (int di = -1; di <= 1; di++) {
+                if (!di && !dj && !dk) continue;
+                if (!avail(g, flag, i + di, j + dj, k + dk)) continue;
+                int c2 = cidx(g, i + di, j + dj, k + dk);
+                for (int q = 0; q < 3; q++) s[q] += w[c2] * dD[q * N3 + c2];
+            }
+    for (int q = 0; q < 3; q++) out[q * N3 + c] = sign * (D[q * N3 + c] + s[q]) / div;
+}
+
+// ---- wall-normal derivative at the EB centroid (Eqs. interpolation_distances, dudn)
+__global__ void k_wall_dudn(GridD g, GeomD geo, const double *__restrict__ u,
+                            double *__restrict__ dudn)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= geo.ncut) return;
+    const int N3 = geo.ncell;
+    const int c = geo.cut[t];
+    int ci[3] = {c % g.nx, (c / g.nx) % g.ny, c / (g.nx * g.ny)};
+    double n[3], b[3];
+    for (int e = 0; e < 3; e++) { n[e] = geo.nrm[e * N3 + c]; b[e] = geo.bcen[e * N3 + c]; }
+    int kax = 0;
+    if (fabs(n[1]) > fabs(n[kax])) kax = 1;
+    if (fabs(n[2]) > fabs(n[kax])) kax = 2;
+    const int k1 = (kax == 0) ? 1 : 0, k2 = (kax == 2) ? 1 : 2;
+    const double s = n[kax] > 0.0 ? 1.0 : -1.0;
+    const int si = n[kax] > 0.0 ? 1 : -1;
+    const double dist[2] = {(s - b[kax]) / n[kax], (2.0 * s - b[kax]) / n[kax]};
+    int cc1[2], cc2[2];
+    double L1[2][3], L2[2][3];
+    bool ok = true;
+    for (int m = 0; m < 2; m++) {
+        double P1 = b[k1] + dist[m] * n[k1], P2 = b[k2] + dist[m] * n[k2];
+        cc1[m] = (int)floor(P1 + 0.5);
+        cc2[m] = (int)floor(P2 + 0.5);
+        double x1 = P1 - cc1[m], x2 = P2 - cc2[m];
+        L1[m][0] = 0.5 * x1 * (x1 - 1.0); L1[m][1] = 1.0 - x1 * x1; L1[m][2] = 0.5 * x1 * (x1 + 1.0);
+        L2[m][0] = 0.5 * x2 * (x2 - 1.0); L2[m][1] = 1.0 - x2 * x2; L2[m][2] = 0.5 * x2 * (x2 + 1.0);
+        for (int q1 = -1; q1 <= 1 && ok; q1++)
+            for (int q2 = -1; q2 <= 1; q2++) {
+                int id[3];
+                id[kax] = ci[kax] + (m + 1) * si;
+                id[k1] = ci[k1] + cc1[m] + q1;
+                id[k2] = ci[k2] + cc2[m] + q2;
+                if (!avail(g, geo.flag, id[0], id[1], id[2])) { ok = false; break; }
+            }
+        if (!ok) break;
+    }
+    int near[3];
+    near[kax] = ci[kax] + si;
+    {
+        double P1 = b[k1] + dist[0] * n[k1], P2 = b[k2] + dist[0] * n[k2];
+        near[k1] = ci[k1] + (int)floor(P1 + 0.5);
+        near[k2] = ci[k2] + (int)floor(P2 + 0.5);
+    }
+    const bool near_ok = avail(g, geo.flag, near[0], near[1], near[2]);
+    for (int q = 0; q < 3; q++) {
+        const double *uq = u + q * N3;
+        double r;
+        if (ok) {
+            double uv[2];
+            for (int m = 0; m < 2; m++) {
+                double v = 0.0;
+                for (int q1 = -1; q1 <= 1; q1++)
+                    for (int q2 = -1; q2 <= 1; q2++) {
+                        int id[3];
+                        id[kax] = ci[kax] + (m + 1) * si;
+                        id[k1] = ci[k1] + cc1[m] + q1;
+                        id[k2] = ci[k2] + cc2[m] + q2;
+                        v += L1[m][q1 + 1] * L2[m][q2 + 1] * uq[cidx(g, id[0], id[1], id[2])];
+                    }
+                uv[m] = v;
+            }
+            double d1 = dist[0], d2 = dist[1];
+            r = (d2 * d2 * uv[0] - d1 * d1 * uv[1]) / (d1 * d2 * (d2 - d1)) / g.h;
+        } else if (near_ok) {
+            r = uq[cidx(g, near[0], near[1], near[2])] / (dist[0] * g.h);
+        } else {
+            r = 0.0;
+        }
+        dudn[q * geo.ncut + t] = r;
+    }
+}
+
+__device__ inline int find_cut(const int *cut, int ncut, int c)
+{
+    int lo = 0, hi = ncut - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = cut[mid];
+        if (v == c) return mid;
+        if (v < c) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// ---- explicit viscous term: D^C of eta (grad u)^T -------------------------
+__global__ void __launch_bounds__(256) k_viscous_dc(GridD g, GeomD geo, const double *__restrict__ u,
+                                                    const double *__restrict__ eta,
+                                                    const double *__restrict__ G,
+                                                    const double *__restrict__ dudn,
+                                                    double *__restrict__ DC)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (geo.flag[c] == 0) {
+        for (int q = 0; q < 3; q++) DC[q * N3 + c] = 0.0;
+        return;
+    }
+    const double *A[3] = {geo.ax, geo.ay, geo.az};
+    const double h = g.h;
+    int cut_t = -1;
+    double nd = 0.0;
+    if (geo.flag[c] == 2 && geo.area[c] > 0.0) {
+        cut_t = find_cut(geo.cut, geo.ncut, c);
+        if (cut_t >= 0)
+            for (int q = 0; q < 3; q++) nd += geo.nrm[q * N3 + c] * dudn[q * geo.ncut + cut_t];
+    }
+    for (int jj = 0; jj < 3; jj++) {
+        double s = 0.0;
+        for (int d = 0; d < 3; d++) {
+            int3 e = unit(d);
+            for (int hs = 0; hs < 2; hs++) {
+                int fi = i + hs * e.x, fj = j + hs * e.y, fk = k + hs * e.z;
+                int f = fidx(g, d, fi, fj, fk);
+                double a = A[d][f];
+                if (a <= 0.0) continue;
+                int pos = d == 0 ? fi : (d == 1 ? fj : fk);
+                double T;
+                if (pos == 0 || pos == dimn(g, d)) {
+                    double val;
+                    if (side_dirichlet(g, 2 * d + hs, d, &val)) {
+                        double ud = u[d * N3 + c];
+                        T = (jj == d) ? eta[c] * (hs ? (val - ud) : (ud - val)) / (0.5 * h) : 0.0;
+                    } else {
+                        T = (jj == d) ? 0.0 : eta[c] * G[(3 * jj + d) * N3 + c];
+                    }
+                } else {
+                    int cL = cidx(g, fi - e.x, fj - e.y, fk - e.z), cR = cidx(g, fi, fj, fk);
+                    double ef = 0.5 * (eta[cL] + eta[cR]);
+                    double der = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) / h
+                                           : 0.5 * (G[(3 * jj + d) * N3 + cL] + G[(3 * jj + d) * N3 + cR]);
+                    T = ef * der;
+                }
+                s += (hs ? 1.0 : -1.0) * a * T;
+            }
+        }
+        if (cut_t >= 0) s += -eta[c] * geo.nrm[jj * N3 + c] * nd * geo.area[c];
+        DC[jj * N3 + c] = s / (geo.alpha[c] * h);
+    }
+}
+
+// Cell-centre gradient of the trilinear interpolant of nodal p, component d.
+__device__ inline double grad_p(const GridD &g, const double *p, int i, int j, int k, int d)
+{
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    double s = 0.0;
+    for (int q1 = 0; q1 < 2; q1++)
+        for (int q2 = 0; q2 < 2; q2++) {
+            int lo[3] = {i, j, k};
+            lo[t1] += q1;
+            lo[t2] += q2;
+            int hi[3] = {lo[0], lo[1], lo[2]};
+            hi[d] += 1;
+            s += p[nidx(g, hi[0], hi[1], hi[2])] - p[nidx(g, lo[0], lo[1], lo[2])];
+        }
+    return s / (4.0 * g.h);
+}
+
+// psi = rho u + dt (rho C + V - grad p + f)
+__global__ void k_psi(GridD g, const uint8_t *__restrict__ flag, const double *__restrict__ u,
+                      const double *__restrict__ C, const double *__restrict__ V,
+                      const double *__restrict__ p, const double *__restrict__ f,
+                      const double *__restrict__ dtp, double rho, double *__restrict__ psi)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    const double dt = *dtp;
+    for (int q = 0; q < 3; q++) {
+        int s = q * N3 + c;
+        if (flag[c] == 0) { psi[s] = 0.0; continue; }
+        double fq = f ? f[s] : 0.0;
+        psi[s] = rho * u[s] + dt * (rho * C[s] + V[s] - grad_p(g, p, i, j, k, q) + fq);
+    }
+}
+
+// u += sgn * (dt/rho) grad p on fluid cells; covered cells set to zero.
+__global__ void k_add_gradp(GridD g, const uint8_t *__restrict__ flag, double *__restrict__ u,
+                            const double *__restrict__ p, const double *__restrict__ dtp,
+                            double rho, double sgn)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    const double coef = *dtp / rho;
+    for (int q = 0; q < 3; q++) {
+        int s = q * N3 + c;
+        if (flag[c] == 0) { u[s] = 0.0; continue; }
+        double gq = grad_p(g, p, i, j, k, q);
+        u[s] = sgn > 0 ? u[s] + coef * gq : u[s] - coef * gq;
+    }
+}
+
+__device__ inline bool node_dirichlet(const GridD &g, int i, int j, int k)
+{
+    int id[3] = {i, j, k};
+    for (int d = 0; d < 3; d++) {
+        if (id[d] == 0 && g.bc[2 * d] == EBV_OUTFLOW) return true;
+        if (id[d] == dimn(g, d) && g.bc[2 * d + 1] == EBV_OUTFLOW) return true;
+    }
+    return false;
+}
+
+// Nodal right-hand side (weak divergence of ut plus the inflow boundary
+// integral), divided by dt/rho so the solve uses the unit-coefficient operator.
+__global__ void k_nodal_rhs(GridD g, GeomD geo, const double *__restrict__ ut,
+                            const double *__restrict__ dtp, double rho, double *__restrict__ b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int n = nidx(g, i, j, k);
+    const int N3 = ncell(g);
+    const double h = g.h;
+    bool act = !node_dirichlet(g, i, j, k);
+    if (act) {
+        bool any = false;
+        for (int oc = 0; oc < 8; oc++)
+            any |= avail(g, geo.flag, i - 1 + (oc & 1), j - 1 + ((oc >> 1) & 1), k - 1 + ((oc >> 2) & 1));
+        act = any;
+    }
+    if (!act) { b[n] = 0.0; return; }
+    double v = 0.0;
+    for (int oc = 0; oc < 8; oc++) {
+        int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+        if (!avail(g, geo.flag, ci, cj, ck)) continue;
+        int c = cidx(g, ci, cj, ck);
+        int o[3] = {i - ci, j - cj, k - ck};
+        for (int d = 0; d < 3; d++)
+            v += geo.alpha[c] * h * h * 0.25 * (o[d] ? 1.0 : -1.0) * ut[d * N3 + c];
+    }
+    int id[3] = {i, j, k};
+    const double *A[3] = {geo.ax, geo.ay, geo.az};
+    for (int d = 0; d < 3; d++)
+        for (int hs = 0; hs < 2; hs++) {
+            int side = 2 * d + hs;
+            if (g.bc[side] != EBV_INFLOW) continue;
+            if (id[d] != (hs ? dimn(g, d) : 0)) continue;
+            double sgn = hs ? 1.0 : -1.0;
+            int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+            for (int q1 = -1; q1 <= 0; q1++)
+                for (int q2 = -1; q2 <= 0; q2++) {
+                    int fid[3] = {i, j, k};
+                    fid[t1] += q1;
+                    fid[t2] += q2;
+                    if (fid[t1] < 0 || fid[t1] >= dimn(g, t1) || fid[t2] < 0 || fid[t2] >= dimn(g, t2))
+                        continue;
+                    double af = A[d][fidx(g, d, fid[0], fid[1], fid[2])];
+                    v -= sgn * g.u_in[d] * af * h * h * 0.25;
+                }
+        }
+    b[n] = v / (*dtp / rho);
+}
+
+// ---- time step --------------------------------------------------------------
+__global__ void k_cfl_max(GridD g, const uint8_t *__restrict__ flag, const double *__restrict__ u,
+                          const double *__restrict__ f, unsigned long long *out)
+{
+    const int N3 = ncell(g);
+    double mc = 0.0, mf = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N3; c += gridDim.x * blockDim.x) {
+        if (flag[c] == 0) continue;
+        double v = (fabs(u[c]) + fabs(u[N3 + c]) + fabs(u[2 * N3 + c])) / g.h;
+        mc = fmax(mc, v);
+        if (f) mf = fmax(mf, (fabs(f[c]) + fabs(f[N3 + c]) + fabs(f[2 * N3 + c])) / g.h);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mc = fmax(mc, __shfl_down_sync(0xffffffffu, mc, o));
+        mf = fmax(mf, __shfl_down_sync(0xffffffffu, mf, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // non-negative doubles order like their bit patterns
+        atomicMax(out, (unsigned long long)__double_as_longlong(mc));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(mf));
+    }
+}
+
+__global__ void k_dt_final(const unsigned long long *mx, double cfl, double cv, double dt_fixed,
+                           double *dt)
+{
+    if (threadIdx.x != 0) return;
+    if (dt_fixed > 0.0) { *dt = dt_fixed; return; }
+    double cc = __longlong_as_double((long long)mx[0]);
+    double cf2 = __longlong_as_double((long long)mx[1]);
+    double ccv = cc + cv;
+    *dt = cfl / (0.5 * (ccv + sqrt(ccv * ccv + 4.0 * cf2)));
+}
+
+__global__ void k_average(double *a, const double *b, int n)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        a[s] = 0.5 * (a[s] + b[s]);
+}
+
+__global__ void k_zero_covered(GridD g, const uint8_t *__restrict__ flag, double *u, int ncomp)
+{
+    const int N3 = ncell(g);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N3; c += gridDim.x * blockDim.x)
+        if (flag[c] == 0)
+            for (int q = 0; q < ncomp; q++) u[q * N3 + c] = 0.0;
+}
+
+// ---- drag and yielded fraction -------------------------------------------
+__global__ void k_drag_terms(GridD g, GeomD geo, const double *__restrict__ eta,
+                             const double *__restrict__ dudn, const double *__restrict__ p,
+                             double *__restrict__ term)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= geo.ncut) return;
+    const int N3 = geo.ncell;
+    const int c = geo.cut[t];
+    const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+    double n[3], b[3], gq[3];
+    for (int e = 0; e < 3; e++) {
+        n[e] = geo.nrm[e * N3 + c];
+        b[e] = geo.bcen[e * N3 + c];
+        gq[e] = dudn[e * geo.ncut + t];
+    }
+    double gn = gq[0] * n[0] + gq[1] * n[1] + gq[2] * n[2];
+    double tz = eta[c] * (n[2] * gn + gq[2]);
+    double pb = 0.0;
+    for (int o = 0; o < 8; o++) {
+        int oi = o & 1, oj = (o >> 1) & 1, ok = (o >> 2) & 1;
+        double w = (oi ? b[0] + 0.5 : 0.5 - b[0]) * (oj ? b[1] + 0.5 : 0.5 - b[1]) *
+                   (ok ? b[2] + 0.5 : 0.5 - b[2]);
+        pb += w * p[nidx(g, i + oi, j + oj, k + ok)];
+    }
+    term[t] = geo.area[c] * g.h * g.h * (tz - pb * n[2]);
+}
+
+template <int kThreads>
+__device__ inline double block_sum(double v)
+{
+    __shared__ double sm[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < kThreads / 32 ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_yield_parts(int N3, const uint8_t *__restrict__ flag,
+                                                     const double *__restrict__ alpha,
+                                                     const double *__restrict__ eta,
+                                                     const double *__restrict__ sr, double tau0,
+                                                     double *__restrict__ part)
+{
+    double vy = 0.0, vt = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N3; c += gridDim.x * blockDim.x) {
+        if (flag[c] == 0) continue;
+        double a = alpha[c];
+        vt += a;
+        if (eta[c] * sr[c] <= (1.0 + 1e-3) * tau0) vy += a;
+    }
+    double sy = block_sum<256>(vy);
+    double st = block_sum<256>(vt);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sy;
+        part[gridDim.x + blockIdx.x] = st;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// Launchers
+// ===========================================================================
+
+ebv_status launch_strain_eta(Ctx *c, const double *u, double *eta, double *srate, double *G)
+{
+    const GridD &g = c->g;
+    if (G)
+        EBV_LAUNCH(c, k_strain_eta<true>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u,
+                   paramsd(c->prm), eta, srate, G);
+    else
+        EBV_LAUNCH(c, k_strain_eta<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u,
+                   paramsd(c->prm), eta, srate, nullptr);
+    return EBV_OK;
+}
+
+ebv_status launch_face_states(Ctx *c, const double *u, double *uf)
+{
+    const GridD &g = c->g;
+    const double *A[3] = {c->ax, c->ay, c->az};
+    size_t off = 0;
+    for (int d = 0; d < 3; d++) {
+        EBV_LAUNCH(c, k_face_states, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)),
+                   block3(), 0, g, d, c->flag, A[d], u, uf + off);
+        off += nface(g, d);
+    }
+    return EBV_OK;
+}
+
+ebv_status launch_mac_rhs(Ctx *c, const double *uf, double *b)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_mac_rhs, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->ax, c->ay, c->az,
+               uf, uf + nface(g, 0), uf + nface(g, 0) + nface(g, 1), b);
+    return EBV_OK;
+}
+
+ebv_status launch_mac_correct(Ctx *c, double *uf, const double *phi)
+{
+    const GridD &g = c->g;
+    const double *A[3] = {c->ax, c->ay, c->az};
+    size_t off = 0;
+    for (int d = 0; d < 3; d++) {
+        EBV_LAUNCH(c, k_mac_correct, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)),
+                   block3(), 0, g, d, A[d], phi, uf + off);
+        off += nface(g, d);
+    }
+    return EBV_OK;
+}
+
+ebv_status launch_redistribute_into(Ctx *c, const double *DC, double sign, double div, double *out)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_redist_a, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->alpha, DC,
+               c->Dh, c->dD, c->wts);
+    EBV_LAUNCH(c, k_redist_b, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->Dh, c->dD,
+               c->wts, sign, div, out);
+    return EBV_OK;
+}
+
+ebv_status launch_convective(Ctx *c, const double *u, const double *uf, double *C)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_convective_dc, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->alpha,
+               c->ax, c->ay, c->az, u, uf, c->DC);
+    return launch_redistribute_into(c, c->DC, -1.0, 1.0, C);
+}
+
+ebv_status launch_viscous_explicit(Ctx *c, const double *u, const double *eta, const double *G,
+                                   double *V)
+{
+    const GridD &g = c->g;
+    GeomD geo = geomd(c);
+    if (c->ncut)
+        EBV_LAUNCH(c, k_wall_dudn, dim3((c->ncut + 127) / 128), dim3(128), 0, g, geo, u, c->dudn);
+    EBV_LAUNCH(c, k_viscous_dc, grid3(g.nx, g.ny, g.nz), block3(), 0, g, geo, u, eta, G, c->dudn,
+               c->DC);
+    return launch_redistribute_into(c, c->DC, 1.0, c->prm.rho, V);
+}
+
+ebv_status launch_psi(Ctx *c, const double *u, const double *C, const double *V, const double *p,
+                      const double *f, double *psi)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_psi, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, C, V, p, f, c->dt_dev,
+               c->prm.rho, psi);
+    return EBV_OK;
+}
+
+ebv_status launch_add_gradp(Ctx *c, double *u, const double *p, double sgn)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_add_gradp, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, p, c->dt_dev,
+               c->prm.rho, sgn);
+    return EBV_OK;
+}
+
+ebv_status launch_nodal_rhs(Ctx *c, const double *ut, double *b)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_nodal_rhs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), ut,
+               c->dt_dev, c->prm.rho, b);
+    return EBV_OK;
+}
+
+ebv_status launch_timestep(Ctx *c, const double *u, const double *f, double dt_fixed)
+{
+    const GridD &g = c->g;
+    EBV_CUDA_TRY(c, cudaMemsetAsync(c->cfl_max, 0, 2 * sizeof(unsigned long long), c->stream));
+    EBV_LAUNCH(c, k_cfl_max, dim3(kReduceBlocks), dim3(256), 0, g, c->flag, u, f, c->cfl_max);
+    const double h = g.h;
+    double cv = 2.0 * c->prm.mu / c->prm.rho * (c->prm.bi_cfl + 1.0) * (3.0 / (h * h));
+    EBV_LAUNCH(c, k_dt_final, dim3(1), dim3(32), 0, c->cfl_max, c->prm.cfl, cv, dt_fixed, c->dt_dev);
+    return EBV_OK;
+}
+
+ebv_status launch_average(Ctx *c, double *a, const double *b, int n)
+{
+    EBV_LAUNCH(c, k_average, dim3(kReduceBlocks), dim3(256), 0, a, b, n);
+    return EBV_OK;
+}
+
+ebv_status launch_zero_covered(Ctx *c, double *u, int ncomp)
+{
+    EBV_LAUNCH(c, k_zero_covered, dim3(kReduceBlocks), dim3(256), 0, c->g, c->flag, u, ncomp);
+    return EBV_OK;
+}
+
+ebv_status launch_drag(Ctx *c, const double *u, const double *p, double *fz, double *yf)
+{
+    const GridD &g = c->g;
+    GeomD geo = geomd(c);
+    const int N3 = ncell(g);
+    // eta and ||gamma|| of u (em/srate scratch), wall gradients, then the sums
+    launch_strain_eta(c, u, c->es, c->srate, nullptr);
+    if (c->ncut) {
+        EBV_LAUNCH(c, k_wall_dudn, dim3((c->ncut + 127) / 128), dim3(128), 0, g, geo, u, c->dudn);
+        EBV_LAUNCH(c, k_drag_terms, dim3((c->ncut + 127) / 128), dim3(128), 0, g, geo, c->es, c->dudn,
+                   p, c->rhs_c);
+        ebv_status s = reduce_sum(c, c->rhs_c, c->ncut, c->scal + 8);
+        if (s != EBV_OK) return s;
+    } else {
+        EBV_CUDA_TRY(c, cudaMemsetAsync(c->scal + 8, 0, sizeof(double), c->stream));
+    }
+    EBV_LAUNCH(c, k_yield_parts, dim3(kReduceBlocks), dim3(256), 0, N3, c->flag, c->alpha, c->es,
+               c->srate, c->prm.tau0, c->part);
+    ebv_status s = reduce_sum(c, c->part, kReduceBlocks, c->scal + 9);
+    if (s != EBV_OK) return s;
+    s = reduce_sum(c, c->part + kReduceBlocks, kReduceBlocks, c->scal + 10);
+    if (s != EBV_OK) return s;
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->scal_host + 8, c->scal + 8, 3 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    *fz = c->scal_host[8];
+    *yf = c->scal_host[10] > 0.0 ? c->scal_host[9] / c->scal_host[10] : 0.0;
+    return EBV_OK;
+}
+
+}  // namespace ebv

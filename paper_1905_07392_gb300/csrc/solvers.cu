@@ -1,0 +1,1206 @@
+// Linear solvers of one step: the cell-centred projection (Poisson), the
+// three semi-implicit viscous Helmholtz solves and the nodal projection
+// (paper Sec. "Numerical algorithm": geometric multigrid for EB systems with a
+// Krylov method at the bottom).
+//
+// Every solve is conjugate gradients in FP64 preconditioned by one symmetric
+// multigrid V-cycle: red-black Gauss-Seidel (red first on the way down, black
+// first on the way up) for the 7-point cell-centred operators, a degree-3
+// Chebyshev-Jacobi smoother for the 27-point nodal operator, averaging /
+// full-weighting restriction, piecewise-constant / trilinear prolongation and
+// an exact dense solve at the bottom.  The V-cycle runs in FP64 or FP32
+// (EBV_FP32_REFINE); residuals, Krylov vectors and solution accumulation stay
+// FP64, so FP32 only enters as a preconditioner.  Dot products use fixed-order
+// block partials, so results are bitwise reproducible run to run.
+#include <math.h>
+
+#include "ebv_internal.cuh"
+
+namespace ebv {
+
+// ===========================================================================
+// Reductions
+// ===========================================================================
+namespace {
+
+template <int kThreads>
+__device__ inline double block_sum(double v)
+{
+    __shared__ double sm[kThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < kThreads / 32 ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+__device__ inline int block_linear() { return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x; }
+__device__ inline int thread_linear() { return (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x; }
+
+// 3-D blocks of 256 threads: block sum keyed on the linear thread index.
+__device__ inline double block_sum3(double v)
+{
+    __shared__ double sm[8];
+    const int t = thread_linear();
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) sm[t >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (t < 32) {
+        r = t < 8 ? sm[t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_final(const double *part, int n, double *out)
+{
+    double v = 0.0;
+    for (int s = threadIdx.x; s < n; s += 1024) v += part[s];
+    v = block_sum<1024>(v);
+    if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void __launch_bounds__(256) k_dot(const double *__restrict__ a, const double *__restrict__ b,
+                                             int n, double *__restrict__ part)
+{
+    double v = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        v += a[s] * b[s];
+    v = block_sum<256>(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+}  // namespace
+
+ebv_status reduce_sum(Ctx *c, const double *part, int nblocks, double *out_dev)
+{
+    EBV_LAUNCH(c, k_reduce_final, dim3(1), dim3(1024), 0, part, nblocks, out_dev);
+    return EBV_OK;
+}
+
+namespace {
+
+// ===========================================================================
+// Cell-centred operator  (A x)_i = extra_i x_i + sum_faces beta_f (x_i - x_nb)
+// (face coefficients include the box faces; x_nb = 0 outside the box)
+// ===========================================================================
+
+template <class T>
+struct CcOp {
+    GridD g;
+    const T *extra, *bx, *by, *bz;
+};
+
+template <class T>
+__device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__restrict__ x,
+                              T &diag, T &off)
+{
+    const GridD &g = A.g;
+    const int c = cidx(g, i, j, k);
+    const T bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
+    const T byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
+    const T bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
+    diag = A.extra[c] + bxl + bxh + byl + byh + bzl + bzh;
+    T s = 0;
+    if (i > 0) s += bxl * x[c - 1];
+    if (i < g.nx - 1) s += bxh * x[c + 1];
+    if (j > 0) s += byl * x[c - g.nx];
+    if (j < g.ny - 1) s += byh * x[c + g.nx];
+    if (k > 0) s += bzl * x[c - g.nx * g.ny];
+    if (k < g.nz - 1) s += bzh * x[c + g.nx * g.ny];
+    off = s;
+}
+
+// One colour of Gauss-Seidel: x_i = (b_i + sum beta x_nb) / diag.
+template <class T>
+__global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, const T *__restrict__ b,
+                                               int color)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const GridD &g = A.g;
+    if (i >= g.nx || j >= g.ny || k >= g.nz || ((i + j + k) & 1) != color) return;
+    T diag, off;
+    cc_row(A, i, j, k, x, diag, off);
+    const int c = cidx(g, i, j, k);
+    x[c] = diag > T(0) ? (b[c] + off) / diag : T(0);
+}
+
+// Residual of the 8 children, averaged into the coarse right-hand side.
+template <class T>
+__global__ void __launch_bounds__(256) k_cc_resid_restrict(CcOp<T> A, const T *__restrict__ x,
+                                                           const T *__restrict__ b, GridD gc,
+                                                           T *__restrict__ bc)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
+    T s = 0;
+    for (int o = 0; o < 8; o++) {
+        int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
+        T diag, off;
+        cc_row(A, i, j, k, x, diag, off);
+        int c = cidx(A.g, i, j, k);
+        s += b[c] - (diag * x[c] - off);
+    }
+    bc[cidx(gc, I, J, K)] = s * T(0.125);
+}
+
+template <class T>
+__global__ void k_cc_prolong(GridD gf, GridD gc, const uint8_t *__restrict__ cov,
+                             const T *__restrict__ xc, T *__restrict__ xf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= gf.nx || j >= gf.ny || k >= gf.nz) return;
+    const int c = cidx(gf, i, j, k);
+    if (cov[c]) return;
+    xf[c] += xc[cidx(gc, i >> 1, j >> 1, k >> 1)];
+}
+
+// Rediscretised coarse operator: face coefficient = (sum of the 4 fine faces) / 16,
+// extra = sum over uncovered children / 8 (identity where all children are covered).
+template <class T>
+__global__ void k_cc_coarsen(GridD gf, const T *__restrict__ ef, const T *__restrict__ bxf,
+                             const T *__restrict__ byf, const T *__restrict__ bzf,
+                             const uint8_t *__restrict__ covf, GridD gc, const uint8_t *__restrict__ covc,
+                             T *__restrict__ ec, T *__restrict__ bxc, T *__restrict__ byc,
+                             T *__restrict__ bzc)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I > gc.nx || J > gc.ny || K > gc.nz) return;
+    if (I < gc.nx && J < gc.ny && K < gc.nz) {
+        const int C = cidx(gc, I, J, K);
+        if (covc[C]) {
+            ec[C] = T(1);
+        } else {
+            T s = 0;
+            for (int o = 0; o < 8; o++) {
+                int c = cidx(gf, 2 * I + (o & 1), 2 * J + ((o >> 1) & 1), 2 * K + ((o >> 2) & 1));
+                if (!covf[c]) s += ef[c];
+            }
+            ec[C] = s * T(0.125);
+        }
+    }
+    const T *bf[3] = {bxf, byf, bzf};
+    T *bcs[3] = {bxc, byc, bzc};
+    const int m[3] = {gc.nx, gc.ny, gc.nz};
+    for (int d = 0; d < 3; d++) {
+        int id[3] = {I, J, K};
+        bool ok = true;
+        for (int e = 0; e < 3; e++) ok &= (e == d) ? id[e] <= m[e] : id[e] < m[e];
+        if (!ok) continue;
+        int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        T s = 0;
+        for (int q1 = 0; q1 < 2; q1++)
+            for (int q2 = 0; q2 < 2; q2++) {
+                int f[3] = {2 * I, 2 * J, 2 * K};
+                f[t1] += q1;
+                f[t2] += q2;
+                s += bf[d][fidx(gf, d, f[0], f[1], f[2])];
+            }
+        bcs[d][fidx(gc, d, I, J, K)] = s * T(0.0625);
+    }
+}
+
+__global__ void k_cov_coarsen(GridD gf, const uint8_t *covf, GridD gc, uint8_t *covc)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
+    int all = 1;
+    for (int o = 0; o < 8; o++)
+        all &= covf[cidx(gf, 2 * I + (o & 1), 2 * J + ((o >> 1) & 1), 2 * K + ((o >> 2) & 1))];
+    covc[cidx(gc, I, J, K)] = (uint8_t)all;
+}
+
+__global__ void k_cov_from_flag(int n, const uint8_t *flag, uint8_t *cov)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        cov[s] = flag[s] == 0;
+}
+
+template <class S, class D>
+__global__ void k_convert(const S *__restrict__ a, D *__restrict__ b, int n)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        b[s] = (D)a[s];
+}
+
+// Level-0 coefficients of the cell-centred projection: beta = a_f / h^2,
+// 2 a_f / h^2 on outflow faces (phi = 0 there), 0 on other box faces.
+__global__ void k_mac_coeffs(GridD g, const uint8_t *__restrict__ flag, const double *__restrict__ ax,
+                             const double *__restrict__ ay, const double *__restrict__ az,
+                             double *__restrict__ extra, double *__restrict__ bx, double *__restrict__ by,
+                             double *__restrict__ bz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const double h2 = g.h * g.h;
+    if (i < g.nx && j < g.ny && k < g.nz) {
+        int c = cidx(g, i, j, k);
+        extra[c] = flag[c] ? 0.0 : 1.0;
+    }
+    const double *A[3] = {ax, ay, az};
+    double *B[3] = {bx, by, bz};
+    int id[3] = {i, j, k};
+    for (int d = 0; d < 3; d++) {
+        bool ok = true;
+        for (int e = 0; e < 3; e++) ok &= (e == d) ? id[e] <= dimn(g, e) : id[e] < dimn(g, e);
+        if (!ok) continue;
+        int f = fidx(g, d, i, j, k);
+        if (id[d] == 0 || id[d] == dimn(g, d)) {
+            int side = 2 * d + (id[d] != 0);
+            B[d][f] = g.bc[side] == EBV_OUTFLOW ? 2.0 * A[d][f] / h2 : 0.0;
+        } else {
+            B[d][f] = A[d][f] / h2;
+        }
+    }
+}
+
+// Level-0 coefficients and right-hand side of the viscous solve of one
+// component (Eq. implicit-viscous, alpha-weighted):
+//   extra = rho alpha + dt eta A_EB / (h^2 delta), delta = max(-n.b, delta_min)
+//   beta  = dt a_f eta_f / h^2, eta_f the mean of the two cells; on a box face
+//           with a Dirichlet condition 2 dt a_f eta / h^2 (the value enters b).
+//   b     = alpha psi + sum of Dirichlet contributions.
+__global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__restrict__ eta,
+                              const double *__restrict__ dtp, int comp,
+                              const double *__restrict__ psi, double *__restrict__ extra,
+                              double *__restrict__ bx, double *__restrict__ by, double *__restrict__ bz,
+                              double *__restrict__ b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const double h2 = g.h * g.h, dt = *dtp;
+    const int N3 = geo.ncell;
+    const double *A[3] = {geo.ax, geo.ay, geo.az};
+    double *B[3] = {bx, by, bz};
+    int id[3] = {i, j, k};
+    for (int d = 0; d < 3; d++) {
+        bool ok = true;
+        for (int e = 0; e < 3; e++) ok &= (e == d) ? id[e] <= dimn(g, e) : id[e] < dimn(g, e);
+        if (!ok) continue;
+        int f = fidx(g, d, i, j, k);
+        double a = A[d][f];
+        if (id[d] == 0 || id[d] == dimn(g, d)) {
+            int hs = id[d] != 0;
+            int cc[3] = {i, j, k};
+            cc[d] -= hs;
+            double val;
+            int c = cidx(g, cc[0], cc[1], cc[2]);
+            B[d][f] = (a > 0.0 && side_dirichlet(g, 2 * d + hs, comp, &val)) ? 2.0 * dt * a * eta[c] / h2
+                                                                              : 0.0;
+        } else {
+            int lo[3] = {i, j, k};
+            lo[d] -= 1;
+            double ef = 0.5 * (eta[cidx(g, lo[0], lo[1], lo[2])] + eta[cidx(g, i, j, k)]);
+            B[d][f] = a > 0.0 ? dt * a * ef / h2 : 0.0;
+        }
+    }
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    const int c = cidx(g, i, j, k);
+    if (geo.flag[c] == 0) {
+        extra[c] = 1.0;
+        b[c] = 0.0;
+        return;
+    }
+    double e = p.rho * geo.alpha[c];
+    if (geo.flag[c] == 2 && geo.area[c] > 0.0) {
+        double nb = 0.0;
+        for (int q = 0; q < 3; q++) nb += geo.nrm[q * N3 + c] * geo.bcen[q * N3 + c];
+        double del = -nb > p.delta_min ? -nb : p.delta_min;
+        e += dt * eta[c] * geo.area[c] / (h2 * del);
+    }
+    extra[c] = e;
+    // Dirichlet contributions of the box faces of this cell (same expression
+    // as the face coefficient above)
+    double rb = 0.0;
+    for (int d = 0; d < 3; d++)
+        for (int hs = 0; hs < 2; hs++) {
+            int pos = id[d] + hs;
+            if (pos != 0 && pos != dimn(g, d)) continue;
+            int fi[3] = {i, j, k};
+            fi[d] += hs;
+            double a = A[d][fidx(g, d, fi[0], fi[1], fi[2])];
+            double val;
+            if (a > 0.0 && side_dirichlet(g, 2 * d + hs, comp, &val))
+                rb += (2.0 * dt * a * eta[c] / h2) * val;
+        }
+    b[c] = geo.alpha[c] * psi[c] + rb;
+}
+
+// q = A p (FP64, level 0) and block partials of p.q
+__global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<double> A, const double *__restrict__ p,
+                                                      double *__restrict__ q, double *__restrict__ part)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    double v = 0.0;
+    if (i < A.g.nx && j < A.g.ny && k < A.g.nz) {
+        double diag, off;
+        cc_row(A, i, j, k, p, diag, off);
+        int c = cidx(A.g, i, j, k);
+        double y = diag * p[c] - off;
+        q[c] = y;
+        v = p[c] * y;
+    }
+    v = block_sum3(v);
+    if (thread_linear() == 0) part[block_linear()] = v;
+}
+
+// ===========================================================================
+// Nodal operator (alpha-weighted trilinear stiffness, unit coefficient):
+//   (A x)_a = h sum_{cells c at a} alpha_c sum_{nodes b of c, active} K(a,b) x_b
+// with K(a,b) = 1/3, 0, -1/12, -1/12 for corners differing in 0, 1, 2, 3
+// coordinates.
+// ===========================================================================
+
+__constant__ double kQ1[4] = {1.0 / 3.0, 0.0, -1.0 / 12.0, -1.0 / 12.0};
+
+template <class T>
+struct NdOp {
+    GridD g;               // cell dims
+    const T *alpha;        // cells
+    const uint8_t *act;    // nodes
+};
+
+template <class T>
+__device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__restrict__ x, T &diag,
+                              T &ax)
+{
+    const GridD &g = A.g;
+    T s = 0, dsum = 0;
+    for (int oc = 0; oc < 8; oc++) {
+        int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+        if (!inbox(g, ci, cj, ck)) continue;
+        T al = A.alpha[cidx(g, ci, cj, ck)];
+        if (!(al > T(0))) continue;
+        int oa = (i - ci) | ((j - cj) << 1) | ((k - ck) << 2);
+        T cs = 0;
+        for (int ob = 0; ob < 8; ob++) {
+            int bi = ci + (ob & 1), bj = cj + ((ob >> 1) & 1), bk = ck + ((ob >> 2) & 1);
+            int n = nidx(g, bi, bj, bk);
+            if (!A.act[n]) continue;
+            cs += T(kQ1[__popc(oa ^ ob)]) * x[n];
+        }
+        s += al * cs;
+        dsum += al;
+    }
+    ax = T(g.h) * s;
+    diag = T(g.h) * dsum * T(1.0 / 3.0);
+}
+
+// One Chebyshev step: r = b - A x_in; d = cd d + cr D^-1 r; x_out = x_in + d.
+template <class T>
+__global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict__ xin, T *__restrict__ xout,
+                                                 T *__restrict__ dvec, const T *__restrict__ b, T cd, T cr,
+                                                 int zero_start)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const GridD &g = A.g;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int n = nidx(g, i, j, k);
+    if (!A.act[n]) {
+        xout[n] = T(0);
+        dvec[n] = T(0);
+        return;
+    }
+    T diag, ax;
+    if (zero_start) {
+        // x_in = 0, d = 0: only the diagonal is needed
+        T dsum = 0;
+        for (int oc = 0; oc < 8; oc++) {
+            int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+            if (!inbox(g, ci, cj, ck)) continue;
+            T al = A.alpha[cidx(g, ci, cj, ck)];
+            if (al > T(0)) dsum += al;
+        }
+        diag = T(g.h) * dsum * T(1.0 / 3.0);
+        T dn = cr * b[n] / diag;
+        dvec[n] = dn;
+        xout[n] = dn;
+        return;
+    }
+    nd_row(A, i, j, k, xin, diag, ax);
+    T r = b[n] - ax;
+    T dn = (cd != T(0) ? cd * dvec[n] : T(0)) + cr * r / diag;
+    dvec[n] = dn;
+    xout[n] = xin[n] + dn;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_nd_resid(NdOp<T> A, const T *__restrict__ x, const T *__restrict__ b,
+                                                  T *__restrict__ r)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const GridD &g = A.g;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    const int n = nidx(g, i, j, k);
+    if (!A.act[n]) { r[n] = T(0); return; }
+    T diag, ax;
+    nd_row(A, i, j, k, x, diag, ax);
+    r[n] = b[n] - ax;
+}
+
+// Full weighting (transpose of trilinear prolongation).
+template <class T>
+__global__ void k_nd_restrict(GridD gf, const T *__restrict__ rf, GridD gc, const uint8_t *__restrict__ actc,
+                              T *__restrict__ bc)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I > gc.nx || J > gc.ny || K > gc.nz) return;
+    const int N = nidx(gc, I, J, K);
+    if (!actc[N]) { bc[N] = T(0); return; }
+    T s = 0;
+    for (int dk = -1; dk <= 1; dk++) {
+        int k = 2 * K + dk;
+        if (k < 0 || k > gf.nz) continue;
+        T wk = dk ? T(0.5) : T(1);
+        for (int dj = -1; dj <= 1; dj++) {
+            int j = 2 * J + dj;
+            if (j < 0 || j > gf.ny) continue;
+            T wj = dj ? T(0.5) : T(1);
+            for (int di = -1; di <= 1; di++) {
+                int i = 2 * I + di;
+                if (i < 0 || i > gf.nx) continue;
+                T wi = di ? T(0.5) : T(1);
+                s += wi * wj * wk * rf[nidx(gf, i, j, k)];
+            }
+        }
+    }
+    bc[N] = s;
+}
+
+template <class T>
+__global__ void k_nd_prolong(GridD gf, const uint8_t *__restrict__ actf, GridD gc, const T *__restrict__ xc,
+                             T *__restrict__ xf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i > gf.nx || j > gf.ny || k > gf.nz) return;
+    const int n = nidx(gf, i, j, k);
+    if (!actf[n]) return;
+    int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+    int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
+    T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
+    T s = 0;
+    s += xc[nidx(gc, i0, j0, k0)];
+    if (i & 1) s += xc[nidx(gc, i1, j0, k0)];
+    if (j & 1) s += xc[nidx(gc, i0, j1, k0)];
+    if (k & 1) s += xc[nidx(gc, i0, j0, k1)];
+    if ((i & 1) && (j & 1)) s += xc[nidx(gc, i1, j1, k0)];
+    if ((i & 1) && (k & 1)) s += xc[nidx(gc, i1, j0, k1)];
+    if ((j & 1) && (k & 1)) s += xc[nidx(gc, i0, j1, k1)];
+    if ((i & 1) && (j & 1) && (k & 1)) s += xc[nidx(gc, i1, j1, k1)];
+    xf[n] += wi * wj * wk * s;
+}
+
+__global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<double> A, const double *__restrict__ p,
+                                                      double *__restrict__ q, double *__restrict__ part)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const GridD &g = A.g;
+    double v = 0.0;
+    if (i <= g.nx && j <= g.ny && k <= g.nz) {
+        const int n = nidx(g, i, j, k);
+        double y;
+        if (!A.act[n]) {
+            y = p[n];
+        } else {
+            double diag, ax;
+            nd_row(A, i, j, k, p, diag, ax);
+            y = ax;
+        }
+        q[n] = y;
+        v = p[n] * y;
+    }
+    v = block_sum3(v);
+    if (thread_linear() == 0) part[block_linear()] = v;
+}
+
+__global__ void k_nd_alpha_coarsen(GridD gf, const double *__restrict__ af, GridD gc, double *__restrict__ ac)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
+    double s = 0.0;
+    for (int o = 0; o < 8; o++)
+        s += af[cidx(gf, 2 * I + (o & 1), 2 * J + ((o >> 1) & 1), 2 * K + ((o >> 2) & 1))];
+    ac[cidx(gc, I, J, K)] = 0.125 * s;
+}
+
+__global__ void k_nd_active(GridD g, const double *__restrict__ alpha, uint8_t *__restrict__ act)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    int id[3] = {i, j, k};
+    bool dir = false;
+    for (int d = 0; d < 3; d++) {
+        if (id[d] == 0 && g.bc[2 * d] == EBV_OUTFLOW) dir = true;
+        if (id[d] == dimn(g, d) && g.bc[2 * d + 1] == EBV_OUTFLOW) dir = true;
+    }
+    bool any = false;
+    for (int oc = 0; oc < 8; oc++) {
+        int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+        if (inbox(g, ci, cj, ck) && alpha[cidx(g, ci, cj, ck)] > 0.0) any = true;
+    }
+    act[nidx(g, i, j, k)] = (!dir && any) ? 1 : 0;
+}
+
+// ===========================================================================
+// Dense bottom solve
+// ===========================================================================
+
+template <class T>
+__global__ void k_cc_bottom_assemble(CcOp<T> A, double *__restrict__ M, int nb)
+{
+    const GridD &g = A.g;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
+        double *row = M + (size_t)r * 2 * nb;
+        for (int s = 0; s < 2 * nb; s++) row[s] = 0.0;
+        row[nb + r] = 1.0;
+        int i = r % g.nx, j = (r / g.nx) % g.ny, k = r / (g.nx * g.ny);
+        double bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
+        double byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
+        double bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
+        double diag = (double)A.extra[r] + bxl + bxh + byl + byh + bzl + bzh;
+        row[r] = diag > 0.0 ? diag : 1.0;
+        if (i > 0) row[r - 1] = -bxl;
+        if (i < g.nx - 1) row[r + 1] = -bxh;
+        if (j > 0) row[r - g.nx] = -byl;
+        if (j < g.ny - 1) row[r + g.nx] = -byh;
+        if (k > 0) row[r - g.nx * g.ny] = -bzl;
+        if (k < g.nz - 1) row[r + g.nx * g.ny] = -bzh;
+    }
+}
+
+__global__ void k_nd_bottom_assemble(GridD g, const double *__restrict__ alpha, const uint8_t *__restrict__ act,
+                                     double *__restrict__ M, int nb)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
+        double *row = M + (size_t)r * 2 * nb;
+        for (int s = 0; s < 2 * nb; s++) row[s] = 0.0;
+        row[nb + r] = 1.0;
+        int i = r % (g.nx + 1), j = (r / (g.nx + 1)) % (g.ny + 1), k = r / ((g.nx + 1) * (g.ny + 1));
+        if (!act[r]) { row[r] = 1.0; continue; }
+        for (int oc = 0; oc < 8; oc++) {
+            int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+            if (!inbox(g, ci, cj, ck)) continue;
+            double al = alpha[cidx(g, ci, cj, ck)];
+            if (!(al > 0.0)) continue;
+            int oa = (i - ci) | ((j - cj) << 1) | ((k - ck) << 2);
+            for (int ob = 0; ob < 8; ob++) {
+                int n = nidx(g, ci + (ob & 1), cj + ((ob >> 1) & 1), ck + ((ob >> 2) & 1));
+                if (!act[n]) continue;
+                row[n] += g.h * al * kQ1[__popc(oa ^ ob)];
+            }
+        }
+    }
+}
+
+// Gauss-Jordan elimination of [M | I] in one CTA (SPD: no pivoting needed);
+// the right half becomes the inverse, copied to inv.
+__global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, int nb, double *__restrict__ inv)
+{
+    __shared__ double fac[kBottomMax];
+    const int w = 2 * nb;
+    for (int col = 0; col < nb; col++) {
+        double piv = M[(size_t)col * w + col];
+        __syncthreads();
+        for (int s = threadIdx.x; s < w; s += blockDim.x) M[(size_t)col * w + s] /= piv;
+        __syncthreads();
+        for (int r = threadIdx.x; r < nb; r += blockDim.x) fac[r] = (r == col) ? 0.0 : M[(size_t)r * w + col];
+        __syncthreads();
+        for (int e = threadIdx.x; e < nb * w; e += blockDim.x) {
+            int r = e / w, s = e - r * w;
+            if (r != col) M[e] -= fac[r] * M[(size_t)col * w + s];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+        int r = e / nb, s = e - r * nb;
+        inv[e] = M[(size_t)r * w + nb + s];
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_bottom_solve(const double *__restrict__ inv, int nb,
+                                                      const T *__restrict__ b, T *__restrict__ x,
+                                                      double scale)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < nb; q++) s += inv[(size_t)r * nb + q] * (double)b[q];
+        x[r] = (T)(s * scale);
+    }
+}
+
+// ===========================================================================
+// Krylov glue
+// ===========================================================================
+enum { S_BB = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_PQ = 4 };
+
+__global__ void __launch_bounds__(256) k_resid_init(const double *__restrict__ b, const double *__restrict__ q,
+                                                    double *__restrict__ r, int n, double *__restrict__ part)
+{
+    double v = 0.0, w = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double rs = b[s] - q[s];
+        r[s] = rs;
+        v += rs * rs;
+        w += b[s] * b[s];
+    }
+    v = block_sum<256>(v);
+    w = block_sum<256>(w);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = v;
+        part[gridDim.x + blockIdx.x] = w;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cg_update(double *__restrict__ x, double *__restrict__ r,
+                                                   const double *__restrict__ p, const double *__restrict__ q,
+                                                   const double *__restrict__ scal, int n, double *__restrict__ part)
+{
+    const double a = scal[S_RZ] / scal[S_PQ];
+    double v = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        x[s] += a * p[s];
+        double rs = r[s] - a * q[s];
+        r[s] = rs;
+        v += rs * rs;
+    }
+    v = block_sum<256>(v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+__global__ void k_cg_pupdate(double *__restrict__ p, const double *__restrict__ z, const double *__restrict__ scal,
+                             int n, int first)
+{
+    const double beta = first ? 0.0 : scal[S_RZ] / scal[S_RZOLD];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        p[s] = first ? z[s] : z[s] + beta * p[s];
+}
+
+__global__ void k_scal_copy(double *scal, int dst, int src)
+{
+    if (threadIdx.x == 0) scal[dst] = scal[src];
+}
+
+__global__ void k_fill(double *a, int n, double v)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) a[s] = v;
+}
+
+__global__ void k_zero_inactive(int n, const uint8_t *__restrict__ act, double *__restrict__ x)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        if (!act[s]) x[s] = 0.0;
+}
+
+template <class T>
+__global__ void k_zero(T *a, int n)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) a[s] = T(0);
+}
+
+template <class T>
+void zero(Ctx *c, T *a, int n)
+{
+    EBV_LAUNCH(c, k_zero<T>, dim3(std::min(kReduceBlocks, (n + 255) / 256)), dim3(256), 0, a, n);
+}
+
+inline dim3 cgrid(const GridD &g) { return grid3(g.nx, g.ny, g.nz); }
+inline dim3 ngrid(const GridD &g) { return grid3(g.nx + 1, g.ny + 1, g.nz + 1); }
+inline int nblocks3(dim3 b) { return b.x * b.y * b.z; }
+
+template <class T>
+CcOp<T> ccop(const CcLevel &L)
+{
+    CcOp<T> A;
+    A.g = L.g;
+    if constexpr (sizeof(T) == 8) {
+        A.extra = (const T *)L.extra_d; A.bx = (const T *)L.bf_d[0]; A.by = (const T *)L.bf_d[1]; A.bz = (const T *)L.bf_d[2];
+    } else {
+        A.extra = (const T *)L.extra_f; A.bx = (const T *)L.bf_f[0]; A.by = (const T *)L.bf_f[1]; A.bz = (const T *)L.bf_f[2];
+    }
+    return A;
+}
+
+template <class T>
+NdOp<T> ndop(const NdLevel &L)
+{
+    NdOp<T> A;
+    A.g = L.g;
+    if constexpr (sizeof(T) == 8) A.alpha = (const T *)L.alpha_d;
+    else A.alpha = (const T *)L.alpha_f;
+    A.act = L.act;
+    return A;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycles
+// ---------------------------------------------------------------------------
+
+template <class T>
+void cc_smooth(Ctx *c, const CcLevel &L, T *x, const T *b, bool red_first)
+{
+    CcOp<T> A = ccop<T>(L);
+    int c0 = red_first ? 0 : 1;
+    EBV_LAUNCH(c, k_cc_gs<T>, cgrid(L.g), block3(), 0, A, x, b, c0);
+    EBV_LAUNCH(c, k_cc_gs<T>, cgrid(L.g), block3(), 0, A, x, b, 1 - c0);
+}
+
+template <class T>
+void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
+{
+    const int nu = 2;
+    const int Lb = H.L - 1;
+    for (int l = 0; l < Lb; l++) {
+        const CcLevel &L = H.lv[l];
+        T *x = l ? (T *)c->lx[l] : x0;
+        const T *b = l ? (const T *)c->lb[l] : b0;
+        zero(c, x, ncell(L.g));
+        for (int s = 0; s < nu; s++) cc_smooth<T>(c, L, x, b, true);
+        const CcLevel &Lc = H.lv[l + 1];
+        EBV_LAUNCH(c, k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, ccop<T>(L), x, b, Lc.g,
+                   (T *)c->lb[l + 1]);
+    }
+    {
+        T *x = Lb ? (T *)c->lx[Lb] : x0;
+        const T *b = Lb ? (const T *)c->lb[Lb] : b0;
+        EBV_LAUNCH(c, k_bottom_solve<T>, dim3((H.nb + 255) / 256), dim3(256), 0, H.binv, H.nb, b, x, 1.0);
+    }
+    for (int l = Lb - 1; l >= 0; l--) {
+        const CcLevel &L = H.lv[l];
+        T *x = l ? (T *)c->lx[l] : x0;
+        const T *b = l ? (const T *)c->lb[l] : b0;
+        EBV_LAUNCH(c, k_cc_prolong<T>, cgrid(L.g), block3(), 0, L.g, H.lv[l + 1].g, L.cov,
+                   (const T *)c->lx[l + 1], x);
+        for (int s = 0; s < nu; s++) cc_smooth<T>(c, L, x, b, false);
+    }
+}
+
+// Chebyshev coefficients on [lam_max / 8, lam_max] of D^-1 A, degree 3.
+struct ChebCoef { double cd[3], cr[3]; };
+inline ChebCoef cheb_coef(double lmax)
+{
+    const double lmin = lmax / 8.0;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    ChebCoef k;
+    double rho0 = 1.0 / sigma;
+    k.cd[0] = 0.0;
+    k.cr[0] = 1.0 / theta;
+    for (int s = 1; s < 3; s++) {
+        double rho1 = 1.0 / (2.0 * sigma - rho0);
+        k.cd[s] = rho1 * rho0;
+        k.cr[s] = 2.0 * rho1 / delta;
+        rho0 = rho1;
+    }
+    return k;
+}
+
+// Chebyshev smoothing of A x = b; x holds the start (zero if zero_start) and
+// the result.  Uses ld (direction) and lt (ping-pong) of the level.
+template <class T>
+void nd_smooth(Ctx *c, const NdLevel &L, int l, T *x, const T *b, bool zero_start)
+{
+    NdOp<T> A = ndop<T>(L);
+    ChebCoef k = cheb_coef(L.lam_max);
+    T *d = (T *)c->ld[l], *t = (T *)c->lt[l];
+    T *src = x, *dst = t;
+    for (int s = 0; s < 3; s++) {
+        EBV_LAUNCH(c, k_nd_cheb<T>, ngrid(L.g), block3(), 0, A, src, dst, d, b, (T)k.cd[s], (T)k.cr[s],
+                   (int)(s == 0 && zero_start));
+        T *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    // three steps: the result is in t; copy back into x by one more swap-free pass
+    if (src != x) {
+        const int n = nnode(L.g);
+        EBV_LAUNCH(c, (k_convert<T, T>), dim3(std::min(kReduceBlocks, (n + 255) / 256)), dim3(256), 0, src, x, n);
+    }
+}
+
+template <class T>
+void nd_vcycle(Ctx *c, NdHier &H, const T *b0, T *x0)
+{
+    const int Lb = H.L - 1;
+    for (int l = 0; l < Lb; l++) {
+        const NdLevel &L = H.lv[l];
+        T *x = l ? (T *)c->lx[l] : x0;
+        const T *b = l ? (const T *)c->lb[l] : b0;
+        nd_smooth<T>(c, L, l, x, b, true);
+        EBV_LAUNCH(c, k_nd_resid<T>, ngrid(L.g), block3(), 0, ndop<T>(L), x, b, (T *)c->lr[l]);
+        const NdLevel &Lc = H.lv[l + 1];
+        EBV_LAUNCH(c, k_nd_restrict<T>, ngrid(Lc.g), block3(), 0, L.g, (const T *)c->lr[l], Lc.g, Lc.act,
+                   (T *)c->lb[l + 1]);
+    }
+    {
+        T *x = Lb ? (T *)c->lx[Lb] : x0;
+        const T *b = Lb ? (const T *)c->lb[Lb] : b0;
+        EBV_LAUNCH(c, k_bottom_solve<T>, dim3((H.nb + 255) / 256), dim3(256), 0, H.binv, H.nb, b, x, 1.0);
+    }
+    for (int l = Lb - 1; l >= 0; l--) {
+        const NdLevel &L = H.lv[l];
+        T *x = l ? (T *)c->lx[l] : x0;
+        const T *b = l ? (const T *)c->lb[l] : b0;
+        EBV_LAUNCH(c, k_nd_prolong<T>, ngrid(L.g), block3(), 0, L.g, L.act, H.lv[l + 1].g,
+                   (const T *)c->lx[l + 1], x);
+        nd_smooth<T>(c, L, l, x, b, false);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioned conjugate gradients
+// ---------------------------------------------------------------------------
+
+struct Problem {
+    virtual ~Problem() {}
+    virtual int n() const = 0;
+    virtual void apply_dot(Ctx *c, const double *p, double *q) = 0;  // partials of p.q into c->part
+    virtual int apply_blocks() const = 0;
+    virtual void precond(Ctx *c, const double *r, double *z) = 0;
+};
+
+inline int vblocks(int n) { return std::min(kReduceBlocks, (n + 255) / 256); }
+
+ebv_status read_scalars(Ctx *c, int first, int count)
+{
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->scal_host + first, c->scal + first, count * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return EBV_OK;
+}
+
+ebv_status pcg(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
+{
+    const int n = P.n();
+    const double tol = c->prm.tol;
+    const int maxit = c->prm.max_iters;
+    double *r = c->kr, *z = c->kz, *p = c->kp, *q = c->kq;
+    int it = 0;
+    double rel = 0.0, bb = 0.0;
+    ebv_status st;
+    for (int restart = 0; restart < 20; restart++) {
+        // true residual
+        P.apply_dot(c, x, q);
+        EBV_LAUNCH(c, k_resid_init, dim3(vblocks(n)), dim3(256), 0, b, q, r, n, c->part);
+        reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
+        reduce_sum(c, c->part + vblocks(n), vblocks(n), c->scal + S_BB);
+        if ((st = read_scalars(c, 0, 2)) != EBV_OK) return st;
+        bb = c->scal_host[S_BB];
+        double rr = c->scal_host[S_RR];
+        if (!std::isfinite(rr) || !std::isfinite(bb)) return c->fail(EBV_ERR_NAN, "non-finite residual");
+        if (bb == 0.0) {
+            EBV_LAUNCH(c, k_fill, dim3(vblocks(n)), dim3(256), 0, x, n, 0.0);
+            rel = 0.0;
+            break;
+        }
+        rel = sqrt(rr / bb);
+        if (rel <= tol || it >= maxit) break;
+        bool first = true;
+        while (it < maxit) {
+            P.precond(c, r, z);
+            EBV_LAUNCH(c, k_dot, dim3(vblocks(n)), dim3(256), 0, r, z, n, c->part);
+            reduce_sum(c, c->part, vblocks(n), c->scal + S_RZ);
+            EBV_LAUNCH(c, k_cg_pupdate, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, (int)first);
+            first = false;
+            P.apply_dot(c, p, q);
+            reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_PQ);
+            EBV_LAUNCH(c, k_cg_update, dim3(vblocks(n)), dim3(256), 0, x, r, p, q, c->scal, n, c->part);
+            reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
+            EBV_LAUNCH(c, k_scal_copy, dim3(1), dim3(32), 0, c->scal, S_RZOLD, S_RZ);
+            it++;
+            if ((st = read_scalars(c, S_RR, 1)) != EBV_OK) return st;
+            double rr2 = c->scal_host[S_RR];
+            if (!std::isfinite(rr2)) return c->fail(EBV_ERR_NAN, "non-finite residual");
+            if (sqrt(rr2 / bb) <= 0.5 * tol) break;
+        }
+    }
+    if (iters) *iters = it;
+    if (res) *res = rel;
+    if (rel > tol && it >= maxit)
+        return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance");
+    return EBV_OK;
+}
+
+struct CcProblem : Problem {
+    CcHier *H;
+    bool fp32;
+    int n() const override { return ncell(H->lv[0].g); }
+    int apply_blocks() const override { return nblocks3(cgrid(H->lv[0].g)); }
+    void apply_dot(Ctx *c, const double *p, double *q) override
+    {
+        EBV_LAUNCH(c, k_cc_apply_dot, cgrid(H->lv[0].g), block3(), 0, ccop<double>(H->lv[0]), p, q, c->part);
+    }
+    void precond(Ctx *c, const double *r, double *z) override
+    {
+        if (!fp32) {
+            cc_vcycle<double>(c, *H, r, z);
+        } else {
+            const int nn = n();
+            EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nn)), dim3(256), 0, r, (float *)c->lb[0], nn);
+            cc_vcycle<float>(c, *H, (const float *)c->lb[0], (float *)c->lx[0]);
+            EBV_LAUNCH(c, (k_convert<float, double>), dim3(vblocks(nn)), dim3(256), 0, (const float *)c->lx[0], z, nn);
+        }
+    }
+};
+
+struct NdProblem : Problem {
+    NdHier *H;
+    bool fp32;
+    int n() const override { return nnode(H->lv[0].g); }
+    int apply_blocks() const override { return nblocks3(ngrid(H->lv[0].g)); }
+    void apply_dot(Ctx *c, const double *p, double *q) override
+    {
+        EBV_LAUNCH(c, k_nd_apply_dot, ngrid(H->lv[0].g), block3(), 0, ndop<double>(H->lv[0]), p, q, c->part);
+    }
+    void precond(Ctx *c, const double *r, double *z) override
+    {
+        if (!fp32) {
+            nd_vcycle<double>(c, *H, r, z);
+        } else {
+            const int nn = n();
+            EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nn)), dim3(256), 0, r, (float *)c->lb[0], nn);
+            nd_vcycle<float>(c, *H, (const float *)c->lb[0], (float *)c->lx[0]);
+            EBV_LAUNCH(c, (k_convert<float, double>), dim3(vblocks(nn)), dim3(256), 0, (const float *)c->lx[0], z, nn);
+        }
+    }
+};
+
+// Coarse levels and FP32 shadows of a cell-centred hierarchy whose level-0
+// FP64 coefficients are set; then the bottom inverse.
+ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
+{
+    CcLevel &L0 = H.lv[0];
+    if (fp32) {
+        const int n = ncell(L0.g);
+        EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(n)), dim3(256), 0, L0.extra_d, L0.extra_f, n);
+        for (int d = 0; d < 3; d++) {
+            int nf = nface(L0.g, d);
+            EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nf)), dim3(256), 0, L0.bf_d[d], L0.bf_f[d], nf);
+        }
+    }
+    for (int l = 0; l + 1 < H.L; l++) {
+        CcLevel &F = H.lv[l], &Cc = H.lv[l + 1];
+        dim3 gr = grid3(Cc.g.nx + 1, Cc.g.ny + 1, Cc.g.nz + 1);
+        if (fp32)
+            EBV_LAUNCH(c, k_cc_coarsen<float>, gr, block3(), 0, F.g, F.extra_f, F.bf_f[0], F.bf_f[1], F.bf_f[2], F.cov,
+                       Cc.g, Cc.cov, Cc.extra_f, Cc.bf_f[0], Cc.bf_f[1], Cc.bf_f[2]);
+        else
+            EBV_LAUNCH(c, k_cc_coarsen<double>, gr, block3(), 0, F.g, F.extra_d, F.bf_d[0], F.bf_d[1], F.bf_d[2],
+                       F.cov, Cc.g, Cc.cov, Cc.extra_d, Cc.bf_d[0], Cc.bf_d[1], Cc.bf_d[2]);
+    }
+    CcLevel &B = H.lv[H.L - 1];
+    if (fp32)
+        EBV_LAUNCH(c, k_cc_bottom_assemble<float>, dim3((H.nb + 127) / 128), dim3(128), 0, ccop<float>(B), H.bmat, H.nb);
+    else
+        EBV_LAUNCH(c, k_cc_bottom_assemble<double>, dim3((H.nb + 127) / 128), dim3(128), 0, ccop<double>(B), H.bmat,
+                   H.nb);
+    EBV_LAUNCH(c, k_gauss_jordan, dim3(1), dim3(1024), 0, H.bmat, H.nb, H.binv);
+    return EBV_OK;
+}
+
+// Level dimensions: halve while every dimension is even and the level has
+// more than 64 cells (cell-centred) / 125 nodes (nodal).
+int plan_levels(const GridD &g0, GridD *out, bool nodal)
+{
+    int L = 0;
+    GridD g = g0;
+    out[L++] = g;
+    while (L < kMaxLevels) {
+        long long sz = nodal ? (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1) : (long long)g.nx * g.ny * g.nz;
+        if (sz <= (nodal ? 125 : 64)) break;
+        if ((g.nx & 1) || (g.ny & 1) || (g.nz & 1)) break;
+        g.nx /= 2; g.ny /= 2; g.nz /= 2;
+        g.h *= 2.0;
+        out[L++] = g;
+    }
+    return L;
+}
+
+template <class T>
+T *dalloc(size_t n, cudaError_t &e)
+{
+    T *p = nullptr;
+    cudaError_t r = cudaMalloc(&p, n * sizeof(T));
+    if (r != cudaSuccess) e = r;
+    return p;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Set-up and public solver entry points
+// ===========================================================================
+
+ebv_status setup_solvers(Ctx *c)
+{
+    const GridD &g = c->g;
+    cudaError_t e = cudaSuccess;
+    GridD gl[kMaxLevels];
+    // cell-centred hierarchies (projection and viscous)
+    int L = plan_levels(g, gl, false);
+    long long nbc = (long long)gl[L - 1].nx * gl[L - 1].ny * gl[L - 1].nz;
+    if (nbc > kBottomMax) return c->fail(EBV_ERR_INVALID, "grid cannot be coarsened to a small bottom level");
+    CcHier *hs[2] = {&c->mac, &c->visc};
+    for (CcHier *H : hs) {
+        H->L = L;
+        H->nb = (int)nbc;
+        for (int l = 0; l < L; l++) {
+            CcLevel &Lv = H->lv[l];
+            Lv.g = gl[l];
+            size_t nc = ncell(gl[l]);
+            Lv.extra_d = dalloc<double>(nc, e);
+            Lv.extra_f = dalloc<float>(nc, e);
+            for (int d = 0; d < 3; d++) {
+                Lv.bf_d[d] = dalloc<double>(nface(gl[l], d), e);
+                Lv.bf_f[d] = dalloc<float>(nface(gl[l], d), e);
+            }
+            if (H == &c->mac) Lv.cov = dalloc<uint8_t>(nc, e);
+            else Lv.cov = c->mac.lv[l].cov;
+        }
+        H->binv = dalloc<double>((size_t)nbc * nbc, e);
+        H->bmat = dalloc<double>((size_t)nbc * 2 * nbc, e);
+    }
+    // nodal hierarchy
+    GridD gn[kMaxLevels];
+    int Ln = plan_levels(g, gn, true);
+    long long nbn = (long long)(gn[Ln - 1].nx + 1) * (gn[Ln - 1].ny + 1) * (gn[Ln - 1].nz + 1);
+    if (nbn > kBottomMax) return c->fail(EBV_ERR_INVALID, "grid cannot be coarsened to a small nodal bottom");
+    c->nd.L = Ln;
+    c->nd.nb = (int)nbn;
+    for (int l = 0; l < Ln; l++) {
+        NdLevel &Lv = c->nd.lv[l];
+        Lv.g = gn[l];
+        size_t nc = ncell(gn[l]);
+        Lv.alpha_d = l ? dalloc<double>(nc, e) : c->alpha;
+        Lv.alpha_f = dalloc<float>(nc, e);
+        Lv.act = dalloc<uint8_t>(nnode(gn[l]), e);
+        Lv.lam_max = 2.0;
+    }
+    c->nd.binv = dalloc<double>((size_t)nbn * nbn, e);
+    c->nd.bmat = dalloc<double>((size_t)nbn * 2 * nbn, e);
+    // level vectors: large enough for nodes of that level (>= cells)
+    int Lmax = std::max(L, Ln);
+    for (int l = 0; l < Lmax; l++) {
+        const GridD &gg = l < Ln ? gn[l] : gl[l];
+        size_t m = (size_t)nnode(gg);
+        c->lx[l] = dalloc<double>(m, e);
+        c->lb[l] = dalloc<double>(m, e);
+        c->lr[l] = dalloc<double>(m, e);
+        c->ld[l] = dalloc<double>(m, e);
+        c->lt[l] = dalloc<double>(m, e);
+    }
+    if (e != cudaSuccess) return c->fail(EBV_ERR_CUDA, std::string("allocation: ") + cudaGetErrorString(e));
+    return EBV_OK;
+}
+
+// Geometry-dependent solver data: projection coefficients, coverage, nodal
+// volume fractions and active nodes, both bottom inverses.
+ebv_status setup_geometry_solvers(Ctx *c)
+{
+    const GridD &g = c->g;
+    // coverage per level
+    EBV_LAUNCH(c, k_cov_from_flag, dim3(vblocks(ncell(g))), dim3(256), 0, ncell(g), c->flag, c->mac.lv[0].cov);
+    for (int l = 0; l + 1 < c->mac.L; l++)
+        EBV_LAUNCH(c, k_cov_coarsen, cgrid(c->mac.lv[l + 1].g), block3(), 0, c->mac.lv[l].g, c->mac.lv[l].cov,
+                   c->mac.lv[l + 1].g, c->mac.lv[l + 1].cov);
+    // projection operator
+    CcLevel &M0 = c->mac.lv[0];
+    EBV_LAUNCH(c, k_mac_coeffs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, c->flag, c->ax, c->ay, c->az,
+               M0.extra_d, M0.bf_d[0], M0.bf_d[1], M0.bf_d[2]);
+    // both precisions of the projection hierarchy are kept
+    ebv_status s = cc_finish_hierarchy(c, c->mac, false);
+    if (s != EBV_OK) return s;
+    if (c->prm.precision == EBV_FP32_REFINE) {
+        // FP32 levels derived from FP64 fine coefficients; the bottom inverse
+        // from the FP32 coarse operator
+        s = cc_finish_hierarchy(c, c->mac, true);
+        if (s != EBV_OK) return s;
+    }
+    // nodal
+    NdHier &N = c->nd;
+    for (int l = 0; l < N.L; l++) {
+        NdLevel &Lv = N.lv[l];
+        if (l) EBV_LAUNCH(c, k_nd_alpha_coarsen, cgrid(Lv.g), block3(), 0, N.lv[l - 1].g, N.lv[l - 1].alpha_d, Lv.g,
+                          Lv.alpha_d);
+        int nc = ncell(Lv.g);
+        EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nc)), dim3(256), 0, Lv.alpha_d, Lv.alpha_f, nc);
+        EBV_LAUNCH(c, k_nd_active, ngrid(Lv.g), block3(), 0, Lv.g, Lv.alpha_d, Lv.act);
+    }
+    const NdLevel &B = N.lv[N.L - 1];
+    EBV_LAUNCH(c, k_nd_bottom_assemble, dim3((N.nb + 127) / 128), dim3(128), 0, B.g, B.alpha_d, B.act, N.bmat, N.nb);
+    EBV_LAUNCH(c, k_gauss_jordan, dim3(1), dim3(1024), 0, N.bmat, N.nb, N.binv);
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res)
+{
+    CcProblem P;
+    P.H = &c->mac;
+    P.fp32 = c->prm.precision == EBV_FP32_REFINE;
+    EBV_LAUNCH(c, k_fill, dim3(vblocks(ncell(c->g))), dim3(256), 0, x, ncell(c->g), 0.0);
+    return pcg(c, P, b, x, iters, res);
+}
+
+ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int comp, double *x, int *iters,
+                      double *res)
+{
+    const GridD &g = c->g;
+    CcLevel &V0 = c->visc.lv[0];
+    EBV_LAUNCH(c, k_visc_coeffs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), paramsd(c->prm), eta,
+               c->dt_dev, comp, psi_comp, V0.extra_d, V0.bf_d[0], V0.bf_d[1], V0.bf_d[2], c->rhs_c);
+    const bool fp32 = c->prm.precision == EBV_FP32_REFINE;
+    ebv_status s = cc_finish_hierarchy(c, c->visc, fp32);
+    if (s != EBV_OK) return s;
+    CcProblem P;
+    P.H = &c->visc;
+    P.fp32 = fp32;
+    return pcg(c, P, c->rhs_c, x, iters, res);
+}
+
+ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *res)
+{
+    const int nn = nnode(c->g);
+    EBV_LAUNCH(c, k_zero_inactive, dim3(vblocks(nn)), dim3(256), 0, nn, c->nd.lv[0].act, x);
+    NdProblem P;
+    P.H = &c->nd;
+    P.fp32 = c->prm.precision == EBV_FP32_REFINE;
+    return pcg(c, P, b, x, iters, res);
+}
+
+}  // namespace ebv

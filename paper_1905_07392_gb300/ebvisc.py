@@ -1,0 +1,301 @@
+"""Thin ctypes binding of ``libebvisc.so`` (C-ABI in ``include/ebvisc.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Field arguments are contiguous float64 CUDA tensors (device
+pointers are passed through); the library queues its work on the CUDA stream
+that was current when the ``Solver`` was created.  There is no CPU fallback:
+if the library is missing or fails to load, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libebvisc.so")
+
+INFLOW, OUTFLOW, SLIP, NOSLIP = 0, 1, 2, 3
+NEWTONIAN, BINGHAM, HERSCHEL_BULKLEY, POWER_LAW, SOUZA_MENDES_DUTRA = 0, 1, 2, 3, 4
+FP64, FP32_REFINE = 0, 1
+STATUS = {0: "EBV_OK", -1: "EBV_ERR_INVALID", -2: "EBV_ERR_CUDA", -3: "EBV_ERR_NOT_CONVERGED",
+          -5: "EBV_ERR_NAN", -6: "EBV_ERR_GEOMETRY"}
+
+
+class EbvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("lo", C.c_double * 3), ("h", C.c_double),
+                ("bc", C.c_int * 6), ("u_in", C.c_double * 3)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("tau0", C.c_double),
+                ("m", C.c_double), ("n_flow", C.c_double), ("eta0", C.c_double),
+                ("model", C.c_int), ("cfl", C.c_double), ("bi_cfl", C.c_double),
+                ("tol", C.c_double), ("max_iters", C.c_int), ("delta_min", C.c_double),
+                ("precision", C.c_int)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("dt", C.c_double), ("drag", C.c_double), ("yield_frac", C.c_double),
+                ("iters", C.c_int * 10), ("res", C.c_double * 10)]
+
+
+IMPLICIT_FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
+
+EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geometry_sphere",
+           "ebv_build_geometry_plane", "ebv_get_geometry", "ebv_update_viscosity", "ebv_derived",
+           "ebv_face_states", "ebv_solve_mac", "ebv_solve_viscous", "ebv_solve_projection",
+           "ebv_timestep", "ebv_advance", "ebv_advance_host", "ebv_drag", "ebv_launch_count",
+           "ebv_last_error", "ebv_destroy"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    sig = {
+        "ebv_create": ([C.POINTER(_Grid), C.POINTER(_Params), vp, C.POINTER(vp)], C.c_int),
+        "ebv_set_params": ([vp, C.POINTER(_Params)], C.c_int),
+        "ebv_build_geometry": ([vp, IMPLICIT_FN, vp], C.c_int),
+        "ebv_build_geometry_sphere": ([vp, dp, C.c_double], C.c_int),
+        "ebv_build_geometry_plane": ([vp, dp, C.c_double], C.c_int),
+        "ebv_get_geometry": ([vp] + [vp] * 8, C.c_int),
+        "ebv_update_viscosity": ([vp, vp, vp, vp], C.c_int),
+        "ebv_derived": ([vp, vp, vp, vp, vp, ip, dp], C.c_int),
+        "ebv_face_states": ([vp, vp, vp], C.c_int),
+        "ebv_solve_mac": ([vp, vp, vp, ip, dp], C.c_int),
+        "ebv_solve_viscous": ([vp, vp, vp, C.c_double, vp, C.POINTER(_Stats)], C.c_int),
+        "ebv_solve_projection": ([vp, vp, vp, C.c_double, C.POINTER(_Stats)], C.c_int),
+        "ebv_timestep": ([vp, vp, vp, dp], C.c_int),
+        "ebv_advance": ([vp, vp, vp, C.c_double, vp, C.POINTER(_Stats)], C.c_int),
+        "ebv_advance_host": ([vp, vp, vp, C.c_int, C.c_double, C.POINTER(_Stats)], C.c_int),
+        "ebv_drag": ([vp, vp, vp, dp, dp], C.c_int),
+        "ebv_launch_count": ([vp], C.c_longlong),
+        "ebv_last_error": ([vp], C.c_char_p),
+        "ebv_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("fields must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check_f64(t, n, name):
+    import torch
+    if t.dtype != torch.float64 or t.numel() != n:
+        raise ValueError(f"{name}: expected {n} float64 values, got {t.numel()} {t.dtype}")
+
+
+def _stats_dict(st):
+    return {"dt": st.dt, "drag": st.drag, "yield_frac": st.yield_frac,
+            "iters": list(st.iters), "res": list(st.res)}
+
+
+class Solver:
+    """One grid, one geometry, one CUDA stream."""
+
+    def __init__(self, n, h, lo=(0.0, 0.0, 0.0), bc=W.CHANNEL_BC, u_in=(0.0, 0.0, 1.0), *,
+                 rho=1.0, mu=1.0, tau0=0.0, m=1e3, n_flow=1.0, eta0=1e3, model=BINGHAM,
+                 cfl=0.5, bi_cfl=0.0, tol=1e-8, max_iters=1000, delta_min=0.25,
+                 precision=FP64, stream=None):
+        import torch
+        self._lib = load()
+        self.n = tuple(int(v) for v in n)
+        self.h = float(h)
+        g = _Grid()
+        g.n[:] = list(self.n)
+        g.lo[:] = [float(v) for v in lo]
+        g.h = self.h
+        g.bc[:] = [int(v) for v in bc]
+        g.u_in[:] = [float(v) for v in u_in]
+        self._grid = g
+        self.params = dict(rho=rho, mu=mu, tau0=tau0, m=m, n_flow=n_flow, eta0=eta0, model=model,
+                           cfl=cfl, bi_cfl=bi_cfl, tol=tol, max_iters=max_iters,
+                           delta_min=delta_min, precision=precision)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        ctx = C.c_void_p()
+        st = self._lib.ebv_create(C.byref(g), C.byref(self._params_c()),
+                                  C.c_void_p(stream.cuda_stream), C.byref(ctx))
+        if st != 0:
+            raise EbvError(st, "ebv_create failed")
+        self._ctx = ctx
+        self._fn_keep = None
+
+    @classmethod
+    def from_workload(cls, w: W.Workload, **kw):
+        args = dict(rho=w.rho, mu=w.mu, tau0=w.tau0, m=w.m, n_flow=w.n_flow, model=w.model,
+                    cfl=w.cfl, bi_cfl=w.bingham)
+        args.update(kw)
+        s = cls((w.n, w.n, w.n), w.h, bc=w.bc, u_in=w.u_in, **args)
+        s.build_sphere(w.centre, w.radius)
+        return s
+
+    def _params_c(self):
+        p = _Params()
+        for k, v in self.params.items():
+            setattr(p, k, int(v) if k in ("model", "max_iters", "precision") else float(v))
+        return p
+
+    def _ok(self, st):
+        if st != 0:
+            msg = self._lib.ebv_last_error(self._ctx).decode()
+            raise EbvError(st, msg)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.ebv_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # sizes
+    @property
+    def ncell(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+    @property
+    def nnode(self):
+        return (self.n[0] + 1) * (self.n[1] + 1) * (self.n[2] + 1)
+
+    def nface(self, d):
+        m = list(self.n)
+        m[d] += 1
+        return m[0] * m[1] * m[2]
+
+    def set_params(self, **kw):
+        self.params.update(kw)
+        self._ok(self._lib.ebv_set_params(self._ctx, C.byref(self._params_c())))
+
+    # geometry
+    def build_sphere(self, centre, radius):
+        c = (C.c_double * 3)(*centre)
+        self._ok(self._lib.ebv_build_geometry_sphere(self._ctx, c, C.c_double(radius)))
+
+    def build_plane(self, normal, d):
+        nv = (C.c_double * 3)(*normal)
+        self._ok(self._lib.ebv_build_geometry_plane(self._ctx, nv, C.c_double(d)))
+
+    def build_geometry(self, fn):
+        """fn(x: tuple of 3 floats) -> float, > 0 in the fluid (called on the host)."""
+        cb = IMPLICIT_FN(lambda x, user: float(fn((x[0], x[1], x[2]))))
+        self._fn_keep = cb
+        self._ok(self._lib.ebv_build_geometry(self._ctx, cb, None))
+
+    def geometry(self):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        N3 = self.ncell
+        out = {"alpha": torch.empty(N3, dtype=torch.float64, device=dev),
+               "ax": torch.empty(self.nface(0), dtype=torch.float64, device=dev),
+               "ay": torch.empty(self.nface(1), dtype=torch.float64, device=dev),
+               "az": torch.empty(self.nface(2), dtype=torch.float64, device=dev),
+               "area": torch.empty(N3, dtype=torch.float64, device=dev),
+               "nrm": torch.empty(3 * N3, dtype=torch.float64, device=dev),
+               "bcen": torch.empty(3 * N3, dtype=torch.float64, device=dev),
+               "flag": torch.empty(N3, dtype=torch.uint8, device=dev)}
+        self._ok(self._lib.ebv_get_geometry(self._ctx, *[_ptr(out[k]) for k in
+                                                          ("alpha", "ax", "ay", "az", "area",
+                                                           "nrm", "bcen", "flag")]))
+        return out
+
+    # stage operations
+    def update_viscosity(self, u, eta, srate=None):
+        _check_f64(u, 3 * self.ncell, "u")
+        _check_f64(eta, self.ncell, "eta")
+        if srate is not None:
+            _check_f64(srate, self.ncell, "srate")
+        self._ok(self._lib.ebv_update_viscosity(self._ctx, _ptr(u), _ptr(eta), _ptr(srate)))
+
+    def derived(self, u, Cv, eta, V):
+        it, res = C.c_int(0), C.c_double(0.0)
+        self._ok(self._lib.ebv_derived(self._ctx, _ptr(u), _ptr(Cv), _ptr(eta), _ptr(V),
+                                       C.byref(it), C.byref(res)))
+        return it.value, res.value
+
+    def face_states(self, u, uf):
+        self._ok(self._lib.ebv_face_states(self._ctx, _ptr(u), _ptr(uf)))
+
+    def solve_mac(self, uf, phi):
+        it, res = C.c_int(0), C.c_double(0.0)
+        self._ok(self._lib.ebv_solve_mac(self._ctx, _ptr(uf), _ptr(phi), C.byref(it),
+                                         C.byref(res)))
+        return it.value, res.value
+
+    def solve_viscous(self, eta, psi, dt, ut):
+        st = _Stats()
+        self._ok(self._lib.ebv_solve_viscous(self._ctx, _ptr(eta), _ptr(psi), C.c_double(dt),
+                                             _ptr(ut), C.byref(st)))
+        return _stats_dict(st)
+
+    def solve_projection(self, ut, p, dt):
+        st = _Stats()
+        self._ok(self._lib.ebv_solve_projection(self._ctx, _ptr(ut), _ptr(p), C.c_double(dt),
+                                                C.byref(st)))
+        return _stats_dict(st)
+
+    def timestep(self, u, f=None):
+        dt = C.c_double(0.0)
+        self._ok(self._lib.ebv_timestep(self._ctx, _ptr(u), _ptr(f), C.byref(dt)))
+        return dt.value
+
+    def advance(self, u, p, dt=0.0, f=None, stats=True):
+        _check_f64(u, 3 * self.ncell, "u")
+        _check_f64(p, self.nnode, "p")
+        st = _Stats()
+        self._ok(self._lib.ebv_advance(self._ctx, _ptr(u), _ptr(p), C.c_double(dt), _ptr(f),
+                                       C.byref(st) if stats else None))
+        return _stats_dict(st) if stats else None
+
+    def advance_host(self, u: np.ndarray, p: np.ndarray, steps: int, dt=0.0):
+        """Steps from host (numpy, float64, contiguous) buffers, updated in place."""
+        for a, n in ((u, 3 * self.ncell), (p, self.nnode)):
+            if a.dtype != np.float64 or a.size != n or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host buffers must be contiguous float64 of the right size")
+        st = _Stats()
+        self._ok(self._lib.ebv_advance_host(self._ctx, C.c_void_p(u.ctypes.data),
+                                            C.c_void_p(p.ctypes.data), C.c_int(steps),
+                                            C.c_double(dt), C.byref(st)))
+        return _stats_dict(st)
+
+    def drag(self, u, p):
+        fz, yf = C.c_double(0.0), C.c_double(0.0)
+        self._ok(self._lib.ebv_drag(self._ctx, _ptr(u), _ptr(p), C.byref(fz), C.byref(yf)))
+        return fz.value, yf.value
+
+    def launch_count(self):
+        return int(self._lib.ebv_launch_count(self._ctx))
