@@ -1,0 +1,371 @@
+"""Throughput of the embedded-boundary viscoplastic step on GB300.
+
+Workload: sphere-in-channel on [0,1]^3 at 256^3 cells, sphere r = 0.1 at the
+centre, Bi = 10 (tau0 = 50), Papanastasiou m = 1e4, inflow (0,0,1) at z = 0,
+outflow at z = 1, slip walls; seeded uniform noise of amplitude 1e-3 on the
+inflow value (synthetic; the paper's sphere study is the template).  A step is
+one full two-stage Runge-Kutta step (Algorithm 1): derived quantities, six
+viscous solves, two cell-centred and two nodal projections, solved to a
+relative residual of 1e-8.  The metric is Mcell-steps/s = cells * steps /
+seconds / 1e6 for the FP32-smoother / FP64-refinement path; the FP64 path is
+measured in the same run.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank advances its own replica (the problem does
+not shard; see the design notes) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s at 256^3 (FP32+refine, 1e-8 tol)"
+UNIT = "Mcell-steps/s"
+CPU_SAMPLE_N = 32  # oracle sample grid (same problem, coarser grid)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="cells per side (256 is the workload)")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_1905_07392_gb300 import workloads as W
+    w = W.sphere_channel_256()
+    if n != 256:
+        w.n = n
+    return w
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(k)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def make_solver(w, precision, tol=1e-8):
+    from paper_1905_07392_gb300 import ebvisc
+    return ebvisc.Solver.from_workload(w, precision=precision, tol=tol, max_iters=2000)
+
+
+def initial_state(s, w, dev):
+    import numpy as np
+    import torch
+    from paper_1905_07392_gb300 import workloads as W
+    alpha = s.geometry()["alpha"]
+    u0 = torch.tensor(W.initial_velocity(w).reshape(3, -1), device=dev)
+    u0 = (u0 * (alpha > 0)).reshape(-1).contiguous()
+    p0 = torch.zeros(s.nnode, dtype=torch.float64, device=dev)
+    return u0, p0
+
+
+def time_steps(s, u, p, steps, warmup, world, profile=False):
+    """Warm-up, then exactly `steps` steps between barriers and syncs, timed
+    with CUDA events on the solver's stream.  Returns (seconds, last stats)."""
+    import torch
+    for _ in range(warmup):
+        s.advance(u, p, stats=False)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches0 = s.launch_count()
+    if profile:
+        s.profile_begin()
+    e0.record(s.stream)
+    for _ in range(steps):
+        s.advance(u, p, stats=False)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    prof = s.profile_end() if profile else None
+    return sec, s.launch_count() - launches0, prof
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# DRAM bytes (read + write) per algorithmic byte, from one ncu capture of the
+# current kernel on a smaller grid (192^3, traffic grows with the cells);
+# the reported traffic is this ratio times the algorithmic bytes per launch.
+NCU_TRAFFIC_RATIO = {"cc_gs_colour_sweep<float>": 1.75}
+
+
+def roofline(prof, cells):
+    """Roofline of the kernel with the largest summed time among those whose
+    algorithmic bytes are stated: bytes per launch over the average
+    CUDA-event launch duration.  Also the top kernels by time."""
+    peak, src = measured_peaks()
+    ks = {k: v for k, v in prof.items() if v["launches"] > 0}
+    total = sum(v["ms"] for v in ks.values())
+    kernels = {}
+    for k, f in sorted(ks.items(), key=lambda kv: -kv[1]["ms"])[:14]:
+        e = {"launches": f["launches"], "ms": round(f["ms"], 3),
+             "share": round(f["ms"] / total, 4)}
+        if f["bytes"] > 0:
+            e["GB/s"] = round(f["bytes"] / (f["ms"] * 1e-3) / 1e9, 1)
+        kernels[k] = e
+    stated = {k: v for k, v in ks.items() if v["bytes"] > 0}
+    top = max(stated, key=lambda k: stated[k]["ms"])
+    v = stated[top]
+    avg_ms = v["ms"] / v["launches"]
+    bytes_per_launch = v["bytes"] / v["launches"]
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": peak,
+            "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "traffic": (round(NCU_TRAFFIC_RATIO[top] * bytes_per_launch, 1)
+                        if top in NCU_TRAFFIC_RATIO else None),
+            "algorithmic_bytes_per_launch": round(bytes_per_launch, 1),
+            "avg_launch_ms": round(avg_ms, 5)}, kernels
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_1905_07392_gb300 import build_lib, ebvisc
+    build_lib.build()
+    dev = torch.device("cuda", local)
+    w = workload(args.n)
+    cells = w.n ** 3
+
+    # FP32 smoother + FP64 refinement (headline)
+    s = make_solver(w, ebvisc.FP32_REFINE)
+    u, p = initial_state(s, w, dev)
+    clocks = Clocks(local)
+    clocks.start()
+    sec, launches, prof = time_steps(s, u, p, args.steps, args.warmup, world, profile=True)
+    ck = clocks.stop()
+    sec = max_over_ranks(sec, world)
+    st = s.advance(u.clone(), p.clone(), stats=True)
+    value = cells * args.steps * world / sec / 1e6
+    roof, kernels = roofline(prof, cells)
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sec / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+           "data": "synthetic (seeded noise on uniform inflow; no dataset)",
+           "config": {"workload": f"sphere_channel_{w.n}^3_bi10_m1e4", "cells": cells,
+                      "sphere_radius": w.radius, "bingham": w.bingham, "m": w.m, "tol": 1e-8,
+                      "precision": "fp32 multigrid, fp64 Krylov/residual/solution",
+                      "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2 (each cell field 134 MB at 256^3)"},
+           "roofline": roof, "kernels": kernels,
+           "clocks": ck, "gpu_launches": launches,
+           "solve_iters_last_step": st["iters"], "dt": st["dt"], "drag": st["drag"],
+           "yield_frac": st["yield_frac"]}
+    s.close()
+
+    if not args.skip_fp64:
+        s64 = make_solver(w, ebvisc.FP64)
+        u64, p64 = initial_state(s64, w, dev)
+        sec64, _, _ = time_steps(s64, u64, p64, args.steps, args.warmup, world)
+        sec64 = max_over_ranks(sec64, world)
+        st64 = s64.advance(u64.clone(), p64.clone(), stats=True)
+        out["fp64"] = {"value": round(cells * args.steps * world / sec64 / 1e6, 3), "unit": UNIT,
+                       "ms_per_step": round(1e3 * sec64 / args.steps, 3),
+                       "solve_iters_last_step": st64["iters"]}
+        # error of the FP32-smoother path against FP64 after the same steps
+        # from the same seeded state
+        def rel(a, b):
+            return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        out["fp32_vs_fp64"] = {"steps": args.warmup + args.steps, "u_rel_l2": rel(u, u64),
+                               "p_rel_l2": rel(p, p64),
+                               "drag_rel": abs(st["drag"] - st64["drag"]) / abs(st64["drag"])}
+        s64.close()
+
+    if not args.skip_e2e:
+        # end to end through the C-ABI with host buffers: every step copies
+        # u and p host->device, advances, and copies them back
+        s = make_solver(w, ebvisc.FP32_REFINE)
+        u, p = initial_state(s, w, dev)
+        uh = torch.empty(u.numel(), dtype=torch.float64, pin_memory=True)
+        ph = torch.empty(p.numel(), dtype=torch.float64, pin_memory=True)
+        uh.copy_(u.cpu())
+        ph.copy_(p.cpu())
+        un, pn = uh.numpy(), ph.numpy()
+        for _ in range(args.warmup):
+            s.advance_host(un, pn, 1)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.advance_host(un, pn, 1)
+        t1 = time.perf_counter()
+        barrier(world)
+        se = max_over_ranks(t1 - t0, world)
+        nb = 8 * (u.numel() + p.numel())
+        out["e2e"] = {"value": round(cells * args.steps * world / se / 1e6, 3), "unit": UNIT,
+                      "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+        s.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_case(n):
+    import numpy as np
+    import oracle as O
+    from paper_1905_07392_gb300 import workloads as W
+    w = workload(256)
+    w.n = n
+    g = O.Grid(n=(n, n, n), h=1.0 / n)
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_SPHERE, p=tuple(w.centre) + (w.radius,)))
+    P = O.Params(tau0=w.tau0, m=w.m, bi_cfl=w.bingham, tol=1e-8, model=w.model)
+    u = (W.initial_velocity(w).reshape(3, -1) * (geo.alpha > 0)).ravel()
+    return O, g, geo, P, u, np.zeros(g.nnode)
+
+
+def cpu_baseline(steps=3):
+    O, g, geo, P, u, p = oracle_case(CPU_SAMPLE_N)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u, p, st = O.advance(g, geo, P, u, p)
+    t = time.perf_counter() - t0
+    return {"value": round(g.ncell * steps / t / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle step(s) of the same problem on a {CPU_SAMPLE_N}^3 grid "
+                      f"(single-threaded C, FP64, tol 1e-8), {t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    O, g, geo, P, u, p = oracle_case(CPU_SAMPLE_N)
+    for _ in range(args.warmup):
+        u, p, st = O.advance(g, geo, P, u, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, p, st = O.advance(g, geo, P, u, p)
+    t = time.perf_counter() - t0
+    value = g.ncell * args.steps / t / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * t / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"sphere_channel_256^3_bi10_m1e4 (oracle sample {CPU_SAMPLE_N}^3)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one oracle step on a {CPU_SAMPLE_N}^3 grid"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    rank, world, local = dist_init(args)
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.skip_cpu and world == 1:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

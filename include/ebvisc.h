@@ -167,6 +167,18 @@ ebv_status ebv_drag(ebv_ctx *ctx, const double *u, const double *p, double *fz_h
 /* Counters for the measurement harness: kernel launches queued since the
  * context was created (host counter). */
 long long ebv_launch_count(const ebv_ctx *ctx);
+
+/* Measurement hook, no part of the method: between begin and end every kernel
+ * launch of the context is bracketed by two CUDA events on its stream.
+ * ebv_profile_end synchronises, aggregates per kernel name and returns the
+ * number of entries; ebv_profile_entry(i) gives an entry's name (static
+ * string), launch count, summed kernel time in ms and summed algorithmic bytes
+ * (the data the method must move, stated for the kernels whose roofline is
+ * reported; 0 for the others). */
+ebv_status ebv_profile_begin(ebv_ctx *ctx);
+ebv_status ebv_profile_end(ebv_ctx *ctx, int *entries);
+ebv_status ebv_profile_entry(ebv_ctx *ctx, int i, const char **name, long long *launches,
+                             double *ms, double *bytes);
 const char *ebv_last_error(const ebv_ctx *ctx);
 void ebv_destroy(ebv_ctx *ctx);
 

@@ -153,7 +153,83 @@ ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f
 
 }  // namespace
 
+namespace ebv {
+bool prof_begin_launch(Ctx *c, const char *name, double nbytes)
+{
+    ProfEvents &P = c->prof;
+    if (P.used * 2 + 2 > P.ev.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return false;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return false; }
+        P.ev.push_back(a);
+        P.ev.push_back(b);
+        P.key.push_back(0);
+        P.bytes.push_back(0.0);
+    }
+    int key = -1;
+    for (size_t q = 0; q < P.names.size() && key < 0; q++)
+        if (P.names[q] == name || strcmp(P.names[q], name) == 0) key = (int)q;
+    if (key < 0) {
+        key = (int)P.names.size();
+        P.names.push_back(name);  // string literals: live for the program
+    }
+    P.key[P.used] = key;
+    P.bytes[P.used] = nbytes;
+    cudaEventRecord(P.ev[2 * P.used], c->stream);
+    return true;
+}
+void prof_end_launch(Ctx *c)
+{
+    ProfEvents &P = c->prof;
+    cudaEventRecord(P.ev[2 * P.used + 1], c->stream);
+    P.used++;
+}
+}  // namespace ebv
+
 extern "C" {
+
+ebv_status ebv_profile_begin(ebv_ctx *c)
+{
+    if (!c) return EBV_ERR_INVALID;
+    c->prof.used = 0;
+    c->prof_on = true;
+    return EBV_OK;
+}
+
+ebv_status ebv_profile_end(ebv_ctx *c, int *entries)
+{
+    if (!c || !entries) return EBV_ERR_INVALID;
+    c->prof_on = false;
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    ProfEvents &P = c->prof;
+    const size_t K = P.names.size();
+    P.agg_launches.assign(K, 0);
+    P.agg_ms.assign(K, 0.0);
+    P.agg_bytes.assign(K, 0.0);
+    for (size_t q = 0; q < P.used; q++) {
+        float t = 0.0f;
+        EBV_CUDA_TRY(c, cudaEventElapsedTime(&t, P.ev[2 * q], P.ev[2 * q + 1]));
+        P.agg_launches[P.key[q]]++;
+        P.agg_ms[P.key[q]] += t;
+        P.agg_bytes[P.key[q]] += P.bytes[q];
+    }
+    P.used = 0;
+    *entries = (int)K;
+    return EBV_OK;
+}
+
+ebv_status ebv_profile_entry(ebv_ctx *c, int i, const char **name, long long *launches, double *ms,
+                             double *bytes)
+{
+    if (!c || !name || !launches || !ms || !bytes) return EBV_ERR_INVALID;
+    ProfEvents &P = c->prof;
+    if (i < 0 || (size_t)i >= P.agg_ms.size()) return c->fail(EBV_ERR_INVALID, "no such profile entry");
+    *name = P.names[i];
+    *launches = P.agg_launches[i];
+    *ms = P.agg_ms[i];
+    *bytes = P.agg_bytes[i];
+    return EBV_OK;
+}
 
 ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stream, ebv_ctx **out)
 {
@@ -415,6 +491,7 @@ void ebv_destroy(ebv_ctx *c)
         cudaFree(c->lx[l]); cudaFree(c->lb[l]); cudaFree(c->lr[l]); cudaFree(c->ld[l]); cudaFree(c->lt[l]);
     }
     if (c->scal_host) cudaFreeHost(c->scal_host);
+    for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     delete c;
 }
 

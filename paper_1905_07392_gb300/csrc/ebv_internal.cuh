@@ -89,7 +89,10 @@ __host__ __device__ inline bool side_dirichlet(const GridD &g, int side, int com
 // Apparent viscosity of the rheology table.
 __device__ inline double eta_of(const ParamsD &p, double sr)
 {
-    double yield = (sr > 0.0) ? -expm1(-p.m * sr) / sr : p.m;
+    // (1 - exp(-m sr)) / sr; once m sr > 40, exp(-m sr) < 2^-57 and
+    // -expm1(-m sr) rounds to 1 exactly, so the exponential is skipped.
+    const double msr = p.m * sr;
+    double yield = (sr > 0.0) ? (msr > 40.0 ? 1.0 / sr : -expm1(-msr) / sr) : p.m;
     double srf = sr > 1.0 / p.m ? sr : 1.0 / p.m;
     switch (p.model) {
     case EBV_NEWTONIAN: return p.mu;
@@ -142,6 +145,19 @@ struct NdHier {
     int nb = 0;
 };
 
+// Measurement hook (ebv_profile_begin/end): while on, every launch is
+// bracketed by two CUDA events on the context stream and keyed by kernel name.
+struct ProfEvents {
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+    std::vector<int> key;          // kernel name index of each pair
+    std::vector<double> bytes;     // algorithmic bytes of each pair (0: not stated)
+    std::vector<const char *> names;
+    size_t used = 0;
+    // aggregated by ebv_profile_end
+    std::vector<long long> agg_launches;
+    std::vector<double> agg_ms, agg_bytes;
+};
+
 struct Ctx {
     GridD g;
     ebv_params prm;
@@ -149,6 +165,8 @@ struct Ctx {
     std::string err;
     long long launches = 0;
     int device = 0;
+    bool prof_on = false;
+    ProfEvents prof;
 
     bool have_geom = false;
     // geometry (device)
@@ -189,12 +207,21 @@ struct Ctx {
     }
 };
 
-// Launch bookkeeping: every kernel launch goes through this macro.
-#define EBV_LAUNCH(ctx, kern, grid, block, smem, ...)                                   \
+// Launch bookkeeping: every kernel launch goes through these macros.
+// EBV_LAUNCH_P names the launch and states the algorithmic bytes it must move
+// (used for the roofline); EBV_LAUNCH names it after the kernel.
+bool prof_begin_launch(struct Ctx *c, const char *name, double nbytes);
+void prof_end_launch(struct Ctx *c);
+#define EBV_LAUNCH_P(ctx, name, nbytes, kern, grid, block, smem, ...)                   \
     do {                                                                                \
+        bool p_ = (ctx)->prof_on;                                                       \
+        if (p_) p_ = prof_begin_launch((ctx), (name), (nbytes));                         \
         kern<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                  \
         (ctx)->launches++;                                                              \
+        if (p_) prof_end_launch((ctx));                                                 \
     } while (0)
+#define EBV_LAUNCH(ctx, kern, grid, block, smem, ...) \
+    EBV_LAUNCH_P(ctx, #kern, 0.0, kern, grid, block, smem, __VA_ARGS__)
 
 #define EBV_CUDA_TRY(ctx, call)                                                          \
     do {                                                                                 \

@@ -40,31 +40,30 @@ __device__ inline double upwind_normal(double uL, double uR)
 // apparent viscosity"): central, one-sided quadratic next to a covered cell,
 // first order with a single neighbour, zero without one.
 __device__ inline double d_robust(const GridD &g, const uint8_t *flag, const double *f, int i,
-                                  int j, int k, int d)
+                                  int j, int k, int d, double ih)
 {
     int3 e = unit(d);
-    const double h = g.h;
     bool ip = avail(g, flag, i + e.x, j + e.y, k + e.z);
     bool im = avail(g, flag, i - e.x, j - e.y, k - e.z);
     double f0 = f[cidx(g, i, j, k)];
     if (ip && im)
-        return (f[cidx(g, i + e.x, j + e.y, k + e.z)] - f[cidx(g, i - e.x, j - e.y, k - e.z)]) /
-               (2.0 * h);
+        return (f[cidx(g, i + e.x, j + e.y, k + e.z)] - f[cidx(g, i - e.x, j - e.y, k - e.z)]) *
+               (0.5 * ih);
     if (im) {
         double f1 = f[cidx(g, i - e.x, j - e.y, k - e.z)];
         if (avail(g, flag, i - 2 * e.x, j - 2 * e.y, k - 2 * e.z)) {
             double f2 = f[cidx(g, i - 2 * e.x, j - 2 * e.y, k - 2 * e.z)];
-            return (0.5 * f2 - 2.0 * f1 + 1.5 * f0) / h;
+            return (0.5 * f2 - 2.0 * f1 + 1.5 * f0) * ih;
         }
-        return (f0 - f1) / h;
+        return (f0 - f1) * ih;
     }
     if (ip) {
         double f1 = f[cidx(g, i + e.x, j + e.y, k + e.z)];
         if (avail(g, flag, i + 2 * e.x, j + 2 * e.y, k + 2 * e.z)) {
             double f2 = f[cidx(g, i + 2 * e.x, j + 2 * e.y, k + 2 * e.z)];
-            return (-1.5 * f0 + 2.0 * f1 - 0.5 * f2) / h;
+            return (-1.5 * f0 + 2.0 * f1 - 0.5 * f2) * ih;
         }
-        return (f1 - f0) / h;
+        return (f1 - f0) * ih;
     }
     return 0.0;
 }
@@ -94,10 +93,11 @@ __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__re
         return;
     }
     double Gm[3][3];
+    const double ih = 1.0 / g.h;
 #pragma unroll
     for (int d = 0; d < 3; d++)
 #pragma unroll
-        for (int q = 0; q < 3; q++) Gm[d][q] = d_robust(g, flag, u + q * N3, i, j, k, d);
+        for (int q = 0; q < 3; q++) Gm[d][q] = d_robust(g, flag, u + q * N3, i, j, k, d, ih);
     double s2 = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; d++)
@@ -690,12 +690,14 @@ __global__ void __launch_bounds__(256) k_yield_parts(int N3, const uint8_t *__re
 ebv_status launch_strain_eta(Ctx *c, const double *u, double *eta, double *srate, double *G)
 {
     const GridD &g = c->g;
+    // u (3 words), flag (1 byte), eta (+ ||gamma||) (+ 9 gradient words)
+    const double nb = (double)ncell(g) * (8.0 * (4 + (srate ? 1 : 0) + (G ? 9 : 0)) + 1.0);
     if (G)
-        EBV_LAUNCH(c, k_strain_eta<true>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u,
-                   paramsd(c->prm), eta, srate, G);
+        EBV_LAUNCH_P(c, "strain_rate_viscosity", nb, k_strain_eta<true>, grid3(g.nx, g.ny, g.nz), block3(), 0, g,
+                     c->flag, u, paramsd(c->prm), eta, srate, G);
     else
-        EBV_LAUNCH(c, k_strain_eta<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u,
-                   paramsd(c->prm), eta, srate, nullptr);
+        EBV_LAUNCH_P(c, "strain_rate_viscosity", nb, k_strain_eta<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g,
+                     c->flag, u, paramsd(c->prm), eta, srate, nullptr);
     return EBV_OK;
 }
 

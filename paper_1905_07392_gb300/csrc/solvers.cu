@@ -117,19 +117,33 @@ __device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__
     off = s;
 }
 
-// One colour of Gauss-Seidel: x_i = (b_i + sum beta x_nb) / diag.
+// One colour of Gauss-Seidel in place: x_i = (b_i + sum beta x_nb) / diag for
+// the cells of colour `color` ((i+j+k) mod 2); with zero_start the other
+// colour reads as 0 (the sweep starts from x = 0) and x is not read.
 template <class T>
 __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, const T *__restrict__ b,
-                                               int color)
+                                               int color, int zero_start)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     const GridD &g = A.g;
-    if (i >= g.nx || j >= g.ny || k >= g.nz || ((i + j + k) & 1) != color) return;
-    T diag, off;
-    cc_row(A, i, j, k, x, diag, off);
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const int c = cidx(g, i, j, k);
+    if (((i + j + k) & 1) != color) {
+        if (zero_start) x[c] = T(0);
+        return;
+    }
+    T diag, off;
+    if (zero_start) {
+        const T bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
+        const T byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
+        const T bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
+        diag = A.extra[c] + bxl + bxh + byl + byh + bzl + bzh;
+        off = T(0);
+    } else {
+        cc_row(A, i, j, k, x, diag, off);
+    }
     x[c] = diag > T(0) ? (b[c] + off) / diag : T(0);
 }
 
@@ -382,30 +396,58 @@ struct NdOp {
     const uint8_t *act;    // nodes
 };
 
+// Row of the nodal operator at node (i,j,k), assembled in stencil form.  With
+// a[r][q][p] the volume fraction of the cell (i-1+p, j-1+q, k-1+r) (0 outside
+// the box), the element matrix gives: centre (1/3) sum a; axis neighbours 0;
+// each face-diagonal neighbour -(sum of the two cells sharing that edge)/12;
+// each body-diagonal neighbour -(the one cell between them)/12.  Inactive
+// neighbours hold x = 0 in every vector the solvers pass here.
 template <class T>
 __device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__restrict__ x, T &diag,
                               T &ax)
 {
     const GridD &g = A.g;
-    T s = 0, dsum = 0;
-    for (int oc = 0; oc < 8; oc++) {
-        int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
-        if (!inbox(g, ci, cj, ck)) continue;
-        T al = A.alpha[cidx(g, ci, cj, ck)];
-        if (!(al > T(0))) continue;
-        int oa = (i - ci) | ((j - cj) << 1) | ((k - ck) << 2);
-        T cs = 0;
-        for (int ob = 0; ob < 8; ob++) {
-            int bi = ci + (ob & 1), bj = cj + ((ob >> 1) & 1), bk = ck + ((ob >> 2) & 1);
-            int n = nidx(g, bi, bj, bk);
-            if (!A.act[n]) continue;
-            cs += T(kQ1[__popc(oa ^ ob)]) * x[n];
+    const int NXn = g.nx + 1, NYn = g.ny + 1;
+    T a[2][2][2];
+    T sa = 0;
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+            for (int p = 0; p < 2; p++) {
+                int ci = i - 1 + p, cj = j - 1 + q, ck = k - 1 + r;
+                T v = inbox(g, ci, cj, ck) ? A.alpha[cidx(g, ci, cj, ck)] : T(0);
+                a[r][q][p] = v;
+                sa += v;
+            }
+    const int n0 = nidx(g, i, j, k);
+    auto X = [&](int di, int dj, int dk) -> T {
+        int ii = i + di, jj = j + dj, kk = k + dk;
+        if ((unsigned)ii > (unsigned)g.nx || (unsigned)jj > (unsigned)g.ny || (unsigned)kk > (unsigned)g.nz)
+            return T(0);
+        return x[n0 + di + dj * NXn + dk * NXn * NYn];
+    };
+    T s = 0;
+    // face diagonals in the xy, xz and yz planes
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            s += (a[0][q][p] + a[1][q][p]) * X(2 * p - 1, 2 * q - 1, 0);
+            s += (a[q][0][p] + a[q][1][p]) * X(2 * p - 1, 0, 2 * q - 1);
+            s += (a[q][p][0] + a[q][p][1]) * X(0, 2 * p - 1, 2 * q - 1);
         }
-        s += al * cs;
-        dsum += al;
-    }
-    ax = T(g.h) * s;
-    diag = T(g.h) * dsum * T(1.0 / 3.0);
+    // body diagonals
+#pragma unroll
+    for (int r = 0; r < 2; r++)
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+            for (int p = 0; p < 2; p++) s += a[r][q][p] * X(2 * p - 1, 2 * q - 1, 2 * r - 1);
+    const T hh = T(g.h);
+    diag = hh * sa * T(1.0 / 3.0);
+    ax = diag * x[n0] - hh * T(1.0 / 12.0) * s;
 }
 
 // One Chebyshev step: r = b - A x_in; d = cd d + cr D^-1 r; x_out = x_in + d.
@@ -495,16 +537,17 @@ __global__ void k_nd_restrict(GridD gf, const T *__restrict__ rf, GridD gc, cons
     bc[N] = s;
 }
 
+// xout = xin + trilinear interpolation of the coarse correction (active nodes).
 template <class T>
 __global__ void k_nd_prolong(GridD gf, const uint8_t *__restrict__ actf, GridD gc, const T *__restrict__ xc,
-                             T *__restrict__ xf)
+                             const T *__restrict__ xin, T *__restrict__ xout)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i > gf.nx || j > gf.ny || k > gf.nz) return;
     const int n = nidx(gf, i, j, k);
-    if (!actf[n]) return;
+    if (!actf[n]) { xout[n] = T(0); return; }
     int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
     int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
     T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
@@ -517,7 +560,7 @@ __global__ void k_nd_prolong(GridD gf, const uint8_t *__restrict__ actf, GridD g
     if ((i & 1) && (k & 1)) s += xc[nidx(gc, i1, j0, k1)];
     if ((j & 1) && (k & 1)) s += xc[nidx(gc, i0, j1, k1)];
     if ((i & 1) && (j & 1) && (k & 1)) s += xc[nidx(gc, i1, j1, k1)];
-    xf[n] += wi * wj * wk * s;
+    xout[n] = xin[n] + wi * wj * wk * s;
 }
 
 __global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<double> A, const double *__restrict__ p,
@@ -728,18 +771,6 @@ __global__ void k_zero_inactive(int n, const uint8_t *__restrict__ act, double *
         if (!act[s]) x[s] = 0.0;
 }
 
-template <class T>
-__global__ void k_zero(T *a, int n)
-{
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) a[s] = T(0);
-}
-
-template <class T>
-void zero(Ctx *c, T *a, int n)
-{
-    EBV_LAUNCH(c, k_zero<T>, dim3(std::min(kReduceBlocks, (n + 255) / 256)), dim3(256), 0, a, n);
-}
-
 inline dim3 cgrid(const GridD &g) { return grid3(g.nx, g.ny, g.nz); }
 inline dim3 ngrid(const GridD &g) { return grid3(g.nx + 1, g.ny + 1, g.nz + 1); }
 inline int nblocks3(dim3 b) { return b.x * b.y * b.z; }
@@ -772,29 +803,39 @@ NdOp<T> ndop(const NdLevel &L)
 // V-cycles
 // ---------------------------------------------------------------------------
 
+// Two red-black Gauss-Seidel sweeps in place (the first from x = 0 when
+// zero_start), each as two colour passes.
 template <class T>
-void cc_smooth(Ctx *c, const CcLevel &L, T *x, const T *b, bool red_first)
+void cc_smooth2(Ctx *c, const CcLevel &L, T *x, T *t, const T *b, bool red_first, bool zero_start)
 {
+    (void)t;
     CcOp<T> A = ccop<T>(L);
-    int c0 = red_first ? 0 : 1;
-    EBV_LAUNCH(c, k_cc_gs<T>, cgrid(L.g), block3(), 0, A, x, b, c0);
-    EBV_LAUNCH(c, k_cc_gs<T>, cgrid(L.g), block3(), 0, A, x, b, 1 - c0);
+    const int c0 = red_first ? 0 : 1;
+    const GridD &g = L.g;
+    // algorithmic bytes of one colour pass: half of one sweep's x read and
+    // write, b, extra and 3 face coefficients
+    const double nb = 3.5 * sizeof(T) * (double)ncell(g);
+    for (int s = 0; s < 2; s++) {
+        const int z = (s == 0 && zero_start) ? 1 : 0;
+        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_gs_colour_sweep<float>" : "cc_gs_colour_sweep<double>", nb, k_cc_gs<T>, cgrid(g), block3(), 0, A, x, b, c0, z);
+        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_gs_colour_sweep<float>" : "cc_gs_colour_sweep<double>", nb, k_cc_gs<T>, cgrid(g), block3(), 0, A, x, b, 1 - c0, 0);
+    }
 }
 
 template <class T>
 void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
 {
-    const int nu = 2;
     const int Lb = H.L - 1;
     for (int l = 0; l < Lb; l++) {
         const CcLevel &L = H.lv[l];
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
-        zero(c, x, ncell(L.g));
-        for (int s = 0; s < nu; s++) cc_smooth<T>(c, L, x, b, true);
+        cc_smooth2<T>(c, L, x, (T *)c->lt[l], b, true, true);
         const CcLevel &Lc = H.lv[l + 1];
-        EBV_LAUNCH(c, k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, ccop<T>(L), x, b, Lc.g,
-                   (T *)c->lb[l + 1]);
+        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_residual_restrict<float>" : "cc_residual_restrict<double>",
+                     (6.0 + 1.0 / 8.0) * sizeof(T) * (double)ncell(L.g),
+                     k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, ccop<T>(L), x, b, Lc.g,
+                     (T *)c->lb[l + 1]);
     }
     {
         T *x = Lb ? (T *)c->lx[Lb] : x0;
@@ -807,7 +848,7 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         const T *b = l ? (const T *)c->lb[l] : b0;
         EBV_LAUNCH(c, k_cc_prolong<T>, cgrid(L.g), block3(), 0, L.g, H.lv[l + 1].g, L.cov,
                    (const T *)c->lx[l + 1], x);
-        for (int s = 0; s < nu; s++) cc_smooth<T>(c, L, x, b, false);
+        cc_smooth2<T>(c, L, x, (T *)c->lt[l], b, false, false);
     }
 }
 
@@ -830,26 +871,24 @@ inline ChebCoef cheb_coef(double lmax)
     return k;
 }
 
-// Chebyshev smoothing of A x = b; x holds the start (zero if zero_start) and
-// the result.  Uses ld (direction) and lt (ping-pong) of the level.
+// Three Chebyshev steps on A x = b, ending in x.  From zero: (0) -> x -> t -> x.
+// Otherwise the start is in t: t -> x -> t -> x.  d is the level's direction.
 template <class T>
-void nd_smooth(Ctx *c, const NdLevel &L, int l, T *x, const T *b, bool zero_start)
+void nd_smooth(Ctx *c, const NdLevel &L, int l, T *x, T *t, const T *b, bool zero_start)
 {
     NdOp<T> A = ndop<T>(L);
     ChebCoef k = cheb_coef(L.lam_max);
-    T *d = (T *)c->ld[l], *t = (T *)c->lt[l];
-    T *src = x, *dst = t;
+    T *d = (T *)c->ld[l];
+    T *src = zero_start ? x : t, *dst = x;
     for (int s = 0; s < 3; s++) {
-        EBV_LAUNCH(c, k_nd_cheb<T>, ngrid(L.g), block3(), 0, A, src, dst, d, b, (T)k.cd[s], (T)k.cr[s],
-                   (int)(s == 0 && zero_start));
-        T *tmp = src;
+        // per node: x in/out, d in/out, b, alpha of one cell (the first step
+        // from zero reads only b and alpha and writes d, x)
+        const bool z0 = s == 0 && zero_start;
+        const double nb = (z0 ? 4.0 : 6.0) * sizeof(T) * (double)nnode(L.g);
+        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "nodal_chebyshev_step<float>" : "nodal_chebyshev_step<double>", nb, k_nd_cheb<T>, ngrid(L.g), block3(), 0, A, src, dst, d, b, (T)k.cd[s],
+                     (T)k.cr[s], (int)z0);
         src = dst;
-        dst = tmp;
-    }
-    // three steps: the result is in t; copy back into x by one more swap-free pass
-    if (src != x) {
-        const int n = nnode(L.g);
-        EBV_LAUNCH(c, (k_convert<T, T>), dim3(std::min(kReduceBlocks, (n + 255) / 256)), dim3(256), 0, src, x, n);
+        dst = (dst == x) ? t : x;
     }
 }
 
@@ -861,7 +900,7 @@ void nd_vcycle(Ctx *c, NdHier &H, const T *b0, T *x0)
         const NdLevel &L = H.lv[l];
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
-        nd_smooth<T>(c, L, l, x, b, true);
+        nd_smooth<T>(c, L, l, x, (T *)c->lt[l], b, true);
         EBV_LAUNCH(c, k_nd_resid<T>, ngrid(L.g), block3(), 0, ndop<T>(L), x, b, (T *)c->lr[l]);
         const NdLevel &Lc = H.lv[l + 1];
         EBV_LAUNCH(c, k_nd_restrict<T>, ngrid(Lc.g), block3(), 0, L.g, (const T *)c->lr[l], Lc.g, Lc.act,
@@ -876,9 +915,10 @@ void nd_vcycle(Ctx *c, NdHier &H, const T *b0, T *x0)
         const NdLevel &L = H.lv[l];
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
+        // t = x + P x_coarse, then smooth from t back into x
         EBV_LAUNCH(c, k_nd_prolong<T>, ngrid(L.g), block3(), 0, L.g, L.act, H.lv[l + 1].g,
-                   (const T *)c->lx[l + 1], x);
-        nd_smooth<T>(c, L, l, x, b, false);
+                   (const T *)c->lx[l + 1], x, (T *)c->lt[l]);
+        nd_smooth<T>(c, L, l, x, (T *)c->lt[l], b, false);
     }
 }
 
@@ -963,7 +1003,9 @@ struct CcProblem : Problem {
     int apply_blocks() const override { return nblocks3(cgrid(H->lv[0].g)); }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
-        EBV_LAUNCH(c, k_cc_apply_dot, cgrid(H->lv[0].g), block3(), 0, ccop<double>(H->lv[0]), p, q, c->part);
+        // p, extra, 3 faces, q: 6 words per cell
+        EBV_LAUNCH_P(c, "cc_apply_fp64", 48.0 * n(), k_cc_apply_dot, cgrid(H->lv[0].g), block3(), 0,
+                     ccop<double>(H->lv[0]), p, q, c->part);
     }
     void precond(Ctx *c, const double *r, double *z) override
     {
@@ -985,7 +1027,9 @@ struct NdProblem : Problem {
     int apply_blocks() const override { return nblocks3(ngrid(H->lv[0].g)); }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
-        EBV_LAUNCH(c, k_nd_apply_dot, ngrid(H->lv[0].g), block3(), 0, ndop<double>(H->lv[0]), p, q, c->part);
+        // p, alpha, q: 3 words per node
+        EBV_LAUNCH_P(c, "nodal_apply_fp64", 24.0 * n(), k_nd_apply_dot, ngrid(H->lv[0].g), block3(), 0,
+                     ndop<double>(H->lv[0]), p, q, c->part);
     }
     void precond(Ctx *c, const double *r, double *z) override
     {

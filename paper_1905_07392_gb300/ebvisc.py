@@ -55,7 +55,8 @@ EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geom
            "ebv_build_geometry_plane", "ebv_get_geometry", "ebv_update_viscosity", "ebv_derived",
            "ebv_face_states", "ebv_solve_mac", "ebv_solve_viscous", "ebv_solve_projection",
            "ebv_timestep", "ebv_advance", "ebv_advance_host", "ebv_drag", "ebv_launch_count",
-           "ebv_last_error", "ebv_destroy"]
+           "ebv_profile_begin", "ebv_profile_end", "ebv_profile_entry", "ebv_last_error",
+           "ebv_destroy"]
 
 _lib = None
 
@@ -87,6 +88,10 @@ def load(path: str = LIB_PATH):
         "ebv_advance_host": ([vp, vp, vp, C.c_int, C.c_double, C.POINTER(_Stats)], C.c_int),
         "ebv_drag": ([vp, vp, vp, dp, dp], C.c_int),
         "ebv_launch_count": ([vp], C.c_longlong),
+        "ebv_profile_begin": ([vp], C.c_int),
+        "ebv_profile_end": ([vp, ip], C.c_int),
+        "ebv_profile_entry": ([vp, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong), dp,
+                               dp], C.c_int),
         "ebv_last_error": ([vp], C.c_char_p),
         "ebv_destroy": ([vp], None),
     }
@@ -299,3 +304,21 @@ class Solver:
 
     def launch_count(self):
         return int(self._lib.ebv_launch_count(self._ctx))
+
+    def profile_begin(self):
+        """Time every kernel launch of this context with CUDA events."""
+        self._ok(self._lib.ebv_profile_begin(self._ctx))
+
+    def profile_end(self):
+        """Per kernel name: launches, summed kernel ms, summed algorithmic bytes."""
+        n = C.c_int(0)
+        self._ok(self._lib.ebv_profile_end(self._ctx, C.byref(n)))
+        out = {}
+        for i in range(n.value):
+            name, L = C.c_char_p(), C.c_longlong(0)
+            ms, by = C.c_double(0.0), C.c_double(0.0)
+            self._ok(self._lib.ebv_profile_entry(self._ctx, i, C.byref(name), C.byref(L),
+                                                 C.byref(ms), C.byref(by)))
+            out[name.value.decode()] = {"launches": int(L.value), "ms": float(ms.value),
+                                        "bytes": float(by.value)}
+        return out
