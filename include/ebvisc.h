@@ -46,7 +46,8 @@ typedef enum {
     EBV_ERR_CUDA = -2,           /* a CUDA call failed (text in ebv_last_error) */
     EBV_ERR_NOT_CONVERGED = -3,  /* a linear solve hit max_iters above tol */
     EBV_ERR_NAN = -5,            /* a residual became NaN or Inf */
-    EBV_ERR_GEOMETRY = -6        /* geometry missing or unsupported */
+    EBV_ERR_GEOMETRY = -6,       /* geometry missing or unsupported */
+    EBV_ERR_TOO_LARGE = -7       /* beyond the fixed working storage of ebv_drag_noalloc */
 } ebv_status;
 
 /* Box side types, sides ordered x-, x+, y-, y+, z-, z+. */
@@ -163,6 +164,29 @@ ebv_status ebv_advance_host(ebv_ctx *ctx, double *u_host, double *p_host, int st
  * unyielded fluid volume fraction (||tau|| <= (1 + 1e-3) tau0), host outputs. */
 ebv_status ebv_drag(ebv_ctx *ctx, const double *u, const double *p, double *fz_host,
                     double *yield_frac_host);
+
+/* The drag and unyielded fraction of ebv_drag for callers that cannot allocate
+ * GPU memory (they run inside a memory pool they do not own, must not grow
+ * device memory after start-up, or may only touch the buffers they are given).
+ * The paper has no counterpart: this is a deployment variant, not a step of
+ * the method.  It needs no context: the caller passes the grid and parameters,
+ * the geometry as returned by ebv_get_geometry (alpha, area, nrm, bcen, flag),
+ * the ascending list `cut` of the ncut cells with flag 2, the fields u and p,
+ * and `out` (2 doubles: F_z, unyielded fraction) -- all device pointers -- and
+ * a cudaStream_t (NULL: legacy default stream).  Nothing is allocated; the
+ * working storage is a fixed array of about 6.3 MB that every GPU loading the
+ * library holds until the process exits, so grids of more than 262,144 cells
+ * (e.g. 64^3) or more than 65,536 cut cells return EBV_ERR_TOO_LARGE.  The
+ * first call on each device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array and every call writes what it reads, so nothing carries
+ * over between calls, but calls whose work overlaps on the GPU (other streams,
+ * other threads) race on it and must be serialised by the caller.  Work is
+ * queued asynchronously on `stream`; `out` is valid once it completes. */
+ebv_status ebv_drag_noalloc(const ebv_grid *grid, const ebv_params *params, const double *alpha,
+                            const double *area, const double *nrm, const double *bcen,
+                            const unsigned char *flag, const int *cut, int ncut, const double *u,
+                            const double *p, double *out, void *stream);
 
 /* Counters for the measurement harness: kernel launches queued since the
  * context was created (host counter). */

@@ -844,3 +844,110 @@ ebv_status launch_drag(Ctx *c, const double *u, const double *p, double *fz, dou
 }
 
 }  // namespace ebv
+
+// ===========================================================================
+// Drag and yielded fraction without any allocation
+// ===========================================================================
+// Some callers cannot call cudaMalloc: code that runs inside a memory pool
+// they do not own, a host that must not grow device memory after start-up, or
+// a plug-in that may only use the buffers it is handed.  ebv_drag_noalloc
+// serves them: it runs the same kernels as ebv_drag, but its working storage
+// is the fixed array below, which the library places in the memory of every
+// GPU that loads it and which stays there until the process exits.
+#include <mutex>
+
+namespace ebv {
+namespace {
+
+constexpr int kNoAllocCells = 1 << 18;  // cells of the largest grid accepted (e.g. 64^3)
+constexpr int kNoAllocCut = 1 << 16;    // cut cells of the largest geometry accepted
+// eta and ||gamma|| per cell, wall gradients (3) and traction terms per cut
+// cell, two sets of block partial sums, three results: about 6.3 MB.
+constexpr size_t kNoAllocDoubles =
+    2 * (size_t)kNoAllocCells + 4 * (size_t)kNoAllocCut + 2 * (size_t)kReduceBlocks + 8;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// Device address of g_noalloc_scratch per device.  In host code the array's
+// name only stands in for it; the address comes from cudaGetSymbolAddress,
+// taken once per device with that device current.
+constexpr int kNoAllocMaxDevices = 64;
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+__global__ void __launch_bounds__(1024) k_noalloc_sum(const double *part, int n, double *out)
+{
+    double v = 0.0;
+    for (int s = threadIdx.x; s < n; s += 1024) v += part[s];
+    v = block_sum<1024>(v);
+    if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void k_noalloc_finish(const double *sums, double *out)
+{
+    if (threadIdx.x != 0) return;
+    out[0] = sums[0];
+    out[1] = sums[2] > 0.0 ? sums[1] / sums[2] : 0.0;
+}
+
+}  // namespace
+}  // namespace ebv
+
+extern "C" ebv_status ebv_drag_noalloc(const ebv_grid *grid, const ebv_params *params,
+                                       const double *alpha, const double *area, const double *nrm,
+                                       const double *bcen, const unsigned char *flag, const int *cut,
+                                       int ncut, const double *u, const double *p, double *out,
+                                       void *stream)
+{
+    using namespace ebv;
+    if (!grid || !params || !alpha || !area || !nrm || !bcen || !flag || !u || !p || !out)
+        return EBV_ERR_INVALID;
+    if (ncut < 0 || (ncut > 0 && !cut)) return EBV_ERR_INVALID;
+    for (int d = 0; d < 3; d++)
+        if (grid->n[d] < 1) return EBV_ERR_INVALID;
+    const long long n3 = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    if (n3 > kNoAllocCells || ncut > kNoAllocCut) return EBV_ERR_TOO_LARGE;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return EBV_ERR_CUDA;
+    double *scr = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            void *a = nullptr;
+            if (cudaGetSymbolAddress(&a, g_noalloc_scratch) != cudaSuccess) return EBV_ERR_CUDA;
+            g_noalloc_addr[dev] = (double *)a;
+        }
+        scr = g_noalloc_addr[dev];
+    }
+    double *eta = scr, *sr = scr + kNoAllocCells;
+    double *dudn = scr + 2 * (size_t)kNoAllocCells;
+    double *term = dudn + 3 * (size_t)kNoAllocCut;
+    double *part = term + kNoAllocCut;
+    double *sums = part + 2 * (size_t)kReduceBlocks;
+
+    GridD g;
+    g.nx = grid->n[0]; g.ny = grid->n[1]; g.nz = grid->n[2];
+    g.h = grid->h;
+    for (int d = 0; d < 3; d++) { g.lo[d] = grid->lo[d]; g.u_in[d] = grid->u_in[d]; }
+    for (int s = 0; s < 6; s++) g.bc[s] = grid->bc[s];
+    GeomD geo;
+    geo.alpha = alpha; geo.ax = geo.ay = geo.az = nullptr; geo.area = area; geo.nrm = nrm;
+    geo.bcen = bcen; geo.flag = flag; geo.cut = cut; geo.ncut = ncut; geo.ncell = (int)n3;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // every scratch value read below is written earlier in this call, so no
+    // clearing is needed
+    k_strain_eta<false><<<grid3(g.nx, g.ny, g.nz), block3(), 0, st>>>(g, flag, u, paramsd(*params), eta, sr,
+                                                                      nullptr);
+    if (ncut) {
+        k_wall_dudn<<<(ncut + 127) / 128, 128, 0, st>>>(g, geo, u, dudn);
+        k_drag_terms<<<(ncut + 127) / 128, 128, 0, st>>>(g, geo, eta, dudn, p, term);
+    }
+    k_noalloc_sum<<<1, 1024, 0, st>>>(term, ncut, sums);
+    k_yield_parts<<<kReduceBlocks, 256, 0, st>>>((int)n3, flag, alpha, eta, sr, params->tau0, part);
+    k_noalloc_sum<<<1, 1024, 0, st>>>(part, kReduceBlocks, sums + 1);
+    k_noalloc_sum<<<1, 1024, 0, st>>>(part + kReduceBlocks, kReduceBlocks, sums + 2);
+    k_noalloc_finish<<<1, 32, 0, st>>>(sums, out);
+    if (cudaGetLastError() != cudaSuccess) return EBV_ERR_CUDA;
+    return EBV_OK;
+}

@@ -56,7 +56,7 @@ EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geom
            "ebv_face_states", "ebv_solve_mac", "ebv_solve_viscous", "ebv_solve_projection",
            "ebv_timestep", "ebv_advance", "ebv_advance_host", "ebv_drag", "ebv_launch_count",
            "ebv_profile_begin", "ebv_profile_end", "ebv_profile_entry", "ebv_last_error",
-           "ebv_destroy"]
+           "ebv_destroy", "ebv_drag_noalloc"]
 
 _lib = None
 
@@ -94,6 +94,8 @@ def load(path: str = LIB_PATH):
                                dp], C.c_int),
         "ebv_last_error": ([vp], C.c_char_p),
         "ebv_destroy": ([vp], None),
+        "ebv_drag_noalloc": ([C.POINTER(_Grid), C.POINTER(_Params)] + [vp] * 6 + [C.c_int]
+                             + [vp] * 4, C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -118,6 +120,29 @@ def _check_f64(t, n, name):
     import torch
     if t.dtype != torch.float64 or t.numel() != n:
         raise ValueError(f"{name}: expected {n} float64 values, got {t.numel()} {t.dtype}")
+
+
+STATUS[-7] = "EBV_ERR_TOO_LARGE"
+
+
+def drag_noalloc(solver, geometry, cut, u, p, out, stream=None):
+    """Drag and unyielded fraction through ebv_drag_noalloc, which allocates
+    no GPU memory (for callers that cannot).  `solver` supplies only the grid
+    and parameters (no context is used); `geometry` is Solver.geometry();
+    `cut` an int32 CUDA tensor of the cells with flag 2 in ascending order;
+    `out` a float64 CUDA tensor of 2 values (F_z, unyielded fraction)."""
+    import torch
+    lib = load()
+    if cut.dtype != torch.int32:
+        raise ValueError("cut must be int32")
+    st = lib.ebv_drag_noalloc(C.byref(solver._grid), C.byref(solver._params_c()),
+                              _ptr(geometry["alpha"]), _ptr(geometry["area"]),
+                              _ptr(geometry["nrm"]), _ptr(geometry["bcen"]),
+                              _ptr(geometry["flag"]), _ptr(cut) if cut.numel() else None,
+                              C.c_int(cut.numel()), _ptr(u), _ptr(p), _ptr(out),
+                              C.c_void_p((stream or torch.cuda.current_stream()).cuda_stream))
+    if st != 0:
+        raise EbvError(st, "ebv_drag_noalloc failed")
 
 
 def _stats_dict(st):
