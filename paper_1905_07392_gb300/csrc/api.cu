@@ -269,9 +269,12 @@ ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stre
     ok &= alloc(&c->ps, NN) && alloc(&c->uf, NF) && alloc(&c->phi, N3) && alloc(&c->G, 9 * N3) &&
           alloc(&c->DC, 3 * N3) && alloc(&c->dD, 3 * N3) && alloc(&c->Dh, 3 * N3) && alloc(&c->wts, N3) &&
           alloc(&c->srate, N3) && alloc(&c->rhs_c, std::max(N3, (size_t)1)) && alloc(&c->rhs_n, NN);
+    ok &= alloc(&c->nearm, N3) && alloc(&c->ff, 3 * NF);
     ok &= alloc(&c->dt_dev, 1) && alloc(&c->cfl_max, 2);
     ok &= alloc(&c->u_host_dev, 3 * N3) && alloc(&c->p_host_dev, NN);
     ok &= alloc(&c->kr, V) && alloc(&c->kz, V) && alloc(&c->kp, V) && alloc(&c->kq, V);
+    ok &= alloc(&c->kr32, V) && alloc(&c->kz32, V) && alloc(&c->kp32, V) && alloc(&c->kq32, V) &&
+          alloc(&c->ke32, V);
     ok &= alloc(&c->part, (size_t)1 << 20) && alloc(&c->scal, 32);
     ok &= cudaMallocHost(&c->scal_host, 32 * sizeof(double)) == cudaSuccess;
     c->vec_len = V;
@@ -464,7 +467,8 @@ void ebv_destroy(ebv_ctx *c)
     void *ptrs[] = {c->alpha, c->ax, c->ay, c->az, c->area, c->nrm, c->bcen, c->flag, c->cut, c->Cm, c->Vm,
                     c->Cs, c->Vs, c->em, c->es, c->psi, c->ut, c->us, c->ps, c->uf, c->phi, c->G, c->DC,
                     c->dD, c->Dh, c->wts, c->dudn, c->srate, c->rhs_c, c->rhs_n, c->u_host_dev, c->p_host_dev,
-                    c->dt_dev, c->cfl_max, c->kr, c->kz, c->kp, c->kq, c->part, c->scal};
+                    c->dt_dev, c->cfl_max, c->kr, c->kz, c->kp, c->kq, c->part, c->scal, c->nearm,
+                    c->nearl, c->ff, c->kr32, c->kz32, c->kp32, c->kq32, c->ke32};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     CcHier *hs[2] = {&c->mac, &c->visc};
@@ -472,7 +476,7 @@ void ebv_destroy(ebv_ctx *c)
         CcHier *H = hs[h];
         for (int l = 0; l < H->L; l++) {
             CcLevel &L = H->lv[l];
-            cudaFree(L.extra_d); cudaFree(L.extra_f);
+            cudaFree(L.extra_d); cudaFree(L.extra_f); cudaFree(L.diag_d); cudaFree(L.diag_f);
             for (int d = 0; d < 3; d++) { cudaFree(L.bf_d[d]); cudaFree(L.bf_f[d]); }
             if (h == 0) cudaFree(L.cov);
         }
@@ -484,6 +488,7 @@ void ebv_destroy(ebv_ctx *c)
         if (l) cudaFree(L.alpha_d);
         cudaFree(L.alpha_f);
         cudaFree(L.act);
+        cudaFree(L.reg);
     }
     cudaFree(c->nd.binv);
     cudaFree(c->nd.bmat);

@@ -116,8 +116,8 @@ inline dim3 grid3(int nx, int ny, int nz) { return dim3((nx + 31) / 32, (ny + 3)
 
 struct CcLevel {
     GridD g;            // dims and h of this level (bc shared)
-    double *extra_d = nullptr, *bf_d[3] = {nullptr, nullptr, nullptr};
-    float *extra_f = nullptr, *bf_f[3] = {nullptr, nullptr, nullptr};
+    double *extra_d = nullptr, *diag_d = nullptr, *bf_d[3] = {nullptr, nullptr, nullptr};
+    float *extra_f = nullptr, *diag_f = nullptr, *bf_f[3] = {nullptr, nullptr, nullptr};
     uint8_t *cov = nullptr;  // 1 where the cell is covered (identity row)
 };
 
@@ -134,6 +134,7 @@ struct NdLevel {
     double *alpha_d = nullptr;   // cell volume fractions at this level
     float *alpha_f = nullptr;
     uint8_t *act = nullptr;      // 1 for active nodes
+    uint8_t *reg = nullptr;      // level 0: 1 where all 8 cells around the node are full
     double lam_max = 2.0;        // bound of the spectrum of D^-1 A
 };
 
@@ -175,12 +176,16 @@ struct Ctx {
     uint8_t *flag = nullptr;
     int *cut = nullptr;
     int ncut = 0;
+    uint8_t *nearm = nullptr;    // 1 for fluid cells that are cut or have a cut neighbour
+    int *nearl = nullptr;        // those cells, ascending
+    int nnear = 0;
 
     // work fields (device)
     double *Cm = nullptr, *Vm = nullptr, *Cs = nullptr, *Vs = nullptr;
     double *em = nullptr, *es = nullptr, *psi = nullptr, *ut = nullptr, *us = nullptr;
     double *ps = nullptr, *uf = nullptr, *phi = nullptr, *G = nullptr, *DC = nullptr;
     double *dD = nullptr, *Dh = nullptr, *wts = nullptr, *dudn = nullptr, *srate = nullptr;
+    double *ff = nullptr;        // face fluxes: 3 components x face triple
     double *rhs_c = nullptr;     // cell rhs scratch
     double *rhs_n = nullptr;     // nodal rhs scratch
     double *u_host_dev = nullptr, *p_host_dev = nullptr;  // device copies for host-buffer steps
@@ -195,6 +200,8 @@ struct Ctx {
     void *lt[kMaxLevels] = {};
     // Krylov vectors (FP64)
     double *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr;
+    // FP32 inner Krylov vectors of the refinement solver
+    float *kr32 = nullptr, *kz32 = nullptr, *kp32 = nullptr, *kq32 = nullptr, *ke32 = nullptr;
     double *part = nullptr;      // block partial sums
     double *scal = nullptr;      // device scalars
     double *scal_host = nullptr; // pinned mirror

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__re
 }
 
 // ---- normal face velocities (slopes, extrapolation, upwinding) ------------
-__global__ void k_face_states(GridD g, int d, const uint8_t *__restrict__ flag,
+__global__ void k_face_states(GridD g, int d, const double *__restrict__ S,
                               const double *__restrict__ ap, const double *__restrict__ u,
                               double *__restrict__ uf)
 {
@@ -141,9 +141,10 @@ __global__ void k_face_states(GridD g, int d, const uint8_t *__restrict__ flag,
             else if (g.bc[side] == EBV_OUTFLOW) v = ud[cidx(g, cc[0], cc[1], cc[2])];
         } else {
             int3 e = unit(d);
-            double uL = ud[cidx(g, i - e.x, j - e.y, k - e.z)] +
-                        0.5 * mc_slope(g, flag, ud, i - e.x, j - e.y, k - e.z, d);
-            double uR = ud[cidx(g, i, j, k)] - 0.5 * mc_slope(g, flag, ud, i, j, k, d);
+            const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
+            const double *Sd = S + (3 * d + d) * N3;
+            double uL = ud[cL] + 0.5 * Sd[cL];
+            double uR = ud[cR] - 0.5 * Sd[cR];
             v = upwind_normal(uL, uR);
         }
     }
@@ -195,78 +196,147 @@ __global__ void k_mac_correct(GridD g, int d, const double *__restrict__ ap,
     }
 }
 
-// ---- convective flux divergence (conservative part D^C) -------------------
-__global__ void __launch_bounds__(256) k_convective_dc(GridD g, const uint8_t *__restrict__ flag,
-                                                       const double *__restrict__ alpha,
-                                                       const double *__restrict__ ax,
-                                                       const double *__restrict__ ay,
-                                                       const double *__restrict__ az,
-                                                       const double *__restrict__ u,
-                                                       const double *__restrict__ uf,
-                                                       double *__restrict__ DC)
+// Position of cell c in the ascending list of cut cells, -1 if absent.
+__device__ inline int find_cut(const int *cut, int ncut, int c)
+{
+    int lo = 0, hi = ncut - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = cut[mid];
+        if (v == c) return mid;
+        if (v < c) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// ---- limited slopes of the three components along the three axes ----------
+// S[(3 d + q) N3 + c]: slope of u_q at c along d (zero on covered cells).
+__global__ void __launch_bounds__(256) k_slopes(GridD g, const uint8_t *__restrict__ flag,
+                                                const double *__restrict__ u, double *__restrict__ S)
 {
     CELL_INDEX
     const int N3 = ncell(g);
-    if (flag[c] == 0) {
-        for (int q = 0; q < 3; q++) DC[q * N3 + c] = 0.0;
+    const bool fl = flag[c] != 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+            S[(3 * d + q) * N3 + c] = fl ? mc_slope(g, flag, u + q * N3, i, j, k, d) : 0.0;
+}
+
+// ---- convective face fluxes  F_q = a_f * (upwinded state of u_q) * u^F ------
+// One thread per face of normal d; F holds 3 components of the face triple.
+__global__ void __launch_bounds__(256) k_conv_flux(GridD g, int d, const double *__restrict__ ap,
+                                                   const double *__restrict__ u,
+                                                   const double *__restrict__ S,
+                                                   const double *__restrict__ ufd, double *__restrict__ F,
+                                                   int nft, int off)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    if (i >= mx || j >= my || k >= mz) return;
+    const int f = fidx(g, d, i, j, k);
+    const int N3 = ncell(g);
+    const double a = ap[f];
+    if (a <= 0.0) {
+        for (int q = 0; q < 3; q++) F[q * nft + off + f] = 0.0;
         return;
     }
-    const double *A[3] = {ax, ay, az};
-    const double *U[3] = {uf, uf + nface(g, 0), uf + nface(g, 0) + nface(g, 1)};
-    for (int q = 0; q < 3; q++) {
-        const double *uq = u + q * N3;
-        double s = 0.0;
-        for (int d = 0; d < 3; d++) {
-            int3 e = unit(d);
-            for (int hs = 0; hs < 2; hs++) {
-                int fi = i + hs * e.x, fj = j + hs * e.y, fk = k + hs * e.z;
-                int f = fidx(g, d, fi, fj, fk);
-                double a = A[d][f];
-                if (a <= 0.0) continue;
-                int pos = d == 0 ? fi : (d == 1 ? fj : fk);
-                double w = U[d][f], state;
-                if (pos == 0 || pos == dimn(g, d)) {
-                    state = (g.bc[2 * d + hs] == EBV_INFLOW) ? g.u_in[q] : uq[c];
-                } else {
-                    int Li = fi - e.x, Lj = fj - e.y, Lk = fk - e.z;
-                    double sL = uq[cidx(g, Li, Lj, Lk)] + 0.5 * mc_slope(g, flag, uq, Li, Lj, Lk, d);
-                    double sR = uq[cidx(g, fi, fj, fk)] - 0.5 * mc_slope(g, flag, uq, fi, fj, fk, d);
-                    state = w > 0.0 ? sL : (w < 0.0 ? sR : 0.5 * (sL + sR));
-                }
-                s += (hs ? 1.0 : -1.0) * a * state * w;
-            }
+    const double w = ufd[f];
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    int3 e = unit(d);
+    if (pos == 0 || pos == dimn(g, d)) {
+        const int hs = pos != 0;
+        const int c = cidx(g, i - hs * e.x, j - hs * e.y, k - hs * e.z);
+        const bool in = g.bc[2 * d + hs] == EBV_INFLOW;
+        for (int q = 0; q < 3; q++) {
+            double state = in ? g.u_in[q] : u[q * N3 + c];
+            F[q * nft + off + f] = a * state * w;
         }
-        DC[q * N3 + c] = s / (alpha[c] * g.h);
+        return;
+    }
+    const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
+    for (int q = 0; q < 3; q++) {
+        double sL = u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL];
+        double sR = u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR];
+        double state = w > 0.0 ? sL : (w < 0.0 ? sR : 0.5 * (sL + sR));
+        F[q * nft + off + f] = a * state * w;
     }
 }
 
+// ---- conservative divergence D^C of a face flux triple (3 components) -----
+// With kEB the viscous EB wall flux -eta n_q (n . du/dn) A_EB is added.
+template <bool kEB>
+__global__ void __launch_bounds__(256) k_flux_div(GridD g, GeomD geo, const double *__restrict__ F, int nft,
+                                                  const double *__restrict__ eta,
+                                                  const double *__restrict__ dudn, double *__restrict__ DC)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (geo.flag[c] == 0) {
+        for (int q = 0; q < 3; q++) DC[q * N3 + c] = 0.0;
+        return;
+    }
+    const int off[3] = {0, nface(g, 0), nface(g, 0) + nface(g, 1)};
+    double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        int3 e = unit(d);
+        const int flo = off[d] + fidx(g, d, i, j, k), fhi = off[d] + fidx(g, d, i + e.x, j + e.y, k + e.z);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            s[q] += -F[q * nft + flo];
+            s[q] += F[q * nft + fhi];
+        }
+    }
+    if (kEB && geo.flag[c] == 2 && geo.area[c] > 0.0) {
+        int t = find_cut(geo.cut, geo.ncut, c);
+        if (t >= 0) {
+            double nd = 0.0;
+            for (int q = 0; q < 3; q++) nd += geo.nrm[q * N3 + c] * dudn[q * geo.ncut + t];
+            for (int q = 0; q < 3; q++) s[q] += -eta[c] * geo.nrm[q * N3 + c] * nd * geo.area[c];
+        }
+    }
+    const double inv = 1.0 / (geo.alpha[c] * g.h);
+    for (int q = 0; q < 3; q++) DC[q * N3 + c] = s[q] * inv;
+}
+
 // ---- hybrid flux divergence and redistribution (3 components) -------------
-// Pass 1: D^H and the excess dD, with the weight w = 1 / sum of neighbour alpha.
-__global__ void __launch_bounds__(256) k_redist_a(GridD g, const uint8_t *__restrict__ flag,
+// A fluid cell none of whose 26 neighbours is cut has alpha = 1 and only
+// full neighbours, so D = D^H = D^C exactly (its excess and its neighbours'
+// excess vanish).  Such cells take the direct path; the cells of the `near`
+// list (cut cells and their neighbours) take the two passes below.
+__global__ void k_redist_far(GridD g, const uint8_t *__restrict__ flag, const uint8_t *__restrict__ near,
+                             const double *__restrict__ DC, double sign, double div, double *__restrict__ out)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (near[c]) return;
+    for (int q = 0; q < 3; q++) {
+        double v = flag[c] ? sign * DC[q * N3 + c] : 0.0;
+        out[q * N3 + c] = div == 1.0 ? v : v / div;
+    }
+}
+
+// Pass 1 on the near cells: D^H and, for cut cells, the excess dD and the
+// weight w = 1 / (sum of neighbour alpha).
+__global__ void __launch_bounds__(256) k_redist_a(GridD g, const int *__restrict__ list, int nlist,
+                                                  const uint8_t *__restrict__ flag,
                                                   const double *__restrict__ alpha,
                                                   const double *__restrict__ DC,
                                                   double *__restrict__ D, double *__restrict__ dD,
                                                   double *__restrict__ w)
 {
-    CELL_INDEX
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nlist) return;
+    const int c = list[t];
+    const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
     const int N3 = ncell(g);
-    if (flag[c] == 0) {
-        for (int q = 0; q < 3; q++) { D[q * N3 + c] = 0.0; dD[q * N3 + c] = 0.0; }
-        w[c] = 0.0;
-        return;
-    }
     const double al = alpha[c];
     if (flag[c] == 1) {  // alpha = 1: D^H = D^C, no excess
         for (int q = 0; q < 3; q++) { D[q * N3 + c] = DC[q * N3 + c]; dD[q * N3 + c] = 0.0; }
-        double sa = 0.0;
-        for (int dk = -1; dk <= 1; dk++)
-            for (int dj = -1; dj <= 1; dj++)
-                for (int di = -1; di <= 1; di++) {
-                    if (!di && !dj && !dk) continue;
-                    if (!avail(g, flag, i + di, j + dj, k + dk)) continue;
-                    sa += alpha[cidx(g, i + di, j + dj, k + dk)];
-                }
-        w[c] = sa > 0.0 ? 1.0 / sa : 0.0;
         return;
     }
     double sa = 0.0, sad[3] = {0.0, 0.0, 0.0};
@@ -289,26 +359,28 @@ __global__ void __launch_bounds__(256) k_redist_a(GridD g, const uint8_t *__rest
     w[c] = sa > 0.0 ? 1.0 / sa : 0.0;
 }
 
-// Pass 2: add the neighbours' weighted excess; out = sign * D / div.
-__global__ void __launch_bounds__(256) k_redist_b(GridD g, const uint8_t *__restrict__ flag,
+// Pass 2 on the near cells: add the cut neighbours' weighted excess (full
+// neighbours have none); out = sign * D / div.
+__global__ void __launch_bounds__(256) k_redist_b(GridD g, const int *__restrict__ list, int nlist,
+                                                  const uint8_t *__restrict__ flag,
                                                   const double *__restrict__ D,
                                                   const double *__restrict__ dD,
                                                   const double *__restrict__ w, double sign,
                                                   double div, double *__restrict__ out)
 {
-    CELL_INDEX
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nlist) return;
+    const int c = list[t];
+    const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
     const int N3 = ncell(g);
-    if (flag[c] == 0) {
-        for (int q = 0; q < 3; q++) out[q * N3 + c] = 0.0;
-        return;
-    }
     double s[3] = {0.0, 0.0, 0.0};
     for (int dk = -1; dk <= 1; dk++)
         for (int dj = -1; dj <= 1; dj++)
             for (int di = -1; di <= 1; di++) {
                 if (!di && !dj && !dk) continue;
-                if (!avail(g, flag, i + di, j + dj, k + dk)) continue;
+                if (!inbox(g, i + di, j + dj, k + dk)) continue;
                 int c2 = cidx(g, i + di, j + dj, k + dk);
+                if (flag[c2] != 2) continue;
                 for (int q = 0; q < 3; q++) s[q] += w[c2] * dD[q * N3 + c2];
             }
     for (int q = 0; q < 3; q++) out[q * N3 + c] = sign * (D[q * N3 + c] + s[q]) / div;
@@ -388,76 +460,59 @@ __global__ void k_wall_dudn(GridD g, GeomD geo, const double *__restrict__ u,
     }
 }
 
-__device__ inline int find_cut(const int *cut, int ncut, int c)
+// ---- viscous face fluxes  F_j = a_f eta_f d u_d / d x_j (face normal d) ---
+// eta_f: mean of the two cells; d u_d/d x_d: two-point difference; the
+// transverse derivatives: mean of the two cells' robust gradients G.  Box
+// faces: Dirichlet (ghost at h/2) or Neumann for u_d.
+__global__ void __launch_bounds__(256) k_visc_flux(GridD g, int d, const double *__restrict__ ap,
+                                                   const double *__restrict__ u,
+                                                   const double *__restrict__ eta,
+                                                   const double *__restrict__ G, double *__restrict__ F,
+                                                   int nft, int off)
 {
-    int lo = 0, hi = ncut - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int v = cut[mid];
-        if (v == c) return mid;
-        if (v < c) lo = mid + 1; else hi = mid - 1;
-    }
-    return -1;
-}
-
-// ---- explicit viscous term: D^C of eta (grad u)^T -------------------------
-__global__ void __launch_bounds__(256) k_viscous_dc(GridD g, GeomD geo, const double *__restrict__ u,
-                                                    const double *__restrict__ eta,
-                                                    const double *__restrict__ G,
-                                                    const double *__restrict__ dudn,
-                                                    double *__restrict__ DC)
-{
-    CELL_INDEX
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    if (i >= mx || j >= my || k >= mz) return;
+    const int f = fidx(g, d, i, j, k);
     const int N3 = ncell(g);
-    if (geo.flag[c] == 0) {
-        for (int q = 0; q < 3; q++) DC[q * N3 + c] = 0.0;
+    const double a = ap[f];
+    if (a <= 0.0) {
+        for (int q = 0; q < 3; q++) F[q * nft + off + f] = 0.0;
         return;
     }
-    const double *A[3] = {geo.ax, geo.ay, geo.az};
-    const double h = g.h;
-    int cut_t = -1;
-    double nd = 0.0;
-    if (geo.flag[c] == 2 && geo.area[c] > 0.0) {
-        cut_t = find_cut(geo.cut, geo.ncut, c);
-        if (cut_t >= 0)
-            for (int q = 0; q < 3; q++) nd += geo.nrm[q * N3 + c] * dudn[q * geo.ncut + cut_t];
-    }
-    for (int jj = 0; jj < 3; jj++) {
-        double s = 0.0;
-        for (int d = 0; d < 3; d++) {
-            int3 e = unit(d);
-            for (int hs = 0; hs < 2; hs++) {
-                int fi = i + hs * e.x, fj = j + hs * e.y, fk = k + hs * e.z;
-                int f = fidx(g, d, fi, fj, fk);
-                double a = A[d][f];
-                if (a <= 0.0) continue;
-                int pos = d == 0 ? fi : (d == 1 ? fj : fk);
-                double T;
-                if (pos == 0 || pos == dimn(g, d)) {
-                    double val;
-                    if (side_dirichlet(g, 2 * d + hs, d, &val)) {
-                        double ud = u[d * N3 + c];
-                        T = (jj == d) ? eta[c] * (hs ? (val - ud) : (ud - val)) / (0.5 * h) : 0.0;
-                    } else {
-                        T = (jj == d) ? 0.0 : eta[c] * G[(3 * jj + d) * N3 + c];
-                    }
-                } else {
-                    int cL = cidx(g, fi - e.x, fj - e.y, fk - e.z), cR = cidx(g, fi, fj, fk);
-                    double ef = 0.5 * (eta[cL] + eta[cR]);
-                    double der = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) / h
-                                           : 0.5 * (G[(3 * jj + d) * N3 + cL] + G[(3 * jj + d) * N3 + cR]);
-                    T = ef * der;
-                }
-                s += (hs ? 1.0 : -1.0) * a * T;
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    int3 e = unit(d);
+    const double ih = 1.0 / g.h;
+    if (pos == 0 || pos == dimn(g, d)) {
+        const int hs = pos != 0;
+        const int c = cidx(g, i - hs * e.x, j - hs * e.y, k - hs * e.z);
+        double val;
+        const bool dir = side_dirichlet(g, 2 * d + hs, d, &val);
+        for (int jj = 0; jj < 3; jj++) {
+            double T;
+            if (dir) {
+                double ud = u[d * N3 + c];
+                T = (jj == d) ? eta[c] * (hs ? (val - ud) : (ud - val)) * (2.0 * ih) : 0.0;
+            } else {
+                T = (jj == d) ? 0.0 : eta[c] * G[(3 * jj + d) * N3 + c];
             }
+            F[jj * nft + off + f] = a * T;
         }
-        if (cut_t >= 0) s += -eta[c] * geo.nrm[jj * N3 + c] * nd * geo.area[c];
-        DC[jj * N3 + c] = s / (geo.alpha[c] * h);
+        return;
+    }
+    const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
+    const double ef = 0.5 * (eta[cL] + eta[cR]);
+    for (int jj = 0; jj < 3; jj++) {
+        double der = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) * ih
+                               : 0.5 * (G[(3 * jj + d) * N3 + cL] + G[(3 * jj + d) * N3 + cR]);
+        F[jj * nft + off + f] = a * (ef * der);
     }
 }
 
 // Cell-centre gradient of the trilinear interpolant of nodal p, component d.
-__device__ inline double grad_p(const GridD &g, const double *p, int i, int j, int k, int d)
+__device__ inline double grad_p(const GridD &g, const double *p, int i, int j, int k, int d, double q4h)
 {
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     double s = 0.0;
@@ -470,7 +525,7 @@ __device__ inline double grad_p(const GridD &g, const double *p, int i, int j, i
             hi[d] += 1;
             s += p[nidx(g, hi[0], hi[1], hi[2])] - p[nidx(g, lo[0], lo[1], lo[2])];
         }
-    return s / (4.0 * g.h);
+    return s * q4h;  // q4h = 1 / (4 h)
 }
 
 // psi = rho u + dt (rho C + V - grad p + f)
@@ -486,7 +541,7 @@ __global__ void k_psi(GridD g, const uint8_t *__restrict__ flag, const double *_
         int s = q * N3 + c;
         if (flag[c] == 0) { psi[s] = 0.0; continue; }
         double fq = f ? f[s] : 0.0;
-        psi[s] = rho * u[s] + dt * (rho * C[s] + V[s] - grad_p(g, p, i, j, k, q) + fq);
+        psi[s] = rho * u[s] + dt * (rho * C[s] + V[s] - grad_p(g, p, i, j, k, q, 0.25 / g.h) + fq);
     }
 }
 
@@ -501,7 +556,7 @@ __global__ void k_add_gradp(GridD g, const uint8_t *__restrict__ flag, double *_
     for (int q = 0; q < 3; q++) {
         int s = q * N3 + c;
         if (flag[c] == 0) { u[s] = 0.0; continue; }
-        double gq = grad_p(g, p, i, j, k, q);
+        double gq = grad_p(g, p, i, j, k, q, 0.25 / g.h);
         u[s] = sgn > 0 ? u[s] + coef * gq : u[s] - coef * gq;
     }
 }
@@ -701,14 +756,17 @@ ebv_status launch_strain_eta(Ctx *c, const double *u, double *eta, double *srate
     return EBV_OK;
 }
 
+// Slopes of u into c->G (read again by launch_convective, before the viscous
+// part overwrites c->G with the velocity gradient), then the face states.
 ebv_status launch_face_states(Ctx *c, const double *u, double *uf)
 {
     const GridD &g = c->g;
+    EBV_LAUNCH(c, k_slopes, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, c->G);
     const double *A[3] = {c->ax, c->ay, c->az};
     size_t off = 0;
     for (int d = 0; d < 3; d++) {
         EBV_LAUNCH(c, k_face_states, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)),
-                   block3(), 0, g, d, c->flag, A[d], u, uf + off);
+                   block3(), 0, g, d, c->G, A[d], u, uf + off);
         off += nface(g, d);
     }
     return EBV_OK;
@@ -738,18 +796,32 @@ ebv_status launch_mac_correct(Ctx *c, double *uf, const double *phi)
 ebv_status launch_redistribute_into(Ctx *c, const double *DC, double sign, double div, double *out)
 {
     const GridD &g = c->g;
-    EBV_LAUNCH(c, k_redist_a, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->alpha, DC,
-               c->Dh, c->dD, c->wts);
-    EBV_LAUNCH(c, k_redist_b, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->Dh, c->dD,
-               c->wts, sign, div, out);
+    EBV_LAUNCH(c, k_redist_far, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, DC, sign, div, out);
+    if (c->nnear) {
+        dim3 gr((c->nnear + 127) / 128);
+        EBV_LAUNCH(c, k_redist_a, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->alpha, DC, c->Dh, c->dD,
+                   c->wts);
+        EBV_LAUNCH(c, k_redist_b, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->Dh, c->dD, c->wts, sign,
+                   div, out);
+    }
     return EBV_OK;
 }
 
 ebv_status launch_convective(Ctx *c, const double *u, const double *uf, double *C)
 {
     const GridD &g = c->g;
-    EBV_LAUNCH(c, k_convective_dc, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->alpha,
-               c->ax, c->ay, c->az, u, uf, c->DC);
+    const int nft = nface(g, 0) + nface(g, 1) + nface(g, 2);
+    // the slopes of u are in c->G (launch_face_states)
+    const double *ufd[3] = {uf, uf + nface(g, 0), uf + nface(g, 0) + nface(g, 1)};
+    const double *A[3] = {c->ax, c->ay, c->az};
+    int off = 0;
+    for (int d = 0; d < 3; d++) {
+        EBV_LAUNCH(c, k_conv_flux, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
+                   A[d], u, c->G, ufd[d], c->ff, nft, off);
+        off += nface(g, d);
+    }
+    EBV_LAUNCH(c, k_flux_div<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, geomd(c), c->ff, nft, nullptr,
+               nullptr, c->DC);
     return launch_redistribute_into(c, c->DC, -1.0, 1.0, C);
 }
 
@@ -760,7 +832,15 @@ ebv_status launch_viscous_explicit(Ctx *c, const double *u, const double *eta, c
     GeomD geo = geomd(c);
     if (c->ncut)
         EBV_LAUNCH(c, k_wall_dudn, dim3((c->ncut + 127) / 128), dim3(128), 0, g, geo, u, c->dudn);
-    EBV_LAUNCH(c, k_viscous_dc, grid3(g.nx, g.ny, g.nz), block3(), 0, g, geo, u, eta, G, c->dudn,
+    const int nft = nface(g, 0) + nface(g, 1) + nface(g, 2);
+    const double *A[3] = {c->ax, c->ay, c->az};
+    int off = 0;
+    for (int d = 0; d < 3; d++) {
+        EBV_LAUNCH(c, k_visc_flux, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
+                   A[d], u, eta, G, c->ff, nft, off);
+        off += nface(g, d);
+    }
+    EBV_LAUNCH(c, k_flux_div<true>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, geo, c->ff, nft, eta, c->dudn,
                c->DC);
     return launch_redistribute_into(c, c->DC, 1.0, c->prm.rho, V);
 }

@@ -257,8 +257,40 @@ ebv_status build_geometry_host(Ctx *c, ebv_implicit_fn fn, void *user)
                 }
             }
 
-    // 5. upload
+    // 5. cells next to the EB: fluid cells that are cut or have a cut cell
+    //    among their 26 neighbours (the only cells redistribution changes)
+    std::vector<uint8_t> nearm(N3, 0);
+    std::vector<int> nearl;
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c0 = cidx(g, i, j, k);
+                if (H.flag[c0] == 0) continue;
+                bool nb = false;
+                for (int dk = -1; dk <= 1 && !nb; dk++)
+                    for (int dj = -1; dj <= 1 && !nb; dj++)
+                        for (int di = -1; di <= 1; di++) {
+                            int ii = i + di, jj = j + dj, kk = k + dk;
+                            if (ii < 0 || jj < 0 || kk < 0 || ii >= NX || jj >= NY || kk >= NZ) continue;
+                            if (H.flag[cidx(g, ii, jj, kk)] == 2) { nb = true; break; }
+                        }
+                if (nb) {
+                    nearm[c0] = 1;
+                    nearl.push_back((int)c0);
+                }
+            }
+
+    // 6. upload
     cudaStream_t s = c->stream;
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->nearm, nearm.data(), N3, cudaMemcpyHostToDevice, s));
+    if (c->nearl) cudaFree(c->nearl);
+    c->nearl = nullptr;
+    c->nnear = (int)nearl.size();
+    if (c->nnear) {
+        EBV_CUDA_TRY(c, cudaMalloc(&c->nearl, c->nnear * sizeof(int)));
+        EBV_CUDA_TRY(c, cudaMemcpyAsync(c->nearl, nearl.data(), c->nnear * sizeof(int),
+                                        cudaMemcpyHostToDevice, s));
+    }
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->alpha, H.alpha.data(), N3 * 8, cudaMemcpyHostToDevice, s));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ax, H.a[0].data(), H.a[0].size() * 8, cudaMemcpyHostToDevice, s));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ay, H.a[1].data(), H.a[1].size() * 8, cudaMemcpyHostToDevice, s));

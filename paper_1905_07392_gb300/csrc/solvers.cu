@@ -88,13 +88,15 @@ namespace {
 
 // ===========================================================================
 // Cell-centred operator  (A x)_i = extra_i x_i + sum_faces beta_f (x_i - x_nb)
-// (face coefficients include the box faces; x_nb = 0 outside the box)
+// (face coefficients include the box faces; x_nb = 0 outside the box).
+// Each level stores extra (for coarsening) and the full diagonal
+// diag = extra + sum of the 6 face coefficients (for the smoother and apply).
 // ===========================================================================
 
 template <class T>
 struct CcOp {
     GridD g;
-    const T *extra, *bx, *by, *bz;
+    const T *diag, *bx, *by, *bz;
 };
 
 template <class T>
@@ -106,7 +108,7 @@ __device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__
     const T bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
     const T byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
     const T bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
-    diag = A.extra[c] + bxl + bxh + byl + byh + bzl + bzh;
+    diag = A.diag[c];
     T s = 0;
     if (i > 0) s += bxl * x[c - 1];
     if (i < g.nx - 1) s += bxh * x[c + 1];
@@ -136,10 +138,7 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
     }
     T diag, off;
     if (zero_start) {
-        const T bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
-        const T byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
-        const T bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
-        diag = A.extra[c] + bxl + bxh + byl + byh + bzl + bzh;
+        diag = A.diag[c];
         off = T(0);
     } else {
         cc_row(A, i, j, k, x, diag, off);
@@ -228,6 +227,20 @@ __global__ void k_cc_coarsen(GridD gf, const T *__restrict__ ef, const T *__rest
     }
 }
 
+// diag = extra + the six face coefficients of the cell.
+template <class T>
+__global__ void k_cc_make_diag(GridD g, const T *__restrict__ extra, const T *__restrict__ bx,
+                               const T *__restrict__ by, const T *__restrict__ bz, T *__restrict__ diag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    const int c = cidx(g, i, j, k);
+    diag[c] = extra[c] + bx[fidx(g, 0, i, j, k)] + bx[fidx(g, 0, i + 1, j, k)] + by[fidx(g, 1, i, j, k)] +
+              by[fidx(g, 1, i, j + 1, k)] + bz[fidx(g, 2, i, j, k)] + bz[fidx(g, 2, i, j, k + 1)];
+}
+
 __global__ void k_cov_coarsen(GridD gf, const uint8_t *covf, GridD gc, uint8_t *covc)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -303,6 +316,7 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const double h2 = g.h * g.h, dt = *dtp;
+    const double dth2 = dt / h2;  // one division per thread; the faces multiply
     const int N3 = geo.ncell;
     const double *A[3] = {geo.ax, geo.ay, geo.az};
     double *B[3] = {bx, by, bz};
@@ -319,13 +333,12 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
             cc[d] -= hs;
             double val;
             int c = cidx(g, cc[0], cc[1], cc[2]);
-            B[d][f] = (a > 0.0 && side_dirichlet(g, 2 * d + hs, comp, &val)) ? 2.0 * dt * a * eta[c] / h2
-                                                                              : 0.0;
+            B[d][f] = (a > 0.0 && side_dirichlet(g, 2 * d + hs, comp, &val)) ? 2.0 * dth2 * a * eta[c] : 0.0;
         } else {
             int lo[3] = {i, j, k};
             lo[d] -= 1;
             double ef = 0.5 * (eta[cidx(g, lo[0], lo[1], lo[2])] + eta[cidx(g, i, j, k)]);
-            B[d][f] = a > 0.0 ? dt * a * ef / h2 : 0.0;
+            B[d][f] = a > 0.0 ? dth2 * a * ef : 0.0;
         }
     }
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
@@ -355,26 +368,28 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
             double a = A[d][fidx(g, d, fi[0], fi[1], fi[2])];
             double val;
             if (a > 0.0 && side_dirichlet(g, 2 * d + hs, comp, &val))
-                rb += (2.0 * dt * a * eta[c] / h2) * val;
+                rb += (2.0 * dth2 * a * eta[c]) * val;
         }
     b[c] = geo.alpha[c] * psi[c] + rb;
 }
 
 // q = A p (FP64, level 0) and block partials of p.q
-__global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<double> A, const double *__restrict__ p,
-                                                      double *__restrict__ q, double *__restrict__ part)
+// (partials of the dot product in FP64 for either precision)
+template <class T>
+__global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__restrict__ p, T *__restrict__ q,
+                                                      double *__restrict__ part)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     double v = 0.0;
     if (i < A.g.nx && j < A.g.ny && k < A.g.nz) {
-        double diag, off;
+        T diag, off;
         cc_row(A, i, j, k, p, diag, off);
         int c = cidx(A.g, i, j, k);
-        double y = diag * p[c] - off;
+        T y = diag * p[c] - off;
         q[c] = y;
-        v = p[c] * y;
+        v = (double)(p[c] * y);
     }
     v = block_sum3(v);
     if (thread_linear() == 0) part[block_linear()] = v;
@@ -394,6 +409,7 @@ struct NdOp {
     GridD g;               // cell dims
     const T *alpha;        // cells
     const uint8_t *act;    // nodes
+    const uint8_t *reg;    // nodes whose 8 cells are full (level 0), else nullptr
 };
 
 // Row of the nodal operator at node (i,j,k), assembled in stencil form.  With
@@ -408,6 +424,21 @@ __device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__
 {
     const GridD &g = A.g;
     const int NXn = g.nx + 1, NYn = g.ny + 1;
+    if (A.reg && A.reg[nidx(g, i, j, k)]) {
+        // all 8 cells full (so the node is interior): the constant stencil
+        // 8/3 at the centre, -1/6 on the 12 face diagonals, -1/12 on the 8
+        // body diagonals (times h)
+        const T *xc = x + nidx(g, i, j, k);
+        const int sy = NXn, sz = NXn * NYn;
+        T fd = xc[1 + sy] + xc[-1 + sy] + xc[1 - sy] + xc[-1 - sy] + xc[1 + sz] + xc[-1 + sz] + xc[1 - sz] +
+               xc[-1 - sz] + xc[sy + sz] + xc[-sy + sz] + xc[sy - sz] + xc[-sy - sz];
+        T bd = xc[1 + sy + sz] + xc[-1 + sy + sz] + xc[1 - sy + sz] + xc[-1 - sy + sz] + xc[1 + sy - sz] +
+               xc[-1 + sy - sz] + xc[1 - sy - sz] + xc[-1 - sy - sz];
+        const T hh = T(g.h);
+        diag = hh * T(8.0 / 3.0);
+        ax = diag * xc[0] - hh * T(1.0 / 12.0) * (T(2) * fd + bd);
+        return;
+    }
     T a[2][2][2];
     T sa = 0;
 #pragma unroll
@@ -563,8 +594,9 @@ __global__ void k_nd_prolong(GridD gf, const uint8_t *__restrict__ actf, GridD g
     xout[n] = xin[n] + wi * wj * wk * s;
 }
 
-__global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<double> A, const double *__restrict__ p,
-                                                      double *__restrict__ q, double *__restrict__ part)
+template <class T>
+__global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<T> A, const T *__restrict__ p, T *__restrict__ q,
+                                                      double *__restrict__ part)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -573,16 +605,16 @@ __global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<double> A, const doub
     double v = 0.0;
     if (i <= g.nx && j <= g.ny && k <= g.nz) {
         const int n = nidx(g, i, j, k);
-        double y;
+        T y;
         if (!A.act[n]) {
             y = p[n];
         } else {
-            double diag, ax;
+            T diag, ax;
             nd_row(A, i, j, k, p, diag, ax);
             y = ax;
         }
         q[n] = y;
-        v = p[n] * y;
+        v = (double)(p[n] * y);
     }
     v = block_sum3(v);
     if (thread_linear() == 0) part[block_linear()] = v;
@@ -598,6 +630,20 @@ __global__ void k_nd_alpha_coarsen(GridD gf, const double *__restrict__ af, Grid
     for (int o = 0; o < 8; o++)
         s += af[cidx(gf, 2 * I + (o & 1), 2 * J + ((o >> 1) & 1), 2 * K + ((o >> 2) & 1))];
     ac[cidx(gc, I, J, K)] = 0.125 * s;
+}
+
+__global__ void k_nd_regular(GridD g, const double *__restrict__ alpha, uint8_t *__restrict__ reg)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i > g.nx || j > g.ny || k > g.nz) return;
+    bool all = true;
+    for (int oc = 0; oc < 8; oc++) {
+        int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
+        if (!inbox(g, ci, cj, ck) || alpha[cidx(g, ci, cj, ck)] != 1.0) all = false;
+    }
+    reg[nidx(g, i, j, k)] = all ? 1 : 0;
 }
 
 __global__ void k_nd_active(GridD g, const double *__restrict__ alpha, uint8_t *__restrict__ act)
@@ -636,7 +682,7 @@ __global__ void k_cc_bottom_assemble(CcOp<T> A, double *__restrict__ M, int nb)
         double bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
         double byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
         double bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
-        double diag = (double)A.extra[r] + bxl + bxh + byl + byh + bzl + bzh;
+        double diag = (double)A.diag[r];
         row[r] = diag > 0.0 ? diag : 1.0;
         if (i > 0) row[r - 1] = -bxl;
         if (i < g.nx - 1) row[r + 1] = -bxh;
@@ -755,6 +801,68 @@ __global__ void k_cg_pupdate(double *__restrict__ p, const double *__restrict__ 
         p[s] = first ? z[s] : z[s] + beta * p[s];
 }
 
+// --- refinement: FP64 residual into an FP32 vector, FP32 inner CG, FP64 update.
+// Per-thread sums of the FP32 kernels stay FP32 (a few dozen terms), block and
+// final sums are FP64.
+
+__global__ void __launch_bounds__(256) k_resid_to32(const double *__restrict__ b, const double *__restrict__ q,
+                                                    float *__restrict__ r, int n, double *__restrict__ part)
+{
+    double v = 0.0, w = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double rs = b[s] - q[s];
+        r[s] = (float)rs;
+        v += rs * rs;
+        w += b[s] * b[s];
+    }
+    v = block_sum<256>(v);
+    w = block_sum<256>(w);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = v;
+        part[gridDim.x + blockIdx.x] = w;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_dot32(const float *__restrict__ a, const float *__restrict__ b, int n,
+                                               double *__restrict__ part)
+{
+    float v = 0.0f;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) v += a[s] * b[s];
+    double dv = block_sum<256>((double)v);
+    if (threadIdx.x == 0) part[blockIdx.x] = dv;
+}
+
+// e += a p, r -= a q (e starts from 0 when first), partials of r.r
+__global__ void __launch_bounds__(256) k_cg_update32(float *__restrict__ e, float *__restrict__ r,
+                                                     const float *__restrict__ p, const float *__restrict__ q,
+                                                     const double *__restrict__ scal, int n, int first,
+                                                     double *__restrict__ part)
+{
+    const float a = (float)(scal[S_RZ] / scal[S_PQ]);
+    float v = 0.0f;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        e[s] = first ? a * p[s] : e[s] + a * p[s];
+        float rs = r[s] - a * q[s];
+        r[s] = rs;
+        v += rs * rs;
+    }
+    double dv = block_sum<256>((double)v);
+    if (threadIdx.x == 0) part[blockIdx.x] = dv;
+}
+
+__global__ void k_cg_pupdate32(float *__restrict__ p, const float *__restrict__ z, const double *__restrict__ scal,
+                               int n, int first)
+{
+    const float beta = first ? 0.0f : (float)(scal[S_RZ] / scal[S_RZOLD]);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        p[s] = first ? z[s] : z[s] + beta * p[s];
+}
+
+__global__ void k_add32to64(double *__restrict__ x, const float *__restrict__ e, int n)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) x[s] += (double)e[s];
+}
+
 __global__ void k_scal_copy(double *scal, int dst, int src)
 {
     if (threadIdx.x == 0) scal[dst] = scal[src];
@@ -781,11 +889,23 @@ CcOp<T> ccop(const CcLevel &L)
     CcOp<T> A;
     A.g = L.g;
     if constexpr (sizeof(T) == 8) {
-        A.extra = (const T *)L.extra_d; A.bx = (const T *)L.bf_d[0]; A.by = (const T *)L.bf_d[1]; A.bz = (const T *)L.bf_d[2];
+        A.diag = (const T *)L.diag_d; A.bx = (const T *)L.bf_d[0]; A.by = (const T *)L.bf_d[1]; A.bz = (const T *)L.bf_d[2];
     } else {
-        A.extra = (const T *)L.extra_f; A.bx = (const T *)L.bf_f[0]; A.by = (const T *)L.bf_f[1]; A.bz = (const T *)L.bf_f[2];
+        A.diag = (const T *)L.diag_f; A.bx = (const T *)L.bf_f[0]; A.by = (const T *)L.bf_f[1]; A.bz = (const T *)L.bf_f[2];
     }
     return A;
+}
+
+// diag of level L from its extra and faces, in precision T.
+template <class T>
+void cc_make_diag(Ctx *c, CcLevel &L)
+{
+    if constexpr (sizeof(T) == 8)
+        EBV_LAUNCH(c, k_cc_make_diag<double>, cgrid(L.g), block3(), 0, L.g, L.extra_d, L.bf_d[0], L.bf_d[1],
+                   L.bf_d[2], L.diag_d);
+    else
+        EBV_LAUNCH(c, k_cc_make_diag<float>, cgrid(L.g), block3(), 0, L.g, L.extra_f, L.bf_f[0], L.bf_f[1],
+                   L.bf_f[2], L.diag_f);
 }
 
 template <class T>
@@ -796,6 +916,7 @@ NdOp<T> ndop(const NdLevel &L)
     if constexpr (sizeof(T) == 8) A.alpha = (const T *)L.alpha_d;
     else A.alpha = (const T *)L.alpha_f;
     A.act = L.act;
+    A.reg = L.reg;
     return A;
 }
 
@@ -929,9 +1050,13 @@ void nd_vcycle(Ctx *c, NdHier &H, const T *b0, T *x0)
 struct Problem {
     virtual ~Problem() {}
     virtual int n() const = 0;
-    virtual void apply_dot(Ctx *c, const double *p, double *q) = 0;  // partials of p.q into c->part
     virtual int apply_blocks() const = 0;
+    // q = A p with block partials of p.q in c->part, in FP64 or FP32
+    virtual void apply_dot(Ctx *c, const double *p, double *q) = 0;
+    virtual void apply_dot32(Ctx *c, const float *p, float *q) = 0;
+    // z = one V-cycle applied to r, in FP64 or FP32
     virtual void precond(Ctx *c, const double *r, double *z) = 0;
+    virtual void precond32(Ctx *c, const float *r, float *z) = 0;
 };
 
 inline int vblocks(int n) { return std::min(kReduceBlocks, (n + 255) / 256); }
@@ -996,62 +1121,123 @@ ebv_status pcg(Ctx *c, Problem &P, const double *b, double *x, int *iters, doubl
     return EBV_OK;
 }
 
+// Iterative refinement for the FP32 path: the residual r = b - A x and the
+// solution update x += e are FP64; each correction e solves A e = r with
+// conjugate gradients run entirely in FP32 (vectors, operator with FP32
+// coefficients, V-cycle) until its residual drops by `inner_drop` (or it
+// stalls), so FP64 arithmetic is spent once per refinement step instead of in
+// every Krylov iteration.
+ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
+{
+    const int n = P.n();
+    const double tol = c->prm.tol;
+    const int maxit = c->prm.max_iters;
+    const double inner_drop = 1e-4;
+    float *r = c->kr32, *z = c->kz32, *p = c->kp32, *q = c->kq32, *e = c->ke32;
+    int it = 0;
+    double rel = 0.0;
+    ebv_status st;
+    for (int outer = 0; outer < 60; outer++) {
+        P.apply_dot(c, x, c->kq);
+        EBV_LAUNCH(c, k_resid_to32, dim3(vblocks(n)), dim3(256), 0, b, c->kq, r, n, c->part);
+        reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
+        reduce_sum(c, c->part + vblocks(n), vblocks(n), c->scal + S_BB);
+        if ((st = read_scalars(c, 0, 2)) != EBV_OK) return st;
+        const double bb = c->scal_host[S_BB], rr0 = c->scal_host[S_RR];
+        if (!std::isfinite(rr0) || !std::isfinite(bb)) return c->fail(EBV_ERR_NAN, "non-finite residual");
+        if (bb == 0.0) {
+            EBV_LAUNCH(c, k_fill, dim3(vblocks(n)), dim3(256), 0, x, n, 0.0);
+            rel = 0.0;
+            break;
+        }
+        rel = sqrt(rr0 / bb);
+        if (rel <= tol || it >= maxit) break;
+        // inner FP32 CG from e = 0 until |r| <= target (relative to this step's r)
+        const double target2 = rr0 * std::max(inner_drop, 0.5 * tol / rel) * std::max(inner_drop, 0.5 * tol / rel);
+        double prev = rr0;
+        int stall = 0;
+        for (int k = 0; it < maxit; k++) {
+            P.precond32(c, r, z);
+            EBV_LAUNCH(c, k_dot32, dim3(vblocks(n)), dim3(256), 0, r, z, n, c->part);
+            reduce_sum(c, c->part, vblocks(n), c->scal + S_RZ);
+            EBV_LAUNCH(c, k_cg_pupdate32, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, (int)(k == 0));
+            P.apply_dot32(c, p, q);
+            reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_PQ);
+            EBV_LAUNCH(c, k_cg_update32, dim3(vblocks(n)), dim3(256), 0, e, r, p, q, c->scal, n, (int)(k == 0),
+                       c->part);
+            reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
+            EBV_LAUNCH(c, k_scal_copy, dim3(1), dim3(32), 0, c->scal, S_RZOLD, S_RZ);
+            it++;
+            if ((st = read_scalars(c, S_RR, 1)) != EBV_OK) return st;
+            const double rr = c->scal_host[S_RR];
+            if (!std::isfinite(rr)) return c->fail(EBV_ERR_NAN, "non-finite residual");
+            if (rr <= target2) break;
+            // FP32 round-off floor: stop the inner solve when it no longer gains
+            if (rr > 0.25 * prev) { if (++stall >= 3) break; } else stall = 0;
+            prev = rr;
+        }
+        EBV_LAUNCH(c, k_add32to64, dim3(vblocks(n)), dim3(256), 0, x, e, n);
+    }
+    if (iters) *iters = it;
+    if (res) *res = rel;
+    if (rel > tol) return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance");
+    return EBV_OK;
+}
+
 struct CcProblem : Problem {
     CcHier *H;
-    bool fp32;
     int n() const override { return ncell(H->lv[0].g); }
     int apply_blocks() const override { return nblocks3(cgrid(H->lv[0].g)); }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
-        // p, extra, 3 faces, q: 6 words per cell
-        EBV_LAUNCH_P(c, "cc_apply_fp64", 48.0 * n(), k_cc_apply_dot, cgrid(H->lv[0].g), block3(), 0,
+        // p, diagonal, 3 faces, q: 6 words per cell
+        EBV_LAUNCH_P(c, "cc_apply_fp64", 48.0 * n(), k_cc_apply_dot<double>, cgrid(H->lv[0].g), block3(), 0,
                      ccop<double>(H->lv[0]), p, q, c->part);
     }
-    void precond(Ctx *c, const double *r, double *z) override
+    void apply_dot32(Ctx *c, const float *p, float *q) override
     {
-        if (!fp32) {
-            cc_vcycle<double>(c, *H, r, z);
-        } else {
-            const int nn = n();
-            EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nn)), dim3(256), 0, r, (float *)c->lb[0], nn);
-            cc_vcycle<float>(c, *H, (const float *)c->lb[0], (float *)c->lx[0]);
-            EBV_LAUNCH(c, (k_convert<float, double>), dim3(vblocks(nn)), dim3(256), 0, (const float *)c->lx[0], z, nn);
-        }
+        EBV_LAUNCH_P(c, "cc_apply_fp32", 24.0 * n(), k_cc_apply_dot<float>, cgrid(H->lv[0].g), block3(), 0,
+                     ccop<float>(H->lv[0]), p, q, c->part);
     }
+    void precond(Ctx *c, const double *r, double *z) override { cc_vcycle<double>(c, *H, r, z); }
+    void precond32(Ctx *c, const float *r, float *z) override { cc_vcycle<float>(c, *H, r, z); }
 };
 
 struct NdProblem : Problem {
     NdHier *H;
-    bool fp32;
     int n() const override { return nnode(H->lv[0].g); }
     int apply_blocks() const override { return nblocks3(ngrid(H->lv[0].g)); }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
         // p, alpha, q: 3 words per node
-        EBV_LAUNCH_P(c, "nodal_apply_fp64", 24.0 * n(), k_nd_apply_dot, ngrid(H->lv[0].g), block3(), 0,
+        EBV_LAUNCH_P(c, "nodal_apply_fp64", 24.0 * n(), k_nd_apply_dot<double>, ngrid(H->lv[0].g), block3(), 0,
                      ndop<double>(H->lv[0]), p, q, c->part);
     }
-    void precond(Ctx *c, const double *r, double *z) override
+    void apply_dot32(Ctx *c, const float *p, float *q) override
     {
-        if (!fp32) {
-            nd_vcycle<double>(c, *H, r, z);
-        } else {
-            const int nn = n();
-            EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nn)), dim3(256), 0, r, (float *)c->lb[0], nn);
-            nd_vcycle<float>(c, *H, (const float *)c->lb[0], (float *)c->lx[0]);
-            EBV_LAUNCH(c, (k_convert<float, double>), dim3(vblocks(nn)), dim3(256), 0, (const float *)c->lx[0], z, nn);
-        }
+        EBV_LAUNCH_P(c, "nodal_apply_fp32", 12.0 * n(), k_nd_apply_dot<float>, ngrid(H->lv[0].g), block3(), 0,
+                     ndop<float>(H->lv[0]), p, q, c->part);
     }
+    void precond(Ctx *c, const double *r, double *z) override { nd_vcycle<double>(c, *H, r, z); }
+    void precond32(Ctx *c, const float *r, float *z) override { nd_vcycle<float>(c, *H, r, z); }
 };
+
+ebv_status solve(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
+{
+    if (c->prm.precision == EBV_FP32_REFINE) return pcg_refine(c, P, b, x, iters, res);
+    return pcg(c, P, b, x, iters, res);
+}
 
 // Coarse levels and FP32 shadows of a cell-centred hierarchy whose level-0
 // FP64 coefficients are set; then the bottom inverse.
 ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
 {
     CcLevel &L0 = H.lv[0];
+    cc_make_diag<double>(c, L0);
     if (fp32) {
         const int n = ncell(L0.g);
         EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(n)), dim3(256), 0, L0.extra_d, L0.extra_f, n);
+        EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(n)), dim3(256), 0, L0.diag_d, L0.diag_f, n);
         for (int d = 0; d < 3; d++) {
             int nf = nface(L0.g, d);
             EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nf)), dim3(256), 0, L0.bf_d[d], L0.bf_f[d], nf);
@@ -1060,12 +1246,15 @@ ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
     for (int l = 0; l + 1 < H.L; l++) {
         CcLevel &F = H.lv[l], &Cc = H.lv[l + 1];
         dim3 gr = grid3(Cc.g.nx + 1, Cc.g.ny + 1, Cc.g.nz + 1);
-        if (fp32)
+        if (fp32) {
             EBV_LAUNCH(c, k_cc_coarsen<float>, gr, block3(), 0, F.g, F.extra_f, F.bf_f[0], F.bf_f[1], F.bf_f[2], F.cov,
                        Cc.g, Cc.cov, Cc.extra_f, Cc.bf_f[0], Cc.bf_f[1], Cc.bf_f[2]);
-        else
+            cc_make_diag<float>(c, Cc);
+        } else {
             EBV_LAUNCH(c, k_cc_coarsen<double>, gr, block3(), 0, F.g, F.extra_d, F.bf_d[0], F.bf_d[1], F.bf_d[2],
                        F.cov, Cc.g, Cc.cov, Cc.extra_d, Cc.bf_d[0], Cc.bf_d[1], Cc.bf_d[2]);
+            cc_make_diag<double>(c, Cc);
+        }
     }
     CcLevel &B = H.lv[H.L - 1];
     if (fp32)
@@ -1129,6 +1318,8 @@ ebv_status setup_solvers(Ctx *c)
             size_t nc = ncell(gl[l]);
             Lv.extra_d = dalloc<double>(nc, e);
             Lv.extra_f = dalloc<float>(nc, e);
+            Lv.diag_d = dalloc<double>(nc, e);
+            Lv.diag_f = dalloc<float>(nc, e);
             for (int d = 0; d < 3; d++) {
                 Lv.bf_d[d] = dalloc<double>(nface(gl[l], d), e);
                 Lv.bf_f[d] = dalloc<float>(nface(gl[l], d), e);
@@ -1153,6 +1344,7 @@ ebv_status setup_solvers(Ctx *c)
         Lv.alpha_d = l ? dalloc<double>(nc, e) : c->alpha;
         Lv.alpha_f = dalloc<float>(nc, e);
         Lv.act = dalloc<uint8_t>(nnode(gn[l]), e);
+        Lv.reg = l ? nullptr : dalloc<uint8_t>(nnode(gn[l]), e);
         Lv.lam_max = 2.0;
     }
     c->nd.binv = dalloc<double>((size_t)nbn * nbn, e);
@@ -1204,6 +1396,7 @@ ebv_status setup_geometry_solvers(Ctx *c)
         int nc = ncell(Lv.g);
         EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nc)), dim3(256), 0, Lv.alpha_d, Lv.alpha_f, nc);
         EBV_LAUNCH(c, k_nd_active, ngrid(Lv.g), block3(), 0, Lv.g, Lv.alpha_d, Lv.act);
+        if (Lv.reg) EBV_LAUNCH(c, k_nd_regular, ngrid(Lv.g), block3(), 0, Lv.g, Lv.alpha_d, Lv.reg);
     }
     const NdLevel &B = N.lv[N.L - 1];
     EBV_LAUNCH(c, k_nd_bottom_assemble, dim3((N.nb + 127) / 128), dim3(128), 0, B.g, B.alpha_d, B.act, N.bmat, N.nb);
@@ -1216,9 +1409,8 @@ ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res
 {
     CcProblem P;
     P.H = &c->mac;
-    P.fp32 = c->prm.precision == EBV_FP32_REFINE;
     EBV_LAUNCH(c, k_fill, dim3(vblocks(ncell(c->g))), dim3(256), 0, x, ncell(c->g), 0.0);
-    return pcg(c, P, b, x, iters, res);
+    return solve(c, P, b, x, iters, res);
 }
 
 ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int comp, double *x, int *iters,
@@ -1233,8 +1425,7 @@ ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int com
     if (s != EBV_OK) return s;
     CcProblem P;
     P.H = &c->visc;
-    P.fp32 = fp32;
-    return pcg(c, P, c->rhs_c, x, iters, res);
+    return solve(c, P, c->rhs_c, x, iters, res);
 }
 
 ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *res)
@@ -1243,8 +1434,7 @@ ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *r
     EBV_LAUNCH(c, k_zero_inactive, dim3(vblocks(nn)), dim3(256), 0, nn, c->nd.lv[0].act, x);
     NdProblem P;
     P.H = &c->nd;
-    P.fp32 = c->prm.precision == EBV_FP32_REFINE;
-    return pcg(c, P, b, x, iters, res);
+    return solve(c, P, b, x, iters, res);
 }
 
 }  // namespace ebv
