@@ -122,28 +122,60 @@ __device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__
 // One colour of Gauss-Seidel in place: x_i = (b_i + sum beta x_nb) / diag for
 // the cells of colour `color` ((i+j+k) mod 2); with zero_start the other
 // colour reads as 0 (the sweep starts from x = 0) and x is not read.
+// Thread (t, j, kk) owns the x-pair (2t, 2t+1) of row j on planes
+// GS_PZ kk .. GS_PZ kk + GS_PZ - 1 and updates the cell of colour `color` in
+// each: every lane works.  All operands of its GS_PZ updates are loaded before
+// any result is stored (the updated cells are never read in the same pass), so
+// the loads of all of them are in flight together.
+constexpr int GS_PZ = 2;
 template <class T>
 __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, const T *__restrict__ b,
                                                int color, int zero_start)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int kk = blockIdx.z * blockDim.z + threadIdx.z;
     const GridD &g = A.g;
-    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
-    const int c = cidx(g, i, j, k);
-    if (((i + j + k) & 1) != color) {
-        if (zero_start) x[c] = T(0);
-        return;
+    if (2 * t >= g.nx || j >= g.ny) return;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    T val[GS_PZ];
+    int cc[GS_PZ];
+#pragma unroll
+    for (int h = 0; h < GS_PZ; h++) {
+        const int k = GS_PZ * kk + h;
+        const int i = 2 * t + ((j + k + color) & 1);
+        cc[h] = -1;
+        val[h] = T(0);
+        if (k >= g.nz || i >= g.nx) continue;
+        const int c = cidx(g, i, j, k);
+        cc[h] = c;
+        const T diag = A.diag[c], bc = b[c];
+        T off = 0;
+        if (!zero_start) {
+            const T bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
+            const T byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
+            const T bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
+            const T xw = i > 0 ? x[c - 1] : T(0), xe = i < g.nx - 1 ? x[c + 1] : T(0);
+            const T xs = j > 0 ? x[c - sy] : T(0), xn = j < g.ny - 1 ? x[c + sy] : T(0);
+            const T xd = k > 0 ? x[c - sz] : T(0), xu = k < g.nz - 1 ? x[c + sz] : T(0);
+            if (i > 0) off += bxl * xw;
+            if (i < g.nx - 1) off += bxh * xe;
+            if (j > 0) off += byl * xs;
+            if (j < g.ny - 1) off += byh * xn;
+            if (k > 0) off += bzl * xd;
+            if (k < g.nz - 1) off += bzh * xu;
+        }
+        val[h] = diag > T(0) ? (bc + off) / diag : T(0);
     }
-    T diag, off;
-    if (zero_start) {
-        diag = A.diag[c];
-        off = T(0);
-    } else {
-        cc_row(A, i, j, k, x, diag, off);
+#pragma unroll
+    for (int h = 0; h < GS_PZ; h++) {
+        if (zero_start) {
+            const int k = GS_PZ * kk + h;
+            const int io = 2 * t + 1 - ((j + k + color) & 1);
+            if (k < g.nz && io < g.nx) x[cidx(g, io, j, k)] = T(0);
+        }
+        if (cc[h] >= 0) x[cc[h]] = val[h];
     }
-    x[c] = diag > T(0) ? (b[c] + off) / diag : T(0);
 }
 
 // Residual of the 8 children, averaged into the coarse right-hand side.
@@ -934,12 +966,16 @@ void cc_smooth2(Ctx *c, const CcLevel &L, T *x, T *t, const T *b, bool red_first
     const int c0 = red_first ? 0 : 1;
     const GridD &g = L.g;
     // algorithmic bytes of one colour pass: half of one sweep's x read and
-    // write, b, extra and 3 face coefficients
+    // write, b, diagonal and 3 face coefficients
     const double nb = 3.5 * sizeof(T) * (double)ncell(g);
+    // threads: x-pairs x rows x groups of GS_PZ planes, blocks of 32 x 4 x 2
+    const int nzg = (g.nz + GS_PZ - 1) / GS_PZ;
+    const dim3 gr(((g.nx + 1) / 2 + 31) / 32, (g.ny + 3) / 4, (nzg + 1) / 2);
+    const char *name = sizeof(T) == 4 ? "cc_gs_colour_sweep<float>" : "cc_gs_colour_sweep<double>";
     for (int s = 0; s < 2; s++) {
         const int z = (s == 0 && zero_start) ? 1 : 0;
-        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_gs_colour_sweep<float>" : "cc_gs_colour_sweep<double>", nb, k_cc_gs<T>, cgrid(g), block3(), 0, A, x, b, c0, z);
-        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_gs_colour_sweep<float>" : "cc_gs_colour_sweep<double>", nb, k_cc_gs<T>, cgrid(g), block3(), 0, A, x, b, 1 - c0, 0);
+        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, block3(), 0, A, x, b, c0, z);
+        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, block3(), 0, A, x, b, 1 - c0, 0);
     }
 }
 
