@@ -255,6 +255,7 @@ ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stre
     GridD &g = c->g;
     g.nx = grid->n[0]; g.ny = grid->n[1]; g.nz = grid->n[2];
     g.h = grid->h;
+    g.ih = 1.0 / grid->h;
     for (int d = 0; d < 3; d++) { g.lo[d] = grid->lo[d]; g.u_in[d] = grid->u_in[d]; }
     for (int s = 0; s < 6; s++) g.bc[s] = grid->bc[s];
     const size_t N3 = ncell(g), NN = nnode(g), NF = nface(g, 0) + nface(g, 1) + nface(g, 2);

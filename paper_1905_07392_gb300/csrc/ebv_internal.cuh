@@ -23,6 +23,7 @@ constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs; fixed for determini
 struct GridD {
     int nx, ny, nz;
     double h;
+    double ih;   // 1 / h, so kernels multiply instead of dividing in FP64
     double lo[3];
     int bc[6];
     double u_in[3];

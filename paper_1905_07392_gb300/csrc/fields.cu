@@ -20,12 +20,27 @@ __device__ inline double mc_slope(const GridD &g, const uint8_t *flag, const dou
     double f0 = f[cidx(g, i, j, k)];
     double fp = f[cidx(g, i + e.x, j + e.y, k + e.z)];
     double fm = f[cidx(g, i - e.x, j - e.y, k - e.z)];
-    double dl = f0 - fm, dr = fp - f0, dc = 0.5 * (fp - fm);
-    if (dl * dr <= 0.0) return 0.0;
-    double m = fabs(dc);
-    m = fmin(m, 2.0 * fabs(dl));
-    m = fmin(m, 2.0 * fabs(dr));
-    return dc > 0.0 ? m : -m;
+    double dl = f0 - fm, dr = fp - f0, dd = fp - fm;
+    // The limiter  m = min(|dd|/2, 2|dl|, 2|dr|)  only scales by powers of
+    // two and compares, so on normal numbers it is exact on the IEEE bit
+    // patterns: the integer pipe does it and FP64 issues just the three
+    // differences.  dl*dr <= 0 is read off the sign bits (the product of two
+    // nonzero differences of O(1) data does not underflow).
+    const long long kAbs = 0x7fffffffffffffffLL, kE = 1LL << 52;
+    long long bl = __double_as_longlong(dl), br = __double_as_longlong(dr), bd = __double_as_longlong(dd);
+    long long al = bl & kAbs, ar = br & kAbs, ad = bd & kAbs;
+    if (al == 0 || ar == 0 || (bl ^ br) < 0) return 0.0;
+    // exponent fields in [3, 2044]: x4 and /2 stay normal and finite
+    const long long lo = 3 * kE, hi = 2044 * kE;
+    if (al < lo || ar < lo || (ad != 0 && ad < lo) || al >= hi || ar >= hi || ad >= hi) {
+        double m = fabs(0.5 * dd);
+        m = fmin(m, 2.0 * fabs(dl));
+        m = fmin(m, 2.0 * fabs(dr));
+        return dd > 0.0 ? m : -m;
+    }
+    long long m4 = min(ad, min(al + 2 * kE, ar + 2 * kE));   // min(|dd|, 4|dl|, 4|dr|)
+    long long m = m4 == 0 ? 0 : m4 - kE;                     // halved
+    return __longlong_as_double(bd > 0 ? m : (m | ~kAbs));
 }
 
 // Godunov state of Burgers' equation from the two extrapolated normal velocities.
@@ -93,7 +108,7 @@ __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__re
         return;
     }
     double Gm[3][3];
-    const double ih = 1.0 / g.h;
+    const double ih = g.ih;
 #pragma unroll
     for (int d = 0; d < 3; d++)
 #pragma unroll
@@ -168,7 +183,7 @@ __global__ void k_mac_rhs(GridD g, const uint8_t *__restrict__ flag, const doubl
         int flo = fidx(g, d, i, j, k), fhi = fidx(g, d, i + e.x, j + e.y, k + e.z);
         s += A[d][fhi] * U[d][fhi] - A[d][flo] * U[d][flo];
     }
-    b[c] = -s / g.h;
+    b[c] = -s * g.ih;
 }
 
 __global__ void k_mac_correct(GridD g, int d, const double *__restrict__ ap,
@@ -188,11 +203,11 @@ __global__ void k_mac_correct(GridD g, int d, const double *__restrict__ ap,
         int cc[3] = {i, j, k};
         cc[d] -= hs;
         double pc = phi[cidx(g, cc[0], cc[1], cc[2])];
-        double grad = hs ? (0.0 - pc) / (0.5 * g.h) : (pc - 0.0) / (0.5 * g.h);
+        double grad = hs ? (0.0 - pc) * (2.0 * g.ih) : (pc - 0.0) * (2.0 * g.ih);
         uf[f] -= grad;
     } else {
         int3 e = unit(d);
-        uf[f] -= (phi[cidx(g, i, j, k)] - phi[cidx(g, i - e.x, j - e.y, k - e.z)]) / g.h;
+        uf[f] -= (phi[cidx(g, i, j, k)] - phi[cidx(g, i - e.x, j - e.y, k - e.z)]) * g.ih;
     }
 }
 
@@ -299,7 +314,7 @@ __global__ void __launch_bounds__(256) k_flux_div(GridD g, GeomD geo, const doub
             for (int q = 0; q < 3; q++) s[q] += -eta[c] * geo.nrm[q * N3 + c] * nd * geo.area[c];
         }
     }
-    const double inv = 1.0 / (geo.alpha[c] * g.h);
+    const double inv = geo.flag[c] == 1 ? g.ih : 1.0 / (geo.alpha[c] * g.h);   // alpha = 1 on regular cells
     for (int q = 0; q < 3; q++) DC[q * N3 + c] = s[q] * inv;
 }
 
@@ -484,7 +499,7 @@ __global__ void __launch_bounds__(256) k_visc_flux(GridD g, int d, const double 
     }
     const int pos = d == 0 ? i : (d == 1 ? j : k);
     int3 e = unit(d);
-    const double ih = 1.0 / g.h;
+    const double ih = g.ih;
     if (pos == 0 || pos == dimn(g, d)) {
         const int hs = pos != 0;
         const int c = cidx(g, i - hs * e.x, j - hs * e.y, k - hs * e.z);
@@ -541,7 +556,7 @@ __global__ void k_psi(GridD g, const uint8_t *__restrict__ flag, const double *_
         int s = q * N3 + c;
         if (flag[c] == 0) { psi[s] = 0.0; continue; }
         double fq = f ? f[s] : 0.0;
-        psi[s] = rho * u[s] + dt * (rho * C[s] + V[s] - grad_p(g, p, i, j, k, q, 0.25 / g.h) + fq);
+        psi[s] = rho * u[s] + dt * (rho * C[s] + V[s] - grad_p(g, p, i, j, k, q, 0.25 * g.ih) + fq);
     }
 }
 
@@ -556,7 +571,7 @@ __global__ void k_add_gradp(GridD g, const uint8_t *__restrict__ flag, double *_
     for (int q = 0; q < 3; q++) {
         int s = q * N3 + c;
         if (flag[c] == 0) { u[s] = 0.0; continue; }
-        double gq = grad_p(g, p, i, j, k, q, 0.25 / g.h);
+        double gq = grad_p(g, p, i, j, k, q, 0.25 * g.ih);
         u[s] = sgn > 0 ? u[s] + coef * gq : u[s] - coef * gq;
     }
 }
@@ -631,9 +646,9 @@ __global__ void k_cfl_max(GridD g, const uint8_t *__restrict__ flag, const doubl
     double mc = 0.0, mf = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N3; c += gridDim.x * blockDim.x) {
         if (flag[c] == 0) continue;
-        double v = (fabs(u[c]) + fabs(u[N3 + c]) + fabs(u[2 * N3 + c])) / g.h;
+        double v = (fabs(u[c]) + fabs(u[N3 + c]) + fabs(u[2 * N3 + c])) * g.ih;
         mc = fmax(mc, v);
-        if (f) mf = fmax(mf, (fabs(f[c]) + fabs(f[N3 + c]) + fabs(f[2 * N3 + c])) / g.h);
+        if (f) mf = fmax(mf, (fabs(f[c]) + fabs(f[N3 + c]) + fabs(f[2 * N3 + c])) * g.ih);
     }
     for (int o = 16; o > 0; o >>= 1) {
         mc = fmax(mc, __shfl_down_sync(0xffffffffu, mc, o));
@@ -1008,6 +1023,7 @@ extern "C" ebv_status ebv_drag_noalloc(const ebv_grid *grid, const ebv_params *p
     GridD g;
     g.nx = grid->n[0]; g.ny = grid->n[1]; g.nz = grid->n[2];
     g.h = grid->h;
+    g.ih = 1.0 / grid->h;
     for (int d = 0; d < 3; d++) { g.lo[d] = grid->lo[d]; g.u_in[d] = grid->u_in[d]; }
     for (int s = 0; s < 6; s++) g.bc[s] = grid->bc[s];
     GeomD geo;

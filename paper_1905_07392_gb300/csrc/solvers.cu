@@ -407,21 +407,34 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
 
 // q = A p (FP64, level 0) and block partials of p.q
 // (partials of the dot product in FP64 for either precision)
+// Each thread handles planes 2kk and 2kk+1 of column (i, j).
 template <class T>
 __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__restrict__ p, T *__restrict__ q,
                                                       double *__restrict__ part)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int kk = blockIdx.z * blockDim.z + threadIdx.z;
     double v = 0.0;
-    if (i < A.g.nx && j < A.g.ny && k < A.g.nz) {
-        T diag, off;
-        cc_row(A, i, j, k, p, diag, off);
-        int c = cidx(A.g, i, j, k);
-        T y = diag * p[c] - off;
-        q[c] = y;
-        v = (double)(p[c] * y);
+    if (i < A.g.nx && j < A.g.ny) {
+        T y[2], pc[2];
+        int cc[2] = {-1, -1};
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int k = 2 * kk + h;
+            if (k >= A.g.nz) continue;
+            T diag, off;
+            cc_row(A, i, j, k, p, diag, off);
+            cc[h] = cidx(A.g, i, j, k);
+            pc[h] = p[cc[h]];
+            y[h] = diag * pc[h] - off;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+            if (cc[h] >= 0) {
+                q[cc[h]] = y[h];
+                v += (double)(pc[h] * y[h]);
+            }
     }
     v = block_sum3(v);
     if (thread_linear() == 0) part[block_linear()] = v;
@@ -956,10 +969,20 @@ NdOp<T> ndop(const NdLevel &L)
 // V-cycles
 // ---------------------------------------------------------------------------
 
+// Profiler names of the colour sweeps, by precision and level (level 0 is
+// HBM-bound; the coarse levels are latency- and launch-bound).
+static const char *const kGsName[2][8] = {
+    {"cc_gs_colour_sweep<double> L0", "cc_gs_colour_sweep<double> L1", "cc_gs_colour_sweep<double> L2",
+     "cc_gs_colour_sweep<double> L3", "cc_gs_colour_sweep<double> L4", "cc_gs_colour_sweep<double> L5",
+     "cc_gs_colour_sweep<double> L6", "cc_gs_colour_sweep<double> L7+"},
+    {"cc_gs_colour_sweep<float> L0", "cc_gs_colour_sweep<float> L1", "cc_gs_colour_sweep<float> L2",
+     "cc_gs_colour_sweep<float> L3", "cc_gs_colour_sweep<float> L4", "cc_gs_colour_sweep<float> L5",
+     "cc_gs_colour_sweep<float> L6", "cc_gs_colour_sweep<float> L7+"}};
+
 // Two red-black Gauss-Seidel sweeps in place (the first from x = 0 when
 // zero_start), each as two colour passes.
 template <class T>
-void cc_smooth2(Ctx *c, const CcLevel &L, T *x, T *t, const T *b, bool red_first, bool zero_start)
+void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red_first, bool zero_start)
 {
     (void)t;
     CcOp<T> A = ccop<T>(L);
@@ -971,7 +994,7 @@ void cc_smooth2(Ctx *c, const CcLevel &L, T *x, T *t, const T *b, bool red_first
     // threads: x-pairs x rows x groups of GS_PZ planes, blocks of 32 x 4 x 2
     const int nzg = (g.nz + GS_PZ - 1) / GS_PZ;
     const dim3 gr(((g.nx + 1) / 2 + 31) / 32, (g.ny + 3) / 4, (nzg + 1) / 2);
-    const char *name = sizeof(T) == 4 ? "cc_gs_colour_sweep<float>" : "cc_gs_colour_sweep<double>";
+    const char *name = kGsName[sizeof(T) == 4][l < 7 ? l : 7];
     for (int s = 0; s < 2; s++) {
         const int z = (s == 0 && zero_start) ? 1 : 0;
         EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, block3(), 0, A, x, b, c0, z);
@@ -987,7 +1010,7 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         const CcLevel &L = H.lv[l];
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
-        cc_smooth2<T>(c, L, x, (T *)c->lt[l], b, true, true);
+        cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, true, true);
         const CcLevel &Lc = H.lv[l + 1];
         EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_residual_restrict<float>" : "cc_residual_restrict<double>",
                      (6.0 + 1.0 / 8.0) * sizeof(T) * (double)ncell(L.g),
@@ -1005,7 +1028,7 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         const T *b = l ? (const T *)c->lb[l] : b0;
         EBV_LAUNCH(c, k_cc_prolong<T>, cgrid(L.g), block3(), 0, L.g, H.lv[l + 1].g, L.cov,
                    (const T *)c->lx[l + 1], x);
-        cc_smooth2<T>(c, L, x, (T *)c->lt[l], b, false, false);
+        cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, false, false);
     }
 }
 
@@ -1223,16 +1246,18 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
 struct CcProblem : Problem {
     CcHier *H;
     int n() const override { return ncell(H->lv[0].g); }
-    int apply_blocks() const override { return nblocks3(cgrid(H->lv[0].g)); }
+    // two planes per thread
+    dim3 agrid() const { const GridD &g = H->lv[0].g; return grid3(g.nx, g.ny, (g.nz + 1) / 2); }
+    int apply_blocks() const override { return nblocks3(agrid()); }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
         // p, diagonal, 3 faces, q: 6 words per cell
-        EBV_LAUNCH_P(c, "cc_apply_fp64", 48.0 * n(), k_cc_apply_dot<double>, cgrid(H->lv[0].g), block3(), 0,
+        EBV_LAUNCH_P(c, "cc_apply_fp64", 48.0 * n(), k_cc_apply_dot<double>, agrid(), block3(), 0,
                      ccop<double>(H->lv[0]), p, q, c->part);
     }
     void apply_dot32(Ctx *c, const float *p, float *q) override
     {
-        EBV_LAUNCH_P(c, "cc_apply_fp32", 24.0 * n(), k_cc_apply_dot<float>, cgrid(H->lv[0].g), block3(), 0,
+        EBV_LAUNCH_P(c, "cc_apply_fp32", 24.0 * n(), k_cc_apply_dot<float>, agrid(), block3(), 0,
                      ccop<float>(H->lv[0]), p, q, c->part);
     }
     void precond(Ctx *c, const double *r, double *z) override { cc_vcycle<double>(c, *H, r, z); }
@@ -1315,6 +1340,7 @@ int plan_levels(const GridD &g0, GridD *out, bool nodal)
         if ((g.nx & 1) || (g.ny & 1) || (g.nz & 1)) break;
         g.nx /= 2; g.ny /= 2; g.nz /= 2;
         g.h *= 2.0;
+        g.ih *= 0.5;
         out[L++] = g;
     }
     return L;
