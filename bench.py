@@ -148,12 +148,18 @@ def initial_state(s, w, dev):
     return u0, p0
 
 
-def time_steps(s, u, p, steps, warmup, world, profile=False):
+def time_steps(s, u, p, steps, warmup, world, profile=False, graph=False):
     """Warm-up, then exactly `steps` steps between barriers and syncs, timed
-    with CUDA events on the solver's stream.  Returns (seconds, last stats)."""
+    with CUDA events on the solver's stream.  graph: each step is one launch
+    of the captured step graph (captured during the warm-up); otherwise the
+    step's kernels are issued one by one (with profile: each bracketed by
+    CUDA events).  Returns (seconds, kernel launches, profile or None)."""
     import torch
-    for _ in range(warmup):
-        s.advance(u, p, stats=False)
+    if graph:
+        s.advance_graph(u, p, steps=warmup, stats=False)
+    else:
+        for _ in range(warmup):
+            s.advance(u, p, stats=False)
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -163,8 +169,11 @@ def time_steps(s, u, p, steps, warmup, world, profile=False):
     if profile:
         s.profile_begin()
     e0.record(s.stream)
-    for _ in range(steps):
-        s.advance(u, p, stats=False)
+    if graph:
+        s.advance_graph(u, p, steps=steps, stats=False)
+    else:
+        for _ in range(steps):
+            s.advance(u, p, stats=False)
     e1.record(s.stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -227,15 +236,22 @@ def run_ours(args, rank, world, local):
     w = workload(args.n)
     cells = w.n ** 3
 
-    # FP32 smoother + FP64 refinement (headline)
+    # FP32 smoother + FP64 refinement (headline): each step one launch of the
+    # captured step graph
     s = make_solver(w, ebvisc.FP32_REFINE)
     u, p = initial_state(s, w, dev)
     clocks = Clocks(local)
     clocks.start()
-    sec, launches, prof = time_steps(s, u, p, args.steps, args.warmup, world, profile=True)
+    sec, launches, _ = time_steps(s, u, p, args.steps, args.warmup, world, graph=True)
     ck = clocks.stop()
     sec = max_over_ranks(sec, world)
     st = s.advance(u.clone(), p.clone(), stats=True)
+    # kernel breakdown and roofline: the same steps issued kernel by kernel,
+    # each launch bracketed by CUDA events (graph nodes cannot be timed singly)
+    ue, pe = initial_state(s, w, dev)
+    sec_e, _, prof = time_steps(s, ue, pe, args.steps, args.warmup, world, profile=True)
+    sec_e = max_over_ranks(sec_e, world)
+    del ue, pe
     value = cells * args.steps * world / sec / 1e6
     roof, kernels = roofline(prof, cells)
 
@@ -249,6 +265,11 @@ def run_ours(args, rank, world, local):
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (each cell field 134 MB at 256^3)"},
            "roofline": roof, "kernels": kernels,
+           "step_launch": "one CUDA graph launch per step (solver loops as conditional nodes)",
+           "eager": {"value": round(cells * args.steps * world / sec_e / 1e6, 3), "unit": UNIT,
+                     "ms_per_step": round(1e3 * sec_e / args.steps, 3),
+                     "note": "kernel-by-kernel issue with per-launch CUDA events; roofline and "
+                             "kernels are measured here"},
            "clocks": ck, "gpu_launches": launches,
            "solve_iters_last_step": st["iters"], "dt": st["dt"], "drag": st["drag"],
            "yield_frac": st["yield_frac"]}
@@ -257,7 +278,7 @@ def run_ours(args, rank, world, local):
     if not args.skip_fp64:
         s64 = make_solver(w, ebvisc.FP64)
         u64, p64 = initial_state(s64, w, dev)
-        sec64, _, _ = time_steps(s64, u64, p64, args.steps, args.warmup, world)
+        sec64, _, _ = time_steps(s64, u64, p64, args.steps, args.warmup, world, graph=True)
         sec64 = max_over_ranks(sec64, world)
         st64 = s64.advance(u64.clone(), p64.clone(), stats=True)
         out["fp64"] = {"value": round(cells * args.steps * world / sec64 / 1e6, 3), "unit": UNIT,

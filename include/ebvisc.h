@@ -156,8 +156,20 @@ ebv_status ebv_timestep(ebv_ctx *ctx, const double *u, const double *f, double *
  * the CFL step.  f: body force 3 x cells or NULL.  stats (host) or NULL. */
 ebv_status ebv_advance(ebv_ctx *ctx, double *u, double *p, double dt, const double *f,
                        ebv_step_stats *stats);
+/* `steps` steps of Algorithm 1 in place, as ebv_advance, from one captured
+ * CUDA graph per (u, p, dt, f): every solver loop of the step is a
+ * conditional WHILE node whose condition a device kernel sets, so each step
+ * is one graph launch with no host synchronisation inside it.  The graph is
+ * captured on the first call (and again when u, p, dt, f, the parameters or
+ * the geometry change); the call synchronises once at the end.  A failed
+ * solve in any step gives EBV_ERR_NAN / EBV_ERR_NOT_CONVERGED (the failing
+ * solve slot is named in ebv_last_error); the steps after it still ran.
+ * stats (host, or NULL): the last step's iterations, residuals, dt, drag. */
+ebv_status ebv_advance_graph(ebv_ctx *ctx, double *u, double *p, double dt, const double *f, int steps,
+                             ebv_step_stats *stats);
 /* `steps` steps from HOST buffers: copies u_host, p_host to the device, runs
- * the steps, copies the result back.  Uses the context's own device copies. */
+ * the steps (as ebv_advance_graph), copies the result back.  Uses the
+ * context's own device copies. */
 ebv_status ebv_advance_host(ebv_ctx *ctx, double *u_host, double *p_host, int steps, double dt,
                             ebv_step_stats *last);
 /* Drag F_z on the body (Eq. drag-force, surface normal into the fluid) and the

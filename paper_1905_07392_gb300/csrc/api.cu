@@ -46,6 +46,15 @@ double plane_fn(const double x[3], void *user)
     return s[0] * x[0] + s[1] * x[1] + s[2] * x[2] - s[3];
 }
 
+void drop_step_graph(Ctx *c)
+{
+    if (c->step_exec) {
+        cudaStreamSynchronize(c->stream);
+        cudaGraphExecDestroy(c->step_exec);
+        c->step_exec = nullptr;
+    }
+}
+
 ebv_status need_geom(Ctx *c)
 {
     if (!c->have_geom) return c->fail(EBV_ERR_GEOMETRY, "no geometry built");
@@ -71,10 +80,11 @@ ebv_status set_dt(Ctx *c, double dt)
     } while (0)
 
 // Algorithm 2 for velocity u: C, eta, V (and the projected face velocities in c->uf).
-ebv_status derived(Ctx *c, const double *u, double *C, double *eta, double *V, int *it, double *res)
+ebv_status derived(Ctx *c, const double *u, double *C, double *eta, double *V, int *it, double *res, int slot)
 {
     TRY(launch_face_states(c, u, c->uf));
     TRY(launch_mac_rhs(c, c->uf, c->rhs_c));
+    c->cur_slot = slot;
     TRY(mac_solve(c, c->rhs_c, c->phi, it, res));
     TRY(launch_mac_correct(c, c->uf, c->phi));
     TRY(launch_convective(c, u, c->uf, C));
@@ -98,6 +108,7 @@ ebv_status viscous_update(Ctx *c, const double *eta, const double *psi, double *
     for (int q = 0; q < 3; q++) {
         int it = 0;
         double res = 0.0;
+        c->cur_slot = slot + q;
         TRY(visc_solve(c, eta, psi + (size_t)q * N3, q, ut + (size_t)q * N3, &it, &res));
         if (st) { st->iters[slot + q] = it; st->res[slot + q] = res; }
     }
@@ -111,6 +122,7 @@ ebv_status nodal_projection(Ctx *c, double *ut, double *p, ebv_step_stats *st, i
     TRY(launch_nodal_rhs(c, ut, c->rhs_n));
     int it = 0;
     double res = 0.0;
+    c->cur_slot = slot;
     TRY(nodal_solve(c, c->rhs_n, p, &it, &res));
     if (st) { st->iters[slot] = it; st->res[slot] = res; }
     TRY(launch_add_gradp(c, ut, p, -1.0));
@@ -125,14 +137,14 @@ ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f
     memset(&loc, 0, sizeof loc);
     TRY(launch_timestep(c, u, f, dt));
     // Predictor
-    TRY(derived(c, u, c->Cm, c->em, c->Vm, &loc.iters[0], &loc.res[0]));
+    TRY(derived(c, u, c->Cm, c->em, c->Vm, &loc.iters[0], &loc.res[0], 0));
     TRY(launch_psi(c, u, c->Cm, c->Vm, p, f, c->psi));
     TRY(viscous_update(c, c->em, c->psi, c->ut, &loc, 1));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ps, p, NN * 8, cudaMemcpyDeviceToDevice, c->stream));
     TRY(nodal_projection(c, c->ut, c->ps, &loc, 4));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->us, c->ut, 3 * N3 * 8, cudaMemcpyDeviceToDevice, c->stream));
     // Corrector
-    TRY(derived(c, c->us, c->Cs, c->es, c->Vs, &loc.iters[5], &loc.res[5]));
+    TRY(derived(c, c->us, c->Cs, c->es, c->Vs, &loc.iters[5], &loc.res[5], 5));
     TRY(launch_average(c, c->Cm, c->Cs, (int)(3 * N3)));
     TRY(launch_average(c, c->Vm, c->Vs, (int)(3 * N3)));
     TRY(launch_average(c, c->em, c->es, (int)N3));
@@ -146,6 +158,94 @@ ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f
                                         c->stream));
         TRY(launch_drag(c, u, p, &loc.drag, &loc.yield_frac));  // synchronises
         loc.dt = c->scal_host[14];
+        *st = loc;
+    }
+    return EBV_OK;
+}
+
+// Captures one step of Algorithm 1 for (u, p, dt, f) into a graph: the
+// solver loops become conditional WHILE nodes, so one graph launch runs a
+// whole step with no host round trip.  The capture itself issues no work.
+ebv_status capture_step(Ctx *c, double *u, double *p, double dt, const double *f)
+{
+    drop_step_graph(c);
+    for (cudaStream_t &s : c->cap_stream)
+        if (!s) EBV_CUDA_TRY(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    const bool prof = c->prof_on;
+    cudaStream_t user = c->stream;
+    c->prof_on = false;
+    c->stream = c->cap_stream[0];
+    c->capturing = true;
+    c->cap_depth = 0;
+    c->cap_err.clear();
+    c->loop_recs.clear();
+    const long long l0 = c->launches;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    ebv_status st = EBV_OK;
+    if (e == cudaSuccess) st = advance_impl(c, u, p, dt, f, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(c->stream, &g) : e;
+    const long long captured = c->launches - l0;
+    c->launches = l0;
+    c->capturing = false;
+    c->stream = user;
+    c->prof_on = prof;
+    if (st != EBV_OK || e2 != cudaSuccess || !c->cap_err.empty()) {
+        if (g) cudaGraphDestroy(g);
+        if (st != EBV_OK) return st;
+        return c->fail(EBV_ERR_CUDA, std::string("step capture: ") +
+                                         (c->cap_err.empty() ? cudaGetErrorString(e2) : c->cap_err.c_str()));
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&c->step_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        c->step_exec = nullptr;
+        return c->fail(EBV_ERR_CUDA, std::string("step graph instantiate: ") + cudaGetErrorString(e3));
+    }
+    long long in_loops = 0;
+    for (const Ctx::LoopRec &r : c->loop_recs) in_loops += r.per_outer + r.per_inner;
+    c->graph_top_launches = captured - in_loops;
+    c->gkey_u = u; c->gkey_p = p; c->gkey_f = f; c->gkey_dt = dt;
+    return EBV_OK;
+}
+
+// `steps` launches of the captured step, then one synchronisation: the
+// step's error word, the launch count and (if asked) the last step's stats.
+ebv_status advance_graph_impl(Ctx *c, double *u, double *p, double dt, const double *f, int steps,
+                              ebv_step_stats *st)
+{
+    if (!c->step_exec || c->gkey_u != u || c->gkey_p != p || c->gkey_f != f || c->gkey_dt != dt)
+        TRY(capture_step(c, u, p, dt, f));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(c->ctl + C_STEPERR, 0, sizeof(int), c->stream));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(c->sstat + kSstatAcc, 0, 2 * kSolveSlots * sizeof(double), c->stream));
+    for (int s = 0; s < steps; s++) EBV_CUDA_TRY(c, cudaGraphLaunch(c->step_exec, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ctl_host, c->ctl, C_LEN * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->sstat_host, c->sstat, kSstatLen * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(&c->scal_host[14], c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    long long n = steps * c->graph_top_launches;
+    for (const Ctx::LoopRec &r : c->loop_recs)
+        n += (long long)(r.per_inner * c->sstat_host[kSstatAcc + 2 * r.slot] +
+                         r.per_outer * c->sstat_host[kSstatAcc + 2 * r.slot + 1]);
+    c->launches += n;
+    const int fe = c->ctl_host[C_STEPERR];
+    if (fe) {
+        const int e = fe / 100, slot = fe % 100;
+        return c->fail(e == E_NAN ? EBV_ERR_NAN : EBV_ERR_NOT_CONVERGED,
+                       std::string(e == E_NAN ? "non-finite residual" : "linear solve did not reach the tolerance") +
+                           " (solve slot " + std::to_string(slot) + ")");
+    }
+    if (st) {
+        ebv_step_stats loc;
+        memset(&loc, 0, sizeof loc);
+        for (int q = 0; q < 10; q++) {
+            loc.iters[q] = (int)c->sstat_host[3 * q];
+            loc.res[q] = c->sstat_host[3 * q + 1];
+        }
+        loc.dt = c->scal_host[14];
+        TRY(launch_drag(c, u, p, &loc.drag, &loc.yield_frac));
         *st = loc;
     }
     return EBV_OK;
@@ -278,6 +378,9 @@ ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stre
           alloc(&c->ke32, V);
     ok &= alloc(&c->part, (size_t)1 << 20) && alloc(&c->scal, 32);
     ok &= cudaMallocHost(&c->scal_host, 32 * sizeof(double)) == cudaSuccess;
+    ok &= alloc(&c->ctl, C_LEN) && alloc(&c->sstat, kSstatLen);
+    ok &= cudaMallocHost(&c->ctl_host, C_LEN * sizeof(int)) == cudaSuccess;
+    ok &= cudaMallocHost(&c->sstat_host, kSstatLen * sizeof(double)) == cudaSuccess;
     c->vec_len = V;
     if (!ok) {
         ebv_destroy(c);
@@ -288,6 +391,8 @@ ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stre
         return EBV_ERR_INVALID;
     }
     cudaMemsetAsync(c->scal, 0, 32 * sizeof(double), c->stream);
+    cudaMemsetAsync(c->ctl, 0, C_LEN * sizeof(int), c->stream);
+    cudaMemsetAsync(c->sstat, 0, kSstatLen * sizeof(double), c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         ebv_destroy(c);
         return EBV_ERR_CUDA;
@@ -302,6 +407,7 @@ ebv_status ebv_set_params(ebv_ctx *c, const ebv_params *params)
     std::string why;
     if (check_params(params, why) != EBV_OK) return c->fail(EBV_ERR_INVALID, why);
     bool prec_changed = params->precision != c->prm.precision;
+    drop_step_graph(c);
     c->prm = *params;
     if (prec_changed && c->have_geom) return setup_geometry_solvers(c);
     return EBV_OK;
@@ -310,6 +416,7 @@ ebv_status ebv_set_params(ebv_ctx *c, const ebv_params *params)
 ebv_status ebv_build_geometry(ebv_ctx *c, ebv_implicit_fn fn, void *user)
 {
     if (!c || !fn) return EBV_ERR_INVALID;
+    drop_step_graph(c);
     TRY(build_geometry_host(c, fn, user));
     TRY(setup_geometry_solvers(c));
     EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -366,7 +473,7 @@ ebv_status ebv_derived(ebv_ctx *c, const double *u, double *C, double *eta, doub
 {
     if (!c || !u || !C || !eta || !V) return EBV_ERR_INVALID;
     TRY(need_geom(c));
-    TRY(derived(c, u, C, eta, V, iters, res));
+    TRY(derived(c, u, C, eta, V, iters, res, 0));
     EBV_CUDA_TRY(c, cudaGetLastError());
     return EBV_OK;
 }
@@ -385,6 +492,7 @@ ebv_status ebv_solve_mac(ebv_ctx *c, double *uf, double *phi, int *iters, double
     if (!c || !uf || !phi) return EBV_ERR_INVALID;
     TRY(need_geom(c));
     TRY(launch_mac_rhs(c, uf, c->rhs_c));
+    c->cur_slot = 0;
     TRY(mac_solve(c, c->rhs_c, phi, iters, res));
     TRY(launch_mac_correct(c, uf, phi));
     EBV_CUDA_TRY(c, cudaGetLastError());
@@ -433,6 +541,16 @@ ebv_status ebv_advance(ebv_ctx *c, double *u, double *p, double dt, const double
     return EBV_OK;
 }
 
+ebv_status ebv_advance_graph(ebv_ctx *c, double *u, double *p, double dt, const double *f, int steps,
+                             ebv_step_stats *st)
+{
+    if (!c || !u || !p || steps < 0) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(advance_graph_impl(c, u, p, dt, f, steps, st));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
 ebv_status ebv_advance_host(ebv_ctx *c, double *u_host, double *p_host, int steps, double dt,
                             ebv_step_stats *last)
 {
@@ -441,8 +559,7 @@ ebv_status ebv_advance_host(ebv_ctx *c, double *u_host, double *p_host, int step
     const size_t N3 = ncell(c->g), NN = nnode(c->g);
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->u_host_dev, u_host, 3 * N3 * 8, cudaMemcpyHostToDevice, c->stream));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->p_host_dev, p_host, NN * 8, cudaMemcpyHostToDevice, c->stream));
-    for (int s = 0; s < steps; s++)
-        TRY(advance_impl(c, c->u_host_dev, c->p_host_dev, dt, nullptr, (s == steps - 1) ? last : nullptr));
+    TRY(advance_graph_impl(c, c->u_host_dev, c->p_host_dev, dt, nullptr, steps, last));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(u_host, c->u_host_dev, 3 * N3 * 8, cudaMemcpyDeviceToHost, c->stream));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(p_host, c->p_host_dev, NN * 8, cudaMemcpyDeviceToHost, c->stream));
     EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -497,6 +614,13 @@ void ebv_destroy(ebv_ctx *c)
         cudaFree(c->lx[l]); cudaFree(c->lb[l]); cudaFree(c->lr[l]); cudaFree(c->ld[l]); cudaFree(c->lt[l]);
     }
     if (c->scal_host) cudaFreeHost(c->scal_host);
+    drop_step_graph(c);
+    cudaFree(c->ctl);
+    cudaFree(c->sstat);
+    if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    if (c->sstat_host) cudaFreeHost(c->sstat_host);
+    for (cudaStream_t s : c->cap_stream)
+        if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     delete c;
 }

@@ -19,6 +19,16 @@ namespace ebv {
 constexpr int kMaxLevels = 16;
 constexpr int kBottomMax = 512;      // largest dense bottom system (unknowns)
 constexpr int kReduceBlocks = 1216;  // 8 per SM on 152 SMs; fixed for determinism
+constexpr int kSolveSlots = 16;       // solve statistics slots (10 per step)
+// sstat: [3 s] iterations, [3 s + 1] relative residual, [3 s + 2] outer passes
+// of the last solve in slot s; from kSstatAcc: per slot, running sums of
+// iterations and of outer-body passes (launch accounting of captured steps).
+constexpr int kSstatAcc = 3 * kSolveSlots;
+constexpr int kSstatLen = kSstatAcc + 2 * kSolveSlots;
+// control words: loop conditions, iteration counters, error words
+enum { C_COND_OUT = 0, C_COND_IN = 1, C_IT = 2, C_K = 3, C_NOUT = 4, C_STALL = 5, C_ERR = 6, C_ZERO = 7,
+       C_STEPERR = 8, C_LEN = 16 };
+enum { E_NAN = 1, E_NOTCONV = 2 };
 
 struct GridD {
     int nx, ny, nz;
@@ -120,6 +130,7 @@ struct CcLevel {
     double *extra_d = nullptr, *diag_d = nullptr, *bf_d[3] = {nullptr, nullptr, nullptr};
     float *extra_f = nullptr, *diag_f = nullptr, *bf_f[3] = {nullptr, nullptr, nullptr};
     uint8_t *cov = nullptr;  // 1 where the cell is covered (identity row)
+    dim3 gs_blk = dim3(32, 4, 2);  // colour-pass block shape (autotuned per level)
 };
 
 struct CcHier {
@@ -137,6 +148,7 @@ struct NdLevel {
     uint8_t *act = nullptr;      // 1 for active nodes
     uint8_t *reg = nullptr;      // level 0: 1 where all 8 cells around the node are full
     double lam_max = 2.0;        // bound of the spectrum of D^-1 A
+    dim3 ch_blk = dim3(32, 4, 2);  // Chebyshev-step block shape (autotuned per level)
 };
 
 struct NdHier {
@@ -207,6 +219,27 @@ struct Ctx {
     double *scal = nullptr;      // device scalars
     double *scal_host = nullptr; // pinned mirror
     size_t vec_len = 0;
+
+    // Solver loop control lives on the device: the convergence tests run in
+    // one-thread kernels that write a condition word (read back by the host
+    // loop in eager mode) and, inside a captured graph, set the handle of a
+    // conditional WHILE node, so a whole step runs without the host.
+    int *ctl = nullptr;           // condition words, counters, error words
+    int *ctl_host = nullptr;      // pinned mirror
+    double *sstat = nullptr;      // per solve slot: iterations, relative residual, outer passes
+    double *sstat_host = nullptr; // pinned mirror
+    int cur_slot = 0;             // slot of the solve being issued
+    bool capturing = false;       // issuing into a graph capture
+    int cap_depth = 0;            // nesting of conditional bodies being captured
+    cudaStream_t cap_stream[4] = {};
+    std::string cap_err;          // first failure while capturing
+    struct LoopRec { int slot, per_outer, per_inner; };
+    std::vector<LoopRec> loop_recs;   // launches per loop pass of each captured solve
+    long long graph_top_launches = 0; // launches of the captured step outside loop bodies
+    // the captured step (one graph launch = one step)
+    cudaGraphExec_t step_exec = nullptr;
+    const void *gkey_u = nullptr, *gkey_p = nullptr, *gkey_f = nullptr;
+    double gkey_dt = 0.0;
 
     ebv_status fail(ebv_status s, const std::string &m)
     {

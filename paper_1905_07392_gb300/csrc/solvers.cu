@@ -802,7 +802,117 @@ __global__ void __launch_bounds__(256) k_bottom_solve(const double *__restrict__
 // ===========================================================================
 // Krylov glue
 // ===========================================================================
-enum { S_BB = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_PQ = 4 };
+enum { S_BB = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_PQ = 4, S_REL = 16, S_PREV = 17, S_T2 = 18 };
+
+// Writes a loop condition: the control word (polled by the host in eager
+// mode) and, inside a captured graph, the conditional node's handle.
+__device__ inline void set_cond(int *ctl, int slot, int v, cudaGraphConditionalHandle h, int use_h)
+{
+    ctl[slot] = v;
+    if (use_h) cudaGraphSetConditional(h, v ? 1u : 0u);
+}
+
+__global__ void k_set_cond(int *ctl, int slot, int v, cudaGraphConditionalHandle h, int use_h)
+{
+    if (threadIdx.x == 0) set_cond(ctl, slot, v, h, use_h);
+}
+
+__global__ void k_solve_begin(int *ctl)
+{
+    if (threadIdx.x == 0) {
+        ctl[C_IT] = 0; ctl[C_K] = 0; ctl[C_NOUT] = 0; ctl[C_STALL] = 0; ctl[C_ERR] = 0; ctl[C_ZERO] = 0;
+    }
+}
+
+// After a true residual (S_RR = |b - A x|^2, S_BB = |b|^2): record the
+// relative residual and decide whether another CG pass (FP64 path: a
+// restart; refinement path: one correction solve) runs.  Passes are capped
+// at max_pass, iterations at maxit; a non-finite norm stops with E_NAN; b = 0
+// flags x for zeroing.  For refinement, the inner target and stall state of
+// the coming correction solve are set here.
+__global__ void k_outer_check(double *scal, int *ctl, double tol, int maxit, int max_pass, int refine,
+                              double inner_drop, cudaGraphConditionalHandle h, int use_h)
+{
+    if (threadIdx.x) return;
+    const double bb = scal[S_BB], rr = scal[S_RR];
+    int go = 0;
+    if (ctl[C_ERR] == 0) {
+        if (!isfinite(rr) || !isfinite(bb)) {
+            ctl[C_ERR] = E_NAN;
+        } else if (bb == 0.0) {
+            ctl[C_ZERO] = 1;
+            scal[S_REL] = 0.0;
+        } else {
+            const double rel = sqrt(rr / bb);
+            scal[S_REL] = rel;
+            go = rel > tol && ctl[C_IT] < maxit && ctl[C_NOUT] < max_pass;
+            if (go && refine) {
+                const double f = fmax(inner_drop, 0.5 * tol / rel);
+                scal[S_T2] = rr * f * f;
+                scal[S_PREV] = rr;
+                ctl[C_STALL] = 0;
+            }
+        }
+    }
+    ctl[C_NOUT]++;
+    ctl[C_K] = 0;
+    set_cond(ctl, C_COND_OUT, go, h, use_h);
+}
+
+// After one CG iteration (S_RR = recursive residual norm^2).  FP64 path:
+// continue while |r|/|b| > tol/2.  Refinement path: continue until the
+// correction's residual is below its target, or it has stalled (three
+// iterations in a row that do not cut |r|^2 by 4: the FP32 round-off floor).
+__global__ void k_inner_check(double *scal, int *ctl, double tol, int maxit, int refine,
+                              cudaGraphConditionalHandle h, int use_h)
+{
+    if (threadIdx.x) return;
+    scal[S_RZOLD] = scal[S_RZ];
+    ctl[C_IT]++;
+    ctl[C_K]++;
+    const double rr = scal[S_RR];
+    int go = 1;
+    if (!isfinite(rr)) {
+        ctl[C_ERR] = E_NAN;
+        go = 0;
+    } else if (!refine) {
+        go = sqrt(rr / scal[S_BB]) > 0.5 * tol;
+    } else if (rr <= scal[S_T2]) {
+        go = 0;
+    } else {
+        if (rr > 0.25 * scal[S_PREV]) {
+            if (++ctl[C_STALL] >= 3) go = 0;
+        } else {
+            ctl[C_STALL] = 0;
+        }
+        scal[S_PREV] = rr;
+    }
+    if (ctl[C_IT] >= maxit) go = 0;
+    set_cond(ctl, C_COND_IN, go, h, use_h);
+}
+
+// End of a solve: per-slot statistics, and the step's first failure
+// (100 x error + slot) kept in C_STEPERR.
+__global__ void k_solve_end(const double *scal, int *ctl, double tol, double *sstat, int slot)
+{
+    if (threadIdx.x) return;
+    const double rel = scal[S_REL];
+    sstat[3 * slot] = ctl[C_IT];
+    sstat[3 * slot + 1] = rel;
+    sstat[3 * slot + 2] = ctl[C_NOUT];
+    int e = ctl[C_ERR];
+    if (e == 0 && !(rel <= tol)) e = E_NOTCONV;
+    if (e) ctl[C_ERR] = e;
+    if (e && ctl[C_STEPERR] == 0) ctl[C_STEPERR] = 100 * e + slot;
+    sstat[kSstatAcc + 2 * slot] += ctl[C_IT];
+    sstat[kSstatAcc + 2 * slot + 1] += ctl[C_NOUT] - 1;
+}
+
+__global__ void k_zero_if(double *x, int n, const int *ctl)
+{
+    if (!ctl[C_ZERO]) return;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) x[s] = 0.0;
+}
 
 __global__ void __launch_bounds__(256) k_resid_init(const double *__restrict__ b, const double *__restrict__ q,
                                                     double *__restrict__ r, int n, double *__restrict__ part)
@@ -839,8 +949,9 @@ __global__ void __launch_bounds__(256) k_cg_update(double *__restrict__ x, doubl
 }
 
 __global__ void k_cg_pupdate(double *__restrict__ p, const double *__restrict__ z, const double *__restrict__ scal,
-                             int n, int first)
+                             int n, const int *__restrict__ ctl)
 {
+    const int first = ctl[C_K] == 0;
     const double beta = first ? 0.0 : scal[S_RZ] / scal[S_RZOLD];
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
         p[s] = first ? z[s] : z[s] + beta * p[s];
@@ -880,9 +991,10 @@ __global__ void __launch_bounds__(256) k_dot32(const float *__restrict__ a, cons
 // e += a p, r -= a q (e starts from 0 when first), partials of r.r
 __global__ void __launch_bounds__(256) k_cg_update32(float *__restrict__ e, float *__restrict__ r,
                                                      const float *__restrict__ p, const float *__restrict__ q,
-                                                     const double *__restrict__ scal, int n, int first,
-                                                     double *__restrict__ part)
+                                                     const double *__restrict__ scal, int n,
+                                                     const int *__restrict__ ctl, double *__restrict__ part)
 {
+    const int first = ctl[C_K] == 0;
     const float a = (float)(scal[S_RZ] / scal[S_PQ]);
     float v = 0.0f;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -896,8 +1008,9 @@ __global__ void __launch_bounds__(256) k_cg_update32(float *__restrict__ e, floa
 }
 
 __global__ void k_cg_pupdate32(float *__restrict__ p, const float *__restrict__ z, const double *__restrict__ scal,
-                               int n, int first)
+                               int n, const int *__restrict__ ctl)
 {
+    const int first = ctl[C_K] == 0;
     const float beta = first ? 0.0f : (float)(scal[S_RZ] / scal[S_RZOLD]);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
         p[s] = first ? z[s] : z[s] + beta * p[s];
@@ -906,11 +1019,6 @@ __global__ void k_cg_pupdate32(float *__restrict__ p, const float *__restrict__ 
 __global__ void k_add32to64(double *__restrict__ x, const float *__restrict__ e, int n)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) x[s] += (double)e[s];
-}
-
-__global__ void k_scal_copy(double *scal, int dst, int src)
-{
-    if (threadIdx.x == 0) scal[dst] = scal[src];
 }
 
 __global__ void k_fill(double *a, int n, double v)
@@ -981,6 +1089,16 @@ static const char *const kGsName[2][8] = {
 
 // Two red-black Gauss-Seidel sweeps in place (the first from x = 0 when
 // zero_start), each as two colour passes.
+inline dim3 gs_grid(const GridD &g, dim3 bk)
+{
+    const int nzg = (g.nz + GS_PZ - 1) / GS_PZ;
+    return dim3(((g.nx + 1) / 2 + bk.x - 1) / bk.x, (g.ny + bk.y - 1) / bk.y, (nzg + bk.z - 1) / bk.z);
+}
+inline dim3 ch_grid(const GridD &g, dim3 bk)
+{
+    return dim3((g.nx + 1 + bk.x - 1) / bk.x, (g.ny + 1 + bk.y - 1) / bk.y, (g.nz + 1 + bk.z - 1) / bk.z);
+}
+
 template <class T>
 void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red_first, bool zero_start)
 {
@@ -991,14 +1109,13 @@ void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool re
     // algorithmic bytes of one colour pass: half of one sweep's x read and
     // write, b, diagonal and 3 face coefficients
     const double nb = 3.5 * sizeof(T) * (double)ncell(g);
-    // threads: x-pairs x rows x groups of GS_PZ planes, blocks of 32 x 4 x 2
-    const int nzg = (g.nz + GS_PZ - 1) / GS_PZ;
-    const dim3 gr(((g.nx + 1) / 2 + 31) / 32, (g.ny + 3) / 4, (nzg + 1) / 2);
+    // threads: x-pairs x rows x groups of GS_PZ planes, in the level's block shape
+    const dim3 bk = L.gs_blk, gr = gs_grid(g, bk);
     const char *name = kGsName[sizeof(T) == 4][l < 7 ? l : 7];
     for (int s = 0; s < 2; s++) {
         const int z = (s == 0 && zero_start) ? 1 : 0;
-        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, block3(), 0, A, x, b, c0, z);
-        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, block3(), 0, A, x, b, 1 - c0, 0);
+        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, bk, 0, A, x, b, c0, z);
+        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, bk, 0, A, x, b, 1 - c0, 0);
     }
 }
 
@@ -1065,7 +1182,8 @@ void nd_smooth(Ctx *c, const NdLevel &L, int l, T *x, T *t, const T *b, bool zer
         // from zero reads only b and alpha and writes d, x)
         const bool z0 = s == 0 && zero_start;
         const double nb = (z0 ? 4.0 : 6.0) * sizeof(T) * (double)nnode(L.g);
-        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "nodal_chebyshev_step<float>" : "nodal_chebyshev_step<double>", nb, k_nd_cheb<T>, ngrid(L.g), block3(), 0, A, src, dst, d, b, (T)k.cd[s],
+        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "nodal_chebyshev_step<float>" : "nodal_chebyshev_step<double>", nb,
+                     k_nd_cheb<T>, ch_grid(L.g, L.ch_blk), L.ch_blk, 0, A, src, dst, d, b, (T)k.cd[s],
                      (T)k.cr[s], (int)z0);
         src = dst;
         dst = (dst == x) ? t : x;
@@ -1120,64 +1238,163 @@ struct Problem {
 
 inline int vblocks(int n) { return std::min(kReduceBlocks, (n + 255) / 256); }
 
-ebv_status read_scalars(Ctx *c, int first, int count)
+// A loop whose condition is decided on the device.  Eager mode: next()
+// reads the condition word back (one synchronisation per pass).  Capture
+// mode: the first next() adds a conditional WHILE node after the work issued
+// so far and redirects the context's stream into the node's body graph; the
+// second ends the body capture.  The kernel that sets the condition before
+// the loop and the last kernel of the body take (h, use_h).
+struct DevLoop {
+    Ctx *c;
+    int slot;
+    cudaGraphConditionalHandle h = 0;
+    int use_h = 0;
+    int pass = 0;
+    cudaStream_t saved = nullptr, body = nullptr;
+    long long l0 = 0;
+    int inner_count = 0;   // launches of a nested loop's body (capture mode)
+
+    DevLoop(Ctx *c_, int slot_) : c(c_), slot(slot_)
+    {
+        if (!c->capturing) return;
+        cudaStreamCaptureStatus st;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g) != cudaSuccess ||
+            st != cudaStreamCaptureStatusActive ||
+            cudaGraphConditionalHandleCreate(&h, g, 0, 0) != cudaSuccess) {
+            if (c->cap_err.empty()) c->cap_err = "conditional handle";
+            return;
+        }
+        use_h = 1;
+    }
+
+    bool next()
+    {
+        if (!c->capturing) {
+            if (cudaMemcpyAsync(c->ctl_host + slot, c->ctl + slot, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return false;
+            return c->ctl_host[slot] != 0;
+        }
+        if (pass == 0) {
+            pass = 1;
+            if (!use_h || c->cap_depth + 1 >= 4) {
+                if (c->cap_err.empty()) c->cap_err = "loop nesting";
+                return false;
+            }
+            cudaStreamCaptureStatus st;
+            cudaGraph_t g = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            if (cudaStreamGetCaptureInfo(c->stream, &st, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+                cudaGraphAddNode(&node, g, deps, nullptr, nd, &np) != cudaSuccess ||
+                cudaStreamUpdateCaptureDependencies(c->stream, &node, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies) != cudaSuccess) {
+                if (c->cap_err.empty()) c->cap_err = "conditional node";
+                return false;
+            }
+            body = c->cap_stream[++c->cap_depth];
+            if (cudaStreamBeginCaptureToGraph(body, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+                c->cap_depth--;
+                if (c->cap_err.empty()) c->cap_err = "body capture";
+                return false;
+            }
+            saved = c->stream;
+            c->stream = body;
+            l0 = c->launches;
+            return true;
+        }
+        if (pass == 1) {
+            pass = 2;
+            cudaGraph_t gb = nullptr;
+            if (cudaStreamEndCapture(body, &gb) != cudaSuccess && c->cap_err.empty()) c->cap_err = "body end";
+            c->stream = saved;
+            c->cap_depth--;
+        }
+        return false;
+    }
+    // launches captured in the body (valid after the loop in capture mode)
+    int body_launches() const { return (int)(c->launches - l0); }
+};
+
+// Issues the end-of-solve kernels and, in eager mode, reads the solve's
+// statistics and status back.
+ebv_status finish_solve(Ctx *c, double *x, int n, int *iters, double *res)
 {
-    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->scal_host + first, c->scal + first, count * sizeof(double),
+    EBV_LAUNCH(c, k_zero_if, dim3(vblocks(n)), dim3(256), 0, x, n, c->ctl);
+    EBV_LAUNCH(c, k_solve_end, dim3(1), dim3(32), 0, c->scal, c->ctl, c->prm.tol, c->sstat, c->cur_slot);
+    if (c->capturing) {
+        if (iters) *iters = 0;
+        if (res) *res = 0.0;
+        return EBV_OK;
+    }
+    const int s = c->cur_slot;
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->sstat_host + 3 * s, c->sstat + 3 * s, 3 * sizeof(double),
                                     cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ctl_host + C_ERR, c->ctl + C_ERR, sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
     EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (iters) *iters = (int)c->sstat_host[3 * s];
+    if (res) *res = c->sstat_host[3 * s + 1];
+    if (c->ctl_host[C_ERR] == E_NAN) return c->fail(EBV_ERR_NAN, "non-finite residual");
+    if (c->ctl_host[C_ERR] == E_NOTCONV)
+        return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance");
     return EBV_OK;
 }
 
+// Preconditioned CG in FP64, restarted from the true residual whenever the
+// recursive one has dropped below tol/2 but the true one is still above tol
+// (at most 20 passes).
 ebv_status pcg(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
 {
     const int n = P.n();
     const double tol = c->prm.tol;
     const int maxit = c->prm.max_iters;
     double *r = c->kr, *z = c->kz, *p = c->kp, *q = c->kq;
-    int it = 0;
-    double rel = 0.0, bb = 0.0;
-    ebv_status st;
-    for (int restart = 0; restart < 20; restart++) {
-        // true residual
+    auto true_residual = [&]() {
         P.apply_dot(c, x, q);
         EBV_LAUNCH(c, k_resid_init, dim3(vblocks(n)), dim3(256), 0, b, q, r, n, c->part);
         reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
         reduce_sum(c, c->part + vblocks(n), vblocks(n), c->scal + S_BB);
-        if ((st = read_scalars(c, 0, 2)) != EBV_OK) return st;
-        bb = c->scal_host[S_BB];
-        double rr = c->scal_host[S_RR];
-        if (!std::isfinite(rr) || !std::isfinite(bb)) return c->fail(EBV_ERR_NAN, "non-finite residual");
-        if (bb == 0.0) {
-            EBV_LAUNCH(c, k_fill, dim3(vblocks(n)), dim3(256), 0, x, n, 0.0);
-            rel = 0.0;
-            break;
-        }
-        rel = sqrt(rr / bb);
-        if (rel <= tol || it >= maxit) break;
-        bool first = true;
-        while (it < maxit) {
+    };
+    EBV_LAUNCH(c, k_solve_begin, dim3(1), dim3(32), 0, c->ctl);
+    DevLoop outer(c, C_COND_OUT);
+    true_residual();
+    EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 20, 0, 0.0, outer.h,
+               outer.use_h);
+    int inner_count = 0;
+    while (outer.next()) {
+        DevLoop inner(c, C_COND_IN);
+        EBV_LAUNCH(c, k_set_cond, dim3(1), dim3(32), 0, c->ctl, C_COND_IN, 1, inner.h, inner.use_h);
+        while (inner.next()) {
             P.precond(c, r, z);
             EBV_LAUNCH(c, k_dot, dim3(vblocks(n)), dim3(256), 0, r, z, n, c->part);
             reduce_sum(c, c->part, vblocks(n), c->scal + S_RZ);
-            EBV_LAUNCH(c, k_cg_pupdate, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, (int)first);
-            first = false;
+            EBV_LAUNCH(c, k_cg_pupdate, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, c->ctl);
             P.apply_dot(c, p, q);
             reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_PQ);
             EBV_LAUNCH(c, k_cg_update, dim3(vblocks(n)), dim3(256), 0, x, r, p, q, c->scal, n, c->part);
             reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
-            EBV_LAUNCH(c, k_scal_copy, dim3(1), dim3(32), 0, c->scal, S_RZOLD, S_RZ);
-            it++;
-            if ((st = read_scalars(c, S_RR, 1)) != EBV_OK) return st;
-            double rr2 = c->scal_host[S_RR];
-            if (!std::isfinite(rr2)) return c->fail(EBV_ERR_NAN, "non-finite residual");
-            if (sqrt(rr2 / bb) <= 0.5 * tol) break;
+            EBV_LAUNCH(c, k_inner_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 0, inner.h,
+                       inner.use_h);
         }
+        inner_count = inner.body_launches();
+        true_residual();
+        EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 20, 0, 0.0, outer.h,
+                   outer.use_h);
     }
-    if (iters) *iters = it;
-    if (res) *res = rel;
-    if (rel > tol && it >= maxit)
-        return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance");
-    return EBV_OK;
+    if (c->capturing)
+        c->loop_recs.push_back({c->cur_slot, outer.body_launches() - inner_count, inner_count});
+    if (!c->cap_err.empty() && c->capturing) return c->fail(EBV_ERR_CUDA, "graph capture: " + c->cap_err);
+    return finish_solve(c, x, n, iters, res);
 }
 
 // Iterative refinement for the FP32 path: the residual r = b - A x and the
@@ -1185,7 +1402,7 @@ ebv_status pcg(Ctx *c, Problem &P, const double *b, double *x, int *iters, doubl
 // conjugate gradients run entirely in FP32 (vectors, operator with FP32
 // coefficients, V-cycle) until its residual drops by `inner_drop` (or it
 // stalls), so FP64 arithmetic is spent once per refinement step instead of in
-// every Krylov iteration.
+// every Krylov iteration.  At most 60 corrections.
 ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
 {
     const int n = P.n();
@@ -1193,54 +1410,43 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
     const int maxit = c->prm.max_iters;
     const double inner_drop = 1e-4;
     float *r = c->kr32, *z = c->kz32, *p = c->kp32, *q = c->kq32, *e = c->ke32;
-    int it = 0;
-    double rel = 0.0;
-    ebv_status st;
-    for (int outer = 0; outer < 60; outer++) {
+    auto true_residual = [&]() {
         P.apply_dot(c, x, c->kq);
         EBV_LAUNCH(c, k_resid_to32, dim3(vblocks(n)), dim3(256), 0, b, c->kq, r, n, c->part);
         reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
         reduce_sum(c, c->part + vblocks(n), vblocks(n), c->scal + S_BB);
-        if ((st = read_scalars(c, 0, 2)) != EBV_OK) return st;
-        const double bb = c->scal_host[S_BB], rr0 = c->scal_host[S_RR];
-        if (!std::isfinite(rr0) || !std::isfinite(bb)) return c->fail(EBV_ERR_NAN, "non-finite residual");
-        if (bb == 0.0) {
-            EBV_LAUNCH(c, k_fill, dim3(vblocks(n)), dim3(256), 0, x, n, 0.0);
-            rel = 0.0;
-            break;
-        }
-        rel = sqrt(rr0 / bb);
-        if (rel <= tol || it >= maxit) break;
-        // inner FP32 CG from e = 0 until |r| <= target (relative to this step's r)
-        const double target2 = rr0 * std::max(inner_drop, 0.5 * tol / rel) * std::max(inner_drop, 0.5 * tol / rel);
-        double prev = rr0;
-        int stall = 0;
-        for (int k = 0; it < maxit; k++) {
+    };
+    EBV_LAUNCH(c, k_solve_begin, dim3(1), dim3(32), 0, c->ctl);
+    DevLoop outer(c, C_COND_OUT);
+    true_residual();
+    EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 60, 1, inner_drop, outer.h,
+               outer.use_h);
+    int inner_count = 0;
+    while (outer.next()) {
+        DevLoop inner(c, C_COND_IN);
+        EBV_LAUNCH(c, k_set_cond, dim3(1), dim3(32), 0, c->ctl, C_COND_IN, 1, inner.h, inner.use_h);
+        while (inner.next()) {
             P.precond32(c, r, z);
             EBV_LAUNCH(c, k_dot32, dim3(vblocks(n)), dim3(256), 0, r, z, n, c->part);
             reduce_sum(c, c->part, vblocks(n), c->scal + S_RZ);
-            EBV_LAUNCH(c, k_cg_pupdate32, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, (int)(k == 0));
+            EBV_LAUNCH(c, k_cg_pupdate32, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, c->ctl);
             P.apply_dot32(c, p, q);
             reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_PQ);
-            EBV_LAUNCH(c, k_cg_update32, dim3(vblocks(n)), dim3(256), 0, e, r, p, q, c->scal, n, (int)(k == 0),
-                       c->part);
+            EBV_LAUNCH(c, k_cg_update32, dim3(vblocks(n)), dim3(256), 0, e, r, p, q, c->scal, n, c->ctl, c->part);
             reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
-            EBV_LAUNCH(c, k_scal_copy, dim3(1), dim3(32), 0, c->scal, S_RZOLD, S_RZ);
-            it++;
-            if ((st = read_scalars(c, S_RR, 1)) != EBV_OK) return st;
-            const double rr = c->scal_host[S_RR];
-            if (!std::isfinite(rr)) return c->fail(EBV_ERR_NAN, "non-finite residual");
-            if (rr <= target2) break;
-            // FP32 round-off floor: stop the inner solve when it no longer gains
-            if (rr > 0.25 * prev) { if (++stall >= 3) break; } else stall = 0;
-            prev = rr;
+            EBV_LAUNCH(c, k_inner_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 1, inner.h,
+                       inner.use_h);
         }
+        inner_count = inner.body_launches();
         EBV_LAUNCH(c, k_add32to64, dim3(vblocks(n)), dim3(256), 0, x, e, n);
+        true_residual();
+        EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 60, 1, inner_drop,
+                   outer.h, outer.use_h);
     }
-    if (iters) *iters = it;
-    if (res) *res = rel;
-    if (rel > tol) return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance");
-    return EBV_OK;
+    if (c->capturing)
+        c->loop_recs.push_back({c->cur_slot, outer.body_launches() - inner_count, inner_count});
+    if (!c->cap_err.empty() && c->capturing) return c->fail(EBV_ERR_CUDA, "graph capture: " + c->cap_err);
+    return finish_solve(c, x, n, iters, res);
 }
 
 struct CcProblem : Problem {
@@ -1428,6 +1634,8 @@ ebv_status setup_solvers(Ctx *c)
 
 // Geometry-dependent solver data: projection coefficients, coverage, nodal
 // volume fractions and active nodes, both bottom inverses.
+ebv_status autotune_shapes(Ctx *c);
+
 ebv_status setup_geometry_solvers(Ctx *c)
 {
     const GridD &g = c->g;
@@ -1464,7 +1672,72 @@ ebv_status setup_geometry_solvers(Ctx *c)
     EBV_LAUNCH(c, k_nd_bottom_assemble, dim3((N.nb + 127) / 128), dim3(128), 0, B.g, B.alpha_d, B.act, N.bmat, N.nb);
     EBV_LAUNCH(c, k_gauss_jordan, dim3(1), dim3(1024), 0, N.bmat, N.nb, N.binv);
     EBV_CUDA_TRY(c, cudaGetLastError());
+    return autotune_shapes(c);
+}
+
+// Launch-shape autotuner.  For every level it times each candidate block
+// shape of the colour pass (on the projection operator) and of the nodal
+// Chebyshev step, on zeroed scratch vectors in the precision the solves
+// use, and keeps the fastest; the viscous hierarchy shares the shapes of the
+// projection hierarchy (same level sizes).  The smoothers' results do not
+// depend on the shape: every update of a pass reads only values that the
+// pass does not write.
+template <class T>
+ebv_status autotune_shapes_t(Ctx *c)
+{
+    static const dim3 cand[] = {dim3(32, 4, 2), dim3(32, 8, 1), dim3(32, 2, 4), dim3(16, 8, 2),
+                                dim3(64, 4, 1), dim3(64, 2, 2), dim3(16, 16, 1), dim3(128, 2, 1)};
+    const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+    T *x = (T *)(sizeof(T) == 4 ? (void *)c->kz32 : (void *)c->kz);
+    T *y = (T *)(sizeof(T) == 4 ? (void *)c->kp32 : (void *)c->kp);
+    T *d = (T *)(sizeof(T) == 4 ? (void *)c->kq32 : (void *)c->kq);
+    T *b = (T *)(sizeof(T) == 4 ? (void *)c->kr32 : (void *)c->kr);
+    for (T *v : {x, y, d, b}) EBV_CUDA_TRY(c, cudaMemsetAsync(v, 0, c->vec_len * sizeof(T), c->stream));
+    cudaEvent_t e0, e1;
+    EBV_CUDA_TRY(c, cudaEventCreate(&e0));
+    EBV_CUDA_TRY(c, cudaEventCreate(&e1));
+    auto time_it = [&](auto launch) -> float {
+        launch();
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 4; r++) launch();
+        cudaEventRecord(e1, c->stream);
+        float ms = 1e30f;
+        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    for (int l = 0; l < c->mac.L; l++) {
+        CcLevel &L = c->mac.lv[l];
+        CcOp<T> A = ccop<T>(L);
+        float best = 1e30f;
+        for (int q = 0; q < nc; q++) {
+            const dim3 bk = cand[q], gr = gs_grid(L.g, bk);
+            float ms = time_it([&]() { k_cc_gs<T><<<gr, bk, 0, c->stream>>>(A, x, b, 0, 0); });
+            if (ms < best) { best = ms; L.gs_blk = bk; }
+        }
+        c->visc.lv[l].gs_blk = L.gs_blk;
+    }
+    ChebCoef k = cheb_coef(2.0);
+    for (int l = 0; l < c->nd.L; l++) {
+        NdLevel &L = c->nd.lv[l];
+        NdOp<T> A = ndop<T>(L);
+        float best = 1e30f;
+        for (int q = 0; q < nc; q++) {
+            const dim3 bk = cand[q], gr = ch_grid(L.g, bk);
+            float ms = time_it([&]() {
+                k_nd_cheb<T><<<gr, bk, 0, c->stream>>>(A, x, y, d, b, (T)k.cd[1], (T)k.cr[1], 0);
+            });
+            if (ms < best) { best = ms; L.ch_blk = bk; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    EBV_CUDA_TRY(c, cudaGetLastError());
     return EBV_OK;
+}
+
+ebv_status autotune_shapes(Ctx *c)
+{
+    return c->prm.precision == EBV_FP32_REFINE ? autotune_shapes_t<float>(c) : autotune_shapes_t<double>(c);
 }
 
 ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res)

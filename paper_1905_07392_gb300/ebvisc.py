@@ -54,7 +54,7 @@ IMPLICIT_FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
 EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geometry_sphere",
            "ebv_build_geometry_plane", "ebv_get_geometry", "ebv_update_viscosity", "ebv_derived",
            "ebv_face_states", "ebv_solve_mac", "ebv_solve_viscous", "ebv_solve_projection",
-           "ebv_timestep", "ebv_advance", "ebv_advance_host", "ebv_drag", "ebv_launch_count",
+           "ebv_timestep", "ebv_advance", "ebv_advance_graph", "ebv_advance_host", "ebv_drag", "ebv_launch_count",
            "ebv_profile_begin", "ebv_profile_end", "ebv_profile_entry", "ebv_last_error",
            "ebv_destroy", "ebv_drag_noalloc"]
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
         "ebv_solve_projection": ([vp, vp, vp, C.c_double, C.POINTER(_Stats)], C.c_int),
         "ebv_timestep": ([vp, vp, vp, dp], C.c_int),
         "ebv_advance": ([vp, vp, vp, C.c_double, vp, C.POINTER(_Stats)], C.c_int),
+        "ebv_advance_graph": ([vp, vp, vp, C.c_double, vp, C.c_int, C.POINTER(_Stats)], C.c_int),
         "ebv_advance_host": ([vp, vp, vp, C.c_int, C.c_double, C.POINTER(_Stats)], C.c_int),
         "ebv_drag": ([vp, vp, vp, dp, dp], C.c_int),
         "ebv_launch_count": ([vp], C.c_longlong),
@@ -309,6 +310,15 @@ class Solver:
         st = _Stats()
         self._ok(self._lib.ebv_advance(self._ctx, _ptr(u), _ptr(p), C.c_double(dt), _ptr(f),
                                        C.byref(st) if stats else None))
+        return _stats_dict(st) if stats else None
+
+    def advance_graph(self, u, p, steps=1, dt=0.0, f=None, stats=True):
+        """`steps` steps in place, each one launch of the captured step graph."""
+        _check_f64(u, 3 * self.ncell, "u")
+        _check_f64(p, self.nnode, "p")
+        st = _Stats()
+        self._ok(self._lib.ebv_advance_graph(self._ctx, _ptr(u), _ptr(p), C.c_double(dt), _ptr(f),
+                                             C.c_int(steps), C.byref(st) if stats else None))
         return _stats_dict(st) if stats else None
 
     def advance_host(self, u: np.ndarray, p: np.ndarray, steps: int, dt=0.0):
