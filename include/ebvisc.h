@@ -218,6 +218,42 @@ ebv_status ebv_profile_entry(ebv_ctx *ctx, int i, const char **name, long long *
 const char *ebv_last_error(const ebv_ctx *ctx);
 void ebv_destroy(ebv_ctx *ctx);
 
+/* ---- Batches ------------------------------------------------------------
+ * A parameter sweep of independent problems (the paper computes drag
+ * coefficients over a range of Bingham numbers, Sec. "Evaluation", flows past
+ * a cylinder and a sphere; running many such problems at once is this
+ * library's own deployment form, not a step of the method).  Instance i has
+ * its own grid, parameters, geometry, work fields and hierarchies, exactly as
+ * a context from ebv_create; every step of all instances is ONE launch of a
+ * graph that forks into one branch per instance (each branch the instance's
+ * captured step, its solver loops conditional nodes of its own), so
+ * instances converge independently while their kernels share the GPU. */
+typedef struct ebv_batch ebv_batch;
+/* n instances: grids[i], params[i]; work queued on `stream` (cudaStream_t).
+ * Allocates everything up front; errors as ebv_create (first failing one). */
+ebv_status ebv_batch_create(int n, const ebv_grid *grids, const ebv_params *params, void *stream,
+                            ebv_batch **out);
+/* Sphere geometry per instance: c_r holds n rows (cx, cy, cz, r), host
+ * memory.  The host builders run in parallel threads; then each instance's
+ * hierarchies are set up and its smoother launch shapes autotuned. */
+ebv_status ebv_batch_build_spheres(ebv_batch *batch, const double *c_r);
+/* Instance i's context (owned by the batch: do not destroy), NULL if out of
+ * range; any single-context call may be made on it between batch steps. */
+ebv_ctx *ebv_batch_instance(ebv_batch *batch, int i);
+/* `steps` CFL steps of every instance: u[i] (3 x cells) and p[i] (nodes) are
+ * device pointers (host arrays of n pointers), updated in place.  The graph
+ * is captured on the first call and again when a pointer changes; one
+ * synchronisation at the end.  A failed solve gives the status of the first
+ * failing instance (named in ebv_batch_last_error).  stats: n entries (host)
+ * for the last step, or NULL. */
+ebv_status ebv_batch_advance(ebv_batch *batch, double *const *u, double *const *p, int steps,
+                             ebv_step_stats *stats);
+/* Sum of the instances' kernel launch counters (see ebv_launch_count). */
+long long ebv_batch_launch_count(const ebv_batch *batch);
+const char *ebv_batch_last_error(const ebv_batch *batch);
+/* Destroys the instances and the batch graph. */
+void ebv_batch_destroy(ebv_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <new>
+#include <thread>
 
 #include "ebv_internal.cuh"
 
@@ -163,33 +164,106 @@ ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f
     return EBV_OK;
 }
 
-// Captures one step of Algorithm 1 for (u, p, dt, f) into a graph: the
-// solver loops become conditional WHILE nodes, so one graph launch runs a
-// whole step with no host round trip.  The capture itself issues no work.
-ebv_status capture_step(Ctx *c, double *u, double *p, double dt, const double *f)
+// Redirects a context's issue into its capture stream (already capturing or
+// joined to a capture); returns the saved state for end_ctx_capture.
+struct CtxCapture {
+    cudaStream_t user;
+    bool prof;
+    long long l0;
+};
+ebv_status begin_ctx_capture(Ctx *c, CtxCapture &k)
 {
-    drop_step_graph(c);
     for (cudaStream_t &s : c->cap_stream)
         if (!s) EBV_CUDA_TRY(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    const bool prof = c->prof_on;
-    cudaStream_t user = c->stream;
+    k.prof = c->prof_on;
+    k.user = c->stream;
+    k.l0 = c->launches;
     c->prof_on = false;
     c->stream = c->cap_stream[0];
     c->capturing = true;
     c->cap_depth = 0;
     c->cap_err.clear();
     c->loop_recs.clear();
-    const long long l0 = c->launches;
+    return EBV_OK;
+}
+// Restores the context; records the launches captured outside loop bodies.
+void end_ctx_capture(Ctx *c, const CtxCapture &k)
+{
+    const long long captured = c->launches - k.l0;
+    c->launches = k.l0;
+    c->capturing = false;
+    c->stream = k.user;
+    c->prof_on = k.prof;
+    long long in_loops = 0;
+    for (const Ctx::LoopRec &r : c->loop_recs) in_loops += r.per_outer + r.per_inner;
+    c->graph_top_launches = captured - in_loops;
+}
+// Launches that `steps` launches of the captured step ran (from the device's
+// per-slot iteration sums, read back into sstat_host).
+long long graph_launches(const Ctx *c, int steps)
+{
+    long long n = steps * c->graph_top_launches;
+    for (const Ctx::LoopRec &r : c->loop_recs)
+        n += (long long)(r.per_inner * c->sstat_host[kSstatAcc + 2 * r.slot] +
+                         r.per_outer * c->sstat_host[kSstatAcc + 2 * r.slot + 1]);
+    return n;
+}
+ebv_status step_error(Ctx *c)
+{
+    const int fe = c->ctl_host[C_STEPERR];
+    if (!fe) return EBV_OK;
+    const int e = fe / 100, slot = fe % 100;
+    return c->fail(e == E_NAN ? EBV_ERR_NAN : EBV_ERR_NOT_CONVERGED,
+                   std::string(e == E_NAN ? "non-finite residual" : "linear solve did not reach the tolerance") +
+                       " (solve slot " + std::to_string(slot) + ")");
+}
+
+// Captures one step of Algorithm 1 for (u, p, dt, f) into a graph: the
+// solver loops become conditional WHILE nodes, so one graph launch runs a
+// whole step with no host round trip.  The capture itself issues no work.
+// Before a run of captured steps: clear the error word and the launch sums.
+ebv_status graph_reset(Ctx *c, cudaStream_t s)
+{
+    EBV_CUDA_TRY(c, cudaMemsetAsync(c->ctl + C_STEPERR, 0, sizeof(int), s));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(c->sstat + kSstatAcc, 0, 2 * kSolveSlots * sizeof(double), s));
+    return EBV_OK;
+}
+// After it: control words, solve statistics and dt to the pinned mirrors.
+ebv_status graph_readback(Ctx *c, cudaStream_t s)
+{
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ctl_host, c->ctl, C_LEN * sizeof(int), cudaMemcpyDeviceToHost, s));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->sstat_host, c->sstat, kSstatLen * sizeof(double), cudaMemcpyDeviceToHost, s));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(&c->scal_host[14], c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return EBV_OK;
+}
+
+// The last captured step's statistics (sstat_host, scal_host[14] read back)
+// plus drag and unyielded fraction of (u, p).
+ebv_status graph_stats(Ctx *c, const double *u, const double *p, ebv_step_stats *st)
+{
+    ebv_step_stats loc;
+    memset(&loc, 0, sizeof loc);
+    for (int q = 0; q < 10; q++) {
+        loc.iters[q] = (int)c->sstat_host[3 * q];
+        loc.res[q] = c->sstat_host[3 * q + 1];
+    }
+    loc.dt = c->scal_host[14];
+    TRY(launch_drag(c, u, p, &loc.drag, &loc.yield_frac));
+    *st = loc;
+    return EBV_OK;
+}
+
+ebv_status capture_step(Ctx *c, double *u, double *p, double dt, const double *f)
+{
+    drop_step_graph(c);
+    CtxCapture k;
+    TRY(begin_ctx_capture(c, k));
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     ebv_status st = EBV_OK;
     if (e == cudaSuccess) st = advance_impl(c, u, p, dt, f, nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(c->stream, &g) : e;
-    const long long captured = c->launches - l0;
-    c->launches = l0;
-    c->capturing = false;
-    c->stream = user;
-    c->prof_on = prof;
+    end_ctx_capture(c, k);
     if (st != EBV_OK || e2 != cudaSuccess || !c->cap_err.empty()) {
         if (g) cudaGraphDestroy(g);
         if (st != EBV_OK) return st;
@@ -202,9 +276,6 @@ ebv_status capture_step(Ctx *c, double *u, double *p, double dt, const double *f
         c->step_exec = nullptr;
         return c->fail(EBV_ERR_CUDA, std::string("step graph instantiate: ") + cudaGetErrorString(e3));
     }
-    long long in_loops = 0;
-    for (const Ctx::LoopRec &r : c->loop_recs) in_loops += r.per_outer + r.per_inner;
-    c->graph_top_launches = captured - in_loops;
     c->gkey_u = u; c->gkey_p = p; c->gkey_f = f; c->gkey_dt = dt;
     return EBV_OK;
 }
@@ -216,38 +287,13 @@ ebv_status advance_graph_impl(Ctx *c, double *u, double *p, double dt, const dou
 {
     if (!c->step_exec || c->gkey_u != u || c->gkey_p != p || c->gkey_f != f || c->gkey_dt != dt)
         TRY(capture_step(c, u, p, dt, f));
-    EBV_CUDA_TRY(c, cudaMemsetAsync(c->ctl + C_STEPERR, 0, sizeof(int), c->stream));
-    EBV_CUDA_TRY(c, cudaMemsetAsync(c->sstat + kSstatAcc, 0, 2 * kSolveSlots * sizeof(double), c->stream));
+    TRY(graph_reset(c, c->stream));
     for (int s = 0; s < steps; s++) EBV_CUDA_TRY(c, cudaGraphLaunch(c->step_exec, c->stream));
-    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ctl_host, c->ctl, C_LEN * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->sstat_host, c->sstat, kSstatLen * sizeof(double), cudaMemcpyDeviceToHost,
-                                    c->stream));
-    EBV_CUDA_TRY(c, cudaMemcpyAsync(&c->scal_host[14], c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost,
-                                    c->stream));
+    TRY(graph_readback(c, c->stream));
     EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    long long n = steps * c->graph_top_launches;
-    for (const Ctx::LoopRec &r : c->loop_recs)
-        n += (long long)(r.per_inner * c->sstat_host[kSstatAcc + 2 * r.slot] +
-                         r.per_outer * c->sstat_host[kSstatAcc + 2 * r.slot + 1]);
-    c->launches += n;
-    const int fe = c->ctl_host[C_STEPERR];
-    if (fe) {
-        const int e = fe / 100, slot = fe % 100;
-        return c->fail(e == E_NAN ? EBV_ERR_NAN : EBV_ERR_NOT_CONVERGED,
-                       std::string(e == E_NAN ? "non-finite residual" : "linear solve did not reach the tolerance") +
-                           " (solve slot " + std::to_string(slot) + ")");
-    }
-    if (st) {
-        ebv_step_stats loc;
-        memset(&loc, 0, sizeof loc);
-        for (int q = 0; q < 10; q++) {
-            loc.iters[q] = (int)c->sstat_host[3 * q];
-            loc.res[q] = c->sstat_host[3 * q + 1];
-        }
-        loc.dt = c->scal_host[14];
-        TRY(launch_drag(c, u, p, &loc.drag, &loc.yield_frac));
-        *st = loc;
-    }
+    c->launches += graph_launches(c, steps);
+    TRY(step_error(c));
+    if (st) TRY(graph_stats(c, u, p, st));
     return EBV_OK;
 }
 
@@ -623,6 +669,214 @@ void ebv_destroy(ebv_ctx *c)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: independent instances (own grid, parameters, geometry and
+// multigrid hierarchies), advanced together by ONE graph launch per step.
+// The batch graph forks from an origin stream into one branch per instance;
+// each branch is that instance's captured step (its solver loops are
+// conditional nodes of its own), so instances converge independently and
+// their kernels overlap on the GPU.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct ebv_batch {
+    std::vector<ebv_ctx *> ctx;
+    cudaStream_t stream = nullptr;     // caller's stream: graph launches
+    cudaStream_t origin = nullptr;     // capture origin
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void *> key;     // u, p of every instance at capture
+    std::string err;
+    ebv_status fail(ebv_status s, const std::string &m)
+    {
+        err = m;
+        return s;
+    }
+};
+
+namespace {
+
+void drop_batch_graph(ebv_batch *b)
+{
+    if (b->exec) {
+        cudaStreamSynchronize(b->stream);
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+}
+
+ebv_status capture_batch(ebv_batch *b, double *const *u, double *const *p)
+{
+    drop_batch_graph(b);
+    const int n = (int)b->ctx.size();
+    if (!b->origin && cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess)
+        return b->fail(EBV_ERR_CUDA, "stream");
+    if (!b->fork && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+        return b->fail(EBV_ERR_CUDA, "event");
+    while ((int)b->join.size() < n) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return b->fail(EBV_ERR_CUDA, "event");
+        b->join.push_back(e);
+    }
+    if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return b->fail(EBV_ERR_CUDA, "batch capture begin");
+    ebv_status st = EBV_OK;
+    std::string why;
+    if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) { st = EBV_ERR_CUDA; why = "fork"; }
+    for (int i = 0; i < n && st == EBV_OK; i++) {
+        Ctx *c = b->ctx[i];
+        CtxCapture k;
+        if ((st = begin_ctx_capture(c, k)) != EBV_OK) { why = c->err; break; }
+        if (cudaStreamWaitEvent(c->stream, b->fork, 0) != cudaSuccess) {
+            end_ctx_capture(c, k);
+            st = EBV_ERR_CUDA;
+            why = "branch join";
+            break;
+        }
+        st = advance_impl(c, u[i], p[i], 0.0, nullptr, nullptr);
+        if (st == EBV_OK && !c->cap_err.empty()) { st = EBV_ERR_CUDA; why = c->cap_err; }
+        if (st != EBV_OK && why.empty()) why = c->err;
+        if (st == EBV_OK && (cudaEventRecord(b->join[i], c->stream) != cudaSuccess ||
+                             cudaStreamWaitEvent(b->origin, b->join[i], 0) != cudaSuccess)) {
+            st = EBV_ERR_CUDA;
+            why = "branch merge";
+        }
+        end_ctx_capture(c, k);
+        if (st != EBV_OK) why = "instance " + std::to_string(i) + ": " + why;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->origin, &g);
+    if (st != EBV_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return b->fail(st != EBV_OK ? st : EBV_ERR_CUDA, "batch capture: " + (why.empty() ? cudaGetErrorString(e) : why));
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return b->fail(EBV_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+    }
+    b->key.assign(2 * n, nullptr);
+    for (int i = 0; i < n; i++) { b->key[2 * i] = u[i]; b->key[2 * i + 1] = p[i]; }
+    return EBV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ebv_status ebv_batch_create(int n, const ebv_grid *grids, const ebv_params *params, void *stream, ebv_batch **out)
+{
+    if (n < 1 || !grids || !params || !out) return EBV_ERR_INVALID;
+    *out = nullptr;
+    ebv_batch *b = new (std::nothrow) ebv_batch();
+    if (!b) return EBV_ERR_INVALID;
+    b->stream = (cudaStream_t)stream;
+    for (int i = 0; i < n; i++) {
+        ebv_ctx *c = nullptr;
+        ebv_status st = ebv_create(grids + i, params + i, stream, &c);
+        if (st != EBV_OK) {
+            ebv_batch_destroy(b);
+            return st;
+        }
+        b->ctx.push_back(c);
+    }
+    *out = b;
+    return EBV_OK;
+}
+
+ebv_status ebv_batch_build_spheres(ebv_batch *b, const double *c_r)
+{
+    if (!b || !c_r) return EBV_ERR_INVALID;
+    drop_batch_graph(b);
+    const int n = (int)b->ctx.size();
+    for (ebv_ctx *c : b->ctx) drop_step_graph(c);
+    // host builders in parallel (one instance per thread, a few threads)
+    std::vector<ebv_status> st(n, EBV_OK);
+    const int nt = std::max(1, std::min(n, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; t++)
+        pool.emplace_back([&, t]() {
+            for (int i = t; i < n; i += nt) {
+                double sp[4] = {c_r[4 * i], c_r[4 * i + 1], c_r[4 * i + 2], c_r[4 * i + 3]};
+                st[i] = build_geometry_host(b->ctx[i], sphere_fn, sp);
+            }
+        });
+    for (std::thread &th : pool) th.join();
+    for (int i = 0; i < n; i++) {
+        if (st[i] != EBV_OK) return b->fail(st[i], "instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+        // hierarchies and launch-shape tuning, one instance at a time
+        ebv_status s2 = setup_geometry_solvers(b->ctx[i]);
+        if (s2 == EBV_OK && cudaStreamSynchronize(b->ctx[i]->stream) != cudaSuccess) s2 = EBV_ERR_CUDA;
+        if (s2 != EBV_OK) return b->fail(s2, "instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+    }
+    return EBV_OK;
+}
+
+ebv_ctx *ebv_batch_instance(ebv_batch *b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->ctx.size()) return nullptr;
+    return b->ctx[i];
+}
+
+ebv_status ebv_batch_advance(ebv_batch *b, double *const *u, double *const *p, int steps, ebv_step_stats *stats)
+{
+    if (!b || !u || !p || steps < 0) return EBV_ERR_INVALID;
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; i++) {
+        if (!u[i] || !p[i]) return b->fail(EBV_ERR_INVALID, "null field pointer");
+        if (!b->ctx[i]->have_geom) return b->fail(EBV_ERR_GEOMETRY, "instance " + std::to_string(i) + ": no geometry");
+    }
+    bool same = b->exec && (int)b->key.size() == 2 * n;
+    for (int i = 0; same && i < n; i++) same = b->key[2 * i] == u[i] && b->key[2 * i + 1] == p[i];
+    if (!same) TRY(capture_batch(b, u, p));
+    for (ebv_ctx *c : b->ctx)
+        if (graph_reset(c, b->stream) != EBV_OK) return b->fail(EBV_ERR_CUDA, c->err);
+    for (int s = 0; s < steps; s++)
+        if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return b->fail(EBV_ERR_CUDA, "batch graph launch");
+    for (ebv_ctx *c : b->ctx)
+        if (graph_readback(c, b->stream) != EBV_OK) return b->fail(EBV_ERR_CUDA, c->err);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return b->fail(EBV_ERR_CUDA, "batch synchronise");
+    ebv_status first = EBV_OK;
+    for (int i = 0; i < n; i++) {
+        Ctx *c = b->ctx[i];
+        c->launches += graph_launches(c, steps);
+        ebv_status e = step_error(c);
+        if (e != EBV_OK && first == EBV_OK) {
+            first = e;
+            b->err = "instance " + std::to_string(i) + ": " + c->err;
+        }
+    }
+    if (first != EBV_OK) return first;
+    if (stats)
+        for (int i = 0; i < n; i++)
+            if (graph_stats(b->ctx[i], u[i], p[i], stats + i) != EBV_OK)
+                return b->fail(EBV_ERR_CUDA, "instance " + std::to_string(i) + ": " + b->ctx[i]->err);
+    return EBV_OK;
+}
+
+long long ebv_batch_launch_count(const ebv_batch *b)
+{
+    long long n = 0;
+    if (b)
+        for (const ebv_ctx *c : b->ctx) n += c->launches;
+    return n;
+}
+
+const char *ebv_batch_last_error(const ebv_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+void ebv_batch_destroy(ebv_batch *b)
+{
+    if (!b) return;
+    drop_batch_graph(b);
+    for (ebv_ctx *c : b->ctx) ebv_destroy(c);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    delete b;
 }
 
 }  // extern "C"

@@ -56,7 +56,9 @@ EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geom
            "ebv_face_states", "ebv_solve_mac", "ebv_solve_viscous", "ebv_solve_projection",
            "ebv_timestep", "ebv_advance", "ebv_advance_graph", "ebv_advance_host", "ebv_drag", "ebv_launch_count",
            "ebv_profile_begin", "ebv_profile_end", "ebv_profile_entry", "ebv_last_error",
-           "ebv_destroy", "ebv_drag_noalloc"]
+           "ebv_destroy", "ebv_drag_noalloc", "ebv_batch_create", "ebv_batch_build_spheres",
+           "ebv_batch_instance", "ebv_batch_advance", "ebv_batch_launch_count",
+           "ebv_batch_last_error", "ebv_batch_destroy"]
 
 _lib = None
 
@@ -97,6 +99,15 @@ def load(path: str = LIB_PATH):
         "ebv_destroy": ([vp], None),
         "ebv_drag_noalloc": ([C.POINTER(_Grid), C.POINTER(_Params)] + [vp] * 6 + [C.c_int]
                              + [vp] * 4, C.c_int),
+        "ebv_batch_create": ([C.c_int, C.POINTER(_Grid), C.POINTER(_Params), vp, C.POINTER(vp)],
+                             C.c_int),
+        "ebv_batch_build_spheres": ([vp, dp], C.c_int),
+        "ebv_batch_instance": ([vp, C.c_int], vp),
+        "ebv_batch_advance": ([vp, C.POINTER(vp), C.POINTER(vp), C.c_int, C.POINTER(_Stats)],
+                              C.c_int),
+        "ebv_batch_launch_count": ([vp], C.c_longlong),
+        "ebv_batch_last_error": ([vp], C.c_char_p),
+        "ebv_batch_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -205,7 +216,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "_ctx", None):
-            self._lib.ebv_destroy(self._ctx)
+            if getattr(self, "_owned", True):
+                self._lib.ebv_destroy(self._ctx)
             self._ctx = None
 
     def __del__(self):
@@ -357,3 +369,88 @@ class Solver:
             out[name.value.decode()] = {"launches": int(L.value), "ms": float(ms.value),
                                         "bytes": float(by.value)}
         return out
+
+
+class Batch:
+    """Independent sphere-channel instances (each its own grid, rheology and
+    sphere) advanced together: every step of all of them is one launch of a
+    graph with one branch per instance (ebv_batch_*)."""
+
+    def __init__(self, workloads, precision=FP32_REFINE, tol=1e-8, max_iters=2000, stream=None):
+        import torch
+        self._lib = load()
+        self.workloads = list(workloads)
+        n = len(self.workloads)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        # per instance: a Solver-shaped description (no context of its own)
+        self._views = []
+        grids = (_Grid * n)()
+        params = (_Params * n)()
+        for q, w in enumerate(self.workloads):
+            v = Solver.__new__(Solver)
+            v._lib, v.n, v.h, v.stream, v._fn_keep, v._owned = self._lib, (w.n,) * 3, w.h, stream, None, False
+            v.params = dict(rho=w.rho, mu=w.mu, tau0=w.tau0, m=w.m, n_flow=w.n_flow, eta0=1e3,
+                            model=w.model, cfl=w.cfl, bi_cfl=w.bingham, tol=tol, max_iters=max_iters,
+                            delta_min=0.25, precision=precision)
+            g = _Grid()
+            g.n[:] = [w.n] * 3
+            g.lo[:] = [0.0, 0.0, 0.0]
+            g.h = w.h
+            g.bc[:] = [int(b) for b in w.bc]
+            g.u_in[:] = [float(x) for x in w.u_in]
+            v._grid = g
+            grids[q] = g
+            params[q] = v._params_c()
+            self._views.append(v)
+        b = C.c_void_p()
+        st = self._lib.ebv_batch_create(n, grids, params, C.c_void_p(stream.cuda_stream), C.byref(b))
+        if st != 0:
+            raise EbvError(st, "ebv_batch_create failed")
+        self._b = b
+        for q, v in enumerate(self._views):
+            v._ctx = C.c_void_p(self._lib.ebv_batch_instance(b, q))
+
+    def __len__(self):
+        return len(self._views)
+
+    def _ok(self, st):
+        if st != 0:
+            raise EbvError(st, self._lib.ebv_batch_last_error(self._b).decode())
+
+    def build_spheres(self):
+        """Each instance's sphere (centre, radius of its workload)."""
+        c_r = np.array([list(w.centre) + [w.radius] for w in self.workloads], dtype=np.float64)
+        self._ok(self._lib.ebv_batch_build_spheres(self._b, c_r.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def instance(self, q) -> Solver:
+        """Instance q as a Solver (the batch owns its context)."""
+        return self._views[q]
+
+    def advance(self, us, ps, steps=1, stats=True):
+        n = len(self._views)
+        for q, v in enumerate(self._views):
+            _check_f64(us[q], 3 * v.ncell, f"u[{q}]")
+            _check_f64(ps[q], v.nnode, f"p[{q}]")
+        U = (C.c_void_p * n)(*[_ptr(t) for t in us])
+        P = (C.c_void_p * n)(*[_ptr(t) for t in ps])
+        st = (_Stats * n)()
+        self._ok(self._lib.ebv_batch_advance(self._b, U, P, C.c_int(steps), st if stats else None))
+        return [_stats_dict(x) for x in st] if stats else None
+
+    def launch_count(self):
+        return int(self._lib.ebv_batch_launch_count(self._b))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            for v in self._views:
+                v._ctx = None
+            self._lib.ebv_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
