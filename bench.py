@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="issue every step kernel by kernel (no step graph), e.g. under a profiler")
     return ap.parse_args()
 
 
@@ -243,7 +245,7 @@ def run_ours(args, rank, world, local):
     u, p = initial_state(s, w, dev)
     clocks = Clocks(local)
     clocks.start()
-    sec, launches, _ = time_steps(s, u, p, args.steps, args.warmup, world, graph=True)
+    sec, launches, _ = time_steps(s, u, p, args.steps, args.warmup, world, graph=not args.eager)
     ck = clocks.stop()
     sec = max_over_ranks(sec, world)
     st = s.advance(u.clone(), p.clone(), stats=True)
@@ -266,7 +268,8 @@ def run_ours(args, rank, world, local):
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (each cell field 134 MB at 256^3)"},
            "roofline": roof, "kernels": kernels,
-           "step_launch": "one CUDA graph launch per step (solver loops as conditional nodes)",
+           "step_launch": ("kernel by kernel" if args.eager else
+                           "one CUDA graph launch per step (solver loops as conditional nodes)"),
            "eager": {"value": round(cells * args.steps * world / sec_e / 1e6, 3), "unit": UNIT,
                      "ms_per_step": round(1e3 * sec_e / args.steps, 3),
                      "note": "kernel-by-kernel issue with per-launch CUDA events; roofline and "
