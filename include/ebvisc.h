@@ -81,6 +81,9 @@ typedef struct {
     int max_iters;    /* Krylov iterations per solve */
     double delta_min; /* lower bound (cell units) of the wall distance in the implicit EB flux */
     int precision;    /* EBV_FP64 or EBV_FP32_REFINE */
+    int advect;       /* 1: Algorithm 1 as printed; 0: creeping flow, the convective term C = 0
+                         (the paper's evaluation runs at Re = 1e-3, Sec. "Cylinder moving through
+                         Bingham fluid"); the adjoint (ebv_adjoint_step) needs 0 */
 } ebv_params;
 
 typedef struct {

@@ -47,7 +47,8 @@ class _Params(C.Structure):
     _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("tau0", C.c_double),
                 ("m", C.c_double), ("n_flow", C.c_double), ("eta0", C.c_double),
                 ("model", C.c_int), ("cfl", C.c_double), ("bi_cfl", C.c_double),
-                ("tol", C.c_double), ("max_iters", C.c_int), ("delta_min", C.c_double)]
+                ("tol", C.c_double), ("max_iters", C.c_int), ("delta_min", C.c_double),
+                ("advect", C.c_int)]
 
 
 class _Shape(C.Structure):
@@ -144,6 +145,7 @@ class Params:
     tol: float = 1e-13
     max_iters: int = 200000
     delta_min: float = 0.25
+    advect: int = 1
 
     def c(self):
         p = _Params()
@@ -152,6 +154,7 @@ class Params:
             setattr(p, k, float(getattr(self, k)))
         p.model = int(self.model)
         p.max_iters = int(self.max_iters)
+        p.advect = int(self.advect)
         return p
 
 

@@ -1158,10 +1158,16 @@ void og_derived(const og_grid *g, const og_geom *geo, const og_params *p, const 
     size_t nft = nface(g, 0) + nface(g, 1) + nface(g, 2);
     double *uf = malloc(nft * sizeof(double)), *phi = malloc(N3 * sizeof(double));
     double res = 0.0;
-    og_face_states(g, geo, u, uf);
-    int it = og_mac_project(g, geo, uf, phi, p->tol, p->max_iters, &res);
-    if (st) { st->iters[0] = it; st->res[0] = res; }
-    og_convective(g, geo, u, uf, C);
+    if (p->advect) {
+        og_face_states(g, geo, u, uf);
+        int it = og_mac_project(g, geo, uf, phi, p->tol, p->max_iters, &res);
+        if (st) { st->iters[0] = it; st->res[0] = res; }
+        og_convective(g, geo, u, uf, C);
+    } else {
+        /* creeping flow (the paper's evaluation, Re = 1e-3): no convective term */
+        for (size_t s = 0; s < 3 * N3; s++) C[s] = 0.0;
+        if (st) { st->iters[0] = 0; st->res[0] = 0.0; }
+    }
     og_strain_eta(g, geo, p, u, eta, srate);
     og_viscous_explicit(g, geo, p, u, eta, V);
     free(uf);

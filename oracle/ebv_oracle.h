@@ -42,6 +42,7 @@ typedef struct {
     double tol;         /* relative residual for every linear solve */
     int max_iters;
     double delta_min;   /* lower bound of wall distance (cell units) in the implicit EB term */
+    int advect;         /* 1: Algorithm 1 as printed; 0: creeping flow, convective term C = 0 */
 } og_params;
 
 typedef struct {

@@ -26,6 +26,7 @@ ebv_status check_params(const ebv_params *p, std::string &why)
     if (!(p->cfl > 0.0)) { why = "cfl must be > 0"; return EBV_ERR_INVALID; }
     if (!(p->delta_min > 0.0)) { why = "delta_min must be > 0"; return EBV_ERR_INVALID; }
     if (p->precision != EBV_FP64 && p->precision != EBV_FP32_REFINE) { why = "unknown precision"; return EBV_ERR_INVALID; }
+    if (p->advect != 0 && p->advect != 1) { why = "advect must be 0 or 1"; return EBV_ERR_INVALID; }
     return EBV_OK;
 }
 
@@ -83,12 +84,19 @@ ebv_status set_dt(Ctx *c, double dt)
 // Algorithm 2 for velocity u: C, eta, V (and the projected face velocities in c->uf).
 ebv_status derived(Ctx *c, const double *u, double *C, double *eta, double *V, int *it, double *res, int slot)
 {
-    TRY(launch_face_states(c, u, c->uf));
-    TRY(launch_mac_rhs(c, c->uf, c->rhs_c));
-    c->cur_slot = slot;
-    TRY(mac_solve(c, c->rhs_c, c->phi, it, res));
-    TRY(launch_mac_correct(c, c->uf, c->phi));
-    TRY(launch_convective(c, u, c->uf, C));
+    if (c->prm.advect) {
+        TRY(launch_face_states(c, u, c->uf));
+        TRY(launch_mac_rhs(c, c->uf, c->rhs_c));
+        c->cur_slot = slot;
+        TRY(mac_solve(c, c->rhs_c, c->phi, it, res));
+        TRY(launch_mac_correct(c, c->uf, c->phi));
+        TRY(launch_convective(c, u, c->uf, C));
+    } else {
+        // creeping flow: no convective term, no face velocities to project
+        EBV_CUDA_TRY(c, cudaMemsetAsync(C, 0, 3 * (size_t)ncell(c->g) * sizeof(double), c->stream));
+        if (it) *it = 0;
+        if (res) *res = 0.0;
+    }
     TRY(launch_strain_eta(c, u, eta, nullptr, c->G));
     TRY(launch_viscous_explicit(c, u, eta, c->G, V));
     return EBV_OK;

@@ -41,7 +41,7 @@ class _Params(C.Structure):
                 ("m", C.c_double), ("n_flow", C.c_double), ("eta0", C.c_double),
                 ("model", C.c_int), ("cfl", C.c_double), ("bi_cfl", C.c_double),
                 ("tol", C.c_double), ("max_iters", C.c_int), ("delta_min", C.c_double),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("advect", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -168,7 +168,7 @@ class Solver:
     def __init__(self, n, h, lo=(0.0, 0.0, 0.0), bc=W.CHANNEL_BC, u_in=(0.0, 0.0, 1.0), *,
                  rho=1.0, mu=1.0, tau0=0.0, m=1e3, n_flow=1.0, eta0=1e3, model=BINGHAM,
                  cfl=0.5, bi_cfl=0.0, tol=1e-8, max_iters=1000, delta_min=0.25,
-                 precision=FP64, stream=None):
+                 precision=FP64, advect=1, stream=None):
         import torch
         self._lib = load()
         self.n = tuple(int(v) for v in n)
@@ -182,7 +182,7 @@ class Solver:
         self._grid = g
         self.params = dict(rho=rho, mu=mu, tau0=tau0, m=m, n_flow=n_flow, eta0=eta0, model=model,
                            cfl=cfl, bi_cfl=bi_cfl, tol=tol, max_iters=max_iters,
-                           delta_min=delta_min, precision=precision)
+                           delta_min=delta_min, precision=precision, advect=advect)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -206,7 +206,7 @@ class Solver:
     def _params_c(self):
         p = _Params()
         for k, v in self.params.items():
-            setattr(p, k, int(v) if k in ("model", "max_iters", "precision") else float(v))
+            setattr(p, k, int(v) if k in ("model", "max_iters", "precision", "advect") else float(v))
         return p
 
     def _ok(self, st):
@@ -393,7 +393,7 @@ class Batch:
             v._lib, v.n, v.h, v.stream, v._fn_keep, v._owned = self._lib, (w.n,) * 3, w.h, stream, None, False
             v.params = dict(rho=w.rho, mu=w.mu, tau0=w.tau0, m=w.m, n_flow=w.n_flow, eta0=1e3,
                             model=w.model, cfl=w.cfl, bi_cfl=w.bingham, tol=tol, max_iters=max_iters,
-                            delta_min=0.25, precision=precision)
+                            delta_min=0.25, precision=precision, advect=1)
             g = _Grid()
             g.n[:] = [w.n] * 3
             g.lo[:] = [0.0, 0.0, 0.0]

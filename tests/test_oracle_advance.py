@@ -81,3 +81,28 @@ def test_timestep_limits(O):
     forced = O.Params(mu=0.0, cfl=0.5)
     assert O.timestep(g, geo, forced, 0 * u.ravel(), f.ravel()) == pytest.approx(
         0.5 / np.sqrt(4.0 / g.h), rel=1e-14)
+
+
+def test_creeping_newtonian_step_is_affine(O):
+    """With C = 0 (creeping flow) and a Newtonian fluid the step at fixed dt
+    is affine in (u, p, f): S(a x + (1 - a) y) = a S(x) + (1 - a) S(y).  The
+    full step (advect = 1) is not (the convective term is quadratic): this
+    pins that the switch removes exactly that term and nothing else."""
+    n = 8
+    g = O.Grid(n=(n, n, n), h=1.0 / n)
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_SPHERE, p=(0.5, 0.5, 0.5, 0.2)))
+    rng = np.random.default_rng(3)
+    fluid = np.tile(geo.alpha > 0, 3)
+    xs = [((rng.normal(size=3 * g.ncell) + 0.3) * fluid, rng.normal(size=g.nnode),
+           rng.normal(size=3 * g.ncell) * fluid) for _ in range(2)]
+    a = 0.3
+    mix = tuple(a * p + (1 - a) * q for p, q in zip(*xs))
+    gaps = {}
+    for advect in (0, 1):
+        P = O.Params(model=O.NEWTONIAN, tau0=0.0, tol=1e-14, advect=advect)
+        out = [O.advance(g, geo, P, u, p, dt=1e-3, f=f)[:2] for (u, p, f) in xs + [mix]]
+        du = out[2][0] - (a * out[0][0] + (1 - a) * out[1][0])
+        dp = out[2][1] - (a * out[0][1] + (1 - a) * out[1][1])
+        gaps[advect] = max(np.abs(du).max() / np.abs(out[2][0]).max(), np.abs(dp).max() / np.abs(out[2][1]).max())
+    assert gaps[0] < 1e-11
+    assert gaps[1] > 1e-6
