@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="issue every step kernel by kernel (no step graph), e.g. under a profiler")
     return ap.parse_args()
@@ -323,6 +324,58 @@ def run_ours(args, rank, world, local):
 
     if not args.skip_batch:
         out["batch_sweep"] = run_batch(dev, world)
+    if not args.skip_adjoint:
+        out["adjoint"] = run_adjoint(dev)
+    return out
+
+
+def run_adjoint(dev, n=128, steps=40, every=8):
+    """Drag sensitivities of the creeping-flow step: 128^3 sphere channel
+    (r = 0.125, Bi = 5, m = 1e3), a seeded Gaussian body force (sigma 0.1),
+    40 steps at the initial CFL step, checkpoints every 8 steps; gradient with
+    respect to tau0, mu and f by the adjoint, dJ/dtau0 also by central
+    differences (forward solves to 1e-13)."""
+    import torch
+    from paper_1905_07392_gb300 import ebvisc
+    from paper_1905_07392_gb300 import workloads as W
+    w = W.Workload("adjoint_128", n=n, radius=0.125, tau0=W.tau0_for_bingham(5.0, 0.125), m=1e3, seed=3)
+    out = {}
+    for prec, name in ((ebvisc.FP32_REFINE, "fp32_refine"), (ebvisc.FP64, "fp64")):
+        s = ebvisc.Solver.from_workload(w, precision=prec, tol=1e-13, max_iters=20000, advect=0)
+        fluid = (s.geometry()["alpha"] > 0).to(torch.float64)
+        u0 = (torch.tensor(W.initial_velocity(w).reshape(3, -1), device=dev) * fluid).reshape(-1).contiguous()
+        p0 = torch.zeros(s.nnode, dtype=torch.float64, device=dev)
+        f = (torch.tensor(W.body_force(w).reshape(3, -1), device=dev) * fluid).reshape(-1).contiguous()
+        dt = s.timestep(u0, f)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, gt, gm, fb = s.drag_gradient(u0, p0, dt, steps, every, f=f)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        entry = {"J": J, "dJ_dtau0": gt, "dJ_dmu": gm, "dJ_df_l2": float(torch.linalg.vector_norm(fb)),
+                 "seconds": round(t_adj, 3)}
+        if prec == ebvisc.FP32_REFINE:
+            def J_of(t):
+                s.set_params(tau0=t)
+                u, p = u0.clone(), p0.clone()
+                acc = 0.0
+                for _ in range(steps):
+                    acc += s.advance(u, p, dt=dt, f=f, stats=True)["drag"]
+                return acc / steps
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            J0 = J_of(w.tau0)
+            t_fwd = time.perf_counter() - t0
+            h = 1e-6 * w.tau0
+            fd = (J_of(w.tau0 + h) - J_of(w.tau0 - h)) / (2 * h)
+            s.set_params(tau0=w.tau0)
+            entry.update({"fd_dJ_dtau0": fd, "rel_err_tau0": abs(gt - fd) / abs(fd),
+                          "forward_seconds": round(t_fwd, 3),
+                          "adjoint_over_forward": round(t_adj / t_fwd, 2), "J_forward": J0})
+        out[name] = entry
+        s.close()
+    out.update({"workload": f"sphere_channel_{n}^3_bi5_m1e3_creeping", "steps": steps, "checkpoint_every": every,
+                "dt": dt, "tol": 1e-13})
     return out
 
 

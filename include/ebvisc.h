@@ -221,6 +221,44 @@ ebv_status ebv_profile_entry(ebv_ctx *ctx, int i, const char **name, long long *
 const char *ebv_last_error(const ebv_ctx *ctx);
 void ebv_destroy(ebv_ctx *ctx);
 
+/* ---- Adjoint (drag sensitivities) ----------------------------------------
+ * Reverse mode of the creeping-flow step (advect = 0; the paper's evaluation
+ * runs at Re = 1e-3, Sec. "Cylinder moving through Bingham fluid") at a fixed
+ * dt, for the sensitivities of the drag of Eq. drag-force to the yield stress
+ * tau0, the plastic viscosity mu and a per-cell body force f: hand-written
+ * adjoints of the strain-rate/viscosity update, the explicit viscous term
+ * (face fluxes, EB wall flux of Eq. dudn, redistribution), the eta-dependence
+ * of the semi-implicit viscous operator, the nodal projection and the drag;
+ * the adjoint solves reuse the (symmetric) viscous and nodal multigrid-CG
+ * solves in the context's precision.  Rheologies: Newtonian, Bingham,
+ * Herschel-Bulkley, power law.  dt, which Eq. cfl:dt ties to u and f, is a
+ * fixed input (its own sensitivity is not propagated).  The first adjoint
+ * call allocates the context's adjoint workspace (about 90 doubles per
+ * cell); forward steps never allocate.  EBV_ERR_INVALID if advect != 0, dt
+ * <= 0 or the rheology has no adjoint.
+ *
+ * One step: given the state (u, p) at the step's start (device, unchanged),
+ * dt and f (3 x cells or NULL), and in u_bar, p_bar the adjoints of the
+ * step's outputs, overwrites u_bar, p_bar with the adjoints of its inputs,
+ * adds the adjoint of f to f_bar (3 x cells, device, or NULL) and adds
+ * dJ/dtau0, dJ/dmu of this step to grads[0], grads[1] (host). */
+ebv_status ebv_adjoint_step(ebv_ctx *ctx, const double *u, const double *p, double dt, const double *f,
+                            double *u_bar, double *p_bar, double *f_bar, double *grads);
+/* Adds w times the gradient of the drag F_z(u, p) (eta from u) to u_bar,
+ * p_bar (device) and its tau0, mu parts to grads[0..1] (host). */
+ebv_status ebv_drag_adjoint(ebv_ctx *ctx, const double *u, const double *p, double w, double *u_bar,
+                            double *p_bar, double *grads);
+/* Doubles of device workspace ebv_drag_gradient needs for (steps, every). */
+ebv_status ebv_drag_gradient_workspace(const ebv_ctx *ctx, int steps, int every, long long *ndoubles);
+/* J = (1/steps) sum_{s=1..steps} F_z(u_s, p_s) over `steps` creeping-flow
+ * steps from (u0, p0) (device, unchanged) at fixed dt with body force f
+ * (3 x cells or NULL), and its gradient: grads[0] = dJ/dtau0, grads[1] =
+ * dJ/dmu (host), f_bar = dJ/df (3 x cells, device, or NULL).  Stores (u, p)
+ * every `every` steps in `work` (device, ebv_drag_gradient_workspace doubles)
+ * and recomputes each segment's states before reversing it. */
+ebv_status ebv_drag_gradient(ebv_ctx *ctx, const double *u0, const double *p0, const double *f, double dt,
+                             int steps, int every, double *work, double *J, double *grads, double *f_bar);
+
 /* ---- Batches ------------------------------------------------------------
  * A parameter sweep of independent problems (the paper computes drag
  * coefficients over a range of Bingham numbers, Sec. "Evaluation", flows past

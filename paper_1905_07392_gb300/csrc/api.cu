@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <new>
 #include <thread>
+#include <utility>
+#include <vector>
 
 #include "ebv_internal.cuh"
 
@@ -671,12 +673,308 @@ void ebv_destroy(ebv_ctx *c)
     drop_step_graph(c);
     cudaFree(c->ctl);
     cudaFree(c->sstat);
+    if (c->adj) cudaFree(c->adj);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
     if (c->sstat_host) cudaFreeHost(c->sstat_host);
     for (cudaStream_t s : c->cap_stream)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
     delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the creeping-flow step (advect = 0, fixed dt) and of the drag,
+// for drag sensitivities with respect to tau0, mu and a body-force field.
+// The forward step is recomputed from its start state, keeping what the
+// reverse pass reads; the reverse pass runs the adjoint kernels of
+// adjoint.cu and the transposed solves (the viscous and nodal operators are
+// symmetric, so their adjoint solves are the same multigrid-CG solves).
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct AdjBufs {
+    double *em, *es, *eb, *Gm, *Gs, *Vm, *Vs, *Va, *psi, *utm, *uts, *us, *zero3, *t3;
+    double *ebm, *ebs, *ebb, *Gb, *Vbs, *Vbm, *psib, *usb, *utb, *lam, *DCb, *tb, *etad;
+    double *ffb, *dudnb, *ps, *psb, *nb1, *nb2, *ua, *pa, *grads;
+};
+
+// Carves the adjoint workspace into B (allocated on first use, once per
+// context; the forward step itself never allocates).
+ebv_status adj_buffers(Ctx *c, AdjBufs &B)
+{
+    const size_t N3 = ncell(c->g), NN = nnode(c->g), NF = nface(c->g, 0) + nface(c->g, 1) + nface(c->g, 2);
+    const size_t NC = (size_t)c->ncut + 1;
+    // offsets first, pointers once the block exists
+    size_t off = 0;
+    std::vector<std::pair<double **, size_t>> parts;
+    auto take = [&](double **dst, size_t n) { parts.push_back({dst, off}); off += n; };
+    for (double **d : {&B.em, &B.es, &B.eb, &B.ebm, &B.ebs, &B.ebb, &B.lam, &B.etad}) take(d, N3);
+    for (double **d : {&B.Gm, &B.Gs, &B.Gb}) take(d, 9 * N3);
+    for (double **d : {&B.Vm, &B.Vs, &B.Va, &B.psi, &B.utm, &B.uts, &B.us, &B.zero3, &B.t3, &B.Vbs, &B.Vbm, &B.psib,
+                       &B.usb, &B.utb, &B.DCb, &B.tb, &B.ua})
+        take(d, 3 * N3);
+    take(&B.ffb, 3 * NF);
+    take(&B.dudnb, 3 * NC);
+    for (double **d : {&B.ps, &B.psb, &B.nb1, &B.nb2, &B.pa}) take(d, NN);
+    take(&B.grads, 8);
+    auto layout = [&](double *base) {
+        for (auto &pr : parts) *pr.first = base + pr.second;
+    };
+    const size_t need = off;
+    if (c->adj_len < need) {
+        if (c->adj) cudaFree(c->adj);
+        c->adj = nullptr;
+        c->adj_len = 0;
+        EBV_CUDA_TRY(c, cudaMalloc(&c->adj, need * sizeof(double)));
+        c->adj_len = need;
+    }
+    layout(c->adj);
+    return EBV_OK;
+}
+
+ebv_status adj_check(Ctx *c, double dt)
+{
+    if (c->prm.advect != 0)
+        return c->fail(EBV_ERR_INVALID, "the adjoint covers the creeping-flow step: set advect = 0");
+    if (c->prm.model != EBV_NEWTONIAN && c->prm.model != EBV_BINGHAM && c->prm.model != EBV_HERSCHEL_BULKLEY &&
+        c->prm.model != EBV_POWER_LAW)
+        return c->fail(EBV_ERR_INVALID, "no adjoint for this rheology");
+    if (!(dt > 0.0)) return c->fail(EBV_ERR_INVALID, "the adjoint needs a fixed dt > 0");
+    return EBV_OK;
+}
+
+// Adjoint of the nodal projection (ut, p_old) -> (u, p): given the adjoints
+// (ubo, pbo) of its outputs, utb = adjoint of ut; pold_b += adjoint of p_old.
+//   u1 = mask(ut + c G p_old); p = L^-1 (D u1 + bc) / c; u = mask(u1 - c G p)
+ebv_status proj_adjoint(Ctx *c, AdjBufs &B, double dt, const double *ubo, const double *pbo, double *utb,
+                        double *pold_b)
+{
+    const size_t NN = nnode(c->g);
+    const double cc = dt / c->prm.rho;
+    TRY(adj_mask_scale(c, 3, ubo, 1.0, B.t3));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(B.nb1, pbo, NN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    TRY(adj_gradp_t(c, B.t3, -cc, B.nb1, 1));
+    TRY(adj_zero_inactive_nodes(c, B.nb1));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.nb2, 0, NN * sizeof(double), c->stream));
+    int it = 0;
+    double res = 0.0;
+    TRY(nodal_solve(c, B.nb1, B.nb2, &it, &res));
+    TRY(adj_nodal_rhs_t(c, B.nb2, B.t3));
+    TRY(adj_mask_scale(c, 3, B.t3, 1.0, utb));
+    TRY(adj_gradp_t(c, utb, cc, pold_b, 1));
+    return EBV_OK;
+}
+
+// Adjoint of the three viscous solves A_q(eta) x_q = alpha psi_q + b_q(eta):
+// psib = adjoint of psi, etab += adjoint of eta, from xb = adjoint of x.
+ebv_status visc_adjoint(Ctx *c, AdjBufs &B, const double *eta, const double *x, const double *xb, double *psib,
+                        double *etab)
+{
+    const size_t N3 = ncell(c->g);
+    for (int q = 0; q < 3; q++) {
+        int it = 0;
+        double res = 0.0;
+        TRY(visc_solve_rhs(c, eta, q, xb + q * N3, B.lam, &it, &res));
+        TRY(adj_alpha_times(c, B.lam, psib + q * N3));
+        TRY(adj_visc_eta(c, q, B.lam, x + q * N3, etab));
+    }
+    return EBV_OK;
+}
+
+// One step's reverse pass.  In: state (u, p) at the step's start, dt, f; ub,
+// pb the adjoints of the step's outputs.  Out: ub, pb the adjoints of u, p;
+// fb += adjoint of f (if fb); grads_dev[0..1] += d/dtau0, d/dmu.
+ebv_status adjoint_step_impl(Ctx *c, const double *u, const double *p, double dt, const double *f, double *ub,
+                             double *pb, double *fb, AdjBufs &B)
+{
+    const size_t N3 = ncell(c->g), NN = nnode(c->g);
+    cudaStream_t s = c->stream;
+    TRY(set_dt(c, dt));
+    // ---- forward, keeping the intermediates (as advance_impl with C = 0)
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.zero3, 0, 3 * N3 * sizeof(double), s));
+    TRY(launch_strain_eta(c, u, B.em, nullptr, B.Gm));
+    TRY(launch_viscous_explicit(c, u, B.em, B.Gm, B.Vm));
+    TRY(launch_psi(c, u, B.zero3, B.Vm, p, f, B.psi));
+    TRY(viscous_update(c, B.em, B.psi, B.utm, nullptr, 1));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(B.us, B.utm, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(B.ps, p, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(nodal_projection(c, B.us, B.ps, nullptr, 4));      // u*, p*
+    TRY(launch_strain_eta(c, B.us, B.es, nullptr, B.Gs));
+    TRY(launch_viscous_explicit(c, B.us, B.es, B.Gs, B.Vs));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(B.eb, B.em, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(launch_average(c, B.eb, B.es, (int)N3));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(B.Va, B.Vm, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(launch_average(c, B.Va, B.Vs, (int)(3 * N3)));
+    TRY(launch_psi(c, u, B.zero3, B.Va, B.ps, f, B.psi));
+    TRY(viscous_update(c, B.eb, B.psi, B.uts, nullptr, 6));
+    // ---- reverse
+    // corrector projection: (ub, pb) -> utb (adjoint of the corrector's ut), psb (of p*)
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.psb, 0, NN * sizeof(double), s));
+    TRY(proj_adjoint(c, B, dt, ub, pb, B.utb, B.psb));
+    // from here ub, pb accumulate the adjoints of the step's inputs u, p
+    EBV_CUDA_TRY(c, cudaMemsetAsync(ub, 0, 3 * N3 * sizeof(double), s));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(pb, 0, NN * sizeof(double), s));
+    // corrector viscous solves with eta_avg
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.ebb, 0, N3 * sizeof(double), s));
+    TRY(visc_adjoint(c, B, B.eb, B.uts, B.utb, B.psib, B.ebb));
+    // corrector psi = rho u + dt (V_avg - grad p* + f), V_avg = (V_m + V_s) / 2:
+    // V_s bar = V_m bar = dt psi bar / 2
+    TRY(adj_psi(c, B.psib, dt, 0.5 * dt, ub, B.Vbs, 0, fb));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(B.Vbm, B.Vbs, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(adj_gradp_t(c, B.psib, -dt, B.psb, 1));   // psi is 0 on covered cells; k_gradp_t reads fluid cells
+    // eta_avg = (eta_m + eta_s) / 2
+    TRY(adj_mask_scale(c, 1, B.ebb, 0.5, B.ebs));
+    TRY(adj_mask_scale(c, 1, B.ebb, 0.5, B.ebm));
+    // corrector explicit viscous term and eta, G of u*
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.usb, 0, 3 * N3 * sizeof(double), s));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.Gb, 0, 9 * N3 * sizeof(double), s));
+    TRY(adj_viscous_explicit(c, B.us, B.es, B.Gs, B.Vbs, B.usb, B.ebs, B.Gb, B.ffb, B.DCb, B.tb, B.dudnb));
+    TRY(adj_strain_eta(c, B.us, B.ebs, B.Gb, B.usb, B.grads));
+    // predictor projection: (usb, psb) -> utb, pb += (adjoint of p via u1 = ut + c G p)
+    TRY(proj_adjoint(c, B, dt, B.usb, B.psb, B.utb, pb));
+    // predictor viscous solves with eta_m
+    TRY(visc_adjoint(c, B, B.em, B.utm, B.utb, B.psib, B.ebm));
+    // predictor psi = rho u + dt (V_m - grad p + f)
+    TRY(adj_psi(c, B.psib, dt, dt, ub, B.Vbm, 1, fb));
+    TRY(adj_gradp_t(c, B.psib, -dt, pb, 1));
+    // predictor explicit viscous term and eta, G of u
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.Gb, 0, 9 * N3 * sizeof(double), s));
+    TRY(adj_viscous_explicit(c, u, B.em, B.Gm, B.Vbm, ub, B.ebm, B.Gb, B.ffb, B.DCb, B.tb, B.dudnb));
+    TRY(adj_strain_eta(c, u, B.ebm, B.Gb, ub, B.grads));
+    return EBV_OK;
+}
+
+// Adjoint of w F_z(u, p) (Eq. drag-force, eta = eta(u)): ub, pb, grads += .
+// (F_z is linear in p, so p itself is not read.)
+ebv_status drag_adjoint_impl(Ctx *c, const double *u, double w, double *ub, double *pb, AdjBufs &B)
+{
+    const size_t N3 = ncell(c->g);
+    TRY(launch_strain_eta(c, u, B.etad, nullptr, nullptr));
+    TRY(launch_wall_dudn(c, u, c->dudn));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.ebb, 0, N3 * sizeof(double), c->stream));
+    if (c->ncut) {
+        EBV_CUDA_TRY(c, cudaMemsetAsync(B.dudnb, 0, 3 * (size_t)c->ncut * sizeof(double), c->stream));
+        TRY(adj_drag(c, B.etad, w, B.ebb, B.dudnb, pb));
+        TRY(adj_wall_dudn(c, B.dudnb, ub));
+    }
+    TRY(adj_strain_eta(c, u, B.ebb, nullptr, ub, B.grads));
+    return EBV_OK;
+}
+
+ebv_status read_grads(Ctx *c, AdjBufs &B, double *grads)
+{
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->scal_host + 20, B.grads, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (grads) {
+        grads[0] += c->scal_host[20];
+        grads[1] += c->scal_host[21];
+    }
+    return EBV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ebv_status ebv_adjoint_step(ebv_ctx *c, const double *u, const double *p, double dt, const double *f,
+                            double *u_bar, double *p_bar, double *f_bar, double *grads)
+{
+    if (!c || !u || !p || !u_bar || !p_bar) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(adj_check(c, dt));
+    AdjBufs B;
+    TRY(adj_buffers(c, B));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.grads, 0, 2 * sizeof(double), c->stream));
+    TRY(adjoint_step_impl(c, u, p, dt, f, u_bar, p_bar, f_bar, B));
+    TRY(read_grads(c, B, grads));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_drag_adjoint(ebv_ctx *c, const double *u, const double *p, double w, double *u_bar, double *p_bar,
+                            double *grads)
+{
+    if (!c || !u || !p || !u_bar || !p_bar) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    if (c->prm.model == EBV_SOUZA_MENDES_DUTRA) return c->fail(EBV_ERR_INVALID, "no adjoint for this rheology");
+    AdjBufs B;
+    TRY(adj_buffers(c, B));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.grads, 0, 2 * sizeof(double), c->stream));
+    TRY(drag_adjoint_impl(c, u, w, u_bar, p_bar, B));
+    TRY(read_grads(c, B, grads));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_drag_gradient_workspace(const ebv_ctx *c, int steps, int every, long long *ndoubles)
+{
+    if (!c || steps < 1 || every < 1 || !ndoubles) return EBV_ERR_INVALID;
+    const long long S = 3LL * ncell(c->g) + nnode(c->g);
+    const long long nck = (steps + every - 1) / every;
+    *ndoubles = S * (nck + std::min(every, steps) + 1);
+    return EBV_OK;
+}
+
+// J = (1/steps) sum_{s=1..steps} F_z(u_s, p_s) over `steps` creeping-flow
+// steps from (u0, p0) at fixed dt, and its gradient with respect to tau0, mu
+// and the body force f.  Checkpoints every `every` steps; each segment is
+// recomputed forward (its states kept) before its steps are reversed.
+ebv_status ebv_drag_gradient(ebv_ctx *c, const double *u0, const double *p0, const double *f, double dt, int steps,
+                             int every, double *work, double *J, double *grads, double *f_bar)
+{
+    if (!c || !u0 || !p0 || !work || !J || !grads || steps < 1 || every < 1) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(adj_check(c, dt));
+    const size_t N3 = ncell(c->g), NN = nnode(c->g), S = 3 * N3 + NN;
+    const int nck = (steps + every - 1) / every;
+    double *ck = work;                      // nck checkpoints (u, p)
+    double *st = work + (size_t)nck * S;    // the states of one segment
+    cudaStream_t s = c->stream;
+    // forward: checkpoints and the objective
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(st, u0, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(st + 3 * N3, p0, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double Jsum = 0.0;
+    for (int k = 0; k < steps; k++) {
+        if (k % every == 0)
+            EBV_CUDA_TRY(c, cudaMemcpyAsync(ck + (size_t)(k / every) * S, st, S * sizeof(double),
+                                            cudaMemcpyDeviceToDevice, s));
+        TRY(advance_impl(c, st, st + 3 * N3, dt, f, nullptr));
+        double fz = 0.0, yf = 0.0;
+        TRY(launch_drag(c, st, st + 3 * N3, &fz, &yf));
+        Jsum += fz;
+    }
+    *J = Jsum / steps;
+    // reverse: the adjoint state (ua, pa) starts at zero; each step adds its
+    // objective term, then is reversed
+    AdjBufs B;
+    TRY(adj_buffers(c, B));
+    double *ua = B.ua, *pa = B.pa;
+    EBV_CUDA_TRY(c, cudaMemsetAsync(ua, 0, 3 * N3 * sizeof(double), s));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(pa, 0, NN * sizeof(double), s));
+    EBV_CUDA_TRY(c, cudaMemsetAsync(B.grads, 0, 2 * sizeof(double), s));
+    if (f_bar) EBV_CUDA_TRY(c, cudaMemsetAsync(f_bar, 0, 3 * N3 * sizeof(double), s));
+    for (int q = nck - 1; q >= 0; q--) {
+        const int k0 = q * every, k1 = std::min(k0 + every, steps);
+        // states k0 .. k1 of this segment, recomputed from its checkpoint
+        EBV_CUDA_TRY(c, cudaMemcpyAsync(st, ck + (size_t)q * S, S * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int k = k0; k < k1; k++) {
+            double *a = st + (size_t)(k - k0) * S, *b = a + S;
+            EBV_CUDA_TRY(c, cudaMemcpyAsync(b, a, S * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            TRY(advance_impl(c, b, b + 3 * N3, dt, f, nullptr));
+        }
+        for (int k = k1 - 1; k >= k0; k--) {
+            double *a = st + (size_t)(k - k0) * S, *b = a + S;
+            TRY(drag_adjoint_impl(c, b, 1.0 / steps, ua, pa, B));
+            TRY(adjoint_step_impl(c, a, a + 3 * N3, dt, f, ua, pa, f_bar, B));
+        }
+    }
+    grads[0] = grads[1] = 0.0;
+    TRY(read_grads(c, B, grads));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -236,6 +236,9 @@ struct Ctx {
     struct LoopRec { int slot, per_outer, per_inner; };
     std::vector<LoopRec> loop_recs;   // launches per loop pass of each captured solve
     long long graph_top_launches = 0; // launches of the captured step outside loop bodies
+    // adjoint workspace (allocated by the first adjoint call)
+    double *adj = nullptr;
+    size_t adj_len = 0;
     // the captured step (one graph launch = one step)
     cudaGraphExec_t step_exec = nullptr;
     const void *gkey_u = nullptr, *gkey_p = nullptr, *gkey_f = nullptr;
@@ -306,6 +309,24 @@ ebv_status launch_timestep(Ctx *c, const double *u, const double *f, double dt_f
 ebv_status launch_average(Ctx *c, double *a, const double *b, int n);
 ebv_status launch_drag(Ctx *c, const double *u, const double *p, double *fz, double *yf);
 ebv_status launch_zero_covered(Ctx *c, double *u, int ncomp);
+ebv_status launch_wall_dudn(Ctx *c, const double *u, double *dudn);
+// adjoint.cu (reverse pieces of the creeping-flow step)
+ebv_status adj_strain_eta(Ctx *c, const double *u, const double *eta_bar, const double *G_bar, double *u_bar,
+                          double *grads_dev);
+ebv_status adj_wall_dudn(Ctx *c, const double *dudn_bar, double *u_bar);
+ebv_status adj_viscous_explicit(Ctx *c, const double *u, const double *eta, const double *G, const double *V_bar,
+                                double *u_bar, double *eta_bar, double *G_bar, double *Fb, double *DCb, double *tb,
+                                double *dudn_bar);
+ebv_status adj_visc_eta(Ctx *c, int comp, const double *lam, const double *x, double *eta_bar);
+ebv_status adj_gradp_t(Ctx *c, const double *w, double scale, double *out, int accumulate);
+ebv_status adj_nodal_rhs_t(Ctx *c, const double *rb, double *ub);
+ebv_status adj_drag(Ctx *c, const double *eta, double wJ, double *eta_bar, double *dudn_bar, double *p_bar);
+ebv_status adj_psi(Ctx *c, const double *psib, double dt, double vs, double *ub, double *Vb, int vb_acc,
+                   double *fb);
+ebv_status adj_mask_scale(Ctx *c, int ncomp, const double *b, double s, double *a);
+ebv_status adj_alpha_times(Ctx *c, const double *lam, double *a);
+ebv_status adj_axpby(Ctx *c, int n, double a, const double *x, double b, double *y);
+ebv_status adj_zero_inactive_nodes(Ctx *c, double *x);
 // solvers.cu
 ebv_status setup_solvers(Ctx *c);
 ebv_status setup_geometry_solvers(Ctx *c);
@@ -313,6 +334,10 @@ ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res
 ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int comp, double *x,
                       int *iters, double *res);
 ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *res);
+// A(eta) x = rhs for velocity component comp (the viscous operator with the
+// given right-hand side instead of alpha psi + boundary terms), from x = 0
+ebv_status visc_solve_rhs(Ctx *c, const double *eta, int comp, const double *rhs, double *x, int *iters,
+                          double *res);
 // reductions (solvers.cu)
 ebv_status reduce_sum(Ctx *c, const double *part, int nblocks, double *out_dev);
 

@@ -840,13 +840,20 @@ ebv_status launch_convective(Ctx *c, const double *u, const double *uf, double *
     return launch_redistribute_into(c, c->DC, -1.0, 1.0, C);
 }
 
+ebv_status launch_wall_dudn(Ctx *c, const double *u, double *dudn)
+{
+    if (c->ncut)
+        EBV_LAUNCH(c, k_wall_dudn, dim3((c->ncut + 127) / 128), dim3(128), 0, c->g, geomd(c), u, dudn);
+    return EBV_OK;
+}
+
 ebv_status launch_viscous_explicit(Ctx *c, const double *u, const double *eta, const double *G,
                                    double *V)
 {
     const GridD &g = c->g;
     GeomD geo = geomd(c);
-    if (c->ncut)
-        EBV_LAUNCH(c, k_wall_dudn, dim3((c->ncut + 127) / 128), dim3(128), 0, g, geo, u, c->dudn);
+    ebv_status s0 = launch_wall_dudn(c, u, c->dudn);
+    if (s0 != EBV_OK) return s0;
     const int nft = nface(g, 0) + nface(g, 1) + nface(g, 2);
     const double *A[3] = {c->ax, c->ay, c->az};
     int off = 0;

@@ -1763,6 +1763,25 @@ ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int com
     return solve(c, P, c->rhs_c, x, iters, res);
 }
 
+ebv_status visc_solve_rhs(Ctx *c, const double *eta, int comp, const double *rhs, double *x, int *iters,
+                          double *res)
+{
+    const GridD &g = c->g;
+    const int n = ncell(g);
+    CcLevel &V0 = c->visc.lv[0];
+    // coefficients of A(eta); the right-hand side it writes is replaced
+    EBV_LAUNCH(c, k_visc_coeffs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), paramsd(c->prm), eta,
+               c->dt_dev, comp, rhs, V0.extra_d, V0.bf_d[0], V0.bf_d[1], V0.bf_d[2], c->rhs_c);
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(c->rhs_c, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    const bool fp32 = c->prm.precision == EBV_FP32_REFINE;
+    ebv_status s = cc_finish_hierarchy(c, c->visc, fp32);
+    if (s != EBV_OK) return s;
+    EBV_LAUNCH(c, k_fill, dim3(vblocks(n)), dim3(256), 0, x, n, 0.0);
+    CcProblem P;
+    P.H = &c->visc;
+    return solve(c, P, c->rhs_c, x, iters, res);
+}
+
 ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *res)
 {
     const int nn = nnode(c->g);

@@ -58,7 +58,8 @@ EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geom
            "ebv_profile_begin", "ebv_profile_end", "ebv_profile_entry", "ebv_last_error",
            "ebv_destroy", "ebv_drag_noalloc", "ebv_batch_create", "ebv_batch_build_spheres",
            "ebv_batch_instance", "ebv_batch_advance", "ebv_batch_launch_count",
-           "ebv_batch_last_error", "ebv_batch_destroy"]
+           "ebv_batch_last_error", "ebv_batch_destroy", "ebv_adjoint_step", "ebv_drag_adjoint",
+           "ebv_drag_gradient_workspace", "ebv_drag_gradient"]
 
 _lib = None
 
@@ -108,6 +109,10 @@ def load(path: str = LIB_PATH):
         "ebv_batch_launch_count": ([vp], C.c_longlong),
         "ebv_batch_last_error": ([vp], C.c_char_p),
         "ebv_batch_destroy": ([vp], None),
+        "ebv_adjoint_step": ([vp, vp, vp, C.c_double, vp, vp, vp, vp, dp], C.c_int),
+        "ebv_drag_adjoint": ([vp, vp, vp, C.c_double, vp, vp, dp], C.c_int),
+        "ebv_drag_gradient_workspace": ([vp, C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
+        "ebv_drag_gradient": ([vp, vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, dp, dp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -344,6 +349,37 @@ class Solver:
                                             C.c_double(dt), C.byref(st)))
         return _stats_dict(st)
 
+    # adjoint (creeping-flow step, fixed dt)
+    def adjoint_step(self, u, p, dt, u_bar, p_bar, f=None, f_bar=None):
+        """Reverse of one step from (u, p): u_bar, p_bar (adjoints of the
+        outputs) become the adjoints of the inputs; f_bar += adjoint of f.
+        Returns (dJ/dtau0, dJ/dmu) of this step."""
+        g = (C.c_double * 2)(0.0, 0.0)
+        self._ok(self._lib.ebv_adjoint_step(self._ctx, _ptr(u), _ptr(p), C.c_double(dt), _ptr(f), _ptr(u_bar),
+                                            _ptr(p_bar), _ptr(f_bar), g))
+        return g[0], g[1]
+
+    def drag_adjoint(self, u, p, w, u_bar, p_bar):
+        """u_bar, p_bar += w grad F_z(u, p); returns w (dF_z/dtau0, dF_z/dmu)."""
+        g = (C.c_double * 2)(0.0, 0.0)
+        self._ok(self._lib.ebv_drag_adjoint(self._ctx, _ptr(u), _ptr(p), C.c_double(w), _ptr(u_bar), _ptr(p_bar),
+                                            g))
+        return g[0], g[1]
+
+    def drag_gradient(self, u0, p0, dt, steps, every=8, f=None, f_grad=True):
+        """Time-averaged drag J over `steps` creeping-flow steps from (u0, p0)
+        and (dJ/dtau0, dJ/dmu, dJ/df or None), checkpointing every `every`."""
+        import torch
+        n = C.c_longlong(0)
+        self._ok(self._lib.ebv_drag_gradient_workspace(self._ctx, steps, every, C.byref(n)))
+        work = torch.empty(n.value, dtype=torch.float64, device=u0.device)
+        J = C.c_double(0.0)
+        g = (C.c_double * 2)(0.0, 0.0)
+        fb = torch.empty_like(u0) if f_grad else None
+        self._ok(self._lib.ebv_drag_gradient(self._ctx, _ptr(u0), _ptr(p0), _ptr(f), C.c_double(dt), steps, every,
+                                             _ptr(work), C.byref(J), g, _ptr(fb)))
+        return J.value, g[0], g[1], fb
+
     def drag(self, u, p):
         fz, yf = C.c_double(0.0), C.c_double(0.0)
         self._ok(self._lib.ebv_drag(self._ctx, _ptr(u), _ptr(p), C.byref(fz), C.byref(yf)))
@@ -454,3 +490,44 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _drag_objective_class():
+    import torch
+
+    class DragObjective(torch.autograd.Function):
+        """J(tau0, mu, f) = time-averaged drag of `steps` creeping-flow steps;
+        forward runs ebv_drag_gradient (objective and gradient in one pass),
+        backward scales the stored gradient."""
+
+        @staticmethod
+        def forward(ctx, tau0, mu, f, solver, u0, p0, dt, steps, every):
+            solver.set_params(tau0=float(tau0), mu=float(mu))
+            J, gt, gm, fb = solver.drag_gradient(u0, p0, dt, steps, every, f=f.detach(),
+                                                 f_grad=f.requires_grad)
+            ctx.grads = (gt, gm, fb)
+            ctx.like = (tau0, mu)
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gt, gm, fb = ctx.grads
+            t, m = ctx.like
+            dt_ = torch.as_tensor(gt, dtype=t.dtype, device=t.device) * gJ.to(t.device)
+            dm_ = torch.as_tensor(gm, dtype=m.dtype, device=m.device) * gJ.to(m.device)
+            df_ = fb * gJ.to(fb.device) if fb is not None else None
+            return dt_, dm_, df_, None, None, None, None, None, None
+
+    return DragObjective
+
+
+_DragObjective = None
+
+
+def drag_objective(solver, tau0, mu, f, u0, p0, dt, steps, every=8):
+    """Differentiable time-averaged drag: tau0, mu (0-dim tensors) and f
+    (3 x cells CUDA tensor) may require grad."""
+    global _DragObjective
+    if _DragObjective is None:
+        _DragObjective = _drag_objective_class()
+    return _DragObjective.apply(tau0, mu, f, solver, u0, p0, dt, steps, every)
