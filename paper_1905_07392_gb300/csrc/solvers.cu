@@ -99,19 +99,42 @@ struct CcOp {
     const T *diag, *bx, *by, *bz;
 };
 
+// Array layout of the cell-centred multigrid, by precision.  FP64 arrays are
+// in the natural order (x fastest).  FP32 arrays -- the coefficients of every
+// level, the V-cycle vectors and the inner Krylov vectors of the refinement
+// solver -- are "row-split": within every x-row the even-i entries come first,
+// then the odd-i ones.  A colour of a red-black pass then reads and writes
+// contiguous half-rows (the cells of one colour in a row all have the same
+// parity of i) instead of every other word of every sector; only the x-face
+// coefficients are still read whole.  Rows keep their length and place, so
+// neighbours in y and z are at the same offsets as in the natural order.
+__host__ __device__ inline int spos(int m, int i) { return (i & 1) ? ((m + 1) >> 1) + (i >> 1) : (i >> 1); }
+template <class T>
+__host__ __device__ inline int cix(const GridD &g, int i, int j, int k)
+{
+    return (k * g.ny + j) * g.nx + (sizeof(T) == 4 ? spos(g.nx, i) : i);
+}
+template <class T>
+__host__ __device__ inline int fidxT(const GridD &g, int d, int i, int j, int k)
+{
+    if (d == 0) return (k * g.ny + j) * (g.nx + 1) + (sizeof(T) == 4 ? spos(g.nx + 1, i) : i);
+    if (d == 1) return (k * (g.ny + 1) + j) * g.nx + (sizeof(T) == 4 ? spos(g.nx, i) : i);
+    return (k * g.ny + j) * g.nx + (sizeof(T) == 4 ? spos(g.nx, i) : i);
+}
+
 template <class T>
 __device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__restrict__ x,
                               T &diag, T &off)
 {
     const GridD &g = A.g;
-    const int c = cidx(g, i, j, k);
-    const T bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
-    const T byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
-    const T bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
+    const int c = cix<T>(g, i, j, k);
+    const T bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
+    const T byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
+    const T bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
     diag = A.diag[c];
     T s = 0;
-    if (i > 0) s += bxl * x[c - 1];
-    if (i < g.nx - 1) s += bxh * x[c + 1];
+    if (i > 0) s += bxl * x[cix<T>(g, i - 1, j, k)];
+    if (i < g.nx - 1) s += bxh * x[cix<T>(g, i + 1, j, k)];
     if (j > 0) s += byl * x[c - g.nx];
     if (j < g.ny - 1) s += byh * x[c + g.nx];
     if (k > 0) s += bzl * x[c - g.nx * g.ny];
@@ -147,15 +170,16 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
         cc[h] = -1;
         val[h] = T(0);
         if (k >= g.nz || i >= g.nx) continue;
-        const int c = cidx(g, i, j, k);
+        const int c = cix<T>(g, i, j, k);
         cc[h] = c;
         const T diag = A.diag[c], bc = b[c];
         T off = 0;
         if (!zero_start) {
-            const T bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
-            const T byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
-            const T bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
-            const T xw = i > 0 ? x[c - 1] : T(0), xe = i < g.nx - 1 ? x[c + 1] : T(0);
+            const T bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
+            const T byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
+            const T bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
+            const T xw = i > 0 ? x[cix<T>(g, i - 1, j, k)] : T(0);
+            const T xe = i < g.nx - 1 ? x[cix<T>(g, i + 1, j, k)] : T(0);
             const T xs = j > 0 ? x[c - sy] : T(0), xn = j < g.ny - 1 ? x[c + sy] : T(0);
             const T xd = k > 0 ? x[c - sz] : T(0), xu = k < g.nz - 1 ? x[c + sz] : T(0);
             if (i > 0) off += bxl * xw;
@@ -172,7 +196,7 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
         if (zero_start) {
             const int k = GS_PZ * kk + h;
             const int io = 2 * t + 1 - ((j + k + color) & 1);
-            if (k < g.nz && io < g.nx) x[cidx(g, io, j, k)] = T(0);
+            if (k < g.nz && io < g.nx) x[cix<T>(g, io, j, k)] = T(0);
         }
         if (cc[h] >= 0) x[cc[h]] = val[h];
     }
@@ -193,10 +217,10 @@ __global__ void __launch_bounds__(256) k_cc_resid_restrict(CcOp<T> A, const T *_
         int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
         T diag, off;
         cc_row(A, i, j, k, x, diag, off);
-        int c = cidx(A.g, i, j, k);
+        int c = cix<T>(A.g, i, j, k);
         s += b[c] - (diag * x[c] - off);
     }
-    bc[cidx(gc, I, J, K)] = s * T(0.125);
+    bc[cix<T>(gc, I, J, K)] = s * T(0.125);
 }
 
 template <class T>
@@ -207,9 +231,8 @@ __global__ void k_cc_prolong(GridD gf, GridD gc, const uint8_t *__restrict__ cov
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i >= gf.nx || j >= gf.ny || k >= gf.nz) return;
-    const int c = cidx(gf, i, j, k);
-    if (cov[c]) return;
-    xf[c] += xc[cidx(gc, i >> 1, j >> 1, k >> 1)];
+    if (cov[cidx(gf, i, j, k)]) return;
+    xf[cix<T>(gf, i, j, k)] += xc[cix<T>(gc, i >> 1, j >> 1, k >> 1)];
 }
 
 // Rediscretised coarse operator: face coefficient = (sum of the 4 fine faces) / 16,
@@ -226,14 +249,14 @@ __global__ void k_cc_coarsen(GridD gf, const T *__restrict__ ef, const T *__rest
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I > gc.nx || J > gc.ny || K > gc.nz) return;
     if (I < gc.nx && J < gc.ny && K < gc.nz) {
-        const int C = cidx(gc, I, J, K);
-        if (covc[C]) {
+        const int C = cix<T>(gc, I, J, K);
+        if (covc[cidx(gc, I, J, K)]) {
             ec[C] = T(1);
         } else {
             T s = 0;
             for (int o = 0; o < 8; o++) {
-                int c = cidx(gf, 2 * I + (o & 1), 2 * J + ((o >> 1) & 1), 2 * K + ((o >> 2) & 1));
-                if (!covf[c]) s += ef[c];
+                const int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
+                if (!covf[cidx(gf, i, j, k)]) s += ef[cix<T>(gf, i, j, k)];
             }
             ec[C] = s * T(0.125);
         }
@@ -253,9 +276,9 @@ __global__ void k_cc_coarsen(GridD gf, const T *__restrict__ ef, const T *__rest
                 int f[3] = {2 * I, 2 * J, 2 * K};
                 f[t1] += q1;
                 f[t2] += q2;
-                s += bf[d][fidx(gf, d, f[0], f[1], f[2])];
+                s += bf[d][fidxT<T>(gf, d, f[0], f[1], f[2])];
             }
-        bcs[d][fidx(gc, d, I, J, K)] = s * T(0.0625);
+        bcs[d][fidxT<T>(gc, d, I, J, K)] = s * T(0.0625);
     }
 }
 
@@ -268,9 +291,10 @@ __global__ void k_cc_make_diag(GridD g, const T *__restrict__ extra, const T *__
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
-    const int c = cidx(g, i, j, k);
-    diag[c] = extra[c] + bx[fidx(g, 0, i, j, k)] + bx[fidx(g, 0, i + 1, j, k)] + by[fidx(g, 1, i, j, k)] +
-              by[fidx(g, 1, i, j + 1, k)] + bz[fidx(g, 2, i, j, k)] + bz[fidx(g, 2, i, j, k + 1)];
+    const int c = cix<T>(g, i, j, k);
+    diag[c] = extra[c] + bx[fidxT<T>(g, 0, i, j, k)] + bx[fidxT<T>(g, 0, i + 1, j, k)] +
+              by[fidxT<T>(g, 1, i, j, k)] + by[fidxT<T>(g, 1, i, j + 1, k)] + bz[fidxT<T>(g, 2, i, j, k)] +
+              bz[fidxT<T>(g, 2, i, j, k + 1)];
 }
 
 __global__ void k_cov_coarsen(GridD gf, const uint8_t *covf, GridD gc, uint8_t *covc)
@@ -296,6 +320,48 @@ __global__ void k_convert(const S *__restrict__ a, D *__restrict__ b, int n)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
         b[s] = (D)a[s];
+}
+
+// FP64 natural-order array of cells (d < 0) or of faces of normal d -> FP32
+// row-split copy.
+__global__ void k_to_split(GridD g, int d, const double *__restrict__ a, float *__restrict__ b)
+{
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    const int n = mx * my * mz;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const int i = s % mx, j = (s / mx) % my, k = s / (mx * my);
+        b[d < 0 ? cix<float>(g, i, j, k) : fidxT<float>(g, d, i, j, k)] = (float)a[s];
+    }
+}
+
+// r = b - q into an FP32 row-split vector, block partials of |r|^2, |b|^2
+// (the cell-centred form of k_resid_to32)
+__global__ void __launch_bounds__(256) k_resid_to32_split(GridD g, const double *__restrict__ b,
+                                                          const double *__restrict__ q, float *__restrict__ r,
+                                                          double *__restrict__ part)
+{
+    const int n = ncell(g);
+    double v = 0.0, w = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const double rs = b[s] - q[s];
+        r[cix<float>(g, s % g.nx, (s / g.nx) % g.ny, s / (g.nx * g.ny))] = (float)rs;
+        v += rs * rs;
+        w += b[s] * b[s];
+    }
+    v = block_sum<256>(v);
+    w = block_sum<256>(w);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = v;
+        part[gridDim.x + blockIdx.x] = w;
+    }
+}
+
+// x += e with e an FP32 row-split vector
+__global__ void k_add32to64_split(GridD g, double *__restrict__ x, const float *__restrict__ e)
+{
+    const int n = ncell(g);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        x[s] += (double)e[cix<float>(g, s % g.nx, (s / g.nx) % g.ny, s / (g.nx * g.ny))];
 }
 
 // Level-0 coefficients of the cell-centred projection: beta = a_f / h^2,
@@ -425,7 +491,7 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
             if (k >= A.g.nz) continue;
             T diag, off;
             cc_row(A, i, j, k, p, diag, off);
-            cc[h] = cidx(A.g, i, j, k);
+            cc[h] = cix<T>(A.g, i, j, k);
             pc[h] = p[cc[h]];
             y[h] = diag * pc[h] - off;
         }
@@ -724,10 +790,10 @@ __global__ void k_cc_bottom_assemble(CcOp<T> A, double *__restrict__ M, int nb)
         for (int s = 0; s < 2 * nb; s++) row[s] = 0.0;
         row[nb + r] = 1.0;
         int i = r % g.nx, j = (r / g.nx) % g.ny, k = r / (g.nx * g.ny);
-        double bxl = A.bx[fidx(g, 0, i, j, k)], bxh = A.bx[fidx(g, 0, i + 1, j, k)];
-        double byl = A.by[fidx(g, 1, i, j, k)], byh = A.by[fidx(g, 1, i, j + 1, k)];
-        double bzl = A.bz[fidx(g, 2, i, j, k)], bzh = A.bz[fidx(g, 2, i, j, k + 1)];
-        double diag = (double)A.diag[r];
+        double bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
+        double byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
+        double bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
+        double diag = (double)A.diag[cix<T>(g, i, j, k)];
         row[r] = diag > 0.0 ? diag : 1.0;
         if (i > 0) row[r - 1] = -bxl;
         if (i < g.nx - 1) row[r + 1] = -bxh;
@@ -787,15 +853,21 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, i
     }
 }
 
+// x = scale inv b; the dense system is numbered in the natural order, the
+// vectors of a row-split (FP32 cell-centred) level are mapped through g.
 template <class T>
 __global__ void __launch_bounds__(256) k_bottom_solve(const double *__restrict__ inv, int nb,
                                                       const T *__restrict__ b, T *__restrict__ x,
-                                                      double scale)
+                                                      double scale, GridD g, int split)
 {
+    auto pos = [&](int r) {
+        if (!split) return r;
+        return cix<float>(g, r % g.nx, (r / g.nx) % g.ny, r / (g.nx * g.ny));
+    };
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int q = 0; q < nb; q++) s += inv[(size_t)r * nb + q] * (double)b[q];
-        x[r] = (T)(s * scale);
+        for (int q = 0; q < nb; q++) s += inv[(size_t)r * nb + q] * (double)b[pos(q)];
+        x[pos(r)] = (T)(s * scale);
     }
 }
 
@@ -1137,7 +1209,8 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
     {
         T *x = Lb ? (T *)c->lx[Lb] : x0;
         const T *b = Lb ? (const T *)c->lb[Lb] : b0;
-        EBV_LAUNCH(c, k_bottom_solve<T>, dim3((H.nb + 255) / 256), dim3(256), 0, H.binv, H.nb, b, x, 1.0);
+        EBV_LAUNCH(c, k_bottom_solve<T>, dim3((H.nb + 255) / 256), dim3(256), 0, H.binv, H.nb, b, x, 1.0,
+                   H.lv[Lb].g, (int)(sizeof(T) == 4));
     }
     for (int l = Lb - 1; l >= 0; l--) {
         const CcLevel &L = H.lv[l];
@@ -1207,7 +1280,8 @@ void nd_vcycle(Ctx *c, NdHier &H, const T *b0, T *x0)
     {
         T *x = Lb ? (T *)c->lx[Lb] : x0;
         const T *b = Lb ? (const T *)c->lb[Lb] : b0;
-        EBV_LAUNCH(c, k_bottom_solve<T>, dim3((H.nb + 255) / 256), dim3(256), 0, H.binv, H.nb, b, x, 1.0);
+        EBV_LAUNCH(c, k_bottom_solve<T>, dim3((H.nb + 255) / 256), dim3(256), 0, H.binv, H.nb, b, x, 1.0,
+                   H.lv[Lb].g, 0);
     }
     for (int l = Lb - 1; l >= 0; l--) {
         const NdLevel &L = H.lv[l];
@@ -1234,6 +1308,11 @@ struct Problem {
     // z = one V-cycle applied to r, in FP64 or FP32
     virtual void precond(Ctx *c, const double *r, double *z) = 0;
     virtual void precond32(Ctx *c, const float *r, float *z) = 0;
+    // FP64 <-> FP32 vectors of the refinement solver (the FP32 side in the
+    // layout of the problem's FP32 multigrid): r = b - q with block partials
+    // of |r|^2 and |b|^2 in c->part; x += e
+    virtual void resid_to32(Ctx *c, const double *b, const double *q, float *r) = 0;
+    virtual void add32(Ctx *c, double *x, const float *e) = 0;
 };
 
 inline int vblocks(int n) { return std::min(kReduceBlocks, (n + 255) / 256); }
@@ -1412,7 +1491,7 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
     float *r = c->kr32, *z = c->kz32, *p = c->kp32, *q = c->kq32, *e = c->ke32;
     auto true_residual = [&]() {
         P.apply_dot(c, x, c->kq);
-        EBV_LAUNCH(c, k_resid_to32, dim3(vblocks(n)), dim3(256), 0, b, c->kq, r, n, c->part);
+        P.resid_to32(c, b, c->kq, r);
         reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
         reduce_sum(c, c->part + vblocks(n), vblocks(n), c->scal + S_BB);
     };
@@ -1438,7 +1517,7 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
                        inner.use_h);
         }
         inner_count = inner.body_launches();
-        EBV_LAUNCH(c, k_add32to64, dim3(vblocks(n)), dim3(256), 0, x, e, n);
+        P.add32(c, x, e);
         true_residual();
         EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 60, 1, inner_drop,
                    outer.h, outer.use_h);
@@ -1468,6 +1547,14 @@ struct CcProblem : Problem {
     }
     void precond(Ctx *c, const double *r, double *z) override { cc_vcycle<double>(c, *H, r, z); }
     void precond32(Ctx *c, const float *r, float *z) override { cc_vcycle<float>(c, *H, r, z); }
+    void resid_to32(Ctx *c, const double *b, const double *q, float *r) override
+    {
+        EBV_LAUNCH(c, k_resid_to32_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, b, q, r, c->part);
+    }
+    void add32(Ctx *c, double *x, const float *e) override
+    {
+        EBV_LAUNCH(c, k_add32to64_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, x, e);
+    }
 };
 
 struct NdProblem : Problem {
@@ -1487,6 +1574,14 @@ struct NdProblem : Problem {
     }
     void precond(Ctx *c, const double *r, double *z) override { nd_vcycle<double>(c, *H, r, z); }
     void precond32(Ctx *c, const float *r, float *z) override { nd_vcycle<float>(c, *H, r, z); }
+    void resid_to32(Ctx *c, const double *b, const double *q, float *r) override
+    {
+        EBV_LAUNCH(c, k_resid_to32, dim3(vblocks(n())), dim3(256), 0, b, q, r, n(), c->part);
+    }
+    void add32(Ctx *c, double *x, const float *e) override
+    {
+        EBV_LAUNCH(c, k_add32to64, dim3(vblocks(n())), dim3(256), 0, x, e, n());
+    }
 };
 
 ebv_status solve(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
@@ -1503,12 +1598,10 @@ ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
     cc_make_diag<double>(c, L0);
     if (fp32) {
         const int n = ncell(L0.g);
-        EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(n)), dim3(256), 0, L0.extra_d, L0.extra_f, n);
-        EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(n)), dim3(256), 0, L0.diag_d, L0.diag_f, n);
-        for (int d = 0; d < 3; d++) {
-            int nf = nface(L0.g, d);
-            EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nf)), dim3(256), 0, L0.bf_d[d], L0.bf_f[d], nf);
-        }
+        EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, L0.extra_d, L0.extra_f);
+        EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, L0.diag_d, L0.diag_f);
+        for (int d = 0; d < 3; d++)
+            EBV_LAUNCH(c, k_to_split, dim3(vblocks(nface(L0.g, d))), dim3(256), 0, L0.g, d, L0.bf_d[d], L0.bf_f[d]);
     }
     for (int l = 0; l + 1 < H.L; l++) {
         CcLevel &F = H.lv[l], &Cc = H.lv[l + 1];
