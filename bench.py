@@ -325,23 +325,27 @@ def run_ours(args, rank, world, local):
     if not args.skip_batch:
         out["batch_sweep"] = run_batch(dev, world)
     if not args.skip_adjoint:
-        out["adjoint"] = run_adjoint(dev)
+        for key, adv in (("adjoint", 0), ("adjoint_full_step", 1)):
+            try:
+                out[key] = run_adjoint(dev, advect=adv)
+            except Exception as e:  # reported in the line; the rest of the measurement stands
+                out[key] = {"error": str(e)}
     return out
 
 
-def run_adjoint(dev, n=128, steps=40, every=8):
-    """Drag sensitivities of the creeping-flow step: 128^3 sphere channel
-    (r = 0.125, Bi = 5, m = 1e3), a seeded Gaussian body force (sigma 0.1),
-    40 steps at the initial CFL step, checkpoints every 8 steps; gradient with
-    respect to tau0, mu and f by the adjoint, dJ/dtau0 also by central
-    differences (forward solves to 1e-13)."""
+def run_adjoint(dev, n=128, steps=40, every=8, advect=0):
+    """Drag sensitivities of the step (advect = 0: creeping flow; 1: with the
+    convective term): 128^3 sphere channel (r = 0.125, Bi = 5, m = 1e3), a
+    seeded Gaussian body force (sigma 0.1), 40 steps at the initial CFL step,
+    checkpoints every 8 steps; gradient with respect to tau0, mu and f by the
+    adjoint, dJ/dtau0 also by central differences (forward solves to 1e-13)."""
     import torch
     from paper_1905_07392_gb300 import ebvisc
     from paper_1905_07392_gb300 import workloads as W
     w = W.Workload("adjoint_128", n=n, radius=0.125, tau0=W.tau0_for_bingham(5.0, 0.125), m=1e3, seed=3)
     out = {}
     for prec, name in ((ebvisc.FP32_REFINE, "fp32_refine"), (ebvisc.FP64, "fp64")):
-        s = ebvisc.Solver.from_workload(w, precision=prec, tol=1e-13, max_iters=20000, advect=0)
+        s = ebvisc.Solver.from_workload(w, precision=prec, tol=1e-13, max_iters=20000, advect=advect)
         fluid = (s.geometry()["alpha"] > 0).to(torch.float64)
         u0 = (torch.tensor(W.initial_velocity(w).reshape(3, -1), device=dev) * fluid).reshape(-1).contiguous()
         p0 = torch.zeros(s.nnode, dtype=torch.float64, device=dev)
@@ -374,7 +378,8 @@ def run_adjoint(dev, n=128, steps=40, every=8):
                           "adjoint_over_forward": round(t_adj / t_fwd, 2), "J_forward": J0})
         out[name] = entry
         s.close()
-    out.update({"workload": f"sphere_channel_{n}^3_bi5_m1e3_creeping", "steps": steps, "checkpoint_every": every,
+    form = "full_step" if advect else "creeping"
+    out.update({"workload": f"sphere_channel_{n}^3_bi5_m1e3_{form}", "steps": steps, "checkpoint_every": every,
                 "dt": dt, "tol": 1e-13})
     return out
 

@@ -222,20 +222,24 @@ const char *ebv_last_error(const ebv_ctx *ctx);
 void ebv_destroy(ebv_ctx *ctx);
 
 /* ---- Adjoint (drag sensitivities) ----------------------------------------
- * Reverse mode of the creeping-flow step (advect = 0; the paper's evaluation
- * runs at Re = 1e-3, Sec. "Cylinder moving through Bingham fluid") at a fixed
- * dt, for the sensitivities of the drag of Eq. drag-force to the yield stress
- * tau0, the plastic viscosity mu and a per-cell body force f: hand-written
- * adjoints of the strain-rate/viscosity update, the explicit viscous term
- * (face fluxes, EB wall flux of Eq. dudn, redistribution), the eta-dependence
- * of the semi-implicit viscous operator, the nodal projection and the drag;
- * the adjoint solves reuse the (symmetric) viscous and nodal multigrid-CG
- * solves in the context's precision.  Rheologies: Newtonian, Bingham,
+ * Reverse mode of the step of Algorithm 1 at a fixed dt, in the form the
+ * context's `advect` selects (1: with the convective term; 0: creeping flow,
+ * as in the paper's evaluation at Re = 1e-3, Sec. "Cylinder moving through
+ * Bingham fluid"), for the sensitivities of the drag of Eq. drag-force to the
+ * yield stress tau0, the plastic viscosity mu and a per-cell body force f:
+ * hand-written adjoints of the limited slopes, upwinded face states, MAC
+ * projection and convective fluxes, of the strain-rate/viscosity update, the
+ * explicit viscous term (face fluxes, EB wall flux of Eq. dudn,
+ * redistribution), the eta-dependence of the semi-implicit viscous operator,
+ * the nodal projection and the drag; the adjoint solves reuse the
+ * (symmetric) projection, viscous and nodal multigrid-CG solves in the
+ * context's precision.  The limiter and the upwinding are piecewise linear:
+ * the reverse pass takes the branch the forward took.  Rheologies: Newtonian, Bingham,
  * Herschel-Bulkley, power law.  dt, which Eq. cfl:dt ties to u and f, is a
  * fixed input (its own sensitivity is not propagated).  The first adjoint
- * call allocates the context's adjoint workspace (about 90 doubles per
- * cell); forward steps never allocate.  EBV_ERR_INVALID if advect != 0, dt
- * <= 0 or the rheology has no adjoint.
+ * call allocates the context's adjoint workspace (about 150 doubles per
+ * cell); forward steps never allocate.  EBV_ERR_INVALID if dt <= 0 or the
+ * rheology has no adjoint.
  *
  * One step: given the state (u, p) at the step's start (device, unchanged),
  * dt and f (3 x cells or NULL), and in u_bar, p_bar the adjoints of the
@@ -250,8 +254,7 @@ ebv_status ebv_drag_adjoint(ebv_ctx *ctx, const double *u, const double *p, doub
                             double *p_bar, double *grads);
 /* Doubles of device workspace ebv_drag_gradient needs for (steps, every). */
 ebv_status ebv_drag_gradient_workspace(const ebv_ctx *ctx, int steps, int every, long long *ndoubles);
-/* J = (1/steps) sum_{s=1..steps} F_z(u_s, p_s) over `steps` creeping-flow
- * steps from (u0, p0) (device, unchanged) at fixed dt with body force f
+/* J = (1/steps) sum_{s=1..steps} F_z(u_s, p_s) over `steps` steps from (u0, p0) (device, unchanged) at fixed dt with body force f
  * (3 x cells or NULL), and its gradient: grads[0] = dJ/dtau0, grads[1] =
  * dJ/dmu (host), f_bar = dJ/df (3 x cells, device, or NULL).  Stores (u, p)
  * every `every` steps in `work` (device, ebv_drag_gradient_workspace doubles)

@@ -1,6 +1,6 @@
-// Reverse-mode kernels of the creeping-flow step (convective term off): for
-// each forward kernel of the step, a kernel that takes the adjoint of its
-// outputs and adds the adjoint of its inputs.  Each mirrors its forward
+// Reverse-mode kernels of the step of Algorithm 1 (with or without the
+// convective term): for each forward kernel of the step, a kernel that takes
+// the adjoint of its outputs and adds the adjoint of its inputs.  Each mirrors its forward
 // kernel's stencil (same branches, same weights); where the forward kernel
 // gathers from several cells the reverse one scatters with FP64 atomics, or
 // gathers the transposed stencil where that is as simple.
@@ -15,6 +15,10 @@
 //   grad_p (k_psi, k_add_gradp)  k_gradp_t
 //   k_nodal_rhs (in ut)       k_nodal_rhs_t
 //   k_drag_terms              k_drag_adj
+//   k_slopes                  k_slopes_adj        (MC limiter)
+//   k_face_states             k_face_states_adj   (Godunov upwinding)
+//   k_mac_rhs / k_mac_correct k_mac_rhs_adj / k_mac_correct_adj (with one MAC solve)
+//   k_conv_flux               k_conv_flux_adj
 #include <algorithm>
 
 #include "ebv_internal.cuh"
@@ -605,19 +609,219 @@ __global__ void k_drag_adj(GridD g, GeomD geo, const double *__restrict__ eta, c
     }
 }
 
+// ---- convective term (Algorithm 2, advect = 1) -----------------------------------
+// Forward: S = MC-limited slopes of u; uf = upwinded extrapolated normal
+// velocities; MAC projection uF = uf - grad phi, A phi = D uf; F_q = a
+// state_q uF with the state upwinded by uF; C = -R(div F).  The reverse
+// pieces below take the branch each forward kernel took (the limiter's
+// minimum, the Godunov case, the sign of uF), so they are exact wherever the
+// forward is differentiable.
+
+// Limited slope of f along d at (i,j,k) as a stencil (cells c-e, c, c+e):
+// zero, dd/2, 2 dl or 2 dr by the forward's branch.
+__device__ inline void mc_slope_w(const GridD &g, const uint8_t *flag, const double *f, int i, int j, int k, int d,
+                                  int *idx, double *w)
+{
+    int3 e = unit3(d);
+    idx[0] = cidx(g, i - e.x, j - e.y, k - e.z);
+    idx[1] = cidx(g, i, j, k);
+    idx[2] = cidx(g, i + e.x, j + e.y, k + e.z);
+    w[0] = w[1] = w[2] = 0.0;
+    if (!avail(g, flag, i + e.x, j + e.y, k + e.z) || !avail(g, flag, i - e.x, j - e.y, k - e.z)) return;
+    const double f0 = f[idx[1]], fp = f[idx[2]], fm = f[idx[0]];
+    const double dl = f0 - fm, dr = fp - f0, dd = fp - fm;
+    if (dl == 0.0 || dr == 0.0 || (dl < 0.0) != (dr < 0.0)) return;
+    // m = min(|dd|/2, 2|dl|, 2|dr|) with the sign of dd (dl, dr, dd share it)
+    double m = fabs(0.5 * dd);
+    int br = 0;
+    if (2.0 * fabs(dl) < m) { m = 2.0 * fabs(dl); br = 1; }
+    if (2.0 * fabs(dr) < m) { m = 2.0 * fabs(dr); br = 2; }
+    if (br == 0) { w[2] = 0.5; w[0] = -0.5; }
+    else if (br == 1) { w[1] = 2.0; w[0] = -2.0; }
+    else { w[2] = 2.0; w[1] = -2.0; }
+}
+
+__global__ void __launch_bounds__(256) k_slopes_adj(GridD g, const uint8_t *__restrict__ flag,
+                                                    const double *__restrict__ u, const double *__restrict__ Sb,
+                                                    double *__restrict__ ub)
+{
+    ADJ_CELL
+    if (!flag[c]) return;
+    const int N3 = ncell(g);
+    for (int d = 0; d < 3; d++)
+        for (int q = 0; q < 3; q++) {
+            const double sb = Sb[(3 * d + q) * N3 + c];
+            if (sb == 0.0) continue;
+            int idx[3];
+            double w[3];
+            mc_slope_w(g, flag, u + q * N3, i, j, k, d, idx, w);
+            for (int r = 0; r < 3; r++)
+                if (w[r] != 0.0) atomicAdd(&ub[q * N3 + idx[r]], w[r] * sb);
+        }
+}
+
+// Face flux F_q = a state_q uF: adjoint of the state (to u, S) and of uF.
+__global__ void __launch_bounds__(256) k_conv_flux_adj(GridD g, int d, const double *__restrict__ ap,
+                                                       const double *__restrict__ u, const double *__restrict__ S,
+                                                       const double *__restrict__ uFd,
+                                                       const double *__restrict__ Fb, int nft, int off,
+                                                       double *__restrict__ ub, double *__restrict__ Sb,
+                                                       double *__restrict__ uFbd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    if (i >= mx || j >= my || k >= mz) return;
+    const int f = fidx(g, d, i, j, k);
+    const int N3 = ncell(g);
+    const double a = ap[f];
+    if (a <= 0.0) { uFbd[f] = 0.0; return; }
+    const double w = uFd[f];
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    int3 e = unit3(d);
+    double wb = 0.0;
+    if (pos == 0 || pos == dimn(g, d)) {
+        const int hs = pos != 0;
+        const int c = cidx(g, i - hs * e.x, j - hs * e.y, k - hs * e.z);
+        const bool in = g.bc[2 * d + hs] == EBV_INFLOW;
+        for (int q = 0; q < 3; q++) {
+            const double fb = Fb[q * nft + off + f];
+            const double state = in ? g.u_in[q] : u[q * N3 + c];
+            wb += a * state * fb;
+            if (!in) atomicAdd(&ub[q * N3 + c], a * w * fb);
+        }
+        uFbd[f] = wb;
+        return;
+    }
+    const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
+    for (int q = 0; q < 3; q++) {
+        const double fb = Fb[q * nft + off + f];
+        const double sL = u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL];
+        const double sR = u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR];
+        const double state = w > 0.0 ? sL : (w < 0.0 ? sR : 0.5 * (sL + sR));
+        wb += a * state * fb;
+        const double stb = a * w * fb;
+        const double wl = w > 0.0 ? 1.0 : (w < 0.0 ? 0.0 : 0.5), wr = 1.0 - wl;
+        if (wl != 0.0 && stb != 0.0) {
+            atomicAdd(&ub[q * N3 + cL], wl * stb);
+            atomicAdd(&Sb[(3 * d + q) * N3 + cL], 0.5 * wl * stb);
+        }
+        if (wr != 0.0 && stb != 0.0) {
+            atomicAdd(&ub[q * N3 + cR], wr * stb);
+            atomicAdd(&Sb[(3 * d + q) * N3 + cR], -0.5 * wr * stb);
+        }
+    }
+    uFbd[f] = wb;
+}
+
+// uF = uf - grad phi (faces with a > 0; outflow box faces with phi = 0 at the
+// ghost, h/2 away): phi_bar(c) = sum over the cell's faces of d uF_f/d phi_c uF_bar_f.
+__global__ void k_mac_correct_adj(GridD g, const double *__restrict__ ax, const double *__restrict__ ay,
+                                  const double *__restrict__ az, const double *__restrict__ uFb,
+                                  double *__restrict__ phib)
+{
+    ADJ_CELL
+    const double *A[3] = {ax, ay, az};
+    const int off[3] = {0, nface(g, 0), nface(g, 0) + nface(g, 1)};
+    int id[3] = {i, j, k};
+    double s = 0.0;
+    for (int d = 0; d < 3; d++)
+        for (int hs = 0; hs < 2; hs++) {
+            int fi[3] = {i, j, k};
+            fi[d] += hs;
+            const int f = fidx(g, d, fi[0], fi[1], fi[2]);
+            if (!(A[d][f] > 0.0)) continue;
+            const double b = uFb[off[d] + f];
+            const int pos = id[d] + hs;
+            if (pos == 0 || pos == dimn(g, d)) {
+                if (g.bc[2 * d + hs] != EBV_OUTFLOW) continue;
+                // high side: uF -= (0 - phi) 2/h; low side: uF -= (phi - 0) 2/h
+                s += (hs ? 1.0 : -1.0) * 2.0 * g.ih * b;
+            } else {
+                // interior: uF -= (phi_R - phi_L)/h; this cell is L on its high face, R on its low face
+                s += (hs ? 1.0 : -1.0) * g.ih * b;
+            }
+        }
+    phib[c] = s;
+}
+
+// b = -(1/h) sum (a uf) over the cell's faces (fluid cells): uf_bar += the transpose.
+__global__ void k_mac_rhs_adj(GridD g, int d, const uint8_t *__restrict__ flag, const double *__restrict__ ap,
+                              const double *__restrict__ bb, double *__restrict__ ufbd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    if (i >= mx || j >= my || k >= mz) return;
+    const int f = fidx(g, d, i, j, k);
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    int3 e = unit3(d);
+    double v = 0.0;
+    if (pos > 0) {  // low cell: this is its high face (+)
+        const int cL = cidx(g, i - e.x, j - e.y, k - e.z);
+        if (flag[cL]) v += bb[cL];
+    }
+    if (pos < dimn(g, d)) {  // high cell: its low face (-)
+        const int cR = cidx(g, i, j, k);
+        if (flag[cR]) v -= bb[cR];
+    }
+    ufbd[f] += -g.ih * ap[f] * v;
+}
+
+// Normal face velocity (extrapolated, Godunov upwinded; outflow box face: the
+// cell value): its adjoint to u_d and S_dd.
+__global__ void __launch_bounds__(256) k_face_states_adj(GridD g, int d, const double *__restrict__ ap,
+                                                         const double *__restrict__ u, const double *__restrict__ S,
+                                                         const double *__restrict__ ufbd, double *__restrict__ ub,
+                                                         double *__restrict__ Sb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
+    if (i >= mx || j >= my || k >= mz) return;
+    const int f = fidx(g, d, i, j, k);
+    if (!(ap[f] > 0.0)) return;
+    const double fb = ufbd[f];
+    if (fb == 0.0) return;
+    const int N3 = ncell(g);
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    int3 e = unit3(d);
+    if (pos == 0 || pos == dimn(g, d)) {
+        const int hs = pos != 0;
+        if (g.bc[2 * d + hs] == EBV_OUTFLOW)
+            atomicAdd(&ub[d * N3 + cidx(g, i - hs * e.x, j - hs * e.y, k - hs * e.z)], fb);
+        return;
+    }
+    const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
+    const double uL = u[d * N3 + cL] + 0.5 * S[(3 * d + d) * N3 + cL];
+    const double uR = u[d * N3 + cR] - 0.5 * S[(3 * d + d) * N3 + cR];
+    if (uL > 0.0 && uL + uR > 0.0) {
+        atomicAdd(&ub[d * N3 + cL], fb);
+        atomicAdd(&Sb[(3 * d + d) * N3 + cL], 0.5 * fb);
+    } else if (uR < 0.0 && uL + uR < 0.0) {
+        atomicAdd(&ub[d * N3 + cR], fb);
+        atomicAdd(&Sb[(3 * d + d) * N3 + cR], -0.5 * fb);
+    }
+}
+
 // ---- elementwise pieces ------------------------------------------------------------
 // psi = rho u + dt (V - grad p + f) on fluid cells: u_bar += rho psi_bar,
 // V_bar = vs psi_bar (or += when accumulating; vs is dt times the weight V
 // has in psi), f_bar += dt psi_bar.
 __global__ void k_psi_adj(int N3, const uint8_t *__restrict__ flag, const double *__restrict__ psib, double rho,
                           double dt, double vs, double *__restrict__ ub, double *__restrict__ Vb, int vb_acc,
-                          double *__restrict__ fb)
+                          double *__restrict__ fb, double *__restrict__ Cb)
 {
+    // psi also holds dt rho C (with V's weight): C_bar = rho vs psi_bar
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < 3 * N3; s += gridDim.x * blockDim.x) {
         const int c = s % N3;
         const double pb = flag[c] ? psib[s] : 0.0;
         ub[s] += rho * pb;
         Vb[s] = vb_acc ? Vb[s] + vs * pb : vs * pb;
+        if (Cb) Cb[s] = vb_acc ? Cb[s] + rho * vs * pb : rho * vs * pb;
         if (fb) fb[s] += dt * pb;
     }
 }
@@ -748,6 +952,51 @@ ebv_status adj_viscous_explicit(Ctx *c, const double *u, const double *eta, cons
     return EBV_OK;
 }
 
+// C(u) = -R(div F(u, S(u), uF(u))): ub += (dC/du)^T Cb.  S: the forward
+// slopes of u, uF: its projected face velocities.  Work: DCb, tb (3 x cells),
+// Fb (3 x faces), Sb (9 x cells), uFb (faces), phib, bb (cells).
+ebv_status adj_convective(Ctx *c, const double *u, const double *S, const double *uF, const double *Cb, double *ub,
+                          double *DCb, double *tb, double *Fb, double *Sb, double *uFb, double *phib, double *bb)
+{
+    const GridD &g = c->g;
+    GeomD geo = geomd(c);
+    const int N3 = ncell(g), nft = nface(g, 0) + nface(g, 1) + nface(g, 2);
+    const int offs[3] = {0, nface(g, 0), nface(g, 0) + nface(g, 1)};
+    const double *A[3] = {c->ax, c->ay, c->az};
+    // redistribution (sign -1, no division) and the divergence
+    EBV_LAUNCH(c, k_redist_adj_far, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, Cb, -1.0, 1.0, DCb);
+    if (c->nnear) {
+        dim3 gr((c->nnear + 127) / 128);
+        EBV_LAUNCH(c, k_redist_adj_a, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->alpha, Cb, -1.0, 1.0, DCb,
+                   tb);
+        EBV_LAUNCH(c, k_redist_adj_b, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->alpha, tb, DCb);
+    }
+    for (int d = 0; d < 3; d++)
+        EBV_LAUNCH(c, k_flux_div_adj_faces, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g,
+                   d, geo, DCb, nft, offs[d], Fb);
+    // fluxes: to u, S and the projected face velocities
+    EBV_CUDA_TRY(c, cudaMemsetAsync(Sb, 0, 9 * (size_t)N3 * sizeof(double), c->stream));
+    for (int d = 0; d < 3; d++)
+        EBV_LAUNCH(c, k_conv_flux_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
+                   A[d], u, S, uF + offs[d], Fb, nft, offs[d], ub, Sb, uFb + offs[d]);
+    // MAC projection: phi_bar, the adjoint solve, then the face divergence
+    EBV_LAUNCH(c, k_mac_correct_adj, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->ax, c->ay, c->az, uFb, phib);
+    int it = 0;
+    double res = 0.0;
+    c->cur_slot = 11;
+    ebv_status st = mac_solve(c, phib, bb, &it, &res);
+    if (st != EBV_OK) return st;
+    for (int d = 0; d < 3; d++)
+        EBV_LAUNCH(c, k_mac_rhs_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
+                   c->flag, A[d], bb, uFb + offs[d]);
+    // face states and slopes
+    for (int d = 0; d < 3; d++)
+        EBV_LAUNCH(c, k_face_states_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
+                   A[d], u, S, uFb + offs[d], ub, Sb);
+    EBV_LAUNCH(c, k_slopes_adj, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, Sb, ub);
+    return EBV_OK;
+}
+
 ebv_status adj_visc_eta(Ctx *c, int comp, const double *lam, const double *x, double *eta_bar)
 {
     const GridD &g = c->g;
@@ -780,11 +1029,12 @@ ebv_status adj_drag(Ctx *c, const double *eta, double wJ, double *eta_bar, doubl
     return EBV_OK;
 }
 
-ebv_status adj_psi(Ctx *c, const double *psib, double dt, double vs, double *ub, double *Vb, int vb_acc, double *fb)
+ebv_status adj_psi(Ctx *c, const double *psib, double dt, double vs, double *ub, double *Vb, int vb_acc, double *fb,
+                   double *Cb)
 {
     const int N3 = ncell(c->g);
     EBV_LAUNCH(c, k_psi_adj, dim3(eblocks(3LL * N3)), dim3(256), 0, N3, c->flag, psib, c->prm.rho, dt, vs, ub, Vb,
-               vb_acc, fb);
+               vb_acc, fb, Cb);
     return EBV_OK;
 }
 

@@ -698,6 +698,9 @@ struct AdjBufs {
     double *em, *es, *eb, *Gm, *Gs, *Vm, *Vs, *Va, *psi, *utm, *uts, *us, *zero3, *t3;
     double *ebm, *ebs, *ebb, *Gb, *Vbs, *Vbm, *psib, *usb, *utb, *lam, *DCb, *tb, *etad;
     double *ffb, *dudnb, *ps, *psb, *nb1, *nb2, *ua, *pa, *grads;
+    // convective term: slopes and projected face velocities of both stages,
+    // C of both stages and its average, their adjoints and work
+    double *Sm, *Ss, *uFm, *uFs, *Cm, *Cs, *Ca, *Cbm, *Cbs, *Sb, *uFb, *phib, *bbc;
 };
 
 // Carves the adjoint workspace into B (allocated on first use, once per
@@ -710,12 +713,13 @@ ebv_status adj_buffers(Ctx *c, AdjBufs &B)
     size_t off = 0;
     std::vector<std::pair<double **, size_t>> parts;
     auto take = [&](double **dst, size_t n) { parts.push_back({dst, off}); off += n; };
-    for (double **d : {&B.em, &B.es, &B.eb, &B.ebm, &B.ebs, &B.ebb, &B.lam, &B.etad}) take(d, N3);
-    for (double **d : {&B.Gm, &B.Gs, &B.Gb}) take(d, 9 * N3);
+    for (double **d : {&B.em, &B.es, &B.eb, &B.ebm, &B.ebs, &B.ebb, &B.lam, &B.etad, &B.phib, &B.bbc}) take(d, N3);
+    for (double **d : {&B.Gm, &B.Gs, &B.Gb, &B.Sm, &B.Ss, &B.Sb}) take(d, 9 * N3);
     for (double **d : {&B.Vm, &B.Vs, &B.Va, &B.psi, &B.utm, &B.uts, &B.us, &B.zero3, &B.t3, &B.Vbs, &B.Vbm, &B.psib,
-                       &B.usb, &B.utb, &B.DCb, &B.tb, &B.ua})
+                       &B.usb, &B.utb, &B.DCb, &B.tb, &B.ua, &B.Cm, &B.Cs, &B.Ca, &B.Cbm, &B.Cbs})
         take(d, 3 * N3);
     take(&B.ffb, 3 * NF);
+    for (double **d : {&B.uFm, &B.uFs, &B.uFb}) take(d, NF);
     take(&B.dudnb, 3 * NC);
     for (double **d : {&B.ps, &B.psb, &B.nb1, &B.nb2, &B.pa}) take(d, NN);
     take(&B.grads, 8);
@@ -736,8 +740,6 @@ ebv_status adj_buffers(Ctx *c, AdjBufs &B)
 
 ebv_status adj_check(Ctx *c, double dt)
 {
-    if (c->prm.advect != 0)
-        return c->fail(EBV_ERR_INVALID, "the adjoint covers the creeping-flow step: set advect = 0");
     if (c->prm.model != EBV_NEWTONIAN && c->prm.model != EBV_BINGHAM && c->prm.model != EBV_HERSCHEL_BULKLEY &&
         c->prm.model != EBV_POWER_LAW)
         return c->fail(EBV_ERR_INVALID, "no adjoint for this rheology");
@@ -760,6 +762,7 @@ ebv_status proj_adjoint(Ctx *c, AdjBufs &B, double dt, const double *ubo, const 
     EBV_CUDA_TRY(c, cudaMemsetAsync(B.nb2, 0, NN * sizeof(double), c->stream));
     int it = 0;
     double res = 0.0;
+    c->cur_slot = 13;
     TRY(nodal_solve(c, B.nb1, B.nb2, &it, &res));
     TRY(adj_nodal_rhs_t(c, B.nb2, B.t3));
     TRY(adj_mask_scale(c, 3, B.t3, 1.0, utb));
@@ -776,6 +779,7 @@ ebv_status visc_adjoint(Ctx *c, AdjBufs &B, const double *eta, const double *x, 
     for (int q = 0; q < 3; q++) {
         int it = 0;
         double res = 0.0;
+        c->cur_slot = 12;
         TRY(visc_solve_rhs(c, eta, q, xb + q * N3, B.lam, &it, &res));
         TRY(adj_alpha_times(c, B.lam, psib + q * N3));
         TRY(adj_visc_eta(c, q, B.lam, x + q * N3, etab));
@@ -792,22 +796,44 @@ ebv_status adjoint_step_impl(Ctx *c, const double *u, const double *p, double dt
     const size_t N3 = ncell(c->g), NN = nnode(c->g);
     cudaStream_t s = c->stream;
     TRY(set_dt(c, dt));
-    // ---- forward, keeping the intermediates (as advance_impl with C = 0)
-    EBV_CUDA_TRY(c, cudaMemsetAsync(B.zero3, 0, 3 * N3 * sizeof(double), s));
+    const bool adv = c->prm.advect != 0;
+    // the convective term of state w (as derived() computes it): slopes into
+    // S, projected face velocities into uF, C into C
+    auto convective = [&](const double *w, double *S, double *uF, double *C) -> ebv_status {
+        if (!adv) {
+            EBV_CUDA_TRY(c, cudaMemsetAsync(C, 0, 3 * N3 * sizeof(double), s));
+            return EBV_OK;
+        }
+        TRY(launch_face_states(c, w, uF));   // slopes of w in c->G
+        EBV_CUDA_TRY(c, cudaMemcpyAsync(S, c->G, 9 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        TRY(launch_mac_rhs(c, uF, c->rhs_c));
+        int it = 0;
+        double res = 0.0;
+        c->cur_slot = 10;   // the reverse pass's solves use slots 10..13
+        TRY(mac_solve(c, c->rhs_c, c->phi, &it, &res));
+        TRY(launch_mac_correct(c, uF, c->phi));
+        TRY(launch_convective(c, w, uF, C));
+        return EBV_OK;
+    };
+    // ---- forward, keeping the intermediates (as advance_impl)
+    TRY(convective(u, B.Sm, B.uFm, B.Cm));
     TRY(launch_strain_eta(c, u, B.em, nullptr, B.Gm));
     TRY(launch_viscous_explicit(c, u, B.em, B.Gm, B.Vm));
-    TRY(launch_psi(c, u, B.zero3, B.Vm, p, f, B.psi));
+    TRY(launch_psi(c, u, B.Cm, B.Vm, p, f, B.psi));
     TRY(viscous_update(c, B.em, B.psi, B.utm, nullptr, 1));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(B.us, B.utm, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(B.ps, p, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
     TRY(nodal_projection(c, B.us, B.ps, nullptr, 4));      // u*, p*
+    TRY(convective(B.us, B.Ss, B.uFs, B.Cs));
     TRY(launch_strain_eta(c, B.us, B.es, nullptr, B.Gs));
     TRY(launch_viscous_explicit(c, B.us, B.es, B.Gs, B.Vs));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(B.Ca, B.Cm, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(launch_average(c, B.Ca, B.Cs, (int)(3 * N3)));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(B.eb, B.em, N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     TRY(launch_average(c, B.eb, B.es, (int)N3));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(B.Va, B.Vm, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     TRY(launch_average(c, B.Va, B.Vs, (int)(3 * N3)));
-    TRY(launch_psi(c, u, B.zero3, B.Va, B.ps, f, B.psi));
+    TRY(launch_psi(c, u, B.Ca, B.Va, B.ps, f, B.psi));
     TRY(viscous_update(c, B.eb, B.psi, B.uts, nullptr, 6));
     // ---- reverse
     // corrector projection: (ub, pb) -> utb (adjoint of the corrector's ut), psb (of p*)
@@ -821,8 +847,9 @@ ebv_status adjoint_step_impl(Ctx *c, const double *u, const double *p, double dt
     TRY(visc_adjoint(c, B, B.eb, B.uts, B.utb, B.psib, B.ebb));
     // corrector psi = rho u + dt (V_avg - grad p* + f), V_avg = (V_m + V_s) / 2:
     // V_s bar = V_m bar = dt psi bar / 2
-    TRY(adj_psi(c, B.psib, dt, 0.5 * dt, ub, B.Vbs, 0, fb));
+    TRY(adj_psi(c, B.psib, dt, 0.5 * dt, ub, B.Vbs, 0, fb, adv ? B.Cbs : nullptr));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(B.Vbm, B.Vbs, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (adv) EBV_CUDA_TRY(c, cudaMemcpyAsync(B.Cbm, B.Cbs, 3 * N3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     TRY(adj_gradp_t(c, B.psib, -dt, B.psb, 1));   // psi is 0 on covered cells; k_gradp_t reads fluid cells
     // eta_avg = (eta_m + eta_s) / 2
     TRY(adj_mask_scale(c, 1, B.ebb, 0.5, B.ebs));
@@ -832,17 +859,20 @@ ebv_status adjoint_step_impl(Ctx *c, const double *u, const double *p, double dt
     EBV_CUDA_TRY(c, cudaMemsetAsync(B.Gb, 0, 9 * N3 * sizeof(double), s));
     TRY(adj_viscous_explicit(c, B.us, B.es, B.Gs, B.Vbs, B.usb, B.ebs, B.Gb, B.ffb, B.DCb, B.tb, B.dudnb));
     TRY(adj_strain_eta(c, B.us, B.ebs, B.Gb, B.usb, B.grads));
+    if (adv)
+        TRY(adj_convective(c, B.us, B.Ss, B.uFs, B.Cbs, B.usb, B.DCb, B.tb, B.ffb, B.Sb, B.uFb, B.phib, B.bbc));
     // predictor projection: (usb, psb) -> utb, pb += (adjoint of p via u1 = ut + c G p)
     TRY(proj_adjoint(c, B, dt, B.usb, B.psb, B.utb, pb));
     // predictor viscous solves with eta_m
     TRY(visc_adjoint(c, B, B.em, B.utm, B.utb, B.psib, B.ebm));
     // predictor psi = rho u + dt (V_m - grad p + f)
-    TRY(adj_psi(c, B.psib, dt, dt, ub, B.Vbm, 1, fb));
+    TRY(adj_psi(c, B.psib, dt, dt, ub, B.Vbm, 1, fb, adv ? B.Cbm : nullptr));
     TRY(adj_gradp_t(c, B.psib, -dt, pb, 1));
     // predictor explicit viscous term and eta, G of u
     EBV_CUDA_TRY(c, cudaMemsetAsync(B.Gb, 0, 9 * N3 * sizeof(double), s));
     TRY(adj_viscous_explicit(c, u, B.em, B.Gm, B.Vbm, ub, B.ebm, B.Gb, B.ffb, B.DCb, B.tb, B.dudnb));
     TRY(adj_strain_eta(c, u, B.ebm, B.Gb, ub, B.grads));
+    if (adv) TRY(adj_convective(c, u, B.Sm, B.uFm, B.Cbm, ub, B.DCb, B.tb, B.ffb, B.Sb, B.uFb, B.phib, B.bbc));
     return EBV_OK;
 }
 

@@ -322,7 +322,9 @@ ebv_status adj_gradp_t(Ctx *c, const double *w, double scale, double *out, int a
 ebv_status adj_nodal_rhs_t(Ctx *c, const double *rb, double *ub);
 ebv_status adj_drag(Ctx *c, const double *eta, double wJ, double *eta_bar, double *dudn_bar, double *p_bar);
 ebv_status adj_psi(Ctx *c, const double *psib, double dt, double vs, double *ub, double *Vb, int vb_acc,
-                   double *fb);
+                   double *fb, double *Cb);
+ebv_status adj_convective(Ctx *c, const double *u, const double *S, const double *uF, const double *Cb, double *ub,
+                          double *DCb, double *tb, double *Fb, double *Sb, double *uFb, double *phib, double *bb);
 ebv_status adj_mask_scale(Ctx *c, int ncomp, const double *b, double s, double *a);
 ebv_status adj_alpha_times(Ctx *c, const double *lam, double *a);
 ebv_status adj_axpby(Ctx *c, int n, double a, const double *x, double b, double *y);

@@ -705,6 +705,71 @@ __global__ void k_nd_prolong(GridD gf, const uint8_t *__restrict__ actf, GridD g
     xout[n] = xin[n] + wi * wj * wk * s;
 }
 
+// ---- level-0 nodal kernels in columns ---------------------------------------------
+// On the finest level most nodes are regular (all 8 cells full), where the row
+// is  ax = (8/3) h x_c - (h/12) (2 fd + bd)  with fd the 12 face-diagonal and
+// bd the 8 body-diagonal neighbours.  Along a column (i, j), plane k's 3x3
+// patch gives P_k (its 4 corners) and E_k (its 4 edge neighbours), and
+//   fd = P_k + E_{k-1} + E_{k+1},   bd = P_{k-1} + P_{k+1},
+// so a thread that walks NZB nodes up a column loads each plane once and
+// forms each row from rolling sums: about half the FP64 arithmetic of the
+// per-node form, which is what bounds the FP64 apply on this GPU (in FP32 the
+// per-node form, with four times the threads in flight, is faster).  Other
+// nodes take nd_row.
+constexpr int NZB = 4;
+
+template <class T>
+__device__ inline void plane_pe(const GridD &g, const T *__restrict__ x, int i, int j, int k, T &P, T &E)
+{
+    if ((unsigned)k > (unsigned)g.nz) { P = T(0); E = T(0); return; }
+    const int NXn = g.nx + 1;
+    const T *c = x + nidx(g, i, j, k);
+    P = (c[-1 - NXn] + c[1 - NXn]) + (c[-1 + NXn] + c[1 + NXn]);
+    E = (c[-1] + c[1]) + (c[-NXn] + c[NXn]);
+}
+
+// q = A p on level 0 with block partials of p.q (k_nd_apply_dot, NZB nodes per thread).
+template <class T>
+__global__ void __launch_bounds__(256) k_nd_apply_dot_col(NdOp<T> A, const T *__restrict__ p, T *__restrict__ q,
+                                                          double *__restrict__ part)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k0 = (blockIdx.z * blockDim.z + threadIdx.z) * NZB;
+    const GridD &g = A.g;
+    double v = 0.0;
+    if (i <= g.nx && j <= g.ny && k0 <= g.nz) {
+        const bool inner = i > 0 && i < g.nx && j > 0 && j < g.ny;
+        const T hh = T(g.h);
+        T Pm = 0, Em = 0, P0 = 0, E0 = 0, Pp = 0, Ep = 0;
+        if (inner) {
+            plane_pe(g, p, i, j, k0 - 1, Pm, Em);
+            plane_pe(g, p, i, j, k0, P0, E0);
+        }
+        for (int h = 0; h < NZB; h++) {
+            const int k = k0 + h;
+            if (k > g.nz) break;
+            if (inner) plane_pe(g, p, i, j, k + 1, Pp, Ep);
+            const int n = nidx(g, i, j, k);
+            T y;
+            if (!A.act[n]) {
+                y = p[n];
+            } else if (inner && A.reg[n]) {
+                y = hh * T(8.0 / 3.0) * p[n] - hh * T(1.0 / 12.0) * (T(2) * (P0 + Em + Ep) + (Pm + Pp));
+            } else {
+                T diag, ax;
+                nd_row(A, i, j, k, p, diag, ax);
+                y = ax;
+            }
+            q[n] = y;
+            v += (double)(p[n] * y);
+            Pm = P0; Em = E0; P0 = Pp; E0 = Ep;
+        }
+    }
+    v = block_sum3(v);
+    if (thread_linear() == 0) part[block_linear()] = v;
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<T> A, const T *__restrict__ p, T *__restrict__ q,
                                                       double *__restrict__ part)
@@ -1106,6 +1171,8 @@ __global__ void k_zero_inactive(int n, const uint8_t *__restrict__ act, double *
 
 inline dim3 cgrid(const GridD &g) { return grid3(g.nx, g.ny, g.nz); }
 inline dim3 ngrid(const GridD &g) { return grid3(g.nx + 1, g.ny + 1, g.nz + 1); }
+// columns of NZB nodes along z (the level-0 nodal kernels)
+inline dim3 ncolgrid(const GridD &g) { return grid3(g.nx + 1, g.ny + 1, (g.nz + NZB) / NZB); }
 inline int nblocks3(dim3 b) { return b.x * b.y * b.z; }
 
 template <class T>
@@ -1301,7 +1368,8 @@ void nd_vcycle(Ctx *c, NdHier &H, const T *b0, T *x0)
 struct Problem {
     virtual ~Problem() {}
     virtual int n() const = 0;
-    virtual int apply_blocks() const = 0;
+    virtual int apply_blocks() const = 0;      // partial sums written by apply_dot
+    virtual int apply_blocks32() const { return apply_blocks(); }   // by apply_dot32
     // q = A p with block partials of p.q in c->part, in FP64 or FP32
     virtual void apply_dot(Ctx *c, const double *p, double *q) = 0;
     virtual void apply_dot32(Ctx *c, const float *p, float *q) = 0;
@@ -1423,9 +1491,13 @@ ebv_status finish_solve(Ctx *c, double *x, int n, int *iters, double *res)
     EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (iters) *iters = (int)c->sstat_host[3 * s];
     if (res) *res = c->sstat_host[3 * s + 1];
-    if (c->ctl_host[C_ERR] == E_NAN) return c->fail(EBV_ERR_NAN, "non-finite residual");
+    if (c->ctl_host[C_ERR] == E_NAN)
+        return c->fail(EBV_ERR_NAN, "non-finite residual (solve slot " + std::to_string(s) + ")");
     if (c->ctl_host[C_ERR] == E_NOTCONV)
-        return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance");
+        return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance (solve slot " +
+                                                  std::to_string(s) + ", relative residual " +
+                                                  std::to_string(c->sstat_host[3 * s + 1]) + ", " +
+                                                  std::to_string((int)c->sstat_host[3 * s]) + " iterations)");
     return EBV_OK;
 }
 
@@ -1510,7 +1582,7 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
             reduce_sum(c, c->part, vblocks(n), c->scal + S_RZ);
             EBV_LAUNCH(c, k_cg_pupdate32, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, c->ctl);
             P.apply_dot32(c, p, q);
-            reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_PQ);
+            reduce_sum(c, c->part, P.apply_blocks32(), c->scal + S_PQ);
             EBV_LAUNCH(c, k_cg_update32, dim3(vblocks(n)), dim3(256), 0, e, r, p, q, c->scal, n, c->ctl, c->part);
             reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
             EBV_LAUNCH(c, k_inner_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 1, inner.h,
@@ -1560,12 +1632,13 @@ struct CcProblem : Problem {
 struct NdProblem : Problem {
     NdHier *H;
     int n() const override { return nnode(H->lv[0].g); }
-    int apply_blocks() const override { return nblocks3(ngrid(H->lv[0].g)); }
+    int apply_blocks() const override { return nblocks3(ncolgrid(H->lv[0].g)); }
+    int apply_blocks32() const override { return nblocks3(ngrid(H->lv[0].g)); }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
         // p, alpha, q: 3 words per node
-        EBV_LAUNCH_P(c, "nodal_apply_fp64", 24.0 * n(), k_nd_apply_dot<double>, ngrid(H->lv[0].g), block3(), 0,
-                     ndop<double>(H->lv[0]), p, q, c->part);
+        EBV_LAUNCH_P(c, "nodal_apply_fp64", 24.0 * n(), k_nd_apply_dot_col<double>, ncolgrid(H->lv[0].g), block3(),
+                     0, ndop<double>(H->lv[0]), p, q, c->part);
     }
     void apply_dot32(Ctx *c, const float *p, float *q) override
     {

@@ -1,10 +1,15 @@
-"""Adjoint of the creeping-flow step (ebv_adjoint_step / ebv_drag_gradient):
-drag sensitivities with respect to the yield stress, the plastic viscosity
-and a per-cell body force, checked against central finite differences of the
-same forward on the GPU (forward solves converged to 1e-13, so the
-difference quotient is accurate to ~1e-7) and of the FP64 oracle's forward.
-Sphere channel, Bingham (Bi = 5, m = 1e3), fixed dt from the CFL limit of the
-initial state, checkpointing every 2 steps."""
+"""Adjoint of the step (ebv_adjoint_step / ebv_drag_gradient), in both forms:
+creeping flow (advect = 0) and with the convective term (advect = 1): drag
+sensitivities with respect to the yield stress, the plastic viscosity and a
+per-cell body force, checked against central finite differences of the same
+forward on the GPU (forward solves converged to 1e-13, so the difference
+quotient is accurate to ~1e-7) and of the FP64 oracle's forward.  Sphere
+channel, Bingham (Bi = 5, m = 1e3), fixed dt from the CFL limit of the
+initial state, checkpointing every 2 steps.  With the convective term the
+limiter and the upwinding are piecewise linear: the seeded noise of the
+initial state keeps their decisions away from ties (a uniform flow would sit
+on the limiter's kink in every cell), so no kink lies within a difference
+step."""
 import numpy as np
 import pytest
 
@@ -26,12 +31,12 @@ def E():
     return ebvisc
 
 
-def _setup(E, precision, newtonian=False):
+def _setup(E, precision, newtonian=False, advect=0):
     from paper_1905_07392_gb300 import workloads as W
     w = W.Workload("adjoint_small", n=N, radius=R, tau0=W.tau0_for_bingham(5.0, R), m=1e3, seed=17)
     if newtonian:
         w = W.Workload("adjoint_small_newtonian", n=N, radius=R, tau0=0.0, model=W.NEWTONIAN, seed=17)
-    s = E.Solver.from_workload(w, precision=precision, tol=1e-13, max_iters=20000, advect=0)
+    s = E.Solver.from_workload(w, precision=precision, tol=1e-13, max_iters=20000, advect=advect)
     alpha = s.geometry()["alpha"]
     fluid = (alpha > 0).to(torch.float64)
     u0 = (torch.tensor(W.initial_velocity(w).reshape(3, -1), device=DEV) * fluid).reshape(-1).contiguous()
@@ -53,9 +58,9 @@ def _fd(fun, x, h):
     return (fun(x + h) - fun(x - h)) / (2 * h)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_drag_gradient_matches_finite_differences(E, precision):
-    w, s, u0, p0, f, dt, fluid = _setup(E, precision)
+@pytest.mark.parametrize("precision,advect", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_drag_gradient_matches_finite_differences(E, precision, advect):
+    w, s, u0, p0, f, dt, fluid = _setup(E, precision, advect=advect)
     J, gt, gm, fb = s.drag_gradient(u0, p0, dt, STEPS, EVERY, f=f)
     assert J == pytest.approx(_objective(s, u0, p0, f, dt), rel=1e-12)
     tau0, mu = s.params["tau0"], s.params["mu"]
@@ -97,14 +102,15 @@ def test_checkpointing_does_not_change_the_gradient(E):
         assert float((fb - outs[0][3]).abs().max()) <= 1e-12 * float(outs[0][3].abs().max())
 
 
-@pytest.mark.parametrize("newtonian,eps,tol", [(True, 1e-3, 1e-9), (False, 1e-7, 1e-5)])
-def test_single_step_adjoint_is_the_transpose(E, newtonian, eps, tol):
+@pytest.mark.parametrize("newtonian,advect,eps,tol", [(True, 0, 1e-3, 1e-9), (False, 0, 1e-7, 1e-5),
+                                                     (False, 1, 1e-7, 1e-5)])
+def test_single_step_adjoint_is_the_transpose(E, newtonian, advect, eps, tol):
     """<w, dS(u) du> = <S'(u)^T w, du>: the reverse pass of one step against a
     central difference of the forward step along a seeded perturbation of
     the initial velocity.  Newtonian: the creeping step is affine in u, so
     the difference is exact up to the solves.  Bingham (m = 1e3): eta varies
     on strain rates of 1/m, so the step must move u by much less than h/m."""
-    w, s, u0, p0, f, dt, fluid = _setup(E, 0, newtonian)
+    w, s, u0, p0, f, dt, fluid = _setup(E, 0, newtonian, advect)
     g = torch.Generator(device="cpu").manual_seed(9)
     du = torch.randn(3 * s.ncell, generator=g, dtype=torch.float64).to(DEV) * fluid.repeat(3)
     wu = torch.randn(3 * s.ncell, generator=g, dtype=torch.float64).to(DEV) * fluid.repeat(3)
@@ -138,10 +144,11 @@ def test_autograd_function(E):
     assert float((fr.grad - fb).abs().max()) <= 1e-12 * float(fb.abs().max())
 
 
-def test_gradient_matches_oracle_finite_differences(E, O):
+@pytest.mark.parametrize("advect", [0, 1])
+def test_gradient_matches_oracle_finite_differences(E, O, advect):
     """Against the FP64 oracle's own forward (same problem, same dt): central
     differences of its time-averaged drag in tau0 and mu."""
-    w, s, u0, p0, f, dt, fluid = _setup(E, 0)
+    w, s, u0, p0, f, dt, fluid = _setup(E, 0, advect=advect)
     J, gt, gm, _ = s.drag_gradient(u0, p0, dt, STEPS, EVERY, f=f, f_grad=False)
     g = O.Grid(n=(N, N, N), h=1.0 / N, bc=w.bc, u_in=w.u_in)
     geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_SPHERE, p=tuple(w.centre) + (R,)))
@@ -149,7 +156,7 @@ def test_gradient_matches_oracle_finite_differences(E, O):
 
     def J_o(tau0, mu):
         P = O.Params(rho=w.rho, mu=mu, tau0=tau0, m=w.m, model=w.model, bi_cfl=w.bingham, tol=1e-13,
-                     max_iters=200000, advect=0)
+                     max_iters=200000, advect=advect)
         u, p = u0h.copy(), np.zeros(g.nnode)
         acc = 0.0
         for _ in range(STEPS):
