@@ -58,6 +58,31 @@ __device__ inline double block_sum3(double v)
     return r;
 }
 
+// Block sum of per-thread partials of type T, returned in FP64.  FP64 keeps
+// FP64 throughout (block_sum3).  FP32 partials are summed in FP32 within the
+// warp (32 terms) and in FP64 across warps: FP64 arithmetic is scarce on this
+// GPU, and per-cell FP64 work in a kernel that streams FP32 data made FP64 the
+// bound of the FP32 operator apply.
+template <class T>
+__device__ inline double block_sum3_t(T v)
+{
+    if constexpr (sizeof(T) == 8) {
+        return block_sum3(v);
+    } else {
+        __shared__ double sm[8];
+        const int t = thread_linear();
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((t & 31) == 0) sm[t >> 5] = (double)v;
+        __syncthreads();
+        double r = 0.0;
+        if (t < 32) {
+            r = t < 8 ? sm[t] : 0.0;
+            for (int o = 4; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+        }
+        return r;
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_reduce_final(const double *part, int n, double *out)
 {
     double v = 0.0;
@@ -150,10 +175,17 @@ __device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__
 // each: every lane works.  All operands of its GS_PZ updates are loaded before
 // any result is stored (the updated cells are never read in the same pass), so
 // the loads of all of them are in flight together.
+// kCorr: the pass that follows the coarse-grid correction.  Since a pass
+// never reads the old value of the cells it updates, prolongation (x += the
+// coarse correction xc of the parent cell, on uncovered cells) is folded into
+// the neighbour reads: x_nb + xc(parent(nb)), the very sums a separate
+// prolongation kernel would store.  A covered neighbour's face coefficient is
+// 0, so adding to it changes nothing either.
 constexpr int GS_PZ = 2;
-template <class T>
+template <class T, bool kCorr = false>
 __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, const T *__restrict__ b,
-                                               int color, int zero_start)
+                                               int color, int zero_start, const T *__restrict__ xc = nullptr,
+                                               GridD gc = GridD())
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -178,10 +210,18 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
             const T bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
             const T byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
             const T bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
-            const T xw = i > 0 ? x[cix<T>(g, i - 1, j, k)] : T(0);
-            const T xe = i < g.nx - 1 ? x[cix<T>(g, i + 1, j, k)] : T(0);
-            const T xs = j > 0 ? x[c - sy] : T(0), xn = j < g.ny - 1 ? x[c + sy] : T(0);
-            const T xd = k > 0 ? x[c - sz] : T(0), xu = k < g.nz - 1 ? x[c + sz] : T(0);
+            auto cor = [&](int ii, int jj, int kq) -> T {
+                return kCorr ? xc[cix<T>(gc, ii >> 1, jj >> 1, kq >> 1)] : T(0);
+            };
+            const T xw = i > 0 ? (kCorr ? x[cix<T>(g, i - 1, j, k)] + cor(i - 1, j, k) : x[cix<T>(g, i - 1, j, k)])
+                               : T(0);
+            const T xe = i < g.nx - 1
+                             ? (kCorr ? x[cix<T>(g, i + 1, j, k)] + cor(i + 1, j, k) : x[cix<T>(g, i + 1, j, k)])
+                             : T(0);
+            const T xs = j > 0 ? (kCorr ? x[c - sy] + cor(i, j - 1, k) : x[c - sy]) : T(0);
+            const T xn = j < g.ny - 1 ? (kCorr ? x[c + sy] + cor(i, j + 1, k) : x[c + sy]) : T(0);
+            const T xd = k > 0 ? (kCorr ? x[c - sz] + cor(i, j, k - 1) : x[c - sz]) : T(0);
+            const T xu = k < g.nz - 1 ? (kCorr ? x[c + sz] + cor(i, j, k + 1) : x[c + sz]) : T(0);
             if (i > 0) off += bxl * xw;
             if (i < g.nx - 1) off += bxh * xe;
             if (j > 0) off += byl * xs;
@@ -221,18 +261,6 @@ __global__ void __launch_bounds__(256) k_cc_resid_restrict(CcOp<T> A, const T *_
         s += b[c] - (diag * x[c] - off);
     }
     bc[cix<T>(gc, I, J, K)] = s * T(0.125);
-}
-
-template <class T>
-__global__ void k_cc_prolong(GridD gf, GridD gc, const uint8_t *__restrict__ cov,
-                             const T *__restrict__ xc, T *__restrict__ xf)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    if (i >= gf.nx || j >= gf.ny || k >= gf.nz) return;
-    if (cov[cidx(gf, i, j, k)]) return;
-    xf[cix<T>(gf, i, j, k)] += xc[cix<T>(gc, i >> 1, j >> 1, k >> 1)];
 }
 
 // Rediscretised coarse operator: face coefficient = (sum of the 4 fine faces) / 16,
@@ -471,9 +499,9 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
     b[c] = geo.alpha[c] * psi[c] + rb;
 }
 
-// q = A p (FP64, level 0) and block partials of p.q
-// (partials of the dot product in FP64 for either precision)
-// Each thread handles planes 2kk and 2kk+1 of column (i, j).
+// q = A p (level 0) and block partials of p.q in FP64 (per thread and warp
+// in T, see block_sum3_t).  Each thread handles planes 2kk and 2kk+1 of
+// column (i, j).
 template <class T>
 __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__restrict__ p, T *__restrict__ q,
                                                       double *__restrict__ part)
@@ -481,7 +509,7 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int kk = blockIdx.z * blockDim.z + threadIdx.z;
-    double v = 0.0;
+    T v = 0;
     if (i < A.g.nx && j < A.g.ny) {
         T y[2], pc[2];
         int cc[2] = {-1, -1};
@@ -499,11 +527,11 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
         for (int h = 0; h < 2; h++)
             if (cc[h] >= 0) {
                 q[cc[h]] = y[h];
-                v += (double)(pc[h] * y[h]);
+                v += pc[h] * y[h];
             }
     }
-    v = block_sum3(v);
-    if (thread_linear() == 0) part[block_linear()] = v;
+    const double vs = block_sum3_t<T>(v);
+    if (thread_linear() == 0) part[block_linear()] = vs;
 }
 
 // ===========================================================================
@@ -778,7 +806,7 @@ __global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<T> A, const T *__rest
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     const GridD &g = A.g;
-    double v = 0.0;
+    T v = 0;
     if (i <= g.nx && j <= g.ny && k <= g.nz) {
         const int n = nidx(g, i, j, k);
         T y;
@@ -790,10 +818,10 @@ __global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<T> A, const T *__rest
             y = ax;
         }
         q[n] = y;
-        v = (double)(p[n] * y);
+        v = p[n] * y;
     }
-    v = block_sum3(v);
-    if (thread_linear() == 0) part[block_linear()] = v;
+    const double vs = block_sum3_t<T>(v);
+    if (thread_linear() == 0) part[block_linear()] = vs;
 }
 
 __global__ void k_nd_alpha_coarsen(GridD gf, const double *__restrict__ af, GridD gc, double *__restrict__ ac)
@@ -1239,7 +1267,8 @@ inline dim3 ch_grid(const GridD &g, dim3 bk)
 }
 
 template <class T>
-void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red_first, bool zero_start)
+void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red_first, bool zero_start,
+                const T *xc = nullptr, const GridD *gc = nullptr)
 {
     (void)t;
     CcOp<T> A = ccop<T>(L);
@@ -1253,8 +1282,12 @@ void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool re
     const char *name = kGsName[sizeof(T) == 4][l < 7 ? l : 7];
     for (int s = 0; s < 2; s++) {
         const int z = (s == 0 && zero_start) ? 1 : 0;
-        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, bk, 0, A, x, b, c0, z);
-        EBV_LAUNCH_P(c, name, nb, k_cc_gs<T>, gr, bk, 0, A, x, b, 1 - c0, 0);
+        if (s == 0 && xc)  // the first pass after the coarse-grid correction (+ the coarse array)
+            EBV_LAUNCH_P(c, name, nb + 0.125 * sizeof(T) * (double)ncell(g), (k_cc_gs<T, true>), gr, bk, 0, A, x, b,
+                         c0, z, xc, *gc);
+        else
+            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, c0, z, nullptr, GridD());
+        EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, 1 - c0, 0, nullptr, GridD());
     }
 }
 
@@ -1283,9 +1316,8 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         const CcLevel &L = H.lv[l];
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
-        EBV_LAUNCH(c, k_cc_prolong<T>, cgrid(L.g), block3(), 0, L.g, H.lv[l + 1].g, L.cov,
-                   (const T *)c->lx[l + 1], x);
-        cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, false, false);
+        // prolongation folded into the first colour pass of the post-smoothing
+        cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, false, false, (const T *)c->lx[l + 1], &H.lv[l + 1].g);
     }
 }
 
@@ -1877,7 +1909,7 @@ ebv_status autotune_shapes_t(Ctx *c)
         float best = 1e30f;
         for (int q = 0; q < nc; q++) {
             const dim3 bk = cand[q], gr = gs_grid(L.g, bk);
-            float ms = time_it([&]() { k_cc_gs<T><<<gr, bk, 0, c->stream>>>(A, x, b, 0, 0); });
+            float ms = time_it([&]() { k_cc_gs<T, false><<<gr, bk, 0, c->stream>>>(A, x, b, 0, 0, nullptr, GridD()); });
             if (ms < best) { best = ms; L.gs_blk = bk; }
         }
         c->visc.lv[l].gs_blk = L.gs_blk;
