@@ -182,6 +182,44 @@ __device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__
 // prolongation kernel would store.  A covered neighbour's face coefficient is
 // 0, so adding to it changes nothing either.
 constexpr int GS_PZ = 2;
+
+// The Gauss-Seidel value of cell (i,j,k): (b + sum beta x_nb) / diag, 0 on
+// cells with no diagonal (see k_cc_gs for kCorr and zero_start).
+template <class T, bool kCorr>
+__device__ inline T gs_cell(const CcOp<T> &A, const T *__restrict__ x, const T *__restrict__ b, int i, int j,
+                            int k, int zero_start, const T *__restrict__ xc, const GridD &gc)
+{
+    const GridD &g = A.g;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    const int c = cix<T>(g, i, j, k);
+    const T diag = A.diag[c], bc = b[c];
+    T off = 0;
+    if (!zero_start) {
+        const T bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
+        const T byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
+        const T bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
+        auto cor = [&](int ii, int jj, int kq) -> T {
+            return kCorr ? xc[cix<T>(gc, ii >> 1, jj >> 1, kq >> 1)] : T(0);
+        };
+        const T xw = i > 0 ? (kCorr ? x[cix<T>(g, i - 1, j, k)] + cor(i - 1, j, k) : x[cix<T>(g, i - 1, j, k)])
+                           : T(0);
+        const T xe = i < g.nx - 1
+                         ? (kCorr ? x[cix<T>(g, i + 1, j, k)] + cor(i + 1, j, k) : x[cix<T>(g, i + 1, j, k)])
+                         : T(0);
+        const T xs = j > 0 ? (kCorr ? x[c - sy] + cor(i, j - 1, k) : x[c - sy]) : T(0);
+        const T xn = j < g.ny - 1 ? (kCorr ? x[c + sy] + cor(i, j + 1, k) : x[c + sy]) : T(0);
+        const T xd = k > 0 ? (kCorr ? x[c - sz] + cor(i, j, k - 1) : x[c - sz]) : T(0);
+        const T xu = k < g.nz - 1 ? (kCorr ? x[c + sz] + cor(i, j, k + 1) : x[c + sz]) : T(0);
+        if (i > 0) off += bxl * xw;
+        if (i < g.nx - 1) off += bxh * xe;
+        if (j > 0) off += byl * xs;
+        if (j < g.ny - 1) off += byh * xn;
+        if (k > 0) off += bzl * xd;
+        if (k < g.nz - 1) off += bzh * xu;
+    }
+    return diag > T(0) ? (bc + off) / diag : T(0);
+}
+
 template <class T, bool kCorr = false>
 __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, const T *__restrict__ b,
                                                int color, int zero_start, const T *__restrict__ xc = nullptr,
@@ -192,7 +230,6 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
     const int kk = blockIdx.z * blockDim.z + threadIdx.z;
     const GridD &g = A.g;
     if (2 * t >= g.nx || j >= g.ny) return;
-    const int sy = g.nx, sz = g.nx * g.ny;
     T val[GS_PZ];
     int cc[GS_PZ];
 #pragma unroll
@@ -202,34 +239,8 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
         cc[h] = -1;
         val[h] = T(0);
         if (k >= g.nz || i >= g.nx) continue;
-        const int c = cix<T>(g, i, j, k);
-        cc[h] = c;
-        const T diag = A.diag[c], bc = b[c];
-        T off = 0;
-        if (!zero_start) {
-            const T bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
-            const T byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
-            const T bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
-            auto cor = [&](int ii, int jj, int kq) -> T {
-                return kCorr ? xc[cix<T>(gc, ii >> 1, jj >> 1, kq >> 1)] : T(0);
-            };
-            const T xw = i > 0 ? (kCorr ? x[cix<T>(g, i - 1, j, k)] + cor(i - 1, j, k) : x[cix<T>(g, i - 1, j, k)])
-                               : T(0);
-            const T xe = i < g.nx - 1
-                             ? (kCorr ? x[cix<T>(g, i + 1, j, k)] + cor(i + 1, j, k) : x[cix<T>(g, i + 1, j, k)])
-                             : T(0);
-            const T xs = j > 0 ? (kCorr ? x[c - sy] + cor(i, j - 1, k) : x[c - sy]) : T(0);
-            const T xn = j < g.ny - 1 ? (kCorr ? x[c + sy] + cor(i, j + 1, k) : x[c + sy]) : T(0);
-            const T xd = k > 0 ? (kCorr ? x[c - sz] + cor(i, j, k - 1) : x[c - sz]) : T(0);
-            const T xu = k < g.nz - 1 ? (kCorr ? x[c + sz] + cor(i, j, k + 1) : x[c + sz]) : T(0);
-            if (i > 0) off += bxl * xw;
-            if (i < g.nx - 1) off += bxh * xe;
-            if (j > 0) off += byl * xs;
-            if (j < g.ny - 1) off += byh * xn;
-            if (k > 0) off += bzl * xd;
-            if (k < g.nz - 1) off += bzh * xu;
-        }
-        val[h] = diag > T(0) ? (bc + off) / diag : T(0);
+        cc[h] = cix<T>(g, i, j, k);
+        val[h] = gs_cell<T, kCorr>(A, x, b, i, j, k, zero_start, xc, gc);
     }
 #pragma unroll
     for (int h = 0; h < GS_PZ; h++) {
@@ -242,6 +253,22 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
     }
 }
 
+// Residual of the 8 children of coarse cell (I,J,K), averaged.
+template <class T>
+__device__ inline T rr_cell(const CcOp<T> &A, const T *__restrict__ x, const T *__restrict__ b, int I, int J,
+                            int K)
+{
+    T s = 0;
+    for (int o = 0; o < 8; o++) {
+        int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
+        T diag, off;
+        cc_row(A, i, j, k, x, diag, off);
+        int c = cix<T>(A.g, i, j, k);
+        s += b[c] - (diag * x[c] - off);
+    }
+    return s * T(0.125);
+}
+
 // Residual of the 8 children, averaged into the coarse right-hand side.
 template <class T>
 __global__ void __launch_bounds__(256) k_cc_resid_restrict(CcOp<T> A, const T *__restrict__ x,
@@ -252,15 +279,7 @@ __global__ void __launch_bounds__(256) k_cc_resid_restrict(CcOp<T> A, const T *_
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
-    T s = 0;
-    for (int o = 0; o < 8; o++) {
-        int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
-        T diag, off;
-        cc_row(A, i, j, k, x, diag, off);
-        int c = cix<T>(A.g, i, j, k);
-        s += b[c] - (diag * x[c] - off);
-    }
-    bc[cix<T>(gc, I, J, K)] = s * T(0.125);
+    bc[cix<T>(gc, I, J, K)] = rr_cell<T>(A, x, b, I, J, K);
 }
 
 // Rediscretised coarse operator: face coefficient = (sum of the 4 fine faces) / 16,
@@ -948,19 +967,93 @@ __global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, i
 
 // x = scale inv b; the dense system is numbered in the natural order, the
 // vectors of a row-split (FP32 cell-centred) level are mapped through g.
+__device__ inline int bottom_pos(const GridD &g, int split, int r)
+{
+    if (!split) return r;
+    return cix<float>(g, r % g.nx, (r / g.nx) % g.ny, r / (g.nx * g.ny));
+}
+template <class T>
+__device__ inline void bottom_row(const double *__restrict__ inv, int nb, const T *__restrict__ b,
+                                  T *__restrict__ x, double scale, const GridD &g, int split, int r)
+{
+    double s = 0.0;
+    for (int q = 0; q < nb; q++) s += inv[(size_t)r * nb + q] * (double)b[bottom_pos(g, split, q)];
+    x[bottom_pos(g, split, r)] = (T)(s * scale);
+}
 template <class T>
 __global__ void __launch_bounds__(256) k_bottom_solve(const double *__restrict__ inv, int nb,
                                                       const T *__restrict__ b, T *__restrict__ x,
                                                       double scale, GridD g, int split)
 {
-    auto pos = [&](int r) {
-        if (!split) return r;
-        return cix<float>(g, r % g.nx, (r / g.nx) % g.ny, r / (g.nx * g.ny));
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x)
+        bottom_row(inv, nb, b, x, scale, g, split, r);
+}
+
+// ---- the coarse end of the cell-centred V-cycle in one CTA ------------------------
+// Levels of at most kCoarseCells cells cannot fill the GPU, and as separate
+// launches they cost more in launch latency than in work.  Below such a
+// level one persistent block of 1024 threads runs the rest of the V-cycle --
+// pre-smoothing, residual and restriction down to the bottom, the bottom
+// solve, then correction and post-smoothing back up -- with the same steps
+// and per-cell arithmetic as the per-level kernels (gs_cell, rr_cell,
+// bottom_row) and a block barrier wherever those have a kernel boundary, so
+// its results are bit for bit those of the per-level path.
+constexpr int kCoarseCells = 4096;
+constexpr int kCoarseMax = 8;
+template <class T>
+struct CoarseVC {
+    int n;                    // levels handled; the last is the bottom
+    CcOp<T> A[kCoarseMax];
+    T *x[kCoarseMax];
+    T *b[kCoarseMax];         // b[0] given, the others written by restriction
+    const double *binv;       // bottom inverse (natural numbering)
+    int nb;
+};
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_cc_coarse_vcycle(CoarseVC<T> D)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // one colour pass on level l (first = the pass after the coarse correction)
+    auto pass = [&](int l, int color, int zero_start, bool first_up) {
+        const CcOp<T> &A = D.A[l];
+        const GridD &g = A.g;
+        const int n = ncell(g);
+        T *x = D.x[l];
+        for (int s = tid; s < n; s += nt) {
+            const int i = s % g.nx, j = (s / g.nx) % g.ny, k = s / (g.nx * g.ny);
+            if (((i + j + k) & 1) == color)
+                x[cix<T>(g, i, j, k)] = first_up ? gs_cell<T, true>(A, x, D.b[l], i, j, k, 0, D.x[l + 1], D.A[l + 1].g)
+                                                 : gs_cell<T, false>(A, x, D.b[l], i, j, k, zero_start, x, g);
+            else if (zero_start)
+                x[cix<T>(g, i, j, k)] = T(0);
+        }
+        __syncthreads();
     };
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int q = 0; q < nb; q++) s += inv[(size_t)r * nb + q] * (double)b[pos(q)];
-        x[pos(r)] = (T)(s * scale);
+    const int L = D.n - 1;
+    for (int l = 0; l < L; l++) {
+        // two red-black sweeps, red first, the first from zero
+        pass(l, 0, 1, false);
+        pass(l, 1, 0, false);
+        pass(l, 0, 0, false);
+        pass(l, 1, 0, false);
+        const GridD &gc = D.A[l + 1].g;
+        const int nc = ncell(gc);
+        for (int s = tid; s < nc; s += nt) {
+            const int I = s % gc.nx, J = (s / gc.nx) % gc.ny, K = s / (gc.nx * gc.ny);
+            D.b[l + 1][cix<T>(gc, I, J, K)] = rr_cell<T>(D.A[l], D.x[l], D.b[l], I, J, K);
+        }
+        __syncthreads();
+    }
+    for (int r = tid; r < D.nb; r += nt)
+        bottom_row(D.binv, D.nb, D.b[L], D.x[L], 1.0, D.A[L].g, (int)(sizeof(T) == 4), r);
+    __syncthreads();
+    for (int l = L - 1; l >= 0; l--) {
+        // two sweeps, black first; the first pass takes the coarse correction
+        pass(l, 1, 0, true);
+        pass(l, 0, 0, false);
+        pass(l, 1, 0, false);
+        pass(l, 0, 0, false);
     }
 }
 
@@ -1295,7 +1388,10 @@ template <class T>
 void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
 {
     const int Lb = H.L - 1;
-    for (int l = 0; l < Lb; l++) {
+    // levels l0 .. Lb (each at most kCoarseCells cells) run in one CTA
+    int l0 = Lb;
+    while (l0 > 0 && ncell(H.lv[l0 - 1].g) <= kCoarseCells && Lb - l0 + 2 <= kCoarseMax) l0--;
+    for (int l = 0; l < l0; l++) {
         const CcLevel &L = H.lv[l];
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
@@ -1306,13 +1402,26 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
                      k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, ccop<T>(L), x, b, Lc.g,
                      (T *)c->lb[l + 1]);
     }
-    {
+    if (l0 < Lb) {
+        CoarseVC<T> D;
+        D.n = Lb - l0 + 1;
+        for (int q = 0; q < D.n; q++) {
+            const int l = l0 + q;
+            D.A[q] = ccop<T>(H.lv[l]);
+            D.x[q] = l ? (T *)c->lx[l] : x0;
+            D.b[q] = l ? (T *)c->lb[l] : (T *)b0;
+        }
+        D.binv = H.binv;
+        D.nb = H.nb;
+        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_coarse_vcycle<float>" : "cc_coarse_vcycle<double>", 0.0,
+                     k_cc_coarse_vcycle<T>, dim3(1), dim3(1024), 0, D);
+    } else {
         T *x = Lb ? (T *)c->lx[Lb] : x0;
         const T *b = Lb ? (const T *)c->lb[Lb] : b0;
         EBV_LAUNCH(c, k_bottom_solve<T>, dim3((H.nb + 255) / 256), dim3(256), 0, H.binv, H.nb, b, x, 1.0,
                    H.lv[Lb].g, (int)(sizeof(T) == 4));
     }
-    for (int l = Lb - 1; l >= 0; l--) {
+    for (int l = l0 - 1; l >= 0; l--) {
         const CcLevel &L = H.lv[l];
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
