@@ -576,6 +576,19 @@ struct NdOp {
 // each face-diagonal neighbour -(sum of the two cells sharing that edge)/12;
 // each body-diagonal neighbour -(the one cell between them)/12.  Inactive
 // neighbours hold x = 0 in every vector the solvers pass here.
+// Sums of the 12 face-diagonal (fd) and 8 body-diagonal (bd) neighbours of
+// interior node n.
+template <class T>
+__device__ inline void nd_regular_sums(const GridD &g, const T *__restrict__ x, int n, T &fd, T &bd)
+{
+    const T *xc = x + n;
+    const int sy = g.nx + 1, sz = (g.nx + 1) * (g.ny + 1);
+    fd = xc[1 + sy] + xc[-1 + sy] + xc[1 - sy] + xc[-1 - sy] + xc[1 + sz] + xc[-1 + sz] + xc[1 - sz] +
+         xc[-1 - sz] + xc[sy + sz] + xc[-sy + sz] + xc[sy - sz] + xc[-sy - sz];
+    bd = xc[1 + sy + sz] + xc[-1 + sy + sz] + xc[1 - sy + sz] + xc[-1 - sy + sz] + xc[1 + sy - sz] +
+         xc[-1 + sy - sz] + xc[1 - sy - sz] + xc[-1 - sy - sz];
+}
+
 template <class T>
 __device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__restrict__ x, T &diag,
                               T &ax)
@@ -586,15 +599,11 @@ __device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__
         // all 8 cells full (so the node is interior): the constant stencil
         // 8/3 at the centre, -1/6 on the 12 face diagonals, -1/12 on the 8
         // body diagonals (times h)
-        const T *xc = x + nidx(g, i, j, k);
-        const int sy = NXn, sz = NXn * NYn;
-        T fd = xc[1 + sy] + xc[-1 + sy] + xc[1 - sy] + xc[-1 - sy] + xc[1 + sz] + xc[-1 + sz] + xc[1 - sz] +
-               xc[-1 - sz] + xc[sy + sz] + xc[-sy + sz] + xc[sy - sz] + xc[-sy - sz];
-        T bd = xc[1 + sy + sz] + xc[-1 + sy + sz] + xc[1 - sy + sz] + xc[-1 - sy + sz] + xc[1 + sy - sz] +
-               xc[-1 + sy - sz] + xc[1 - sy - sz] + xc[-1 - sy - sz];
+        T fd, bd;
+        nd_regular_sums(g, x, nidx(g, i, j, k), fd, bd);
         const T hh = T(g.h);
         diag = hh * T(8.0 / 3.0);
-        ax = diag * xc[0] - hh * T(1.0 / 12.0) * (T(2) * fd + bd);
+        ax = diag * x[nidx(g, i, j, k)] - hh * T(1.0 / 12.0) * (T(2) * fd + bd);
         return;
     }
     T a[2][2][2];
@@ -651,7 +660,19 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
     const GridD &g = A.g;
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const int n = nidx(g, i, j, k);
-    if (!A.act[n]) {
+    // Every load the node can need is issued before any branch on them (one
+    // round trip to memory instead of act -> reg -> stencil -> b, d): the
+    // regular stencil's sums are formed speculatively on interior nodes.
+    const uint8_t on = A.act[n];
+    const uint8_t rg = (A.reg && !zero_start) ? A.reg[n] : 0;
+    const T bn = b[n];
+    T fd = T(0), bd = T(0), xn = T(0), dold = T(0);
+    if (!zero_start) {
+        xn = xin[n];
+        dold = dvec[n];
+        if (A.reg && i > 0 && i < g.nx && j > 0 && j < g.ny && k > 0 && k < g.nz) nd_regular_sums(g, xin, n, fd, bd);
+    }
+    if (!on) {
         xout[n] = T(0);
         dvec[n] = T(0);
         return;
@@ -667,16 +688,22 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
             if (al > T(0)) dsum += al;
         }
         diag = T(g.h) * dsum * T(1.0 / 3.0);
-        T dn = cr * b[n] / diag;
+        T dn = cr * bn / diag;
         dvec[n] = dn;
         xout[n] = dn;
         return;
     }
-    nd_row(A, i, j, k, xin, diag, ax);
-    T r = b[n] - ax;
-    T dn = (cd != T(0) ? cd * dvec[n] : T(0)) + cr * r / diag;
+    if (rg) {   // regular nodes are interior: the sums above are theirs
+        const T hh = T(g.h);
+        diag = hh * T(8.0 / 3.0);
+        ax = diag * xn - hh * T(1.0 / 12.0) * (T(2) * fd + bd);
+    } else {
+        nd_row(A, i, j, k, xin, diag, ax);
+    }
+    T r = bn - ax;
+    T dn = (cd != T(0) ? cd * dold : T(0)) + cr * r / diag;
     dvec[n] = dn;
-    xout[n] = xin[n] + dn;
+    xout[n] = xn + dn;
 }
 
 template <class T>
