@@ -211,7 +211,7 @@ def roofline(prof, cells):
     ks = {k: v for k, v in prof.items() if v["launches"] > 0}
     total = sum(v["ms"] for v in ks.values())
     kernels = {}
-    for k, f in sorted(ks.items(), key=lambda kv: -kv[1]["ms"])[:14]:
+    for k, f in sorted(ks.items(), key=lambda kv: -kv[1]["ms"])[:24]:
         e = {"launches": f["launches"], "ms": round(f["ms"], 3),
              "share": round(f["ms"] / total, 4)}
         if f["bytes"] > 0:

@@ -273,11 +273,15 @@ __global__ void __launch_bounds__(256) k_conv_flux(GridD g, int d, const double 
         return;
     }
     const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
+    // only the upwind side's state is formed (fewer FP64 operations)
+    const double aw = a * w;
     for (int q = 0; q < 3; q++) {
-        double sL = u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL];
-        double sR = u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR];
-        double state = w > 0.0 ? sL : (w < 0.0 ? sR : 0.5 * (sL + sR));
-        F[q * nft + off + f] = a * state * w;
+        double state;
+        if (w > 0.0) state = u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL];
+        else if (w < 0.0) state = u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR];
+        else state = 0.5 * ((u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL]) +
+                            (u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR]));
+        F[q * nft + off + f] = aw * state;
     }
 }
 
@@ -518,11 +522,13 @@ __global__ void __launch_bounds__(256) k_visc_flux(GridD g, int d, const double 
         return;
     }
     const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
-    const double ef = 0.5 * (eta[cL] + eta[cR]);
+    // W = a eta_f; the normal derivative's 1/h and the transverse mean's 1/2
+    // are folded into W once (fewer FP64 operations)
+    const double W = (0.5 * a) * (eta[cL] + eta[cR]);
+    const double Wn = W * ih, Wt = 0.5 * W;
     for (int jj = 0; jj < 3; jj++) {
-        double der = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) * ih
-                               : 0.5 * (G[(3 * jj + d) * N3 + cL] + G[(3 * jj + d) * N3 + cR]);
-        F[jj * nft + off + f] = a * (ef * der);
+        F[jj * nft + off + f] = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) * Wn
+                                          : (G[(3 * jj + d) * N3 + cL] + G[(3 * jj + d) * N3 + cR]) * Wt;
     }
 }
 
