@@ -561,15 +561,15 @@ __global__ void k_gradp_t(GridD g, const uint8_t *__restrict__ flag, const doubl
 }
 
 // ---- nodal right-hand side, transposed in ut: ub(d, c) += sum over the
-// active corner nodes of alpha h^2/4 (+-1) rb(n) / (dt/rho).
+// active corner nodes of alpha h^2/4 (+-1) rb(n) rho/dt.
 __global__ void k_nodal_rhs_t(GridD g, GeomD geo, const uint8_t *__restrict__ act, const double *__restrict__ rb,
-                              const double *__restrict__ dtp, double rho, double *__restrict__ ub)
+                              const double *__restrict__ dtp, double *__restrict__ ub)
 {
     ADJ_CELL
     if (geo.flag[c] == 0) return;
     const int N3 = geo.ncell;
     const double h = g.h;
-    const double wgt = geo.alpha[c] * h * h * 0.25 / (*dtp / rho);
+    const double wgt = geo.alpha[c] * h * h * 0.25 * dtp[DT_RHO_DT];
     double s[3] = {0.0, 0.0, 0.0};
     for (int oc = 0; oc < 8; oc++) {
         const int o[3] = {oc & 1, (oc >> 1) & 1, (oc >> 2) & 1};
@@ -1017,7 +1017,7 @@ ebv_status adj_nodal_rhs_t(Ctx *c, const double *rb, double *ub)
 {
     const GridD &g = c->g;
     EBV_LAUNCH(c, k_nodal_rhs_t, grid3(g.nx, g.ny, g.nz), block3(), 0, g, geomd(c), c->nd.lv[0].act, rb, c->dt_dev,
-               c->prm.rho, ub);
+               ub);
     return EBV_OK;
 }
 

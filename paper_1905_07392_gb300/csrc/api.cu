@@ -65,15 +65,15 @@ ebv_status need_geom(Ctx *c)
     return EBV_OK;
 }
 
-__global__ void k_set_scalar(double *dst, double v)
+__global__ void k_set_dt(double *d, double dt, double rho, double h)
 {
-    if (threadIdx.x == 0) *dst = v;
+    if (threadIdx.x == 0) store_dt(d, dt, rho, h);
 }
 
 ebv_status set_dt(Ctx *c, double dt)
 {
     if (!(dt > 0.0)) return c->fail(EBV_ERR_INVALID, "dt must be > 0");
-    EBV_LAUNCH(c, k_set_scalar, dim3(1), dim3(32), 0, c->dt_dev, dt);
+    EBV_LAUNCH(c, k_set_dt, dim3(1), dim3(32), 0, c->dt_dev, dt, c->prm.rho, c->g.h);
     return EBV_OK;
 }
 
@@ -116,11 +116,12 @@ ebv_status viscous_update(Ctx *c, const double *eta, const double *psi, double *
 {
     const int N3 = ncell(c->g);
     EBV_LAUNCH(c, k_init_guess, dim3(kReduceBlocks), dim3(256), 0, N3, c->flag, psi, c->prm.rho, ut);
+    TRY(visc_build(c, eta));
     for (int q = 0; q < 3; q++) {
         int it = 0;
         double res = 0.0;
         c->cur_slot = slot + q;
-        TRY(visc_solve(c, eta, psi + (size_t)q * N3, q, ut + (size_t)q * N3, &it, &res));
+        TRY(visc_solve(c, psi + (size_t)q * N3, q, ut + (size_t)q * N3, &it, &res));
         if (st) { st->iters[slot + q] = it; st->res[slot + q] = res; }
     }
     return EBV_OK;
@@ -427,7 +428,7 @@ ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stre
           alloc(&c->DC, 3 * N3) && alloc(&c->dD, 3 * N3) && alloc(&c->Dh, 3 * N3) && alloc(&c->wts, N3) &&
           alloc(&c->srate, N3) && alloc(&c->rhs_c, std::max(N3, (size_t)1)) && alloc(&c->rhs_n, NN);
     ok &= alloc(&c->nearm, N3) && alloc(&c->ff, 3 * NF);
-    ok &= alloc(&c->dt_dev, 1) && alloc(&c->cfl_max, 2);
+    ok &= alloc(&c->dt_dev, DT_NSCALAR) && alloc(&c->cfl_max, 2);
     ok &= alloc(&c->u_host_dev, 3 * N3) && alloc(&c->p_host_dev, NN);
     ok &= alloc(&c->kr, V) && alloc(&c->kz, V) && alloc(&c->kp, V) && alloc(&c->kq, V);
     ok &= alloc(&c->kr32, V) && alloc(&c->kz32, V) && alloc(&c->kp32, V) && alloc(&c->kq32, V) &&
@@ -650,11 +651,12 @@ void ebv_destroy(ebv_ctx *c)
         CcHier *H = hs[h];
         for (int l = 0; l < H->L; l++) {
             CcLevel &L = H->lv[l];
-            cudaFree(L.extra_d); cudaFree(L.extra_f); cudaFree(L.diag_d); cudaFree(L.diag_f);
+            cudaFree(L.extra_d); cudaFree(L.extra_f);
+            for (int q = 0; q < H->nvar; q++) { cudaFree(H->vdiag_d[q][l]); cudaFree(H->vdiag_f[q][l]); }
             for (int d = 0; d < 3; d++) { cudaFree(L.bf_d[d]); cudaFree(L.bf_f[d]); }
             if (h == 0) cudaFree(L.cov);
         }
-        cudaFree(H->binv);
+        for (int q = 0; q < H->nvar; q++) cudaFree(H->vbinv[q]);
         cudaFree(H->bmat);
     }
     for (int l = 0; l < c->nd.L; l++) {
@@ -776,11 +778,12 @@ ebv_status visc_adjoint(Ctx *c, AdjBufs &B, const double *eta, const double *x, 
                         double *etab)
 {
     const size_t N3 = ncell(c->g);
+    TRY(visc_build(c, eta));
     for (int q = 0; q < 3; q++) {
         int it = 0;
         double res = 0.0;
         c->cur_slot = 12;
-        TRY(visc_solve_rhs(c, eta, q, xb + q * N3, B.lam, &it, &res));
+        TRY(visc_solve_rhs(c, q, xb + q * N3, B.lam, &it, &res));
         TRY(adj_alpha_times(c, B.lam, psib + q * N3));
         TRY(adj_visc_eta(c, q, B.lam, x + q * N3, etab));
     }

@@ -97,6 +97,17 @@ __host__ __device__ inline bool side_dirichlet(const GridD &g, int side, int com
     }
 }
 
+// The device-side time step: dt and the scalars every cell would otherwise
+// derive from it with an FP64 division, computed once where dt is set.
+enum { DT_DT = 0, DT_DT_RHO = 1, DT_RHO_DT = 2, DT_DTH2 = 3, DT_NSCALAR = 4 };
+__device__ inline void store_dt(double *d, double dt, double rho, double h)
+{
+    d[DT_DT] = dt;
+    d[DT_DT_RHO] = dt / rho;
+    d[DT_RHO_DT] = rho / dt;
+    d[DT_DTH2] = dt / (h * h);
+}
+
 // Apparent viscosity of the rheology table.
 __device__ inline double eta_of(const ParamsD &p, double sr)
 {
@@ -136,10 +147,30 @@ struct CcLevel {
 struct CcHier {
     int L = 0;                 // number of levels (level L-1 is the bottom)
     CcLevel lv[kMaxLevels];
-    double *binv = nullptr;    // bottom inverse, nb x nb
-    double *bmat = nullptr;    // scratch for the bottom factorisation, nb x 2nb
+    double *binv = nullptr;    // bottom inverse of the selected variant, nb x nb
+    double *bmat = nullptr;    // scratch for the bottom factorisations, nvar x nb x 2nb
     int nb = 0;
+    // Variants of one operator that differ only in which box faces enter the
+    // diagonal (the three velocity components of the viscous solve: a slip
+    // wall is a Dirichlet side for the normal component only).  A box face
+    // couples no two cells, so extra and the face arrays are shared; each
+    // variant has its own diagonals and bottom inverse, and select_variant()
+    // points lv[].diag_d / diag_f and binv at those of one variant.
+    int nvar = 1;
+    unsigned side_mask[3] = {0x3fu, 0x3fu, 0x3fu};  // bit s: box side s enters the diagonal
+    double *vdiag_d[3][kMaxLevels] = {};
+    float *vdiag_f[3][kMaxLevels] = {};
+    double *vbinv[3] = {};
 };
+
+inline void select_variant(CcHier &H, int q)
+{
+    for (int l = 0; l < H.L; l++) {
+        H.lv[l].diag_d = H.vdiag_d[q][l];
+        H.lv[l].diag_f = H.vdiag_f[q][l];
+    }
+    H.binv = H.vbinv[q];
+}
 
 struct NdLevel {
     GridD g;                     // cell dims of this level
@@ -202,7 +233,7 @@ struct Ctx {
     double *rhs_c = nullptr;     // cell rhs scratch
     double *rhs_n = nullptr;     // nodal rhs scratch
     double *u_host_dev = nullptr, *p_host_dev = nullptr;  // device copies for host-buffer steps
-    double *dt_dev = nullptr;    // device-side time step
+    double *dt_dev = nullptr;    // device-side time step and its derived scalars (DT_*)
     unsigned long long *cfl_max = nullptr;  // [0] convective, [1] forcing (bit patterns)
 
     // solvers
@@ -333,13 +364,15 @@ ebv_status adj_zero_inactive_nodes(Ctx *c, double *x);
 ebv_status setup_solvers(Ctx *c);
 ebv_status setup_geometry_solvers(Ctx *c);
 ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res);
-ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int comp, double *x,
-                      int *iters, double *res);
+// operators A_q(eta) of the three viscous solves (q = velocity component):
+// shared coefficients, per-component diagonals and bottom inverses
+ebv_status visc_build(Ctx *c, const double *eta);
+// A_q x = alpha psi_q + boundary terms, after visc_build
+ebv_status visc_solve(Ctx *c, const double *psi_comp, int comp, double *x, int *iters, double *res);
 ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *res);
-// A(eta) x = rhs for velocity component comp (the viscous operator with the
-// given right-hand side instead of alpha psi + boundary terms), from x = 0
-ebv_status visc_solve_rhs(Ctx *c, const double *eta, int comp, const double *rhs, double *x, int *iters,
-                          double *res);
+// A_q x = rhs (the viscous operator with the given right-hand side instead of
+// alpha psi + boundary terms), from x = 0, after visc_build
+ebv_status visc_solve_rhs(Ctx *c, int comp, const double *rhs, double *x, int *iters, double *res);
 // reductions (solvers.cu)
 ebv_status reduce_sum(Ctx *c, const double *part, int nblocks, double *out_dev);
 

@@ -571,9 +571,9 @@ __global__ void k_psi(GridD g, const uint8_t *__restrict__ flag, const double *_
 }
 
 // u += sgn * (dt/rho) grad p on fluid cells; covered cells set to zero.
+// (dt/rho) / (4h) scales the pair sums of grad_p3 in one product.
 __global__ void k_add_gradp(GridD g, const uint8_t *__restrict__ flag, double *__restrict__ u,
-                            const double *__restrict__ p, const double *__restrict__ dtp,
-                            double rho, double sgn)
+                            const double *__restrict__ p, const double *__restrict__ dtp, double sgn)
 {
     CELL_INDEX
     const int N3 = ncell(g);
@@ -581,12 +581,11 @@ __global__ void k_add_gradp(GridD g, const uint8_t *__restrict__ flag, double *_
         for (int q = 0; q < 3; q++) u[q * N3 + c] = 0.0;
         return;
     }
-    const double coef = *dtp / rho;
     double gr[3];
-    grad_p3(g, p, i, j, k, 0.25 * g.ih, gr);
+    grad_p3(g, p, i, j, k, dtp[DT_DT_RHO] * (0.25 * g.ih), gr);
     for (int q = 0; q < 3; q++) {
         int s = q * N3 + c;
-        u[s] = sgn > 0 ? u[s] + coef * gr[q] : u[s] - coef * gr[q];
+        u[s] = sgn > 0 ? u[s] + gr[q] : u[s] - gr[q];
     }
 }
 
@@ -601,9 +600,9 @@ __device__ inline bool node_dirichlet(const GridD &g, int i, int j, int k)
 }
 
 // Nodal right-hand side (weak divergence of ut plus the inflow boundary
-// integral), divided by dt/rho so the solve uses the unit-coefficient operator.
+// integral), times rho/dt so the solve uses the unit-coefficient operator.
 __global__ void k_nodal_rhs(GridD g, GeomD geo, const double *__restrict__ ut,
-                            const double *__restrict__ dtp, double rho, double *__restrict__ b)
+                            const double *__restrict__ dtp, double *__restrict__ b)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -653,7 +652,7 @@ __global__ void k_nodal_rhs(GridD g, GeomD geo, const double *__restrict__ ut,
                     v -= sgn * g.u_in[d] * af * h * h * 0.25;
                 }
         }
-    b[n] = v / (*dtp / rho);
+    b[n] = v * dtp[DT_RHO_DT];
 }
 
 // ---- time step --------------------------------------------------------------
@@ -679,15 +678,15 @@ __global__ void k_cfl_max(GridD g, const uint8_t *__restrict__ flag, const doubl
     }
 }
 
-__global__ void k_dt_final(const unsigned long long *mx, double cfl, double cv, double dt_fixed,
-                           double *dt)
+__global__ void k_dt_final(const unsigned long long *mx, double cfl, double cv, double dt_fixed, double rho,
+                           double h, double *dt)
 {
     if (threadIdx.x != 0) return;
-    if (dt_fixed > 0.0) { *dt = dt_fixed; return; }
+    if (dt_fixed > 0.0) { store_dt(dt, dt_fixed, rho, h); return; }
     double cc = __longlong_as_double((long long)mx[0]);
     double cf2 = __longlong_as_double((long long)mx[1]);
     double ccv = cc + cv;
-    *dt = cfl / (0.5 * (ccv + sqrt(ccv * ccv + 4.0 * cf2)));
+    store_dt(dt, cfl / (0.5 * (ccv + sqrt(ccv * ccv + 4.0 * cf2))), rho, h);
 }
 
 __global__ void k_average(double *a, const double *b, int n)
@@ -897,8 +896,7 @@ ebv_status launch_psi(Ctx *c, const double *u, const double *C, const double *V,
 ebv_status launch_add_gradp(Ctx *c, double *u, const double *p, double sgn)
 {
     const GridD &g = c->g;
-    EBV_LAUNCH(c, k_add_gradp, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, p, c->dt_dev,
-               c->prm.rho, sgn);
+    EBV_LAUNCH(c, k_add_gradp, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, p, c->dt_dev, sgn);
     return EBV_OK;
 }
 
@@ -906,7 +904,7 @@ ebv_status launch_nodal_rhs(Ctx *c, const double *ut, double *b)
 {
     const GridD &g = c->g;
     EBV_LAUNCH(c, k_nodal_rhs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), ut,
-               c->dt_dev, c->prm.rho, b);
+               c->dt_dev, b);
     return EBV_OK;
 }
 
@@ -917,7 +915,7 @@ ebv_status launch_timestep(Ctx *c, const double *u, const double *f, double dt_f
     EBV_LAUNCH(c, k_cfl_max, dim3(kReduceBlocks), dim3(256), 0, g, c->flag, u, f, c->cfl_max);
     const double h = g.h;
     double cv = 2.0 * c->prm.mu / c->prm.rho * (c->prm.bi_cfl + 1.0) * (3.0 / (h * h));
-    EBV_LAUNCH(c, k_dt_final, dim3(1), dim3(32), 0, c->cfl_max, c->prm.cfl, cv, dt_fixed, c->dt_dev);
+    EBV_LAUNCH(c, k_dt_final, dim3(1), dim3(32), 0, c->cfl_max, c->prm.cfl, cv, dt_fixed, c->prm.rho, h, c->dt_dev);
     return EBV_OK;
 }
 

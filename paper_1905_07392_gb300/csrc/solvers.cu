@@ -329,19 +329,35 @@ __global__ void k_cc_coarsen(GridD gf, const T *__restrict__ ef, const T *__rest
     }
 }
 
-// diag = extra + the six face coefficients of the cell.
+// diag = extra + the six face coefficients of the cell, for each of nvar
+// variants of the operator: a face on box side s counts for variant q only if
+// bit s of side mask q (bits 6q .. 6q+5 of masks) is set.  Sums in the same
+// order for every variant, so a variant with all bits set is the plain sum.
 template <class T>
 __global__ void k_cc_make_diag(GridD g, const T *__restrict__ extra, const T *__restrict__ bx,
-                               const T *__restrict__ by, const T *__restrict__ bz, T *__restrict__ diag)
+                               const T *__restrict__ by, const T *__restrict__ bz, int nvar, unsigned masks,
+                               T *__restrict__ d0, T *__restrict__ d1, T *__restrict__ d2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const int c = cix<T>(g, i, j, k);
-    diag[c] = extra[c] + bx[fidxT<T>(g, 0, i, j, k)] + bx[fidxT<T>(g, 0, i + 1, j, k)] +
-              by[fidxT<T>(g, 1, i, j, k)] + by[fidxT<T>(g, 1, i, j + 1, k)] + bz[fidxT<T>(g, 2, i, j, k)] +
-              bz[fidxT<T>(g, 2, i, j, k + 1)];
+    const T e = extra[c];
+    const T f[6] = {bx[fidxT<T>(g, 0, i, j, k)], bx[fidxT<T>(g, 0, i + 1, j, k)],
+                    by[fidxT<T>(g, 1, i, j, k)], by[fidxT<T>(g, 1, i, j + 1, k)],
+                    bz[fidxT<T>(g, 2, i, j, k)], bz[fidxT<T>(g, 2, i, j, k + 1)]};
+    // box side of each face, -1 for a face between two cells
+    const int sd[6] = {i == 0 ? 0 : -1, i == g.nx - 1 ? 1 : -1, j == 0 ? 2 : -1,
+                       j == g.ny - 1 ? 3 : -1, k == 0 ? 4 : -1, k == g.nz - 1 ? 5 : -1};
+    T *out[3] = {d0, d1, d2};
+    for (int q = 0; q < nvar; q++) {
+        const unsigned m = masks >> (6 * q);
+        T s = e;
+#pragma unroll
+        for (int t = 0; t < 6; t++) s += (sd[t] < 0 || ((m >> sd[t]) & 1u)) ? f[t] : T(0);
+        out[q][c] = s;
+    }
 }
 
 __global__ void k_cov_coarsen(GridD gf, const uint8_t *covf, GridD gc, uint8_t *covc)
@@ -378,28 +394,6 @@ __global__ void k_to_split(GridD g, int d, const double *__restrict__ a, float *
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const int i = s % mx, j = (s / mx) % my, k = s / (mx * my);
         b[d < 0 ? cix<float>(g, i, j, k) : fidxT<float>(g, d, i, j, k)] = (float)a[s];
-    }
-}
-
-// r = b - q into an FP32 row-split vector, block partials of |r|^2, |b|^2
-// (the cell-centred form of k_resid_to32)
-__global__ void __launch_bounds__(256) k_resid_to32_split(GridD g, const double *__restrict__ b,
-                                                          const double *__restrict__ q, float *__restrict__ r,
-                                                          double *__restrict__ part)
-{
-    const int n = ncell(g);
-    double v = 0.0, w = 0.0;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const double rs = b[s] - q[s];
-        r[cix<float>(g, s % g.nx, (s / g.nx) % g.ny, s / (g.nx * g.ny))] = (float)rs;
-        v += rs * rs;
-        w += b[s] * b[s];
-    }
-    v = block_sum<256>(v);
-    w = block_sum<256>(w);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = v;
-        part[gridDim.x + blockIdx.x] = w;
     }
 }
 
@@ -444,24 +438,24 @@ __global__ void k_mac_coeffs(GridD g, const uint8_t *__restrict__ flag, const do
     }
 }
 
-// Level-0 coefficients and right-hand side of the viscous solve of one
-// component (Eq. implicit-viscous, alpha-weighted):
+// Level-0 coefficients of the viscous solves (Eq. implicit-viscous,
+// alpha-weighted), shared by the three velocity components:
 //   extra = rho alpha + dt eta A_EB / (h^2 delta), delta = max(-n.b, delta_min)
 //   beta  = dt a_f eta_f / h^2, eta_f the mean of the two cells; on a box face
-//           with a Dirichlet condition 2 dt a_f eta / h^2 (the value enters b).
-//   b     = alpha psi + sum of Dirichlet contributions.
+//           2 dt a_f eta / h^2, the coefficient of a Dirichlet condition there.
+// A box face enters the diagonal of component q only where the side is a
+// Dirichlet side for q (k_cc_make_diag's side masks); its value enters the
+// right-hand side (k_visc_rhs).
 __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__restrict__ eta,
-                              const double *__restrict__ dtp, int comp,
-                              const double *__restrict__ psi, double *__restrict__ extra,
-                              double *__restrict__ bx, double *__restrict__ by, double *__restrict__ bz,
-                              double *__restrict__ b)
+                              const double *__restrict__ dtp, double *__restrict__ extra,
+                              double *__restrict__ bx, double *__restrict__ by, double *__restrict__ bz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i > g.nx || j > g.ny || k > g.nz) return;
-    const double h2 = g.h * g.h, dt = *dtp;
-    const double dth2 = dt / h2;  // one division per thread; the faces multiply
+    const double h2 = g.h * g.h, dt = dtp[DT_DT];
+    const double dth2 = dtp[DT_DTH2];  // dt / h^2
     const int N3 = geo.ncell;
     const double *A[3] = {geo.ax, geo.ay, geo.az};
     double *B[3] = {bx, by, bz};
@@ -473,12 +467,9 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
         int f = fidx(g, d, i, j, k);
         double a = A[d][f];
         if (id[d] == 0 || id[d] == dimn(g, d)) {
-            int hs = id[d] != 0;
             int cc[3] = {i, j, k};
-            cc[d] -= hs;
-            double val;
-            int c = cidx(g, cc[0], cc[1], cc[2]);
-            B[d][f] = (a > 0.0 && side_dirichlet(g, 2 * d + hs, comp, &val)) ? 2.0 * dth2 * a * eta[c] : 0.0;
+            cc[d] -= id[d] != 0;
+            B[d][f] = a > 0.0 ? 2.0 * dth2 * a * eta[cidx(g, cc[0], cc[1], cc[2])] : 0.0;
         } else {
             int lo[3] = {i, j, k};
             lo[d] -= 1;
@@ -490,7 +481,6 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
     const int c = cidx(g, i, j, k);
     if (geo.flag[c] == 0) {
         extra[c] = 1.0;
-        b[c] = 0.0;
         return;
     }
     double e = p.rho * geo.alpha[c];
@@ -501,8 +491,26 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
         e += dt * eta[c] * geo.area[c] / (h2 * del);
     }
     extra[c] = e;
-    // Dirichlet contributions of the box faces of this cell (same expression
-    // as the face coefficient above)
+}
+
+// Right-hand side of the viscous solve of component comp: alpha psi plus, for
+// each box face of the cell on a Dirichlet side of comp, its coefficient
+// (k_visc_coeffs) times the boundary value.
+__global__ void k_visc_rhs(GridD g, GeomD geo, int comp, const double *__restrict__ psi,
+                           const double *__restrict__ bx, const double *__restrict__ by,
+                           const double *__restrict__ bz, double *__restrict__ b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    const int c = cidx(g, i, j, k);
+    if (geo.flag[c] == 0) {
+        b[c] = 0.0;
+        return;
+    }
+    const double *B[3] = {bx, by, bz};
+    const int id[3] = {i, j, k};
     double rb = 0.0;
     for (int d = 0; d < 3; d++)
         for (int hs = 0; hs < 2; hs++) {
@@ -510,10 +518,8 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
             if (pos != 0 && pos != dimn(g, d)) continue;
             int fi[3] = {i, j, k};
             fi[d] += hs;
-            double a = A[d][fidx(g, d, fi[0], fi[1], fi[2])];
             double val;
-            if (a > 0.0 && side_dirichlet(g, 2 * d + hs, comp, &val))
-                rb += (2.0 * dth2 * a * eta[c]) * val;
+            if (side_dirichlet(g, 2 * d + hs, comp, &val)) rb += B[d][fidx(g, d, fi[0], fi[1], fi[2])] * val;
         }
     b[c] = geo.alpha[c] * psi[c] + rb;
 }
@@ -521,9 +527,13 @@ __global__ void k_visc_coeffs(GridD g, GeomD geo, ParamsD p, const double *__res
 // q = A p (level 0) and block partials of p.q in FP64 (per thread and warp
 // in T, see block_sum3_t).  Each thread handles planes 2kk and 2kk+1 of
 // column (i, j).
-template <class T>
+// q = A p with block partials of p.q; with kRes (FP64) instead the
+// residual r = b - A p, stored as an FP32 row-split vector, with block
+// partials of |r|^2 (the refinement solver's true residual in one pass).
+template <class T, bool kRes = false>
 __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__restrict__ p, T *__restrict__ q,
-                                                      double *__restrict__ part)
+                                                      double *__restrict__ part, const T *__restrict__ b = nullptr,
+                                                      float *__restrict__ r32 = nullptr)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -545,8 +555,14 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
 #pragma unroll
         for (int h = 0; h < 2; h++)
             if (cc[h] >= 0) {
-                q[cc[h]] = y[h];
-                v += pc[h] * y[h];
+                if constexpr (kRes) {
+                    const T rs = b[cc[h]] - y[h];
+                    r32[cix<float>(A.g, i, j, 2 * kk + h)] = (float)rs;
+                    v += rs * rs;
+                } else {
+                    q[cc[h]] = y[h];
+                    v += pc[h] * y[h];
+                }
             }
     }
     const double vs = block_sum3_t<T>(v);
@@ -803,9 +819,12 @@ __device__ inline void plane_pe(const GridD &g, const T *__restrict__ x, int i, 
 }
 
 // q = A p on level 0 with block partials of p.q (k_nd_apply_dot, NZB nodes per thread).
-template <class T>
+// kRes: r = b - A p as an FP32 vector with partials of |r|^2 instead of q
+// and p.q (as k_cc_apply_dot).
+template <class T, bool kRes = false>
 __global__ void __launch_bounds__(256) k_nd_apply_dot_col(NdOp<T> A, const T *__restrict__ p, T *__restrict__ q,
-                                                          double *__restrict__ part)
+                                                          double *__restrict__ part, const T *__restrict__ b = nullptr,
+                                                          float *__restrict__ r32 = nullptr)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -835,8 +854,14 @@ __global__ void __launch_bounds__(256) k_nd_apply_dot_col(NdOp<T> A, const T *__
                 nd_row(A, i, j, k, p, diag, ax);
                 y = ax;
             }
-            q[n] = y;
-            v += (double)(p[n] * y);
+            if constexpr (kRes) {
+                const T rs = b[n] - y;
+                r32[n] = (float)rs;
+                v += (double)(rs * rs);
+            } else {
+                q[n] = y;
+                v += (double)(p[n] * y);
+            }
             Pm = P0; Em = E0; P0 = Pp; E0 = Ep;
         }
     }
@@ -968,11 +993,16 @@ __global__ void k_nd_bottom_assemble(GridD g, const double *__restrict__ alpha, 
 }
 
 // Gauss-Jordan elimination of [M | I] in one CTA (SPD: no pivoting needed);
-// the right half becomes the inverse, copied to inv.
-__global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ M, int nb, double *__restrict__ inv)
+// the right half becomes the inverse, copied to inv.  CTA q of the grid
+// inverts matrix q of the nb x 2nb matrices stored one after another in M into
+// inv_q (up to three at once: the variants of one operator).
+__global__ void __launch_bounds__(1024) k_gauss_jordan(double *__restrict__ Mall, int nb, double *inv0,
+                                                       double *inv1, double *inv2)
 {
     __shared__ double fac[kBottomMax];
     const int w = 2 * nb;
+    double *__restrict__ M = Mall + (size_t)blockIdx.x * nb * w;
+    double *__restrict__ inv = blockIdx.x == 0 ? inv0 : (blockIdx.x == 1 ? inv1 : inv2);
     for (int col = 0; col < nb; col++) {
         double piv = M[(size_t)col * w + col];
         __syncthreads();
@@ -1037,33 +1067,58 @@ struct CoarseVC {
     int nb;
 };
 
-template <class T>
-__global__ void __launch_bounds__(1024) k_cc_coarse_vcycle(CoarseVC<T> D)
+// One colour pass of the coarse kernel on level l: thread tid takes the
+// (x-pair, row) slots tid, tid + 1024, ... and in each the cell of colour
+// `color`; as in k_cc_gs, every operand of its (at most kCoarseSlots) updates
+// is loaded before any result is stored, so the L2 round trips overlap.
+// With zero_start the other cell of each slot is set to 0.
+constexpr int kCoarseThreads = 1024;
+constexpr int kCoarseSlots = (kCoarseCells + kCoarseThreads - 1) / kCoarseThreads;  // x-pairs: <= cells
+template <class T, bool kCorr>
+__device__ inline void coarse_pass(const CoarseVC<T> &D, int l, int color, int zero_start)
 {
+    const CcOp<T> &A = D.A[l];
+    const GridD &g = A.g;
+    const int hx = (g.nx + 1) >> 1, slots = hx * g.ny * g.nz;
+    T *x = D.x[l];
+    T val[kCoarseSlots];
+    int cc[kCoarseSlots], co[kCoarseSlots];
+#pragma unroll
+    for (int u = 0; u < kCoarseSlots; u++) {
+        const int m = threadIdx.x + u * kCoarseThreads;
+        cc[u] = -1;
+        co[u] = -1;
+        val[u] = T(0);
+        if (m >= slots) continue;
+        const int t = m % hx, jk = m / hx, j = jk % g.ny, k = jk / g.ny;
+        const int par = (j + k + color) & 1;
+        const int i = 2 * t + par, io = 2 * t + 1 - par;
+        if (io < g.nx) co[u] = cix<T>(g, io, j, k);
+        if (i >= g.nx) continue;
+        cc[u] = cix<T>(g, i, j, k);
+        val[u] = kCorr ? gs_cell<T, true>(A, x, D.b[l], i, j, k, 0, D.x[l + 1], D.A[l + 1].g)
+                       : gs_cell<T, false>(A, x, D.b[l], i, j, k, zero_start, x, g);
+    }
+#pragma unroll
+    for (int u = 0; u < kCoarseSlots; u++) {
+        if (zero_start && co[u] >= 0) x[co[u]] = T(0);
+        if (cc[u] >= 0) x[cc[u]] = val[u];
+    }
+    __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kCoarseThreads) k_cc_coarse_vcycle(CoarseVC<T> D)
+{
+    __shared__ double bs[kBottomMax];
     const int tid = threadIdx.x, nt = blockDim.x;
-    // one colour pass on level l (first = the pass after the coarse correction)
-    auto pass = [&](int l, int color, int zero_start, bool first_up) {
-        const CcOp<T> &A = D.A[l];
-        const GridD &g = A.g;
-        const int n = ncell(g);
-        T *x = D.x[l];
-        for (int s = tid; s < n; s += nt) {
-            const int i = s % g.nx, j = (s / g.nx) % g.ny, k = s / (g.nx * g.ny);
-            if (((i + j + k) & 1) == color)
-                x[cix<T>(g, i, j, k)] = first_up ? gs_cell<T, true>(A, x, D.b[l], i, j, k, 0, D.x[l + 1], D.A[l + 1].g)
-                                                 : gs_cell<T, false>(A, x, D.b[l], i, j, k, zero_start, x, g);
-            else if (zero_start)
-                x[cix<T>(g, i, j, k)] = T(0);
-        }
-        __syncthreads();
-    };
     const int L = D.n - 1;
     for (int l = 0; l < L; l++) {
         // two red-black sweeps, red first, the first from zero
-        pass(l, 0, 1, false);
-        pass(l, 1, 0, false);
-        pass(l, 0, 0, false);
-        pass(l, 1, 0, false);
+        coarse_pass<T, false>(D, l, 0, 1);
+        coarse_pass<T, false>(D, l, 1, 0);
+        coarse_pass<T, false>(D, l, 0, 0);
+        coarse_pass<T, false>(D, l, 1, 0);
         const GridD &gc = D.A[l + 1].g;
         const int nc = ncell(gc);
         for (int s = tid; s < nc; s += nt) {
@@ -1072,15 +1127,27 @@ __global__ void __launch_bounds__(1024) k_cc_coarse_vcycle(CoarseVC<T> D)
         }
         __syncthreads();
     }
-    for (int r = tid; r < D.nb; r += nt)
-        bottom_row(D.binv, D.nb, D.b[L], D.x[L], 1.0, D.A[L].g, (int)(sizeof(T) == 4), r);
-    __syncthreads();
+    // bottom: x = inv b, b gathered once into natural order (same sums as bottom_row)
+    {
+        const GridD &gb = D.A[L].g;
+        const int split = (int)(sizeof(T) == 4);
+        for (int q = tid; q < D.nb; q += nt) bs[q] = (double)D.b[L][bottom_pos(gb, split, q)];
+        __syncthreads();
+        for (int r = tid; r < D.nb; r += nt) {
+            const double *__restrict__ row = D.binv + (size_t)r * D.nb;
+            double sum = 0.0;
+#pragma unroll 8
+            for (int q = 0; q < D.nb; q++) sum += row[q] * bs[q];
+            D.x[L][bottom_pos(gb, split, r)] = (T)(sum * 1.0);
+        }
+        __syncthreads();
+    }
     for (int l = L - 1; l >= 0; l--) {
         // two sweeps, black first; the first pass takes the coarse correction
-        pass(l, 1, 0, true);
-        pass(l, 0, 0, false);
-        pass(l, 1, 0, false);
-        pass(l, 0, 0, false);
+        coarse_pass<T, true>(D, l, 1, 0);
+        coarse_pass<T, false>(D, l, 0, 0);
+        coarse_pass<T, false>(D, l, 1, 0);
+        coarse_pass<T, false>(D, l, 0, 0);
     }
 }
 
@@ -1246,24 +1313,6 @@ __global__ void k_cg_pupdate(double *__restrict__ p, const double *__restrict__ 
 // Per-thread sums of the FP32 kernels stay FP32 (a few dozen terms), block and
 // final sums are FP64.
 
-__global__ void __launch_bounds__(256) k_resid_to32(const double *__restrict__ b, const double *__restrict__ q,
-                                                    float *__restrict__ r, int n, double *__restrict__ part)
-{
-    double v = 0.0, w = 0.0;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        double rs = b[s] - q[s];
-        r[s] = (float)rs;
-        v += rs * rs;
-        w += b[s] * b[s];
-    }
-    v = block_sum<256>(v);
-    w = block_sum<256>(w);
-    if (threadIdx.x == 0) {
-        part[blockIdx.x] = v;
-        part[gridDim.x + blockIdx.x] = w;
-    }
-}
-
 __global__ void __launch_bounds__(256) k_dot32(const float *__restrict__ a, const float *__restrict__ b, int n,
                                                double *__restrict__ part)
 {
@@ -1336,16 +1385,19 @@ CcOp<T> ccop(const CcLevel &L)
     return A;
 }
 
-// diag of level L from its extra and faces, in precision T.
+// diagonals of every variant of level l from its extra and faces, in precision T.
 template <class T>
-void cc_make_diag(Ctx *c, CcLevel &L)
+void cc_make_diag(Ctx *c, CcHier &H, int l)
 {
+    const CcLevel &L = H.lv[l];
+    unsigned masks = 0;
+    for (int q = 0; q < H.nvar; q++) masks |= (H.side_mask[q] & 0x3fu) << (6 * q);
     if constexpr (sizeof(T) == 8)
         EBV_LAUNCH(c, k_cc_make_diag<double>, cgrid(L.g), block3(), 0, L.g, L.extra_d, L.bf_d[0], L.bf_d[1],
-                   L.bf_d[2], L.diag_d);
+                   L.bf_d[2], H.nvar, masks, H.vdiag_d[0][l], H.vdiag_d[1][l], H.vdiag_d[2][l]);
     else
         EBV_LAUNCH(c, k_cc_make_diag<float>, cgrid(L.g), block3(), 0, L.g, L.extra_f, L.bf_f[0], L.bf_f[1],
-                   L.bf_f[2], L.diag_f);
+                   L.bf_f[2], H.nvar, masks, H.vdiag_f[0][l], H.vdiag_f[1][l], H.vdiag_f[2][l]);
 }
 
 template <class T>
@@ -1545,9 +1597,9 @@ struct Problem {
     virtual void precond(Ctx *c, const double *r, double *z) = 0;
     virtual void precond32(Ctx *c, const float *r, float *z) = 0;
     // FP64 <-> FP32 vectors of the refinement solver (the FP32 side in the
-    // layout of the problem's FP32 multigrid): r = b - q with block partials
-    // of |r|^2 and |b|^2 in c->part; x += e
-    virtual void resid_to32(Ctx *c, const double *b, const double *q, float *r) = 0;
+    // layout of the problem's FP32 multigrid): r = b - A x in FP64 with
+    // apply_blocks() block partials of |r|^2 in c->part; x += e
+    virtual void resid32(Ctx *c, const double *b, const double *x, float *r) = 0;
     virtual void add32(Ctx *c, double *x, const float *e) = 0;
 };
 
@@ -1730,12 +1782,12 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
     const double inner_drop = 1e-4;
     float *r = c->kr32, *z = c->kz32, *p = c->kp32, *q = c->kq32, *e = c->ke32;
     auto true_residual = [&]() {
-        P.apply_dot(c, x, c->kq);
-        P.resid_to32(c, b, c->kq, r);
-        reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
-        reduce_sum(c, c->part + vblocks(n), vblocks(n), c->scal + S_BB);
+        P.resid32(c, b, x, r);
+        reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_RR);
     };
     EBV_LAUNCH(c, k_solve_begin, dim3(1), dim3(32), 0, c->ctl);
+    EBV_LAUNCH(c, k_dot, dim3(vblocks(n)), dim3(256), 0, b, b, n, c->part);
+    reduce_sum(c, c->part, vblocks(n), c->scal + S_BB);
     DevLoop outer(c, C_COND_OUT);
     true_residual();
     EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 60, 1, inner_drop, outer.h,
@@ -1787,9 +1839,11 @@ struct CcProblem : Problem {
     }
     void precond(Ctx *c, const double *r, double *z) override { cc_vcycle<double>(c, *H, r, z); }
     void precond32(Ctx *c, const float *r, float *z) override { cc_vcycle<float>(c, *H, r, z); }
-    void resid_to32(Ctx *c, const double *b, const double *q, float *r) override
+    void resid32(Ctx *c, const double *b, const double *x, float *r) override
     {
-        EBV_LAUNCH(c, k_resid_to32_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, b, q, r, c->part);
+        // x, diagonal, 3 faces, b read, r (FP32) written: 6.5 words per cell
+        EBV_LAUNCH_P(c, "cc_resid_fp64", 52.0 * n(), (k_cc_apply_dot<double, true>), agrid(), block3(), 0,
+                     ccop<double>(H->lv[0]), x, (double *)nullptr, c->part, b, r);
     }
     void add32(Ctx *c, double *x, const float *e) override
     {
@@ -1815,9 +1869,11 @@ struct NdProblem : Problem {
     }
     void precond(Ctx *c, const double *r, double *z) override { nd_vcycle<double>(c, *H, r, z); }
     void precond32(Ctx *c, const float *r, float *z) override { nd_vcycle<float>(c, *H, r, z); }
-    void resid_to32(Ctx *c, const double *b, const double *q, float *r) override
+    void resid32(Ctx *c, const double *b, const double *x, float *r) override
     {
-        EBV_LAUNCH(c, k_resid_to32, dim3(vblocks(n())), dim3(256), 0, b, q, r, n(), c->part);
+        // x, alpha, b read, r (FP32) written: 3.5 words per node
+        EBV_LAUNCH_P(c, "nodal_resid_fp64", 28.0 * n(), (k_nd_apply_dot_col<double, true>), ncolgrid(H->lv[0].g),
+                     block3(), 0, ndop<double>(H->lv[0]), x, (double *)nullptr, c->part, b, r);
     }
     void add32(Ctx *c, double *x, const float *e) override
     {
@@ -1836,11 +1892,12 @@ ebv_status solve(Ctx *c, Problem &P, const double *b, double *x, int *iters, dou
 ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
 {
     CcLevel &L0 = H.lv[0];
-    cc_make_diag<double>(c, L0);
+    cc_make_diag<double>(c, H, 0);
     if (fp32) {
         const int n = ncell(L0.g);
         EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, L0.extra_d, L0.extra_f);
-        EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, L0.diag_d, L0.diag_f);
+        for (int q = 0; q < H.nvar; q++)
+            EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, H.vdiag_d[q][0], H.vdiag_f[q][0]);
         for (int d = 0; d < 3; d++)
             EBV_LAUNCH(c, k_to_split, dim3(vblocks(nface(L0.g, d))), dim3(256), 0, L0.g, d, L0.bf_d[d], L0.bf_f[d]);
     }
@@ -1850,20 +1907,30 @@ ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
         if (fp32) {
             EBV_LAUNCH(c, k_cc_coarsen<float>, gr, block3(), 0, F.g, F.extra_f, F.bf_f[0], F.bf_f[1], F.bf_f[2], F.cov,
                        Cc.g, Cc.cov, Cc.extra_f, Cc.bf_f[0], Cc.bf_f[1], Cc.bf_f[2]);
-            cc_make_diag<float>(c, Cc);
+            cc_make_diag<float>(c, H, l + 1);
         } else {
             EBV_LAUNCH(c, k_cc_coarsen<double>, gr, block3(), 0, F.g, F.extra_d, F.bf_d[0], F.bf_d[1], F.bf_d[2],
                        F.cov, Cc.g, Cc.cov, Cc.extra_d, Cc.bf_d[0], Cc.bf_d[1], Cc.bf_d[2]);
-            cc_make_diag<double>(c, Cc);
+            cc_make_diag<double>(c, H, l + 1);
         }
     }
-    CcLevel &B = H.lv[H.L - 1];
-    if (fp32)
-        EBV_LAUNCH(c, k_cc_bottom_assemble<float>, dim3((H.nb + 127) / 128), dim3(128), 0, ccop<float>(B), H.bmat, H.nb);
-    else
-        EBV_LAUNCH(c, k_cc_bottom_assemble<double>, dim3((H.nb + 127) / 128), dim3(128), 0, ccop<double>(B), H.bmat,
-                   H.nb);
-    EBV_LAUNCH(c, k_gauss_jordan, dim3(1), dim3(1024), 0, H.bmat, H.nb, H.binv);
+    const int lb = H.L - 1;
+    const size_t msz = (size_t)H.nb * 2 * H.nb;
+    for (int q = 0; q < H.nvar; q++) {
+        if (fp32) {
+            CcOp<float> A = ccop<float>(H.lv[lb]);
+            A.diag = H.vdiag_f[q][lb];
+            EBV_LAUNCH(c, k_cc_bottom_assemble<float>, dim3((H.nb + 127) / 128), dim3(128), 0, A, H.bmat + q * msz,
+                       H.nb);
+        } else {
+            CcOp<double> A = ccop<double>(H.lv[lb]);
+            A.diag = H.vdiag_d[q][lb];
+            EBV_LAUNCH(c, k_cc_bottom_assemble<double>, dim3((H.nb + 127) / 128), dim3(128), 0, A, H.bmat + q * msz,
+                       H.nb);
+        }
+    }
+    EBV_LAUNCH(c, k_gauss_jordan, dim3(H.nvar), dim3(1024), 0, H.bmat, H.nb, H.vbinv[0], H.vbinv[1], H.vbinv[2]);
+    select_variant(H, 0);
     return EBV_OK;
 }
 
@@ -1911,6 +1978,18 @@ ebv_status setup_solvers(Ctx *c)
     long long nbc = (long long)gl[L - 1].nx * gl[L - 1].ny * gl[L - 1].nz;
     if (nbc > kBottomMax) return c->fail(EBV_ERR_INVALID, "grid cannot be coarsened to a small bottom level");
     CcHier *hs[2] = {&c->mac, &c->visc};
+    // the projection operator has one variant; the viscous one a variant per
+    // velocity component, whose diagonals take the box faces of its Dirichlet sides
+    c->mac.nvar = 1;
+    c->mac.side_mask[0] = 0x3fu;
+    c->visc.nvar = 3;
+    for (int q = 0; q < 3; q++) {
+        unsigned m = 0;
+        double val;
+        for (int sd = 0; sd < 6; sd++)
+            if (side_dirichlet(g, sd, q, &val)) m |= 1u << sd;
+        c->visc.side_mask[q] = m;
+    }
     for (CcHier *H : hs) {
         H->L = L;
         H->nb = (int)nbc;
@@ -1920,8 +1999,10 @@ ebv_status setup_solvers(Ctx *c)
             size_t nc = ncell(gl[l]);
             Lv.extra_d = dalloc<double>(nc, e);
             Lv.extra_f = dalloc<float>(nc, e);
-            Lv.diag_d = dalloc<double>(nc, e);
-            Lv.diag_f = dalloc<float>(nc, e);
+            for (int q = 0; q < H->nvar; q++) {
+                H->vdiag_d[q][l] = dalloc<double>(nc, e);
+                H->vdiag_f[q][l] = dalloc<float>(nc, e);
+            }
             for (int d = 0; d < 3; d++) {
                 Lv.bf_d[d] = dalloc<double>(nface(gl[l], d), e);
                 Lv.bf_f[d] = dalloc<float>(nface(gl[l], d), e);
@@ -1929,8 +2010,9 @@ ebv_status setup_solvers(Ctx *c)
             if (H == &c->mac) Lv.cov = dalloc<uint8_t>(nc, e);
             else Lv.cov = c->mac.lv[l].cov;
         }
-        H->binv = dalloc<double>((size_t)nbc * nbc, e);
-        H->bmat = dalloc<double>((size_t)nbc * 2 * nbc, e);
+        for (int q = 0; q < H->nvar; q++) H->vbinv[q] = dalloc<double>((size_t)nbc * nbc, e);
+        H->bmat = dalloc<double>((size_t)H->nvar * nbc * 2 * nbc, e);
+        select_variant(*H, 0);
     }
     // nodal hierarchy
     GridD gn[kMaxLevels];
@@ -2004,7 +2086,8 @@ ebv_status setup_geometry_solvers(Ctx *c)
     }
     const NdLevel &B = N.lv[N.L - 1];
     EBV_LAUNCH(c, k_nd_bottom_assemble, dim3((N.nb + 127) / 128), dim3(128), 0, B.g, B.alpha_d, B.act, N.bmat, N.nb);
-    EBV_LAUNCH(c, k_gauss_jordan, dim3(1), dim3(1024), 0, N.bmat, N.nb, N.binv);
+    EBV_LAUNCH(c, k_gauss_jordan, dim3(1), dim3(1024), 0, N.bmat, N.nb, N.binv, (double *)nullptr,
+               (double *)nullptr);
     EBV_CUDA_TRY(c, cudaGetLastError());
     return autotune_shapes(c);
 }
@@ -2082,34 +2165,32 @@ ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res
     return solve(c, P, b, x, iters, res);
 }
 
-ebv_status visc_solve(Ctx *c, const double *eta, const double *psi_comp, int comp, double *x, int *iters,
-                      double *res)
+ebv_status visc_build(Ctx *c, const double *eta)
 {
     const GridD &g = c->g;
     CcLevel &V0 = c->visc.lv[0];
     EBV_LAUNCH(c, k_visc_coeffs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), paramsd(c->prm), eta,
-               c->dt_dev, comp, psi_comp, V0.extra_d, V0.bf_d[0], V0.bf_d[1], V0.bf_d[2], c->rhs_c);
-    const bool fp32 = c->prm.precision == EBV_FP32_REFINE;
-    ebv_status s = cc_finish_hierarchy(c, c->visc, fp32);
-    if (s != EBV_OK) return s;
+               c->dt_dev, V0.extra_d, V0.bf_d[0], V0.bf_d[1], V0.bf_d[2]);
+    return cc_finish_hierarchy(c, c->visc, c->prm.precision == EBV_FP32_REFINE);
+}
+
+ebv_status visc_solve(Ctx *c, const double *psi_comp, int comp, double *x, int *iters, double *res)
+{
+    const GridD &g = c->g;
+    CcLevel &V0 = c->visc.lv[0];
+    EBV_LAUNCH(c, k_visc_rhs, cgrid(g), block3(), 0, g, geomd(c), comp, psi_comp, V0.bf_d[0], V0.bf_d[1],
+               V0.bf_d[2], c->rhs_c);
+    select_variant(c->visc, comp);
     CcProblem P;
     P.H = &c->visc;
     return solve(c, P, c->rhs_c, x, iters, res);
 }
 
-ebv_status visc_solve_rhs(Ctx *c, const double *eta, int comp, const double *rhs, double *x, int *iters,
-                          double *res)
+ebv_status visc_solve_rhs(Ctx *c, int comp, const double *rhs, double *x, int *iters, double *res)
 {
-    const GridD &g = c->g;
-    const int n = ncell(g);
-    CcLevel &V0 = c->visc.lv[0];
-    // coefficients of A(eta); the right-hand side it writes is replaced
-    EBV_LAUNCH(c, k_visc_coeffs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), paramsd(c->prm), eta,
-               c->dt_dev, comp, rhs, V0.extra_d, V0.bf_d[0], V0.bf_d[1], V0.bf_d[2], c->rhs_c);
+    const int n = ncell(c->g);
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->rhs_c, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    const bool fp32 = c->prm.precision == EBV_FP32_REFINE;
-    ebv_status s = cc_finish_hierarchy(c, c->visc, fp32);
-    if (s != EBV_OK) return s;
+    select_variant(c->visc, comp);
     EBV_LAUNCH(c, k_fill, dim3(vblocks(n)), dim3(256), 0, x, n, 0.0);
     CcProblem P;
     P.H = &c->visc;
