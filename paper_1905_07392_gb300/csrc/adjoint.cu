@@ -415,13 +415,15 @@ __global__ void k_flux_div_adj_wall(GridD g, GeomD geo, const double *__restrict
 // Forward: far cells out = sign DC / div; near cells (pass a) D = al DC +
 // (1 - al) dnc, dD = al (1 - al)(DC - dnc), dnc = sum_nb alpha DC / sum_nb
 // alpha, and (pass b) out = sign (D + sum over cut neighbours w dD) / div.
+// kDiv: divide by div; without it div is 1 and no division is issued.
+template <bool kDiv>
 __global__ void k_redist_adj_far(GridD g, const uint8_t *__restrict__ flag, const uint8_t *__restrict__ near,
                                  const double *__restrict__ ob, double sign, double div, double *__restrict__ DCb)
 {
     ADJ_CELL
     const int N3 = ncell(g);
     if (near[c]) return;
-    for (int q = 0; q < 3; q++) DCb[q * N3 + c] = flag[c] ? sign * (div == 1.0 ? ob[q * N3 + c] : ob[q * N3 + c] / div) : 0.0;
+    for (int q = 0; q < 3; q++) DCb[q * N3 + c] = flag[c] ? sign * (kDiv ? ob[q * N3 + c] / div : ob[q * N3 + c]) : 0.0;
 }
 
 // Near cells: the adjoint of D (self) and, for cut cells, of dD (gathered from
@@ -920,8 +922,12 @@ ebv_status adj_viscous_explicit(Ctx *c, const double *u, const double *eta, cons
     ebv_status st = launch_wall_dudn(c, u, c->dudn);
     if (st != EBV_OK) return st;
     // redistribution (sign +1, divided by rho)
-    EBV_LAUNCH(c, k_redist_adj_far, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, V_bar, 1.0,
-               c->prm.rho, DCb);
+    if (c->prm.rho != 1.0)
+        EBV_LAUNCH(c, k_redist_adj_far<true>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, V_bar, 1.0,
+                   c->prm.rho, DCb);
+    else
+        EBV_LAUNCH(c, k_redist_adj_far<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, V_bar, 1.0,
+                   c->prm.rho, DCb);
     if (c->nnear) {
         dim3 gr((c->nnear + 127) / 128);
         EBV_LAUNCH(c, k_redist_adj_a, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->alpha, V_bar, 1.0,
@@ -964,7 +970,8 @@ ebv_status adj_convective(Ctx *c, const double *u, const double *S, const double
     const int offs[3] = {0, nface(g, 0), nface(g, 0) + nface(g, 1)};
     const double *A[3] = {c->ax, c->ay, c->az};
     // redistribution (sign -1, no division) and the divergence
-    EBV_LAUNCH(c, k_redist_adj_far, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, Cb, -1.0, 1.0, DCb);
+    EBV_LAUNCH(c, k_redist_adj_far<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, Cb, -1.0, 1.0,
+               DCb);
     if (c->nnear) {
         dim3 gr((c->nnear + 127) / 128);
         EBV_LAUNCH(c, k_redist_adj_a, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->alpha, Cb, -1.0, 1.0, DCb,

@@ -665,9 +665,11 @@ void ebv_destroy(ebv_ctx *c)
         cudaFree(L.alpha_f);
         cudaFree(L.act);
         cudaFree(L.reg);
+        cudaFree(L.irr);
     }
     cudaFree(c->nd.binv);
     cudaFree(c->nd.bmat);
+
     for (int l = 0; l < kMaxLevels; l++) {
         cudaFree(c->lx[l]); cudaFree(c->lb[l]); cudaFree(c->lr[l]); cudaFree(c->ld[l]); cudaFree(c->lt[l]);
     }

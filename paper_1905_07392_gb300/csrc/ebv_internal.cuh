@@ -51,6 +51,7 @@ struct ParamsD {
     double rho, mu, tau0, m, n_flow, eta0;
     int model;
     double delta_min;
+    double inv_m;  // 1/m (the floor of the strain rate in the power laws)
 };
 
 __host__ __device__ inline int cidx(const GridD &g, int i, int j, int k)
@@ -108,21 +109,22 @@ __device__ inline void store_dt(double *d, double dt, double rho, double h)
     d[DT_DTH2] = dt / (h * h);
 }
 
-// Apparent viscosity of the rheology table.
-__device__ inline double eta_of(const ParamsD &p, double sr)
+// Apparent viscosity of the rheology table at strain rate sr, given its
+// reciprocal rsr (the laws take their sr -> 0 limits at sr = 0).
+__device__ inline double eta_of(const ParamsD &p, double sr, double rsr)
 {
     // (1 - exp(-m sr)) / sr; once m sr > 40, exp(-m sr) < 2^-57 and
     // -expm1(-m sr) rounds to 1 exactly, so the exponential is skipped.
     const double msr = p.m * sr;
-    double yield = (sr > 0.0) ? (msr > 40.0 ? 1.0 / sr : -expm1(-msr) / sr) : p.m;
-    double srf = sr > 1.0 / p.m ? sr : 1.0 / p.m;
+    double yield = (sr > 0.0) ? (msr > 40.0 ? 1.0 : -expm1(-msr)) * rsr : p.m;
+    double srf = sr > p.inv_m ? sr : p.inv_m;
     switch (p.model) {
     case EBV_NEWTONIAN: return p.mu;
     case EBV_BINGHAM: return p.mu + p.tau0 * yield;
     case EBV_HERSCHEL_BULKLEY: return p.mu * pow(srf, p.n_flow - 1.0) + p.tau0 * yield;
     case EBV_POWER_LAW: return p.mu * pow(srf, p.n_flow - 1.0);
     case EBV_SOUZA_MENDES_DUTRA: {
-        double y2 = (sr > 0.0) ? -expm1(-p.eta0 * sr / p.tau0) / sr : p.eta0 / p.tau0;
+        double y2 = (sr > 0.0) ? -expm1(-p.eta0 * sr / p.tau0) * rsr : p.eta0 / p.tau0;
         return p.mu * pow(srf, p.n_flow - 1.0) + p.tau0 * y2;
     }
     }
@@ -177,7 +179,10 @@ struct NdLevel {
     double *alpha_d = nullptr;   // cell volume fractions at this level
     float *alpha_f = nullptr;
     uint8_t *act = nullptr;      // 1 for active nodes
-    uint8_t *reg = nullptr;      // level 0: 1 where all 8 cells around the node are full
+    uint8_t *reg = nullptr;      // 1 where all 8 cells around the node are full (levels that
+                                 // take the plane march, else null)
+    int *irr = nullptr;          // with reg: the active nodes that are not regular, ascending
+    int nirr = 0;
     double lam_max = 2.0;        // bound of the spectrum of D^-1 A
     dim3 ch_blk = dim3(32, 4, 2);  // Chebyshev-step block shape (autotuned per level)
 };
@@ -318,6 +323,7 @@ inline ParamsD paramsd(const ebv_params &p)
     ParamsD q;
     q.rho = p.rho; q.mu = p.mu; q.tau0 = p.tau0; q.m = p.m; q.n_flow = p.n_flow; q.eta0 = p.eta0;
     q.model = p.model; q.delta_min = p.delta_min;
+    q.inv_m = 1.0 / p.m;
     return q;
 }
 

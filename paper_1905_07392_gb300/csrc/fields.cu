@@ -113,16 +113,14 @@ __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__re
     for (int d = 0; d < 3; d++)
 #pragma unroll
         for (int q = 0; q < 3; q++) Gm[d][q] = d_robust(g, flag, u + q * N3, i, j, k, d, ih);
-    double s2 = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; d++)
-#pragma unroll
-        for (int q = 0; q < 3; q++) {
-            double gam = Gm[d][q] + Gm[q][d];
-            s2 += gam * gam;
-        }
-    double sr = sqrt(0.5 * s2);
-    eta[c] = eta_of(p, sr);
+    // sr^2 = |G + G^T|^2 / 2 = 2 (G_00^2 + G_11^2 + G_22^2) + the squares of
+    // the three off-diagonal sums; sr and 1/sr from one reciprocal square root
+    const double xy = Gm[0][1] + Gm[1][0], xz = Gm[0][2] + Gm[2][0], yz = Gm[1][2] + Gm[2][1];
+    const double s = 2.0 * (Gm[0][0] * Gm[0][0] + Gm[1][1] * Gm[1][1] + Gm[2][2] * Gm[2][2]) +
+                     (xy * xy + xz * xz + yz * yz);
+    const double rsr = s > 0.0 ? rsqrt(s) : 0.0;
+    const double sr = s * rsr;
+    eta[c] = eta_of(p, sr, rsr);
     if (srate) srate[c] = sr;
     if (kWriteG)
 #pragma unroll
@@ -327,6 +325,10 @@ __global__ void __launch_bounds__(256) k_flux_div(GridD g, GeomD geo, const doub
 // full neighbours, so D = D^H = D^C exactly (its excess and its neighbours'
 // excess vanish).  Such cells take the direct path; the cells of the `near`
 // list (cut cells and their neighbours) take the two passes below.
+// kDiv: out = v / div; without it div is 1 and no division is issued (a
+// division the branch skips is still evaluated when the compiler turns the
+// branch into a select).
+template <bool kDiv>
 __global__ void k_redist_far(GridD g, const uint8_t *__restrict__ flag, const uint8_t *__restrict__ near,
                              const double *__restrict__ DC, double sign, double div, double *__restrict__ out)
 {
@@ -335,7 +337,7 @@ __global__ void k_redist_far(GridD g, const uint8_t *__restrict__ flag, const ui
     if (near[c]) return;
     for (int q = 0; q < 3; q++) {
         double v = flag[c] ? sign * DC[q * N3 + c] : 0.0;
-        out[q * N3 + c] = div == 1.0 ? v : v / div;
+        out[q * N3 + c] = kDiv ? v / div : v;
     }
 }
 
@@ -379,7 +381,8 @@ __global__ void __launch_bounds__(256) k_redist_a(GridD g, const int *__restrict
 }
 
 // Pass 2 on the near cells: add the cut neighbours' weighted excess (full
-// neighbours have none); out = sign * D / div.
+// neighbours have none); out = sign * D / div (kDiv as in k_redist_far).
+template <bool kDiv>
 __global__ void __launch_bounds__(256) k_redist_b(GridD g, const int *__restrict__ list, int nlist,
                                                   const uint8_t *__restrict__ flag,
                                                   const double *__restrict__ D,
@@ -402,7 +405,10 @@ __global__ void __launch_bounds__(256) k_redist_b(GridD g, const int *__restrict
                 if (flag[c2] != 2) continue;
                 for (int q = 0; q < 3; q++) s[q] += w[c2] * dD[q * N3 + c2];
             }
-    for (int q = 0; q < 3; q++) out[q * N3 + c] = sign * (D[q * N3 + c] + s[q]) / div;
+    for (int q = 0; q < 3; q++) {
+        const double v = sign * (D[q * N3 + c] + s[q]);
+        out[q * N3 + c] = kDiv ? v / div : v;
+    }
 }
 
 // ---- wall-normal derivative at the EB centroid (Eqs. interpolation_distances, dudn)
@@ -828,13 +834,23 @@ ebv_status launch_mac_correct(Ctx *c, double *uf, const double *phi)
 ebv_status launch_redistribute_into(Ctx *c, const double *DC, double sign, double div, double *out)
 {
     const GridD &g = c->g;
-    EBV_LAUNCH(c, k_redist_far, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, DC, sign, div, out);
+    const bool dv = div != 1.0;
+    if (dv)
+        EBV_LAUNCH(c, k_redist_far<true>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, DC, sign, div,
+                   out);
+    else
+        EBV_LAUNCH(c, k_redist_far<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, c->nearm, DC, sign, div,
+                   out);
     if (c->nnear) {
         dim3 gr((c->nnear + 127) / 128);
         EBV_LAUNCH(c, k_redist_a, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->alpha, DC, c->Dh, c->dD,
                    c->wts);
-        EBV_LAUNCH(c, k_redist_b, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->Dh, c->dD, c->wts, sign,
-                   div, out);
+        if (dv)
+            EBV_LAUNCH(c, k_redist_b<true>, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->Dh, c->dD, c->wts,
+                       sign, div, out);
+        else
+            EBV_LAUNCH(c, k_redist_b<false>, gr, dim3(128), 0, g, c->nearl, c->nnear, c->flag, c->Dh, c->dD, c->wts,
+                       sign, div, out);
     }
     return EBV_OK;
 }

@@ -13,6 +13,7 @@
 // FP64, so FP32 only enters as a preconditioner.  Dot products use fixed-order
 // block partials, so results are bitwise reproducible run to run.
 #include <math.h>
+#include <vector>
 
 #include "ebv_internal.cuh"
 
@@ -581,6 +582,7 @@ __constant__ double kQ1[4] = {1.0 / 3.0, 0.0, -1.0 / 12.0, -1.0 / 12.0};
 template <class T>
 struct NdOp {
     GridD g;               // cell dims
+    T h;                   // g.h in the operator's precision
     const T *alpha;        // cells
     const uint8_t *act;    // nodes
     const uint8_t *reg;    // nodes whose 8 cells are full (level 0), else nullptr
@@ -617,7 +619,7 @@ __device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__
         // body diagonals (times h)
         T fd, bd;
         nd_regular_sums(g, x, nidx(g, i, j, k), fd, bd);
-        const T hh = T(g.h);
+        const T hh = A.h;
         diag = hh * T(8.0 / 3.0);
         ax = diag * x[nidx(g, i, j, k)] - hh * T(1.0 / 12.0) * (T(2) * fd + bd);
         return;
@@ -659,7 +661,7 @@ __device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__
         for (int q = 0; q < 2; q++)
 #pragma unroll
             for (int p = 0; p < 2; p++) s += a[r][q][p] * X(2 * p - 1, 2 * q - 1, 2 * r - 1);
-    const T hh = T(g.h);
+    const T hh = A.h;
     diag = hh * sa * T(1.0 / 3.0);
     ax = diag * x[n0] - hh * T(1.0 / 12.0) * s;
 }
@@ -703,14 +705,14 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
             T al = A.alpha[cidx(g, ci, cj, ck)];
             if (al > T(0)) dsum += al;
         }
-        diag = T(g.h) * dsum * T(1.0 / 3.0);
+        diag = A.h * dsum * T(1.0 / 3.0);
         T dn = cr * bn / diag;
         dvec[n] = dn;
         xout[n] = dn;
         return;
     }
     if (rg) {   // regular nodes are interior: the sums above are theirs
-        const T hh = T(g.h);
+        const T hh = A.h;
         diag = hh * T(8.0 / 3.0);
         ax = diag * xn - hh * T(1.0 / 12.0) * (T(2) * fd + bd);
     } else {
@@ -720,6 +722,150 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
     T dn = (cd != T(0) ? cd * dold : T(0)) + cr * r / diag;
     dvec[n] = dn;
     xout[n] = xn + dn;
+}
+
+// ---- level-0 nodal passes in plane-sum form -----------------------------------
+// With E_x, E_y, E_z the sums of the two neighbours along one axis, the
+// regular stencil's face-diagonal sum is (E_x E_y + E_x E_z + E_y E_z) x and
+// its body-diagonal sum E_x E_y E_z x.  Per plane k let A_k = the four axis
+// neighbours within the plane and B_k = its four in-plane diagonals; then
+//   face diagonals of node k = B_k + A_{k-1} + A_{k+1},
+//   body diagonals of node k = B_{k-1} + B_{k+1}.
+// A block of NT_X x NT_Y threads owns as many node columns and marches NT_Z
+// planes: each plane of x (with its one-node halo) is staged in shared memory
+// while the next plane's loads are in flight (two buffers: the one written at
+// plane kk was last read at plane kk - 2, before every thread passed plane
+// kk - 1's barrier), A and B of three planes stay in registers, and the node
+// operands are fetched one plane ahead.  The tile kernel takes the regular
+// and the inactive nodes; the active nodes that are not regular (box faces,
+// cut cells: a few per cent) are listed once and take nd_row in k_nd_irr, so
+// no warp of the march diverges into the general row.  Modes:
+//   ND_CHEB   one Chebyshev step, as k_nd_cheb (out = x_out, d updated);
+//   ND_RESID  out = b - A x, as k_nd_resid;
+//   ND_APPLY  out = A x (x on inactive nodes) with block partials of x.out.
+// The sums are associated differently from the one-node kernels.
+enum { ND_CHEB = 0, ND_RESID = 1, ND_APPLY = 2 };
+constexpr int NT_X = 32, NT_Y = 8, NT_Z = 16;
+constexpr long long kTileNodes = 1 << 20;   // coarse levels with at least this many nodes march too
+constexpr int NT_W = NT_X + 2, NT_H = NT_Y + 2, NT_N = NT_W * NT_H;
+constexpr int NT_SLOTS = (NT_N + NT_X * NT_Y - 1) / (NT_X * NT_Y);
+
+inline dim3 nd_tile_grid(const GridD &g)
+{
+    return dim3((g.nx + 1 + NT_X - 1) / NT_X, (g.ny + 1 + NT_Y - 1) / NT_Y, (g.nz + 1 + NT_Z - 1) / NT_Z);
+}
+
+template <class T, int kMode>
+__global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__restrict__ xin, T *__restrict__ out,
+                                                       T *__restrict__ dvec, const T *__restrict__ b, T cd, T cr,
+                                                       double *__restrict__ part)
+{
+    __shared__ T sx[2][NT_H][NT_W];
+    const GridD &g = A.g;
+    const int NX = g.nx + 1, NY = g.ny + 1, NZ = g.nz + 1;
+    const int sy = NX, sz = NX * NY;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * NT_X + tx;
+    const int i0 = blockIdx.x * NT_X, j0 = blockIdx.y * NT_Y, k0 = blockIdx.z * NT_Z;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool col = i < NX && j < NY;
+    const int kend = min(k0 + NT_Z, NZ);   // nodes k0 .. kend-1; planes k0-1 .. kend
+    // halo-tile slots of this thread: offset within a plane, -1 outside the box
+    int soff[NT_SLOTS];
+#pragma unroll
+    for (int u = 0; u < NT_SLOTS; u++) {
+        const int sl = tid + u * NT_X * NT_Y;
+        const int rr = sl / NT_W, qq = sl - rr * NT_W;
+        const int gi = i0 - 1 + qq, gj = j0 - 1 + rr;
+        soff[u] = (sl < NT_N && gi >= 0 && gi < NX && gj >= 0 && gj < NY) ? gj * sy + gi : -1;
+    }
+    T pre[NT_SLOTS];
+    auto fetch = [&](int kk) {
+#pragma unroll
+        for (int u = 0; u < NT_SLOTS; u++)
+            pre[u] = (soff[u] >= 0 && kk >= 0 && kk < NZ) ? xin[kk * sz + soff[u]] : T(0);
+    };
+    const T dreg = A.h * T(8.0 / 3.0), h12 = A.h * T(1.0 / 12.0);
+    const T crd = cr / dreg;   // regular nodes: cr / diag
+    T Am = 0, Bm = 0, A0 = 0, B0 = 0, X0 = 0;
+    uint8_t on_c = 0, rg_c = 0, on_n = 0, rg_n = 0;
+    T b_c = 0, d_c = 0, b_n = 0, d_n = 0;
+    T v = 0;   // ND_APPLY: this thread's part of x.out
+    fetch(k0 - 1);
+    for (int kk = k0 - 1; kk <= kend; kk++) {
+        T(*S)[NT_W] = sx[kk & 1];
+#pragma unroll
+        for (int u = 0; u < NT_SLOTS; u++) {
+            const int sl = tid + u * NT_X * NT_Y;
+            if (sl < NT_N) (&S[0][0])[sl] = pre[u];
+        }
+        if (kk < kend) fetch(kk + 1);
+        // operands of node kk, finalised at the next plane
+        if (col && kk >= k0 && kk < kend) {
+            const int n = kk * sz + j * sy + i;
+            on_n = A.act[n];
+            rg_n = A.reg[n];
+            if (kMode != ND_APPLY) b_n = b[n];
+            if (kMode == ND_CHEB) d_n = dvec[n];
+        }
+        __syncthreads();
+        const T xc = S[ty + 1][tx + 1];
+        const T An = (S[ty + 1][tx] + S[ty + 1][tx + 2]) + (S[ty][tx + 1] + S[ty + 2][tx + 1]);
+        const T Bn = (S[ty][tx] + S[ty][tx + 2]) + (S[ty + 2][tx] + S[ty + 2][tx + 2]);
+        const int k = kk - 1;
+        if (col && k >= k0 && k < kend) {
+            const int n = k * sz + j * sy + i;
+            if (!on_c) {
+                if (kMode == ND_CHEB) { out[n] = T(0); dvec[n] = T(0); }
+                if (kMode == ND_RESID) out[n] = T(0);
+                if (kMode == ND_APPLY) { out[n] = X0; v += X0 * X0; }
+            } else if (rg_c) {
+                const T ax = dreg * X0 - h12 * (T(2) * (B0 + Am + An) + (Bm + Bn));
+                if (kMode == ND_CHEB) {
+                    const T dn = (cd != T(0) ? cd * d_c : T(0)) + crd * (b_c - ax);
+                    dvec[n] = dn;
+                    out[n] = X0 + dn;
+                }
+                if (kMode == ND_RESID) out[n] = b_c - ax;
+                if (kMode == ND_APPLY) { out[n] = ax; v += X0 * ax; }
+            }
+        }
+        Am = A0; Bm = B0; A0 = An; B0 = Bn; X0 = xc;
+        on_c = on_n; rg_c = rg_n; b_c = b_n; d_c = d_n;
+    }
+    if constexpr (kMode == ND_APPLY) {
+        const double vs = block_sum3_t<T>(v);
+        if (thread_linear() == 0) part[block_linear()] = vs;
+    }
+}
+
+// The listed nodes (active, not regular) of a level-0 pass: nd_row per node,
+// the same outputs as k_nd_tile's mode; ND_APPLY partials per block.
+template <class T, int kMode>
+__global__ void __launch_bounds__(256) k_nd_irr(NdOp<T> A, const int *__restrict__ list, int nlist,
+                                                const T *__restrict__ xin, T *__restrict__ out, T *__restrict__ dvec,
+                                                const T *__restrict__ b, T cd, T cr, double *__restrict__ part)
+{
+    const GridD &g = A.g;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    T v = 0;
+    if (t < nlist) {
+        const int n = list[t];
+        const int NX = g.nx + 1, NY = g.ny + 1;
+        const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
+        T diag, ax;
+        nd_row(A, i, j, k, xin, diag, ax);
+        if (kMode == ND_CHEB) {
+            const T dn = (cd != T(0) ? cd * dvec[n] : T(0)) + cr * (b[n] - ax) / diag;
+            dvec[n] = dn;
+            out[n] = xin[n] + dn;
+        }
+        if (kMode == ND_RESID) out[n] = b[n] - ax;
+        if (kMode == ND_APPLY) { out[n] = ax; v = xin[n] * ax; }
+    }
+    if constexpr (kMode == ND_APPLY) {
+        const double vs = block_sum3_t<T>(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = vs;
+    }
 }
 
 template <class T>
@@ -818,7 +964,7 @@ __device__ inline void plane_pe(const GridD &g, const T *__restrict__ x, int i, 
     E = (c[-1] + c[1]) + (c[-NXn] + c[NXn]);
 }
 
-// q = A p on level 0 with block partials of p.q (k_nd_apply_dot, NZB nodes per thread).
+// q = A p on level 0 with block partials of p.q, NZB nodes per thread.
 // kRes: r = b - A p as an FP32 vector with partials of |r|^2 instead of q
 // and p.q (as k_cc_apply_dot).
 template <class T, bool kRes = false>
@@ -833,7 +979,7 @@ __global__ void __launch_bounds__(256) k_nd_apply_dot_col(NdOp<T> A, const T *__
     double v = 0.0;
     if (i <= g.nx && j <= g.ny && k0 <= g.nz) {
         const bool inner = i > 0 && i < g.nx && j > 0 && j < g.ny;
-        const T hh = T(g.h);
+        const T hh = A.h;
         T Pm = 0, Em = 0, P0 = 0, E0 = 0, Pp = 0, Ep = 0;
         if (inner) {
             plane_pe(g, p, i, j, k0 - 1, Pm, Em);
@@ -867,32 +1013,6 @@ __global__ void __launch_bounds__(256) k_nd_apply_dot_col(NdOp<T> A, const T *__
     }
     v = block_sum3(v);
     if (thread_linear() == 0) part[block_linear()] = v;
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_nd_apply_dot(NdOp<T> A, const T *__restrict__ p, T *__restrict__ q,
-                                                      double *__restrict__ part)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z * blockDim.z + threadIdx.z;
-    const GridD &g = A.g;
-    T v = 0;
-    if (i <= g.nx && j <= g.ny && k <= g.nz) {
-        const int n = nidx(g, i, j, k);
-        T y;
-        if (!A.act[n]) {
-            y = p[n];
-        } else {
-            T diag, ax;
-            nd_row(A, i, j, k, p, diag, ax);
-            y = ax;
-        }
-        q[n] = y;
-        v = p[n] * y;
-    }
-    const double vs = block_sum3_t<T>(v);
-    if (thread_linear() == 0) part[block_linear()] = vs;
 }
 
 __global__ void k_nd_alpha_coarsen(GridD gf, const double *__restrict__ af, GridD gc, double *__restrict__ ac)
@@ -1107,10 +1227,11 @@ __device__ inline void coarse_pass(const CoarseVC<T> &D, int l, int color, int z
     __syncthreads();
 }
 
+// The V-cycle from level 0 of D down to its bottom and back; bs holds the
+// bottom right-hand side in natural order.
 template <class T>
-__global__ void __launch_bounds__(kCoarseThreads) k_cc_coarse_vcycle(CoarseVC<T> D)
+__device__ inline void coarse_vcycle_body(const CoarseVC<T> &D, double *bs)
 {
-    __shared__ double bs[kBottomMax];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int L = D.n - 1;
     for (int l = 0; l < L; l++) {
@@ -1134,7 +1255,7 @@ __global__ void __launch_bounds__(kCoarseThreads) k_cc_coarse_vcycle(CoarseVC<T>
         for (int q = tid; q < D.nb; q += nt) bs[q] = (double)D.b[L][bottom_pos(gb, split, q)];
         __syncthreads();
         for (int r = tid; r < D.nb; r += nt) {
-            const double *__restrict__ row = D.binv + (size_t)r * D.nb;
+            const double *row = D.binv + (size_t)r * D.nb;
             double sum = 0.0;
 #pragma unroll 8
             for (int q = 0; q < D.nb; q++) sum += row[q] * bs[q];
@@ -1148,6 +1269,88 @@ __global__ void __launch_bounds__(kCoarseThreads) k_cc_coarse_vcycle(CoarseVC<T>
         coarse_pass<T, false>(D, l, 0, 0);
         coarse_pass<T, false>(D, l, 1, 0);
         coarse_pass<T, false>(D, l, 0, 0);
+    }
+}
+
+// Asynchronous global -> shared copies of n elements of 4 or 8 bytes
+// (cp.async, one per element and thread: all in flight together).
+template <class E>
+__device__ inline void stage_async(E *dst, const E *src, int n)
+{
+    static_assert(sizeof(E) == 4 || sizeof(E) == 8, "4- or 8-byte elements");
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + s);
+        if constexpr (sizeof(E) == 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + s) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src + s) : "memory");
+    }
+}
+
+// Shared-memory footprint of the staged coarse V-cycle (bytes): the bottom
+// inverse (if staged) first, then per level the diagonal and faces (levels
+// that smooth), x and b.
+template <class T>
+__host__ __device__ inline size_t coarse_stage_bytes(const CoarseVC<T> &D, int with_binv)
+{
+    size_t e = 0;
+    for (int q = 0; q < D.n; q++) {
+        const GridD &g = D.A[q].g;
+        if (q + 1 < D.n) e += (size_t)ncell(g) + nface(g, 0) + nface(g, 1) + nface(g, 2);
+        e += 2 * (size_t)ncell(g);
+    }
+    return e * sizeof(T) + (with_binv ? (size_t)D.nb * D.nb * sizeof(double) : 0);
+}
+constexpr size_t kCoarseStageMax = 200 * 1024;  // dynamic shared memory of the staged form
+
+// kStage: every array the V-cycle touches is first copied into shared memory
+// (the level vectors need no copy: they are written before being read, and
+// b of the top level is the one input), the V-cycle runs there, and x of the
+// top level -- the correction the next finer level reads -- is copied back.
+// Same arithmetic in the same order as the unstaged form.
+template <class T, bool kStage>
+__global__ void __launch_bounds__(kCoarseThreads) k_cc_coarse_vcycle(CoarseVC<T> D, int stage_binv)
+{
+    __shared__ double bs[kBottomMax];
+    if constexpr (!kStage) {
+        coarse_vcycle_body<T>(D, bs);
+    } else {
+        extern __shared__ __align__(16) unsigned char dyn[];
+        // the staged level table lives in shared memory too (thread 0 writes it)
+        __shared__ __align__(16) unsigned char tbl[sizeof(CoarseVC<T>)];
+        CoarseVC<T> &S = *reinterpret_cast<CoarseVC<T> *>(tbl);
+        const bool t0 = threadIdx.x == 0;
+        if (t0) S = D;
+        unsigned char *ptr = dyn;
+        if (stage_binv) {
+            double *bi = (double *)ptr;
+            stage_async(bi, D.binv, D.nb * D.nb);
+            if (t0) S.binv = bi;
+            ptr += (size_t)D.nb * D.nb * sizeof(double);
+        }
+        T *sp = (T *)ptr;
+        for (int q = 0; q < D.n; q++) {
+            const GridD &g = D.A[q].g;
+            const int nc = ncell(g);
+            if (q + 1 < D.n) {
+                T *dg = sp, *fx = dg + nc, *fy = fx + nface(g, 0), *fz = fy + nface(g, 1);
+                stage_async(dg, D.A[q].diag, nc);
+                stage_async(fx, D.A[q].bx, nface(g, 0));
+                stage_async(fy, D.A[q].by, nface(g, 1));
+                stage_async(fz, D.A[q].bz, nface(g, 2));
+                if (t0) { S.A[q].diag = dg; S.A[q].bx = fx; S.A[q].by = fy; S.A[q].bz = fz; }
+                sp = fz + nface(g, 2);
+            }
+            if (q == 0) stage_async(sp + nc, (const T *)D.b[0], nc);
+            if (t0) { S.x[q] = sp; S.b[q] = sp + nc; }
+            sp += 2 * nc;
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();
+        coarse_vcycle_body<T>(S, bs);
+        const int n0 = ncell(D.A[0].g);
+        const T *x0s = S.x[0];
+        for (int s = threadIdx.x; s < n0; s += blockDim.x) D.x[0][s] = x0s[s];
     }
 }
 
@@ -1405,6 +1608,7 @@ NdOp<T> ndop(const NdLevel &L)
 {
     NdOp<T> A;
     A.g = L.g;
+    A.h = (T)L.g.h;
     if constexpr (sizeof(T) == 8) A.alpha = (const T *)L.alpha_d;
     else A.alpha = (const T *)L.alpha_f;
     A.act = L.act;
@@ -1492,8 +1696,15 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         }
         D.binv = H.binv;
         D.nb = H.nb;
-        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_coarse_vcycle<float>" : "cc_coarse_vcycle<double>", 0.0,
-                     k_cc_coarse_vcycle<T>, dim3(1), dim3(1024), 0, D);
+        // staged in shared memory when it fits (with the bottom inverse if that fits too)
+        int sb = coarse_stage_bytes(D, 1) <= kCoarseStageMax;
+        const size_t bytes = coarse_stage_bytes(D, sb);
+        if (bytes <= kCoarseStageMax)
+            EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_coarse_vcycle<float>" : "cc_coarse_vcycle<double>", 0.0,
+                         (k_cc_coarse_vcycle<T, true>), dim3(1), dim3(kCoarseThreads), bytes, D, sb);
+        else
+            EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_coarse_vcycle<float>" : "cc_coarse_vcycle<double>", 0.0,
+                         (k_cc_coarse_vcycle<T, false>), dim3(1), dim3(kCoarseThreads), 0, D, 0);
     } else {
         T *x = Lb ? (T *)c->lx[Lb] : x0;
         const T *b = Lb ? (const T *)c->lb[Lb] : b0;
@@ -1530,6 +1741,26 @@ inline ChebCoef cheb_coef(double lmax)
 
 // Three Chebyshev steps on A x = b, ending in x.  From zero: (0) -> x -> t -> x.
 // Otherwise the start is in t: t -> x -> t -> x.  d is the level's direction.
+// A nodal pass on a level with regular-node flags: the plane march over the
+// regular and inactive nodes, then the listed nodes (their ND_APPLY partials
+// follow the march's).
+inline int nd_tile_blocks(const GridD &g)
+{
+    const dim3 gr = nd_tile_grid(g);
+    return (int)(gr.x * gr.y * gr.z);
+}
+template <class T, int kMode>
+void nd_tile_pass(Ctx *c, const NdLevel &L, const char *name, double nbytes, const T *xin, T *out, T *d,
+                const T *b, T cd, T cr, double *part)
+{
+    const NdOp<T> A = ndop<T>(L);
+    EBV_LAUNCH_P(c, name, nbytes, (k_nd_tile<T, kMode>), nd_tile_grid(L.g), dim3(NT_X, NT_Y), 0, A, xin, out, d, b,
+                 cd, cr, part);
+    if (L.nirr)
+        EBV_LAUNCH(c, (k_nd_irr<T, kMode>), dim3((L.nirr + 255) / 256), dim3(256), 0, A, L.irr, L.nirr, xin, out, d,
+                   b, cd, cr, part ? part + nd_tile_blocks(L.g) : nullptr);
+}
+
 template <class T>
 void nd_smooth(Ctx *c, const NdLevel &L, int l, T *x, T *t, const T *b, bool zero_start)
 {
@@ -1542,9 +1773,15 @@ void nd_smooth(Ctx *c, const NdLevel &L, int l, T *x, T *t, const T *b, bool zer
         // from zero reads only b and alpha and writes d, x)
         const bool z0 = s == 0 && zero_start;
         const double nb = (z0 ? 4.0 : 6.0) * sizeof(T) * (double)nnode(L.g);
-        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "nodal_chebyshev_step<float>" : "nodal_chebyshev_step<double>", nb,
-                     k_nd_cheb<T>, ch_grid(L.g, L.ch_blk), L.ch_blk, 0, A, src, dst, d, b, (T)k.cd[s],
-                     (T)k.cr[s], (int)z0);
+        if (!z0 && L.reg)   // levels with regular-node flags: plane-sum form
+            nd_tile_pass<T, ND_CHEB>(c, L,
+                                   sizeof(T) == 4 ? (l ? "nodal_chebyshev_step<float> L1+" : "nodal_chebyshev_step<float> L0")
+                                                  : (l ? "nodal_chebyshev_step<double> L1+" : "nodal_chebyshev_step<double> L0"),
+                                   nb, src, dst, d, b, (T)k.cd[s], (T)k.cr[s], nullptr);
+        else
+            EBV_LAUNCH_P(c, sizeof(T) == 4 ? "nodal_chebyshev_step<float>" : "nodal_chebyshev_step<double>", nb,
+                         k_nd_cheb<T>, ch_grid(L.g, L.ch_blk), L.ch_blk, 0, A, src, dst, d, b, (T)k.cd[s],
+                         (T)k.cr[s], (int)z0);
         src = dst;
         dst = (dst == x) ? t : x;
     }
@@ -1559,7 +1796,11 @@ void nd_vcycle(Ctx *c, NdHier &H, const T *b0, T *x0)
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
         nd_smooth<T>(c, L, l, x, (T *)c->lt[l], b, true);
-        EBV_LAUNCH(c, k_nd_resid<T>, ngrid(L.g), block3(), 0, ndop<T>(L), x, b, (T *)c->lr[l]);
+        if (L.reg)
+            nd_tile_pass<T, ND_RESID>(c, L, l ? "k_nd_resid<T> tiled L1+" : "k_nd_resid<T> tiled L0", 0.0, x, (T *)c->lr[l], nullptr, b, T(0), T(0),
+                                    nullptr);
+        else
+            EBV_LAUNCH(c, k_nd_resid<T>, ngrid(L.g), block3(), 0, ndop<T>(L), x, b, (T *)c->lr[l]);
         const NdLevel &Lc = H.lv[l + 1];
         EBV_LAUNCH(c, k_nd_restrict<T>, ngrid(Lc.g), block3(), 0, L.g, (const T *)c->lr[l], Lc.g, Lc.act,
                    (T *)c->lb[l + 1]);
@@ -1855,7 +2096,10 @@ struct NdProblem : Problem {
     NdHier *H;
     int n() const override { return nnode(H->lv[0].g); }
     int apply_blocks() const override { return nblocks3(ncolgrid(H->lv[0].g)); }
-    int apply_blocks32() const override { return nblocks3(ngrid(H->lv[0].g)); }
+    int apply_blocks32() const override
+    {
+        return nd_tile_blocks(H->lv[0].g) + (H->lv[0].nirr ? (H->lv[0].nirr + 255) / 256 : 0);
+    }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
         // p, alpha, q: 3 words per node
@@ -1864,8 +2108,8 @@ struct NdProblem : Problem {
     }
     void apply_dot32(Ctx *c, const float *p, float *q) override
     {
-        EBV_LAUNCH_P(c, "nodal_apply_fp32", 12.0 * n(), k_nd_apply_dot<float>, ngrid(H->lv[0].g), block3(), 0,
-                     ndop<float>(H->lv[0]), p, q, c->part);
+        nd_tile_pass<float, ND_APPLY>(c, H->lv[0], "nodal_apply_fp32", 12.0 * n(), p, q, nullptr, nullptr, 0.0f,
+                                    0.0f, c->part);
     }
     void precond(Ctx *c, const double *r, double *z) override { nd_vcycle<double>(c, *H, r, z); }
     void precond32(Ctx *c, const float *r, float *z) override { nd_vcycle<float>(c, *H, r, z); }
@@ -1972,6 +2216,11 @@ ebv_status setup_solvers(Ctx *c)
 {
     const GridD &g = c->g;
     cudaError_t e = cudaSuccess;
+    // the staged coarse V-cycle takes up to kCoarseStageMax of dynamic shared memory
+    EBV_CUDA_TRY(c, cudaFuncSetAttribute(k_cc_coarse_vcycle<float, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseStageMax));
+    EBV_CUDA_TRY(c, cudaFuncSetAttribute(k_cc_coarse_vcycle<double, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoarseStageMax));
     GridD gl[kMaxLevels];
     // cell-centred hierarchies (projection and viscous)
     int L = plan_levels(g, gl, false);
@@ -2028,7 +2277,9 @@ ebv_status setup_solvers(Ctx *c)
         Lv.alpha_d = l ? dalloc<double>(nc, e) : c->alpha;
         Lv.alpha_f = dalloc<float>(nc, e);
         Lv.act = dalloc<uint8_t>(nnode(gn[l]), e);
-        Lv.reg = l ? nullptr : dalloc<uint8_t>(nnode(gn[l]), e);
+        // regular-node flags (and the plane march) where the level is large
+        // enough to fill the GPU with marching blocks
+        Lv.reg = (l == 0 || nnode(gn[l]) >= kTileNodes) ? dalloc<uint8_t>(nnode(gn[l]), e) : nullptr;
         Lv.lam_max = 2.0;
     }
     c->nd.binv = dalloc<double>((size_t)nbn * nbn, e);
@@ -2083,6 +2334,27 @@ ebv_status setup_geometry_solvers(Ctx *c)
         EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(nc)), dim3(256), 0, Lv.alpha_d, Lv.alpha_f, nc);
         EBV_LAUNCH(c, k_nd_active, ngrid(Lv.g), block3(), 0, Lv.g, Lv.alpha_d, Lv.act);
         if (Lv.reg) EBV_LAUNCH(c, k_nd_regular, ngrid(Lv.g), block3(), 0, Lv.g, Lv.alpha_d, Lv.reg);
+    }
+    for (int l = 0; l < N.L; l++) {
+        // levels with regular-node flags: the active nodes that are not
+        // regular, in ascending order, for the listed half of their passes
+        NdLevel &Lv = N.lv[l];
+        if (!Lv.reg) continue;
+        const int nn = nnode(Lv.g);
+        std::vector<uint8_t> act(nn), reg(nn);
+        EBV_CUDA_TRY(c, cudaMemcpyAsync(act.data(), Lv.act, nn, cudaMemcpyDeviceToHost, c->stream));
+        EBV_CUDA_TRY(c, cudaMemcpyAsync(reg.data(), Lv.reg, nn, cudaMemcpyDeviceToHost, c->stream));
+        EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        std::vector<int> irr;
+        for (int n = 0; n < nn; n++)
+            if (act[n] && !reg[n]) irr.push_back(n);
+        if (Lv.irr) cudaFree(Lv.irr);
+        Lv.irr = nullptr;
+        Lv.nirr = (int)irr.size();
+        if (Lv.nirr) {
+            EBV_CUDA_TRY(c, cudaMalloc(&Lv.irr, irr.size() * sizeof(int)));
+            EBV_CUDA_TRY(c, cudaMemcpy(Lv.irr, irr.data(), irr.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
     }
     const NdLevel &B = N.lv[N.L - 1];
     EBV_LAUNCH(c, k_nd_bottom_assemble, dim3((N.nb + 127) / 128), dim3(128), 0, B.g, B.alpha_d, B.act, N.bmat, N.nb);
