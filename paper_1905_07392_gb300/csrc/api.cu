@@ -652,11 +652,13 @@ void ebv_destroy(ebv_ctx *c)
         for (int l = 0; l < H->L; l++) {
             CcLevel &L = H->lv[l];
             cudaFree(L.extra_d); cudaFree(L.extra_f);
-            for (int q = 0; q < H->nvar; q++) { cudaFree(H->vdiag_d[q][l]); cudaFree(H->vdiag_f[q][l]); }
-            for (int d = 0; d < 3; d++) { cudaFree(L.bf_d[d]); cudaFree(L.bf_f[d]); }
+            for (int q = 0; q < H->nvar; q++) {
+                cudaFree(H->vdiag_d[q][l]); cudaFree(H->vdiag_f[q][l]); cudaFree(H->vdinv_f[q][l]);
+            }
+            for (int d = 0; d < 3; d++) { cudaFree(L.bf_d[d]); cudaFree(L.bf_f[d]); cudaFree(L.bf_h[d]); }
             if (h == 0) cudaFree(L.cov);
         }
-        for (int q = 0; q < H->nvar; q++) cudaFree(H->vbinv[q]);
+        for (int q = 0; q < H->nvar; q++) { cudaFree(H->vbinv[q]); cudaFree(H->vdiag_a[q]); }
         cudaFree(H->bmat);
     }
     for (int l = 0; l < c->nd.L; l++) {

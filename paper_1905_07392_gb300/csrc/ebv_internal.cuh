@@ -6,6 +6,7 @@
 // Cell availability for stencils is "inside the box and flag != 0".
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -141,7 +142,13 @@ inline dim3 grid3(int nx, int ny, int nz) { return dim3((nx + 31) / 32, (ny + 3)
 struct CcLevel {
     GridD g;            // dims and h of this level (bc shared)
     double *extra_d = nullptr, *diag_d = nullptr, *bf_d[3] = {nullptr, nullptr, nullptr};
-    float *extra_f = nullptr, *diag_f = nullptr, *bf_f[3] = {nullptr, nullptr, nullptr};
+    float *extra_f = nullptr, *bf_f[3] = {nullptr, nullptr, nullptr};
+    // FP32 multigrid: the V-cycle operator has BF16 face coefficients (bf_h,
+    // rounded from bf_f) and the diagonal diag_f formed from those rounded
+    // faces; the level-0 Krylov operator keeps the FP32 faces with diag_a.
+    float *diag_f = nullptr, *diag_a = nullptr;
+    float *dinv_f = nullptr;   // 1/diag_f (0 where diag_f <= 0), the smoother's multiplier
+    __nv_bfloat16 *bf_h[3] = {nullptr, nullptr, nullptr};
     uint8_t *cov = nullptr;  // 1 where the cell is covered (identity row)
     dim3 gs_blk = dim3(32, 4, 2);  // colour-pass block shape (autotuned per level)
 };
@@ -162,6 +169,8 @@ struct CcHier {
     unsigned side_mask[3] = {0x3fu, 0x3fu, 0x3fu};  // bit s: box side s enters the diagonal
     double *vdiag_d[3][kMaxLevels] = {};
     float *vdiag_f[3][kMaxLevels] = {};
+    float *vdinv_f[3][kMaxLevels] = {};
+    float *vdiag_a[3] = {};   // level 0, FP32 Krylov operator
     double *vbinv[3] = {};
 };
 
@@ -170,7 +179,9 @@ inline void select_variant(CcHier &H, int q)
     for (int l = 0; l < H.L; l++) {
         H.lv[l].diag_d = H.vdiag_d[q][l];
         H.lv[l].diag_f = H.vdiag_f[q][l];
+        H.lv[l].dinv_f = H.vdinv_f[q][l];
     }
+    H.lv[0].diag_a = H.vdiag_a[q];
     H.binv = H.vbinv[q];
 }
 

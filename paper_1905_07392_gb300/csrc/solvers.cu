@@ -119,11 +119,21 @@ namespace {
 // diag = extra + sum of the 6 face coefficients (for the smoother and apply).
 // ===========================================================================
 
-template <class T>
+// Cell-centred operator of one level: diagonal (precision T) and face
+// coefficients (storage F, widened to T when read).
+template <class T, class F = T>
 struct CcOp {
     GridD g;
-    const T *diag, *bx, *by, *bz;
+    const T *diag;
+    const F *bx, *by, *bz;
+    const T *dinv = nullptr;   // FP32 V-cycle: 1/diag (0 where diag <= 0)
 };
+// The V-cycle's operator: in FP32 its faces are stored in BF16 (half the
+// bytes of the face arrays every colour pass reads whole); the Krylov
+// operator it preconditions keeps FP32 faces (CcOp<T>).
+template <class T> struct VFace { using type = T; };
+template <> struct VFace<float> { using type = __nv_bfloat16; };
+template <class T> using VOp = CcOp<T, typename VFace<T>::type>;
 
 // Array layout of the cell-centred multigrid, by precision.  FP64 arrays are
 // in the natural order (x fastest).  FP32 arrays -- the coefficients of every
@@ -148,19 +158,58 @@ __host__ __device__ inline int fidxT(const GridD &g, int d, int i, int j, int k)
     return (k * g.ny + j) * g.nx + (sizeof(T) == 4 ? spos(g.nx, i) : i);
 }
 
+// Positions of cell (i,j,k), of its two x-neighbours and of its six faces in
+// the level's layout (cix / fidxT), from the start of its row.  Row-split
+// (FP32): with t = i/2 the even cells of a row sit at rc + t and the odd ones
+// at rc + h + t (h = ceil(nx/2), rc the row's start), so the x-neighbours of
+// an even cell are odd cells t-1 and t and those of an odd cell even cells t
+// and t+1; x-face rows (nx+1 faces, hf = ceil((nx+1)/2)) start at rc + k ny + j.
+// Natural order (FP64): the plain offsets.  In both, a y-face row is the cell
+// row shifted by k nx and a z-face row the cell row itself.
+struct CellPos {
+    int c, xw, xe, fx0, fx1, fy0, fy1, fz0, fz1;
+};
 template <class T>
-__device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__restrict__ x,
+__device__ inline CellPos cell_pos(const GridD &g, int i, int j, int k)
+{
+    CellPos p;
+    const int rc = (k * g.ny + j) * g.nx;
+    if constexpr (sizeof(T) == 4) {
+        const int t = i >> 1, odd = i & 1, h = (g.nx + 1) >> 1, hf = (g.nx + 2) >> 1;
+        const int rf = rc + k * g.ny + j;
+        p.c = rc + (odd ? h + t : t);
+        p.xw = rc + (odd ? t : h + t - 1);
+        p.xe = rc + (odd ? t + 1 : h + t);
+        p.fx0 = rf + (odd ? hf + t : t);
+        p.fx1 = rf + (odd ? t + 1 : hf + t);
+    } else {
+        p.c = rc + i;
+        p.xw = p.c - 1;
+        p.xe = p.c + 1;
+        p.fx0 = rc + k * g.ny + j + i;
+        p.fx1 = p.fx0 + 1;
+    }
+    p.fy0 = p.c + k * g.nx;
+    p.fy1 = p.fy0 + g.nx;
+    p.fz0 = p.c;
+    p.fz1 = p.c + g.nx * g.ny;
+    return p;
+}
+
+template <class T, class F>
+__device__ inline void cc_row(const CcOp<T, F> &A, int i, int j, int k, const T *__restrict__ x,
                               T &diag, T &off)
 {
     const GridD &g = A.g;
-    const int c = cix<T>(g, i, j, k);
-    const T bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
-    const T byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
-    const T bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
+    const CellPos p = cell_pos<T>(g, i, j, k);
+    const int c = p.c;
+    const T bxl = T(A.bx[p.fx0]), bxh = T(A.bx[p.fx1]);
+    const T byl = T(A.by[p.fy0]), byh = T(A.by[p.fy1]);
+    const T bzl = T(A.bz[p.fz0]), bzh = T(A.bz[p.fz1]);
     diag = A.diag[c];
     T s = 0;
-    if (i > 0) s += bxl * x[cix<T>(g, i - 1, j, k)];
-    if (i < g.nx - 1) s += bxh * x[cix<T>(g, i + 1, j, k)];
+    if (i > 0) s += bxl * x[p.xw];
+    if (i < g.nx - 1) s += bxh * x[p.xe];
     if (j > 0) s += byl * x[c - g.nx];
     if (j < g.ny - 1) s += byh * x[c + g.nx];
     if (k > 0) s += bzl * x[c - g.nx * g.ny];
@@ -185,28 +234,27 @@ __device__ inline void cc_row(const CcOp<T> &A, int i, int j, int k, const T *__
 constexpr int GS_PZ = 2;
 
 // The Gauss-Seidel value of cell (i,j,k): (b + sum beta x_nb) / diag, 0 on
-// cells with no diagonal (see k_cc_gs for kCorr and zero_start).
+// cells with no diagonal (see k_cc_gs for kCorr and zero_start); FP32 levels
+// multiply by the stored inverse diagonal instead of dividing.
 template <class T, bool kCorr>
-__device__ inline T gs_cell(const CcOp<T> &A, const T *__restrict__ x, const T *__restrict__ b, int i, int j,
+__device__ inline T gs_cell(const VOp<T> &A, const T *__restrict__ x, const T *__restrict__ b, int i, int j,
                             int k, int zero_start, const T *__restrict__ xc, const GridD &gc)
 {
     const GridD &g = A.g;
     const int sy = g.nx, sz = g.nx * g.ny;
-    const int c = cix<T>(g, i, j, k);
-    const T diag = A.diag[c], bc = b[c];
+    const CellPos p = cell_pos<T>(g, i, j, k);
+    const int c = p.c;
+    const T diag = sizeof(T) == 4 ? T(0) : A.diag[c], bc = b[c];
     T off = 0;
     if (!zero_start) {
-        const T bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
-        const T byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
-        const T bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
+        const T bxl = T(A.bx[p.fx0]), bxh = T(A.bx[p.fx1]);
+        const T byl = T(A.by[p.fy0]), byh = T(A.by[p.fy1]);
+        const T bzl = T(A.bz[p.fz0]), bzh = T(A.bz[p.fz1]);
         auto cor = [&](int ii, int jj, int kq) -> T {
             return kCorr ? xc[cix<T>(gc, ii >> 1, jj >> 1, kq >> 1)] : T(0);
         };
-        const T xw = i > 0 ? (kCorr ? x[cix<T>(g, i - 1, j, k)] + cor(i - 1, j, k) : x[cix<T>(g, i - 1, j, k)])
-                           : T(0);
-        const T xe = i < g.nx - 1
-                         ? (kCorr ? x[cix<T>(g, i + 1, j, k)] + cor(i + 1, j, k) : x[cix<T>(g, i + 1, j, k)])
-                         : T(0);
+        const T xw = i > 0 ? (kCorr ? x[p.xw] + cor(i - 1, j, k) : x[p.xw]) : T(0);
+        const T xe = i < g.nx - 1 ? (kCorr ? x[p.xe] + cor(i + 1, j, k) : x[p.xe]) : T(0);
         const T xs = j > 0 ? (kCorr ? x[c - sy] + cor(i, j - 1, k) : x[c - sy]) : T(0);
         const T xn = j < g.ny - 1 ? (kCorr ? x[c + sy] + cor(i, j + 1, k) : x[c + sy]) : T(0);
         const T xd = k > 0 ? (kCorr ? x[c - sz] + cor(i, j, k - 1) : x[c - sz]) : T(0);
@@ -218,11 +266,12 @@ __device__ inline T gs_cell(const CcOp<T> &A, const T *__restrict__ x, const T *
         if (k > 0) off += bzl * xd;
         if (k < g.nz - 1) off += bzh * xu;
     }
+    if constexpr (sizeof(T) == 4) return (bc + off) * A.dinv[c];
     return diag > T(0) ? (bc + off) / diag : T(0);
 }
 
 template <class T, bool kCorr = false>
-__global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, const T *__restrict__ b,
+__global__ void __launch_bounds__(256) k_cc_gs(VOp<T> A, T *__restrict__ x, const T *__restrict__ b,
                                                int color, int zero_start, const T *__restrict__ xc = nullptr,
                                                GridD gc = GridD())
 {
@@ -256,23 +305,35 @@ __global__ void __launch_bounds__(256) k_cc_gs(CcOp<T> A, T *__restrict__ x, con
 
 // Residual of the 8 children of coarse cell (I,J,K), averaged.
 template <class T>
-__device__ inline T rr_cell(const CcOp<T> &A, const T *__restrict__ x, const T *__restrict__ b, int I, int J,
+__device__ inline T rr_cell(const VOp<T> &A, const T *__restrict__ x, const T *__restrict__ b, int I, int J,
                             int K)
 {
+    // child by child with the layout's index functions: with the children's
+    // parities known after unrolling these fold to row offsets in few
+    // registers (this kernel is latency-bound: occupancy counts more)
+    const GridD &g = A.g;
     T s = 0;
     for (int o = 0; o < 8; o++) {
-        int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
-        T diag, off;
-        cc_row(A, i, j, k, x, diag, off);
-        int c = cix<T>(A.g, i, j, k);
-        s += b[c] - (diag * x[c] - off);
+        const int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
+        const int c = cix<T>(g, i, j, k);
+        const T bxl = T(A.bx[fidxT<T>(g, 0, i, j, k)]), bxh = T(A.bx[fidxT<T>(g, 0, i + 1, j, k)]);
+        const T byl = T(A.by[fidxT<T>(g, 1, i, j, k)]), byh = T(A.by[fidxT<T>(g, 1, i, j + 1, k)]);
+        const T bzl = T(A.bz[fidxT<T>(g, 2, i, j, k)]), bzh = T(A.bz[fidxT<T>(g, 2, i, j, k + 1)]);
+        T off = 0;
+        if (i > 0) off += bxl * x[cix<T>(g, i - 1, j, k)];
+        if (i < g.nx - 1) off += bxh * x[cix<T>(g, i + 1, j, k)];
+        if (j > 0) off += byl * x[c - g.nx];
+        if (j < g.ny - 1) off += byh * x[c + g.nx];
+        if (k > 0) off += bzl * x[c - g.nx * g.ny];
+        if (k < g.nz - 1) off += bzh * x[c + g.nx * g.ny];
+        s += b[c] - (A.diag[c] * x[c] - off);
     }
     return s * T(0.125);
 }
 
 // Residual of the 8 children, averaged into the coarse right-hand side.
 template <class T>
-__global__ void __launch_bounds__(256) k_cc_resid_restrict(CcOp<T> A, const T *__restrict__ x,
+__global__ void __launch_bounds__(256) k_cc_resid_restrict(VOp<T> A, const T *__restrict__ x,
                                                            const T *__restrict__ b, GridD gc,
                                                            T *__restrict__ bc)
 {
@@ -334,10 +395,14 @@ __global__ void k_cc_coarsen(GridD gf, const T *__restrict__ ef, const T *__rest
 // variants of the operator: a face on box side s counts for variant q only if
 // bit s of side mask q (bits 6q .. 6q+5 of masks) is set.  Sums in the same
 // order for every variant, so a variant with all bits set is the plain sum.
-template <class T>
+// kRound: the faces as the V-cycle stores them (rounded to BF16), so that its
+// operator keeps diag = extra + sum of its own faces.
+template <class T, bool kRound = false>
 __global__ void k_cc_make_diag(GridD g, const T *__restrict__ extra, const T *__restrict__ bx,
                                const T *__restrict__ by, const T *__restrict__ bz, int nvar, unsigned masks,
-                               T *__restrict__ d0, T *__restrict__ d1, T *__restrict__ d2)
+                               T *__restrict__ d0, T *__restrict__ d1, T *__restrict__ d2,
+                               T *__restrict__ i0 = nullptr, T *__restrict__ i1 = nullptr,
+                               T *__restrict__ i2 = nullptr)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -345,19 +410,25 @@ __global__ void k_cc_make_diag(GridD g, const T *__restrict__ extra, const T *__
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
     const int c = cix<T>(g, i, j, k);
     const T e = extra[c];
-    const T f[6] = {bx[fidxT<T>(g, 0, i, j, k)], bx[fidxT<T>(g, 0, i + 1, j, k)],
-                    by[fidxT<T>(g, 1, i, j, k)], by[fidxT<T>(g, 1, i, j + 1, k)],
-                    bz[fidxT<T>(g, 2, i, j, k)], bz[fidxT<T>(g, 2, i, j, k + 1)]};
+    T f[6] = {bx[fidxT<T>(g, 0, i, j, k)], bx[fidxT<T>(g, 0, i + 1, j, k)],
+              by[fidxT<T>(g, 1, i, j, k)], by[fidxT<T>(g, 1, i, j + 1, k)],
+              bz[fidxT<T>(g, 2, i, j, k)], bz[fidxT<T>(g, 2, i, j, k + 1)]};
+    if constexpr (kRound) {
+#pragma unroll
+        for (int t = 0; t < 6; t++) f[t] = __bfloat162float(__float2bfloat16_rn(f[t]));
+    }
     // box side of each face, -1 for a face between two cells
     const int sd[6] = {i == 0 ? 0 : -1, i == g.nx - 1 ? 1 : -1, j == 0 ? 2 : -1,
                        j == g.ny - 1 ? 3 : -1, k == 0 ? 4 : -1, k == g.nz - 1 ? 5 : -1};
     T *out[3] = {d0, d1, d2};
+    T *inv[3] = {i0, i1, i2};
     for (int q = 0; q < nvar; q++) {
         const unsigned m = masks >> (6 * q);
         T s = e;
 #pragma unroll
         for (int t = 0; t < 6; t++) s += (sd[t] < 0 || ((m >> sd[t]) & 1u)) ? f[t] : T(0);
         out[q][c] = s;
+        if (inv[q]) inv[q][c] = s > T(0) ? T(1) / s : T(0);
     }
 }
 
@@ -396,6 +467,13 @@ __global__ void k_to_split(GridD g, int d, const double *__restrict__ a, float *
         const int i = s % mx, j = (s / mx) % my, k = s / (mx * my);
         b[d < 0 ? cix<float>(g, i, j, k) : fidxT<float>(g, d, i, j, k)] = (float)a[s];
     }
+}
+
+// FP32 face coefficients -> the V-cycle's BF16 copy (same layout)
+__global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *__restrict__ b, int n)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        b[s] = __float2bfloat16_rn(a[s]);
 }
 
 // x += e with e an FP32 row-split vector
@@ -742,9 +820,12 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
 // no warp of the march diverges into the general row.  Modes:
 //   ND_CHEB   one Chebyshev step, as k_nd_cheb (out = x_out, d updated);
 //   ND_RESID  out = b - A x, as k_nd_resid;
-//   ND_APPLY  out = A x (x on inactive nodes) with block partials of x.out.
+//   ND_APPLY  out = A x (x on inactive nodes) with block partials of x.out;
+//   ND_RES32  r = b - A x (b - x on inactive nodes) in T, stored to the FP32
+//             vector out32, with block partials of |r|^2 (the refinement
+//             solver's true residual; T = double).
 // The sums are associated differently from the one-node kernels.
-enum { ND_CHEB = 0, ND_RESID = 1, ND_APPLY = 2 };
+enum { ND_CHEB = 0, ND_RESID = 1, ND_APPLY = 2, ND_RES32 = 3 };
 constexpr int NT_X = 32, NT_Y = 8, NT_Z = 16;
 constexpr long long kTileNodes = 1 << 20;   // coarse levels with at least this many nodes march too
 constexpr int NT_W = NT_X + 2, NT_H = NT_Y + 2, NT_N = NT_W * NT_H;
@@ -758,7 +839,7 @@ inline dim3 nd_tile_grid(const GridD &g)
 template <class T, int kMode>
 __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__restrict__ xin, T *__restrict__ out,
                                                        T *__restrict__ dvec, const T *__restrict__ b, T cd, T cr,
-                                                       double *__restrict__ part)
+                                                       double *__restrict__ part, float *__restrict__ out32)
 {
     __shared__ T sx[2][NT_H][NT_W];
     const GridD &g = A.g;
@@ -789,7 +870,7 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
     T Am = 0, Bm = 0, A0 = 0, B0 = 0, X0 = 0;
     uint8_t on_c = 0, rg_c = 0, on_n = 0, rg_n = 0;
     T b_c = 0, d_c = 0, b_n = 0, d_n = 0;
-    T v = 0;   // ND_APPLY: this thread's part of x.out
+    T v = 0;   // ND_APPLY, ND_RES32: this thread's part of x.out, |r|^2
     fetch(k0 - 1);
     for (int kk = k0 - 1; kk <= kend; kk++) {
         T(*S)[NT_W] = sx[kk & 1];
@@ -818,6 +899,11 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 if (kMode == ND_CHEB) { out[n] = T(0); dvec[n] = T(0); }
                 if (kMode == ND_RESID) out[n] = T(0);
                 if (kMode == ND_APPLY) { out[n] = X0; v += X0 * X0; }
+                if (kMode == ND_RES32) {
+                    const T rs = b_c - X0;
+                    out32[n] = (float)rs;
+                    v += rs * rs;
+                }
             } else if (rg_c) {
                 const T ax = dreg * X0 - h12 * (T(2) * (B0 + Am + An) + (Bm + Bn));
                 if (kMode == ND_CHEB) {
@@ -827,12 +913,17 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 }
                 if (kMode == ND_RESID) out[n] = b_c - ax;
                 if (kMode == ND_APPLY) { out[n] = ax; v += X0 * ax; }
+                if (kMode == ND_RES32) {
+                    const T rs = b_c - ax;
+                    out32[n] = (float)rs;
+                    v += rs * rs;
+                }
             }
         }
         Am = A0; Bm = B0; A0 = An; B0 = Bn; X0 = xc;
         on_c = on_n; rg_c = rg_n; b_c = b_n; d_c = d_n;
     }
-    if constexpr (kMode == ND_APPLY) {
+    if constexpr (kMode == ND_APPLY || kMode == ND_RES32) {
         const double vs = block_sum3_t<T>(v);
         if (thread_linear() == 0) part[block_linear()] = vs;
     }
@@ -843,7 +934,8 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
 template <class T, int kMode>
 __global__ void __launch_bounds__(256) k_nd_irr(NdOp<T> A, const int *__restrict__ list, int nlist,
                                                 const T *__restrict__ xin, T *__restrict__ out, T *__restrict__ dvec,
-                                                const T *__restrict__ b, T cd, T cr, double *__restrict__ part)
+                                                const T *__restrict__ b, T cd, T cr, double *__restrict__ part,
+                                                float *__restrict__ out32)
 {
     const GridD &g = A.g;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -861,8 +953,13 @@ __global__ void __launch_bounds__(256) k_nd_irr(NdOp<T> A, const int *__restrict
         }
         if (kMode == ND_RESID) out[n] = b[n] - ax;
         if (kMode == ND_APPLY) { out[n] = ax; v = xin[n] * ax; }
+        if (kMode == ND_RES32) {
+            const T rs = b[n] - ax;
+            out32[n] = (float)rs;
+            v = rs * rs;
+        }
     }
-    if constexpr (kMode == ND_APPLY) {
+    if constexpr (kMode == ND_APPLY || kMode == ND_RES32) {
         const double vs = block_sum3_t<T>(v);
         if (threadIdx.x == 0) part[blockIdx.x] = vs;
     }
@@ -941,80 +1038,6 @@ __global__ void k_nd_prolong(GridD gf, const uint8_t *__restrict__ actf, GridD g
     xout[n] = xin[n] + wi * wj * wk * s;
 }
 
-// ---- level-0 nodal kernels in columns ---------------------------------------------
-// On the finest level most nodes are regular (all 8 cells full), where the row
-// is  ax = (8/3) h x_c - (h/12) (2 fd + bd)  with fd the 12 face-diagonal and
-// bd the 8 body-diagonal neighbours.  Along a column (i, j), plane k's 3x3
-// patch gives P_k (its 4 corners) and E_k (its 4 edge neighbours), and
-//   fd = P_k + E_{k-1} + E_{k+1},   bd = P_{k-1} + P_{k+1},
-// so a thread that walks NZB nodes up a column loads each plane once and
-// forms each row from rolling sums: about half the FP64 arithmetic of the
-// per-node form, which is what bounds the FP64 apply on this GPU (in FP32 the
-// per-node form, with four times the threads in flight, is faster).  Other
-// nodes take nd_row.
-constexpr int NZB = 4;
-
-template <class T>
-__device__ inline void plane_pe(const GridD &g, const T *__restrict__ x, int i, int j, int k, T &P, T &E)
-{
-    if ((unsigned)k > (unsigned)g.nz) { P = T(0); E = T(0); return; }
-    const int NXn = g.nx + 1;
-    const T *c = x + nidx(g, i, j, k);
-    P = (c[-1 - NXn] + c[1 - NXn]) + (c[-1 + NXn] + c[1 + NXn]);
-    E = (c[-1] + c[1]) + (c[-NXn] + c[NXn]);
-}
-
-// q = A p on level 0 with block partials of p.q, NZB nodes per thread.
-// kRes: r = b - A p as an FP32 vector with partials of |r|^2 instead of q
-// and p.q (as k_cc_apply_dot).
-template <class T, bool kRes = false>
-__global__ void __launch_bounds__(256) k_nd_apply_dot_col(NdOp<T> A, const T *__restrict__ p, T *__restrict__ q,
-                                                          double *__restrict__ part, const T *__restrict__ b = nullptr,
-                                                          float *__restrict__ r32 = nullptr)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k0 = (blockIdx.z * blockDim.z + threadIdx.z) * NZB;
-    const GridD &g = A.g;
-    double v = 0.0;
-    if (i <= g.nx && j <= g.ny && k0 <= g.nz) {
-        const bool inner = i > 0 && i < g.nx && j > 0 && j < g.ny;
-        const T hh = A.h;
-        T Pm = 0, Em = 0, P0 = 0, E0 = 0, Pp = 0, Ep = 0;
-        if (inner) {
-            plane_pe(g, p, i, j, k0 - 1, Pm, Em);
-            plane_pe(g, p, i, j, k0, P0, E0);
-        }
-        for (int h = 0; h < NZB; h++) {
-            const int k = k0 + h;
-            if (k > g.nz) break;
-            if (inner) plane_pe(g, p, i, j, k + 1, Pp, Ep);
-            const int n = nidx(g, i, j, k);
-            T y;
-            if (!A.act[n]) {
-                y = p[n];
-            } else if (inner && A.reg[n]) {
-                y = hh * T(8.0 / 3.0) * p[n] - hh * T(1.0 / 12.0) * (T(2) * (P0 + Em + Ep) + (Pm + Pp));
-            } else {
-                T diag, ax;
-                nd_row(A, i, j, k, p, diag, ax);
-                y = ax;
-            }
-            if constexpr (kRes) {
-                const T rs = b[n] - y;
-                r32[n] = (float)rs;
-                v += (double)(rs * rs);
-            } else {
-                q[n] = y;
-                v += (double)(p[n] * y);
-            }
-            Pm = P0; Em = E0; P0 = Pp; E0 = Ep;
-        }
-    }
-    v = block_sum3(v);
-    if (thread_linear() == 0) part[block_linear()] = v;
-}
-
 __global__ void k_nd_alpha_coarsen(GridD gf, const double *__restrict__ af, GridD gc, double *__restrict__ ac)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1066,7 +1089,7 @@ __global__ void k_nd_active(GridD g, const double *__restrict__ alpha, uint8_t *
 // ===========================================================================
 
 template <class T>
-__global__ void k_cc_bottom_assemble(CcOp<T> A, double *__restrict__ M, int nb)
+__global__ void k_cc_bottom_assemble(VOp<T> A, double *__restrict__ M, int nb)
 {
     const GridD &g = A.g;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nb; r += gridDim.x * blockDim.x) {
@@ -1074,9 +1097,9 @@ __global__ void k_cc_bottom_assemble(CcOp<T> A, double *__restrict__ M, int nb)
         for (int s = 0; s < 2 * nb; s++) row[s] = 0.0;
         row[nb + r] = 1.0;
         int i = r % g.nx, j = (r / g.nx) % g.ny, k = r / (g.nx * g.ny);
-        double bxl = A.bx[fidxT<T>(g, 0, i, j, k)], bxh = A.bx[fidxT<T>(g, 0, i + 1, j, k)];
-        double byl = A.by[fidxT<T>(g, 1, i, j, k)], byh = A.by[fidxT<T>(g, 1, i, j + 1, k)];
-        double bzl = A.bz[fidxT<T>(g, 2, i, j, k)], bzh = A.bz[fidxT<T>(g, 2, i, j, k + 1)];
+        double bxl = (double)T(A.bx[fidxT<T>(g, 0, i, j, k)]), bxh = (double)T(A.bx[fidxT<T>(g, 0, i + 1, j, k)]);
+        double byl = (double)T(A.by[fidxT<T>(g, 1, i, j, k)]), byh = (double)T(A.by[fidxT<T>(g, 1, i, j + 1, k)]);
+        double bzl = (double)T(A.bz[fidxT<T>(g, 2, i, j, k)]), bzh = (double)T(A.bz[fidxT<T>(g, 2, i, j, k + 1)]);
         double diag = (double)A.diag[cix<T>(g, i, j, k)];
         row[r] = diag > 0.0 ? diag : 1.0;
         if (i > 0) row[r - 1] = -bxl;
@@ -1180,7 +1203,7 @@ constexpr int kCoarseMax = 8;
 template <class T>
 struct CoarseVC {
     int n;                    // levels handled; the last is the bottom
-    CcOp<T> A[kCoarseMax];
+    VOp<T> A[kCoarseMax];
     T *x[kCoarseMax];
     T *b[kCoarseMax];         // b[0] given, the others written by restriction
     const double *binv;       // bottom inverse (natural numbering)
@@ -1197,7 +1220,7 @@ constexpr int kCoarseSlots = (kCoarseCells + kCoarseThreads - 1) / kCoarseThread
 template <class T, bool kCorr>
 __device__ inline void coarse_pass(const CoarseVC<T> &D, int l, int color, int zero_start)
 {
-    const CcOp<T> &A = D.A[l];
+    const VOp<T> &A = D.A[l];
     const GridD &g = A.g;
     const int hx = (g.nx + 1) >> 1, slots = hx * g.ny * g.nz;
     T *x = D.x[l];
@@ -1272,34 +1295,45 @@ __device__ inline void coarse_vcycle_body(const CoarseVC<T> &D, double *bs)
     }
 }
 
-// Asynchronous global -> shared copies of n elements of 4 or 8 bytes
-// (cp.async, one per element and thread: all in flight together).
+// Asynchronous global -> shared copies of n elements (cp.async, 4 or 8 bytes
+// per copy, all in flight together).  2-byte elements go as 4-byte pairs:
+// both addresses 4-byte aligned, and for odd n the source holds one element
+// more (the face arrays of the V-cycle are allocated with one spare).
 template <class E>
 __device__ inline void stage_async(E *dst, const E *src, int n)
 {
-    static_assert(sizeof(E) == 4 || sizeof(E) == 8, "4- or 8-byte elements");
-    for (int s = threadIdx.x; s < n; s += blockDim.x) {
-        const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + s);
-        if constexpr (sizeof(E) == 4)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + s) : "memory");
-        else
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src + s) : "memory");
+    static_assert(sizeof(E) == 2 || sizeof(E) == 4 || sizeof(E) == 8, "2-, 4- or 8-byte elements");
+    if constexpr (sizeof(E) == 2) {
+        stage_async((uint32_t *)dst, (const uint32_t *)src, (n + 1) >> 1);
+    } else {
+        for (int s = threadIdx.x; s < n; s += blockDim.x) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + s);
+            if constexpr (sizeof(E) == 4)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + s) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src + s) : "memory");
+        }
     }
 }
 
-// Shared-memory footprint of the staged coarse V-cycle (bytes): the bottom
-// inverse (if staged) first, then per level the diagonal and faces (levels
-// that smooth), x and b.
+// Shared-memory layout of the staged coarse V-cycle: the bottom inverse (if
+// staged) first, then per level the diagonal and the three face arrays
+// (levels that smooth), x and b; every array starts on a 16-byte boundary.
+__host__ __device__ inline size_t stage_align(size_t b) { return (b + 15) & ~(size_t)15; }
 template <class T>
 __host__ __device__ inline size_t coarse_stage_bytes(const CoarseVC<T> &D, int with_binv)
 {
-    size_t e = 0;
+    using F = typename VFace<T>::type;
+    size_t b = with_binv ? stage_align((size_t)D.nb * D.nb * sizeof(double)) : 0;
     for (int q = 0; q < D.n; q++) {
         const GridD &g = D.A[q].g;
-        if (q + 1 < D.n) e += (size_t)ncell(g) + nface(g, 0) + nface(g, 1) + nface(g, 2);
-        e += 2 * (size_t)ncell(g);
+        if (q + 1 < D.n) {
+            b += (sizeof(T) == 4 ? 2 : 1) * stage_align((size_t)ncell(g) * sizeof(T));   // diag (and 1/diag)
+            for (int d = 0; d < 3; d++) b += stage_align((size_t)nface(g, d) * sizeof(F));
+        }
+        b += 2 * stage_align((size_t)ncell(g) * sizeof(T));
     }
-    return e * sizeof(T) + (with_binv ? (size_t)D.nb * D.nb * sizeof(double) : 0);
+    return b;
 }
 constexpr size_t kCoarseStageMax = 200 * 1024;  // dynamic shared memory of the staged form
 
@@ -1321,29 +1355,42 @@ __global__ void __launch_bounds__(kCoarseThreads) k_cc_coarse_vcycle(CoarseVC<T>
         CoarseVC<T> &S = *reinterpret_cast<CoarseVC<T> *>(tbl);
         const bool t0 = threadIdx.x == 0;
         if (t0) S = D;
+        using F = typename VFace<T>::type;
         unsigned char *ptr = dyn;
         if (stage_binv) {
             double *bi = (double *)ptr;
             stage_async(bi, D.binv, D.nb * D.nb);
             if (t0) S.binv = bi;
-            ptr += (size_t)D.nb * D.nb * sizeof(double);
+            ptr += stage_align((size_t)D.nb * D.nb * sizeof(double));
         }
-        T *sp = (T *)ptr;
         for (int q = 0; q < D.n; q++) {
             const GridD &g = D.A[q].g;
             const int nc = ncell(g);
             if (q + 1 < D.n) {
-                T *dg = sp, *fx = dg + nc, *fy = fx + nface(g, 0), *fz = fy + nface(g, 1);
+                T *dg = (T *)ptr;
+                ptr += stage_align((size_t)nc * sizeof(T));
                 stage_async(dg, D.A[q].diag, nc);
-                stage_async(fx, D.A[q].bx, nface(g, 0));
-                stage_async(fy, D.A[q].by, nface(g, 1));
-                stage_async(fz, D.A[q].bz, nface(g, 2));
-                if (t0) { S.A[q].diag = dg; S.A[q].bx = fx; S.A[q].by = fy; S.A[q].bz = fz; }
-                sp = fz + nface(g, 2);
+                if constexpr (sizeof(T) == 4) {
+                    T *di = (T *)ptr;
+                    ptr += stage_align((size_t)nc * sizeof(T));
+                    stage_async(di, D.A[q].dinv, nc);
+                    if (t0) S.A[q].dinv = di;
+                }
+                F *fc[3];
+                const F *src[3] = {D.A[q].bx, D.A[q].by, D.A[q].bz};
+                for (int d = 0; d < 3; d++) {
+                    fc[d] = (F *)ptr;
+                    ptr += stage_align((size_t)nface(g, d) * sizeof(F));
+                    stage_async(fc[d], src[d], nface(g, d));
+                }
+                if (t0) { S.A[q].diag = dg; S.A[q].bx = fc[0]; S.A[q].by = fc[1]; S.A[q].bz = fc[2]; }
             }
-            if (q == 0) stage_async(sp + nc, (const T *)D.b[0], nc);
-            if (t0) { S.x[q] = sp; S.b[q] = sp + nc; }
-            sp += 2 * nc;
+            T *xs = (T *)ptr;
+            ptr += stage_align((size_t)nc * sizeof(T));
+            T *bs2 = (T *)ptr;
+            ptr += stage_align((size_t)nc * sizeof(T));
+            if (q == 0) stage_async(bs2, (const T *)D.b[0], nc);
+            if (t0) { S.x[q] = xs; S.b[q] = bs2; }
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
@@ -1571,10 +1618,9 @@ __global__ void k_zero_inactive(int n, const uint8_t *__restrict__ act, double *
 
 inline dim3 cgrid(const GridD &g) { return grid3(g.nx, g.ny, g.nz); }
 inline dim3 ngrid(const GridD &g) { return grid3(g.nx + 1, g.ny + 1, g.nz + 1); }
-// columns of NZB nodes along z (the level-0 nodal kernels)
-inline dim3 ncolgrid(const GridD &g) { return grid3(g.nx + 1, g.ny + 1, (g.nz + NZB) / NZB); }
 inline int nblocks3(dim3 b) { return b.x * b.y * b.z; }
 
+// The Krylov operator of level L (FP32: level 0 only, FP32 faces, diag_a).
 template <class T>
 CcOp<T> ccop(const CcLevel &L)
 {
@@ -1583,12 +1629,28 @@ CcOp<T> ccop(const CcLevel &L)
     if constexpr (sizeof(T) == 8) {
         A.diag = (const T *)L.diag_d; A.bx = (const T *)L.bf_d[0]; A.by = (const T *)L.bf_d[1]; A.bz = (const T *)L.bf_d[2];
     } else {
-        A.diag = (const T *)L.diag_f; A.bx = (const T *)L.bf_f[0]; A.by = (const T *)L.bf_f[1]; A.bz = (const T *)L.bf_f[2];
+        A.diag = (const T *)L.diag_a; A.bx = (const T *)L.bf_f[0]; A.by = (const T *)L.bf_f[1]; A.bz = (const T *)L.bf_f[2];
     }
     return A;
 }
 
-// diagonals of every variant of level l from its extra and faces, in precision T.
+// The V-cycle operator of level L (FP32: BF16 faces, diag_f).
+template <class T>
+VOp<T> vop(const CcLevel &L)
+{
+    VOp<T> A;
+    A.g = L.g;
+    if constexpr (sizeof(T) == 8) {
+        A.diag = (const T *)L.diag_d; A.bx = (const T *)L.bf_d[0]; A.by = (const T *)L.bf_d[1]; A.bz = (const T *)L.bf_d[2];
+    } else {
+        A.diag = (const T *)L.diag_f; A.bx = L.bf_h[0]; A.by = L.bf_h[1]; A.bz = L.bf_h[2];
+        A.dinv = (const T *)L.dinv_f;
+    }
+    return A;
+}
+
+// diagonals of every variant of level l from its extra and faces, in precision
+// T (FP32: the V-cycle's, from the faces rounded as it stores them).
 template <class T>
 void cc_make_diag(Ctx *c, CcHier &H, int l)
 {
@@ -1599,8 +1661,18 @@ void cc_make_diag(Ctx *c, CcHier &H, int l)
         EBV_LAUNCH(c, k_cc_make_diag<double>, cgrid(L.g), block3(), 0, L.g, L.extra_d, L.bf_d[0], L.bf_d[1],
                    L.bf_d[2], H.nvar, masks, H.vdiag_d[0][l], H.vdiag_d[1][l], H.vdiag_d[2][l]);
     else
-        EBV_LAUNCH(c, k_cc_make_diag<float>, cgrid(L.g), block3(), 0, L.g, L.extra_f, L.bf_f[0], L.bf_f[1],
-                   L.bf_f[2], H.nvar, masks, H.vdiag_f[0][l], H.vdiag_f[1][l], H.vdiag_f[2][l]);
+        EBV_LAUNCH(c, (k_cc_make_diag<float, true>), cgrid(L.g), block3(), 0, L.g, L.extra_f, L.bf_f[0], L.bf_f[1],
+                   L.bf_f[2], H.nvar, masks, H.vdiag_f[0][l], H.vdiag_f[1][l], H.vdiag_f[2][l], H.vdinv_f[0][l],
+                   H.vdinv_f[1][l], H.vdinv_f[2][l]);
+}
+
+// The V-cycle's BF16 copy of the FP32 faces of level L.
+inline void cc_faces_bf16(Ctx *c, CcLevel &L)
+{
+    for (int d = 0; d < 3; d++) {
+        const int n = nface(L.g, d);
+        EBV_LAUNCH(c, k_to_bf16, dim3(std::min(kReduceBlocks, (n + 255) / 256)), dim3(256), 0, L.bf_f[d], L.bf_h[d], n);
+    }
 }
 
 template <class T>
@@ -1647,12 +1719,12 @@ void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool re
                 const T *xc = nullptr, const GridD *gc = nullptr)
 {
     (void)t;
-    CcOp<T> A = ccop<T>(L);
+    VOp<T> A = vop<T>(L);
     const int c0 = red_first ? 0 : 1;
     const GridD &g = L.g;
     // algorithmic bytes of one colour pass: half of one sweep's x read and
-    // write, b, diagonal and 3 face coefficients
-    const double nb = 3.5 * sizeof(T) * (double)ncell(g);
+    // write, b, diagonal and 3 face coefficients (in their storage type)
+    const double nb = 0.5 * ((4.0 * sizeof(T) + 3.0 * sizeof(typename VFace<T>::type)) * (double)ncell(g));
     // threads: x-pairs x rows x groups of GS_PZ planes, in the level's block shape
     const dim3 bk = L.gs_blk, gr = gs_grid(g, bk);
     const char *name = kGsName[sizeof(T) == 4][l < 7 ? l : 7];
@@ -1680,9 +1752,10 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         const T *b = l ? (const T *)c->lb[l] : b0;
         cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, true, true);
         const CcLevel &Lc = H.lv[l + 1];
+        // x, b, diagonal, 3 faces (storage type) read, 1/8 word written
         EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_residual_restrict<float>" : "cc_residual_restrict<double>",
-                     (6.0 + 1.0 / 8.0) * sizeof(T) * (double)ncell(L.g),
-                     k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, ccop<T>(L), x, b, Lc.g,
+                     ((3.0 + 1.0 / 8.0) * sizeof(T) + 3.0 * sizeof(typename VFace<T>::type)) * (double)ncell(L.g),
+                     k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, vop<T>(L), x, b, Lc.g,
                      (T *)c->lb[l + 1]);
     }
     if (l0 < Lb) {
@@ -1690,7 +1763,7 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         D.n = Lb - l0 + 1;
         for (int q = 0; q < D.n; q++) {
             const int l = l0 + q;
-            D.A[q] = ccop<T>(H.lv[l]);
+            D.A[q] = vop<T>(H.lv[l]);
             D.x[q] = l ? (T *)c->lx[l] : x0;
             D.b[q] = l ? (T *)c->lb[l] : (T *)b0;
         }
@@ -1751,15 +1824,17 @@ inline int nd_tile_blocks(const GridD &g)
 }
 template <class T, int kMode>
 void nd_tile_pass(Ctx *c, const NdLevel &L, const char *name, double nbytes, const T *xin, T *out, T *d,
-                const T *b, T cd, T cr, double *part)
+                const T *b, T cd, T cr, double *part, float *out32 = nullptr)
 {
     const NdOp<T> A = ndop<T>(L);
     EBV_LAUNCH_P(c, name, nbytes, (k_nd_tile<T, kMode>), nd_tile_grid(L.g), dim3(NT_X, NT_Y), 0, A, xin, out, d, b,
-                 cd, cr, part);
+                 cd, cr, part, out32);
     if (L.nirr)
         EBV_LAUNCH(c, (k_nd_irr<T, kMode>), dim3((L.nirr + 255) / 256), dim3(256), 0, A, L.irr, L.nirr, xin, out, d,
-                   b, cd, cr, part ? part + nd_tile_blocks(L.g) : nullptr);
+                   b, cd, cr, part ? part + nd_tile_blocks(L.g) : nullptr, out32);
 }
+// partial sums written by nd_tile_pass on level L
+inline int nd_tile_parts(const NdLevel &L) { return nd_tile_blocks(L.g) + (L.nirr ? (L.nirr + 255) / 256 : 0); }
 
 template <class T>
 void nd_smooth(Ctx *c, const NdLevel &L, int l, T *x, T *t, const T *b, bool zero_start)
@@ -1831,6 +1906,7 @@ struct Problem {
     virtual int n() const = 0;
     virtual int apply_blocks() const = 0;      // partial sums written by apply_dot
     virtual int apply_blocks32() const { return apply_blocks(); }   // by apply_dot32
+    virtual int resid_blocks() const { return apply_blocks(); }     // by resid32
     // q = A p with block partials of p.q in c->part, in FP64 or FP32
     virtual void apply_dot(Ctx *c, const double *p, double *q) = 0;
     virtual void apply_dot32(Ctx *c, const float *p, float *q) = 0;
@@ -1839,8 +1915,9 @@ struct Problem {
     virtual void precond32(Ctx *c, const float *r, float *z) = 0;
     // FP64 <-> FP32 vectors of the refinement solver (the FP32 side in the
     // layout of the problem's FP32 multigrid): r = b - A x in FP64 with
-    // apply_blocks() block partials of |r|^2 in c->part; x += e
+    // resid_blocks() block partials of |r|^2 in c->part; x += e
     virtual void resid32(Ctx *c, const double *b, const double *x, float *r) = 0;
+    virtual void to32(Ctx *c, const double *b, float *r) = 0;   // r = b in the FP32 layout
     virtual void add32(Ctx *c, double *x, const float *e) = 0;
 };
 
@@ -2015,20 +2092,28 @@ ebv_status pcg(Ctx *c, Problem &P, const double *b, double *x, int *iters, doubl
 // coefficients, V-cycle) until its residual drops by `inner_drop` (or it
 // stalls), so FP64 arithmetic is spent once per refinement step instead of in
 // every Krylov iteration.  At most 60 corrections.
-ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
+ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res, bool x_zero)
 {
     const int n = P.n();
     const double tol = c->prm.tol;
     const int maxit = c->prm.max_iters;
     const double inner_drop = 1e-4;
     float *r = c->kr32, *z = c->kz32, *p = c->kp32, *q = c->kq32, *e = c->ke32;
+    // x_zero: the first residual is b itself (its norm is |b|^2, reduced below)
+    bool first_is_b = x_zero;
     auto true_residual = [&]() {
+        if (first_is_b) {
+            first_is_b = false;
+            P.to32(c, b, r);
+            return;
+        }
         P.resid32(c, b, x, r);
-        reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_RR);
+        reduce_sum(c, c->part, P.resid_blocks(), c->scal + S_RR);
     };
     EBV_LAUNCH(c, k_solve_begin, dim3(1), dim3(32), 0, c->ctl);
     EBV_LAUNCH(c, k_dot, dim3(vblocks(n)), dim3(256), 0, b, b, n, c->part);
     reduce_sum(c, c->part, vblocks(n), c->scal + S_BB);
+    if (x_zero) reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
     DevLoop outer(c, C_COND_OUT);
     true_residual();
     EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 60, 1, inner_drop, outer.h,
@@ -2090,21 +2175,21 @@ struct CcProblem : Problem {
     {
         EBV_LAUNCH(c, k_add32to64_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, x, e);
     }
+    void to32(Ctx *c, const double *b, float *r) override
+    {
+        EBV_LAUNCH(c, k_to_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, -1, b, r);
+    }
 };
 
 struct NdProblem : Problem {
     NdHier *H;
     int n() const override { return nnode(H->lv[0].g); }
-    int apply_blocks() const override { return nblocks3(ncolgrid(H->lv[0].g)); }
-    int apply_blocks32() const override
-    {
-        return nd_tile_blocks(H->lv[0].g) + (H->lv[0].nirr ? (H->lv[0].nirr + 255) / 256 : 0);
-    }
+    int apply_blocks() const override { return nd_tile_parts(H->lv[0]); }
     void apply_dot(Ctx *c, const double *p, double *q) override
     {
-        // p, alpha, q: 3 words per node
-        EBV_LAUNCH_P(c, "nodal_apply_fp64", 24.0 * n(), k_nd_apply_dot_col<double>, ncolgrid(H->lv[0].g), block3(),
-                     0, ndop<double>(H->lv[0]), p, q, c->part);
+        // p read, q written, act and reg flags: 2.25 words per node
+        nd_tile_pass<double, ND_APPLY>(c, H->lv[0], "nodal_apply_fp64", 18.0 * n(), p, q, nullptr, nullptr, 0.0, 0.0,
+                                       c->part);
     }
     void apply_dot32(Ctx *c, const float *p, float *q) override
     {
@@ -2115,19 +2200,25 @@ struct NdProblem : Problem {
     void precond32(Ctx *c, const float *r, float *z) override { nd_vcycle<float>(c, *H, r, z); }
     void resid32(Ctx *c, const double *b, const double *x, float *r) override
     {
-        // x, alpha, b read, r (FP32) written: 3.5 words per node
-        EBV_LAUNCH_P(c, "nodal_resid_fp64", 28.0 * n(), (k_nd_apply_dot_col<double, true>), ncolgrid(H->lv[0].g),
-                     block3(), 0, ndop<double>(H->lv[0]), x, (double *)nullptr, c->part, b, r);
+        // x, b read, r (FP32) written, act and reg flags: 5.25 words per node
+        nd_tile_pass<double, ND_RES32>(c, H->lv[0], "nodal_resid_fp64", 22.0 * n(), x, nullptr, nullptr, b, 0.0,
+                                       0.0, c->part, r);
     }
     void add32(Ctx *c, double *x, const float *e) override
     {
         EBV_LAUNCH(c, k_add32to64, dim3(vblocks(n())), dim3(256), 0, x, e, n());
     }
+    void to32(Ctx *c, const double *b, float *r) override
+    {
+        EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(n())), dim3(256), 0, b, r, n());
+    }
 };
 
-ebv_status solve(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res)
+// x_zero: x holds zeros on entry (lets the refinement solver skip its first
+// operator application)
+ebv_status solve(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res, bool x_zero = false)
 {
-    if (c->prm.precision == EBV_FP32_REFINE) return pcg_refine(c, P, b, x, iters, res);
+    if (c->prm.precision == EBV_FP32_REFINE) return pcg_refine(c, P, b, x, iters, res, x_zero);
     return pcg(c, P, b, x, iters, res);
 }
 
@@ -2138,12 +2229,16 @@ ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
     CcLevel &L0 = H.lv[0];
     cc_make_diag<double>(c, H, 0);
     if (fp32) {
+        // level 0 in FP32: the Krylov operator (the FP64 diagonal rounded),
+        // then the V-cycle's BF16 faces and the diagonal formed from them
         const int n = ncell(L0.g);
         EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, L0.extra_d, L0.extra_f);
         for (int q = 0; q < H.nvar; q++)
-            EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, H.vdiag_d[q][0], H.vdiag_f[q][0]);
+            EBV_LAUNCH(c, k_to_split, dim3(vblocks(n)), dim3(256), 0, L0.g, -1, H.vdiag_d[q][0], H.vdiag_a[q]);
         for (int d = 0; d < 3; d++)
             EBV_LAUNCH(c, k_to_split, dim3(vblocks(nface(L0.g, d))), dim3(256), 0, L0.g, d, L0.bf_d[d], L0.bf_f[d]);
+        cc_faces_bf16(c, L0);
+        cc_make_diag<float>(c, H, 0);
     }
     for (int l = 0; l + 1 < H.L; l++) {
         CcLevel &F = H.lv[l], &Cc = H.lv[l + 1];
@@ -2151,6 +2246,7 @@ ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
         if (fp32) {
             EBV_LAUNCH(c, k_cc_coarsen<float>, gr, block3(), 0, F.g, F.extra_f, F.bf_f[0], F.bf_f[1], F.bf_f[2], F.cov,
                        Cc.g, Cc.cov, Cc.extra_f, Cc.bf_f[0], Cc.bf_f[1], Cc.bf_f[2]);
+            cc_faces_bf16(c, Cc);
             cc_make_diag<float>(c, H, l + 1);
         } else {
             EBV_LAUNCH(c, k_cc_coarsen<double>, gr, block3(), 0, F.g, F.extra_d, F.bf_d[0], F.bf_d[1], F.bf_d[2],
@@ -2162,12 +2258,12 @@ ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
     const size_t msz = (size_t)H.nb * 2 * H.nb;
     for (int q = 0; q < H.nvar; q++) {
         if (fp32) {
-            CcOp<float> A = ccop<float>(H.lv[lb]);
+            VOp<float> A = vop<float>(H.lv[lb]);
             A.diag = H.vdiag_f[q][lb];
             EBV_LAUNCH(c, k_cc_bottom_assemble<float>, dim3((H.nb + 127) / 128), dim3(128), 0, A, H.bmat + q * msz,
                        H.nb);
         } else {
-            CcOp<double> A = ccop<double>(H.lv[lb]);
+            VOp<double> A = vop<double>(H.lv[lb]);
             A.diag = H.vdiag_d[q][lb];
             EBV_LAUNCH(c, k_cc_bottom_assemble<double>, dim3((H.nb + 127) / 128), dim3(128), 0, A, H.bmat + q * msz,
                        H.nb);
@@ -2251,10 +2347,14 @@ ebv_status setup_solvers(Ctx *c)
             for (int q = 0; q < H->nvar; q++) {
                 H->vdiag_d[q][l] = dalloc<double>(nc, e);
                 H->vdiag_f[q][l] = dalloc<float>(nc, e);
+                H->vdinv_f[q][l] = dalloc<float>(nc, e);
+                if (l == 0) H->vdiag_a[q] = dalloc<float>(nc, e);
             }
             for (int d = 0; d < 3; d++) {
                 Lv.bf_d[d] = dalloc<double>(nface(gl[l], d), e);
                 Lv.bf_f[d] = dalloc<float>(nface(gl[l], d), e);
+                // one spare element: the coarse kernel stages BF16 arrays in 4-byte pairs
+                Lv.bf_h[d] = dalloc<__nv_bfloat16>(nface(gl[l], d) + 1, e);
             }
             if (H == &c->mac) Lv.cov = dalloc<uint8_t>(nc, e);
             else Lv.cov = c->mac.lv[l].cov;
@@ -2396,7 +2496,7 @@ ebv_status autotune_shapes_t(Ctx *c)
     };
     for (int l = 0; l < c->mac.L; l++) {
         CcLevel &L = c->mac.lv[l];
-        CcOp<T> A = ccop<T>(L);
+        VOp<T> A = vop<T>(L);
         float best = 1e30f;
         for (int q = 0; q < nc; q++) {
             const dim3 bk = cand[q], gr = gs_grid(L.g, bk);
@@ -2434,7 +2534,7 @@ ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res
     CcProblem P;
     P.H = &c->mac;
     EBV_LAUNCH(c, k_fill, dim3(vblocks(ncell(c->g))), dim3(256), 0, x, ncell(c->g), 0.0);
-    return solve(c, P, b, x, iters, res);
+    return solve(c, P, b, x, iters, res, true);
 }
 
 ebv_status visc_build(Ctx *c, const double *eta)
@@ -2466,7 +2566,7 @@ ebv_status visc_solve_rhs(Ctx *c, int comp, const double *rhs, double *x, int *i
     EBV_LAUNCH(c, k_fill, dim3(vblocks(n)), dim3(256), 0, x, n, 0.0);
     CcProblem P;
     P.H = &c->visc;
-    return solve(c, P, c->rhs_c, x, iters, res);
+    return solve(c, P, c->rhs_c, x, iters, res, true);
 }
 
 ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *res)
