@@ -270,16 +270,21 @@ __device__ inline T gs_cell(const VOp<T> &A, const T *__restrict__ x, const T *_
     return diag > T(0) ? (bc + off) / diag : T(0);
 }
 
-template <class T, bool kCorr = false>
+// kDot (the last pass of a V-cycle on the finest level): also block partials
+// of b.x over both cells of every x-pair -- the updated one and its partner of
+// the other colour, which this pass does not change -- i.e. r.z of the
+// preconditioned CG, without a separate pass over both vectors.
+template <class T, bool kCorr = false, bool kDot = false>
 __global__ void __launch_bounds__(256) k_cc_gs(VOp<T> A, T *__restrict__ x, const T *__restrict__ b,
                                                int color, int zero_start, const T *__restrict__ xc = nullptr,
-                                               GridD gc = GridD())
+                                               GridD gc = GridD(), double *__restrict__ part = nullptr)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int kk = blockIdx.z * blockDim.z + threadIdx.z;
     const GridD &g = A.g;
-    if (2 * t >= g.nx || j >= g.ny) return;
+    const bool act = 2 * t < g.nx && j < g.ny;
+    if (!kDot && !act) return;   // (with kDot every thread reaches the block sum)
     T val[GS_PZ];
     int cc[GS_PZ];
 #pragma unroll
@@ -288,10 +293,11 @@ __global__ void __launch_bounds__(256) k_cc_gs(VOp<T> A, T *__restrict__ x, cons
         const int i = 2 * t + ((j + k + color) & 1);
         cc[h] = -1;
         val[h] = T(0);
-        if (k >= g.nz || i >= g.nx) continue;
+        if (!act || k >= g.nz || i >= g.nx) continue;
         cc[h] = cix<T>(g, i, j, k);
         val[h] = gs_cell<T, kCorr>(A, x, b, i, j, k, zero_start, xc, gc);
     }
+    T dot = T(0);
 #pragma unroll
     for (int h = 0; h < GS_PZ; h++) {
         if (zero_start) {
@@ -300,6 +306,19 @@ __global__ void __launch_bounds__(256) k_cc_gs(VOp<T> A, T *__restrict__ x, cons
             if (k < g.nz && io < g.nx) x[cix<T>(g, io, j, k)] = T(0);
         }
         if (cc[h] >= 0) x[cc[h]] = val[h];
+        if constexpr (kDot) {
+            const int k = GS_PZ * kk + h;
+            const int io = 2 * t + 1 - ((j + k + color) & 1);
+            if (cc[h] >= 0) dot += b[cc[h]] * val[h];
+            if (act && k < g.nz && io < g.nx) {
+                const int co = cix<T>(g, io, j, k);
+                dot += b[co] * x[co];
+            }
+        }
+    }
+    if constexpr (kDot) {
+        const double sdot = block_sum3_t<T>(dot);
+        if (thread_linear() == 0) part[block_linear()] = sdot;
     }
 }
 
@@ -310,10 +329,15 @@ __device__ inline T rr_cell(const VOp<T> &A, const T *__restrict__ x, const T *_
 {
     // child by child with the layout's index functions: with the children's
     // parities known after unrolling these fold to row offsets in few
-    // registers (this kernel is latency-bound: occupancy counts more)
+    // registers (this kernel is latency-bound: occupancy counts more).
+    // Only the 4 red children ((i+j+k) even) are summed: the restriction
+    // follows pre-smoothing whose last pass updated every black cell from its
+    // current neighbours, so a black cell's residual is 0 up to rounding.
     const GridD &g = A.g;
     T s = 0;
+#pragma unroll
     for (int o = 0; o < 8; o++) {
+        if (__popc(o) & 1) continue;   // black child
         const int i = 2 * I + (o & 1), j = 2 * J + ((o >> 1) & 1), k = 2 * K + ((o >> 2) & 1);
         const int c = cix<T>(g, i, j, k);
         const T bxl = T(A.bx[fidxT<T>(g, 0, i, j, k)]), bxh = T(A.bx[fidxT<T>(g, 0, i + 1, j, k)]);
@@ -1465,10 +1489,9 @@ __global__ void k_outer_check(double *scal, int *ctl, double tol, int maxit, int
 // continue while |r|/|b| > tol/2.  Refinement path: continue until the
 // correction's residual is below its target, or it has stalled (three
 // iterations in a row that do not cut |r|^2 by 4: the FP32 round-off floor).
-__global__ void k_inner_check(double *scal, int *ctl, double tol, int maxit, int refine,
-                              cudaGraphConditionalHandle h, int use_h)
+__device__ inline void inner_check(double *scal, int *ctl, double tol, int maxit, int refine,
+                                   cudaGraphConditionalHandle h, int use_h)
 {
-    if (threadIdx.x) return;
     scal[S_RZOLD] = scal[S_RZ];
     ctl[C_IT]++;
     ctl[C_K]++;
@@ -1491,6 +1514,21 @@ __global__ void k_inner_check(double *scal, int *ctl, double tol, int maxit, int
     }
     if (ctl[C_IT] >= maxit) go = 0;
     set_cond(ctl, C_COND_IN, go, h, use_h);
+}
+
+// S_RR = the sum of the update's n block partials, then the same decision
+// (one launch instead of a reduction and a check).
+__global__ void __launch_bounds__(1024) k_reduce_inner_check(const double *part, int n, double *scal, int *ctl,
+                                                             double tol, int maxit, int refine,
+                                                             cudaGraphConditionalHandle h, int use_h)
+{
+    double v = 0.0;
+    for (int s = threadIdx.x; s < n; s += 1024) v += part[s];
+    v = block_sum<1024>(v);
+    if (threadIdx.x == 0) {
+        scal[S_RR] = v;
+        inner_check(scal, ctl, tol, maxit, refine, h, use_h);
+    }
 }
 
 // End of a solve: per-slot statistics, and the step's first failure
@@ -1714,9 +1752,11 @@ inline dim3 ch_grid(const GridD &g, dim3 bk)
     return dim3((g.nx + 1 + bk.x - 1) / bk.x, (g.ny + 1 + bk.y - 1) / bk.y, (g.nz + 1 + bk.z - 1) / bk.z);
 }
 
+// dot_part: the last pass also writes block partials of b.x (k_cc_gs kDot);
+// returns their number (0 without dot_part).
 template <class T>
-void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red_first, bool zero_start,
-                const T *xc = nullptr, const GridD *gc = nullptr)
+int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red_first, bool zero_start,
+               const T *xc = nullptr, const GridD *gc = nullptr, double *dot_part = nullptr)
 {
     (void)t;
     VOp<T> A = vop<T>(L);
@@ -1735,12 +1775,20 @@ void cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool re
                          c0, z, xc, *gc);
         else
             EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, c0, z, nullptr, GridD());
-        EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, 1 - c0, 0, nullptr, GridD());
+        if (s == 1 && dot_part)
+            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false, true>), gr, bk, 0, A, x, b, 1 - c0, 0, nullptr, GridD(),
+                         dot_part);
+        else
+            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, 1 - c0, 0, nullptr, GridD());
     }
+    return dot_part ? (int)(gr.x * gr.y * gr.z) : 0;
 }
 
+// One V-cycle x0 = M b0.  dot_part: the finest level's last pass also
+// writes block partials of b0.x0; returns their number (0 when the whole
+// V-cycle runs in the coarse kernel, or without dot_part).
 template <class T>
-void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
+int cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0, double *dot_part = nullptr)
 {
     const int Lb = H.L - 1;
     // levels l0 .. Lb (each at most kCoarseCells cells) run in one CTA
@@ -1789,8 +1837,11 @@ void cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0)
         T *x = l ? (T *)c->lx[l] : x0;
         const T *b = l ? (const T *)c->lb[l] : b0;
         // prolongation folded into the first colour pass of the post-smoothing
-        cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, false, false, (const T *)c->lx[l + 1], &H.lv[l + 1].g);
+        const int nd = cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, false, false, (const T *)c->lx[l + 1],
+                                     &H.lv[l + 1].g, l == 0 ? dot_part : nullptr);
+        if (l == 0) return nd;
     }
+    return 0;
 }
 
 // Chebyshev coefficients on [lam_max / 8, lam_max] of D^-1 A, degree 3.
@@ -1913,6 +1964,13 @@ struct Problem {
     // z = one V-cycle applied to r, in FP64 or FP32
     virtual void precond(Ctx *c, const double *r, double *z) = 0;
     virtual void precond32(Ctx *c, const float *r, float *z) = 0;
+    // precond32 that may also leave block partials of r.z in c->part:
+    // returns their number, 0 if it did not
+    virtual int precond32_dot(Ctx *c, const float *r, float *z)
+    {
+        precond32(c, r, z);
+        return 0;
+    }
     // FP64 <-> FP32 vectors of the refinement solver (the FP32 side in the
     // layout of the problem's FP32 multigrid): r = b - A x in FP64 with
     // resid_blocks() block partials of |r|^2 in c->part; x += e
@@ -2071,9 +2129,8 @@ ebv_status pcg(Ctx *c, Problem &P, const double *b, double *x, int *iters, doubl
             P.apply_dot(c, p, q);
             reduce_sum(c, c->part, P.apply_blocks(), c->scal + S_PQ);
             EBV_LAUNCH(c, k_cg_update, dim3(vblocks(n)), dim3(256), 0, x, r, p, q, c->scal, n, c->part);
-            reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
-            EBV_LAUNCH(c, k_inner_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 0, inner.h,
-                       inner.use_h);
+            EBV_LAUNCH(c, k_reduce_inner_check, dim3(1), dim3(1024), 0, c->part, vblocks(n), c->scal, c->ctl, tol,
+                       maxit, 0, inner.h, inner.use_h);
         }
         inner_count = inner.body_launches();
         true_residual();
@@ -2123,16 +2180,15 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
         DevLoop inner(c, C_COND_IN);
         EBV_LAUNCH(c, k_set_cond, dim3(1), dim3(32), 0, c->ctl, C_COND_IN, 1, inner.h, inner.use_h);
         while (inner.next()) {
-            P.precond32(c, r, z);
-            EBV_LAUNCH(c, k_dot32, dim3(vblocks(n)), dim3(256), 0, r, z, n, c->part);
-            reduce_sum(c, c->part, vblocks(n), c->scal + S_RZ);
+            const int nd = P.precond32_dot(c, r, z);
+            if (!nd) EBV_LAUNCH(c, k_dot32, dim3(vblocks(n)), dim3(256), 0, r, z, n, c->part);
+            reduce_sum(c, c->part, nd ? nd : vblocks(n), c->scal + S_RZ);
             EBV_LAUNCH(c, k_cg_pupdate32, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, c->ctl);
             P.apply_dot32(c, p, q);
             reduce_sum(c, c->part, P.apply_blocks32(), c->scal + S_PQ);
             EBV_LAUNCH(c, k_cg_update32, dim3(vblocks(n)), dim3(256), 0, e, r, p, q, c->scal, n, c->ctl, c->part);
-            reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
-            EBV_LAUNCH(c, k_inner_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 1, inner.h,
-                       inner.use_h);
+            EBV_LAUNCH(c, k_reduce_inner_check, dim3(1), dim3(1024), 0, c->part, vblocks(n), c->scal, c->ctl, tol,
+                       maxit, 1, inner.h, inner.use_h);
         }
         inner_count = inner.body_launches();
         P.add32(c, x, e);
@@ -2165,6 +2221,7 @@ struct CcProblem : Problem {
     }
     void precond(Ctx *c, const double *r, double *z) override { cc_vcycle<double>(c, *H, r, z); }
     void precond32(Ctx *c, const float *r, float *z) override { cc_vcycle<float>(c, *H, r, z); }
+    int precond32_dot(Ctx *c, const float *r, float *z) override { return cc_vcycle<float>(c, *H, r, z, c->part); }
     void resid32(Ctx *c, const double *b, const double *x, float *r) override
     {
         // x, diagonal, 3 faces, b read, r (FP32) written: 6.5 words per cell
