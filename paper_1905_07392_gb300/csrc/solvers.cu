@@ -629,10 +629,10 @@ __global__ void k_visc_rhs(GridD g, GeomD geo, int comp, const double *__restric
 
 // q = A p (level 0) and block partials of p.q in FP64 (per thread and warp
 // in T, see block_sum3_t).  Each thread handles planes 2kk and 2kk+1 of
-// column (i, j).
-// q = A p with block partials of p.q; with kRes (FP64) instead the
-// residual r = b - A p, stored as an FP32 row-split vector, with block
-// partials of |r|^2 (the refinement solver's true residual in one pass).
+// column (i, j).  With kRes (FP64) instead the residual r = b - A p, stored
+// as an FP32 row-split vector, with block partials of |r|^2 (the refinement
+// solver's true residual in one pass; |r|^2 only decides convergence, so it
+// is summed from the stored FP32 values, per thread and warp in FP32).
 template <class T, bool kRes = false>
 __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__restrict__ p, T *__restrict__ q,
                                                       double *__restrict__ part, const T *__restrict__ b = nullptr,
@@ -642,6 +642,7 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int kk = blockIdx.z * blockDim.z + threadIdx.z;
     T v = 0;
+    float vr = 0.0f;
     if (i < A.g.nx && j < A.g.ny) {
         T y[2], pc[2];
         int cc[2] = {-1, -1};
@@ -659,16 +660,16 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
         for (int h = 0; h < 2; h++)
             if (cc[h] >= 0) {
                 if constexpr (kRes) {
-                    const T rs = b[cc[h]] - y[h];
-                    r32[cix<float>(A.g, i, j, 2 * kk + h)] = (float)rs;
-                    v += rs * rs;
+                    const float r = (float)(b[cc[h]] - y[h]);
+                    r32[cix<float>(A.g, i, j, 2 * kk + h)] = r;
+                    vr += r * r;
                 } else {
                     q[cc[h]] = y[h];
                     v += pc[h] * y[h];
                 }
             }
     }
-    const double vs = block_sum3_t<T>(v);
+    const double vs = kRes ? block_sum3_t<float>(vr) : block_sum3_t<T>(v);
     if (thread_linear() == 0) part[block_linear()] = vs;
 }
 
@@ -894,7 +895,8 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
     T Am = 0, Bm = 0, A0 = 0, B0 = 0, X0 = 0;
     uint8_t on_c = 0, rg_c = 0, on_n = 0, rg_n = 0;
     T b_c = 0, d_c = 0, b_n = 0, d_n = 0;
-    T v = 0;   // ND_APPLY, ND_RES32: this thread's part of x.out, |r|^2
+    T v = 0;          // ND_APPLY: this thread's part of x.out
+    float vr = 0.0f;  // ND_RES32: its part of |r|^2, from the stored FP32 values
     fetch(k0 - 1);
     for (int kk = k0 - 1; kk <= kend; kk++) {
         T(*S)[NT_W] = sx[kk & 1];
@@ -924,9 +926,9 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 if (kMode == ND_RESID) out[n] = T(0);
                 if (kMode == ND_APPLY) { out[n] = X0; v += X0 * X0; }
                 if (kMode == ND_RES32) {
-                    const T rs = b_c - X0;
-                    out32[n] = (float)rs;
-                    v += rs * rs;
+                    const float r = (float)(b_c - X0);
+                    out32[n] = r;
+                    vr += r * r;
                 }
             } else if (rg_c) {
                 const T ax = dreg * X0 - h12 * (T(2) * (B0 + Am + An) + (Bm + Bn));
@@ -938,9 +940,9 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 if (kMode == ND_RESID) out[n] = b_c - ax;
                 if (kMode == ND_APPLY) { out[n] = ax; v += X0 * ax; }
                 if (kMode == ND_RES32) {
-                    const T rs = b_c - ax;
-                    out32[n] = (float)rs;
-                    v += rs * rs;
+                    const float r = (float)(b_c - ax);
+                    out32[n] = r;
+                    vr += r * r;
                 }
             }
         }
@@ -948,7 +950,7 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
         on_c = on_n; rg_c = rg_n; b_c = b_n; d_c = d_n;
     }
     if constexpr (kMode == ND_APPLY || kMode == ND_RES32) {
-        const double vs = block_sum3_t<T>(v);
+        const double vs = kMode == ND_RES32 ? block_sum3_t<float>(vr) : block_sum3_t<T>(v);
         if (thread_linear() == 0) part[block_linear()] = vs;
     }
 }
@@ -978,9 +980,9 @@ __global__ void __launch_bounds__(256) k_nd_irr(NdOp<T> A, const int *__restrict
         if (kMode == ND_RESID) out[n] = b[n] - ax;
         if (kMode == ND_APPLY) { out[n] = ax; v = xin[n] * ax; }
         if (kMode == ND_RES32) {
-            const T rs = b[n] - ax;
-            out32[n] = (float)rs;
-            v = rs * rs;
+            const float r = (float)(b[n] - ax);
+            out32[n] = r;
+            v = T(r) * T(r);
         }
     }
     if constexpr (kMode == ND_APPLY || kMode == ND_RES32) {
