@@ -1778,12 +1778,16 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
         else
             EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, c0, z, nullptr, GridD());
         if (s == 1 && dot_part)
-            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false, true>), gr, bk, 0, A, x, b, 1 - c0, 0, nullptr, GridD(),
-                         dot_part);
+            // fixed block shape: the grouping of its partial sums must not
+            // follow the autotuned shape, or results would depend on timing
+            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false, true>), gs_grid(g, block3()), block3(), 0, A, x, b, 1 - c0,
+                         0, nullptr, GridD(), dot_part);
         else
             EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, 1 - c0, 0, nullptr, GridD());
     }
-    return dot_part ? (int)(gr.x * gr.y * gr.z) : 0;
+    if (!dot_part) return 0;
+    const dim3 gd = gs_grid(g, block3());
+    return (int)(gd.x * gd.y * gd.z);
 }
 
 // One V-cycle x0 = M b0.  dot_part: the finest level's last pass also
@@ -2529,7 +2533,8 @@ ebv_status setup_geometry_solvers(Ctx *c)
 // use, and keeps the fastest; the viscous hierarchy shares the shapes of the
 // projection hierarchy (same level sizes).  The smoothers' results do not
 // depend on the shape: every update of a pass reads only values that the
-// pass does not write.
+// pass does not write (the one pass that also sums r.z keeps the default
+// shape, so its partial sums are grouped the same way).
 template <class T>
 ebv_status autotune_shapes_t(Ctx *c)
 {

@@ -177,12 +177,18 @@ def test_advance_three_steps(E, O, precision):
         assert st["yield_frac"] == pytest.approx(sto["yield_frac"], abs=1e-12)
 
 
-def test_ragged_odd_bottom(E, O):
-    """A box with unequal sides and a bottom level of odd size (24 x 24 x 48 -> 3 x 3 x 6)."""
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("walls", ["slip", "noslip"])
+def test_ragged_odd_bottom(E, O, precision, walls):
+    """A box with unequal sides and a bottom level of odd size (24 x 24 x 48 -> 3 x 3 x 6), in both
+    precisions (the FP32 multigrid's row-split levels of odd width, its BF16 faces, the partial
+    tiles of the nodal plane march) and with slip walls (each velocity component's viscous
+    operator has its own Dirichlet sides) or no-slip walls (all share them)."""
     n = (24, 24, 48)
     h = 1.0 / 24
-    bc = (O.SLIP, O.SLIP, O.SLIP, O.SLIP, O.INFLOW, O.OUTFLOW)
-    s = E.Solver(n, h, bc=bc, tol=1e-13, max_iters=5000, tau0=1.0, m=1e3, bi_cfl=0.3)
+    w = O.SLIP if walls == "slip" else O.NOSLIP
+    bc = (w, w, w, w, O.INFLOW, O.OUTFLOW)
+    s = E.Solver(n, h, bc=bc, tol=1e-13, max_iters=5000, tau0=1.0, m=1e3, bi_cfl=0.3, precision=precision)
     s.build_sphere((0.5, 0.5, 0.9), 0.15)
     g = O.Grid(n=n, h=h, bc=bc)
     geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_SPHERE, p=(0.5, 0.5, 0.9, 0.15)))
