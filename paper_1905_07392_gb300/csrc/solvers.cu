@@ -500,13 +500,6 @@ __global__ void k_to_bf16(const float *__restrict__ a, __nv_bfloat16 *__restrict
         b[s] = __float2bfloat16_rn(a[s]);
 }
 
-// x += e with e an FP32 row-split vector
-__global__ void k_add32to64_split(GridD g, double *__restrict__ x, const float *__restrict__ e)
-{
-    const int n = ncell(g);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-        x[s] += (double)e[cix<float>(g, s % g.nx, (s / g.nx) % g.ny, s / (g.nx * g.ny))];
-}
 
 // Level-0 coefficients of the cell-centred projection: beta = a_f / h^2,
 // 2 a_f / h^2 on outflow faces (phi = 0 there), 0 on other box faces.
@@ -770,6 +763,8 @@ __device__ inline void nd_row(const NdOp<T> &A, int i, int j, int k, const T *__
 }
 
 // One Chebyshev step: r = b - A x_in; d = cd d + cr D^-1 r; x_out = x_in + d.
+// Node by node: the first step from zero on every level, and all steps on the
+// levels without regular-node flags (the others take the plane march).
 template <class T>
 __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict__ xin, T *__restrict__ xout,
                                                  T *__restrict__ dvec, const T *__restrict__ b, T cd, T cr,
@@ -781,17 +776,13 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
     const GridD &g = A.g;
     if (i > g.nx || j > g.ny || k > g.nz) return;
     const int n = nidx(g, i, j, k);
-    // Every load the node can need is issued before any branch on them (one
-    // round trip to memory instead of act -> reg -> stencil -> b, d): the
-    // regular stencil's sums are formed speculatively on interior nodes.
+    // the node's own operands are loaded before any branch on them
     const uint8_t on = A.act[n];
-    const uint8_t rg = (A.reg && !zero_start) ? A.reg[n] : 0;
     const T bn = b[n];
-    T fd = T(0), bd = T(0), xn = T(0), dold = T(0);
+    T xn = T(0), dold = T(0);
     if (!zero_start) {
         xn = xin[n];
         dold = dvec[n];
-        if (A.reg && i > 0 && i < g.nx && j > 0 && j < g.ny && k > 0 && k < g.nz) nd_regular_sums(g, xin, n, fd, bd);
     }
     if (!on) {
         xout[n] = T(0);
@@ -814,13 +805,7 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
         xout[n] = dn;
         return;
     }
-    if (rg) {   // regular nodes are interior: the sums above are theirs
-        const T hh = A.h;
-        diag = hh * T(8.0 / 3.0);
-        ax = diag * xn - hh * T(1.0 / 12.0) * (T(2) * fd + bd);
-    } else {
-        nd_row(A, i, j, k, xin, diag, ax);
-    }
+    nd_row(A, i, j, k, xin, diag, ax);
     T r = bn - ax;
     T dn = (cd != T(0) ? cd * dold : T(0)) + cr * r / diag;
     dvec[n] = dn;
@@ -1612,17 +1597,16 @@ __global__ void __launch_bounds__(256) k_dot32(const float *__restrict__ a, cons
     if (threadIdx.x == 0) part[blockIdx.x] = dv;
 }
 
-// e += a p, r -= a q (e starts from 0 when first), partials of r.r
-__global__ void __launch_bounds__(256) k_cg_update32(float *__restrict__ e, float *__restrict__ r,
-                                                     const float *__restrict__ p, const float *__restrict__ q,
+// r -= a q with a = rz/pq, partials of r.r.  (The solution update e += a p
+// of the same iteration is deferred to the next k_cg_pupdate32, which reads
+// p anyway, and after the last iteration to k_add32to64*.)
+__global__ void __launch_bounds__(256) k_cg_update32(float *__restrict__ r, const float *__restrict__ q,
                                                      const double *__restrict__ scal, int n,
-                                                     const int *__restrict__ ctl, double *__restrict__ part)
+                                                     double *__restrict__ part)
 {
-    const int first = ctl[C_K] == 0;
     const float a = (float)(scal[S_RZ] / scal[S_PQ]);
     float v = 0.0f;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        e[s] = first ? a * p[s] : e[s] + a * p[s];
         float rs = r[s] - a * q[s];
         r[s] = rs;
         v += rs * rs;
@@ -1631,18 +1615,53 @@ __global__ void __launch_bounds__(256) k_cg_update32(float *__restrict__ e, floa
     if (threadIdx.x == 0) part[blockIdx.x] = dv;
 }
 
-__global__ void k_cg_pupdate32(float *__restrict__ p, const float *__restrict__ z, const double *__restrict__ scal,
-                               int n, const int *__restrict__ ctl)
+// Iteration k of the FP32 CG: p = z (k = 0) or z + beta p, beta = rz/rz_old;
+// for k >= 1 first the previous iteration's solution update with the old p,
+// e = a p (k = 1) or e + a p, a = rz_old/pq (that iteration's step).
+__global__ void k_cg_pupdate32(float *__restrict__ p, float *__restrict__ e, const float *__restrict__ z,
+                               const double *__restrict__ scal, int n, const int *__restrict__ ctl)
 {
-    const int first = ctl[C_K] == 0;
-    const float beta = first ? 0.0f : (float)(scal[S_RZ] / scal[S_RZOLD]);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-        p[s] = first ? z[s] : z[s] + beta * p[s];
+    const int k = ctl[C_K];
+    const float beta = k == 0 ? 0.0f : (float)(scal[S_RZ] / scal[S_RZOLD]);
+    const float a = k == 0 ? 0.0f : (float)(scal[S_RZOLD] / scal[S_PQ]);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        if (k == 0) {
+            p[s] = z[s];
+        } else {
+            const float po = p[s];
+            e[s] = k == 1 ? a * po : e[s] + a * po;
+            p[s] = z[s] + beta * po;
+        }
+    }
 }
 
-__global__ void k_add32to64(double *__restrict__ x, const float *__restrict__ e, int n)
+// After the last of the correction solve's k = ctl[C_K] iterations: its
+// deferred solution update (a = rz_old/pq of that iteration) as in
+// k_cg_pupdate32, then the FP64 solution x += e.
+__device__ inline float final_e(const float *__restrict__ e, const float *__restrict__ p, float a, int k, int s)
 {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) x[s] += (double)e[s];
+    return k == 1 ? a * p[s] : e[s] + a * p[s];
+}
+
+__global__ void k_add32to64(double *__restrict__ x, const float *__restrict__ e, const float *__restrict__ p,
+                            const double *__restrict__ scal, const int *__restrict__ ctl, int n)
+{
+    const int k = ctl[C_K];
+    const float a = (float)(scal[S_RZOLD] / scal[S_PQ]);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        x[s] += (double)final_e(e, p, a, k, s);
+}
+
+// k_add32to64 with e and p FP32 row-split vectors
+__global__ void k_add32to64_split(GridD g, double *__restrict__ x, const float *__restrict__ e,
+                                  const float *__restrict__ p, const double *__restrict__ scal,
+                                  const int *__restrict__ ctl)
+{
+    const int n = ncell(g);
+    const int k = ctl[C_K];
+    const float a = (float)(scal[S_RZOLD] / scal[S_PQ]);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        x[s] += (double)final_e(e, p, a, k, cix<float>(g, s % g.nx, (s / g.nx) % g.ny, s / (g.nx * g.ny)));
 }
 
 __global__ void k_fill(double *a, int n, double v)
@@ -1982,7 +2001,8 @@ struct Problem {
     // resid_blocks() block partials of |r|^2 in c->part; x += e
     virtual void resid32(Ctx *c, const double *b, const double *x, float *r) = 0;
     virtual void to32(Ctx *c, const double *b, float *r) = 0;   // r = b in the FP32 layout
-    virtual void add32(Ctx *c, double *x, const float *e) = 0;
+    // x += e + the deferred last step of the correction solve (search direction p)
+    virtual void add32(Ctx *c, double *x, const float *e, const float *p) = 0;
 };
 
 inline int vblocks(int n) { return std::min(kReduceBlocks, (n + 255) / 256); }
@@ -2189,15 +2209,15 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
             const int nd = P.precond32_dot(c, r, z);
             if (!nd) EBV_LAUNCH(c, k_dot32, dim3(vblocks(n)), dim3(256), 0, r, z, n, c->part);
             reduce_sum(c, c->part, nd ? nd : vblocks(n), c->scal + S_RZ);
-            EBV_LAUNCH(c, k_cg_pupdate32, dim3(vblocks(n)), dim3(256), 0, p, z, c->scal, n, c->ctl);
+            EBV_LAUNCH(c, k_cg_pupdate32, dim3(vblocks(n)), dim3(256), 0, p, e, z, c->scal, n, c->ctl);
             P.apply_dot32(c, p, q);
             reduce_sum(c, c->part, P.apply_blocks32(), c->scal + S_PQ);
-            EBV_LAUNCH(c, k_cg_update32, dim3(vblocks(n)), dim3(256), 0, e, r, p, q, c->scal, n, c->ctl, c->part);
+            EBV_LAUNCH(c, k_cg_update32, dim3(vblocks(n)), dim3(256), 0, r, q, c->scal, n, c->part);
             EBV_LAUNCH(c, k_reduce_inner_check, dim3(1), dim3(1024), 0, c->part, vblocks(n), c->scal, c->ctl, tol,
                        maxit, 1, inner.h, inner.use_h);
         }
         inner_count = inner.body_launches();
-        P.add32(c, x, e);
+        P.add32(c, x, e, p);
         true_residual();
         EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 60, 1, inner_drop,
                    outer.h, outer.use_h);
@@ -2234,9 +2254,9 @@ struct CcProblem : Problem {
         EBV_LAUNCH_P(c, "cc_resid_fp64", 52.0 * n(), (k_cc_apply_dot<double, true>), agrid(), block3(), 0,
                      ccop<double>(H->lv[0]), x, (double *)nullptr, c->part, b, r);
     }
-    void add32(Ctx *c, double *x, const float *e) override
+    void add32(Ctx *c, double *x, const float *e, const float *p) override
     {
-        EBV_LAUNCH(c, k_add32to64_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, x, e);
+        EBV_LAUNCH(c, k_add32to64_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, x, e, p, c->scal, c->ctl);
     }
     void to32(Ctx *c, const double *b, float *r) override
     {
@@ -2267,9 +2287,9 @@ struct NdProblem : Problem {
         nd_tile_pass<double, ND_RES32>(c, H->lv[0], "nodal_resid_fp64", 22.0 * n(), x, nullptr, nullptr, b, 0.0,
                                        0.0, c->part, r);
     }
-    void add32(Ctx *c, double *x, const float *e) override
+    void add32(Ctx *c, double *x, const float *e, const float *p) override
     {
-        EBV_LAUNCH(c, k_add32to64, dim3(vblocks(n())), dim3(256), 0, x, e, n());
+        EBV_LAUNCH(c, k_add32to64, dim3(vblocks(n())), dim3(256), 0, x, e, p, c->scal, c->ctl, n());
     }
     void to32(Ctx *c, const double *b, float *r) override
     {
