@@ -55,8 +55,12 @@ enum { EBV_INFLOW = 0, EBV_OUTFLOW = 1, EBV_SLIP = 2, EBV_NOSLIP = 3 };
 /* Rheology (paper Table "Generalised Newtonian fluid models"). */
 enum { EBV_NEWTONIAN = 0, EBV_BINGHAM = 1, EBV_HERSCHEL_BULKLEY = 2, EBV_POWER_LAW = 3,
        EBV_SOUZA_MENDES_DUTRA = 4 };
-/* Precision of the multigrid smoother and transfers; the Krylov vectors,
- * residuals, solution accumulation and geometry are always FP64. */
+/* Precision of the linear solves.  EBV_FP64: conjugate gradients and
+ * multigrid in FP64.  EBV_FP32_REFINE: FP64 iterative refinement (FP64
+ * operator, residual and solution) around corrections solved by FP32
+ * conjugate gradients with an FP32 multigrid preconditioner whose V-cycle
+ * stores its cell-centred face coefficients in BF16; both converge to
+ * ebv_params.tol.  Geometry and every field are FP64 in both. */
 enum { EBV_FP64 = 0, EBV_FP32_REFINE = 1 };
 
 typedef struct {
@@ -83,7 +87,7 @@ typedef struct {
     int precision;    /* EBV_FP64 or EBV_FP32_REFINE */
     int advect;       /* 1: Algorithm 1 as printed; 0: creeping flow, the convective term C = 0
                          (the paper's evaluation runs at Re = 1e-3, Sec. "Cylinder moving through
-                         Bingham fluid"); the adjoint (ebv_adjoint_step) needs 0 */
+                         Bingham fluid"); the adjoint (ebv_adjoint_step) follows either */
 } ebv_params;
 
 typedef struct {
