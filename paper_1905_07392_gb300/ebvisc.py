@@ -349,7 +349,7 @@ class Solver:
                                             C.c_double(dt), C.byref(st)))
         return _stats_dict(st)
 
-    # adjoint (creeping-flow step, fixed dt)
+    # adjoint of the step (the form the solver's `advect` selects), fixed dt
     def adjoint_step(self, u, p, dt, u_bar, p_bar, f=None, f_bar=None):
         """Reverse of one step from (u, p): u_bar, p_bar (adjoints of the
         outputs) become the adjoints of the inputs; f_bar += adjoint of f.
@@ -367,8 +367,9 @@ class Solver:
         return g[0], g[1]
 
     def drag_gradient(self, u0, p0, dt, steps, every=8, f=None, f_grad=True):
-        """Time-averaged drag J over `steps` creeping-flow steps from (u0, p0)
-        and (dJ/dtau0, dJ/dmu, dJ/df or None), checkpointing every `every`."""
+        """Time-averaged drag J over `steps` steps (with or without the
+        convective term, per `advect`) from (u0, p0) and (dJ/dtau0, dJ/dmu,
+        dJ/df or None), checkpointing every `every`."""
         import torch
         n = C.c_longlong(0)
         self._ok(self._lib.ebv_drag_gradient_workspace(self._ctx, steps, every, C.byref(n)))
@@ -496,7 +497,7 @@ def _drag_objective_class():
     import torch
 
     class DragObjective(torch.autograd.Function):
-        """J(tau0, mu, f) = time-averaged drag of `steps` creeping-flow steps;
+        """J(tau0, mu, f) = time-averaged drag of `steps` steps of the solver;
         forward runs ebv_drag_gradient (objective and gradient in one pass),
         backward scales the stored gradient."""
 
