@@ -1905,9 +1905,11 @@ void nd_tile_pass(Ctx *c, const NdLevel &L, const char *name, double nbytes, con
     const NdOp<T> A = ndop<T>(L);
     EBV_LAUNCH_P(c, name, nbytes, (k_nd_tile<T, kMode>), nd_tile_grid(L.g), dim3(NT_X, NT_Y), 0, A, xin, out, d, b,
                  cd, cr, part, out32);
+    static const char *const kIrrName[4] = {"nodal_listed_nodes chebyshev", "nodal_listed_nodes residual",
+                                            "nodal_listed_nodes apply", "nodal_listed_nodes refinement residual"};
     if (L.nirr)
-        EBV_LAUNCH(c, (k_nd_irr<T, kMode>), dim3((L.nirr + 255) / 256), dim3(256), 0, A, L.irr, L.nirr, xin, out, d,
-                   b, cd, cr, part ? part + nd_tile_blocks(L.g) : nullptr, out32);
+        EBV_LAUNCH_P(c, kIrrName[kMode], 0.0, (k_nd_irr<T, kMode>), dim3((L.nirr + 255) / 256), dim3(256), 0, A, L.irr,
+                     L.nirr, xin, out, d, b, cd, cr, part ? part + nd_tile_blocks(L.g) : nullptr, out32);
 }
 // partial sums written by nd_tile_pass on level L
 inline int nd_tile_parts(const NdLevel &L) { return nd_tile_blocks(L.g) + (L.nirr ? (L.nirr + 255) / 256 : 0); }
