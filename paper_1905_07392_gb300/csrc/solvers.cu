@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(256) k_nd_cheb(NdOp<T> A, const T *__restrict_
     xout[n] = xn + dn;
 }
 
-// ---- level-0 nodal passes in plane-sum form -----------------------------------
+// ---- nodal passes in plane-sum form (levels with regular-node flags) ------------
 // With E_x, E_y, E_z the sums of the two neighbours along one axis, the
 // regular stencil's face-diagonal sum is (E_x E_y + E_x E_z + E_y E_z) x and
 // its body-diagonal sum E_x E_y E_z x.  Per plane k let A_k = the four axis
@@ -2307,8 +2307,10 @@ ebv_status solve(Ctx *c, Problem &P, const double *b, double *x, int *iters, dou
     return pcg(c, P, b, x, iters, res);
 }
 
-// Coarse levels and FP32 shadows of a cell-centred hierarchy whose level-0
-// FP64 coefficients are set; then the bottom inverse.
+// Coarse levels of a cell-centred hierarchy whose level-0 FP64 coefficients
+// are set: the diagonals of every variant, in FP32 also the level-0 Krylov
+// operator and on every level the V-cycle's BF16 faces with the diagonal (and
+// its inverse) formed from them; then the bottom inverses of all variants.
 ebv_status cc_finish_hierarchy(Ctx *c, CcHier &H, bool fp32)
 {
     CcLevel &L0 = H.lv[0];
