@@ -26,9 +26,9 @@
  * (face-centred EB operator, alpha-weighted trilinear nodal operator, MC
  * limiter, upwind rule, wall-distance bound, fallbacks of the wall gradient).
  *
- * parity unpinned: og_drag (only the pressure part is pinned, by the
- * buoyancy identity; the viscous traction is checked against the CUDA path
- * alone).
+ * og_drag is pinned in both parts: the pressure part by the buoyancy
+ * identity, the viscous traction by plane walls in a Newtonian shear or
+ * extension flow, where Eq. dudn is exact.
  */
 #include "ebv_oracle.h"
 

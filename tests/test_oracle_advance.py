@@ -5,6 +5,11 @@
   problem (x -> 1-x, y -> 1-y, x <-> y): catches transposed indices.
 - Drag, pressure part: p = -z with u = 0 gives the buoyancy F_z = |body|
   (Eq. drag-force with the surface normal pointing into the fluid), O(h^2).
+- Drag, viscous part: a plane wall with the Newtonian shear or extension flow
+  u_z = gamma * (distance to the wall) and p = 0 has the traction
+  mu gamma (1 + n_z^2) per unit wall area, which the wall-normal derivative
+  of Eq. dudn reproduces exactly (it is exact on such fields): each term of
+  the traction is checked by one wall orientation.
 - Time step (Eqs. cfl:dt .. cfl:viscous:new): the classical limits.
 """
 import numpy as np
@@ -62,6 +67,28 @@ def test_buoyancy_drag_second_order(O):
         errs.append(abs(fz - 4.0 / 3.0 * np.pi * r ** 3))
         assert yf == 1.0  # a fluid at rest is unyielded everywhere
     assert np.log2(errs[1] / errs[2]) > 1.5, errs
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_viscous_traction_drag_exact(O, axis):
+    n = 16
+    g = O.Grid(n=(n, n, n), h=1.0 / n)
+    x0 = 0.3 + 0.25 * g.h                       # inside a cell layer: one layer of cut cells
+    nv = [0.0, 0.0, 0.0]
+    nv[axis] = 1.0                              # fluid on the side x_axis > x0
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_PLANE, p=tuple(nv) + (x0,)))
+    mu, gamma = 1.3, 0.7
+    xc = (np.arange(n) + 0.5) * g.h
+    coord = [np.broadcast_to(xc[None, None, :], (n, n, n)), np.broadcast_to(xc[None, :, None], (n, n, n)),
+             np.broadcast_to(xc[:, None, None], (n, n, n))][axis].ravel()
+    u = np.zeros((3, g.ncell))
+    u[2] = np.where(geo.alpha > 0, gamma * (coord - x0), 0.0)
+    P = O.Params(model=O.NEWTONIAN, mu=mu)
+    fz, _ = O.drag(g, geo, P, u.ravel(), np.zeros(g.nnode))
+    wall = geo.area.sum() * g.h ** 2
+    assert wall == pytest.approx(1.0, rel=1e-12)  # the plane spans the unit cross-section
+    nz2 = nv[2] ** 2
+    assert fz == pytest.approx(mu * gamma * (1.0 + nz2) * wall, rel=1e-11)
 
 
 def test_timestep_limits(O):
