@@ -12,7 +12,8 @@ measured in the same run.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank advances its own replica (the problem does
-not shard; see the design notes) and rank 0 prints one JSON line.
+not shard: one problem's solves would need a halo exchange per smoother pass
+and an all-reduce per dot product) and rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -62,14 +63,20 @@ def workload(n):
 # distributed plumbing (replicas)
 # ---------------------------------------------------------------------------
 def dist_init(args):
+    """Rank, world size and local rank from the launcher's environment; for
+    world > 1 a process group over NCCL (one GPU per rank), or over gloo on a
+    host without CUDA (the same plumbing, exercised by the CPU tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return rank, world, local
 
 
@@ -80,13 +87,21 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The largest x over all ranks (the timed region's slowest rank)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(cells, steps, world, sec):
+    """Whole-job Mcell-steps/s: every rank advances its own replica of `cells`
+    cells for `steps` steps; sec is the slowest rank's time."""
+    return cells * steps * world / sec / 1e6
 
 
 # ---------------------------------------------------------------------------
@@ -256,7 +271,7 @@ def run_ours(args, rank, world, local):
     sec_e, _, prof = time_steps(s, ue, pe, args.steps, args.warmup, world, profile=True)
     sec_e = max_over_ranks(sec_e, world)
     del ue, pe
-    value = cells * args.steps * world / sec / 1e6
+    value = job_value(cells, args.steps, world, sec)
     roof, kernels = roofline(prof, cells)
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -271,7 +286,7 @@ def run_ours(args, rank, world, local):
            "roofline": roof, "kernels": kernels,
            "step_launch": ("kernel by kernel" if args.eager else
                            "one CUDA graph launch per step (solver loops as conditional nodes)"),
-           "eager": {"value": round(cells * args.steps * world / sec_e / 1e6, 3), "unit": UNIT,
+           "eager": {"value": round(job_value(cells, args.steps, world, sec_e), 3), "unit": UNIT,
                      "ms_per_step": round(1e3 * sec_e / args.steps, 3),
                      "note": "kernel-by-kernel issue with per-launch CUDA events; roofline and "
                              "kernels are measured here"},
@@ -286,7 +301,7 @@ def run_ours(args, rank, world, local):
         sec64, _, _ = time_steps(s64, u64, p64, args.steps, args.warmup, world, graph=True)
         sec64 = max_over_ranks(sec64, world)
         st64 = s64.advance(u64.clone(), p64.clone(), stats=True)
-        out["fp64"] = {"value": round(cells * args.steps * world / sec64 / 1e6, 3), "unit": UNIT,
+        out["fp64"] = {"value": round(job_value(cells, args.steps, world, sec64), 3), "unit": UNIT,
                        "ms_per_step": round(1e3 * sec64 / args.steps, 3),
                        "solve_iters_last_step": st64["iters"]}
         # error of the FP32-smoother path against FP64 after the same steps
@@ -318,7 +333,7 @@ def run_ours(args, rank, world, local):
         barrier(world)
         se = max_over_ranks(t1 - t0, world)
         nb = 8 * (u.numel() + p.numel())
-        out["e2e"] = {"value": round(cells * args.steps * world / se / 1e6, 3), "unit": UNIT,
+        out["e2e"] = {"value": round(job_value(cells, args.steps, world, se), 3), "unit": UNIT,
                       "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
         s.close()
 

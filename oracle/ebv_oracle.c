@@ -22,9 +22,10 @@
  *   - Semi-implicit viscous update: Eq. implicit-viscous.
  *   - Nodal projection: Sec. "Incompressibility constraint".
  *   - Drag: Eq. drag-force; yield criterion ||tau|| <= (1 + delta) tau0.
- * Readings where the paper is silent are the ones listed in the design notes
- * (face-centred EB operator, alpha-weighted trilinear nodal operator, MC
- * limiter, upwind rule, wall-distance bound, fallbacks of the wall gradient).
+ * Where the paper is silent this oracle reads it as: a face-centred EB
+ * operator, an alpha-weighted trilinear nodal operator, the MC limiter, the
+ * upwind rule, a lower bound of the wall distance, and fallbacks of the wall
+ * gradient when its stencil leaves the fluid.
  *
  * og_drag is pinned in both parts: the pressure part by the buoyancy
  * identity, the viscous traction by plane walls in a Newtonian shear or
