@@ -46,6 +46,47 @@ def test_eta_limits(O):
     assert O.eta_of(Ph5, 0.0) == pytest.approx(np.sqrt(1e3), rel=1e-14)  # floor 1/m
 
 
+def test_eta_power_law_closed_values(O):
+    """Power law (Table "Generalised Newtonian fluid models": kappa s^(n-1)),
+    the OG_POWERLAW branch itself: closed values for n = 0.5 and n = 2, the
+    floor s >= 1/m for n < 1, n = 1 is Newtonian, no yield term whatever tau0."""
+    P = O.Params(mu=3.0, tau0=7.0, m=100.0, n_flow=0.5, model=O.POWERLAW)
+    assert O.eta_of(P, 4.0) == pytest.approx(1.5, rel=1e-15)       # 3 / sqrt(4)
+    assert O.eta_of(P, 0.25) == pytest.approx(6.0, rel=1e-15)      # 3 / sqrt(1/4)
+    assert O.eta_of(P, 1e-6) == pytest.approx(30.0, rel=1e-15)     # floored at 1/m = 0.01
+    assert O.eta_of(P, 0.0) == pytest.approx(30.0, rel=1e-15)
+    P2 = O.Params(mu=3.0, tau0=7.0, m=100.0, n_flow=2.0, model=O.POWERLAW)
+    for sr in (0.5, 2.0, 9.0):
+        assert O.eta_of(P2, sr) == pytest.approx(3.0 * sr, rel=1e-15)   # shear thickening
+    P1 = O.Params(mu=3.0, tau0=7.0, m=100.0, n_flow=1.0, model=O.POWERLAW)
+    for sr in (0.0, 0.3, 5.0):
+        assert O.eta_of(P1, sr) == pytest.approx(3.0, rel=1e-15)
+    # log-slope (n - 1) between any two strain rates above the floor
+    for sr in (0.05, 1.0, 40.0):
+        r = np.log(O.eta_of(P, 2.0 * sr) / O.eta_of(P, sr)) / np.log(2.0)
+        assert r == pytest.approx(-0.5, abs=1e-14)
+
+
+def test_eta_souza_mendes_dutra_closed_values(O):
+    """Souza Mendes-Dutra (Table "Generalised Newtonian fluid models":
+    kappa s^(n-1) + tau0 (1 - exp(-eta0 s / tau0)) / s): a closed value at
+    eta0 s / tau0 = 1, the s -> 0 limit kappa (1/m)^(n-1) + eta0, the
+    large-s stress tau0 + kappa s^n, and the identity with the regularised
+    Herschel-Bulkley law when eta0 = tau0 m."""
+    P = O.Params(mu=1.0, tau0=2.0, eta0=4.0, m=1e3, n_flow=1.0, model=O.SMD)
+    assert O.eta_of(P, 0.5) == pytest.approx(1.0 + 4.0 * (1.0 - np.exp(-1.0)), rel=1e-15)
+    assert O.eta_of(P, 0.0) == pytest.approx(1.0 + 4.0, rel=1e-15)
+    Pn = O.Params(mu=0.7, tau0=2.0, eta0=4.0, m=1e3, n_flow=0.5, model=O.SMD)
+    assert O.eta_of(Pn, 0.0) == pytest.approx(0.7 * np.sqrt(1e3) + 4.0, rel=1e-14)
+    sr = 1e4
+    assert O.eta_of(Pn, sr) * sr == pytest.approx(2.0 + 0.7 * sr ** 0.5, rel=1e-15)
+    for n in (0.5, 1.0, 1.6):
+        Ps = O.Params(mu=0.7, tau0=2.0, eta0=2.0 * 250.0, m=250.0, n_flow=n, model=O.SMD)
+        Ph = O.Params(mu=0.7, tau0=2.0, m=250.0, n_flow=n, model=O.HB)
+        for s_ in (0.0, 1e-3, 0.02, 1.0, 30.0):
+            assert O.eta_of(Ps, s_) == pytest.approx(O.eta_of(Ph, s_), rel=1e-14)
+
+
 def test_yield_strain_printed_value(O):
     rows = [l.split() for l in open(os.path.join(GOLDEN, "yield_strain.txt"))
             if l.strip() and not l.startswith("#")]
