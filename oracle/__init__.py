@@ -1,7 +1,7 @@
-"""TEST INFRASTRUCTURE ONLY: ctypes wrapper of the plain FP64 C oracle.
+"""TEST INFRASTRUCTURE ONLY: ctypes wrapper of the plain FP64 C++ oracle.
 
 The oracle restates the embedded-boundary viscoplastic flow step of
-arXiv:1905.07392 on the CPU (see ``ebv_oracle.c`` for the passages each
+arXiv:1905.07392 on the CPU (see ``ebv_oracle.cpp`` for the passages each
 function follows).  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import this package.  It shares no code with
 the CUDA library.
@@ -16,8 +16,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "ebv_oracle.c")
+_SRC = os.path.join(_HERE, "ebv_oracle.cpp")
 _HDR = os.path.join(_HERE, "ebv_oracle.h")
+_DUAL = os.path.join(_HERE, "og_dual.h")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 INFLOW, OUTFLOW, SLIP, NOSLIP = 0, 1, 2, 3
@@ -26,14 +27,15 @@ SHAPE_NONE, SHAPE_SPHERE, SHAPE_PLANE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, -O2)."""
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (g++ -O2, OpenMP,
+    no floating-point contraction)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     stale = (not os.path.exists(_LIB)) or any(
-        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR, _DUAL))
     if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -79,6 +81,7 @@ def lib():
         _lib.og_wall_dudn.restype = C.c_double
         _lib.og_ncell.restype = C.c_size_t
         _lib.og_nnode.restype = C.c_size_t
+        _lib.og_drag_tangent.restype = C.c_int
     return _lib
 
 
@@ -391,3 +394,20 @@ def advance(grid, geo, params, u, p, dt=0.0, f=None):
                      C.c_double(dt), _p(f), C.byref(st))
     return u, p, {"dt": st.dt, "drag": st.drag, "yield_frac": st.yield_frac,
                   "iters": list(st.iters), "res": list(st.res)}
+
+
+def drag_tangent(grid, geo, params, u0, p0, dt, steps, f=None, df=None, dtau0=0.0, dmu=0.0):
+    """Time-averaged drag J over `steps` steps at fixed dt and its exact
+    directional derivative along (dtau0, dmu, df), by forward-mode dual
+    numbers through the whole oracle step.  Returns (J, dJ)."""
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    p0 = np.ascontiguousarray(p0, dtype=np.float64)
+    f = None if f is None else np.ascontiguousarray(f, dtype=np.float64)
+    df = None if df is None else np.ascontiguousarray(df, dtype=np.float64)
+    J, dJ = C.c_double(0.0), C.c_double(0.0)
+    rc = lib().og_drag_tangent(C.byref(grid.c()), C.byref(geo.c()), C.byref(params.c()), _p(u0), _p(p0),
+                               _p(f), _p(df), C.c_double(dtau0), C.c_double(dmu), C.c_double(dt),
+                               C.c_int(steps), C.byref(J), C.byref(dJ))
+    if rc != 0:
+        raise ValueError("og_drag_tangent: dt must be > 0 and steps >= 1")
+    return J.value, dJ.value

@@ -1,5 +1,5 @@
 /*
- * ebv_oracle.c -- TEST INFRASTRUCTURE ONLY (see ebv_oracle.h).
+ * ebv_oracle.cpp -- TEST INFRASTRUCTURE ONLY (see ebv_oracle.h).
  *
  * A plain FP64 restatement of the embedded-boundary (EB) viscoplastic flow
  * step of Sverdrup, Almgren & Nikiforakis (arXiv:1905.07392), written for a
@@ -27,9 +27,24 @@
  * upwind rule, a lower bound of the wall distance, and fallbacks of the wall
  * gradient when its stencil leaves the fluid.
  *
+ * Scalar type.  Every function that carries flow quantities (velocity,
+ * pressure, viscosity and the operators built from them) is a template on its
+ * scalar R.  R = double is the oracle; R = Dual (og_dual.h) runs the same
+ * code in forward-mode dual numbers and gives exact directional derivatives
+ * (og_drag_tangent).  The geometry is always double.  A linear solve in dual
+ * numbers solves for the value part and then, with the same operator, for the
+ * derivative part (the derivative of A x = b is A x' = b' - A' x).
+ *
+ * Threads.  Loops over cells, faces and nodes run in OpenMP threads; each
+ * iteration writes only its own entries, so the results do not depend on the
+ * thread count.  Sums (dot products, drag) add fixed chunks in a fixed order,
+ * also independent of the thread count.
+ *
  * og_drag is pinned in both parts: the pressure part by the buoyancy
  * identity, the viscous traction by plane walls in a Newtonian shear or
- * extension flow, where Eq. dudn is exact.
+ * extension flow, where Eq. dudn is exact.  The convective term is pinned by
+ * linear, step and quadratic fields, conservation, and the cut-cell flux of a
+ * uniform state; the rheologies by their closed values.
  */
 #include "ebv_oracle.h"
 
@@ -37,68 +52,110 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
+#include <functional>
+#include <vector>
+
+#include "og_dual.h"
+
 #define NX (g->n[0])
 #define NY (g->n[1])
 #define NZ (g->n[2])
 
-size_t og_ncell(const og_grid *g) { return (size_t)NX * NY * NZ; }
-size_t og_nnode(const og_grid *g) { return (size_t)(NX + 1) * (NY + 1) * (NZ + 1); }
+namespace {
 
-static size_t cidx(const og_grid *g, int i, int j, int k)
+using std::vector;
+
+template <class R>
+struct Par {  // og_params with the differentiable parameters in R
+    R rho, mu, tau0, m, n_flow, eta0;
+    int model;
+    double cfl, bi_cfl, tol;
+    int max_iters;
+    double delta_min;
+    int advect;
+};
+
+template <class R>
+Par<R> par_of(const og_params *p)
 {
-    return ((size_t)k * NY + j) * NX + i;
+    Par<R> q;
+    q.rho = p->rho; q.mu = p->mu; q.tau0 = p->tau0; q.m = p->m; q.n_flow = p->n_flow; q.eta0 = p->eta0;
+    q.model = p->model; q.cfl = p->cfl; q.bi_cfl = p->bi_cfl; q.tol = p->tol;
+    q.max_iters = p->max_iters; q.delta_min = p->delta_min; q.advect = p->advect;
+    return q;
 }
-static size_t nidx(const og_grid *g, int i, int j, int k)
-{
-    return ((size_t)k * (NY + 1) + j) * (NX + 1) + i;
-}
+
+size_t cidx(const og_grid *g, int i, int j, int k) { return ((size_t)k * NY + j) * NX + i; }
+size_t nidx(const og_grid *g, int i, int j, int k) { return ((size_t)k * (NY + 1) + j) * (NX + 1) + i; }
 /* Face with normal d whose low corner has integer position (i,j,k); along d
  * the index runs 0..n[d]. */
-static size_t fidx(const og_grid *g, int d, int i, int j, int k)
+size_t fidx(const og_grid *g, int d, int i, int j, int k)
 {
     if (d == 0) return ((size_t)k * NY + j) * (NX + 1) + i;
     if (d == 1) return ((size_t)k * (NY + 1) + j) * NX + i;
     return ((size_t)k * NY + j) * NX + i;
 }
-static size_t nface(const og_grid *g, int d)
+size_t nface(const og_grid *g, int d)
 {
     size_t m = 1;
     for (int e = 0; e < 3; e++) m *= (size_t)(g->n[e] + (e == d));
     return m;
 }
-static const double *farr(const og_geom *geo, int d)
-{
-    return d == 0 ? geo->ax : (d == 1 ? geo->ay : geo->az);
-}
-static int inside(const og_grid *g, int i, int j, int k)
+const double *farr(const og_geom *geo, int d) { return d == 0 ? geo->ax : (d == 1 ? geo->ay : geo->az); }
+int inside(const og_grid *g, int i, int j, int k)
 {
     return i >= 0 && j >= 0 && k >= 0 && i < NX && j < NY && k < NZ;
 }
 /* A cell whose value may enter a stencil: inside the box and not covered. */
-static int avail(const og_grid *g, const og_geom *geo, int i, int j, int k)
+int avail(const og_grid *g, const og_geom *geo, int i, int j, int k)
 {
     return inside(g, i, j, k) && geo->alpha[cidx(g, i, j, k)] > 0.0;
 }
 
+/* Sum of a[q] b[q] over q < n in 256 fixed chunks, added in chunk order. */
+template <class R>
+R dot(const R *a, const R *b, size_t n)
+{
+    const long nch = 256;
+    vector<R> part(nch);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < nch; c++) {
+        size_t lo = n * (size_t)c / nch, hi = n * (size_t)(c + 1) / nch;
+        R s = 0.0;
+        for (size_t q = lo; q < hi; q++) s += a[q] * b[q];
+        part[c] = s;
+    }
+    R s = 0.0;
+    for (long c = 0; c < nch; c++) s += part[c];
+    return s;
+}
+
+}  // namespace
+
+extern "C" size_t og_ncell(const og_grid *g) { return (size_t)NX * NY * NZ; }
+extern "C" size_t og_nnode(const og_grid *g) { return (size_t)(NX + 1) * (NY + 1) * (NZ + 1); }
+
 /* ------------------------------------------------------------------------ */
-/* Geometry                                                                  */
+/* Geometry (double only)                                                    */
 /* ------------------------------------------------------------------------ */
 
-double og_phi(const og_shape *s, const double x[3])
+extern "C" double og_phi(const og_shape *s, const double x[3])
 {
     if (s->kind == OG_SHAPE_SPHERE) {
         double dx = x[0] - s->p[0], dy = x[1] - s->p[1], dz = x[2] - s->p[2];
         return sqrt(dx * dx + dy * dy + dz * dz) - s->p[3];
     }
-    if (s->kind == OG_SHAPE_PLANE)
-        return s->p[0] * x[0] + s->p[1] * x[1] + s->p[2] * x[2] - s->p[3];
+    if (s->kind == OG_SHAPE_PLANE) return s->p[0] * x[0] + s->p[1] * x[1] + s->p[2] * x[2] - s->p[3];
     return 1.0;
 }
 
-static int is_fluid(double phi) { return phi > 0.0; }
+namespace {
+
+int is_fluid(double phi) { return phi > 0.0; }
 
 /* Point on the segment P->Q where phi changes sign, by bisection. */
-static void edge_root(const og_shape *s, const double P[3], const double Q[3], double out[3])
+void edge_root(const og_shape *s, const double P[3], const double Q[3], double out[3])
 {
     double x[3], a = 0.0, b = 1.0;
     int fa = is_fluid(og_phi(s, P));
@@ -111,7 +168,7 @@ static void edge_root(const og_shape *s, const double P[3], const double Q[3], d
     for (int d = 0; d < 3; d++) out[d] = P[d] + t * (Q[d] - P[d]);
 }
 
-static void node_pos(const og_grid *g, int i, int j, int k, double x[3])
+void node_pos(const og_grid *g, int i, int j, int k, double x[3])
 {
     x[0] = g->lo[0] + i * g->h;
     x[1] = g->lo[1] + j * g->h;
@@ -120,7 +177,7 @@ static void node_pos(const og_grid *g, int i, int j, int k, double x[3])
 
 /* Fluid aperture of one face: the polygon made of the fluid corners and the
  * edge crossings, walked around the square; area by the shoelace formula. */
-static double face_fraction(const og_grid *g, const og_shape *s, int d, int i, int j, int k)
+double face_fraction(const og_grid *g, const og_shape *s, int d, int i, int j, int k)
 {
     int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     static const int cu[4] = {0, 1, 1, 0}, cv[4] = {0, 0, 1, 1};
@@ -162,26 +219,32 @@ static double face_fraction(const og_grid *g, const og_shape *s, int d, int i, i
     return a;
 }
 
-typedef struct { double ang; double p[3]; } og_pt;
-static int cmp_pt(const void *a, const void *b)
+struct og_pt {
+    double ang;
+    double p[3];
+};
+int cmp_pt(const void *a, const void *b)
 {
     double x = ((const og_pt *)a)->ang, y = ((const og_pt *)b)->ang;
     return (x > y) - (x < y);
 }
 
-void og_build_geometry(const og_grid *g, const og_shape *s, og_geom *geo)
+}  // namespace
+
+extern "C" void og_build_geometry(const og_grid *g, const og_shape *s, og_geom *geo)
 {
     const double h = g->h;
     for (int d = 0; d < 3; d++) {
         double *a = (double *)farr(geo, d);
         int m[3] = {NX, NY, NZ};
         m[d] += 1;
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < m[2]; k++)
             for (int j = 0; j < m[1]; j++)
-                for (int i = 0; i < m[0]; i++)
-                    a[fidx(g, d, i, j, k)] = face_fraction(g, s, d, i, j, k);
+                for (int i = 0; i < m[0]; i++) a[fidx(g, d, i, j, k)] = face_fraction(g, s, d, i, j, k);
     }
     size_t N3 = og_ncell(g);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
@@ -223,8 +286,7 @@ void og_build_geometry(const og_grid *g, const og_shape *s, og_geom *geo)
                 /* Crossings on the 12 edges, relative to the cell centre, in h. */
                 og_pt P[12];
                 int np = 0;
-                double cc[3] = {g->lo[0] + (i + 0.5) * h, g->lo[1] + (j + 0.5) * h,
-                                g->lo[2] + (k + 0.5) * h};
+                double cc[3] = {g->lo[0] + (i + 0.5) * h, g->lo[1] + (j + 0.5) * h, g->lo[2] + (k + 0.5) * h};
                 for (int d = 0; d < 3; d++) {
                     int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
                     for (int q1 = 0; q1 < 2; q1++)
@@ -283,8 +345,7 @@ void og_build_geometry(const og_grid *g, const og_shape *s, og_geom *geo)
                     cr[1] = u1[2] * u2[0] - u1[0] * u2[2];
                     cr[2] = u1[0] * u2[1] - u1[1] * u2[0];
                     double w = 0.5 * (cr[0] * n[0] + cr[1] * n[1] + cr[2] * n[2]);
-                    for (int e = 0; e < 3; e++)
-                        bsum[e] += w * (M[e] + P[q].p[e] + P[q2].p[e]) / 3.0;
+                    for (int e = 0; e < 3; e++) bsum[e] += w * (M[e] + P[q].p[e] + P[q2].p[e]) / 3.0;
                     bw += w;
                 }
                 double b[3];
@@ -310,51 +371,54 @@ void og_build_geometry(const og_grid *g, const og_shape *s, og_geom *geo)
 /* Strain rate and apparent viscosity                                        */
 /* ------------------------------------------------------------------------ */
 
-double og_eta_of(const og_params *p, double sr)
+namespace {
+
+template <class R>
+R eta_of(const Par<R> &p, const R &sr)
 {
     /* (1 - exp(-sr*m)) / sr, with its limit m at sr = 0. */
-    double yield = (sr > 0.0) ? -expm1(-p->m * sr) / sr : p->m;
-    double srf = sr > 1.0 / p->m ? sr : 1.0 / p->m;
-    switch (p->model) {
-    case OG_NEWTONIAN: return p->mu;
-    case OG_BINGHAM: return p->mu + p->tau0 * yield;
-    case OG_HB: return p->mu * pow(srf, p->n_flow - 1.0) + p->tau0 * yield;
-    case OG_POWERLAW: return p->mu * pow(srf, p->n_flow - 1.0);
+    R yield = (sr > 0.0) ? -expm1(-p.m * sr) / sr : p.m;
+    R floor_ = 1.0 / p.m;
+    R srf = sr > floor_ ? sr : floor_;
+    switch (p.model) {
+    case OG_NEWTONIAN: return p.mu;
+    case OG_BINGHAM: return p.mu + p.tau0 * yield;
+    case OG_HB: return p.mu * pow(srf, p.n_flow - 1.0) + p.tau0 * yield;
+    case OG_POWERLAW: return p.mu * pow(srf, p.n_flow - 1.0);
     case OG_SMD: {
-        double y2 = (sr > 0.0) ? -expm1(-p->eta0 * sr / p->tau0) / sr : p->eta0 / p->tau0;
-        return p->mu * pow(srf, p->n_flow - 1.0) + p->tau0 * y2;
+        R y2 = (sr > 0.0) ? -expm1(-p.eta0 * sr / p.tau0) / sr : p.eta0 / p.tau0;
+        return p.mu * pow(srf, p.n_flow - 1.0) + p.tau0 * y2;
     }
     }
-    return p->mu;
+    return p.mu;
 }
 
 /* du/dx_d at a cell from cell values, following the robust stencils:
  * central when both neighbours exist, the one-sided quadratic when one side
  * is missing, first order if only one neighbour exists, zero otherwise. */
-static double d_cell(const og_grid *g, const og_geom *geo, const double *f, int i, int j, int k,
-                     int d)
+template <class R>
+R d_cell(const og_grid *g, const og_geom *geo, const R *f, int i, int j, int k, int d)
 {
     int e[3] = {0, 0, 0};
     e[d] = 1;
     double h = g->h;
     int ip = avail(g, geo, i + e[0], j + e[1], k + e[2]);
     int im = avail(g, geo, i - e[0], j - e[1], k - e[2]);
-    double f0 = f[cidx(g, i, j, k)];
+    R f0 = f[cidx(g, i, j, k)];
     if (ip && im)
-        return (f[cidx(g, i + e[0], j + e[1], k + e[2])] - f[cidx(g, i - e[0], j - e[1], k - e[2])]) /
-               (2.0 * h);
+        return (f[cidx(g, i + e[0], j + e[1], k + e[2])] - f[cidx(g, i - e[0], j - e[1], k - e[2])]) / (2.0 * h);
     if (im) {
-        double f1 = f[cidx(g, i - e[0], j - e[1], k - e[2])];
+        R f1 = f[cidx(g, i - e[0], j - e[1], k - e[2])];
         if (avail(g, geo, i - 2 * e[0], j - 2 * e[1], k - 2 * e[2])) {
-            double f2 = f[cidx(g, i - 2 * e[0], j - 2 * e[1], k - 2 * e[2])];
+            R f2 = f[cidx(g, i - 2 * e[0], j - 2 * e[1], k - 2 * e[2])];
             return (0.5 * f2 - 2.0 * f1 + 1.5 * f0) / h;
         }
         return (f0 - f1) / h;
     }
     if (ip) {
-        double f1 = f[cidx(g, i + e[0], j + e[1], k + e[2])];
+        R f1 = f[cidx(g, i + e[0], j + e[1], k + e[2])];
         if (avail(g, geo, i + 2 * e[0], j + 2 * e[1], k + 2 * e[2])) {
-            double f2 = f[cidx(g, i + 2 * e[0], j + 2 * e[1], k + 2 * e[2])];
+            R f2 = f[cidx(g, i + 2 * e[0], j + 2 * e[1], k + 2 * e[2])];
             return (-1.5 * f0 + 2.0 * f1 - 0.5 * f2) / h;
         }
         return (f1 - f0) / h;
@@ -362,9 +426,11 @@ static double d_cell(const og_grid *g, const og_geom *geo, const double *f, int 
     return 0.0;
 }
 
-void og_cell_gradient(const og_grid *g, const og_geom *geo, const double *u, double *grad)
+template <class R>
+void cell_gradient(const og_grid *g, const og_geom *geo, const R *u, R *grad)
 {
     size_t N3 = og_ncell(g);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
@@ -372,155 +438,183 @@ void og_cell_gradient(const og_grid *g, const og_geom *geo, const double *u, dou
                 for (int d = 0; d < 3; d++)
                     for (int q = 0; q < 3; q++)
                         grad[(3 * d + q) * N3 + c] =
-                            geo->alpha[c] > 0.0 ? d_cell(g, geo, u + q * N3, i, j, k, d) : 0.0;
+                            geo->alpha[c] > 0.0 ? d_cell(g, geo, u + q * N3, i, j, k, d) : R(0.0);
             }
 }
 
-void og_strain_eta(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
-                   double *eta, double *srate)
+template <class R>
+void strain_eta(const og_grid *g, const og_geom *geo, const Par<R> &p, const R *u, R *eta, R *srate)
 {
     size_t N3 = og_ncell(g);
-    double *G = malloc(9 * N3 * sizeof(double));
-    og_cell_gradient(g, geo, u, G);
-    for (size_t c = 0; c < N3; c++) {
+    vector<R> G(9 * N3);
+    cell_gradient(g, geo, u, G.data());
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < (long)N3; c++) {
         if (geo->alpha[c] <= 0.0) {
             eta[c] = 0.0;
             if (srate) srate[c] = 0.0;
             continue;
         }
-        double s2 = 0.0;
+        R s2 = 0.0;
         for (int d = 0; d < 3; d++)
             for (int q = 0; q < 3; q++) {
-                double gam = G[(3 * d + q) * N3 + c] + G[(3 * q + d) * N3 + c];
+                R gam = G[(3 * d + q) * N3 + c] + G[(3 * q + d) * N3 + c];
                 s2 += gam * gam;
             }
-        double sr = sqrt(0.5 * s2);
-        eta[c] = og_eta_of(p, sr);
+        R sr = sqrt(0.5 * s2);
+        eta[c] = eta_of(p, sr);
         if (srate) srate[c] = sr;
     }
-    free(G);
 }
 
 /* ------------------------------------------------------------------------ */
 /* Generic cell-centred operator and its CG solver                           */
 /* ------------------------------------------------------------------------ */
 
-static const double *barr(int d, const double *bx, const double *by, const double *bz)
+template <class R>
+const R *barr(int d, const R *bx, const R *by, const R *bz)
 {
     return d == 0 ? bx : (d == 1 ? by : bz);
 }
 
-void og_cc_apply(const og_grid *g, const double *extra, const double *bx, const double *by,
-                 const double *bz, const double *x, double *y)
+template <class R>
+void cc_apply(const og_grid *g, const R *extra, const R *bx, const R *by, const R *bz, const R *x, R *y)
 {
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
                 size_t c = cidx(g, i, j, k);
-                double v = extra[c] * x[c];
+                R v = extra[c] * x[c];
                 for (int d = 0; d < 3; d++) {
-                    const double *B = barr(d, bx, by, bz);
+                    const R *B = barr(d, bx, by, bz);
                     int id[3] = {i, j, k};
-                    double blo = B[fidx(g, d, id[0], id[1], id[2])];
+                    R blo = B[fidx(g, d, id[0], id[1], id[2])];
                     id[d] += 1;
-                    double bhi = B[fidx(g, d, id[0], id[1], id[2])];
+                    R bhi = B[fidx(g, d, id[0], id[1], id[2])];
                     int lo[3] = {i, j, k}, hi[3] = {i, j, k};
                     lo[d] -= 1;
                     hi[d] += 1;
-                    double xlo = inside(g, lo[0], lo[1], lo[2]) ? x[cidx(g, lo[0], lo[1], lo[2])] : 0.0;
-                    double xhi = inside(g, hi[0], hi[1], hi[2]) ? x[cidx(g, hi[0], hi[1], hi[2])] : 0.0;
+                    R xlo = inside(g, lo[0], lo[1], lo[2]) ? x[cidx(g, lo[0], lo[1], lo[2])] : R(0.0);
+                    R xhi = inside(g, hi[0], hi[1], hi[2]) ? x[cidx(g, hi[0], hi[1], hi[2])] : R(0.0);
                     v += blo * (x[c] - xlo) + bhi * (x[c] - xhi);
                 }
                 y[c] = v;
             }
 }
 
-static double dot(const double *a, const double *b, size_t n)
+/* Jacobi-preconditioned conjugate gradients on an SPD operator; stops at
+ * ||b - A x|| <= tol ||b|| (true residual checked), or at once when a
+ * residual is not finite (the result is then reported as that residual). */
+int pcg_real(const std::function<void(const double *, double *)> &A, const double *diag, const double *b,
+             double *x, size_t n, double tol, int max_iters, double *res_out)
 {
-    double s = 0.0;
-    for (size_t q = 0; q < n; q++) s += a[q] * b[q];
-    return s;
-}
-
-/* Jacobi-preconditioned conjugate gradients on an SPD operator given by a
- * callback; stops at ||b - A x|| <= tol ||b|| (true residual checked). */
-typedef void (*og_apply_fn)(const void *ctx, const double *x, double *y);
-static int pcg(og_apply_fn A, const void *ctx, const double *diag, const double *b, double *x,
-               size_t n, double tol, int max_iters, double *res_out)
-{
-    double *r = malloc(n * sizeof(double)), *z = malloc(n * sizeof(double));
-    double *pp = malloc(n * sizeof(double)), *q = malloc(n * sizeof(double));
+    vector<double> r(n), z(n), pp(n), q(n);
     double bn = sqrt(dot(b, b, n));
     int it = 0;
     double rel = 0.0;
     if (bn == 0.0) {
         memset(x, 0, n * sizeof(double));
-        goto done;
+        if (res_out) *res_out = rel;
+        return it;
     }
     for (int restart = 0; restart < 20; restart++) {
-        A(ctx, x, q);
-        for (size_t s = 0; s < n; s++) r[s] = b[s] - q[s];
-        rel = sqrt(dot(r, r, n)) / bn;
-        if (rel <= tol || it >= max_iters) break;
-        for (size_t s = 0; s < n; s++) { z[s] = r[s] / diag[s]; pp[s] = z[s]; }
-        double rz = dot(r, z, n);
+        A(x, q.data());
+#pragma omp parallel for schedule(static)
+        for (long s = 0; s < (long)n; s++) r[s] = b[s] - q[s];
+        rel = sqrt(dot(r.data(), r.data(), n)) / bn;
+        if (rel <= tol || it >= max_iters || !std::isfinite(rel)) break;
+#pragma omp parallel for schedule(static)
+        for (long s = 0; s < (long)n; s++) { z[s] = r[s] / diag[s]; pp[s] = z[s]; }
+        double rz = dot(r.data(), z.data(), n);
         while (it < max_iters) {
-            A(ctx, pp, q);
-            double a = rz / dot(pp, q, n);
-            for (size_t s = 0; s < n; s++) { x[s] += a * pp[s]; r[s] -= a * q[s]; }
+            A(pp.data(), q.data());
+            double a = rz / dot(pp.data(), q.data(), n);
+#pragma omp parallel for schedule(static)
+            for (long s = 0; s < (long)n; s++) { x[s] += a * pp[s]; r[s] -= a * q[s]; }
             it++;
-            if (sqrt(dot(r, r, n)) <= 0.5 * tol * bn) break;
-            for (size_t s = 0; s < n; s++) z[s] = r[s] / diag[s];
-            double rz2 = dot(r, z, n);
-            for (size_t s = 0; s < n; s++) pp[s] = z[s] + (rz2 / rz) * pp[s];
+            double rn = sqrt(dot(r.data(), r.data(), n));
+            if (rn <= 0.5 * tol * bn || !std::isfinite(rn)) break;
+#pragma omp parallel for schedule(static)
+            for (long s = 0; s < (long)n; s++) z[s] = r[s] / diag[s];
+            double rz2 = dot(r.data(), z.data(), n);
+#pragma omp parallel for schedule(static)
+            for (long s = 0; s < (long)n; s++) pp[s] = z[s] + (rz2 / rz) * pp[s];
             rz = rz2;
         }
     }
-done:
     if (res_out) *res_out = rel;
-    free(r); free(z); free(pp); free(q);
     return it;
 }
 
-typedef struct {
-    const og_grid *g;
-    const double *extra, *bx, *by, *bz;
-} cc_ctx;
-static void cc_cb(const void *ctx, const double *x, double *y)
+/* The solve in the scalar type R.  For double it is pcg_real.  For Dual
+ * the value part x solves A x = b, then the derivative part x' solves
+ * A x' = b' - A' x with the same (value) operator, each to tol. */
+template <class R>
+int pcg(const std::function<void(const R *, R *)> &A, const R *diag, const R *b, R *x, size_t n, double tol,
+        int max_iters, double *res_out);
+
+template <>
+int pcg<double>(const std::function<void(const double *, double *)> &A, const double *diag, const double *b,
+                double *x, size_t n, double tol, int max_iters, double *res_out)
 {
-    const cc_ctx *c = ctx;
-    og_cc_apply(c->g, c->extra, c->bx, c->by, c->bz, x, y);
+    return pcg_real(A, diag, b, x, n, tol, max_iters, res_out);
 }
 
-int og_cc_solve(const og_grid *g, const double *extra, const double *bx, const double *by,
-                const double *bz, const double *b, double *x, double tol, int max_iters,
-                double *res_out)
+template <>
+int pcg<Dual>(const std::function<void(const Dual *, Dual *)> &A, const Dual *diag, const Dual *b, Dual *x,
+              size_t n, double tol, int max_iters, double *res_out)
+{
+    vector<Dual> xin(n), yout(n);
+    auto Av = [&](const double *xr, double *yr) {
+        for (size_t s = 0; s < n; s++) xin[s] = Dual(xr[s], 0.0);
+        A(xin.data(), yout.data());
+        for (size_t s = 0; s < n; s++) yr[s] = yout[s].v;
+    };
+    vector<double> dv(n), bv(n), xv(n), rd(n), xd(n);
+    for (size_t s = 0; s < n; s++) {
+        dv[s] = diag[s].v;
+        bv[s] = b[s].v;
+        xv[s] = x[s].v;
+        xd[s] = x[s].d;
+    }
+    int it = pcg_real(Av, dv.data(), bv.data(), xv.data(), n, tol, max_iters, res_out);
+    for (size_t s = 0; s < n; s++) xin[s] = Dual(xv[s], 0.0);
+    A(xin.data(), yout.data());
+    for (size_t s = 0; s < n; s++) rd[s] = b[s].d - yout[s].d;
+    pcg_real(Av, dv.data(), rd.data(), xd.data(), n, tol, max_iters, nullptr);
+    for (size_t s = 0; s < n; s++) x[s] = Dual(xv[s], xd[s]);
+    return it;
+}
+
+template <class R>
+int cc_solve(const og_grid *g, const R *extra, const R *bx, const R *by, const R *bz, const R *b, R *x, double tol,
+             int max_iters, double *res_out)
 {
     size_t N3 = og_ncell(g);
-    double *diag = malloc(N3 * sizeof(double));
+    vector<R> diag(N3);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
                 size_t c = cidx(g, i, j, k);
-                double v = extra[c];
+                R v = extra[c];
                 for (int d = 0; d < 3; d++) {
-                    const double *B = barr(d, bx, by, bz);
+                    const R *B = barr(d, bx, by, bz);
                     int id[3] = {i, j, k};
                     v += B[fidx(g, d, id[0], id[1], id[2])];
                     id[d] += 1;
                     v += B[fidx(g, d, id[0], id[1], id[2])];
                 }
-                diag[c] = v > 0.0 ? v : 1.0;
+                diag[c] = v > 0.0 ? v : R(1.0);
             }
-    cc_ctx ctx = {g, extra, bx, by, bz};
-    int it = pcg(cc_cb, &ctx, diag, b, x, N3, tol, max_iters, res_out);
-    free(diag);
-    return it;
+    auto A = [&](const R *xx, R *yy) { cc_apply(g, extra, bx, by, bz, xx, yy); };
+    return pcg<R>(A, diag.data(), b, x, N3, tol, max_iters, res_out);
 }
 
 /* Boundary condition of velocity component `comp` on box side `side`:
  * returns 1 and the value for Dirichlet, 0 for Neumann. */
-static int side_dirichlet(const og_grid *g, int side, int comp, double *val)
+int side_dirichlet(const og_grid *g, int side, int comp, double *val)
 {
     int d = side / 2;
     switch (g->bc[side]) {
@@ -534,13 +628,13 @@ static int side_dirichlet(const og_grid *g, int side, int comp, double *val)
 /* Cell-centred projection operator: alpha-weighted EB Poisson (face-centred
  * fluxes weighted by the apertures), Dirichlet phi = 0 at outflow sides,
  * Neumann elsewhere and on the EB. */
-void og_mac_coeffs(const og_grid *g, const og_geom *geo, double *extra, double *bx, double *by,
-                   double *bz)
+template <class R>
+void mac_coeffs(const og_grid *g, const og_geom *geo, R *extra, R *bx, R *by, R *bz)
 {
     const double h2 = g->h * g->h;
     for (size_t c = 0; c < og_ncell(g); c++) extra[c] = geo->alpha[c] > 0.0 ? 0.0 : 1.0;
     for (int d = 0; d < 3; d++) {
-        double *B = (double *)barr(d, bx, by, bz);
+        R *B = (R *)barr<R>(d, bx, by, bz);
         const double *a = farr(geo, d);
         int m[3] = {NX, NY, NZ};
         m[d] += 1;
@@ -563,26 +657,26 @@ void og_mac_coeffs(const og_grid *g, const og_geom *geo, double *extra, double *
  * alpha-weighted: rho*alpha*u + dt/h^2 sum a_f eta_f (u_i - u_nb)
  * + dt/h^2 eta_i A_EB / delta_i u_i, with delta_i the distance from the EB
  * centroid plane to the cell centre (cell units, bounded below). */
-void og_visc_coeffs(const og_grid *g, const og_geom *geo, const og_params *p, const double *eta,
-                    double dt, int comp, double *extra, double *bx, double *by, double *bz,
-                    double *rhs_bc)
+template <class R>
+void visc_coeffs(const og_grid *g, const og_geom *geo, const Par<R> &p, const R *eta, double dt, int comp, R *extra,
+                 R *bx, R *by, R *bz, R *rhs_bc)
 {
     const double h2 = g->h * g->h;
     size_t N3 = og_ncell(g);
     for (size_t c = 0; c < N3; c++) {
         if (geo->alpha[c] <= 0.0) { extra[c] = 1.0; if (rhs_bc) rhs_bc[c] = 0.0; continue; }
-        double e = p->rho * geo->alpha[c];
+        R e = p.rho * geo->alpha[c];
         if (geo->flag[c] == 2 && geo->area[c] > 0.0) {
             double nb = 0.0;
             for (int q = 0; q < 3; q++) nb += geo->nrm[q * N3 + c] * geo->bcen[q * N3 + c];
-            double del = -nb > p->delta_min ? -nb : p->delta_min;
+            double del = -nb > p.delta_min ? -nb : p.delta_min;
             e += dt * eta[c] * geo->area[c] / (h2 * del);
         }
         extra[c] = e;
         if (rhs_bc) rhs_bc[c] = 0.0;
     }
     for (int d = 0; d < 3; d++) {
-        double *B = (double *)barr(d, bx, by, bz);
+        R *B = (R *)barr<R>(d, bx, by, bz);
         const double *a = farr(geo, d);
         int m[3] = {NX, NY, NZ};
         m[d] += 1;
@@ -607,8 +701,8 @@ void og_visc_coeffs(const og_grid *g, const og_geom *geo, const og_params *p, co
                     } else {
                         int lo[3] = {i, j, k};
                         lo[d] -= 1;
-                        double ef = 0.5 * (eta[cidx(g, lo[0], lo[1], lo[2])] + eta[cidx(g, i, j, k)]);
-                        B[f] = a[f] > 0.0 ? dt * a[f] * ef / h2 : 0.0;
+                        R ef = 0.5 * (eta[cidx(g, lo[0], lo[1], lo[2])] + eta[cidx(g, i, j, k)]);
+                        B[f] = a[f] > 0.0 ? dt * a[f] * ef / h2 : R(0.0);
                     }
                 }
     }
@@ -620,7 +714,7 @@ void og_visc_coeffs(const og_grid *g, const og_geom *geo, const og_params *p, co
 
 /* Trilinear (Q1) stiffness on the unit cube, int grad N_a . grad N_b, from the
  * 1-D integrals: int phi_p phi_q = 1/3 or 1/6, int phi_p' phi_q' = +1 or -1. */
-static double q1_stiff(int oa, int ob)
+double q1_stiff(int oa, int ob)
 {
     double v = 0.0;
     for (int d = 0; d < 3; d++) {
@@ -635,7 +729,7 @@ static double q1_stiff(int oa, int ob)
     return v;
 }
 
-static int node_dirichlet(const og_grid *g, int i, int j, int k)
+int node_dirichlet(const og_grid *g, int i, int j, int k)
 {
     int id[3] = {i, j, k};
     for (int d = 0; d < 3; d++) {
@@ -645,7 +739,7 @@ static int node_dirichlet(const og_grid *g, int i, int j, int k)
     return 0;
 }
 /* A node is active when it is not a Dirichlet node and touches fluid. */
-static int node_active(const og_grid *g, const og_geom *geo, int i, int j, int k)
+int node_active(const og_grid *g, const og_geom *geo, int i, int j, int k)
 {
     if (node_dirichlet(g, i, j, k)) return 0;
     for (int o = 0; o < 8; o++) {
@@ -654,18 +748,32 @@ static int node_active(const og_grid *g, const og_geom *geo, int i, int j, int k
     }
     return 0;
 }
+/* node_active of every node, evaluated once per call (a table, not a change
+ * of the arithmetic). */
+vector<unsigned char> active_nodes(const og_grid *g, const og_geom *geo)
+{
+    vector<unsigned char> act(og_nnode(g));
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k <= NZ; k++)
+        for (int j = 0; j <= NY; j++)
+            for (int i = 0; i <= NX; i++) act[nidx(g, i, j, k)] = (unsigned char)node_active(g, geo, i, j, k);
+    return act;
+}
 
-void og_nodal_apply(const og_grid *g, const og_geom *geo, double coef, const double *p, double *y)
+template <class R>
+void nodal_apply(const og_grid *g, const og_geom *geo, double coef, const R *p, R *y)
 {
     double K[8][8];
     for (int a = 0; a < 8; a++)
         for (int b = 0; b < 8; b++) K[a][b] = q1_stiff(a, b);
+    vector<unsigned char> act = active_nodes(g, geo);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k <= NZ; k++)
         for (int j = 0; j <= NY; j++)
             for (int i = 0; i <= NX; i++) {
                 size_t n = nidx(g, i, j, k);
-                if (!node_active(g, geo, i, j, k)) { y[n] = p[n]; continue; }
-                double v = 0.0;
+                if (!act[n]) { y[n] = p[n]; continue; }
+                R v = 0.0;
                 for (int oc = 0; oc < 8; oc++) {
                     /* cell with this node at local corner oa */
                     int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
@@ -675,7 +783,7 @@ void og_nodal_apply(const og_grid *g, const og_geom *geo, double coef, const dou
                     int oa = (i - ci) | ((j - cj) << 1) | ((k - ck) << 2);
                     for (int ob = 0; ob < 8; ob++) {
                         int bi = ci + (ob & 1), bj = cj + ((ob >> 1) & 1), bk = ck + ((ob >> 2) & 1);
-                        if (!node_active(g, geo, bi, bj, bk)) continue;
+                        if (!act[nidx(g, bi, bj, bk)]) continue;
                         v += al * K[oa][ob] * p[nidx(g, bi, bj, bk)];
                     }
                 }
@@ -686,16 +794,19 @@ void og_nodal_apply(const og_grid *g, const og_geom *geo, double coef, const dou
 /* Right-hand side of the nodal Poisson equation in weak form:
  * sum over cells of alpha_c h^3 grad N_a(centre) . u_c, minus the boundary
  * integral of N_a u_bc . n on inflow sides (zero on walls). */
-void og_nodal_rhs(const og_grid *g, const og_geom *geo, const double *ut, double *rhs)
+template <class R>
+void nodal_rhs(const og_grid *g, const og_geom *geo, const R *ut, R *rhs)
 {
     size_t N3 = og_ncell(g);
     const double h = g->h;
+    vector<unsigned char> act = active_nodes(g, geo);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k <= NZ; k++)
         for (int j = 0; j <= NY; j++)
             for (int i = 0; i <= NX; i++) {
                 size_t n = nidx(g, i, j, k);
-                if (!node_active(g, geo, i, j, k)) { rhs[n] = 0.0; continue; }
-                double v = 0.0;
+                if (!act[n]) { rhs[n] = 0.0; continue; }
+                R v = 0.0;
                 for (int oc = 0; oc < 8; oc++) {
                     int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
                     if (!avail(g, geo, ci, cj, ck)) continue;
@@ -717,8 +828,7 @@ void og_nodal_rhs(const og_grid *g, const og_geom *geo, const double *ut, double
                                 int fid[3] = {i, j, k};
                                 fid[t1] += q1;
                                 fid[t2] += q2;
-                                if (fid[t1] < 0 || fid[t1] >= g->n[t1] || fid[t2] < 0 ||
-                                    fid[t2] >= g->n[t2])
+                                if (fid[t1] < 0 || fid[t1] >= g->n[t1] || fid[t2] < 0 || fid[t2] >= g->n[t2])
                                     continue;
                                 double af = farr(geo, d)[fidx(g, d, fid[0], fid[1], fid[2])];
                                 v -= sgn * g->u_in[d] * af * h * h * 0.25;
@@ -728,29 +838,21 @@ void og_nodal_rhs(const og_grid *g, const og_geom *geo, const double *ut, double
             }
 }
 
-typedef struct {
-    const og_grid *g;
-    const og_geom *geo;
-    double coef;
-} nd_ctx;
-static void nd_cb(const void *ctx, const double *x, double *y)
-{
-    const nd_ctx *c = ctx;
-    og_nodal_apply(c->g, c->geo, c->coef, x, y);
-}
-
-int og_nodal_solve(const og_grid *g, const og_geom *geo, double coef, const double *b, double *p,
-                   double tol, int max_iters, double *res_out)
+template <class R>
+int nodal_solve(const og_grid *g, const og_geom *geo, double coef, const R *b, R *p, double tol, int max_iters,
+                double *res_out)
 {
     size_t NN = og_nnode(g);
-    double *diag = malloc(NN * sizeof(double));
+    vector<R> diag(NN);
     double K00 = q1_stiff(0, 0);
+    vector<unsigned char> act = active_nodes(g, geo);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k <= NZ; k++)
         for (int j = 0; j <= NY; j++)
             for (int i = 0; i <= NX; i++) {
                 size_t n = nidx(g, i, j, k);
                 double v = 0.0;
-                if (node_active(g, geo, i, j, k)) {
+                if (act[n]) {
                     for (int oc = 0; oc < 8; oc++) {
                         int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
                         if (avail(g, geo, ci, cj, ck)) v += geo->alpha[cidx(g, ci, cj, ck)] * K00;
@@ -761,23 +863,23 @@ int og_nodal_solve(const og_grid *g, const og_geom *geo, double coef, const doub
                 }
                 diag[n] = v > 0.0 ? v : 1.0;
             }
-    nd_ctx ctx = {g, geo, coef};
-    int it = pcg(nd_cb, &ctx, diag, b, p, NN, tol, max_iters, res_out);
-    free(diag);
-    return it;
+    auto A = [&](const R *xx, R *yy) { nodal_apply(g, geo, coef, xx, yy); };
+    return pcg<R>(A, diag.data(), b, p, NN, tol, max_iters, res_out);
 }
 
 /* Gradient of the trilinear interpolant of nodal p at each cell centre. */
-void og_cell_grad_p(const og_grid *g, const double *p, double *gp)
+template <class R>
+void cell_grad_p(const og_grid *g, const R *p, R *gp)
 {
     size_t N3 = og_ncell(g);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
                 size_t c = cidx(g, i, j, k);
                 for (int d = 0; d < 3; d++) {
                     int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-                    double s = 0.0;
+                    R s = 0.0;
                     for (int q1 = 0; q1 < 2; q1++)
                         for (int q2 = 0; q2 < 2; q2++) {
                             int lo[3] = {i, j, k};
@@ -798,47 +900,49 @@ void og_cell_grad_p(const og_grid *g, const double *p, double *gp)
 
 /* Monotonised-central limited slope (difference across one cell); zero when
  * a neighbour in that direction is covered or outside the box. */
-static double slope(const og_grid *g, const og_geom *geo, const double *f, int i, int j, int k,
-                    int d)
+template <class R>
+R slope(const og_grid *g, const og_geom *geo, const R *f, int i, int j, int k, int d)
 {
     int e[3] = {0, 0, 0};
     e[d] = 1;
-    if (!avail(g, geo, i + e[0], j + e[1], k + e[2]) || !avail(g, geo, i - e[0], j - e[1], k - e[2]))
-        return 0.0;
-    double f0 = f[cidx(g, i, j, k)];
-    double fp = f[cidx(g, i + e[0], j + e[1], k + e[2])];
-    double fm = f[cidx(g, i - e[0], j - e[1], k - e[2])];
-    double dl = f0 - fm, dr = fp - f0, dc = 0.5 * (fp - fm);
+    if (!avail(g, geo, i + e[0], j + e[1], k + e[2]) || !avail(g, geo, i - e[0], j - e[1], k - e[2])) return 0.0;
+    R f0 = f[cidx(g, i, j, k)];
+    R fp = f[cidx(g, i + e[0], j + e[1], k + e[2])];
+    R fm = f[cidx(g, i - e[0], j - e[1], k - e[2])];
+    R dl = f0 - fm, dr = fp - f0, dc = 0.5 * (fp - fm);
     if (dl * dr <= 0.0) return 0.0;
-    double m = fabs(dc);
+    R m = fabs(dc);
     if (2.0 * fabs(dl) < m) m = 2.0 * fabs(dl);
     if (2.0 * fabs(dr) < m) m = 2.0 * fabs(dr);
     return dc > 0.0 ? m : -m;
 }
 
 /* Upwinding of the face-normal velocity from the two extrapolated states. */
-static double upwind_normal(double uL, double uR)
+template <class R>
+R upwind_normal(const R &uL, const R &uR)
 {
     if (uL > 0.0 && uL + uR > 0.0) return uL;
     if (uR < 0.0 && uL + uR < 0.0) return uR;
     return 0.0;
 }
 
-void og_face_states(const og_grid *g, const og_geom *geo, const double *u, double *uf)
+template <class R>
+void face_states(const og_grid *g, const og_geom *geo, const R *u, R *uf)
 {
     size_t N3 = og_ncell(g);
     size_t off = 0;
     for (int d = 0; d < 3; d++) {
         const double *a = farr(geo, d);
-        const double *ud = u + d * N3;
+        const R *ud = u + d * N3;
         int m[3] = {NX, NY, NZ};
         m[d] += 1;
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < m[2]; k++)
             for (int j = 0; j < m[1]; j++)
                 for (int i = 0; i < m[0]; i++) {
                     int id[3] = {i, j, k};
                     size_t f = fidx(g, d, i, j, k);
-                    double v = 0.0;
+                    R v = 0.0;
                     if (a[f] > 0.0) {
                         int lo[3] = {i, j, k};
                         lo[d] -= 1;
@@ -853,9 +957,8 @@ void og_face_states(const og_grid *g, const og_geom *geo, const double *u, doubl
                             default: v = 0.0;
                             }
                         } else {
-                            double uL = ud[cidx(g, lo[0], lo[1], lo[2])] +
-                                        0.5 * slope(g, geo, ud, lo[0], lo[1], lo[2], d);
-                            double uR = ud[cidx(g, i, j, k)] - 0.5 * slope(g, geo, ud, i, j, k, d);
+                            R uL = ud[cidx(g, lo[0], lo[1], lo[2])] + 0.5 * slope(g, geo, ud, lo[0], lo[1], lo[2], d);
+                            R uR = ud[cidx(g, i, j, k)] - 0.5 * slope(g, geo, ud, i, j, k, d);
                             v = upwind_normal(uL, uR);
                         }
                     }
@@ -865,23 +968,23 @@ void og_face_states(const og_grid *g, const og_geom *geo, const double *u, doubl
     }
 }
 
-int og_mac_project(const og_grid *g, const og_geom *geo, double *uf, double *phi, double tol,
-                   int max_iters, double *res_out)
+template <class R>
+int mac_project(const og_grid *g, const og_geom *geo, R *uf, R *phi, double tol, int max_iters, double *res_out)
 {
     size_t N3 = og_ncell(g);
     size_t nf[3] = {nface(g, 0), nface(g, 1), nface(g, 2)};
-    double *ufd[3] = {uf, uf + nf[0], uf + nf[0] + nf[1]};
-    double *extra = malloc(N3 * sizeof(double)), *b = malloc(N3 * sizeof(double));
-    double *B[3];
-    for (int d = 0; d < 3; d++) B[d] = malloc(nf[d] * sizeof(double));
-    og_mac_coeffs(g, geo, extra, B[0], B[1], B[2]);
+    R *ufd[3] = {uf, uf + nf[0], uf + nf[0] + nf[1]};
+    vector<R> extra(N3), b(N3), B0(nf[0]), B1(nf[1]), B2(nf[2]);
+    R *B[3] = {B0.data(), B1.data(), B2.data()};
+    mac_coeffs(g, geo, extra.data(), B[0], B[1], B[2]);
     const double h = g->h;
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
                 size_t c = cidx(g, i, j, k);
                 if (geo->alpha[c] <= 0.0) { b[c] = 0.0; continue; }
-                double s = 0.0;
+                R s = 0.0;
                 for (int d = 0; d < 3; d++) {
                     int id[3] = {i, j, k};
                     size_t flo = fidx(g, d, id[0], id[1], id[2]);
@@ -892,11 +995,12 @@ int og_mac_project(const og_grid *g, const og_geom *geo, double *uf, double *phi
                 b[c] = -s / h;
             }
     for (size_t c = 0; c < N3; c++) phi[c] = 0.0;
-    int it = og_cc_solve(g, extra, B[0], B[1], B[2], b, phi, tol, max_iters, res_out);
+    int it = cc_solve(g, extra.data(), B[0], B[1], B[2], b.data(), phi, tol, max_iters, res_out);
     for (int d = 0; d < 3; d++) {
         const double *a = farr(geo, d);
         int m[3] = {NX, NY, NZ};
         m[d] += 1;
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < m[2]; k++)
             for (int j = 0; j < m[1]; j++)
                 for (int i = 0; i < m[0]; i++) {
@@ -908,8 +1012,8 @@ int og_mac_project(const og_grid *g, const og_geom *geo, double *uf, double *phi
                         if (g->bc[2 * d + hs] != OG_OUTFLOW) continue;
                         int cc[3] = {i, j, k};
                         if (hs) cc[d] -= 1;
-                        double pc = phi[cidx(g, cc[0], cc[1], cc[2])];
-                        double grad = hs ? (0.0 - pc) / (0.5 * h) : (pc - 0.0) / (0.5 * h);
+                        R pc = phi[cidx(g, cc[0], cc[1], cc[2])];
+                        R grad = hs ? (0.0 - pc) / (0.5 * h) : (pc - 0.0) / (0.5 * h);
                         ufd[d][f] -= grad;
                     } else {
                         int lo[3] = {i, j, k};
@@ -918,25 +1022,27 @@ int og_mac_project(const og_grid *g, const og_geom *geo, double *uf, double *phi
                     }
                 }
     }
-    free(extra); free(b);
-    for (int d = 0; d < 3; d++) free(B[d]);
     return it;
 }
 
 /* Neighbourhood average, hybridisation and redistribution of the excess
  * (Eqs. divergence_nonconservative .. divergence_final), with the
  * neighbourhood read as the 26 surrounding cells that hold fluid. */
-void og_redistribute(const og_grid *g, const og_geom *geo, const double *DC, double *D)
+template <class R>
+void redistribute(const og_grid *g, const og_geom *geo, const R *DC, R *D)
 {
     size_t N3 = og_ncell(g);
-    double *dD = calloc(N3, sizeof(double)), *w = calloc(N3, sizeof(double));
+    vector<R> dD(N3, R(0.0));
+    vector<double> w(N3, 0.0);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
                 size_t c = cidx(g, i, j, k);
                 double al = geo->alpha[c];
                 if (al <= 0.0) { D[c] = 0.0; continue; }
-                double sa = 0.0, sad = 0.0;
+                double sa = 0.0;
+                R sad = 0.0;
                 for (int dk = -1; dk <= 1; dk++)
                     for (int dj = -1; dj <= 1; dj++)
                         for (int di = -1; di <= 1; di++) {
@@ -946,17 +1052,18 @@ void og_redistribute(const og_grid *g, const og_geom *geo, const double *DC, dou
                             sa += geo->alpha[c2];
                             sad += geo->alpha[c2] * DC[c2];
                         }
-                double dnc = sa > 0.0 ? sad / sa : DC[c];
+                R dnc = sa > 0.0 ? sad / sa : DC[c];
                 D[c] = al * DC[c] + (1.0 - al) * dnc; /* hybrid D^H */
                 dD[c] = al * (1.0 - al) * (DC[c] - dnc);
                 w[c] = sa > 0.0 ? 1.0 / sa : 0.0;
             }
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
                 size_t c = cidx(g, i, j, k);
                 if (geo->alpha[c] <= 0.0) continue;
-                double s = 0.0;
+                R s = 0.0;
                 for (int dk = -1; dk <= 1; dk++)
                     for (int dj = -1; dj <= 1; dj++)
                         for (int di = -1; di <= 1; di++) {
@@ -967,28 +1074,27 @@ void og_redistribute(const og_grid *g, const og_geom *geo, const double *DC, dou
                         }
                 D[c] += s;
             }
-    free(dD);
-    free(w);
 }
 
 /* Convective term C = -div(u (x) u^F) with zero EB flux; advected states are
  * the slope-extrapolated cell values upwinded by the projected face velocity. */
-void og_convective(const og_grid *g, const og_geom *geo, const double *u, const double *uf,
-                   double *C)
+template <class R>
+void convective(const og_grid *g, const og_geom *geo, const R *u, const R *uf, R *C)
 {
     size_t N3 = og_ncell(g);
     size_t nf[3] = {nface(g, 0), nface(g, 1), nface(g, 2)};
-    const double *ufd[3] = {uf, uf + nf[0], uf + nf[0] + nf[1]};
+    const R *ufd[3] = {uf, uf + nf[0], uf + nf[0] + nf[1]};
     const double h = g->h;
-    double *DC = malloc(N3 * sizeof(double)), *D = malloc(N3 * sizeof(double));
+    vector<R> DC(N3), D(N3);
     for (int q = 0; q < 3; q++) {
-        const double *uq = u + q * N3;
+        const R *uq = u + q * N3;
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < NZ; k++)
             for (int j = 0; j < NY; j++)
                 for (int i = 0; i < NX; i++) {
                     size_t c = cidx(g, i, j, k);
                     if (geo->alpha[c] <= 0.0) { DC[c] = 0.0; continue; }
-                    double s = 0.0;
+                    R s = 0.0;
                     for (int d = 0; d < 3; d++)
                         for (int hs = 0; hs < 2; hs++) {
                             int id[3] = {i, j, k};
@@ -996,7 +1102,7 @@ void og_convective(const og_grid *g, const og_geom *geo, const double *u, const 
                             size_t f = fidx(g, d, id[0], id[1], id[2]);
                             double a = farr(geo, d)[f];
                             if (a <= 0.0) continue;
-                            double w = ufd[d][f], state;
+                            R w = ufd[d][f], state;
                             if (id[d] == 0 || id[d] == g->n[d]) {
                                 int side = 2 * d + hs;
                                 if (g->bc[side] == OG_INFLOW) state = g->u_in[q];
@@ -1004,22 +1110,18 @@ void og_convective(const og_grid *g, const og_geom *geo, const double *u, const 
                             } else {
                                 int L[3] = {id[0], id[1], id[2]};
                                 L[d] -= 1;
-                                int R[3] = {id[0], id[1], id[2]};
-                                double sL = uq[cidx(g, L[0], L[1], L[2])] +
-                                            0.5 * slope(g, geo, uq, L[0], L[1], L[2], d);
-                                double sR = uq[cidx(g, R[0], R[1], R[2])] -
-                                            0.5 * slope(g, geo, uq, R[0], R[1], R[2], d);
+                                int Rr[3] = {id[0], id[1], id[2]};
+                                R sL = uq[cidx(g, L[0], L[1], L[2])] + 0.5 * slope(g, geo, uq, L[0], L[1], L[2], d);
+                                R sR = uq[cidx(g, Rr[0], Rr[1], Rr[2])] - 0.5 * slope(g, geo, uq, Rr[0], Rr[1], Rr[2], d);
                                 state = w > 0.0 ? sL : (w < 0.0 ? sR : 0.5 * (sL + sR));
                             }
                             s += (hs ? 1.0 : -1.0) * a * state * w;
                         }
                     DC[c] = s / (geo->alpha[c] * h);
                 }
-        og_redistribute(g, geo, DC, D);
+        redistribute(g, geo, DC.data(), D.data());
         for (size_t c = 0; c < N3; c++) C[q * N3 + c] = -D[c];
     }
-    free(DC);
-    free(D);
 }
 
 /* Normal derivative of velocity component `comp` at the EB centroid of a cut
@@ -1028,10 +1130,11 @@ void og_convective(const og_grid *g, const og_geom *geo, const double *u, const 
  * largest |n_d|; values come from biquadratic Lagrange interpolation on the
  * 3x3 cells nearest to the crossing point.  If a needed cell is covered, the
  * nearest cell of the first plane gives a one-point estimate. */
-double og_wall_dudn(const og_grid *g, const og_geom *geo, const double *u, int cell, int comp)
+template <class R>
+R wall_dudn(const og_grid *g, const og_geom *geo, const R *u, int cell, int comp)
 {
     size_t N3 = og_ncell(g);
-    const double *uq = u + (size_t)comp * N3;
+    const R *uq = u + (size_t)comp * N3;
     double n[3], b[3];
     for (int e = 0; e < 3; e++) {
         n[e] = geo->nrm[e * N3 + cell];
@@ -1047,7 +1150,7 @@ double og_wall_dudn(const og_grid *g, const og_geom *geo, const double *u, int c
     int k1 = (kax == 0) ? 1 : 0, k2 = (kax == 2) ? 1 : 2;
     double s = n[kax] > 0.0 ? 1.0 : -1.0;
     double dist[2] = {(s - b[kax]) / n[kax], (2.0 * s - b[kax]) / n[kax]};
-    double uv[2];
+    R uv[2];
     int ok = 1, near[3] = {0, 0, 0};
     for (int m = 0; m < 2 && ok; m++) {
         double P[3];
@@ -1061,7 +1164,7 @@ double og_wall_dudn(const og_grid *g, const og_geom *geo, const double *u, int c
             near[k1] = ci[k1] + c1;
             near[k2] = ci[k2] + c2;
         }
-        double v = 0.0;
+        R v = 0.0;
         for (int q1 = -1; q1 <= 1 && ok; q1++)
             for (int q2 = -1; q2 <= 1; q2++) {
                 int id[3];
@@ -1078,26 +1181,25 @@ double og_wall_dudn(const og_grid *g, const og_geom *geo, const double *u, int c
         double d1 = dist[0], d2 = dist[1];
         return (d2 * d2 * uv[0] - d1 * d1 * uv[1]) / (d1 * d2 * (d2 - d1)) / h;
     }
-    if (avail(g, geo, near[0], near[1], near[2]))
-        return uq[cidx(g, near[0], near[1], near[2])] / (dist[0] * h);
+    if (avail(g, geo, near[0], near[1], near[2])) return uq[cidx(g, near[0], near[1], near[2])] / (dist[0] * h);
     return 0.0;
 }
 
 /* Explicit viscous term V = (1/rho) div(eta (grad u)^T) (Eq. explicit-viscous)
  * with face fluxes eta_f d u_d / d x_j, the EB wall flux from the wall-normal
  * derivative, and the same hybrid redistribution as the convective term. */
-void og_viscous_explicit(const og_grid *g, const og_geom *geo, const og_params *p,
-                         const double *u, const double *eta, double *V)
+template <class R>
+void viscous_explicit(const og_grid *g, const og_geom *geo, const Par<R> &p, const R *u, const R *eta, R *V)
 {
     size_t N3 = og_ncell(g);
     const double h = g->h;
-    double *G = malloc(9 * N3 * sizeof(double));
-    og_cell_gradient(g, geo, u, G);
-    double *DC = malloc(3 * N3 * sizeof(double)), *D = malloc(N3 * sizeof(double));
-    double *dudn = calloc(3 * N3, sizeof(double));
-    for (size_t c = 0; c < N3; c++)
+    vector<R> G(9 * N3), DC(3 * N3), D(N3), dudn(3 * N3, R(0.0));
+    cell_gradient(g, geo, u, G.data());
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < (long)N3; c++)
         if (geo->flag[c] == 2 && geo->area[c] > 0.0)
-            for (int q = 0; q < 3; q++) dudn[q * N3 + c] = og_wall_dudn(g, geo, u, (int)c, q);
+            for (int q = 0; q < 3; q++) dudn[q * N3 + c] = wall_dudn(g, geo, u, (int)c, q);
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < NZ; k++)
         for (int j = 0; j < NY; j++)
             for (int i = 0; i < NX; i++) {
@@ -1105,7 +1207,7 @@ void og_viscous_explicit(const og_grid *g, const og_geom *geo, const og_params *
                 for (int jj = 0; jj < 3; jj++) DC[jj * N3 + c] = 0.0;
                 if (geo->alpha[c] <= 0.0) continue;
                 for (int jj = 0; jj < 3; jj++) {
-                    double s = 0.0;
+                    R s = 0.0;
                     for (int d = 0; d < 3; d++)
                         for (int hs = 0; hs < 2; hs++) {
                             int id[3] = {i, j, k};
@@ -1113,31 +1215,30 @@ void og_viscous_explicit(const og_grid *g, const og_geom *geo, const og_params *
                             size_t f = fidx(g, d, id[0], id[1], id[2]);
                             double a = farr(geo, d)[f];
                             if (a <= 0.0) continue;
-                            double T;
+                            R T;
                             if (id[d] == 0 || id[d] == g->n[d]) {
                                 int side = 2 * d + hs;
                                 double val;
                                 if (side_dirichlet(g, side, d, &val)) {
-                                    double ud = u[d * N3 + c];
-                                    T = (jj == d) ? eta[c] * (hs ? (val - ud) : (ud - val)) / (0.5 * h) : 0.0;
+                                    R ud = u[d * N3 + c];
+                                    T = (jj == d) ? eta[c] * (hs ? (val - ud) : (ud - val)) / (0.5 * h) : R(0.0);
                                 } else {
-                                    T = (jj == d) ? 0.0 : eta[c] * G[(3 * jj + d) * N3 + c];
+                                    T = (jj == d) ? R(0.0) : eta[c] * G[(3 * jj + d) * N3 + c];
                                 }
                             } else {
                                 int L[3] = {id[0], id[1], id[2]};
                                 L[d] -= 1;
                                 size_t cL = cidx(g, L[0], L[1], L[2]);
                                 size_t cR = cidx(g, id[0], id[1], id[2]);
-                                double ef = 0.5 * (eta[cL] + eta[cR]);
-                                double der = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) / h
-                                                       : 0.5 * (G[(3 * jj + d) * N3 + cL] +
-                                                                G[(3 * jj + d) * N3 + cR]);
+                                R ef = 0.5 * (eta[cL] + eta[cR]);
+                                R der = (jj == d) ? (u[d * N3 + cR] - u[d * N3 + cL]) / h
+                                                  : 0.5 * (G[(3 * jj + d) * N3 + cL] + G[(3 * jj + d) * N3 + cR]);
                                 T = ef * der;
                             }
                             s += (hs ? 1.0 : -1.0) * a * T;
                         }
                     if (geo->flag[c] == 2 && geo->area[c] > 0.0) {
-                        double nd = 0.0;
+                        R nd = 0.0;
                         for (int q = 0; q < 3; q++) nd += geo->nrm[q * N3 + c] * dudn[q * N3 + c];
                         /* outward normal of the fluid region on the EB is -n */
                         s += -eta[c] * geo->nrm[jj * N3 + c] * nd * geo->area[c];
@@ -1146,38 +1247,277 @@ void og_viscous_explicit(const og_grid *g, const og_geom *geo, const og_params *
                 }
             }
     for (int q = 0; q < 3; q++) {
-        og_redistribute(g, geo, DC + q * N3, D);
-        for (size_t c = 0; c < N3; c++) V[q * N3 + c] = D[c] / p->rho;
+        redistribute(g, geo, DC.data() + q * N3, D.data());
+        for (size_t c = 0; c < N3; c++) V[q * N3 + c] = D[c] / p.rho;
     }
-    free(G); free(DC); free(D); free(dudn);
 }
 
-void og_derived(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
-                double *C, double *eta, double *V, double *srate, og_stats *st)
+template <class R>
+void derived(const og_grid *g, const og_geom *geo, const Par<R> &p, const R *u, R *C, R *eta, R *V, R *srate,
+             og_stats *st)
 {
     size_t N3 = og_ncell(g);
     size_t nft = nface(g, 0) + nface(g, 1) + nface(g, 2);
-    double *uf = malloc(nft * sizeof(double)), *phi = malloc(N3 * sizeof(double));
+    vector<R> uf(nft), phi(N3);
     double res = 0.0;
-    if (p->advect) {
-        og_face_states(g, geo, u, uf);
-        int it = og_mac_project(g, geo, uf, phi, p->tol, p->max_iters, &res);
+    if (p.advect) {
+        face_states(g, geo, u, uf.data());
+        int it = mac_project(g, geo, uf.data(), phi.data(), p.tol, p.max_iters, &res);
         if (st) { st->iters[0] = it; st->res[0] = res; }
-        og_convective(g, geo, u, uf, C);
+        convective(g, geo, u, uf.data(), C);
     } else {
         /* creeping flow (the paper's evaluation, Re = 1e-3): no convective term */
         for (size_t s = 0; s < 3 * N3; s++) C[s] = 0.0;
         if (st) { st->iters[0] = 0; st->res[0] = 0.0; }
     }
-    og_strain_eta(g, geo, p, u, eta, srate);
-    og_viscous_explicit(g, geo, p, u, eta, V);
-    free(uf);
-    free(phi);
+    strain_eta(g, geo, p, u, eta, srate);
+    viscous_explicit(g, geo, p, u, eta, V);
+}
+
+template <class R>
+int viscous_solve(const og_grid *g, const og_geom *geo, const Par<R> &p, const R *eta, const R *psi, double dt, R *ut,
+                  og_stats *st, int slot)
+{
+    size_t N3 = og_ncell(g);
+    vector<R> extra(N3), rb(N3), b(N3), B0(nface(g, 0)), B1(nface(g, 1)), B2(nface(g, 2));
+    int tot = 0;
+    for (int q = 0; q < 3; q++) {
+        visc_coeffs(g, geo, p, eta, dt, q, extra.data(), B0.data(), B1.data(), B2.data(), rb.data());
+        for (size_t c = 0; c < N3; c++) {
+            b[c] = geo->alpha[c] > 0.0 ? geo->alpha[c] * psi[q * N3 + c] + rb[c] : R(0.0);
+            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? psi[q * N3 + c] / p.rho : R(0.0);
+        }
+        double res = 0.0;
+        int it = cc_solve(g, extra.data(), B0.data(), B1.data(), B2.data(), b.data(), ut + q * N3, p.tol,
+                          p.max_iters, &res);
+        if (st) { st->iters[slot + q] = it; st->res[slot + q] = res; }
+        tot += it;
+    }
+    return tot;
+}
+
+template <class R>
+int nodal_project(const og_grid *g, const og_geom *geo, const Par<R> &p, double dt, R *ut, R *pres, og_stats *st,
+                  int slot)
+{
+    size_t N3 = og_ncell(g), NN = og_nnode(g);
+    vector<R> gp(3 * N3), rhs(NN);
+    double coef = dt / value_of(p.rho);
+    cell_grad_p(g, pres, gp.data());
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++)
+            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? ut[q * N3 + c] + coef * gp[q * N3 + c] : R(0.0);
+    nodal_rhs(g, geo, ut, rhs.data());
+    double res = 0.0;
+    int it = nodal_solve(g, geo, coef, rhs.data(), pres, p.tol, p.max_iters, &res);
+    if (st) { st->iters[slot] = it; st->res[slot] = res; }
+    cell_grad_p(g, pres, gp.data());
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++)
+            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? ut[q * N3 + c] - coef * gp[q * N3 + c] : R(0.0);
+    return it;
+}
+
+template <class R>
+void drag(const og_grid *g, const og_geom *geo, const Par<R> &p, const R *u, const R *pres, R *fz, double *yield_frac)
+{
+    size_t N3 = og_ncell(g);
+    vector<R> eta(N3), sr(N3);
+    strain_eta(g, geo, p, u, eta.data(), sr.data());
+    const double h = g->h;
+    R F = 0.0;
+    double vy = 0.0, vt = 0.0;
+    for (int k = 0; k < NZ; k++)
+        for (int j = 0; j < NY; j++)
+            for (int i = 0; i < NX; i++) {
+                size_t c = cidx(g, i, j, k);
+                double al = geo->alpha[c];
+                if (al <= 0.0) continue;
+                vt += al;
+                if (eta[c] * sr[c] <= (1.0 + 1e-3) * p.tau0) vy += al;
+                if (geo->flag[c] != 2 || geo->area[c] <= 0.0) continue;
+                double n[3], b[3];
+                R gq[3];
+                for (int e = 0; e < 3; e++) {
+                    n[e] = geo->nrm[e * N3 + c];
+                    b[e] = geo->bcen[e * N3 + c];
+                    gq[e] = wall_dudn(g, geo, u, (int)c, e);
+                }
+                R gn = gq[0] * n[0] + gq[1] * n[1] + gq[2] * n[2];
+                R tz = eta[c] * (n[2] * gn + gq[2]);
+                R pb = 0.0;
+                for (int o = 0; o < 8; o++) {
+                    int oi = o & 1, oj = (o >> 1) & 1, ok = (o >> 2) & 1;
+                    double w = (oi ? b[0] + 0.5 : 0.5 - b[0]) * (oj ? b[1] + 0.5 : 0.5 - b[1]) *
+                               (ok ? b[2] + 0.5 : 0.5 - b[2]);
+                    pb += w * pres[nidx(g, i + oi, j + oj, k + ok)];
+                }
+                F += geo->area[c] * h * h * (tz - pb * n[2]);
+            }
+    *fz = F;
+    *yield_frac = vt > 0.0 ? vy / vt : 0.0;
+}
+
+/* Algorithm 1: predictor and corrector with a semi-implicit viscous update
+ * and a nodal projection each, at the time step dt (> 0). */
+template <class R>
+void advance(const og_grid *g, const og_geom *geo, const Par<R> &p, R *u, R *pres, double dt, const R *f,
+             og_stats *st, R *drag_out)
+{
+    size_t N3 = og_ncell(g), V3 = 3 * N3, NN = og_nnode(g);
+    vector<R> Cm(V3), Vm(V3), Cs(V3), Vs(V3), em(N3), es(N3), psi(V3), ut(V3), gp(V3), ps(NN);
+    og_stats loc;
+    memset(&loc, 0, sizeof loc);
+    og_stats tmp;
+    memset(&tmp, 0, sizeof tmp);
+
+    /* Predictor */
+    derived(g, geo, p, u, Cm.data(), em.data(), Vm.data(), (R *)nullptr, &tmp);
+    loc.iters[0] = tmp.iters[0];
+    loc.res[0] = tmp.res[0];
+    cell_grad_p(g, pres, gp.data());
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++) {
+            size_t s = q * N3 + c;
+            R fq = f ? f[s] : R(0.0);
+            psi[s] = geo->alpha[c] > 0.0 ? p.rho * u[s] + dt * (p.rho * Cm[s] + Vm[s] - gp[s] + fq) : R(0.0);
+        }
+    viscous_solve(g, geo, p, em.data(), psi.data(), dt, ut.data(), &loc, 1);
+    for (size_t s = 0; s < NN; s++) ps[s] = pres[s];
+    nodal_project(g, geo, p, dt, ut.data(), ps.data(), &loc, 4);
+    /* ut now holds u*, ps holds p* */
+
+    /* Corrector */
+    derived(g, geo, p, ut.data(), Cs.data(), es.data(), Vs.data(), (R *)nullptr, &tmp);
+    loc.iters[5] = tmp.iters[0];
+    loc.res[5] = tmp.res[0];
+    for (size_t s = 0; s < V3; s++) {
+        Cm[s] = 0.5 * (Cm[s] + Cs[s]);
+        Vm[s] = 0.5 * (Vm[s] + Vs[s]);
+    }
+    for (size_t c = 0; c < N3; c++) em[c] = 0.5 * (em[c] + es[c]);
+    cell_grad_p(g, ps.data(), gp.data());
+    for (int q = 0; q < 3; q++)
+        for (size_t c = 0; c < N3; c++) {
+            size_t s = q * N3 + c;
+            R fq = f ? f[s] : R(0.0);
+            psi[s] = geo->alpha[c] > 0.0 ? p.rho * u[s] + dt * (p.rho * Cm[s] + Vm[s] - gp[s] + fq) : R(0.0);
+        }
+    viscous_solve(g, geo, p, em.data(), psi.data(), dt, ut.data(), &loc, 6);
+    for (size_t s = 0; s < NN; s++) pres[s] = ps[s];
+    nodal_project(g, geo, p, dt, ut.data(), pres, &loc, 9);
+    for (size_t s = 0; s < V3; s++) u[s] = ut[s];
+
+    loc.dt = dt;
+    R fz;
+    drag(g, geo, p, u, pres, &fz, &loc.yield_frac);
+    loc.drag = value_of(fz);
+    if (drag_out) *drag_out = fz;
+    if (st) *st = loc;
+}
+
+}  // namespace
+
+/* ------------------------------------------------------------------------ */
+/* C entry points (double)                                                   */
+/* ------------------------------------------------------------------------ */
+
+extern "C" double og_eta_of(const og_params *p, double sr) { return eta_of(par_of<double>(p), sr); }
+
+extern "C" void og_strain_eta(const og_grid *g, const og_geom *geo, const og_params *p, const double *u, double *eta,
+                              double *srate)
+{
+    strain_eta(g, geo, par_of<double>(p), u, eta, srate);
+}
+
+extern "C" void og_cell_gradient(const og_grid *g, const og_geom *geo, const double *u, double *grad)
+{
+    cell_gradient(g, geo, u, grad);
+}
+
+extern "C" void og_cc_apply(const og_grid *g, const double *extra, const double *bx, const double *by,
+                            const double *bz, const double *x, double *y)
+{
+    cc_apply(g, extra, bx, by, bz, x, y);
+}
+
+extern "C" int og_cc_solve(const og_grid *g, const double *extra, const double *bx, const double *by,
+                           const double *bz, const double *b, double *x, double tol, int max_iters, double *res_out)
+{
+    return cc_solve(g, extra, bx, by, bz, b, x, tol, max_iters, res_out);
+}
+
+extern "C" void og_mac_coeffs(const og_grid *g, const og_geom *geo, double *extra, double *bx, double *by,
+                              double *bz)
+{
+    mac_coeffs(g, geo, extra, bx, by, bz);
+}
+
+extern "C" void og_visc_coeffs(const og_grid *g, const og_geom *geo, const og_params *p, const double *eta, double dt,
+                               int comp, double *extra, double *bx, double *by, double *bz, double *rhs_bc)
+{
+    visc_coeffs(g, geo, par_of<double>(p), eta, dt, comp, extra, bx, by, bz, rhs_bc);
+}
+
+extern "C" void og_nodal_apply(const og_grid *g, const og_geom *geo, double coef, const double *p, double *y)
+{
+    nodal_apply(g, geo, coef, p, y);
+}
+
+extern "C" void og_nodal_rhs(const og_grid *g, const og_geom *geo, const double *ut, double *rhs)
+{
+    nodal_rhs(g, geo, ut, rhs);
+}
+
+extern "C" int og_nodal_solve(const og_grid *g, const og_geom *geo, double coef, const double *b, double *p,
+                              double tol, int max_iters, double *res_out)
+{
+    return nodal_solve(g, geo, coef, b, p, tol, max_iters, res_out);
+}
+
+extern "C" void og_cell_grad_p(const og_grid *g, const double *p, double *gp) { cell_grad_p(g, p, gp); }
+
+extern "C" void og_face_states(const og_grid *g, const og_geom *geo, const double *u, double *uf)
+{
+    face_states(g, geo, u, uf);
+}
+
+extern "C" int og_mac_project(const og_grid *g, const og_geom *geo, double *uf, double *phi, double tol,
+                              int max_iters, double *res_out)
+{
+    return mac_project(g, geo, uf, phi, tol, max_iters, res_out);
+}
+
+extern "C" void og_convective(const og_grid *g, const og_geom *geo, const double *u, const double *uf, double *C)
+{
+    convective(g, geo, u, uf, C);
+}
+
+extern "C" void og_redistribute(const og_grid *g, const og_geom *geo, const double *DC, double *D)
+{
+    redistribute(g, geo, DC, D);
+}
+
+extern "C" void og_viscous_explicit(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                                    const double *eta, double *V)
+{
+    viscous_explicit(g, geo, par_of<double>(p), u, eta, V);
+}
+
+extern "C" double og_wall_dudn(const og_grid *g, const og_geom *geo, const double *u, int cell, int comp)
+{
+    return wall_dudn(g, geo, u, cell, comp);
+}
+
+extern "C" void og_derived(const og_grid *g, const og_geom *geo, const og_params *p, const double *u, double *C,
+                           double *eta, double *V, double *srate, og_stats *st)
+{
+    derived(g, geo, par_of<double>(p), u, C, eta, V, srate, st);
 }
 
 /* Eqs. cfl:dt, cfl:convective, cfl:forcing, cfl:viscous:new. */
-double og_timestep(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
-                   const double *f)
+extern "C" double og_timestep(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                              const double *f)
 {
     size_t N3 = og_ncell(g);
     const double h = g->h;
@@ -1196,155 +1536,63 @@ double og_timestep(const og_grid *g, const og_geom *geo, const og_params *p, con
     return p->cfl / (0.5 * (ccv + sqrt(ccv * ccv + 4.0 * cf2)));
 }
 
-int og_viscous_solve(const og_grid *g, const og_geom *geo, const og_params *p, const double *eta,
-                     const double *psi, double dt, double *ut, og_stats *st, int slot)
+extern "C" int og_viscous_solve(const og_grid *g, const og_geom *geo, const og_params *p, const double *eta,
+                                const double *psi, double dt, double *ut, og_stats *st, int slot)
 {
-    size_t N3 = og_ncell(g);
-    double *extra = malloc(N3 * sizeof(double)), *rb = malloc(N3 * sizeof(double));
-    double *b = malloc(N3 * sizeof(double));
-    double *B[3];
-    for (int d = 0; d < 3; d++) B[d] = malloc(nface(g, d) * sizeof(double));
-    int tot = 0;
-    for (int q = 0; q < 3; q++) {
-        og_visc_coeffs(g, geo, p, eta, dt, q, extra, B[0], B[1], B[2], rb);
-        for (size_t c = 0; c < N3; c++) {
-            b[c] = geo->alpha[c] > 0.0 ? geo->alpha[c] * psi[q * N3 + c] + rb[c] : 0.0;
-            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? psi[q * N3 + c] / p->rho : 0.0;
-        }
-        double res = 0.0;
-        int it = og_cc_solve(g, extra, B[0], B[1], B[2], b, ut + q * N3, p->tol, p->max_iters, &res);
-        if (st) { st->iters[slot + q] = it; st->res[slot + q] = res; }
-        tot += it;
-    }
-    free(extra); free(rb); free(b);
-    for (int d = 0; d < 3; d++) free(B[d]);
-    return tot;
+    return viscous_solve(g, geo, par_of<double>(p), eta, psi, dt, ut, st, slot);
 }
 
-int og_nodal_project(const og_grid *g, const og_geom *geo, const og_params *p, double dt,
-                     double *ut, double *pres, og_stats *st, int slot)
+extern "C" int og_nodal_project(const og_grid *g, const og_geom *geo, const og_params *p, double dt, double *ut,
+                                double *pres, og_stats *st, int slot)
 {
-    size_t N3 = og_ncell(g), NN = og_nnode(g);
-    double *gp = malloc(3 * N3 * sizeof(double)), *rhs = malloc(NN * sizeof(double));
-    double coef = dt / p->rho;
-    og_cell_grad_p(g, pres, gp);
-    for (int q = 0; q < 3; q++)
-        for (size_t c = 0; c < N3; c++)
-            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? ut[q * N3 + c] + coef * gp[q * N3 + c] : 0.0;
-    og_nodal_rhs(g, geo, ut, rhs);
-    double res = 0.0;
-    int it = og_nodal_solve(g, geo, coef, rhs, pres, p->tol, p->max_iters, &res);
-    if (st) { st->iters[slot] = it; st->res[slot] = res; }
-    og_cell_grad_p(g, pres, gp);
-    for (int q = 0; q < 3; q++)
-        for (size_t c = 0; c < N3; c++)
-            ut[q * N3 + c] = geo->alpha[c] > 0.0 ? ut[q * N3 + c] - coef * gp[q * N3 + c] : 0.0;
-    free(gp);
-    free(rhs);
-    return it;
+    return nodal_project(g, geo, par_of<double>(p), dt, ut, pres, st, slot);
 }
 
-void og_drag(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
-             const double *pres, double *fz, double *yield_frac)
+extern "C" void og_drag(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                        const double *pres, double *fz, double *yield_frac)
 {
-    size_t N3 = og_ncell(g);
-    double *eta = malloc(N3 * sizeof(double)), *sr = malloc(N3 * sizeof(double));
-    og_strain_eta(g, geo, p, u, eta, sr);
-    const double h = g->h;
-    double F = 0.0, vy = 0.0, vt = 0.0;
-    for (int k = 0; k < NZ; k++)
-        for (int j = 0; j < NY; j++)
-            for (int i = 0; i < NX; i++) {
-                size_t c = cidx(g, i, j, k);
-                double al = geo->alpha[c];
-                if (al <= 0.0) continue;
-                vt += al;
-                if (eta[c] * sr[c] <= (1.0 + 1e-3) * p->tau0) vy += al;
-                if (geo->flag[c] != 2 || geo->area[c] <= 0.0) continue;
-                double n[3], b[3], gq[3];
-                for (int e = 0; e < 3; e++) {
-                    n[e] = geo->nrm[e * N3 + c];
-                    b[e] = geo->bcen[e * N3 + c];
-                    gq[e] = og_wall_dudn(g, geo, u, (int)c, e);
-                }
-                double gn = gq[0] * n[0] + gq[1] * n[1] + gq[2] * n[2];
-                double tz = eta[c] * (n[2] * gn + gq[2]);
-                double pb = 0.0;
-                for (int o = 0; o < 8; o++) {
-                    int oi = o & 1, oj = (o >> 1) & 1, ok = (o >> 2) & 1;
-                    double w = (oi ? b[0] + 0.5 : 0.5 - b[0]) * (oj ? b[1] + 0.5 : 0.5 - b[1]) *
-                               (ok ? b[2] + 0.5 : 0.5 - b[2]);
-                    pb += w * pres[nidx(g, i + oi, j + oj, k + ok)];
-                }
-                F += geo->area[c] * h * h * (tz - pb * n[2]);
-            }
-    *fz = F;
-    *yield_frac = vt > 0.0 ? vy / vt : 0.0;
-    free(eta);
-    free(sr);
+    drag(g, geo, par_of<double>(p), u, pres, fz, yield_frac);
 }
 
-/* Algorithm 1: predictor and corrector with a semi-implicit viscous update
- * and a nodal projection each. */
-int og_advance(const og_grid *g, const og_geom *geo, const og_params *p, double *u, double *pres,
-               double dt_in, const double *f, og_stats *st)
+extern "C" int og_advance(const og_grid *g, const og_geom *geo, const og_params *p, double *u, double *pres,
+                          double dt_in, const double *f, og_stats *st)
 {
-    size_t N3 = og_ncell(g), V3 = 3 * N3;
     double dt = dt_in > 0.0 ? dt_in : og_timestep(g, geo, p, u, f);
-    double *Cm = malloc(V3 * sizeof(double)), *Vm = malloc(V3 * sizeof(double));
-    double *Cs = malloc(V3 * sizeof(double)), *Vs = malloc(V3 * sizeof(double));
-    double *em = malloc(N3 * sizeof(double)), *es = malloc(N3 * sizeof(double));
-    double *psi = malloc(V3 * sizeof(double)), *ut = malloc(V3 * sizeof(double));
-    double *gp = malloc(V3 * sizeof(double)), *ps = malloc(og_nnode(g) * sizeof(double));
-    og_stats loc;
-    memset(&loc, 0, sizeof loc);
-    og_stats tmp;
+    advance(g, geo, par_of<double>(p), u, pres, dt, f, st, (double *)nullptr);
+    return 0;
+}
 
-    /* Predictor */
-    og_derived(g, geo, p, u, Cm, em, Vm, NULL, &tmp);
-    loc.iters[0] = tmp.iters[0];
-    loc.res[0] = tmp.res[0];
-    og_cell_grad_p(g, pres, gp);
-    for (int q = 0; q < 3; q++)
-        for (size_t c = 0; c < N3; c++) {
-            size_t s = q * N3 + c;
-            double fq = f ? f[s] : 0.0;
-            psi[s] = geo->alpha[c] > 0.0
-                         ? p->rho * u[s] + dt * (p->rho * Cm[s] + Vm[s] - gp[s] + fq)
-                         : 0.0;
-        }
-    og_viscous_solve(g, geo, p, em, psi, dt, ut, &loc, 1);
-    memcpy(ps, pres, og_nnode(g) * sizeof(double));
-    og_nodal_project(g, geo, p, dt, ut, ps, &loc, 4);
-    /* ut now holds u*, ps holds p* */
-
-    /* Corrector */
-    og_derived(g, geo, p, ut, Cs, es, Vs, NULL, &tmp);
-    loc.iters[5] = tmp.iters[0];
-    loc.res[5] = tmp.res[0];
-    for (size_t s = 0; s < V3; s++) {
-        Cm[s] = 0.5 * (Cm[s] + Cs[s]);
-        Vm[s] = 0.5 * (Vm[s] + Vs[s]);
+/* Forward-mode derivative of the time-averaged drag (the objective of the
+ * drag sensitivities): J = (1/S) sum_{s=1..S} F_z(u_s, p_s) over S = steps
+ * steps of Algorithm 1 from (u0, p0) at the fixed time step dt, with the
+ * body force f (or none).  The whole run is made in dual numbers with
+ * tau0 + dtau0 e, mu + dmu e and f + df e, so dJ is the exact directional
+ * derivative of J along (dtau0, dmu, df). */
+extern "C" int og_drag_tangent(const og_grid *g, const og_geom *geo, const og_params *p, const double *u0,
+                               const double *p0, const double *f, const double *df, double dtau0, double dmu,
+                               double dt, int steps, double *J, double *dJ)
+{
+    if (!(dt > 0.0) || steps < 1) return -1;
+    size_t N3 = og_ncell(g), NN = og_nnode(g);
+    Par<Dual> q = par_of<Dual>(p);
+    q.tau0 = Dual(p->tau0, dtau0);
+    q.mu = Dual(p->mu, dmu);
+    vector<Dual> u(3 * N3), pr(NN), fd;
+    for (size_t s = 0; s < 3 * N3; s++) u[s] = Dual(u0[s], 0.0);
+    for (size_t s = 0; s < NN; s++) pr[s] = Dual(p0[s], 0.0);
+    if (f || df) {
+        fd.resize(3 * N3);
+        for (size_t s = 0; s < 3 * N3; s++) fd[s] = Dual(f ? f[s] : 0.0, df ? df[s] : 0.0);
     }
-    for (size_t c = 0; c < N3; c++) em[c] = 0.5 * (em[c] + es[c]);
-    og_cell_grad_p(g, ps, gp);
-    for (int q = 0; q < 3; q++)
-        for (size_t c = 0; c < N3; c++) {
-            size_t s = q * N3 + c;
-            double fq = f ? f[s] : 0.0;
-            psi[s] = geo->alpha[c] > 0.0
-                         ? p->rho * u[s] + dt * (p->rho * Cm[s] + Vm[s] - gp[s] + fq)
-                         : 0.0;
-        }
-    og_viscous_solve(g, geo, p, em, psi, dt, ut, &loc, 6);
-    memcpy(pres, ps, og_nnode(g) * sizeof(double));
-    og_nodal_project(g, geo, p, dt, ut, pres, &loc, 9);
-    memcpy(u, ut, V3 * sizeof(double));
-
-    loc.dt = dt;
-    og_drag(g, geo, p, u, pres, &loc.drag, &loc.yield_frac);
-    if (st) *st = loc;
-    free(Cm); free(Vm); free(Cs); free(Vs); free(em); free(es);
-    free(psi); free(ut); free(gp); free(ps);
+    Dual acc = 0.0;
+    for (int s = 0; s < steps; s++) {
+        Dual fz;
+        advance(g, geo, q, u.data(), pr.data(), dt, fd.empty() ? (const Dual *)nullptr : fd.data(),
+                (og_stats *)nullptr, &fz);
+        acc += fz;
+    }
+    acc /= Dual((double)steps);
+    *J = acc.v;
+    *dJ = acc.d;
     return 0;
 }

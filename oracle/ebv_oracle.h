@@ -14,10 +14,18 @@
  *
  * Parity notes: every elliptic solution is defined as the exact solution of
  * its discrete system; the oracle reaches it with Jacobi-preconditioned CG.
+ *
+ * The implementation (ebv_oracle.cpp) is C++ with C linkage for every entry
+ * point below; its flow arithmetic is written once for a generic scalar and
+ * instantiated in double and in forward-mode dual numbers (og_drag_tangent).
  */
 #ifndef EBV_ORACLE_H
 #define EBV_ORACLE_H
 #include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
 
 /* Domain side types (sides ordered x-, x+, y-, y+, z-, z+). */
 enum { OG_INFLOW = 0, OG_OUTFLOW = 1, OG_SLIP = 2, OG_NOSLIP = 3 };
@@ -120,6 +128,20 @@ int og_advance(const og_grid *g, const og_geom *geo, const og_params *p, double 
 void og_drag(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
              const double *pres, double *fz, double *yield_frac);
 
+/* Forward-mode (dual-number) derivative of J = (1/steps) sum_{s=1..steps}
+ * F_z(u_s, p_s), the drag of Eq. drag-force averaged over `steps` steps of
+ * Algorithm 1 from (u0, p0) at the fixed time step dt > 0 with body force f
+ * (3*N3 or NULL), along the direction tau0 += dtau0, mu += dmu, f += df (df
+ * 3*N3 or NULL).  Writes J and its exact directional derivative dJ; returns
+ * 0, or -1 for dt <= 0 or steps < 1. */
+int og_drag_tangent(const og_grid *g, const og_geom *geo, const og_params *p, const double *u0,
+                    const double *p0, const double *f, const double *df, double dtau0, double dmu,
+                    double dt, int steps, double *J, double *dJ);
+
 size_t og_ncell(const og_grid *g);
 size_t og_nnode(const og_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
 #endif
