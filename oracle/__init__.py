@@ -82,7 +82,13 @@ def lib():
         _lib.og_ncell.restype = C.c_size_t
         _lib.og_nnode.restype = C.c_size_t
         _lib.og_drag_tangent.restype = C.c_int
+        _lib.og_threads.restype = C.c_int
     return _lib
+
+
+def threads() -> int:
+    """Threads the oracle runs on."""
+    return int(lib().og_threads())
 
 
 def _p(a):
@@ -220,6 +226,16 @@ def strain_eta(grid, geo, params, u):
     lib().og_strain_eta(C.byref(grid.c()), C.byref(geo.c()), C.byref(params.c()), _p(u),
                         _p(eta), _p(sr))
     return eta, sr
+
+
+def flow_diagnostics(grid, geo, params, u):
+    """Per cell: Lambda of Eq. ryovar and the yield-stress deviation eta ||g|| / tau0 - 1."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lam = np.zeros(grid.ncell)
+    sdev = np.zeros(grid.ncell)
+    lib().og_flow_diagnostics(C.byref(grid.c()), C.byref(geo.c()), C.byref(params.c()), _p(u), _p(lam),
+                              _p(sdev))
+    return lam, sdev
 
 
 def cell_gradient(grid, geo, u):

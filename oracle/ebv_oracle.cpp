@@ -58,6 +58,10 @@
 
 #include "og_dual.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define NX (g->n[0])
 #define NY (g->n[1])
 #define NZ (g->n[2])
@@ -135,6 +139,16 @@ R dot(const R *a, const R *b, size_t n)
 
 extern "C" size_t og_ncell(const og_grid *g) { return (size_t)NX * NY * NZ; }
 extern "C" size_t og_nnode(const og_grid *g) { return (size_t)(NX + 1) * (NY + 1) * (NZ + 1); }
+
+/* Threads the oracle's loops run on (1 without OpenMP). */
+extern "C" int og_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Geometry (double only)                                                    */
@@ -612,6 +626,26 @@ int cc_solve(const og_grid *g, const R *extra, const R *bx, const R *by, const R
     return pcg<R>(A, diag.data(), b, x, N3, tol, max_iters, res_out);
 }
 
+/* A box with no outflow side (velocity prescribed or walls all round, as in
+ * the paper's cylinder and sphere runs with U on every boundary, or the
+ * Taylor-Green vortex between slip walls) leaves both pressure problems pure
+ * Neumann: their solutions are fixed only up to a constant.  One Dirichlet
+ * point fixes them: the x- face of cell (0,0,0) acts as an outflow face
+ * (phi = 0 beyond it) in the cell-centred projection, and node (0,0,0) is a
+ * Dirichlet node (p = 0) in the nodal one.  With a consistent right-hand side
+ * (zero net boundary flux) the solution is the pure-Neumann one that is zero
+ * at that point. */
+int no_outflow(const og_grid *g)
+{
+    for (int s = 0; s < 6; s++)
+        if (g->bc[s] == OG_OUTFLOW) return 0;
+    return 1;
+}
+int pin_face(const og_grid *g, int d, int i, int j, int k)
+{
+    return d == 0 && i == 0 && j == 0 && k == 0 && no_outflow(g);
+}
+
 /* Boundary condition of velocity component `comp` on box side `side`:
  * returns 1 and the value for Dirichlet, 0 for Neumann. */
 int side_dirichlet(const og_grid *g, int side, int comp, double *val)
@@ -645,7 +679,7 @@ void mac_coeffs(const og_grid *g, const og_geom *geo, R *extra, R *bx, R *by, R 
                     size_t f = fidx(g, d, i, j, k);
                     if (id[d] == 0 || id[d] == g->n[d]) {
                         int side = 2 * d + (id[d] == g->n[d]);
-                        B[f] = g->bc[side] == OG_OUTFLOW ? 2.0 * a[f] / h2 : 0.0;
+                        B[f] = (g->bc[side] == OG_OUTFLOW || pin_face(g, d, i, j, k)) ? 2.0 * a[f] / h2 : 0.0;
                     } else {
                         B[f] = a[f] / h2;
                     }
@@ -731,6 +765,7 @@ double q1_stiff(int oa, int ob)
 
 int node_dirichlet(const og_grid *g, int i, int j, int k)
 {
+    if (i == 0 && j == 0 && k == 0 && no_outflow(g)) return 1;  /* the pinned node */
     int id[3] = {i, j, k};
     for (int d = 0; d < 3; d++) {
         if (id[d] == 0 && g->bc[2 * d] == OG_OUTFLOW) return 1;
@@ -1009,7 +1044,7 @@ int mac_project(const og_grid *g, const og_geom *geo, R *uf, R *phi, double tol,
                     if (a[f] <= 0.0) continue;
                     if (id[d] == 0 || id[d] == g->n[d]) {
                         int hs = id[d] == g->n[d];
-                        if (g->bc[2 * d + hs] != OG_OUTFLOW) continue;
+                        if (g->bc[2 * d + hs] != OG_OUTFLOW && !pin_face(g, d, i, j, k)) continue;
                         int cc[3] = {i, j, k};
                         if (hs) cc[d] -= 1;
                         R pc = phi[cidx(g, cc[0], cc[1], cc[2])];
@@ -1418,6 +1453,31 @@ void advance(const og_grid *g, const og_geom *geo, const Par<R> &p, R *u, R *pre
 
 }  // namespace
 
+/* Flow diagnostics of Sec. "Cylinder moving through Bingham fluid": the flow
+ * topology parameter of Eq. ryovar, Lambda = (||g||^2 - |w|^2) / (||g||^2 +
+ * |w|^2) with ||g|| the strain-rate norm and w = curl u (0 where both vanish),
+ * and the relative deviation from the yield stress, ||tau|| / tau0 - 1 with
+ * ||tau|| = eta ||g|| (0 when tau0 = 0).  Gradients are the robust cell
+ * gradients of the strain-rate step; covered cells get 0. */
+template <class R>
+void flow_diagnostics(const og_grid *g, const og_geom *geo, const Par<R> &p, const R *u, R *lam, R *sdev)
+{
+    size_t N3 = og_ncell(g);
+    vector<R> G(9 * N3), eta(N3), sr(N3);
+    cell_gradient(g, geo, u, G.data());
+    strain_eta(g, geo, p, u, eta.data(), sr.data());
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < (long)N3; c++) {
+        if (geo->alpha[c] <= 0.0) { lam[c] = 0.0; sdev[c] = 0.0; continue; }
+        auto D = [&](int d, int q) -> R { return G[(3 * d + q) * N3 + c]; };  /* du_q / dx_d */
+        R wx = D(1, 2) - D(2, 1), wy = D(2, 0) - D(0, 2), wz = D(0, 1) - D(1, 0);
+        R w2 = wx * wx + wy * wy + wz * wz;
+        R s2 = sr[c] * sr[c];
+        lam[c] = (s2 + w2) > 0.0 ? (s2 - w2) / (s2 + w2) : R(0.0);
+        sdev[c] = p.tau0 > 0.0 ? eta[c] * sr[c] / p.tau0 - 1.0 : R(0.0);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* C entry points (double)                                                   */
 /* ------------------------------------------------------------------------ */
@@ -1428,6 +1488,12 @@ extern "C" void og_strain_eta(const og_grid *g, const og_geom *geo, const og_par
                               double *srate)
 {
     strain_eta(g, geo, par_of<double>(p), u, eta, srate);
+}
+
+extern "C" void og_flow_diagnostics(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                                    double *lam, double *sdev)
+{
+    flow_diagnostics(g, geo, par_of<double>(p), u, lam, sdev);
 }
 
 extern "C" void og_cell_gradient(const og_grid *g, const og_geom *geo, const double *u, double *grad)

@@ -80,6 +80,10 @@ void og_build_geometry(const og_grid *g, const og_shape *s, og_geom *geo);
 double og_eta_of(const og_params *p, double sr);
 void og_strain_eta(const og_grid *g, const og_geom *geo, const og_params *p,
                    const double *u, double *eta, double *srate);
+/* Flow topology parameter Lambda (Eq. ryovar) and yield-stress deviation
+ * eta ||g|| / tau0 - 1 per cell (Sec. "Cylinder moving through Bingham fluid"). */
+void og_flow_diagnostics(const og_grid *g, const og_geom *geo, const og_params *p, const double *u,
+                         double *lam, double *sdev);
 void og_cell_gradient(const og_grid *g, const og_geom *geo, const double *u,
                       double *grad /* 9*N3: grad[(3*d+c)*N3+cell] = du_c/dx_d */);
 
@@ -140,6 +144,8 @@ int og_drag_tangent(const og_grid *g, const og_geom *geo, const og_params *p, co
 
 size_t og_ncell(const og_grid *g);
 size_t og_nnode(const og_grid *g);
+/* Threads the oracle's loops run on (its OpenMP team size; 1 without OpenMP). */
+int og_threads(void);
 
 #ifdef __cplusplus
 }

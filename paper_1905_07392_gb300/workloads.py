@@ -114,3 +114,52 @@ def body_force(w: Workload, sigma: float = 0.1) -> np.ndarray:
 
 def with_steps(w: Workload, steps: int) -> Workload:
     return replace(w, steps=steps)
+
+
+# ---------------------------------------------------------------------------
+# Taylor-Green vortex (Sec. "Spatio-temporal convergence study: Taylor-Green
+# vortices", Eq. taylor-green): unit box in x and y, rho = U = L = 1,
+# mu = 1 / Re.  The paper runs it with periodic sides; the same solution also
+# satisfies slip walls at x, y in {0, 1} exactly (u_n = 0 and zero tangential
+# stress there), and slip walls in z with a field uniform in z, so the box
+# here has slip walls on all six sides.
+# ---------------------------------------------------------------------------
+TG_BC = (SLIP, SLIP, SLIP, SLIP, SLIP, SLIP)
+
+
+def taylor_green(x, y, t, re=100.0):
+    """(u, v, p) of Eq. taylor-green at points (x, y) and time t."""
+    f = np.exp(-8.0 * np.pi ** 2 * t / re)
+    u = np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * f
+    v = -np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y) * f
+    p = 0.25 * (np.cos(4 * np.pi * x) + np.cos(4 * np.pi * y)) * f * f
+    return u, v, p
+
+
+def taylor_green_grid(n, nz=8):
+    """Cells (n, n, nz) of size 1/n: the unit square in x, y, nz cells deep."""
+    return (n, n, nz), 1.0 / n
+
+
+def taylor_green_velocity(n, nz=8, t=0.0, re=100.0):
+    """Cell-centred (u, v, w), shape (3, nz, n, n), at time t."""
+    c = (np.arange(n) + 0.5) / n
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    u, v, _ = taylor_green(X, Y, t, re)
+    out = np.zeros((3, nz, n, n))
+    out[0] = u[None]
+    out[1] = v[None]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The paper's sphere set-up (Sec. "Sphere moving through Bingham fluid"):
+# box [0, 4D] x [0, 4D] x [0, 6D] with u = U e_z on every side (the sphere
+# falls at U through fluid at rest), sphere of diameter D at the centre.
+# ---------------------------------------------------------------------------
+def sphere_box(cells_per_d=16, bi=1.0, m=1e3, D=0.25):
+    n = (4 * cells_per_d, 4 * cells_per_d, 6 * cells_per_d)
+    r = 0.5 * D
+    return Workload(f"sphere_box_{cells_per_d}perD_bi{bi:g}", n=n[0], radius=r, centre=(2 * D, 2 * D, 3 * D),
+                    tau0=tau0_for_bingham(bi, r), m=m, model=BINGHAM if bi > 0 else NEWTONIAN, noise=0.0,
+                    bc=(INFLOW,) * 6, extra={"shape": n, "h": D / cells_per_d})

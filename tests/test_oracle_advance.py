@@ -133,3 +133,44 @@ def test_creeping_newtonian_step_is_affine(O):
         gaps[advect] = max(np.abs(du).max() / np.abs(out[2][0]).max(), np.abs(dp).max() / np.abs(out[2][1]).max())
     assert gaps[0] < 1e-11
     assert gaps[1] > 1e-6
+
+
+def test_taylor_green_between_slip_walls_second_order(O):
+    """Whole step, time and space together (Sec. "Spatio-temporal convergence
+    study: Taylor-Green vortices", Eq. taylor-green): the vortex at Re = 100
+    between slip walls (the periodic solution satisfies them exactly) with
+    dt = h/4 to t = 0.25; the velocity error at the cell centres falls at
+    second order from 16^2 to 32^2 cells in the L1, L2 and max norms.  The box
+    has no outflow side, so both pressure problems take the reference point
+    (nodal p = 0 at node (0,0,0))."""
+    from paper_1905_07392_gb300 import workloads as W
+    errs = []
+    for n in (16, 32):
+        shape, h = W.taylor_green_grid(n)
+        g = O.Grid(n=shape, h=h, bc=W.TG_BC, u_in=(0.0, 0.0, 0.0))
+        geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_NONE))
+        P = O.Params(rho=1.0, mu=0.01, tau0=0.0, model=O.NEWTONIAN, tol=1e-12)
+        u, p = W.taylor_green_velocity(n).ravel(), np.zeros(g.nnode)
+        for _ in range(n):
+            u, p, st = O.advance(g, geo, P, u, p, dt=0.25 / n)
+        assert p[0] == 0.0
+        e = u.reshape(3, -1) - W.taylor_green_velocity(n, t=0.25).reshape(3, -1)
+        mag = np.sqrt((e * e).sum(axis=0))
+        errs.append((mag.mean(), np.sqrt((mag * mag).mean()), mag.max()))
+        assert np.abs(u.reshape(3, -1)[2]).max() < 1e-10   # no flow out of the x-y plane
+    rates = np.log2(np.array(errs[0]) / np.array(errs[1]))
+    assert (rates > 1.8).all(), (errs, rates)
+
+
+def test_uniform_flow_with_velocity_on_every_side_is_steady(O):
+    """u = U e_z on every side (the paper's sphere and cylinder runs) around
+    no body: uniform flow is an exact discrete solution; the pressure problems
+    have no outflow side and take the reference point, so p stays 0."""
+    n = 12
+    g = O.Grid(n=(n, n, n), h=1.0 / n, bc=(O.INFLOW,) * 6, u_in=(0.0, 0.0, 1.0))
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_NONE))
+    P = O.Params(tau0=1.0, m=1e3, bi_cfl=1.0, tol=1e-13)
+    u = np.concatenate([np.zeros(2 * g.ncell), np.ones(g.ncell)])
+    u1, p1, st = O.advance(g, geo, P, u, np.zeros(g.nnode))
+    assert np.abs(u1 - u).max() < 1e-12
+    assert np.abs(p1).max() < 1e-12
