@@ -31,7 +31,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-steps/s at 256^3 (FP32+refine, 1e-8 tol)"
 UNIT = "Mcell-steps/s"
-CPU_SAMPLE_N = 32  # oracle sample grid (same problem, coarser grid)
+CPU_SAMPLE_N = 64  # oracle sample grid (same problem, coarser grid)
+PRECISION = ("FP64 iterative refinement (FP64 operator, residual and solution) around FP32 conjugate "
+             "gradients preconditioned by an FP32 multigrid V-cycle whose cell-centred face coefficients "
+             "are stored in BF16 (nodal V-cycle FP32); geometry and fields FP64")
 
 
 def parse():
@@ -46,6 +49,12 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--skip-fp32-faces", action="store_true")
+    ap.add_argument("--skip-config2", action="store_true")
+    ap.add_argument("--cpu-sample-n", type=int, default=CPU_SAMPLE_N,
+                    help="grid of the oracle sample (cpu_baseline and the reference arm)")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time the oracle on the 128^3 sphere channel (minutes)")
     ap.add_argument("--eager", action="store_true",
                     help="issue every step kernel by kernel (no step graph), e.g. under a profiler")
     return ap.parse_args()
@@ -151,9 +160,9 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def make_solver(w, precision, tol=1e-8):
+def make_solver(w, precision, tol=1e-8, lib=None):
     from paper_1905_07392_gb300 import ebvisc
-    return ebvisc.Solver.from_workload(w, precision=precision, tol=tol, max_iters=2000)
+    return ebvisc.Solver.from_workload(w, precision=precision, tol=tol, max_iters=2000, lib=lib)
 
 
 def initial_state(s, w, dev):
@@ -276,11 +285,11 @@ def run_ours(args, rank, world, local):
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sec / args.steps, 3),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+bf16",
            "data": "synthetic (seeded noise on uniform inflow; no dataset)",
            "config": {"workload": f"sphere_channel_{w.n}^3_bi10_m1e4", "cells": cells,
                       "sphere_radius": w.radius, "bingham": w.bingham, "m": w.m, "tol": 1e-8,
-                      "precision": "fp32 multigrid, fp64 Krylov/residual/solution",
+                      "precision": PRECISION,
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (each cell field 134 MB at 256^3)"},
            "roofline": roof, "kernels": kernels,
@@ -312,6 +321,27 @@ def run_ours(args, rank, world, local):
                                "p_rel_l2": rel(p, p64),
                                "drag_rel": abs(st["drag"] - st64["drag"]) / abs(st64["drag"])}
         s64.close()
+
+    if not args.skip_fp32_faces:
+        # the same path with the V-cycle reading FP32 instead of BF16 face
+        # coefficients (a build variant of the library: only the face type differs)
+        from paper_1905_07392_gb300 import build_lib
+        vlib = ebvisc.load_variant(build_lib.VARIANT_LIB)
+        sf = make_solver(w, ebvisc.FP32_REFINE, lib=vlib)
+        uf, pf = initial_state(sf, w, dev)
+        secf, _, _ = time_steps(sf, uf, pf, args.steps, args.warmup, world, graph=True)
+        secf = max_over_ranks(secf, world)
+        stf = sf.advance(uf.clone(), pf.clone(), stats=True)
+        out["fp32_faces"] = {"value": round(job_value(cells, args.steps, world, secf), 3), "unit": UNIT,
+                             "ms_per_step": round(1e3 * secf / args.steps, 3),
+                             "solve_iters_last_step": stf["iters"],
+                             "note": "same step with the FP32 V-cycle reading FP32 face coefficients "
+                                     "(library build variant EBV_VCYCLE_FP32_FACES); headline uses BF16"}
+        sf.close()
+        del uf, pf
+
+    if not args.skip_config2:
+        out["config2"] = run_config2(dev)
 
     if not args.skip_e2e:
         # end to end through the C-ABI with host buffers: every step copies
@@ -345,6 +375,34 @@ def run_ours(args, rank, world, local):
                 out[key] = run_adjoint(dev, advect=adv)
             except Exception as e:  # reported in the line; the rest of the measurement stands
                 out[key] = {"error": str(e)}
+    return out
+
+
+def run_config2(dev, steps=20, tol=1e-10):
+    """The 128^3 sphere channel (r = 0.125, m = 1e3) for Bi in {0, 1, 10} and
+    Herschel-Bulkley n = 0.5, FP64 path, 20 CFL steps each: drag F_D (Eq.
+    drag-force), Stokes coefficient C_S = F_D / (6 pi mu U R) (Eq. drag-coef;
+    mu is kappa for HB) and unyielded fraction after the last step."""
+    import math
+    import torch
+    from paper_1905_07392_gb300 import ebvisc
+    from paper_1905_07392_gb300 import workloads as W
+    out = {"steps": steps, "tol": tol, "precision": "fp64", "cases": {}}
+    for name, w in (("bi0", W.sphere_channel_128(0.0)), ("bi1", W.sphere_channel_128(1.0)),
+                    ("bi10", W.sphere_channel_128(10.0)), ("hb_n0.5", W.sphere_channel_128(herschel_bulkley=True))):
+        s = ebvisc.Solver.from_workload(w, precision=ebvisc.FP64, tol=tol, max_iters=5000)
+        u, p = initial_state(s, w, dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps - 1):
+            s.advance(u, p, stats=False)
+        st = s.advance(u, p, stats=True)
+        torch.cuda.synchronize()
+        out["cases"][name] = {"bingham": round(w.bingham, 6), "F_D": st["drag"],
+                              "C_S": st["drag"] / (6.0 * math.pi * w.mu * 1.0 * w.radius),
+                              "yield_frac": st["yield_frac"], "dt": st["dt"],
+                              "seconds": round(time.perf_counter() - t0, 3)}
+        s.close()
     return out
 
 
@@ -479,21 +537,58 @@ def oracle_case(n):
     return O, g, geo, P, u, np.zeros(g.nnode)
 
 
-def cpu_baseline(steps=3):
-    O, g, geo, P, u, p = oracle_case(CPU_SAMPLE_N)
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def time_oracle(n, steps, warmup):
+    """Oracle steps of the benchmark's problem on an n^3 grid: `warmup`
+    untimed steps, then `steps` timed; returns (Mcell-steps/s, seconds)."""
+    O, g, geo, P, u, p = oracle_case(n)
+    for _ in range(warmup):
+        u, p, st = O.advance(g, geo, P, u, p)
     t0 = time.perf_counter()
     for _ in range(steps):
         u, p, st = O.advance(g, geo, P, u, p)
     t = time.perf_counter() - t0
-    return {"value": round(g.ncell * steps / t / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle step(s) of the same problem on a {CPU_SAMPLE_N}^3 grid "
-                      f"(single-threaded C, FP64, tol 1e-8), {t:.1f} s"}
+    return g.ncell * steps / t / 1e6, t
+
+
+def cpu_baseline(full=False, n=CPU_SAMPLE_N):
+    import oracle as O
+    value, t = time_oracle(n, 2, 1)
+    out = {"value": round(value, 6), "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+           "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+           "sample": f"2 oracle steps (after 1 warm-up) of the same problem (r = 0.1, Bi = 10, m = 1e4, "
+                     f"tol 1e-8) on a {n}^3 grid, FP64 C++ with OpenMP on {O.threads()} threads, "
+                     f"{t:.1f} s"}
+    if full:
+        v128, t128 = time_oracle(128, 2, 1)
+        out["oracle_128"] = {"value": round(v128, 6), "unit": UNIT, "seconds": round(t128, 1),
+                             "sample": "2 oracle steps after 1 warm-up on the 128^3 grid"}
+    return out
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    O, g, geo, P, u, p = oracle_case(CPU_SAMPLE_N)
+    import oracle as O
+    n = args.cpu_sample_n
+    O_, g, geo, P, u, p = oracle_case(n)
     for _ in range(args.warmup):
         u, p, st = O.advance(g, geo, P, u, p)
     t0 = time.perf_counter()
@@ -501,13 +596,15 @@ def run_reference(args, rank, world):
         u, p, st = O.advance(g, geo, P, u, p)
     t = time.perf_counter() - t0
     value = g.ncell * args.steps / t / 1e6
+    sample = (f"each step: one oracle step of the same problem on a {n}^3 grid "
+              f"(FP64 C++, OpenMP on {O.threads()} threads, tol 1e-8)")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * t / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"sphere_channel_256^3_bi10_m1e4 (oracle sample {CPU_SAMPLE_N}^3)"},
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one oracle step on a {CPU_SAMPLE_N}^3 grid"},
+            "config": {"workload": f"sphere_channel_256^3_bi10_m1e4 (oracle sample {n}^3)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                             "host_cpus": os.cpu_count(), "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -525,7 +622,7 @@ def main():
     out = run_ours(args, rank, world, local)
     if rank == 0:
         if not args.skip_cpu and world == 1:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(full=args.cpu_full, n=args.cpu_sample_n)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -47,7 +47,11 @@ typedef enum {
     EBV_ERR_NOT_CONVERGED = -3,  /* a linear solve hit max_iters above tol */
     EBV_ERR_NAN = -5,            /* a residual became NaN or Inf */
     EBV_ERR_GEOMETRY = -6,       /* geometry missing or unsupported */
-    EBV_ERR_TOO_LARGE = -7       /* beyond the fixed working storage of ebv_drag_noalloc */
+    EBV_ERR_TOO_LARGE = -7,      /* beyond the fixed working storage of ebv_drag_noalloc */
+    EBV_ERR_OOM = -8,            /* a device allocation failed for lack of memory (or past the
+                                    budget of ebv_set_alloc_limit); nothing is left allocated */
+    EBV_ERR_CUDA_PENDING = -9    /* a CUDA error of earlier work was pending on entry; it is
+                                    left in place for its owner (ebv_drag_noalloc) */
 } ebv_status;
 
 /* Box side types, sides ordered x-, x+, y-, y+, z-, z+. */
@@ -96,6 +100,13 @@ typedef struct {
     double yield_frac;  /* fluid volume fraction with ||tau|| <= (1 + 1e-3) tau0 */
     int iters[10];      /* Krylov iterations: MAC, visc x3, nodal (predictor); same (corrector) */
     double res[10];     /* final relative residuals, same order */
+    double div_rel;     /* largest relative divergence the step's four projections leave: the
+                           cell-centred ones' ||D u^F|| / ||D u~^F|| and the nodal ones' relative
+                           residual (the projection is approximate) */
+    float ms[8];        /* GPU time of the step's phases (ebv_advance only; 0 from the graph
+                           forms): time step, predictor derived quantities (Algorithm 2),
+                           predictor viscous solves, predictor projection, the same three for
+                           the corrector, drag.  The phases are also NVTX ranges. */
 } ebv_step_stats;
 
 /* Implicit function of the body: > 0 in the fluid, <= 0 in the body. */
@@ -119,17 +130,60 @@ ebv_status ebv_build_geometry(ebv_ctx *ctx, ebv_implicit_fn fn, void *user);
 ebv_status ebv_build_geometry_sphere(ebv_ctx *ctx, const double c[3], double r);
 /* The same for a half-space n.x > d (tests of planar cuts). */
 ebv_status ebv_build_geometry_plane(ebv_ctx *ctx, const double nrm[3], double d);
+/* Bodies for the device-side geometry builders: the fluid is outside every
+ * body (their union is the EB).  q holds, per kind:
+ *   EBV_BODY_SPHERE    centre x, y, z and radius;
+ *   EBV_BODY_BOX       low corner x, y, z and high corner x, y, z (axis-aligned);
+ *   EBV_BODY_CYLINDER  axis (0, 1 or 2), the centre's two other coordinates in
+ *                      axis order after it ((axis+1) % 3, (axis+2) % 3), radius
+ *                      (infinite along the axis). */
+enum { EBV_BODY_SPHERE = 0, EBV_BODY_BOX = 1, EBV_BODY_CYLINDER = 2 };
+typedef struct {
+    int kind;
+    double q[6];
+} ebv_body;
+/* The geometry of ebv_build_geometry for n spheres (c_r: n rows cx, cy, cz,
+ * r in host memory), computed on the device (the same planar-cut steps, run
+ * by GPU threads per node, edge, face and cell) -- the fast path for large
+ * grids.  Agrees with the host builder to rounding.  n in [1, 16]. */
+ebv_status ebv_build_geometry_spheres(ebv_ctx *ctx, int n, const double *c_r);
+/* The same for any union of up to 16 bodies (host array), e.g. the paper's
+ * sphere-and-cube body (Sec. "Non-trivial particle shape") or its cylinder
+ * (Sec. "Cylinder moving through Bingham fluid"). */
+ebv_status ebv_build_geometry_bodies(ebv_ctx *ctx, int n, const ebv_body *bodies);
 /* Copy the geometry out (device pointers, any may be NULL):
  * alpha, area (cells), ax/ay/az (faces), nrm/bcen (3 x cells; bcen relative
  * to the cell centre in units of h), flag (cells: 0 covered, 1 regular, 2 cut). */
 ebv_status ebv_get_geometry(ebv_ctx *ctx, double *alpha, double *ax, double *ay, double *az,
                             double *area, double *nrm, double *bcen, unsigned char *flag);
 
+/* Resumable state (checkpoint / restart of a run of Algorithm 1).
+ * ebv_save_state writes the grid, the parameters, the geometry and the
+ * fields u (3 x cells) and p (nodes) -- device pointers, unchanged -- to the
+ * file at `path` (host byte order; a file of this library version).
+ * ebv_load_state reads such a file into a context created on the same grid:
+ * it replaces the parameters and the geometry (and rebuilds the solver data
+ * from them, allocating as a geometry build does) and writes u and p (device).
+ * Steps taken from a loaded state are bit for bit those the saving run would
+ * have taken.  EBV_ERR_INVALID for an unreadable or foreign file or another
+ * grid; EBV_ERR_GEOMETRY if no geometry was built (save). */
+ebv_status ebv_save_state(ebv_ctx *ctx, const double *u, const double *p, const char *path);
+ebv_status ebv_load_state(ebv_ctx *ctx, double *u, double *p, const char *path);
+
 /* Fused strain rate and apparent viscosity (paper Sec. "Strain rate tensor and
  * apparent viscosity", Table of rheologies): central differences, one-sided
  * quadratic differences next to covered cells; ||gamma|| = sqrt(tr(g g^T)/2).
  * u: 3 x cells; eta: cells; srate: cells or NULL. */
 ebv_status ebv_update_viscosity(ebv_ctx *ctx, const double *u, double *eta, double *srate);
+
+/* Flow diagnostics of the paper's cylinder and sphere studies (Sec. "Cylinder
+ * moving through Bingham fluid"): per cell the flow topology parameter of
+ * Eq. ryovar, lambda = (||g||^2 - |w|^2) / (||g||^2 + |w|^2) with w = curl u
+ * (-1 rigid rotation, 0 shear, 1 extension; 0 where both vanish), and the
+ * relative deviation from the yield stress, stress_dev = eta ||g|| / tau0 - 1
+ * (negative where unyielded; 0 when tau0 = 0).  Gradients as in
+ * ebv_update_viscosity.  u: 3 x cells; lambda, stress_dev: cells (device). */
+ebv_status ebv_flow_diagnostics(ebv_ctx *ctx, const double *u, double *lambda, double *stress_dev);
 
 /* Derived quantities of Algorithm 2 for a velocity u: convective term C,
  * apparent viscosity eta and explicit viscous term V (3 x cells, cells,
@@ -201,11 +255,26 @@ ebv_status ebv_drag(ebv_ctx *ctx, const double *u, const double *p, double *fz_h
  * share the one array and every call writes what it reads, so nothing carries
  * over between calls, but calls whose work overlaps on the GPU (other streams,
  * other threads) race on it and must be serialised by the caller.  Work is
- * queued asynchronously on `stream`; `out` is valid once it completes. */
+ * queued asynchronously on `stream`; `out` is valid once it completes.
+ * The device address is looked up once per device and kept for the life of
+ * the process: after a cudaDeviceReset the array may move, so a process that
+ * resets a device must not call this entry again (restart the process).
+ * The C side cannot see buffer sizes: the caller guarantees that u holds
+ * 3 x cells, p the nodes, and every entry of `cut` lies in [0, cells) (an
+ * entry outside is skipped).  EBV_ERR_INVALID for a NULL pointer, a
+ * non-positive size or h <= 0; EBV_ERR_CUDA_PENDING if an error of earlier
+ * work was pending on entry (nothing is queued then). */
 ebv_status ebv_drag_noalloc(const ebv_grid *grid, const ebv_params *params, const double *alpha,
                             const double *area, const double *nrm, const double *bcen,
                             const unsigned char *flag, const int *cut, int ncut, const double *u,
                             const double *p, double *out, void *stream);
+
+/* Fault injection on the host, for tests of the out-of-memory path: device
+ * allocations the library makes after this call fail as out-of-memory once
+ * they total more than `bytes` (the call that fails reports EBV_ERR_OOM and
+ * frees what it took); bytes < 0 removes the limit.  Process-wide; the
+ * device is never actually exhausted. */
+void ebv_set_alloc_limit(long long bytes);
 
 /* Counters for the measurement harness: kernel launches queued since the
  * context was created (host counter). */

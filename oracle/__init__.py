@@ -23,7 +23,8 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 INFLOW, OUTFLOW, SLIP, NOSLIP = 0, 1, 2, 3
 NEWTONIAN, BINGHAM, HB, POWERLAW, SMD = 0, 1, 2, 3, 4
-SHAPE_NONE, SHAPE_SPHERE, SHAPE_PLANE = 0, 1, 2
+SHAPE_NONE, SHAPE_SPHERE, SHAPE_PLANE, SHAPE_UNION = 0, 1, 2, 3
+BODY_SPHERE, BODY_BOX, BODY_CYLINDER = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -54,7 +55,8 @@ class _Params(C.Structure):
 
 
 class _Shape(C.Structure):
-    _fields_ = [("kind", C.c_int), ("p", C.c_double * 8)]
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 8), ("nbody", C.c_int), ("bkind", C.c_int * 16),
+                ("bq", C.c_double * 96)]
 
 
 class _Geom(C.Structure):
@@ -171,12 +173,18 @@ class Params:
 class Shape:
     kind: int = SHAPE_SPHERE
     p: tuple = (0.5, 0.5, 0.5, 0.125)
+    bodies: tuple = ()      # SHAPE_UNION: ((BODY_*, (q0, ...)), ...)
 
     def c(self):
         s = _Shape()
         s.kind = self.kind
         vals = list(self.p) + [0.0] * (8 - len(self.p))
         s.p[:] = vals
+        s.nbody = len(self.bodies)
+        for b, (kind, q) in enumerate(self.bodies):
+            s.bkind[b] = int(kind)
+            for e, v in enumerate(q):
+                s.bq[6 * b + e] = float(v)
         return s
 
 

@@ -161,6 +161,34 @@ extern "C" double og_phi(const og_shape *s, const double x[3])
         return sqrt(dx * dx + dy * dy + dz * dz) - s->p[3];
     }
     if (s->kind == OG_SHAPE_PLANE) return s->p[0] * x[0] + s->p[1] * x[1] + s->p[2] * x[2] - s->p[3];
+    if (s->kind == OG_SHAPE_UNION) {
+        /* outside every body: the smallest of the bodies' functions */
+        double v = 1e300;
+        for (int b = 0; b < s->nbody; b++) {
+            const double *q = s->bq[b];
+            double w;
+            if (s->bkind[b] == OG_BODY_SPHERE) {
+                w = sqrt((x[0] - q[0]) * (x[0] - q[0]) + (x[1] - q[1]) * (x[1] - q[1]) +
+                         (x[2] - q[2]) * (x[2] - q[2])) - q[3];
+            } else if (s->bkind[b] == OG_BODY_BOX) {
+                /* signed distance to the box: outside, the distance to its
+                 * nearest point; inside, minus the distance to its surface */
+                double o2 = 0.0, in = -1e300;
+                for (int d = 0; d < 3; d++) {
+                    double below = q[d] - x[d], above = x[d] - q[3 + d];
+                    double gap = below > above ? below : above;
+                    if (gap > 0.0) o2 += gap * gap;
+                    if (gap > in) in = gap;
+                }
+                w = sqrt(o2) + (in < 0.0 ? in : 0.0);
+            } else {
+                int ax = (int)q[0], a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+                w = sqrt((x[a1] - q[1]) * (x[a1] - q[1]) + (x[a2] - q[2]) * (x[a2] - q[2])) - q[3];
+            }
+            if (w < v) v = w;
+        }
+        return v;
+    }
     return 1.0;
 }
 

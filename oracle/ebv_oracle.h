@@ -32,7 +32,11 @@ enum { OG_INFLOW = 0, OG_OUTFLOW = 1, OG_SLIP = 2, OG_NOSLIP = 3 };
 /* Rheology (Table "Generalised Newtonian fluid models"). */
 enum { OG_NEWTONIAN = 0, OG_BINGHAM = 1, OG_HB = 2, OG_POWERLAW = 3, OG_SMD = 4 };
 /* Implicit functions (fluid where phi > 0). */
-enum { OG_SHAPE_NONE = 0, OG_SHAPE_SPHERE = 1, OG_SHAPE_PLANE = 2 };
+enum { OG_SHAPE_NONE = 0, OG_SHAPE_SPHERE = 1, OG_SHAPE_PLANE = 2, OG_SHAPE_UNION = 3 };
+/* Bodies of OG_SHAPE_UNION (the fluid is outside all of them):
+ * sphere: centre, radius; box: low and high corners (axis-aligned);
+ * cylinder: axis, centre in the two other axes ((axis+1)%3, (axis+2)%3), radius. */
+enum { OG_BODY_SPHERE = 0, OG_BODY_BOX = 1, OG_BODY_CYLINDER = 2 };
 
 typedef struct {
     int n[3];
@@ -56,6 +60,9 @@ typedef struct {
 typedef struct {
     int kind;
     double p[8];        /* sphere: cx,cy,cz,r ; plane: nx,ny,nz,d (fluid where n.x > d) */
+    int nbody;          /* OG_SHAPE_UNION: number of bodies (<= 16) */
+    int bkind[16];
+    double bq[16][6];
 } og_shape;
 
 typedef struct {

@@ -12,6 +12,11 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libebvisc.so")
+# Measurement variant: the same sources with the FP32 V-cycle reading FP32
+# face coefficients instead of BF16 ones (only solvers.cu differs).
+VARIANT_LIB = os.path.join(OUT, "libebvisc_fp32faces.so")
+VARIANT_SRC = "solvers.cu"
+VARIANT_DEFINE = "-DEBV_VCYCLE_FP32_FACES"
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
@@ -47,6 +52,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc] + ARCH + FLAGS + ["-c", s, "-o", o])
+    vobj = os.path.join(OUT, "solvers_fp32faces.o")
+    if force or _stale(vobj, [os.path.join(SRC, VARIANT_SRC)] + headers):
+        jobs.append([nvcc] + ARCH + FLAGS + [VARIANT_DEFINE, "-c", os.path.join(SRC, VARIANT_SRC), "-o", vobj])
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         res = list(ex.map(lambda cmd: subprocess.run(cmd, capture_output=True, text=True), jobs))
     for cmd, r in zip(jobs, res):
@@ -54,12 +62,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed: " + " ".join(cmd) + "\n" + r.stdout + r.stderr)
         if verbose and (r.stdout or r.stderr):
             print(r.stdout + r.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
-        r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("link failed\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
+    vobjs = [vobj if os.path.basename(o) == "solvers.o" else o for o in objs]
+    for lib, ob in ((LIB, objs), (VARIANT_LIB, vobjs)):
+        if force or jobs or _stale(lib, ob):
+            tmp = lib + f".{os.getpid()}.tmp"
+            r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + ob, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError("link failed\n" + r.stdout + r.stderr)
+            os.replace(tmp, lib)
     return LIB
 
 

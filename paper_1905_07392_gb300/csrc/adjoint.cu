@@ -737,7 +737,7 @@ __global__ void k_mac_correct_adj(GridD g, const double *__restrict__ ax, const 
             const double b = uFb[off[d] + f];
             const int pos = id[d] + hs;
             if (pos == 0 || pos == dimn(g, d)) {
-                if (g.bc[2 * d + hs] != EBV_OUTFLOW) continue;
+                if (g.bc[2 * d + hs] != EBV_OUTFLOW && !pin_face(g, d, fi[0], fi[1], fi[2])) continue;
                 // high side: uF -= (0 - phi) 2/h; low side: uF -= (phi - 0) 2/h
                 s += (hs ? 1.0 : -1.0) * 2.0 * g.ih * b;
             } else {

@@ -1,6 +1,7 @@
 // C-ABI entry points (include/ebvisc.h): context life cycle, geometry, the
 // stage operations of Algorithm 2 and the step of Algorithm 1.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -11,9 +12,34 @@
 
 #include "ebv_internal.cuh"
 
+#include <atomic>
+
+#include <nvtx3/nvToolsExt.h>
+
 using namespace ebv;
 
 struct ebv_ctx : public Ctx {};
+
+namespace ebv {
+// Allocation budget of ebv_set_alloc_limit: bytes still allowed, or -1 for
+// no limit (the default).
+static std::atomic<long long> g_alloc_budget{-1};
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if ((long long)bytes > b) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_alloc_budget.compare_exchange_weak(b, b - (long long)bytes)) break;
+    }
+    return cudaMalloc(p, bytes);
+}
+}  // namespace ebv
+
+extern "C" void ebv_set_alloc_limit(long long bytes) { g_alloc_budget.store(bytes < 0 ? -1 : bytes); }
 
 namespace {
 
@@ -32,10 +58,17 @@ ebv_status check_params(const ebv_params *p, std::string &why)
     return EBV_OK;
 }
 
+// Outcome of the allocations of one ebv_create: the first failure decides
+// whether the context reports EBV_ERR_OOM or EBV_ERR_CUDA.
+struct AllocState {
+    cudaError_t first = cudaSuccess;
+};
 template <class T>
-bool alloc(T **p, size_t n)
+bool alloc(T **p, size_t n, AllocState &a)
 {
-    return cudaMalloc(p, std::max<size_t>(n, 1) * sizeof(T)) == cudaSuccess;
+    cudaError_t e = dev_malloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess && a.first == cudaSuccess) a.first = e;
+    return e == cudaSuccess;
 }
 
 double sphere_fn(const double x[3], void *user)
@@ -141,36 +174,101 @@ ebv_status nodal_projection(Ctx *c, double *ut, double *p, ebv_step_stats *st, i
     return EBV_OK;
 }
 
+// The largest relative divergence the step's four projections leave: the
+// cell-centred solve's relative residual is ||D u^F|| / ||D u~^F||, the nodal
+// solve's is the relative residual of the (approximate) projection.
+double step_div_rel(const ebv_step_stats &s)
+{
+    return std::max(std::max(s.res[0], s.res[4]), std::max(s.res[5], s.res[9]));
+}
+
+// Phases of an eager step with statistics, timed by CUDA events on the
+// context's stream and marked as NVTX ranges: ms[0] time step, [1] predictor
+// derived quantities (Algorithm 2), [2] predictor viscous solves, [3]
+// predictor projection, [4..6] the same for the corrector, [7] drag and
+// yielded fraction.
+struct Phases {
+    Ctx *c;
+    bool on;
+    int cur = -1;
+    Phases(Ctx *c_, bool want) : c(c_), on(want)
+    {
+        if (on && !c->phase_ev_ok) {
+            bool ok = true;
+            for (cudaEvent_t &e : c->phase_ev) ok &= cudaEventCreate(&e) == cudaSuccess;
+            c->phase_ev_ok = ok;
+        }
+        on = on && c->phase_ev_ok;
+    }
+    void mark(int q, const char *name)
+    {
+        if (cur >= 0) nvtxRangePop();
+        nvtxRangePushA(name);
+        cur = q;
+        if (on) cudaEventRecord(c->phase_ev[q], c->stream);
+    }
+    void end()
+    {
+        if (cur >= 0) nvtxRangePop();
+        cur = -1;
+        if (on) cudaEventRecord(c->phase_ev[8], c->stream);
+    }
+    ~Phases()
+    {
+        if (cur >= 0) nvtxRangePop();
+    }
+    void read(float *ms)
+    {
+        if (!on) return;
+        for (int q = 0; q < 8; q++)
+            if (cudaEventElapsedTime(&ms[q], c->phase_ev[q], c->phase_ev[q + 1]) != cudaSuccess) ms[q] = 0.0f;
+    }
+};
+
 ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f, ebv_step_stats *st)
 {
     const GridD &g = c->g;
     const size_t N3 = ncell(g), NN = nnode(g);
     ebv_step_stats loc;
     memset(&loc, 0, sizeof loc);
+    Phases ph(c, st != nullptr);
+    ph.mark(0, "ebv: time step");
     TRY(launch_timestep(c, u, f, dt));
     // Predictor
+    ph.mark(1, "ebv: predictor derived quantities");
     TRY(derived(c, u, c->Cm, c->em, c->Vm, &loc.iters[0], &loc.res[0], 0));
     TRY(launch_psi(c, u, c->Cm, c->Vm, p, f, c->psi));
+    ph.mark(2, "ebv: predictor viscous solves");
     TRY(viscous_update(c, c->em, c->psi, c->ut, &loc, 1));
+    ph.mark(3, "ebv: predictor nodal projection");
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ps, p, NN * 8, cudaMemcpyDeviceToDevice, c->stream));
     TRY(nodal_projection(c, c->ut, c->ps, &loc, 4));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->us, c->ut, 3 * N3 * 8, cudaMemcpyDeviceToDevice, c->stream));
     // Corrector
+    ph.mark(4, "ebv: corrector derived quantities");
     TRY(derived(c, c->us, c->Cs, c->es, c->Vs, &loc.iters[5], &loc.res[5], 5));
     TRY(launch_average(c, c->Cm, c->Cs, (int)(3 * N3)));
     TRY(launch_average(c, c->Vm, c->Vs, (int)(3 * N3)));
     TRY(launch_average(c, c->em, c->es, (int)N3));
     TRY(launch_psi(c, u, c->Cm, c->Vm, c->ps, f, c->psi));
+    ph.mark(5, "ebv: corrector viscous solves");
     TRY(viscous_update(c, c->em, c->psi, c->ut, &loc, 6));
+    ph.mark(6, "ebv: corrector nodal projection");
     EBV_CUDA_TRY(c, cudaMemcpyAsync(p, c->ps, NN * 8, cudaMemcpyDeviceToDevice, c->stream));
     TRY(nodal_projection(c, c->ut, p, &loc, 9));
     EBV_CUDA_TRY(c, cudaMemcpyAsync(u, c->ut, 3 * N3 * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (st) {
+        ph.mark(7, "ebv: drag");
         EBV_CUDA_TRY(c, cudaMemcpyAsync(&c->scal_host[14], c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost,
                                         c->stream));
+        ph.end();
         TRY(launch_drag(c, u, p, &loc.drag, &loc.yield_frac));  // synchronises
         loc.dt = c->scal_host[14];
+        loc.div_rel = step_div_rel(loc);
+        ph.read(loc.ms);
         *st = loc;
+    } else {
+        ph.end();
     }
     return EBV_OK;
 }
@@ -259,6 +357,7 @@ ebv_status graph_stats(Ctx *c, const double *u, const double *p, ebv_step_stats 
         loc.res[q] = c->sstat_host[3 * q + 1];
     }
     loc.dt = c->scal_host[14];
+    loc.div_rel = step_div_rel(loc);
     TRY(launch_drag(c, u, p, &loc.drag, &loc.yield_frac));
     *st = loc;
     return EBV_OK;
@@ -417,35 +516,40 @@ ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stre
     for (int s = 0; s < 6; s++) g.bc[s] = grid->bc[s];
     const size_t N3 = ncell(g), NN = nnode(g), NF = nface(g, 0) + nface(g, 1) + nface(g, 2);
     const size_t V = std::max(N3, NN);
+    AllocState as;
     bool ok = true;
-    ok &= alloc(&c->alpha, N3) && alloc(&c->ax, nface(g, 0)) && alloc(&c->ay, nface(g, 1)) &&
-          alloc(&c->az, nface(g, 2)) && alloc(&c->area, N3) && alloc(&c->nrm, 3 * N3) &&
-          alloc(&c->bcen, 3 * N3) && alloc(&c->flag, N3);
-    ok &= alloc(&c->Cm, 3 * N3) && alloc(&c->Vm, 3 * N3) && alloc(&c->Cs, 3 * N3) && alloc(&c->Vs, 3 * N3);
-    ok &= alloc(&c->em, N3) && alloc(&c->es, N3) && alloc(&c->psi, 3 * N3) && alloc(&c->ut, 3 * N3) &&
-          alloc(&c->us, 3 * N3);
-    ok &= alloc(&c->ps, NN) && alloc(&c->uf, NF) && alloc(&c->phi, N3) && alloc(&c->G, 9 * N3) &&
-          alloc(&c->DC, 3 * N3) && alloc(&c->dD, 3 * N3) && alloc(&c->Dh, 3 * N3) && alloc(&c->wts, N3) &&
-          alloc(&c->srate, N3) && alloc(&c->rhs_c, std::max(N3, (size_t)1)) && alloc(&c->rhs_n, NN);
-    ok &= alloc(&c->nearm, N3) && alloc(&c->ff, 3 * NF);
-    ok &= alloc(&c->dt_dev, DT_NSCALAR) && alloc(&c->cfl_max, 2);
-    ok &= alloc(&c->u_host_dev, 3 * N3) && alloc(&c->p_host_dev, NN);
-    ok &= alloc(&c->kr, V) && alloc(&c->kz, V) && alloc(&c->kp, V) && alloc(&c->kq, V);
-    ok &= alloc(&c->kr32, V) && alloc(&c->kz32, V) && alloc(&c->kp32, V) && alloc(&c->kq32, V) &&
-          alloc(&c->ke32, V);
-    ok &= alloc(&c->part, (size_t)1 << 20) && alloc(&c->scal, 32);
+    ok &= alloc(&c->alpha, N3, as) && alloc(&c->ax, nface(g, 0), as) && alloc(&c->ay, nface(g, 1), as) &&
+          alloc(&c->az, nface(g, 2), as) && alloc(&c->area, N3, as) && alloc(&c->nrm, 3 * N3, as) &&
+          alloc(&c->bcen, 3 * N3, as) && alloc(&c->flag, N3, as);
+    ok &= alloc(&c->Cm, 3 * N3, as) && alloc(&c->Vm, 3 * N3, as) && alloc(&c->Cs, 3 * N3, as) &&
+          alloc(&c->Vs, 3 * N3, as);
+    ok &= alloc(&c->em, N3, as) && alloc(&c->es, N3, as) && alloc(&c->psi, 3 * N3, as) &&
+          alloc(&c->ut, 3 * N3, as) && alloc(&c->us, 3 * N3, as);
+    ok &= alloc(&c->ps, NN, as) && alloc(&c->uf, NF, as) && alloc(&c->phi, N3, as) && alloc(&c->G, 9 * N3, as) &&
+          alloc(&c->DC, 3 * N3, as) && alloc(&c->dD, 3 * N3, as) && alloc(&c->Dh, 3 * N3, as) &&
+          alloc(&c->wts, N3, as) && alloc(&c->srate, N3, as) && alloc(&c->rhs_c, std::max(N3, (size_t)1), as) &&
+          alloc(&c->rhs_n, NN, as);
+    ok &= alloc(&c->nearm, N3, as) && alloc(&c->ff, 3 * NF, as);
+    ok &= alloc(&c->dt_dev, DT_NSCALAR, as) && alloc(&c->cfl_max, 2, as);
+    ok &= alloc(&c->u_host_dev, 3 * N3, as) && alloc(&c->p_host_dev, NN, as);
+    ok &= alloc(&c->kr, V, as) && alloc(&c->kz, V, as) && alloc(&c->kp, V, as) && alloc(&c->kq, V, as);
+    ok &= alloc(&c->kr32, V, as) && alloc(&c->kz32, V, as) && alloc(&c->kp32, V, as) && alloc(&c->kq32, V, as) &&
+          alloc(&c->ke32, V, as);
+    ok &= alloc(&c->part, (size_t)1 << 20, as) && alloc(&c->scal, 32, as);
     ok &= cudaMallocHost(&c->scal_host, 32 * sizeof(double)) == cudaSuccess;
-    ok &= alloc(&c->ctl, C_LEN) && alloc(&c->sstat, kSstatLen);
+    ok &= alloc(&c->ctl, C_LEN, as) && alloc(&c->sstat, kSstatLen, as);
     ok &= cudaMallocHost(&c->ctl_host, C_LEN * sizeof(int)) == cudaSuccess;
     ok &= cudaMallocHost(&c->sstat_host, kSstatLen * sizeof(double)) == cudaSuccess;
     c->vec_len = V;
     if (!ok) {
         ebv_destroy(c);
-        return EBV_ERR_CUDA;
+        cudaGetLastError();  // an allocation failure leaves no error pending
+        return as.first == cudaErrorMemoryAllocation ? EBV_ERR_OOM : EBV_ERR_CUDA;
     }
-    if (setup_solvers(c) != EBV_OK) {
+    if (ebv_status st = setup_solvers(c); st != EBV_OK) {
         ebv_destroy(c);
-        return EBV_ERR_INVALID;
+        cudaGetLastError();
+        return st == EBV_ERR_OOM ? EBV_ERR_OOM : EBV_ERR_INVALID;
     }
     cudaMemsetAsync(c->scal, 0, 32 * sizeof(double), c->stream);
     cudaMemsetAsync(c->ctl, 0, C_LEN * sizeof(int), c->stream);
@@ -487,11 +591,134 @@ ebv_status ebv_build_geometry_sphere(ebv_ctx *c, const double cen[3], double r)
     return ebv_build_geometry(c, sphere_fn, s);
 }
 
+ebv_status ebv_build_geometry_bodies(ebv_ctx *c, int n, const ebv_body *bodies)
+{
+    if (!c || !bodies || n < 1) return EBV_ERR_INVALID;
+    drop_step_graph(c);
+    TRY(build_geometry_bodies(c, n, bodies));
+    TRY(setup_geometry_solvers(c));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return EBV_OK;
+}
+
+ebv_status ebv_build_geometry_spheres(ebv_ctx *c, int n, const double *c_r)
+{
+    if (!c || !c_r || n < 1 || n > 16) return EBV_ERR_INVALID;
+    ebv_body b[16];
+    for (int q = 0; q < n; q++) {
+        b[q].kind = EBV_BODY_SPHERE;
+        for (int e = 0; e < 4; e++) b[q].q[e] = c_r[4 * q + e];
+        b[q].q[4] = b[q].q[5] = 0.0;
+    }
+    return ebv_build_geometry_bodies(c, n, b);
+}
+
 ebv_status ebv_build_geometry_plane(ebv_ctx *c, const double nrm[3], double d)
 {
     if (!c || !nrm) return EBV_ERR_INVALID;
     double s[4] = {nrm[0], nrm[1], nrm[2], d};
     return ebv_build_geometry(c, plane_fn, s);
+}
+
+// ---- resumable state --------------------------------------------------------
+// File layout: the 8 bytes "EBVSTAT1", the ebv_grid and ebv_params structs,
+// then alpha, the x/y/z apertures, the EB area, normal and centroid (doubles),
+// the flags (bytes), u (3 x cells) and p (nodes) (doubles).
+namespace {
+const char kStateMagic[8] = {'E', 'B', 'V', 'S', 'T', 'A', 'T', '1'};
+
+struct StateFile {
+    FILE *f = nullptr;
+    ~StateFile()
+    {
+        if (f) fclose(f);
+    }
+};
+
+ebv_grid grid_of(const Ctx *c)
+{
+    ebv_grid g;
+    memset(&g, 0, sizeof g);
+    g.n[0] = c->g.nx; g.n[1] = c->g.ny; g.n[2] = c->g.nz;
+    g.h = c->g.h;
+    for (int d = 0; d < 3; d++) { g.lo[d] = c->g.lo[d]; g.u_in[d] = c->g.u_in[d]; }
+    for (int q = 0; q < 6; q++) g.bc[q] = c->g.bc[q];
+    return g;
+}
+}  // namespace
+
+ebv_status ebv_save_state(ebv_ctx *c, const double *u, const double *p, const char *path)
+{
+    if (!c || !u || !p || !path) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    const GridD &g = c->g;
+    const size_t N3 = ncell(g), NN = nnode(g);
+    HostGeom H;
+    H.alpha.resize(N3); H.area.resize(N3); H.nrm.resize(3 * N3); H.bcen.resize(3 * N3); H.flag.resize(N3);
+    for (int d = 0; d < 3; d++) H.a[d].resize(nface(g, d));
+    std::vector<double> uh(3 * N3), ph(NN);
+    const double *src[7] = {c->alpha, c->ax, c->ay, c->az, c->area, c->nrm, c->bcen};
+    std::vector<double> *dst[7] = {&H.alpha, &H.a[0], &H.a[1], &H.a[2], &H.area, &H.nrm, &H.bcen};
+    for (int q = 0; q < 7; q++)
+        EBV_CUDA_TRY(c, cudaMemcpyAsync(dst[q]->data(), src[q], dst[q]->size() * 8, cudaMemcpyDeviceToHost,
+                                        c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(H.flag.data(), c->flag, N3, cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(uh.data(), u, 3 * N3 * 8, cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(ph.data(), p, NN * 8, cudaMemcpyDeviceToHost, c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    StateFile F;
+    F.f = fopen(path, "wb");
+    if (!F.f) return c->fail(EBV_ERR_INVALID, std::string("cannot write ") + path);
+    ebv_grid gr = grid_of(c);
+    bool ok = fwrite(kStateMagic, 1, 8, F.f) == 8 && fwrite(&gr, sizeof gr, 1, F.f) == 1 &&
+              fwrite(&c->prm, sizeof c->prm, 1, F.f) == 1;
+    for (int q = 0; q < 7 && ok; q++) ok = fwrite(dst[q]->data(), 8, dst[q]->size(), F.f) == dst[q]->size();
+    ok = ok && fwrite(H.flag.data(), 1, N3, F.f) == N3 && fwrite(uh.data(), 8, 3 * N3, F.f) == 3 * N3 &&
+         fwrite(ph.data(), 8, NN, F.f) == NN;
+    ok = (fclose(F.f) == 0) && ok;
+    F.f = nullptr;
+    if (!ok) return c->fail(EBV_ERR_INVALID, std::string("write failed: ") + path);
+    return EBV_OK;
+}
+
+ebv_status ebv_load_state(ebv_ctx *c, double *u, double *p, const char *path)
+{
+    if (!c || !u || !p || !path) return EBV_ERR_INVALID;
+    StateFile F;
+    F.f = fopen(path, "rb");
+    if (!F.f) return c->fail(EBV_ERR_INVALID, std::string("cannot read ") + path);
+    char magic[8];
+    ebv_grid gr, mine = grid_of(c);
+    ebv_params prm;
+    if (fread(magic, 1, 8, F.f) != 8 || memcmp(magic, kStateMagic, 8) != 0)
+        return c->fail(EBV_ERR_INVALID, "not a state file of this library");
+    if (fread(&gr, sizeof gr, 1, F.f) != 1 || fread(&prm, sizeof prm, 1, F.f) != 1)
+        return c->fail(EBV_ERR_INVALID, "truncated state file");
+    if (memcmp(&gr, &mine, sizeof gr) != 0) return c->fail(EBV_ERR_INVALID, "the state was saved on another grid");
+    std::string why;
+    if (check_params(&prm, why) != EBV_OK) return c->fail(EBV_ERR_INVALID, "state file parameters: " + why);
+    const GridD &g = c->g;
+    const size_t N3 = ncell(g), NN = nnode(g);
+    HostGeom H;
+    H.alpha.resize(N3); H.area.resize(N3); H.nrm.resize(3 * N3); H.bcen.resize(3 * N3); H.flag.resize(N3);
+    for (int d = 0; d < 3; d++) H.a[d].resize(nface(g, d));
+    std::vector<double> uh(3 * N3), ph(NN);
+    std::vector<double> *dst[7] = {&H.alpha, &H.a[0], &H.a[1], &H.a[2], &H.area, &H.nrm, &H.bcen};
+    bool ok = true;
+    for (int q = 0; q < 7 && ok; q++) ok = fread(dst[q]->data(), 8, dst[q]->size(), F.f) == dst[q]->size();
+    ok = ok && fread(H.flag.data(), 1, N3, F.f) == N3 && fread(uh.data(), 8, 3 * N3, F.f) == 3 * N3 &&
+         fread(ph.data(), 8, NN, F.f) == NN;
+    if (!ok) return c->fail(EBV_ERR_INVALID, "truncated state file");
+    for (size_t q = 0; q < N3; q++)
+        if (H.flag[q] == 2) H.cut.push_back((int)q);
+    drop_step_graph(c);
+    c->prm = prm;
+    TRY(install_geometry(c, H));
+    TRY(setup_geometry_solvers(c));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(u, uh.data(), 3 * N3 * 8, cudaMemcpyHostToDevice, c->stream));
+    EBV_CUDA_TRY(c, cudaMemcpyAsync(p, ph.data(), NN * 8, cudaMemcpyHostToDevice, c->stream));
+    EBV_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return EBV_OK;
 }
 
 ebv_status ebv_get_geometry(ebv_ctx *c, double *alpha, double *ax, double *ay, double *az, double *area,
@@ -522,6 +749,15 @@ ebv_status ebv_update_viscosity(ebv_ctx *c, const double *u, double *eta, double
     if (!c || !u || !eta) return EBV_ERR_INVALID;
     TRY(need_geom(c));
     TRY(launch_strain_eta(c, u, eta, srate, nullptr));
+    EBV_CUDA_TRY(c, cudaGetLastError());
+    return EBV_OK;
+}
+
+ebv_status ebv_flow_diagnostics(ebv_ctx *c, const double *u, double *lambda, double *stress_dev)
+{
+    if (!c || !u || !lambda || !stress_dev) return EBV_ERR_INVALID;
+    TRY(need_geom(c));
+    TRY(launch_flow_diag(c, u, lambda, stress_dev));
     EBV_CUDA_TRY(c, cudaGetLastError());
     return EBV_OK;
 }
@@ -639,6 +875,8 @@ void ebv_destroy(ebv_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->phase_ev_ok)
+        for (cudaEvent_t e : c->phase_ev) cudaEventDestroy(e);
     void *ptrs[] = {c->alpha, c->ax, c->ay, c->az, c->area, c->nrm, c->bcen, c->flag, c->cut, c->Cm, c->Vm,
                     c->Cs, c->Vs, c->em, c->es, c->psi, c->ut, c->us, c->ps, c->uf, c->phi, c->G, c->DC,
                     c->dD, c->Dh, c->wts, c->dudn, c->srate, c->rhs_c, c->rhs_n, c->u_host_dev, c->p_host_dev,
@@ -737,7 +975,7 @@ ebv_status adj_buffers(Ctx *c, AdjBufs &B)
         if (c->adj) cudaFree(c->adj);
         c->adj = nullptr;
         c->adj_len = 0;
-        EBV_CUDA_TRY(c, cudaMalloc(&c->adj, need * sizeof(double)));
+        EBV_CUDA_TRY(c, dev_malloc((void **)&c->adj, need * sizeof(double)));
         c->adj_len = need;
     }
     layout(c->adj);

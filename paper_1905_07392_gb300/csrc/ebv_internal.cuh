@@ -40,6 +40,30 @@ struct GridD {
     double u_in[3];
 };
 
+// A box with no outflow side (velocity prescribed or walls all round: the
+// paper's cylinder and sphere runs with U on every boundary, the Taylor-Green
+// vortex between slip walls) leaves both pressure problems pure Neumann,
+// fixed only up to a constant.  One Dirichlet point fixes them: the x- face
+// of cell (0,0,0) acts as an outflow face (phi = 0 beyond it) in the
+// cell-centred projection, and node (0,0,0) is a Dirichlet node (p = 0) in
+// the nodal one.  With a consistent right-hand side (zero net boundary flux)
+// the solution is the pure-Neumann one that vanishes at that point.  Every
+// level of a hierarchy carries the box sides, so the rule holds on each.
+__host__ __device__ inline bool no_outflow(const GridD &g)
+{
+    for (int s = 0; s < 6; s++)
+        if (g.bc[s] == EBV_OUTFLOW) return false;
+    return true;
+}
+__host__ __device__ inline bool pin_face(const GridD &g, int d, int i, int j, int k)
+{
+    return d == 0 && i == 0 && j == 0 && k == 0 && no_outflow(g);
+}
+__host__ __device__ inline bool pin_node(const GridD &g, int i, int j, int k)
+{
+    return i == 0 && j == 0 && k == 0 && no_outflow(g);
+}
+
 struct GeomD {
     const double *alpha, *ax, *ay, *az, *area, *nrm, *bcen;
     const uint8_t *flag;
@@ -291,6 +315,10 @@ struct Ctx {
     const void *gkey_u = nullptr, *gkey_p = nullptr, *gkey_f = nullptr;
     double gkey_dt = 0.0;
 
+    // per-phase CUDA events of an eager step with statistics (created on first use)
+    cudaEvent_t phase_ev[9] = {};
+    bool phase_ev_ok = false;
+
     ebv_status fail(ebv_status s, const std::string &m)
     {
         err = m;
@@ -318,8 +346,15 @@ void prof_end_launch(struct Ctx *c);
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \
         if (e_ != cudaSuccess)                                                           \
-            return (ctx)->fail(EBV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return (ctx)->fail(e_ == cudaErrorMemoryAllocation ? EBV_ERR_OOM : EBV_ERR_CUDA, \
+                               std::string(#call) + ": " + cudaGetErrorString(e_));      \
     } while (0)
+
+// Every device allocation of the library goes through dev_malloc, which
+// enforces the optional allocation budget of ebv_set_alloc_limit (a host-side
+// fault-injection hook: past the budget it fails as cudaMalloc does when the
+// device is out of memory, without touching the device).
+cudaError_t dev_malloc(void **p, size_t bytes);
 
 inline GeomD geomd(const Ctx *c)
 {
@@ -340,8 +375,19 @@ inline ParamsD paramsd(const ebv_params &p)
 
 // geometry.cu
 ebv_status build_geometry_host(Ctx *c, ebv_implicit_fn fn, void *user);
+ebv_status build_geometry_bodies(Ctx *c, int n, const ebv_body *bodies);
 // fields.cu
+// Geometry on the host: volume fractions, face apertures (three face
+// arrays), EB areas, normals and centroids (3 x cells each), flags and the
+// ascending list of cut cells.
+struct HostGeom {
+    std::vector<double> alpha, a[3], area, nrm, bcen;
+    std::vector<uint8_t> flag;
+    std::vector<int> cut;
+};
+ebv_status install_geometry(Ctx *c, HostGeom &H);
 ebv_status launch_strain_eta(Ctx *c, const double *u, double *eta, double *srate, double *G);
+ebv_status launch_flow_diag(Ctx *c, const double *u, double *lam, double *sdev);
 ebv_status launch_face_states(Ctx *c, const double *u, double *uf);
 ebv_status launch_mac_rhs(Ctx *c, const double *uf, double *b);
 ebv_status launch_mac_correct(Ctx *c, double *uf, const double *phi);

@@ -129,6 +129,38 @@ __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__re
             for (int q = 0; q < 3; q++) G[(3 * d + q) * N3 + c] = Gm[d][q];
 }
 
+// ---- flow diagnostics (Sec. "Cylinder moving through Bingham fluid") ------
+// Lambda of Eq. ryovar, (||g||^2 - |w|^2) / (||g||^2 + |w|^2) with w = curl u
+// (0 where both vanish), and the yield-stress deviation eta ||g|| / tau0 - 1
+// (0 when tau0 = 0), from the same robust gradients as k_strain_eta.
+__global__ void __launch_bounds__(256) k_flow_diag(GridD g, const uint8_t *__restrict__ flag,
+                                                   const double *__restrict__ u, ParamsD p,
+                                                   double *__restrict__ lam, double *__restrict__ sdev)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    if (flag[c] == 0) {
+        lam[c] = 0.0;
+        sdev[c] = 0.0;
+        return;
+    }
+    double Gm[3][3];
+    const double ih = g.ih;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) Gm[d][q] = d_robust(g, flag, u + q * N3, i, j, k, d, ih);
+    const double xy = Gm[0][1] + Gm[1][0], xz = Gm[0][2] + Gm[2][0], yz = Gm[1][2] + Gm[2][1];
+    const double s = 2.0 * (Gm[0][0] * Gm[0][0] + Gm[1][1] * Gm[1][1] + Gm[2][2] * Gm[2][2]) +
+                     (xy * xy + xz * xz + yz * yz);   // ||g||^2
+    const double wx = Gm[1][2] - Gm[2][1], wy = Gm[2][0] - Gm[0][2], wz = Gm[0][1] - Gm[1][0];
+    const double w2 = wx * wx + wy * wy + wz * wz;
+    lam[c] = (s + w2) > 0.0 ? (s - w2) / (s + w2) : 0.0;
+    const double rsr = s > 0.0 ? rsqrt(s) : 0.0;
+    const double sr = s * rsr;
+    sdev[c] = p.tau0 > 0.0 ? eta_of(p, sr, rsr) * sr / p.tau0 - 1.0 : 0.0;
+}
+
 // ---- normal face velocities (slopes, extrapolation, upwinding) ------------
 __global__ void k_face_states(GridD g, int d, const double *__restrict__ S,
                               const double *__restrict__ ap, const double *__restrict__ u,
@@ -197,7 +229,7 @@ __global__ void k_mac_correct(GridD g, int d, const double *__restrict__ ap,
     int id[3] = {i, j, k};
     if (id[d] == 0 || id[d] == dimn(g, d)) {
         int hs = id[d] != 0;
-        if (g.bc[2 * d + hs] != EBV_OUTFLOW) return;
+        if (g.bc[2 * d + hs] != EBV_OUTFLOW && !pin_face(g, d, i, j, k)) return;
         int cc[3] = {i, j, k};
         cc[d] -= hs;
         double pc = phi[cidx(g, cc[0], cc[1], cc[2])];
@@ -419,6 +451,10 @@ __global__ void k_wall_dudn(GridD g, GeomD geo, const double *__restrict__ u,
     if (t >= geo.ncut) return;
     const int N3 = geo.ncell;
     const int c = geo.cut[t];
+    if (c < 0 || c >= N3) {  // a list entry outside the grid contributes nothing
+        for (int q = 0; q < 3; q++) dudn[q * geo.ncut + t] = 0.0;
+        return;
+    }
     int ci[3] = {c % g.nx, (c / g.nx) % g.ny, c / (g.nx * g.ny)};
     double n[3], b[3];
     for (int e = 0; e < 3; e++) { n[e] = geo.nrm[e * N3 + c]; b[e] = geo.bcen[e * N3 + c]; }
@@ -597,6 +633,7 @@ __global__ void k_add_gradp(GridD g, const uint8_t *__restrict__ flag, double *_
 
 __device__ inline bool node_dirichlet(const GridD &g, int i, int j, int k)
 {
+    if (pin_node(g, i, j, k)) return true;
     int id[3] = {i, j, k};
     for (int d = 0; d < 3; d++) {
         if (id[d] == 0 && g.bc[2 * d] == EBV_OUTFLOW) return true;
@@ -718,6 +755,10 @@ __global__ void k_drag_terms(GridD g, GeomD geo, const double *__restrict__ eta,
     if (t >= geo.ncut) return;
     const int N3 = geo.ncell;
     const int c = geo.cut[t];
+    if (c < 0 || c >= N3) {  // a list entry outside the grid contributes nothing
+        term[t] = 0.0;
+        return;
+    }
     const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
     double n[3], b[3], gq[3];
     for (int e = 0; e < 3; e++) {
@@ -791,6 +832,13 @@ ebv_status launch_strain_eta(Ctx *c, const double *u, double *eta, double *srate
     else
         EBV_LAUNCH_P(c, "strain_rate_viscosity", nb, k_strain_eta<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g,
                      c->flag, u, paramsd(c->prm), eta, srate, nullptr);
+    return EBV_OK;
+}
+
+ebv_status launch_flow_diag(Ctx *c, const double *u, double *lam, double *sdev)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_flow_diag, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, paramsd(c->prm), lam, sdev);
     return EBV_OK;
 }
 
@@ -988,6 +1036,7 @@ ebv_status launch_drag(Ctx *c, const double *u, const double *p, double *fz, dou
 // serves them: it runs the same kernels as ebv_drag, but its working storage
 // is the fixed array below, which the library places in the memory of every
 // GPU that loads it and which stays there until the process exits.
+#include <cmath>
 #include <mutex>
 
 namespace ebv {
@@ -1038,6 +1087,10 @@ extern "C" ebv_status ebv_drag_noalloc(const ebv_grid *grid, const ebv_params *p
     if (ncut < 0 || (ncut > 0 && !cut)) return EBV_ERR_INVALID;
     for (int d = 0; d < 3; d++)
         if (grid->n[d] < 1) return EBV_ERR_INVALID;
+    if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return EBV_ERR_INVALID;
+    // An error left by earlier, unrelated work stays pending for its owner;
+    // this call neither reports it as its own nor clears it.
+    if (cudaPeekAtLastError() != cudaSuccess) return EBV_ERR_CUDA_PENDING;
     const long long n3 = (long long)grid->n[0] * grid->n[1] * grid->n[2];
     if (n3 > kNoAllocCells || ncut > kNoAllocCut) return EBV_ERR_TOO_LARGE;
 

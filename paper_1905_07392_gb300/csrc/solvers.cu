@@ -130,9 +130,18 @@ struct CcOp {
 };
 // The V-cycle's operator: in FP32 its faces are stored in BF16 (half the
 // bytes of the face arrays every colour pass reads whole); the Krylov
-// operator it preconditions keeps FP32 faces (CcOp<T>).
+// operator it preconditions keeps FP32 faces (CcOp<T>).  Built with
+// EBV_VCYCLE_FP32_FACES (a measurement variant of the library, not the
+// default) the V-cycle reads the FP32 faces instead, with the diagonal
+// formed from them unrounded; everything else is the same code.
 template <class T> struct VFace { using type = T; };
+#ifdef EBV_VCYCLE_FP32_FACES
+template <> struct VFace<float> { using type = float; };
+constexpr bool kVcycleBf16 = false;
+#else
 template <> struct VFace<float> { using type = __nv_bfloat16; };
+constexpr bool kVcycleBf16 = true;
+#endif
 template <class T> using VOp = CcOp<T, typename VFace<T>::type>;
 
 // Array layout of the cell-centred multigrid, by precision.  FP64 arrays are
@@ -527,7 +536,7 @@ __global__ void k_mac_coeffs(GridD g, const uint8_t *__restrict__ flag, const do
         int f = fidx(g, d, i, j, k);
         if (id[d] == 0 || id[d] == dimn(g, d)) {
             int side = 2 * d + (id[d] != 0);
-            B[d][f] = g.bc[side] == EBV_OUTFLOW ? 2.0 * A[d][f] / h2 : 0.0;
+            B[d][f] = (g.bc[side] == EBV_OUTFLOW || pin_face(g, d, i, j, k)) ? 2.0 * A[d][f] / h2 : 0.0;
         } else {
             B[d][f] = A[d][f] / h2;
         }
@@ -1082,7 +1091,7 @@ __global__ void k_nd_active(GridD g, const double *__restrict__ alpha, uint8_t *
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     if (i > g.nx || j > g.ny || k > g.nz) return;
     int id[3] = {i, j, k};
-    bool dir = false;
+    bool dir = pin_node(g, i, j, k);
     for (int d = 0; d < 3; d++) {
         if (id[d] == 0 && g.bc[2 * d] == EBV_OUTFLOW) dir = true;
         if (id[d] == dimn(g, d) && g.bc[2 * d + 1] == EBV_OUTFLOW) dir = true;
@@ -1702,7 +1711,14 @@ VOp<T> vop(const CcLevel &L)
     if constexpr (sizeof(T) == 8) {
         A.diag = (const T *)L.diag_d; A.bx = (const T *)L.bf_d[0]; A.by = (const T *)L.bf_d[1]; A.bz = (const T *)L.bf_d[2];
     } else {
-        A.diag = (const T *)L.diag_f; A.bx = L.bf_h[0]; A.by = L.bf_h[1]; A.bz = L.bf_h[2];
+        A.diag = (const T *)L.diag_f;
+        if constexpr (kVcycleBf16) {
+            A.bx = L.bf_h[0]; A.by = L.bf_h[1]; A.bz = L.bf_h[2];
+        } else {
+            A.bx = (const typename VFace<T>::type *)L.bf_f[0];
+            A.by = (const typename VFace<T>::type *)L.bf_f[1];
+            A.bz = (const typename VFace<T>::type *)L.bf_f[2];
+        }
         A.dinv = (const T *)L.dinv_f;
     }
     return A;
@@ -1720,7 +1736,7 @@ void cc_make_diag(Ctx *c, CcHier &H, int l)
         EBV_LAUNCH(c, k_cc_make_diag<double>, cgrid(L.g), block3(), 0, L.g, L.extra_d, L.bf_d[0], L.bf_d[1],
                    L.bf_d[2], H.nvar, masks, H.vdiag_d[0][l], H.vdiag_d[1][l], H.vdiag_d[2][l]);
     else
-        EBV_LAUNCH(c, (k_cc_make_diag<float, true>), cgrid(L.g), block3(), 0, L.g, L.extra_f, L.bf_f[0], L.bf_f[1],
+        EBV_LAUNCH(c, (k_cc_make_diag<float, kVcycleBf16>), cgrid(L.g), block3(), 0, L.g, L.extra_f, L.bf_f[0], L.bf_f[1],
                    L.bf_f[2], H.nvar, masks, H.vdiag_f[0][l], H.vdiag_f[1][l], H.vdiag_f[2][l], H.vdinv_f[0][l],
                    H.vdinv_f[1][l], H.vdinv_f[2][l]);
 }
@@ -1728,6 +1744,7 @@ void cc_make_diag(Ctx *c, CcHier &H, int l)
 // The V-cycle's BF16 copy of the FP32 faces of level L.
 inline void cc_faces_bf16(Ctx *c, CcLevel &L)
 {
+    if constexpr (!kVcycleBf16) return;
     for (int d = 0; d < 3; d++) {
         const int n = nface(L.g, d);
         EBV_LAUNCH(c, k_to_bf16, dim3(std::min(kReduceBlocks, (n + 255) / 256)), dim3(256), 0, L.bf_f[d], L.bf_h[d], n);
@@ -2384,7 +2401,7 @@ template <class T>
 T *dalloc(size_t n, cudaError_t &e)
 {
     T *p = nullptr;
-    cudaError_t r = cudaMalloc(&p, n * sizeof(T));
+    cudaError_t r = dev_malloc((void **)&p, n * sizeof(T));
     if (r != cudaSuccess) e = r;
     return p;
 }
@@ -2482,7 +2499,9 @@ ebv_status setup_solvers(Ctx *c)
         c->ld[l] = dalloc<double>(m, e);
         c->lt[l] = dalloc<double>(m, e);
     }
-    if (e != cudaSuccess) return c->fail(EBV_ERR_CUDA, std::string("allocation: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        return c->fail(e == cudaErrorMemoryAllocation ? EBV_ERR_OOM : EBV_ERR_CUDA,
+                       std::string("allocation: ") + cudaGetErrorString(e));
     return EBV_OK;
 }
 
@@ -2539,7 +2558,7 @@ ebv_status setup_geometry_solvers(Ctx *c)
         Lv.irr = nullptr;
         Lv.nirr = (int)irr.size();
         if (Lv.nirr) {
-            EBV_CUDA_TRY(c, cudaMalloc(&Lv.irr, irr.size() * sizeof(int)));
+            EBV_CUDA_TRY(c, dev_malloc((void **)&Lv.irr, irr.size() * sizeof(int)));
             EBV_CUDA_TRY(c, cudaMemcpy(Lv.irr, irr.data(), irr.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
     }

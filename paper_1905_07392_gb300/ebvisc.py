@@ -22,7 +22,7 @@ INFLOW, OUTFLOW, SLIP, NOSLIP = 0, 1, 2, 3
 NEWTONIAN, BINGHAM, HERSCHEL_BULKLEY, POWER_LAW, SOUZA_MENDES_DUTRA = 0, 1, 2, 3, 4
 FP64, FP32_REFINE = 0, 1
 STATUS = {0: "EBV_OK", -1: "EBV_ERR_INVALID", -2: "EBV_ERR_CUDA", -3: "EBV_ERR_NOT_CONVERGED",
-          -5: "EBV_ERR_NAN", -6: "EBV_ERR_GEOMETRY"}
+          -5: "EBV_ERR_NAN", -6: "EBV_ERR_GEOMETRY", -8: "EBV_ERR_OOM"}
 
 
 class EbvError(RuntimeError):
@@ -44,24 +44,42 @@ class _Params(C.Structure):
                 ("precision", C.c_int), ("advect", C.c_int)]
 
 
+class _Body(C.Structure):
+    _fields_ = [("kind", C.c_int), ("q", C.c_double * 6)]
+
+
+BODY_SPHERE, BODY_BOX, BODY_CYLINDER = 0, 1, 2
+
+
 class _Stats(C.Structure):
     _fields_ = [("dt", C.c_double), ("drag", C.c_double), ("yield_frac", C.c_double),
-                ("iters", C.c_int * 10), ("res", C.c_double * 10)]
+                ("iters", C.c_int * 10), ("res", C.c_double * 10), ("div_rel", C.c_double),
+                ("ms", C.c_float * 8)]
+
+
+PHASES = ("timestep", "predictor_derived", "predictor_viscous", "predictor_projection",
+          "corrector_derived", "corrector_viscous", "corrector_projection", "drag")
 
 
 IMPLICIT_FN = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_void_p)
 
 EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geometry_sphere",
-           "ebv_build_geometry_plane", "ebv_get_geometry", "ebv_update_viscosity", "ebv_derived",
+           "ebv_build_geometry_plane", "ebv_get_geometry", "ebv_update_viscosity", "ebv_flow_diagnostics",
+           "ebv_derived",
            "ebv_face_states", "ebv_solve_mac", "ebv_solve_viscous", "ebv_solve_projection",
            "ebv_timestep", "ebv_advance", "ebv_advance_graph", "ebv_advance_host", "ebv_drag", "ebv_launch_count",
            "ebv_profile_begin", "ebv_profile_end", "ebv_profile_entry", "ebv_last_error",
            "ebv_destroy", "ebv_drag_noalloc", "ebv_batch_create", "ebv_batch_build_spheres",
            "ebv_batch_instance", "ebv_batch_advance", "ebv_batch_launch_count",
            "ebv_batch_last_error", "ebv_batch_destroy", "ebv_adjoint_step", "ebv_drag_adjoint",
-           "ebv_drag_gradient_workspace", "ebv_drag_gradient"]
+           "ebv_drag_gradient_workspace", "ebv_drag_gradient", "ebv_set_alloc_limit",
+           "ebv_save_state", "ebv_load_state", "ebv_build_geometry_spheres",
+           "ebv_build_geometry_bodies"]
 
 _lib = None
+
+
+_variants = {}
 
 
 def load(path: str = LIB_PATH):
@@ -69,6 +87,19 @@ def load(path: str = LIB_PATH):
     global _lib
     if _lib is not None:
         return _lib
+    _lib = _open(path)
+    return _lib
+
+
+def load_variant(path: str):
+    """A build variant of the library (same C-ABI, e.g. the FP32-face V-cycle
+    of build_lib.VARIANT_LIB) for Solver(..., lib=...); loaded once per path."""
+    if path not in _variants:
+        _variants[path] = _open(path)
+    return _variants[path]
+
+
+def _open(path):
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
     lib = C.CDLL(path)
@@ -81,6 +112,7 @@ def load(path: str = LIB_PATH):
         "ebv_build_geometry_plane": ([vp, dp, C.c_double], C.c_int),
         "ebv_get_geometry": ([vp] + [vp] * 8, C.c_int),
         "ebv_update_viscosity": ([vp, vp, vp, vp], C.c_int),
+        "ebv_flow_diagnostics": ([vp, vp, vp, vp], C.c_int),
         "ebv_derived": ([vp, vp, vp, vp, vp, ip, dp], C.c_int),
         "ebv_face_states": ([vp, vp, vp], C.c_int),
         "ebv_solve_mac": ([vp, vp, vp, ip, dp], C.c_int),
@@ -113,12 +145,16 @@ def load(path: str = LIB_PATH):
         "ebv_drag_adjoint": ([vp, vp, vp, C.c_double, vp, vp, dp], C.c_int),
         "ebv_drag_gradient_workspace": ([vp, C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
         "ebv_drag_gradient": ([vp, vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, dp, dp, vp], C.c_int),
+        "ebv_set_alloc_limit": ([C.c_longlong], None),
+        "ebv_save_state": ([vp, vp, vp, C.c_char_p], C.c_int),
+        "ebv_build_geometry_spheres": ([vp, C.c_int, dp], C.c_int),
+        "ebv_build_geometry_bodies": ([vp, C.c_int, C.POINTER(_Body)], C.c_int),
+        "ebv_load_state": ([vp, vp, vp, C.c_char_p], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
-    _lib = lib
     return lib
 
 
@@ -140,18 +176,44 @@ def _check_f64(t, n, name):
 
 
 STATUS[-7] = "EBV_ERR_TOO_LARGE"
+STATUS[-9] = "EBV_ERR_CUDA_PENDING"
+
+
+def _check_noalloc_args(grid, geometry, cut, u, p, out):
+    """Sizes and types of ebv_drag_noalloc's buffers.  The C entry sees only
+    pointers, so this is the one place where a short or mistyped buffer (which
+    the kernels would read or write past its end) is refused."""
+    import torch
+    n = [int(v) for v in grid.n]
+    n3 = n[0] * n[1] * n[2]
+    nn = (n[0] + 1) * (n[1] + 1) * (n[2] + 1)
+    _check_f64(out, 2, "out")
+    _check_f64(u, 3 * n3, "u")
+    _check_f64(p, nn, "p")
+    for name, size in (("alpha", n3), ("area", n3), ("nrm", 3 * n3), ("bcen", 3 * n3)):
+        _check_f64(geometry[name], size, name)
+    fl = geometry["flag"]
+    if fl.dtype != torch.uint8 or fl.numel() != n3:
+        raise ValueError(f"flag: expected {n3} uint8 values, got {fl.numel()} {fl.dtype}")
+    if cut.dtype != torch.int32:
+        raise ValueError("cut must be int32")
+    if cut.numel() > n3:
+        raise ValueError(f"cut: {cut.numel()} entries for {n3} cells")
+    if cut.numel() and (int(cut.min()) < 0 or int(cut.max()) >= n3):
+        raise ValueError(f"cut: entries must lie in [0, {n3})")
 
 
 def drag_noalloc(solver, geometry, cut, u, p, out, stream=None):
     """Drag and unyielded fraction through ebv_drag_noalloc, which allocates
     no GPU memory (for callers that cannot).  `solver` supplies only the grid
-    and parameters (no context is used); `geometry` is Solver.geometry();
-    `cut` an int32 CUDA tensor of the cells with flag 2 in ascending order;
-    `out` a float64 CUDA tensor of 2 values (F_z, unyielded fraction)."""
+    and parameters (its ``_grid`` and ``_params_c()``; no context is used);
+    `geometry` is Solver.geometry(); `cut` an int32 CUDA tensor of the cells
+    with flag 2 in ascending order; `out` a float64 CUDA tensor of 2 values
+    (F_z, unyielded fraction).  Every buffer's size and type is checked here
+    before the call."""
     import torch
+    _check_noalloc_args(solver._grid, geometry, cut, u, p, out)
     lib = load()
-    if cut.dtype != torch.int32:
-        raise ValueError("cut must be int32")
     st = lib.ebv_drag_noalloc(C.byref(solver._grid), C.byref(solver._params_c()),
                               _ptr(geometry["alpha"]), _ptr(geometry["area"]),
                               _ptr(geometry["nrm"]), _ptr(geometry["bcen"]),
@@ -164,7 +226,8 @@ def drag_noalloc(solver, geometry, cut, u, p, out, stream=None):
 
 def _stats_dict(st):
     return {"dt": st.dt, "drag": st.drag, "yield_frac": st.yield_frac,
-            "iters": list(st.iters), "res": list(st.res)}
+            "iters": list(st.iters), "res": list(st.res), "div_rel": st.div_rel,
+            "ms": dict(zip(PHASES, [float(v) for v in st.ms]))}
 
 
 class Solver:
@@ -173,9 +236,9 @@ class Solver:
     def __init__(self, n, h, lo=(0.0, 0.0, 0.0), bc=W.CHANNEL_BC, u_in=(0.0, 0.0, 1.0), *,
                  rho=1.0, mu=1.0, tau0=0.0, m=1e3, n_flow=1.0, eta0=1e3, model=BINGHAM,
                  cfl=0.5, bi_cfl=0.0, tol=1e-8, max_iters=1000, delta_min=0.25,
-                 precision=FP64, advect=1, stream=None):
+                 precision=FP64, advect=1, stream=None, lib=None):
         import torch
-        self._lib = load()
+        self._lib = lib if lib is not None else load()
         self.n = tuple(int(v) for v in n)
         self.h = float(h)
         g = _Grid()
@@ -258,6 +321,22 @@ class Solver:
         nv = (C.c_double * 3)(*normal)
         self._ok(self._lib.ebv_build_geometry_plane(self._ctx, nv, C.c_double(d)))
 
+    def build_spheres(self, c_r):
+        """Union of spheres, rows (cx, cy, cz, r), built on the device."""
+        a = np.ascontiguousarray(c_r, dtype=np.float64).reshape(-1, 4)
+        self._ok(self._lib.ebv_build_geometry_spheres(self._ctx, a.shape[0],
+                                                      a.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def build_bodies(self, bodies):
+        """Union of bodies [(kind, (q0, ...)), ...] (BODY_SPHERE / BODY_BOX /
+        BODY_CYLINDER, parameters as in ebvisc.h), built on the device."""
+        arr = (_Body * len(bodies))()
+        for t, (kind, q) in enumerate(bodies):
+            arr[t].kind = int(kind)
+            vals = [float(v) for v in q] + [0.0] * (6 - len(q))
+            arr[t].q[:] = vals
+        self._ok(self._lib.ebv_build_geometry_bodies(self._ctx, len(bodies), arr))
+
     def build_geometry(self, fn):
         """fn(x: tuple of 3 floats) -> float, > 0 in the fluid (called on the host)."""
         cb = IMPLICIT_FN(lambda x, user: float(fn((x[0], x[1], x[2]))))
@@ -282,6 +361,33 @@ class Solver:
         return out
 
     # stage operations
+    def save_state(self, u, p, path):
+        """Grid, parameters, geometry, u and p to a file (ebv_save_state)."""
+        _check_f64(u, 3 * self.ncell, "u")
+        _check_f64(p, self.nnode, "p")
+        self._ok(self._lib.ebv_save_state(self._ctx, _ptr(u), _ptr(p), os.fsencode(path)))
+
+    def load_state(self, u, p, path):
+        """Parameters and geometry from a file of save_state (same grid); u and
+        p receive the saved fields."""
+        _check_f64(u, 3 * self.ncell, "u")
+        _check_f64(p, self.nnode, "p")
+        self._ok(self._lib.ebv_load_state(self._ctx, _ptr(u), _ptr(p), os.fsencode(path)))
+
+    def flow_diagnostics(self, u, lam=None, stress_dev=None):
+        """Per cell: Lambda of Eq. ryovar and the yield-stress deviation
+        eta ||g|| / tau0 - 1; returns (lam, stress_dev) (allocated if None)."""
+        import torch
+        _check_f64(u, 3 * self.ncell, "u")
+        if lam is None:
+            lam = torch.empty(self.ncell, dtype=torch.float64, device=u.device)
+        if stress_dev is None:
+            stress_dev = torch.empty(self.ncell, dtype=torch.float64, device=u.device)
+        _check_f64(lam, self.ncell, "lam")
+        _check_f64(stress_dev, self.ncell, "stress_dev")
+        self._ok(self._lib.ebv_flow_diagnostics(self._ctx, _ptr(u), _ptr(lam), _ptr(stress_dev)))
+        return lam, stress_dev
+
     def update_viscosity(self, u, eta, srate=None):
         _check_f64(u, 3 * self.ncell, "u")
         _check_f64(eta, self.ncell, "eta")

@@ -136,13 +136,20 @@ def taylor_green(x, y, t, re=100.0):
     return u, v, p
 
 
-def taylor_green_grid(n, nz=8):
+def taylor_green_depth(n):
+    """Cells in z: 8, or n/8 from 128 on, so that the multigrid hierarchies
+    still coarsen to a small bottom level."""
+    return max(8, n // 8)
+
+
+def taylor_green_grid(n, nz=None):
     """Cells (n, n, nz) of size 1/n: the unit square in x, y, nz cells deep."""
-    return (n, n, nz), 1.0 / n
+    return (n, n, nz or taylor_green_depth(n)), 1.0 / n
 
 
-def taylor_green_velocity(n, nz=8, t=0.0, re=100.0):
+def taylor_green_velocity(n, nz=None, t=0.0, re=100.0):
     """Cell-centred (u, v, w), shape (3, nz, n, n), at time t."""
+    nz = nz or taylor_green_depth(n)
     c = (np.arange(n) + 0.5) / n
     Y, X = np.meshgrid(c, c, indexing="ij")
     u, v, _ = taylor_green(X, Y, t, re)

@@ -3,7 +3,8 @@ creeping flow (advect = 0) and with the convective term (advect = 1): drag
 sensitivities with respect to the yield stress, the plastic viscosity and a
 per-cell body force, checked against central finite differences of the same
 forward on the GPU (forward solves converged to 1e-13, so the difference
-quotient is accurate to ~1e-7) and of the FP64 oracle's forward.  Sphere
+quotient is accurate to ~1e-7) and of the FP64 oracle's forward, and against
+the oracle's own exact derivatives (forward-mode dual numbers, 1e-8).  Sphere
 channel, Bingham (Bi = 5, m = 1e3), fixed dt from the CFL limit of the
 initial state, checkpointing every 2 steps.  With the convective term the
 limiter and the upwinding are piecewise linear: the seeded noise of the
@@ -19,6 +20,10 @@ torch = pytest.importorskip("torch")
 
 DEV = "cuda:0"
 N, R, STEPS, EVERY = 16, 0.2, 4, 2
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64).ravel(), device=DEV)
 TOL_FD = 1e-5
 
 
@@ -171,3 +176,46 @@ def test_gradient_matches_oracle_finite_differences(E, O, advect):
     fd_m = (J_o(t0, m0 + hm) - J_o(t0, m0 - hm)) / (2 * hm)
     assert abs(gt - fd_t) <= TOL_FD * abs(fd_t), (gt, fd_t)
     assert abs(gm - fd_m) <= TOL_FD * abs(fd_m), (gm, fd_m)
+
+
+@pytest.fixture(scope="module")
+def dual_case(O):
+    """The adjoint configuration on a 32^3 copy (sphere r = 0.125, Bi = 5,
+    m = 1e3, seeded Gaussian body force of sigma 0.1), 8 steps at the CFL
+    step of the initial state: the oracle's forward-mode derivatives of the
+    time-averaged drag along tau0, mu and a seeded body-force direction."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_07392_gb300 import workloads as W
+    w = W.Workload("adjoint_32", n=32, radius=0.125, tau0=W.tau0_for_bingham(5.0, 0.125), m=1e3, seed=3)
+    g = O.Grid(n=(32, 32, 32), h=1.0 / 32)
+    geo = O.build_geometry(g, O.Shape(kind=O.SHAPE_SPHERE, p=tuple(w.centre) + (w.radius,)))
+    fl = geo.alpha > 0
+    u0 = (W.initial_velocity(w).reshape(3, -1) * fl).ravel()
+    f = (W.body_force(w).reshape(3, -1) * fl).ravel()
+    df = (np.random.Generator(np.random.PCG64(77)).normal(0.0, 1.0, (3, g.ncell)) * fl).ravel()
+    P = O.Params(rho=w.rho, mu=w.mu, tau0=w.tau0, m=w.m, model=w.model, bi_cfl=w.bingham, tol=1e-13)
+    dt = O.timestep(g, geo, P, u0, f)
+    p0 = np.zeros(g.nnode)
+    steps = 8
+    out = {}
+    for key, kw in (("tau0", {"dtau0": 1.0}), ("mu", {"dmu": 1.0}), ("f", {"df": df})):
+        out["J"], out[key] = O.drag_tangent(g, geo, P, u0, p0, dt, steps, f=f, **kw)
+    return w, u0, f, df, dt, steps, out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_drag_gradient_matches_dual_oracle(E, dual_case, precision):
+    """dJ/dtau0, dJ/dmu and <dJ/df, df> of the GPU adjoint (ebv_drag_gradient,
+    checkpoints every 4 steps, the step with the convective term) against the
+    oracle's exact forward-mode derivatives, to 1e-8 relative."""
+    w, u0, f, df, dt, steps, ref = dual_case
+    s = E.Solver.from_workload(w, precision=precision, tol=1e-13, max_iters=20000, advect=1)
+    uu, ff = _t(u0), _t(f)
+    p0 = torch.zeros(s.nnode, dtype=torch.float64, device=DEV)
+    J, gt, gm, fb = s.drag_gradient(uu, p0, dt, steps, 4, f=ff)
+    assert J == pytest.approx(ref["J"], rel=1e-9)
+    assert gt == pytest.approx(ref["tau0"], rel=1e-8), (gt, ref["tau0"])
+    assert gm == pytest.approx(ref["mu"], rel=1e-8), (gm, ref["mu"])
+    gf = float(torch.dot(fb, _t(df)))
+    assert gf == pytest.approx(ref["f"], rel=1e-8), (gf, ref["f"])

@@ -158,15 +158,16 @@ def test_nodal_projection(E, O, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_advance_three_steps(E, O, precision):
-    """Sphere channel 32^3 (r = 0.125, tau_y = 1, m = 1e3), three CFL steps."""
+def test_advance_config1_ten_steps(E, O, precision):
+    """The plain-method configuration in full: sphere channel 32^3 (r = 0.125,
+    tau_y = 1, m = 1e3), ten CFL steps, every step against the oracle."""
     s, g, geo, P = _pair(E, O, 32, precision=precision)
     from paper_1905_07392_gb300 import workloads as W
     w = W.sphere_channel_32()
     u0 = (W.initial_velocity(w).reshape(3, -1) * (geo.alpha > 0)).ravel()
     uo, po = u0.copy(), np.zeros(g.nnode)
     u, p = _t(u0), torch.zeros(g.nnode, dtype=torch.float64, device=DEV)
-    for step in range(3):
+    for step in range(w.steps):
         uo, po, sto = O.advance(g, geo, P, uo, po)
         st = s.advance(u, p)
         assert st["dt"] == pytest.approx(sto["dt"], rel=1e-12)
@@ -251,3 +252,22 @@ def test_errors_are_reported(E, O):
     with pytest.raises(E.EbvError) as ei:
         s.advance(u2, torch.zeros(g.nnode, dtype=torch.float64, device=DEV))
     assert ei.value.status == -3
+
+
+@pytest.mark.parametrize("model", ["bingham", "herschel_bulkley"])
+def test_flow_diagnostics(E, O, model):
+    """Lambda of Eq. ryovar and the yield-stress deviation, cell by cell,
+    on a sphere-cut 32^3 box with a seeded velocity field."""
+    prm = {"model": O.HB, "n_flow": 0.5, "tau0": 2.0} if model == "herschel_bulkley" else {"tau0": 2.0}
+    s, g, geo, P = _pair(E, O, 32, **prm)
+    rng = np.random.default_rng(21)
+    x = (np.arange(32) + 0.5) / 32
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    u = np.stack([np.sin(3 * Y) * Z, np.cos(2 * X) + 0.3 * Z, X * Y]) + 0.01 * rng.normal(size=(3, 32, 32, 32))
+    u = (u.reshape(3, -1) * (geo.alpha > 0)).ravel()
+    lam_o, dev_o = O.flow_diagnostics(g, geo, P, u)
+    lam, dev = s.flow_diagnostics(_t(u))
+    lam, dev = lam.cpu().numpy(), dev.cpu().numpy()
+    assert np.abs(lam - lam_o).max() < 1e-10
+    assert np.abs(dev - dev_o).max() <= 1e-12 * np.abs(dev_o).max()
+    assert lam_o.min() < -0.5 and lam_o.max() > 0.5    # the field has rotation- and strain-dominated cells
