@@ -331,6 +331,107 @@ __global__ void __launch_bounds__(256) k_cc_gs(VOp<T> A, T *__restrict__ x, cons
     }
 }
 
+// The colour pass of k_cc_gs (plain form: no coarse correction, no r.z) for
+// FP32 levels whose rows split into half-rows of a multiple of 4 cells (nx a
+// multiple of 8): a thread updates 4 consecutive cells of its colour in one
+// half-row of each of its kPz planes.  The row-split layout makes b, 1/diag,
+// the y and z neighbours (the other colour at the same half-row position in
+// the adjacent rows), the y and z faces and the result 16-byte (FP32) or
+// 8-byte (BF16) vectors; the x neighbours are the other half-row's 4 values
+// plus one beyond, the x faces 8 scalars.  Per cell the same operations in
+// the same order as gs_cell, so the result is bit for bit that of k_cc_gs.
+template <class F>
+__device__ inline void load4(const F *p, float v[4])
+{
+    if constexpr (sizeof(F) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&q.x);
+        const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&q.y);
+        v[0] = __low2float(a); v[1] = __high2float(a); v[2] = __low2float(b); v[3] = __high2float(b);
+    }
+}
+
+template <int kPz>
+__global__ void __launch_bounds__(256) k_cc_gs4(VOp<float> A, float *__restrict__ x, const float *__restrict__ b,
+                                                int color, int zero_start)
+{
+    using F = typename VFace<float>::type;
+    const GridD &g = A.g;
+    const int hx = g.nx >> 1;
+    const int t0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int kb = (blockIdx.z * blockDim.z + threadIdx.z) * kPz;
+    if (t0 >= hx || j >= g.ny) return;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    float val[kPz][4];
+    int pos[kPz], oth[kPz];
+#pragma unroll
+    for (int h = 0; h < kPz; h++) {
+        const int k = kb + h;
+        pos[h] = -1;
+        if (k >= g.nz) continue;
+        const int par = (color + j + k) & 1;            // i parity of this row's cells of the colour
+        const int rc = (k * g.ny + j) * g.nx;
+        const int c = rc + (par ? hx : 0) + t0;         // own half-row, cells t0 .. t0+3
+        const int o = rc + (par ? 0 : hx) + t0;         // the other half-row, same positions
+        pos[h] = c;
+        oth[h] = o;
+        float bc[4], di[4];
+        load4(b + c, bc);
+        load4(A.dinv + c, di);
+        float off[4] = {0.f, 0.f, 0.f, 0.f};
+        if (!zero_start) {
+            float xo[4], xs[4], xn[4], xd[4], xu[4], fy0[4], fy1[4], fz0[4], fz1[4];
+            load4(x + o, xo);
+            const float xb = par ? (t0 + 4 < hx ? x[o + 4] : 0.f) : (t0 > 0 ? x[o - 1] : 0.f);
+            if (j > 0) load4(x + c - sy, xs);
+            if (j < g.ny - 1) load4(x + c + sy, xn);
+            if (k > 0) load4(x + c - sz, xd);
+            if (k < g.nz - 1) load4(x + c + sz, xu);
+            load4(A.by + c + k * g.nx, fy0);
+            load4(A.by + c + k * g.nx + g.nx, fy1);
+            load4(A.bz + c, fz0);
+            load4(A.bz + c + sz, fz1);
+            const int rf = rc + k * g.ny + j, hf = (g.nx + 2) >> 1;
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const int t = t0 + m, i = 2 * t + par;
+                const float bxl = float(A.bx[rf + (par ? hf + t : t)]);
+                const float bxh = float(A.bx[rf + (par ? t + 1 : hf + t)]);
+                const float xw = par ? xo[m] : (m ? xo[m - 1] : xb);
+                const float xe = par ? (m < 3 ? xo[m + 1] : xb) : xo[m];
+                float s = 0.f;
+                if (i > 0) s += bxl * xw;
+                if (i < g.nx - 1) s += bxh * xe;
+                if (j > 0) s += fy0[m] * xs[m];
+                if (j < g.ny - 1) s += fy1[m] * xn[m];
+                if (k > 0) s += fz0[m] * xd[m];
+                if (k < g.nz - 1) s += fz1[m] * xu[m];
+                off[m] = s;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 4; m++) val[h][m] = (bc[m] + off[m]) * di[m];
+    }
+#pragma unroll
+    for (int h = 0; h < kPz; h++) {
+        if (pos[h] < 0) continue;
+        if (zero_start) *reinterpret_cast<float4 *>(x + oth[h]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4 *>(x + pos[h]) = make_float4(val[h][0], val[h][1], val[h][2], val[h][3]);
+    }
+}
+constexpr int GS4_PZ = 2;
+inline bool gs4_ok(const GridD &g) { return (g.nx & 7) == 0; }
+inline dim3 gs4_block() { return dim3(32, 4, 2); }
+inline dim3 gs4_grid(const GridD &g, dim3 bk)
+{
+    const int nq = (g.nx >> 1) / 4, nzg = (g.nz + GS4_PZ - 1) / GS4_PZ;
+    return dim3((nq + bk.x - 1) / bk.x, (g.ny + bk.y - 1) / bk.y, (nzg + bk.z - 1) / bk.z);
+}
+
 // Residual of the 8 children of coarse cell (I,J,K), averaged.
 template <class T>
 __device__ inline T rr_cell(const VOp<T> &A, const T *__restrict__ x, const T *__restrict__ b, int I, int J,
@@ -492,14 +593,24 @@ __global__ void k_convert(const S *__restrict__ a, D *__restrict__ b, int n)
 
 // FP64 natural-order array of cells (d < 0) or of faces of normal d -> FP32
 // row-split copy.
-__global__ void k_to_split(GridD g, int d, const double *__restrict__ a, float *__restrict__ b)
+__global__ void k_to_split(GridD g, int d, const double *__restrict__ a, float *__restrict__ b,
+                           const double *__restrict__ sig = nullptr)
 {
     const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
     const int n = mx * my * mz;
+    const double sc = sig ? *sig : 1.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const int i = s % mx, j = (s / mx) % my, k = s / (mx * my);
-        b[d < 0 ? cix<float>(g, i, j, k) : fidxT<float>(g, d, i, j, k)] = (float)a[s];
+        b[d < 0 ? cix<float>(g, i, j, k) : fidxT<float>(g, d, i, j, k)] = (float)(a[s] * sc);
     }
+}
+
+// r = sig * a in FP32 (the refinement solver's first residual, natural order)
+__global__ void k_to32_scaled(const double *__restrict__ a, float *__restrict__ b, int n,
+                              const double *__restrict__ sig)
+{
+    const double sc = *sig;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) b[s] = (float)(a[s] * sc);
 }
 
 // FP32 face coefficients -> the V-cycle's BF16 copy (same layout)
@@ -638,8 +749,10 @@ __global__ void k_visc_rhs(GridD g, GeomD geo, int comp, const double *__restric
 template <class T, bool kRes = false>
 __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__restrict__ p, T *__restrict__ q,
                                                       double *__restrict__ part, const T *__restrict__ b = nullptr,
-                                                      float *__restrict__ r32 = nullptr)
+                                                      float *__restrict__ r32 = nullptr,
+                                                      const double *__restrict__ sig = nullptr)
 {
+    const double sc = (kRes && sig) ? *sig : 1.0;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int kk = blockIdx.z * blockDim.z + threadIdx.z;
@@ -662,7 +775,7 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
         for (int h = 0; h < 2; h++)
             if (cc[h] >= 0) {
                 if constexpr (kRes) {
-                    const float r = (float)(b[cc[h]] - y[h]);
+                    const float r = (float)((b[cc[h]] - y[h]) * sc);
                     r32[cix<float>(A.g, i, j, 2 * kk + h)] = r;
                     vr += r * r;
                 } else {
@@ -858,8 +971,10 @@ inline dim3 nd_tile_grid(const GridD &g)
 template <class T, int kMode>
 __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__restrict__ xin, T *__restrict__ out,
                                                        T *__restrict__ dvec, const T *__restrict__ b, T cd, T cr,
-                                                       double *__restrict__ part, float *__restrict__ out32)
+                                                       double *__restrict__ part, float *__restrict__ out32,
+                                                       const double *__restrict__ sig)
 {
+    const double sc = (kMode == ND_RES32 && sig) ? *sig : 1.0;
     __shared__ T sx[2][NT_H][NT_W];
     const GridD &g = A.g;
     const int NX = g.nx + 1, NY = g.ny + 1, NZ = g.nz + 1;
@@ -920,7 +1035,7 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 if (kMode == ND_RESID) out[n] = T(0);
                 if (kMode == ND_APPLY) { out[n] = X0; v += X0 * X0; }
                 if (kMode == ND_RES32) {
-                    const float r = (float)(b_c - X0);
+                    const float r = (float)((b_c - X0) * sc);
                     out32[n] = r;
                     vr += r * r;
                 }
@@ -934,7 +1049,7 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 if (kMode == ND_RESID) out[n] = b_c - ax;
                 if (kMode == ND_APPLY) { out[n] = ax; v += X0 * ax; }
                 if (kMode == ND_RES32) {
-                    const float r = (float)(b_c - ax);
+                    const float r = (float)((b_c - ax) * sc);
                     out32[n] = r;
                     vr += r * r;
                 }
@@ -955,8 +1070,9 @@ template <class T, int kMode>
 __global__ void __launch_bounds__(256) k_nd_irr(NdOp<T> A, const int *__restrict__ list, int nlist,
                                                 const T *__restrict__ xin, T *__restrict__ out, T *__restrict__ dvec,
                                                 const T *__restrict__ b, T cd, T cr, double *__restrict__ part,
-                                                float *__restrict__ out32)
+                                                float *__restrict__ out32, const double *__restrict__ sig)
 {
+    const double sc = (kMode == ND_RES32 && sig) ? *sig : 1.0;
     const GridD &g = A.g;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     T v = 0;
@@ -974,7 +1090,7 @@ __global__ void __launch_bounds__(256) k_nd_irr(NdOp<T> A, const int *__restrict
         if (kMode == ND_RESID) out[n] = b[n] - ax;
         if (kMode == ND_APPLY) { out[n] = ax; v = xin[n] * ax; }
         if (kMode == ND_RES32) {
-            const float r = (float)(b[n] - ax);
+            const float r = (float)((b[n] - ax) * sc);
             out32[n] = r;
             v = T(r) * T(r);
         }
@@ -1424,7 +1540,23 @@ __global__ void __launch_bounds__(kCoarseThreads) k_cc_coarse_vcycle(CoarseVC<T>
 // ===========================================================================
 // Krylov glue
 // ===========================================================================
-enum { S_BB = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_PQ = 4, S_REL = 16, S_PREV = 17, S_T2 = 18 };
+enum { S_BB = 0, S_RR = 1, S_RZ = 2, S_RZOLD = 3, S_PQ = 4, S_REL = 16, S_PREV = 17, S_T2 = 18, S_SIG = 19 };
+
+// Scale of the refinement solver's FP32 residuals: a power of two near 1/|b|
+// (1 when |b| is 0 or not finite), so that corrections of right-hand sides far
+// below 1 (down to round-off) do not underflow in FP32.  Multiplying by a
+// power of two is exact, so in the usual range every FP32 operation gives
+// the same bits as without it.  The FP64 norms are scaled alike.
+__global__ void k_set_sigma(double *scal, int x_zero)
+{
+    if (threadIdx.x) return;
+    const double bb = scal[S_BB];
+    double sig = 1.0;
+    if (bb > 0.0 && isfinite(bb)) sig = ldexp(1.0, -ilogb(sqrt(bb)));
+    scal[S_SIG] = sig;
+    scal[S_BB] = bb * sig * sig;
+    if (x_zero) scal[S_RR] = scal[S_BB];
+}
 
 // Writes a loop condition: the control word (polled by the host in eager
 // mode) and, inside a captured graph, the conditional node's handle.
@@ -1657,8 +1789,9 @@ __global__ void k_add32to64(double *__restrict__ x, const float *__restrict__ e,
 {
     const int k = ctl[C_K];
     const float a = (float)(scal[S_RZOLD] / scal[S_PQ]);
+    const double isig = 1.0 / scal[S_SIG];   // exact: a power of two
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-        x[s] += (double)final_e(e, p, a, k, s);
+        x[s] += (double)final_e(e, p, a, k, s) * isig;
 }
 
 // k_add32to64 with e and p FP32 row-split vectors
@@ -1669,8 +1802,9 @@ __global__ void k_add32to64_split(GridD g, double *__restrict__ x, const float *
     const int n = ncell(g);
     const int k = ctl[C_K];
     const float a = (float)(scal[S_RZOLD] / scal[S_PQ]);
+    const double isig = 1.0 / scal[S_SIG];   // exact: a power of two
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-        x[s] += (double)final_e(e, p, a, k, cix<float>(g, s % g.nx, (s / g.nx) % g.ny, s / (g.nx * g.ny)));
+        x[s] += (double)final_e(e, p, a, k, cix<float>(g, s % g.nx, (s / g.nx) % g.ny, s / (g.nx * g.ny))) * isig;
 }
 
 __global__ void k_fill(double *a, int n, double v)
@@ -1808,18 +1942,30 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
     const char *name = kGsName[sizeof(T) == 4][l < 7 ? l : 7];
     for (int s = 0; s < 2; s++) {
         const int z = (s == 0 && zero_start) ? 1 : 0;
+        // the plain passes of FP32 levels with half-rows of a multiple of 4
+        // cells take the vectorised form (same results)
+        auto plain = [&](int color, int zs) {
+            if constexpr (sizeof(T) == 4) {
+                if (gs4_ok(g)) {
+                    EBV_LAUNCH_P(c, name, nb, (k_cc_gs4<GS4_PZ>), gs4_grid(g, gs4_block()), gs4_block(), 0, A, x, b,
+                                 color, zs);
+                    return;
+                }
+            }
+            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, color, zs, nullptr, GridD());
+        };
         if (s == 0 && xc)  // the first pass after the coarse-grid correction (+ the coarse array)
             EBV_LAUNCH_P(c, name, nb + 0.125 * sizeof(T) * (double)ncell(g), (k_cc_gs<T, true>), gr, bk, 0, A, x, b,
                          c0, z, xc, *gc);
         else
-            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, c0, z, nullptr, GridD());
+            plain(c0, z);
         if (s == 1 && dot_part)
             // fixed block shape: the grouping of its partial sums must not
             // follow the autotuned shape, or results would depend on timing
             EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false, true>), gs_grid(g, block3()), block3(), 0, A, x, b, 1 - c0,
                          0, nullptr, GridD(), dot_part);
         else
-            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, 1 - c0, 0, nullptr, GridD());
+            plain(1 - c0, 0);
     }
     if (!dot_part) return 0;
     const dim3 gd = gs_grid(g, block3());
@@ -1917,16 +2063,16 @@ inline int nd_tile_blocks(const GridD &g)
 }
 template <class T, int kMode>
 void nd_tile_pass(Ctx *c, const NdLevel &L, const char *name, double nbytes, const T *xin, T *out, T *d,
-                const T *b, T cd, T cr, double *part, float *out32 = nullptr)
+                const T *b, T cd, T cr, double *part, float *out32 = nullptr, const double *sig = nullptr)
 {
     const NdOp<T> A = ndop<T>(L);
     EBV_LAUNCH_P(c, name, nbytes, (k_nd_tile<T, kMode>), nd_tile_grid(L.g), dim3(NT_X, NT_Y), 0, A, xin, out, d, b,
-                 cd, cr, part, out32);
+                 cd, cr, part, out32, sig);
     static const char *const kIrrName[4] = {"nodal_listed_nodes chebyshev", "nodal_listed_nodes residual",
                                             "nodal_listed_nodes apply", "nodal_listed_nodes refinement residual"};
     if (L.nirr)
         EBV_LAUNCH_P(c, kIrrName[kMode], 0.0, (k_nd_irr<T, kMode>), dim3((L.nirr + 255) / 256), dim3(256), 0, A, L.irr,
-                     L.nirr, xin, out, d, b, cd, cr, part ? part + nd_tile_blocks(L.g) : nullptr, out32);
+                     L.nirr, xin, out, d, b, cd, cr, part ? part + nd_tile_blocks(L.g) : nullptr, out32, sig);
 }
 // partial sums written by nd_tile_pass on level L
 inline int nd_tile_parts(const NdLevel &L) { return nd_tile_blocks(L.g) + (L.nirr ? (L.nirr + 255) / 256 : 0); }
@@ -2215,7 +2361,7 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
     EBV_LAUNCH(c, k_solve_begin, dim3(1), dim3(32), 0, c->ctl);
     EBV_LAUNCH(c, k_dot, dim3(vblocks(n)), dim3(256), 0, b, b, n, c->part);
     reduce_sum(c, c->part, vblocks(n), c->scal + S_BB);
-    if (x_zero) reduce_sum(c, c->part, vblocks(n), c->scal + S_RR);
+    EBV_LAUNCH(c, k_set_sigma, dim3(1), dim3(32), 0, c->scal, x_zero ? 1 : 0);
     DevLoop outer(c, C_COND_OUT);
     true_residual();
     EBV_LAUNCH(c, k_outer_check, dim3(1), dim3(32), 0, c->scal, c->ctl, tol, maxit, 60, 1, inner_drop, outer.h,
@@ -2271,7 +2417,7 @@ struct CcProblem : Problem {
     {
         // x, diagonal, 3 faces, b read, r (FP32) written: 6.5 words per cell
         EBV_LAUNCH_P(c, "cc_resid_fp64", 52.0 * n(), (k_cc_apply_dot<double, true>), agrid(), block3(), 0,
-                     ccop<double>(H->lv[0]), x, (double *)nullptr, c->part, b, r);
+                     ccop<double>(H->lv[0]), x, (double *)nullptr, c->part, b, r, c->scal + S_SIG);
     }
     void add32(Ctx *c, double *x, const float *e, const float *p) override
     {
@@ -2279,7 +2425,7 @@ struct CcProblem : Problem {
     }
     void to32(Ctx *c, const double *b, float *r) override
     {
-        EBV_LAUNCH(c, k_to_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, -1, b, r);
+        EBV_LAUNCH(c, k_to_split, dim3(vblocks(n())), dim3(256), 0, H->lv[0].g, -1, b, r, c->scal + S_SIG);
     }
 };
 
@@ -2304,7 +2450,7 @@ struct NdProblem : Problem {
     {
         // x, b read, r (FP32) written, act and reg flags: 5.25 words per node
         nd_tile_pass<double, ND_RES32>(c, H->lv[0], "nodal_resid_fp64", 22.0 * n(), x, nullptr, nullptr, b, 0.0,
-                                       0.0, c->part, r);
+                                       0.0, c->part, r, c->scal + S_SIG);
     }
     void add32(Ctx *c, double *x, const float *e, const float *p) override
     {
@@ -2312,7 +2458,7 @@ struct NdProblem : Problem {
     }
     void to32(Ctx *c, const double *b, float *r) override
     {
-        EBV_LAUNCH(c, (k_convert<double, float>), dim3(vblocks(n())), dim3(256), 0, b, r, n());
+        EBV_LAUNCH(c, k_to32_scaled, dim3(vblocks(n())), dim3(256), 0, b, r, n(), c->scal + S_SIG);
     }
 };
 

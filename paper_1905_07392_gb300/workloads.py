@@ -170,3 +170,22 @@ def sphere_box(cells_per_d=16, bi=1.0, m=1e3, D=0.25):
     return Workload(f"sphere_box_{cells_per_d}perD_bi{bi:g}", n=n[0], radius=r, centre=(2 * D, 2 * D, 3 * D),
                     tau0=tau0_for_bingham(bi, r), m=m, model=BINGHAM if bi > 0 else NEWTONIAN, noise=0.0,
                     bc=(INFLOW,) * 6, extra={"shape": n, "h": D / cells_per_d})
+
+
+# The paper's non-trivial body (Sec. "Non-trivial particle shape"): the
+# union of a sphere of diameter D centred at (1.8, 1.8, 2.8) D and the cube
+# with opposite corners (1.85, 1.85, 2.85) D and (2.5, 2.5, 3.5) D, in the
+# sphere box [0, 4D]^2 x [0, 6D] with u = U e_z on every side.
+SPHERE_CUBE_D = ((1.8, 1.8, 2.8), 0.5, (1.85, 1.85, 2.85), (2.5, 2.5, 3.5))
+
+
+def sphere_cube_bodies(D=0.25):
+    """(sphere (cx, cy, cz, r), cube (lo..., hi...)) in box units for diameter D."""
+    c, r, lo, hi = SPHERE_CUBE_D
+    return (tuple(D * v for v in c) + (D * r,), tuple(D * v for v in lo) + tuple(D * v for v in hi))
+
+
+def sphere_box_grid(cells_per_d, D=0.25):
+    """Cells (4N, 4N, 6N) of size D/N for N cells per diameter."""
+    n = cells_per_d
+    return (4 * n, 4 * n, 6 * n), D / n

@@ -1,13 +1,20 @@
 """Spatio-temporal convergence of the whole step (Sec. "Spatio-temporal
 convergence study: Taylor-Green vortices", Eq. taylor-green, Table
 tab:convergence): the Taylor-Green vortex at Re = 100 in the unit square
-(8 cells deep), slip walls on all sides (the paper's periodic solution also
-satisfies them exactly), advanced with dt = h/4 to t = 0.25 on 32^2, 64^2
-and 128^2 cells; the velocity error at the cell centres against the exact
-solution must fall at second order in the discrete L1, L2 and max norms, as
-in the paper's table (whose values are not targets: the domain, end time and
-walls differ).  Also the first steps against the oracle, on a box with no
-outflow side (both pressure problems fixed by the one reference point).
+(8 cells deep, n/8 from 128^2), slip walls on all sides (the paper's
+periodic solution also satisfies them exactly), advanced to t = 0.25 with
+the step of Eqs. cfl:dt .. cfl:viscous:new (the last step shortened to end
+there) on 64^2, 128^2 and 256^2 cells.  The velocity error at the cell
+centres against the exact solution must fall at second order (rate > 1.8)
+from 128^2 to 256^2 in the discrete L1, L2 and max norms, and by more than
+1.4 from 64^2 to 128^2; the paper's rates also approach 2 only on the finer
+grids, and its values are not targets (domain, end time and walls differ).
+Algorithm 1 applies the implicit viscous operator with the full step in both
+stages, which is first order in time for that part; the CFL step's viscous
+limit makes the step O(h^2) on fine grids, so the run as a whole converges at
+second order, as in the paper.  Also the first steps against the oracle, on a
+box with no outflow side (both pressure problems fixed by the one reference
+point).
 """
 import numpy as np
 import pytest
@@ -43,9 +50,11 @@ def _errors(E, n, precision):
     s = _solver(E, n, precision, 1e-12)
     u = torch.tensor(W.taylor_green_velocity(n).ravel(), device=DEV)
     p = torch.zeros(s.nnode, dtype=torch.float64, device=DEV)
-    dt = 0.25 / n
-    steps = int(round(T / dt))
-    s.advance_graph(u, p, dt=dt, steps=steps, stats=False)
+    t = 0.0
+    while t < T * (1.0 - 1e-12):
+        dt = min(s.timestep(u), T - t)
+        s.advance(u, p, dt=dt, stats=False)
+        t += dt
     ue = W.taylor_green_velocity(n, t=T, re=RE)
     e = u.cpu().numpy().reshape(ue.shape) - ue
     mag = np.sqrt((e * e).sum(axis=0))
@@ -55,10 +64,11 @@ def _errors(E, n, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_taylor_green_second_order(E, precision):
-    errs = [_errors(E, n, precision) for n in (32, 64, 128)]
+    errs = [_errors(E, n, precision) for n in (64, 128, 256)]
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert (rates[-1] > 1.8).all(), (errs, rates)
-    assert errs[-1][2] < 1e-3, errs
+    assert (rates[0] > 1.4).all(), (errs, rates)
+    assert errs[-1][2] < 1e-4, errs
 
 
 def test_taylor_green_steps_match_oracle(E, O):
