@@ -87,7 +87,10 @@ typedef struct {
     double bi_cfl;    /* Bingham number in the viscous limit, Eq. cfl:viscous:new */
     double tol;       /* relative residual of every linear solve */
     int max_iters;    /* Krylov iterations per solve */
-    double delta_min; /* lower bound (cell units) of the wall distance in the implicit EB flux */
+    double delta_min; /* lower bound (cell units) of the wall distance in the implicit EB flux:
+                         a cell centre behind the EB plane counts as this close to the wall
+                         (0.01 in the bindings; larger values under-enforce no-slip in small
+                         cut cells and raise the drag) */
     int precision;    /* EBV_FP64 or EBV_FP32_REFINE */
     int advect;       /* 1: Algorithm 1 as printed; 0: creeping flow, the convective term C = 0
                          (the paper's evaluation runs at Re = 1e-3, Sec. "Cylinder moving through

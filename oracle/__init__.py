@@ -155,7 +155,7 @@ class Params:
     bi_cfl: float = 0.0
     tol: float = 1e-13
     max_iters: int = 200000
-    delta_min: float = 0.25
+    delta_min: float = 0.01
     advect: int = 1
 
     def c(self):

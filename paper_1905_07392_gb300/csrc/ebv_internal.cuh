@@ -175,6 +175,8 @@ struct CcLevel {
     __nv_bfloat16 *bf_h[3] = {nullptr, nullptr, nullptr};
     uint8_t *cov = nullptr;  // 1 where the cell is covered (identity row)
     dim3 gs_blk = dim3(32, 4, 2);  // colour-pass block shape (autotuned per level)
+    dim3 gs4_blk = dim3(32, 4, 2); // the same for the vectorised FP32 pass
+    int gs4_pz = 2;                // its planes per thread (1 or 2, autotuned)
 };
 
 struct CcHier {

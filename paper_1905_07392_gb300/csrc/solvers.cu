@@ -354,9 +354,12 @@ __device__ inline void load4(const F *p, float v[4])
     }
 }
 
+// kPz = 1 asks for 5 resident blocks per SM (at most 51 registers), kPz = 2
+// for 4: one plane per thread and more warps, or two and more loads per warp.
 template <int kPz>
-__global__ void __launch_bounds__(256) k_cc_gs4(VOp<float> A, float *__restrict__ x, const float *__restrict__ b,
-                                                int color, int zero_start)
+__global__ void __launch_bounds__(256, kPz == 1 ? 5 : 4) k_cc_gs4(VOp<float> A, float *__restrict__ x,
+                                                                 const float *__restrict__ b, int color,
+                                                                 int zero_start)
 {
     using F = typename VFace<float>::type;
     const GridD &g = A.g;
@@ -423,13 +426,17 @@ __global__ void __launch_bounds__(256) k_cc_gs4(VOp<float> A, float *__restrict_
         *reinterpret_cast<float4 *>(x + pos[h]) = make_float4(val[h][0], val[h][1], val[h][2], val[h][3]);
     }
 }
-constexpr int GS4_PZ = 2;
 inline bool gs4_ok(const GridD &g) { return (g.nx & 7) == 0; }
-inline dim3 gs4_block() { return dim3(32, 4, 2); }
-inline dim3 gs4_grid(const GridD &g, dim3 bk)
+inline dim3 gs4_grid(const GridD &g, dim3 bk, int pz)
 {
-    const int nq = (g.nx >> 1) / 4, nzg = (g.nz + GS4_PZ - 1) / GS4_PZ;
+    const int nq = (g.nx >> 1) / 4, nzg = (g.nz + pz - 1) / pz;
     return dim3((nq + bk.x - 1) / bk.x, (g.ny + bk.y - 1) / bk.y, (nzg + bk.z - 1) / bk.z);
+}
+inline void launch_gs4(cudaStream_t st, dim3 bk, int pz, const VOp<float> &A, float *x, const float *b, int color,
+                       int zs)
+{
+    if (pz == 1) k_cc_gs4<1><<<gs4_grid(A.g, bk, 1), bk, 0, st>>>(A, x, b, color, zs);
+    else k_cc_gs4<2><<<gs4_grid(A.g, bk, 2), bk, 0, st>>>(A, x, b, color, zs);
 }
 
 // Residual of the 8 children of coarse cell (I,J,K), averaged.
@@ -1947,8 +1954,12 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
         auto plain = [&](int color, int zs) {
             if constexpr (sizeof(T) == 4) {
                 if (gs4_ok(g)) {
-                    EBV_LAUNCH_P(c, name, nb, (k_cc_gs4<GS4_PZ>), gs4_grid(g, gs4_block()), gs4_block(), 0, A, x, b,
-                                 color, zs);
+                    if (L.gs4_pz == 1)
+                        EBV_LAUNCH_P(c, name, nb, (k_cc_gs4<1>), gs4_grid(g, L.gs4_blk, 1), L.gs4_blk, 0, A, x, b,
+                                     color, zs);
+                    else
+                        EBV_LAUNCH_P(c, name, nb, (k_cc_gs4<2>), gs4_grid(g, L.gs4_blk, 2), L.gs4_blk, 0, A, x, b,
+                                     color, zs);
                     return;
                 }
             }
@@ -2757,6 +2768,23 @@ ebv_status autotune_shapes_t(Ctx *c)
             if (ms < best) { best = ms; L.gs_blk = bk; }
         }
         c->visc.lv[l].gs_blk = L.gs_blk;
+        if constexpr (sizeof(T) == 4) {
+            // the vectorised pass: a thread covers 4 cells of a half-row, so
+            // narrow blocks suit the levels whose rows are short
+            static const dim3 c4[] = {dim3(32, 4, 2), dim3(32, 8, 1), dim3(16, 8, 2), dim3(16, 16, 1),
+                                      dim3(8, 16, 2), dim3(8, 32, 1), dim3(4, 32, 2), dim3(4, 16, 4)};
+            if (gs4_ok(L.g)) {
+                float best4 = 1e30f;
+                for (int pz = 1; pz <= 2; pz++)
+                    for (const dim3 &bk : c4) {
+                        if (bk.x > 2 * (unsigned)((L.g.nx >> 3) + 1)) continue;   // no block wider than twice a row
+                        float ms = time_it([&]() { launch_gs4(c->stream, bk, pz, A, x, b, 0, 0); });
+                        if (ms < best4) { best4 = ms; L.gs4_blk = bk; L.gs4_pz = pz; }
+                    }
+                c->visc.lv[l].gs4_blk = L.gs4_blk;
+                c->visc.lv[l].gs4_pz = L.gs4_pz;
+            }
+        }
     }
     ChebCoef k = cheb_coef(2.0);
     for (int l = 0; l < c->nd.L; l++) {

@@ -235,7 +235,7 @@ class Solver:
 
     def __init__(self, n, h, lo=(0.0, 0.0, 0.0), bc=W.CHANNEL_BC, u_in=(0.0, 0.0, 1.0), *,
                  rho=1.0, mu=1.0, tau0=0.0, m=1e3, n_flow=1.0, eta0=1e3, model=BINGHAM,
-                 cfl=0.5, bi_cfl=0.0, tol=1e-8, max_iters=1000, delta_min=0.25,
+                 cfl=0.5, bi_cfl=0.0, tol=1e-8, max_iters=1000, delta_min=0.01,
                  precision=FP64, advect=1, stream=None, lib=None):
         import torch
         self._lib = lib if lib is not None else load()
@@ -536,7 +536,7 @@ class Batch:
             v._lib, v.n, v.h, v.stream, v._fn_keep, v._owned = self._lib, (w.n,) * 3, w.h, stream, None, False
             v.params = dict(rho=w.rho, mu=w.mu, tau0=w.tau0, m=w.m, n_flow=w.n_flow, eta0=1e3,
                             model=w.model, cfl=w.cfl, bi_cfl=w.bingham, tol=tol, max_iters=max_iters,
-                            delta_min=0.25, precision=precision, advect=1)
+                            delta_min=0.01, precision=precision, advect=1)
             g = _Grid()
             g.n[:] = [w.n] * 3
             g.lo[:] = [0.0, 0.0, 0.0]

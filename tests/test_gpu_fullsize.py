@@ -133,3 +133,46 @@ def test_full_step_256(case, O):
     un = u.cpu().numpy().reshape(3, -1)
     assert np.isfinite(un).all() and (un[:, geo.alpha == 0] == 0).all()
     assert np.isfinite(st["drag"]) and 0.0 <= st["yield_frac"] <= 1.0
+
+
+def test_explicit_terms_256(case, O):
+    """The explicit terms of Algorithm 2 at 256^3: the viscous term V (Eq.
+    explicit-viscous with the EB wall flux of Eq. dudn) element by element
+    against the oracle's, from the same velocity and the oracle's eta; the
+    convective term C through an identity that holds for any face velocity:
+    sum alpha C h^3 equals minus the net flux through the box faces (interior
+    faces cancel, the EB carries none, redistribution conserves), with the
+    GPU's own projected face velocities (the oracle cannot run the 256^3
+    projection solve in test time)."""
+    s, g, geo, P, u0 = case
+    N3 = g.ncell
+    Cv = torch.empty(3 * N3, dtype=torch.float64, device=DEV)
+    V = torch.empty(3 * N3, dtype=torch.float64, device=DEV)
+    eta = torch.empty(N3, dtype=torch.float64, device=DEV)
+    s.derived(_t(u0), Cv, eta, V)
+    eta_o, _ = O.strain_eta(g, geo, P, u0)
+    V_o = O.viscous_explicit(g, geo, P, u0, eta_o)
+    assert np.abs(V.cpu().numpy() - V_o).max() <= 1e-10 * np.abs(V_o).max()
+    # C: the face velocities derived used (face states, projection), recomputed
+    nft = sum(g.nface(d) for d in range(3))
+    uf = torch.empty(nft, dtype=torch.float64, device=DEV)
+    s.face_states(_t(u0), uf)
+    s.solve_mac(uf, torch.empty(N3, dtype=torch.float64, device=DEV))
+    ufd = np.split(uf.cpu().numpy(), np.cumsum([g.nface(d) for d in range(3)])[:2])
+    aps = [geo.ax, geo.ay, geo.az]
+    uq = u0.reshape(3, *g.cshape())
+    C = Cv.cpu().numpy().reshape(3, N3)
+    for q in range(3):
+        net = 0.0
+        for d in range(3):
+            a = aps[d].reshape(g.fshape(d))
+            w = ufd[d].reshape(g.fshape(d))
+            for hs in (0, 1):
+                fi = [slice(None)] * 3
+                fi[2 - d] = -1 if hs else 0
+                state = (np.full(a[tuple(fi)].shape, g.u_in[q]) if g.bc[2 * d + hs] == O.INFLOW
+                         else uq[q][tuple(fi)])
+                net += (1.0 if hs else -1.0) * (a[tuple(fi)] * state * w[tuple(fi)]).sum()
+        total = (geo.alpha * C[q]).sum() * g.h ** 3
+        scale = np.abs(geo.alpha * C[q]).sum() * g.h ** 3 + abs(net) * g.h ** 2
+        assert abs(total + net * g.h ** 2) <= 1e-12 * scale, (q, total, -net * g.h ** 2)

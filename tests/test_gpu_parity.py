@@ -42,7 +42,7 @@ def _pair(E, O, n, centre=(0.5, 0.5, 0.5), r=0.125, plane=None, bc=None, u_in=(0
           tol=1e-13, precision=0, **prm):
     bc = bc or (O.SLIP, O.SLIP, O.SLIP, O.SLIP, O.INFLOW, O.OUTFLOW)
     args = dict(rho=1.0, mu=1.0, tau0=1.0, m=1e3, n_flow=1.0, eta0=1e3, model=O.BINGHAM,
-                cfl=0.5, bi_cfl=0.25, delta_min=0.25)
+                cfl=0.5, bi_cfl=0.25, delta_min=0.01)
     args.update(prm)
     s = E.Solver((n, n, n), 1.0 / n, bc=bc, u_in=u_in, tol=tol, max_iters=5000,
                  precision=precision, **args)

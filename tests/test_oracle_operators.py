@@ -284,7 +284,9 @@ def test_mac_projection_divergence_free(O, sphere16):
 
 def test_eb_dirichlet_manufactured_rates(O):
     """Poisson with u = 0 on the sphere and the box: u = (|x-c|^2 - r^2) S(x).
-    Measured orders of the face-centred EB operator: L1 >= 1.2, Linf >= 0.8."""
+    Measured orders of the face-centred EB operator with the wall distance
+    bounded below at 0.01 cells: L1 1.73, Linf 0.99 (32 -> 64); pinned at
+    L1 >= 1.6, Linf >= 0.9."""
     r = 0.2
     e1, einf = [], []
     for n in (16, 32, 64):
@@ -306,4 +308,4 @@ def test_eb_dirichlet_manufactured_rates(O):
         err = np.abs(xs - f * S)[fl]
         e1.append(err.mean())
         einf.append(err.max())
-    assert np.log2(e1[1] / e1[2]) > 1.2 and np.log2(einf[1] / einf[2]) > 0.8, (e1, einf)
+    assert np.log2(e1[1] / e1[2]) > 1.6 and np.log2(einf[1] / einf[2]) > 0.9, (e1, einf)
