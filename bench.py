@@ -225,7 +225,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per algorithmic byte, from one ncu capture of the
 # current kernel on a smaller grid (192^3, traffic grows with the cells);
 # the reported traffic is this ratio times the algorithmic bytes per launch.
-NCU_TRAFFIC_RATIO = {"cc_gs_colour_sweep<float> L0": 1.15}
+NCU_TRAFFIC_RATIO = {"cc_gs_colour_sweep<float> L0": 1.16}
 
 
 def roofline(prof, cells):
