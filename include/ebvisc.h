@@ -45,6 +45,9 @@ typedef enum {
     EBV_ERR_INVALID = -1,        /* bad argument, size or state */
     EBV_ERR_CUDA = -2,           /* a CUDA call failed (text in ebv_last_error) */
     EBV_ERR_NOT_CONVERGED = -3,  /* a linear solve hit max_iters above tol */
+    EBV_ERR_TIMEOUT = -4,        /* a bounded wait inside a kernel gave up (ebv_set_spin_limit);
+                                    the kernel let its copies in flight land and returned, the
+                                    context stays usable */
     EBV_ERR_NAN = -5,            /* a residual became NaN or Inf */
     EBV_ERR_GEOMETRY = -6,       /* geometry missing or unsupported */
     EBV_ERR_TOO_LARGE = -7,      /* beyond the fixed working storage of ebv_drag_noalloc */
@@ -278,6 +281,22 @@ ebv_status ebv_drag_noalloc(const ebv_grid *grid, const ebv_params *params, cons
  * frees what it took); bytes < 0 removes the limit.  Process-wide; the
  * device is never actually exhausted. */
 void ebv_set_alloc_limit(long long bytes);
+
+/* The smoother's waits on its asynchronous (TMA) tile loads are bounded:
+ * one wait gives up after `cycles` cycles of the SM clock (default about one
+ * second: cycles < 0 restores it), and the solve then ends with
+ * EBV_ERR_TIMEOUT.  cycles = 0 makes every such wait give up at once, which
+ * exercises that path without any fault or hang (for tests).  Process-wide;
+ * read when a step is issued or captured. */
+void ebv_set_spin_limit(long long cycles);
+
+/* How FP32 multigrid levels whose x size is a multiple of 16 run a red-black
+ * sweep: 0 as two colour passes, 1 (default) as whichever of the two colour
+ * passes and the fused one-pass sweep was faster when the context's solvers
+ * were set up, 2 always as the fused sweep.  All give the same results bit
+ * for bit; the switch exists to show that and to measure the difference.
+ * Process-wide; read when a step is issued or captured. */
+void ebv_set_fused_sweep(int mode);
 
 /* Counters for the measurement harness: kernel launches queued since the
  * context was created (host counter). */

@@ -40,6 +40,8 @@ cudaError_t dev_malloc(void **p, size_t bytes)
 }  // namespace ebv
 
 extern "C" void ebv_set_alloc_limit(long long bytes) { g_alloc_budget.store(bytes < 0 ? -1 : bytes); }
+extern "C" void ebv_set_spin_limit(long long cycles) { ebv::set_spin_limit(cycles); }
+extern "C" void ebv_set_fused_sweep(int mode) { ebv::set_fused_sweep(mode); }
 
 namespace {
 
@@ -322,6 +324,12 @@ ebv_status step_error(Ctx *c)
     const int fe = c->ctl_host[C_STEPERR];
     if (!fe) return EBV_OK;
     const int e = fe / 100, slot = fe % 100;
+    if (e == E_SMEM)
+        return c->fail(EBV_ERR_CUDA, "shared memory of the fused sweep not 128-byte aligned (solve slot " +
+                                         std::to_string(slot) + ")");
+    if (e == E_TIMEOUT)
+        return c->fail(EBV_ERR_TIMEOUT, "a bounded wait in the smoother gave up (solve slot " +
+                                            std::to_string(slot) + ")");
     return c->fail(e == E_NAN ? EBV_ERR_NAN : EBV_ERR_NOT_CONVERGED,
                    std::string(e == E_NAN ? "non-finite residual" : "linear solve did not reach the tolerance") +
                        " (solve slot " + std::to_string(slot) + ")");
@@ -894,6 +902,7 @@ void ebv_destroy(ebv_ctx *c)
                 cudaFree(H->vdiag_d[q][l]); cudaFree(H->vdiag_f[q][l]); cudaFree(H->vdinv_f[q][l]);
             }
             for (int d = 0; d < 3; d++) { cudaFree(L.bf_d[d]); cudaFree(L.bf_f[d]); cudaFree(L.bf_h[d]); }
+            cudaFree(L.bxp);
             if (h == 0) cudaFree(L.cov);
         }
         for (int q = 0; q < H->nvar; q++) { cudaFree(H->vbinv[q]); cudaFree(H->vdiag_a[q]); }

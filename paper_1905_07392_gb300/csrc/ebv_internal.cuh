@@ -6,6 +6,7 @@
 // Cell availability for stencils is "inside the box and flag != 0".
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,7 +30,7 @@ constexpr int kSstatLen = kSstatAcc + 2 * kSolveSlots;
 // control words: loop conditions, iteration counters, error words
 enum { C_COND_OUT = 0, C_COND_IN = 1, C_IT = 2, C_K = 3, C_NOUT = 4, C_STALL = 5, C_ERR = 6, C_ZERO = 7,
        C_STEPERR = 8, C_LEN = 16 };
-enum { E_NAN = 1, E_NOTCONV = 2 };
+enum { E_NAN = 1, E_NOTCONV = 2, E_TIMEOUT = 3, E_SMEM = 4 };
 
 struct GridD {
     int nx, ny, nz;
@@ -174,6 +175,12 @@ struct CcLevel {
     float *dinv_f = nullptr;   // 1/diag_f (0 where diag_f <= 0), the smoother's multiplier
     __nv_bfloat16 *bf_h[3] = {nullptr, nullptr, nullptr};
     uint8_t *cov = nullptr;  // 1 where the cell is covered (identity row)
+    void *bxp = nullptr;     // padded x faces of the fused sweep (V-cycle face type), or none
+    // per kind of sweep (from zero, plain, after the coarse correction, with
+    // r.z): the times of the fused sweep [0] and of its colour passes [1],
+    // measured when the solvers are set up (fused never chosen if untimed)
+    float rb_ms[4][2] = {{1e30f, 0.f}, {1e30f, 0.f}, {1e30f, 0.f}, {1e30f, 0.f}};
+    int rb_kz = 0;           // its planes per block (timed), 0 for the model's choice
     dim3 gs_blk = dim3(32, 4, 2);  // colour-pass block shape (autotuned per level)
     dim3 gs4_blk = dim3(32, 4, 2); // the same for the vectorised FP32 pass
     int gs4_pz = 2;                // its planes per thread (1 or 2, autotuned)
@@ -321,12 +328,34 @@ struct Ctx {
     cudaEvent_t phase_ev[9] = {};
     bool phase_ev_ok = false;
 
+    // TMA tensor maps of the fused smoother sweep, encoded on first use per
+    // (array, box kind, level dims); the arrays live as long as the context
+    struct TmaEntry {
+        const void *p;
+        int kind, nx, ny, nz;
+        CUtensorMap m;
+    };
+    std::vector<TmaEntry> tma;
+
     ebv_status fail(ebv_status s, const std::string &m)
     {
         err = m;
         return s;
     }
 };
+
+// Process-wide switches of the smoother (ebv_set_spin_limit,
+// ebv_set_fused_sweep): the bound of one wait inside a kernel in clock64
+// cycles (0: give up at once, for tests of the timeout path), and whether
+// FP32 levels with nx a multiple of 16 take the fused one-pass sweep: 0
+// never, 1 where it timed faster than two colour passes, 2 always (same
+// results in every case).  Read when a launch is issued or captured.
+long long spin_limit();
+int fused_sweep_mode();
+void set_spin_limit(long long cycles);
+void set_fused_sweep(int mode);
+constexpr long long kSpinDefault = 2000000000LL;   // about 1 s at the maximum SM clock
+constexpr long long kRbDrainCycles = 4000000000LL; // waiting for loads in flight after a timeout
 
 // Launch bookkeeping: every kernel launch goes through these macros.
 // EBV_LAUNCH_P names the launch and states the algorithmic bytes it must move

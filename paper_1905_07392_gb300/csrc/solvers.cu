@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "ebv_internal.cuh"
+#include "tma.cuh"
 
 namespace ebv {
 
@@ -437,6 +438,445 @@ inline void launch_gs4(cudaStream_t st, dim3 bk, int pz, const VOp<float> &A, fl
 {
     if (pz == 1) k_cc_gs4<1><<<gs4_grid(A.g, bk, 1), bk, 0, st>>>(A, x, b, color, zs);
     else k_cc_gs4<2><<<gs4_grid(A.g, bk, 2), bk, 0, st>>>(A, x, b, color, zs);
+}
+
+// ---------------------------------------------------------------------------
+// A whole red-black sweep in one pass (FP32 levels with nx a multiple of 16):
+// the cells of colour c0 from the old values of the other colour, then the
+// other colour from the new c0 values, read from x_in and written to x_out
+// (the two passes in place give the same values, bit for bit: each cell is
+// formed by the same operations in the same order as in gs_cell).
+//
+// A block owns a tile of RB_TX x RB_TY cells of every plane of a chunk of
+// planes [z0, z1) and marches it in z.  Step m forms the first colour on
+// plane m over the tile and a one-cell ring around it (the ring's values are
+// the neighbours of the tile's second-colour cells; neighbouring blocks form
+// them too), keeping three planes of these in shared memory, then the second
+// colour on plane m-1 and writes plane m-1 (both colours).  Every operand
+// comes in by TMA tile loads two steps ahead, completed on mbarriers: x (tile
+// + 2-cell ring), b and 1/diag (tile + 1-cell ring), and the x, y and z face
+// coefficients -- the x faces from a copy whose rows are padded to 16-byte
+// strides (bxp: even faces then odd faces, each half RB_HXP(nx) long), since
+// the stored rows hold nx + 1 entries.  No global load is left inside a
+// step.  Per sweep every array is read once from DRAM (the rings come from
+// L2) and x written once: 22 bytes per cell with BF16 faces instead of 28
+// for two colour passes.
+//
+// Out-of-range tile coordinates load as zeros and the cells there are
+// skipped; a neighbour outside the box is not read (the same tests as in
+// gs_cell).  Each wait on a load is bounded (spin cycles of clock64); a wait
+// that gives up sets E_TIMEOUT in ctl[C_ERR], waits (bounded) for the loads
+// still in flight and ends the block, so the solve stops with that status
+// instead of hanging.
+// kZero: x_in is zero (not read).  kCorr: the first colour reads
+// x_in + the coarse correction of the neighbour's parent (prolongation
+// folded in, as in k_cc_gs).  kDot: also the partial b.x_out of every
+// (plane, tile), part[plane * ntiles + tile], summed over the same cells in
+// the same order as k_cc_dot_tiles, which forms them after colour passes.
+constexpr int RB_TX = 64;                 // tile cells along x
+constexpr int RB_HW = RB_TX / 2;          // half-row positions per tile
+constexpr int RB_TY = 16;                 // tile rows
+constexpr int RB_THREADS = RB_TY * (RB_HW / 2);   // one thread per 2 positions of a tile row
+constexpr int RB_XW = RB_HW + 8;          // x / cell box width (FP32): 4 positions each side
+constexpr int RB_FW = RB_HW + 16;         // face box width: 8 positions each side
+constexpr int RB_XR = RB_TY + 4;          // rows of the x box
+constexpr int RB_CR = RB_TY + 2;          // rows of the cell boxes (b, 1/diag, x and z faces, results)
+constexpr int RB_YR = RB_TY + 3;          // rows of the y-face box
+constexpr int RB_NBAR = 3;                // mbarriers (steps in flight + 1)
+static_assert(RB_THREADS == 256, "one thread per 2 positions of each tile row");
+// half-row length of the padded x-face copy: nx/2 + 1 even faces, rounded up to 8
+__host__ __device__ inline int rb_hxp(int nx) { return ((nx / 2 + 1) + 7) / 8 * 8; }
+
+constexpr int al128(int b) { return (b + 127) / 128 * 128; }
+template <class F>
+struct RbSmem {
+    static constexpr int bX = RB_XW * 2 * RB_XR * 4, bC = RB_XW * 2 * RB_CR * 4;
+    static constexpr int bY = RB_FW * 2 * RB_YR * (int)sizeof(F), bZ = RB_FW * 2 * RB_CR * (int)sizeof(F);
+    static constexpr int kX = al128(bX), kC = al128(bC), kY = al128(bY), kZ = al128(bZ);
+    // x: planes m-1, m, m+1 and one ahead; b, 1/diag, x and y faces: m-1, m
+    // and one ahead; z faces: face planes m-1 .. m+1 and one ahead; results
+    // of the first colour: planes m-2 .. m
+    static constexpr int oX = 0, oB = oX + 4 * kX, oD = oB + 3 * kC, oY = oD + 3 * kC, oZ = oY + 3 * kY;
+    static constexpr int oXF = oZ + 4 * kZ, oR = oXF + 3 * kZ, oBar = oR + 3 * kC, oMisc = oBar + 64;
+    static constexpr int bytes = oMisc + 128;
+};
+
+template <class F>
+struct RbArgs {
+    GridD g, gc;            // this level; the coarse level (kCorr)
+    const float *xc;        // coarse correction (kCorr)
+    float *xout;
+    double *part;           // kDot partials
+    int *ctl;
+    int c0, kz;             // first colour, planes per chunk
+    long long spin;         // bound of one wait, clock64 cycles
+};
+
+struct RbMaps {
+    CUtensorMap x, b, d, fx, fy, fz;
+};
+
+template <class F>
+__device__ inline void rb_issue(unsigned char *sm, uint64_t *bar, int q, int m0, int p0, int y0, bool zero,
+                                const RbMaps &tm)
+{
+    using S = RbSmem<F>;
+    const int m = m0 + q;
+    uint64_t *b = bar + q % RB_NBAR;
+    uint32_t bytes = 2 * S::bC + S::bY + 2 * S::bZ;
+    if (!zero) bytes += (q == 0 ? 3 : 1) * S::bX;
+    if (q == 0) bytes += S::bZ;
+    mbar_arrive_expect_tx(b, bytes);
+    if (!zero) {
+        if (q == 0) {
+            tma_load_4d(sm + S::oX + ((m - 1 + 8) & 3) * S::kX, &tm.x, p0 - 4, 0, y0 - 2, m - 1, b);
+            tma_load_4d(sm + S::oX + ((m + 8) & 3) * S::kX, &tm.x, p0 - 4, 0, y0 - 2, m, b);
+        }
+        tma_load_4d(sm + S::oX + ((m + 1 + 8) & 3) * S::kX, &tm.x, p0 - 4, 0, y0 - 2, m + 1, b);
+    }
+    const int sb = (m + 3) % 3;
+    tma_load_4d(sm + S::oB + sb * S::kC, &tm.b, p0 - 4, 0, y0 - 1, m, b);
+    tma_load_4d(sm + S::oD + sb * S::kC, &tm.d, p0 - 4, 0, y0 - 1, m, b);
+    tma_load_4d(sm + S::oY + sb * S::kY, &tm.fy, p0 - 8, 0, y0 - 1, m, b);
+    tma_load_4d(sm + S::oXF + sb * S::kZ, &tm.fx, p0 - 8, 0, y0 - 1, m, b);
+    if (q == 0) tma_load_4d(sm + S::oZ + ((m + 8) & 3) * S::kZ, &tm.fz, p0 - 8, 0, y0 - 1, m, b);
+    tma_load_4d(sm + S::oZ + ((m + 1 + 8) & 3) * S::kZ, &tm.fz, p0 - 8, 0, y0 - 1, m + 1, b);
+}
+
+// Two consecutive face coefficients from shared memory (4- or 8-byte aligned) as floats.
+template <class F>
+__device__ inline float2 ld2f(const F *p)
+{
+    if constexpr (sizeof(F) == 4) {
+        return *reinterpret_cast<const float2 *>(p);
+    } else {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(p);
+        return make_float2(__low2float(v), __high2float(v));
+    }
+}
+
+template <class F, bool kZero, bool kCorr, bool kDot>
+__global__ void __launch_bounds__(RB_THREADS, 2)
+    k_cc_rb_sweep(const __grid_constant__ RbMaps tm, const RbArgs<F> a)
+{
+    using S = RbSmem<F>;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const GridD &g = a.g;
+    const int hx = g.nx >> 1;
+    const int p0 = blockIdx.x * RB_HW, y0 = blockIdx.y * RB_TY;
+    const int z0 = blockIdx.z * a.kz, z1 = min(g.nz, z0 + a.kz);
+    if (z0 >= z1) return;
+    const int tid = threadIdx.x, c1 = 1 - a.c0;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + S::oBar);
+    int *flag = reinterpret_cast<int *>(sm + S::oMisc);
+    double *wsum = reinterpret_cast<double *>(sm + S::oMisc + 16);
+    const int m0 = z0 - 1, nstep = z1 - z0 + 2;
+    auto X = [&](int pl) { return reinterpret_cast<const float *>(sm + S::oX + ((pl + 8) & 3) * S::kX); };
+    auto Bv = [&](int pl) { return reinterpret_cast<const float *>(sm + S::oB + ((pl + 3) % 3) * S::kC); };
+    auto Dv = [&](int pl) { return reinterpret_cast<const float *>(sm + S::oD + ((pl + 3) % 3) * S::kC); };
+    auto FX = [&](int pl) { return reinterpret_cast<const F *>(sm + S::oXF + ((pl + 3) % 3) * S::kZ); };
+    auto FY = [&](int pl) { return reinterpret_cast<const F *>(sm + S::oY + ((pl + 3) % 3) * S::kY); };
+    auto FZ = [&](int pl) { return reinterpret_cast<const F *>(sm + S::oZ + ((pl + 8) & 3) * S::kZ); };
+    auto R = [&](int pl) { return reinterpret_cast<float *>(sm + S::oR + ((pl + 3) % 3) * S::kC); };
+    auto cor = [&](int i, int j, int k) -> float {
+        return kCorr ? a.xc[cix<float>(a.gc, i >> 1, j >> 1, k >> 1)] : 0.f;
+    };
+    if (smem_u32(sm) & 127) {   // tile destinations must be 128-byte aligned: report, load nothing
+        if (tid == 0) atomicCAS(a.ctl + C_ERR, 0, E_SMEM);
+        return;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < RB_NBAR; s++) mbar_init(bar + s, 1);
+        *flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        rb_issue<F>(sm, bar, 0, m0, p0, y0, kZero, tm);
+        rb_issue<F>(sm, bar, 1, m0, p0, y0, kZero, tm);
+    }
+    // second colour and output: thread -> positions pq, pq+1 of both halves of tile row r
+    const int r = tid >> 4, pq = p0 + 2 * (tid & 15);
+    const int j2 = y0 + r;
+    const bool own = j2 < g.ny && pq < hx;
+    for (int q = 0; q < nstep; q++) {
+        const int m = m0 + q;
+        if (!mbar_wait_bounded(bar + q % RB_NBAR, (q / RB_NBAR) & 1, a.spin)) atomicExch(flag, 1);
+        // first colour on plane m over the tile (two positions per thread)
+        // and its one-cell ring (82 cells)
+        if (m >= 0 && m < g.nz) {
+            const float *X0 = X(m - 1), *X1 = X(m), *X2 = X(m + 1), *Bm = Bv(m), *Dm = Dv(m);
+            const F *Fx = FX(m), *Fy = FY(m), *Fz0 = FZ(m), *Fz1 = FZ(m + 1);
+            float *Rm = R(m);
+            const int k = m;
+            auto XI = [&](const float *Xp, int rr, int h2, int qq) { return Xp[(rr * 2 + h2) * RB_XW + qq]; };
+            // one cell (i = 2p + h, j) of box row r1: the operations of gs_cell
+            auto cell = [&](int r1, int j, int h, int p) {
+                const int i = 2 * p + h, qx = p - p0 + 4, qf = p - p0 + 8;
+                const int cc = (r1 * 2 + h) * RB_XW + qx;
+                float off = 0.f;
+                if (!kZero) {
+                    const int rx = r1 + 1;
+                    // x faces i (lo) and i + 1 (hi): even faces in half 0, odd in half 1
+                    const float bxl = float(Fx[(r1 * 2 + h) * RB_FW + qf]);
+                    const float bxh = float(Fx[(r1 * 2 + 1 - h) * RB_FW + qf + h]);
+                    const float fy0 = float(Fy[(r1 * 2 + h) * RB_FW + qf]);
+                    const float fy1 = float(Fy[((r1 + 1) * 2 + h) * RB_FW + qf]);
+                    const float fz0 = float(Fz0[(r1 * 2 + h) * RB_FW + qf]);
+                    const float fz1 = float(Fz1[(r1 * 2 + h) * RB_FW + qf]);
+                    float xw = h ? XI(X1, rx, 0, qx) : XI(X1, rx, 1, qx - 1);
+                    float xe = h ? XI(X1, rx, 0, qx + 1) : XI(X1, rx, 1, qx);
+                    float xs = XI(X1, rx - 1, h, qx), xn = XI(X1, rx + 1, h, qx);
+                    float xd = XI(X0, rx, h, qx), xu = XI(X2, rx, h, qx);
+                    if (kCorr) {
+                        if (i > 0) xw = xw + cor(i - 1, j, k);
+                        if (i < g.nx - 1) xe = xe + cor(i + 1, j, k);
+                        if (j > 0) xs = xs + cor(i, j - 1, k);
+                        if (j < g.ny - 1) xn = xn + cor(i, j + 1, k);
+                        if (k > 0) xd = xd + cor(i, j, k - 1);
+                        if (k < g.nz - 1) xu = xu + cor(i, j, k + 1);
+                    }
+                    if (i > 0) off += bxl * xw;
+                    if (i < g.nx - 1) off += bxh * xe;
+                    if (j > 0) off += fy0 * xs;
+                    if (j < g.ny - 1) off += fy1 * xn;
+                    if (k > 0) off += fz0 * xd;
+                    if (k < g.nz - 1) off += fz1 * xu;
+                }
+                Rm[cc] = (Bm[cc] + off) * Dm[cc];
+            };
+            {   // the tile: positions p, p + 1 of row y0 + r, paired shared-memory loads
+                const int j = y0 + r, h = (a.c0 + j + m) & 1, p = pq;
+                if (own) {
+                    const int r1 = r + 1, rx = r1 + 1, qx = p - p0 + 4, qf = p - p0 + 8;
+                    const int ch = (r1 * 2 + h) * RB_XW + qx, cx = (rx * 2 + h) * RB_XW + qx;
+                    const int co = (rx * 2 + 1 - h) * RB_XW + qx;   // the other half, same positions
+                    const float2 bb = *reinterpret_cast<const float2 *>(Bm + ch);
+                    const float2 dd = *reinterpret_cast<const float2 *>(Dm + ch);
+                    float v[2];
+                    if (!kZero) {
+                        const float2 xs = *reinterpret_cast<const float2 *>(X1 + cx - 2 * RB_XW);
+                        const float2 xn = *reinterpret_cast<const float2 *>(X1 + cx + 2 * RB_XW);
+                        const float2 xd = *reinterpret_cast<const float2 *>(X0 + cx);
+                        const float2 xu = *reinterpret_cast<const float2 *>(X2 + cx);
+                        const float2 xo = *reinterpret_cast<const float2 *>(X1 + co);
+                        // h = 1: neighbours (p, p+1 | p+1, p+2) of half 0; h = 0: (p-1, p | p, p+1) of half 1
+                        const float xb = h ? X1[co + 2] : X1[co - 1];
+                        const float xw2[2] = {h ? xo.x : xb, h ? xo.y : xo.x};
+                        const float xe2[2] = {h ? xo.y : xo.x, h ? xb : xo.y};
+                        const float2 fxl = ld2f(Fx + (r1 * 2 + h) * RB_FW + qf);
+                        const float fxh0 = float(Fx[(r1 * 2 + 1 - h) * RB_FW + qf + h]);
+                        const float fxh1 = float(Fx[(r1 * 2 + 1 - h) * RB_FW + qf + h + 1]);
+                        const float2 fy0 = ld2f(Fy + (r1 * 2 + h) * RB_FW + qf);
+                        const float2 fy1 = ld2f(Fy + ((r1 + 1) * 2 + h) * RB_FW + qf);
+                        const float2 fz0 = ld2f(Fz0 + (r1 * 2 + h) * RB_FW + qf);
+                        const float2 fz1 = ld2f(Fz1 + (r1 * 2 + h) * RB_FW + qf);
+                        const float bxl[2] = {fxl.x, fxl.y}, bxh[2] = {fxh0, fxh1};
+                        const float ys0[2] = {fy0.x, fy0.y}, ys1[2] = {fy1.x, fy1.y};
+                        const float zs0[2] = {fz0.x, fz0.y}, zs1[2] = {fz1.x, fz1.y};
+                        const float vs[2] = {xs.x, xs.y}, vn[2] = {xn.x, xn.y}, vd[2] = {xd.x, xd.y};
+                        const float vu[2] = {xu.x, xu.y}, bv[2] = {bb.x, bb.y}, dv[2] = {dd.x, dd.y};
+#pragma unroll
+                        for (int e = 0; e < 2; e++) {
+                            const int i = 2 * (p + e) + h;
+                            float xw = xw2[e], xe = xe2[e], xs_ = vs[e], xn_ = vn[e], xd_ = vd[e], xu_ = vu[e];
+                            if (kCorr) {
+                                if (i > 0) xw = xw + cor(i - 1, j, k);
+                                if (i < g.nx - 1) xe = xe + cor(i + 1, j, k);
+                                if (j > 0) xs_ = xs_ + cor(i, j - 1, k);
+                                if (j < g.ny - 1) xn_ = xn_ + cor(i, j + 1, k);
+                                if (k > 0) xd_ = xd_ + cor(i, j, k - 1);
+                                if (k < g.nz - 1) xu_ = xu_ + cor(i, j, k + 1);
+                            }
+                            float off = 0.f;
+                            if (i > 0) off += bxl[e] * xw;
+                            if (i < g.nx - 1) off += bxh[e] * xe;
+                            if (j > 0) off += ys0[e] * xs_;
+                            if (j < g.ny - 1) off += ys1[e] * xn_;
+                            if (k > 0) off += zs0[e] * xd_;
+                            if (k < g.nz - 1) off += zs1[e] * xu_;
+                            v[e] = (bv[e] + off) * dv[e];
+                        }
+                    } else {
+                        v[0] = (bb.x + 0.f) * dd.x;
+                        v[1] = (bb.y + 0.f) * dd.y;
+                    }
+                    *reinterpret_cast<float2 *>(Rm + ch) = make_float2(v[0], v[1]);
+                }
+            }
+            // the ring: item t = tid / 3 of every third thread, spread over all warps
+            const int t = tid / 3;
+            if (tid % 3 == 0 && t < 2 * (RB_HW + 1) + RB_TY) {
+                int r1, p;
+                const int w = t < RB_HW + 1 ? t : t - (RB_HW + 1);
+                if (t < 2 * (RB_HW + 1)) {
+                    r1 = t < RB_HW + 1 ? 0 : RB_CR - 1;
+                    const int j = y0 - 1 + r1, h = (a.c0 + j + m) & 1;
+                    p = (h ? p0 - 1 : p0) + w;
+                } else {
+                    r1 = t - 2 * (RB_HW + 1) + 1;
+                    const int j = y0 - 1 + r1, h = (a.c0 + j + m) & 1;
+                    p = h ? p0 - 1 : p0 + RB_HW;
+                }
+                const int j = y0 - 1 + r1, h = (a.c0 + j + m) & 1;
+                if (j >= 0 && j < g.ny && p >= 0 && p < hx) cell(r1, j, h, p);
+            }
+        }
+        __syncthreads();
+        if (*flag) {
+            // a load did not arrive in time: record it, let the loads in
+            // flight land (bounded) and stop this block
+            if (tid == 0) {
+                atomicCAS(a.ctl + C_ERR, 0, E_TIMEOUT);
+                for (int s = q; s < min(nstep, q + 2); s++)
+                    mbar_wait_bounded(bar + s % RB_NBAR, (s / RB_NBAR) & 1, kRbDrainCycles);
+            }
+            return;
+        }
+        // second colour on plane mm = m - 1, and the plane's output
+        const int mm = m - 1;
+        if (q >= 2) {
+            double dsum = 0.0;
+            if (own) {
+                const float *Rc = R(mm), *Bm = Bv(mm);
+                const int rc = r + 1, qx = pq - p0 + 4, h2 = (c1 + j2 + mm) & 1;
+                float s2[2], s1[2];   // second colour (computed), first colour (from R)
+                {
+                    const float *Rl = R(mm - 1), *Rh = R(mm + 1), *Dm = Dv(mm);
+                    const F *Fx = FX(mm), *Fy = FY(mm), *Fz0 = FZ(mm), *Fz1 = FZ(mm + 1);
+                    const int k = mm, j = j2, hh = h2, qf = qx + 4;
+                    const int ch = (rc * 2 + hh) * RB_XW + qx, co = (rc * 2 + 1 - hh) * RB_XW + qx;
+                    // paired loads: own half (b, 1/diag, y and z neighbours), the other half (x neighbours)
+                    const float2 bb = *reinterpret_cast<const float2 *>(Bm + ch);
+                    const float2 dd = *reinterpret_cast<const float2 *>(Dm + ch);
+                    const float2 xs = *reinterpret_cast<const float2 *>(Rc + ch - 2 * RB_XW);
+                    const float2 xn = *reinterpret_cast<const float2 *>(Rc + ch + 2 * RB_XW);
+                    const float2 xd = *reinterpret_cast<const float2 *>(Rl + ch);
+                    const float2 xu = *reinterpret_cast<const float2 *>(Rh + ch);
+                    const float2 xo = *reinterpret_cast<const float2 *>(Rc + co);
+                    const float xb = hh ? Rc[co + 2] : Rc[co - 1];
+                    const float xw2[2] = {hh ? xo.x : xb, hh ? xo.y : xo.x};
+                    const float xe2[2] = {hh ? xo.y : xo.x, hh ? xb : xo.y};
+                    const float2 fxl = ld2f(Fx + (rc * 2 + hh) * RB_FW + qf);
+                    const float bxh[2] = {float(Fx[(rc * 2 + 1 - hh) * RB_FW + qf + hh]),
+                                          float(Fx[(rc * 2 + 1 - hh) * RB_FW + qf + hh + 1])};
+                    const float2 fy0 = ld2f(Fy + (rc * 2 + hh) * RB_FW + qf);
+                    const float2 fy1 = ld2f(Fy + ((rc + 1) * 2 + hh) * RB_FW + qf);
+                    const float2 fz0 = ld2f(Fz0 + (rc * 2 + hh) * RB_FW + qf);
+                    const float2 fz1 = ld2f(Fz1 + (rc * 2 + hh) * RB_FW + qf);
+                    const float bxl[2] = {fxl.x, fxl.y}, ys0[2] = {fy0.x, fy0.y}, ys1[2] = {fy1.x, fy1.y};
+                    const float zs0[2] = {fz0.x, fz0.y}, zs1[2] = {fz1.x, fz1.y};
+                    const float vs[2] = {xs.x, xs.y}, vn[2] = {xn.x, xn.y}, vd[2] = {xd.x, xd.y};
+                    const float vu[2] = {xu.x, xu.y}, bv[2] = {bb.x, bb.y}, dv[2] = {dd.x, dd.y};
+                    s1[0] = xo.x;
+                    s1[1] = xo.y;
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const int i = 2 * (pq + e) + hh;
+                        float off = 0.f;
+                        if (i > 0) off += bxl[e] * xw2[e];
+                        if (i < g.nx - 1) off += bxh[e] * xe2[e];
+                        if (j > 0) off += ys0[e] * vs[e];
+                        if (j < g.ny - 1) off += ys1[e] * vn[e];
+                        if (k > 0) off += zs0[e] * vd[e];
+                        if (k < g.nz - 1) off += zs1[e] * vu[e];
+                        s2[e] = (bv[e] + off) * dv[e];
+                    }
+                }
+                float v[2][2];
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    v[0][e] = h2 ? s1[e] : s2[e];
+                    v[1][e] = h2 ? s2[e] : s1[e];
+                }
+                float *o = a.xout + (size_t)(mm * g.ny + j2) * g.nx + pq;
+                *reinterpret_cast<float2 *>(o) = make_float2(v[0][0], v[0][1]);
+                *reinterpret_cast<float2 *>(o + hx) = make_float2(v[1][0], v[1][1]);
+                if constexpr (kDot) {
+                    float d = 0.f;
+#pragma unroll
+                    for (int h = 0; h < 2; h++)
+#pragma unroll
+                        for (int e = 0; e < 2; e++) d += Bm[(rc * 2 + h) * RB_XW + qx + e] * v[h][e];
+                    dsum = (double)d;
+                }
+            }
+            if constexpr (kDot) {
+                for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+                if ((tid & 31) == 0) wsum[tid >> 5] = dsum;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (kDot && q >= 2) {
+                double s = 0.0;
+                for (int w = 0; w < RB_THREADS / 32; w++) s += wsum[w];
+                a.part[(size_t)mm * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = s;
+            }
+            if (q + 2 < nstep) {
+                fence_proxy_async();
+                rb_issue<F>(sm, bar, q + 2, m0, p0, y0, kZero, tm);
+            }
+        }
+    }
+}
+
+// The padded copy of the x-face coefficients that k_cc_rb_sweep loads: per
+// row, the nx/2 + 1 even faces then, from position rb_hxp(nx), the nx/2 odd
+// ones (zeros in the padding), converted as the V-cycle's copy is.
+template <class F>
+__global__ void k_xface_pad(GridD g, const float *__restrict__ bf, F *__restrict__ out)
+{
+    const int hxp = rb_hxp(g.nx), hf = g.nx / 2 + 1, hx = g.nx / 2;
+    const long long n = 2LL * hxp * g.ny * g.nz;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const int pos = (int)(s % hxp);
+        const long long rh = s / hxp;
+        const int half = (int)(rh & 1);
+        const long long row = rh >> 1;
+        const long long rf = row * (g.nx + 1);
+        float v = 0.f;
+        if (half == 0 && pos < hf) v = bf[rf + pos];
+        if (half == 1 && pos < hx) v = bf[rf + hf + pos];
+        if constexpr (sizeof(F) == 2) out[s] = __float2bfloat16_rn(v);
+        else out[s] = v;
+    }
+}
+
+// The fused sweep's face type: the V-cycle's.
+using RbF = typename VFace<float>::type;
+
+// The (plane, tile) partials of b.x of k_cc_rb_sweep<kDot>, after two colour
+// passes: the same threads, cells, order and sums.  Grid (tiles x, tiles y,
+// nz), RB_THREADS threads.
+__global__ void __launch_bounds__(RB_THREADS) k_cc_dot_tiles(GridD g, const float *__restrict__ b,
+                                                              const float *__restrict__ x, double *__restrict__ part)
+{
+    __shared__ double wsum[RB_THREADS / 32];
+    const int tid = threadIdx.x, hx = g.nx >> 1;
+    const int r = tid >> 4;
+    const int j = blockIdx.y * RB_TY + r, pq = blockIdx.x * RB_HW + 2 * (tid & 15), k = blockIdx.z;
+    double dsum = 0.0;
+    if (j < g.ny && pq < hx) {
+        const size_t o = (size_t)(k * g.ny + j) * g.nx + pq;
+        float d = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const float2 bv = *reinterpret_cast<const float2 *>(b + o + h * hx);
+            const float2 xv = *reinterpret_cast<const float2 *>(x + o + h * hx);
+            d += bv.x * xv.x;
+            d += bv.y * xv.y;
+        }
+        dsum = (double)d;
+    }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
+    if ((tid & 31) == 0) wsum[tid >> 5] = dsum;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < RB_THREADS / 32; w++) s += wsum[w];
+        part[(size_t)k * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
 }
 
 // Residual of the 8 children of coarse cell (I,J,K), averaged.
@@ -1633,7 +2073,7 @@ __device__ inline void inner_check(double *scal, int *ctl, double tol, int maxit
     const double rr = scal[S_RR];
     int go = 1;
     if (!isfinite(rr)) {
-        ctl[C_ERR] = E_NAN;
+        if (ctl[C_ERR] == 0) ctl[C_ERR] = E_NAN;   // (the first error word stands)
         go = 0;
     } else if (!refine) {
         go = sqrt(rr / scal[S_BB]) > 0.5 * tol;
@@ -1647,7 +2087,7 @@ __device__ inline void inner_check(double *scal, int *ctl, double tol, int maxit
         }
         scal[S_PREV] = rr;
     }
-    if (ctl[C_IT] >= maxit) go = 0;
+    if (ctl[C_IT] >= maxit || ctl[C_ERR]) go = 0;   // (an error word set by a kernel ends the solve)
     set_cond(ctl, C_COND_IN, go, h, use_h);
 }
 
@@ -1882,9 +2322,12 @@ void cc_make_diag(Ctx *c, CcHier &H, int l)
                    H.vdinv_f[1][l], H.vdinv_f[2][l]);
 }
 
-// The V-cycle's BF16 copy of the FP32 faces of level L.
+// The V-cycle's BF16 copy of the FP32 faces of level L, and the padded copy
+// of its x faces that the fused sweep loads (in the V-cycle's face type).
 inline void cc_faces_bf16(Ctx *c, CcLevel &L)
 {
+    if (L.bxp)
+        EBV_LAUNCH(c, k_xface_pad<RbF>, dim3(kReduceBlocks), dim3(256), 0, L.g, L.bf_f[0], (RbF *)L.bxp);
     if constexpr (!kVcycleBf16) return;
     for (int d = 0; d < 3; d++) {
         const int n = nface(L.g, d);
@@ -1931,16 +2374,184 @@ inline dim3 ch_grid(const GridD &g, dim3 bk)
     return dim3((g.nx + 1 + bk.x - 1) / bk.x, (g.ny + 1 + bk.y - 1) / bk.y, (g.nz + 1 + bk.z - 1) / bk.z);
 }
 
-// dot_part: the last pass also writes block partials of b.x (k_cc_gs kDot);
-// returns their number (0 without dot_part).
+
+// ---- the fused sweep on the host: where it applies, tensor maps, shape -----
+enum { RB_ZERO = 0, RB_PLAIN = 1, RB_CORR = 2, RB_DOT = 3 };
+constexpr size_t kPartLen = (size_t)1 << 20;   // doubles in c->part
+
+inline int rb_ntiles(const GridD &g) { return ((g.nx / 2 + RB_HW - 1) / RB_HW) * ((g.ny + RB_TY - 1) / RB_TY); }
+
+// FP32 levels whose half-rows are whole multiples of 8 positions (16-byte TMA
+// strides for the BF16 face rows); their r.z partials are per (plane, tile).
+inline bool rb_fusable(const GridD &g)
+{
+    return g.nx % 16 == 0 && g.nx >= 16 && (size_t)rb_ntiles(g) * g.nz <= kPartLen;
+}
+
+// Tensor map of one array of the level, by box kind: 0 x (FP32 cells, tile +
+// 2 rows each side), 1 FP32 cells (tile + 1 row), 2 y faces, 3 z faces, 4 the
+// padded x faces; the array viewed as (half-row position, half, row, plane).
+bool rb_map(Ctx *c, const void *p, int kind, const GridD &g, CUtensorMap *out)
+{
+    if (!p) return false;
+    for (const auto &e : c->tma)
+        if (e.p == p && e.kind == kind && e.nx == g.nx && e.ny == g.ny && e.nz == g.nz) {
+            *out = e.m;
+            return true;
+        }
+    const bool face = kind >= 2;
+    const uint64_t es = face ? sizeof(RbF) : 4;
+    const uint64_t hx = kind == 4 ? (uint64_t)rb_hxp(g.nx) : (uint64_t)g.nx / 2;
+    const uint64_t rows = kind == 2 ? g.ny + 1 : g.ny, planes = kind == 3 ? g.nz + 1 : g.nz;
+    const uint64_t dims[4] = {hx, 2, rows, planes};
+    const uint64_t st[3] = {hx * es, 2 * hx * es, rows * 2 * hx * es};
+    const uint32_t box[4] = {(uint32_t)(face ? RB_FW : RB_XW), 2u,
+                             (uint32_t)(kind == 0 ? RB_XR : (kind == 2 ? RB_YR : RB_CR)), 1u};
+    const CUtensorMapDataType ty = (face && sizeof(RbF) == 2) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    Ctx::TmaEntry e;
+    e.p = p;
+    e.kind = kind;
+    e.nx = g.nx;
+    e.ny = g.ny;
+    e.nz = g.nz;
+    if (!tma_encode_4d(&e.m, ty, const_cast<void *>(p), dims, st, box)) return false;
+    c->tma.push_back(e);
+    *out = e.m;
+    return true;
+}
+
+template <bool kZero, bool kCorr, bool kDot>
+void rb_attr()
+{
+    static bool done = false;
+    if (!done) {
+        done = true;
+        cudaFuncSetAttribute(k_cc_rb_sweep<RbF, kZero, kCorr, kDot>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             RbSmem<RbF>::bytes);
+    }
+}
+
+// Blocks of the fused sweep resident on the device at once.
+int rb_resident()
+{
+    static int res = 0;
+    if (!res) {
+        rb_attr<false, false, false>();
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cc_rb_sweep<RbF, false, false, false>, RB_THREADS,
+                                                      RbSmem<RbF>::bytes);
+        res = std::max(1, per) * std::max(1, sms);
+    }
+    return res;
+}
+
+// Planes per chunk of a block: the fewest waves of resident blocks times the
+// steps of one block (its planes and the two of the chunk's start).
+int rb_kz(const GridD &g)
+{
+    const long long nt = rb_ntiles(g), res = rb_resident();
+    long long best = -1;
+    int bkz = g.nz;
+    for (int nc = 1; nc <= g.nz; nc++) {
+        const int kz = (g.nz + nc - 1) / nc, ncr = (g.nz + kz - 1) / kz;
+        const long long cost = ((nt * ncr + res - 1) / res) * (kz + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            bkz = kz;
+        }
+    }
+    return bkz;
+}
+
+// One fused sweep (maps already encoded by rb_maps).
+void rb_launch(Ctx *c, const char *name, const GridD &g, const RbMaps &tm, float *xout, int c0, int mode,
+               const float *xc, const GridD *gc, double *part, int kz = 0)
+{
+    RbArgs<RbF> a;
+    a.g = g;
+    a.gc = gc ? *gc : GridD();
+    a.xc = xc;
+    a.xout = xout;
+    a.part = part;
+    a.ctl = c->ctl;
+    a.c0 = c0;
+    a.kz = kz > 0 ? kz : rb_kz(g);
+    a.spin = spin_limit();
+    const dim3 gr((g.nx / 2 + RB_HW - 1) / RB_HW, (g.ny + RB_TY - 1) / RB_TY, (g.nz + a.kz - 1) / a.kz);
+    // algorithmic bytes: x written, x read (not from zero), b, 1/diag, three
+    // faces, the coarse correction (1/8 word per cell)
+    const double nb = (double)ncell(g) * (4.0 + (mode == RB_ZERO ? 0.0 : 4.0) + 8.0 + 3.0 * sizeof(RbF) +
+                                          (mode == RB_CORR ? 0.5 : 0.0));
+    const int sb = RbSmem<RbF>::bytes;
+    switch (mode) {
+    case RB_ZERO:
+        rb_attr<true, false, false>();
+        EBV_LAUNCH_P(c, name, nb, (k_cc_rb_sweep<RbF, true, false, false>), gr, dim3(RB_THREADS), sb, tm, a);
+        break;
+    case RB_CORR:
+        rb_attr<false, true, false>();
+        EBV_LAUNCH_P(c, name, nb, (k_cc_rb_sweep<RbF, false, true, false>), gr, dim3(RB_THREADS), sb, tm, a);
+        break;
+    case RB_DOT:
+        rb_attr<false, false, true>();
+        EBV_LAUNCH_P(c, name, nb, (k_cc_rb_sweep<RbF, false, false, true>), gr, dim3(RB_THREADS), sb, tm, a);
+        break;
+    default:
+        rb_attr<false, false, false>();
+        EBV_LAUNCH_P(c, name, nb, (k_cc_rb_sweep<RbF, false, false, false>), gr, dim3(RB_THREADS), sb, tm, a);
+    }
+}
+
+const char *const kRbName[8] = {"cc_rb_sweep<float> L0", "cc_rb_sweep<float> L1", "cc_rb_sweep<float> L2",
+                                "cc_rb_sweep<float> L3", "cc_rb_sweep<float> L4", "cc_rb_sweep<float> L5",
+                                "cc_rb_sweep<float> L6", "cc_rb_sweep<float> L7+"};
+
+// Two red-black sweeps' worth of smoothing is two calls; this is one sweep
+// pair as the V-cycle uses it: sweep 1 (from zero, or after the coarse
+// correction) then sweep 2 (plain, or with r.z partials).
+// dot_part: the last pass also writes partials of b.x -- per (plane, tile)
+// (k_cc_rb_sweep<kDot> or k_cc_dot_tiles) on levels the fused sweep applies
+// to, else per block of k_cc_gs<kDot>; returns their number (0 without
+// dot_part).  FP32 levels with nx a multiple of 16 can run each sweep as one
+// fused pass (x -> t -> x) or as two colour passes, with the same results bit
+// for bit: ebv_set_fused_sweep picks the passes (0), the faster of the two as
+// timed when the solvers are set up (1, the default) or the fused pass (2).
 template <class T>
 int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red_first, bool zero_start,
                const T *xc = nullptr, const GridD *gc = nullptr, double *dot_part = nullptr)
 {
-    (void)t;
     VOp<T> A = vop<T>(L);
     const int c0 = red_first ? 0 : 1;
     const GridD &g = L.g;
+    bool tiles = false;   // r.z partials per (plane, tile)
+    if constexpr (sizeof(T) == 4) {
+        if (rb_fusable(g)) {
+            tiles = true;
+            RbMaps m1, m2;
+            // each kind of sweep (from zero, plain, after the coarse correction,
+            // with r.z) was timed on its own against its colour passes
+            const int mode = fused_sweep_mode();
+            const int k1 = zero_start ? RB_ZERO : (xc ? RB_CORR : RB_PLAIN), k2 = dot_part ? RB_DOT : RB_PLAIN;
+            // (the pair runs x -> t -> x fused, or in place as passes: one form for both)
+            const bool faster = L.rb_ms[k1][0] + L.rb_ms[k2][0] < L.rb_ms[k1][1] + L.rb_ms[k2][1];
+            if ((mode == 2 || (mode == 1 && faster)) && rb_map(c, x, 0, g, &m1.x) && rb_map(c, t, 0, g, &m2.x) &&
+                rb_map(c, b, 1, g, &m1.b) && rb_map(c, A.dinv, 1, g, &m1.d) && rb_map(c, L.bxp, 4, g, &m1.fx) &&
+                rb_map(c, A.by, 2, g, &m1.fy) && rb_map(c, A.bz, 3, g, &m1.fz)) {
+                m2.b = m1.b;
+                m2.d = m1.d;
+                m2.fx = m1.fx;
+                m2.fy = m1.fy;
+                m2.fz = m1.fz;
+                const char *nm = kRbName[l < 7 ? l : 7];
+                rb_launch(c, nm, g, m1, t, c0, k1, xc, gc, nullptr, L.rb_kz);
+                rb_launch(c, nm, g, m2, x, c0, k2, nullptr, nullptr, dot_part, L.rb_kz);
+                return dot_part ? rb_ntiles(g) * g.nz : 0;
+            }
+        }
+    }
     // algorithmic bytes of one colour pass: half of one sweep's x read and
     // write, b, diagonal and 3 face coefficients (in their storage type)
     const double nb = 0.5 * ((4.0 * sizeof(T) + 3.0 * sizeof(typename VFace<T>::type)) * (double)ncell(g));
@@ -1970,7 +2581,7 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
                          c0, z, xc, *gc);
         else
             plain(c0, z);
-        if (s == 1 && dot_part)
+        if (s == 1 && dot_part && !tiles)
             // fixed block shape: the grouping of its partial sums must not
             // follow the autotuned shape, or results would depend on timing
             EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false, true>), gs_grid(g, block3()), block3(), 0, A, x, b, 1 - c0,
@@ -1979,6 +2590,14 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
             plain(1 - c0, 0);
     }
     if (!dot_part) return 0;
+    if constexpr (sizeof(T) == 4) {
+        if (tiles) {
+            const dim3 gt((g.nx / 2 + RB_HW - 1) / RB_HW, (g.ny + RB_TY - 1) / RB_TY, g.nz);
+            EBV_LAUNCH_P(c, "cc_dot_tiles", 8.0 * (double)ncell(g), k_cc_dot_tiles, gt, dim3(RB_THREADS), 0, g,
+                         (const float *)b, (const float *)x, dot_part);
+            return (int)(gt.x * gt.y * gt.z);
+        }
+    }
     const dim3 gd = gs_grid(g, block3());
     return (int)(gd.x * gd.y * gd.z);
 }
@@ -2291,6 +2910,11 @@ ebv_status finish_solve(Ctx *c, double *x, int n, int *iters, double *res)
     if (res) *res = c->sstat_host[3 * s + 1];
     if (c->ctl_host[C_ERR] == E_NAN)
         return c->fail(EBV_ERR_NAN, "non-finite residual (solve slot " + std::to_string(s) + ")");
+    if (c->ctl_host[C_ERR] == E_SMEM)
+        return c->fail(EBV_ERR_CUDA, "shared memory of the fused sweep not 128-byte aligned (solve slot " +
+                                         std::to_string(s) + ")");
+    if (c->ctl_host[C_ERR] == E_TIMEOUT)
+        return c->fail(EBV_ERR_TIMEOUT, "a bounded wait in the smoother gave up (solve slot " + std::to_string(s) + ")");
     if (c->ctl_host[C_ERR] == E_NOTCONV)
         return c->fail(EBV_ERR_NOT_CONVERGED, "linear solve did not reach the tolerance (solve slot " +
                                                   std::to_string(s) + ", relative residual " +
@@ -2617,6 +3241,8 @@ ebv_status setup_solvers(Ctx *c)
                 // one spare element: the coarse kernel stages BF16 arrays in 4-byte pairs
                 Lv.bf_h[d] = dalloc<__nv_bfloat16>(nface(gl[l], d) + 1, e);
             }
+            if (rb_fusable(gl[l]))
+                Lv.bxp = dalloc<RbF>((size_t)2 * rb_hxp(gl[l].nx) * gl[l].ny * gl[l].nz, e);
             if (H == &c->mac) Lv.cov = dalloc<uint8_t>(nc, e);
             else Lv.cov = c->mac.lv[l].cov;
         }
@@ -2784,6 +3410,52 @@ ebv_status autotune_shapes_t(Ctx *c)
                 c->visc.lv[l].gs4_blk = L.gs4_blk;
                 c->visc.lv[l].gs4_pz = L.gs4_pz;
             }
+            // the fused one-pass sweep against its two colour passes (same
+            // results), per kind of sweep: the faster serves it in switch mode 1
+            RbMaps m;
+            for (int q = 0; q < 4; q++) L.rb_ms[q][0] = 1e30f, L.rb_ms[q][1] = 0.f;
+            if (rb_fusable(L.g) && gs4_ok(L.g) && rb_map(c, x, 0, L.g, &m.x) && rb_map(c, b, 1, L.g, &m.b) &&
+                rb_map(c, A.dinv, 1, L.g, &m.d) && rb_map(c, L.bxp, 4, L.g, &m.fx) && rb_map(c, A.by, 2, L.g, &m.fy) &&
+                rb_map(c, A.bz, 3, L.g, &m.fz)) {
+                const long long nl = c->launches;
+                // planes per block: the model's choice, the most planes that
+                // still fill one wave, and half that (results do not depend on it)
+                const int nt = rb_ntiles(L.g), res = rb_resident(), nz = L.g.nz;
+                const int one = std::max(1, res / std::max(1, nt));   // chunks per wave
+                const int kzc[3] = {rb_kz(L.g), (nz + one - 1) / one, (nz + 2 * one - 1) / (2 * one)};
+                float best = 1e30f;
+                for (int kz : kzc) {
+                    const float ms = time_it(
+                        [&]() { rb_launch(c, "autotune", L.g, m, y, 0, RB_PLAIN, nullptr, nullptr, nullptr, kz); });
+                    if (ms < best) { best = ms; L.rb_kz = kz; }
+                }
+                // the correction sweep reads a coarse array: a zeroed vector with the next level's dims
+                const bool has_c = l + 1 < c->mac.L;
+                const GridD gc = has_c ? c->mac.lv[l + 1].g : GridD();
+                const dim3 gt((L.g.nx / 2 + RB_HW - 1) / RB_HW, (L.g.ny + RB_TY - 1) / RB_TY, L.g.nz);
+                const dim3 bk = L.gs_blk, grc = gs_grid(L.g, bk);
+                for (int kind = 0; kind < 4; kind++) {
+                    if (kind == RB_CORR && !has_c) continue;   // (no correction sweep on the last level)
+                    const float *xcv = kind == RB_CORR ? d : nullptr;
+                    const float ms_f = time_it([&]() {
+                        rb_launch(c, "autotune", L.g, m, y, 0, kind, xcv, kind == RB_CORR ? &gc : nullptr,
+                                  kind == RB_DOT ? c->part : nullptr, L.rb_kz);
+                    });
+                    const float ms_p = time_it([&]() {
+                        if (kind == RB_CORR)
+                            k_cc_gs<T, true><<<grc, bk, 0, c->stream>>>(A, x, b, 0, 0, d, gc);
+                        else
+                            launch_gs4(c->stream, L.gs4_blk, L.gs4_pz, A, x, b, 0, kind == RB_ZERO ? 1 : 0);
+                        launch_gs4(c->stream, L.gs4_blk, L.gs4_pz, A, x, b, 1, 0);
+                        if (kind == RB_DOT) k_cc_dot_tiles<<<gt, RB_THREADS, 0, c->stream>>>(L.g, b, x, c->part);
+                    });
+                    L.rb_ms[kind][0] = ms_f;
+                    L.rb_ms[kind][1] = ms_p;
+                }
+                c->launches = nl;
+            }
+            for (int q = 0; q < 4; q++) c->visc.lv[l].rb_ms[q][0] = L.rb_ms[q][0], c->visc.lv[l].rb_ms[q][1] = L.rb_ms[q][1];
+            c->visc.lv[l].rb_kz = L.rb_kz;
         }
     }
     ChebCoef k = cheb_coef(2.0);
@@ -2857,6 +3529,45 @@ ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *r
     NdProblem P;
     P.H = &c->nd;
     return solve(c, P, b, x, iters, res);
+}
+
+
+// ---- process-wide switches and the TMA encoder --------------------------
+namespace {
+long long g_spin = kSpinDefault;
+int g_fused = 1;
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+}  // namespace
+long long spin_limit() { return g_spin; }
+int fused_sweep_mode() { return g_fused; }
+void set_spin_limit(long long cycles) { g_spin = cycles < 0 ? kSpinDefault : cycles; }
+void set_fused_sweep(int mode) { g_fused = mode < 0 ? 0 : (mode > 2 ? 2 : mode); }
+
+bool tma_encode_4d(CUtensorMap *tm, CUtensorMapDataType type, void *base, const uint64_t dims[4],
+                   const uint64_t strides[3], const uint32_t box[4])
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && f)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        else
+            cudaGetLastError();
+    }
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t d[4] = {dims[0], dims[1], dims[2], dims[3]};
+    const cuuint64_t st[3] = {strides[0], strides[1], strides[2]};
+    const cuuint32_t bx[4] = {box[0], box[1], box[2], box[3]};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(tm, type, 4, base, d, st, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace ebv

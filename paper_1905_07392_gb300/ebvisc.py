@@ -22,7 +22,7 @@ INFLOW, OUTFLOW, SLIP, NOSLIP = 0, 1, 2, 3
 NEWTONIAN, BINGHAM, HERSCHEL_BULKLEY, POWER_LAW, SOUZA_MENDES_DUTRA = 0, 1, 2, 3, 4
 FP64, FP32_REFINE = 0, 1
 STATUS = {0: "EBV_OK", -1: "EBV_ERR_INVALID", -2: "EBV_ERR_CUDA", -3: "EBV_ERR_NOT_CONVERGED",
-          -5: "EBV_ERR_NAN", -6: "EBV_ERR_GEOMETRY", -8: "EBV_ERR_OOM"}
+          -4: "EBV_ERR_TIMEOUT", -5: "EBV_ERR_NAN", -6: "EBV_ERR_GEOMETRY", -8: "EBV_ERR_OOM"}
 
 
 class EbvError(RuntimeError):
@@ -73,6 +73,7 @@ EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geom
            "ebv_batch_instance", "ebv_batch_advance", "ebv_batch_launch_count",
            "ebv_batch_last_error", "ebv_batch_destroy", "ebv_adjoint_step", "ebv_drag_adjoint",
            "ebv_drag_gradient_workspace", "ebv_drag_gradient", "ebv_set_alloc_limit",
+           "ebv_set_spin_limit", "ebv_set_fused_sweep",
            "ebv_save_state", "ebv_load_state", "ebv_build_geometry_spheres",
            "ebv_build_geometry_bodies"]
 
@@ -146,6 +147,8 @@ def _open(path):
         "ebv_drag_gradient_workspace": ([vp, C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
         "ebv_drag_gradient": ([vp, vp, vp, vp, C.c_double, C.c_int, C.c_int, vp, dp, dp, vp], C.c_int),
         "ebv_set_alloc_limit": ([C.c_longlong], None),
+        "ebv_set_spin_limit": ([C.c_longlong], None),
+        "ebv_set_fused_sweep": ([C.c_int], None),
         "ebv_save_state": ([vp, vp, vp, C.c_char_p], C.c_int),
         "ebv_build_geometry_spheres": ([vp, C.c_int, dp], C.c_int),
         "ebv_build_geometry_bodies": ([vp, C.c_int, C.POINTER(_Body)], C.c_int),
@@ -605,13 +608,18 @@ def _drag_objective_class():
     class DragObjective(torch.autograd.Function):
         """J(tau0, mu, f) = time-averaged drag of `steps` steps of the solver;
         forward runs ebv_drag_gradient (objective and gradient in one pass),
-        backward scales the stored gradient."""
+        backward scales the stored gradient.  The solver runs at the given
+        tau0 and mu and gets its own parameters back afterwards."""
 
         @staticmethod
         def forward(ctx, tau0, mu, f, solver, u0, p0, dt, steps, every):
+            saved = {"tau0": solver.params["tau0"], "mu": solver.params["mu"]}
             solver.set_params(tau0=float(tau0), mu=float(mu))
-            J, gt, gm, fb = solver.drag_gradient(u0, p0, dt, steps, every, f=f.detach(),
-                                                 f_grad=f.requires_grad)
+            try:
+                J, gt, gm, fb = solver.drag_gradient(u0, p0, dt, steps, every, f=f.detach(),
+                                                     f_grad=f.requires_grad)
+            finally:
+                solver.set_params(**saved)
             ctx.grads = (gt, gm, fb)
             ctx.like = (tau0, mu)
             return torch.tensor(J, dtype=torch.float64)

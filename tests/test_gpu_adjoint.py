@@ -137,12 +137,16 @@ def test_single_step_adjoint_is_the_transpose(E, newtonian, advect, eps, tol):
 
 def test_autograd_function(E):
     w, s, u0, p0, f, dt, fluid = _setup(E, 0)
-    tau0 = torch.tensor(s.params["tau0"], dtype=torch.float64, requires_grad=True)
+    t0 = s.params["tau0"]
+    tau0 = torch.tensor(1.5 * t0, dtype=torch.float64, requires_grad=True)
     mu = torch.tensor(s.params["mu"], dtype=torch.float64, requires_grad=True)
     fr = f.clone().requires_grad_(True)
     J = E.drag_objective(s, tau0, mu, fr, u0, p0, dt, STEPS, EVERY)
     J.backward()
+    assert s.params["tau0"] == t0            # the solver keeps its own parameters
+    s.set_params(tau0=1.5 * t0)
     J2, gt, gm, fb = s.drag_gradient(u0, p0, dt, STEPS, EVERY, f=f)
+    s.set_params(tau0=t0)
     assert float(J.detach()) == J2
     assert float(tau0.grad) == pytest.approx(gt, rel=1e-12)
     assert float(mu.grad) == pytest.approx(gm, rel=1e-12)

@@ -3,8 +3,11 @@ GPU): a NaN in the velocity ends the step's solves with EBV_ERR_NAN (their
 loops stop on a non-finite residual) and the context steps normally from a
 good state afterwards; degenerate geometry gives EBV_ERR_GEOMETRY; an
 allocation past the budget of ebv_set_alloc_limit gives EBV_ERR_OOM with
-nothing left allocated.  Also the step statistics: the relative divergence
-and the per-phase GPU times of an eager step.
+nothing left allocated; a wait of the fused smoother sweep on its tile loads
+that runs out (ebv_set_spin_limit(0): every wait gives up at once, after
+which the kernel lets its loads land and returns) gives EBV_ERR_TIMEOUT and
+the context steps normally afterwards.  Also the step statistics: the
+relative divergence and the per-phase GPU times of an eager step.
 """
 import numpy as np
 import pytest
@@ -88,6 +91,23 @@ def test_allocation_budget_gives_oom_and_nothing_leaks(E):
     assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
     s, u, p, _ = _channel(E)                          # and a context works again
     assert max(s.advance(u, p)["res"]) <= 1e-10
+    s.close()
+
+
+def test_smoother_wait_limit_gives_timeout(E):
+    lib = E.load()
+    s, u, p, _ = _channel(E, n=32, precision=1)      # FP32 levels: 32^3 is smoothed by the fused sweep
+    good_u, good_p = u.clone(), p.clone()
+    lib.ebv_set_spin_limit(0)
+    try:
+        with pytest.raises(E.EbvError) as ei:
+            s.advance(u, p)
+        assert ei.value.status == -4
+    finally:
+        lib.ebv_set_spin_limit(-1)
+    st = s.advance(good_u, good_p)
+    assert max(st["res"]) <= 1e-10
+    assert torch.isfinite(good_u).all()
     s.close()
 
 
