@@ -58,6 +58,9 @@ def parse():
                     help="also time the oracle on the 128^3 sphere channel (minutes)")
     ap.add_argument("--eager", action="store_true",
                     help="issue every step kernel by kernel (no step graph), e.g. under a profiler")
+    ap.add_argument("--fused-sweep", type=int, default=1, choices=[0, 1, 2],
+                    help="smoother sweeps of FP32 levels: 0 colour passes, 1 the faster form per level "
+                         "(timed at set-up, default), 2 the fused one-pass sweep (same results)")
     return ap.parse_args()
 
 
@@ -225,7 +228,7 @@ def measured_peaks():
 # DRAM bytes (read + write) per algorithmic byte, from one ncu capture of the
 # current kernel on a smaller grid (192^3, traffic grows with the cells);
 # the reported traffic is this ratio times the algorithmic bytes per launch.
-NCU_TRAFFIC_RATIO = {"cc_gs_colour_sweep<float> L0": 1.16}
+NCU_TRAFFIC_RATIO = {"cc_gs_colour_pass<float> L0": 1.16, "cc_rb_sweep<float> L0": 1.00}
 
 
 def roofline(prof, cells):
@@ -261,6 +264,7 @@ def run_ours(args, rank, world, local):
     import torch
     from paper_1905_07392_gb300 import build_lib, ebvisc
     build_lib.build()
+    ebvisc.load().ebv_set_fused_sweep(args.fused_sweep)
     dev = torch.device("cuda", local)
     w = workload(args.n)
     cells = w.n ** 3

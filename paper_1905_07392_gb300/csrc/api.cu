@@ -163,9 +163,12 @@ ebv_status viscous_update(Ctx *c, const double *eta, const double *psi, double *
 }
 
 // Nodal projection of ut with old pressure p (in/out), dt on the device.
-ebv_status nodal_projection(Ctx *c, double *ut, double *p, ebv_step_stats *st, int slot)
+// gpa: (dt/rho) grad p stored by the k_psi of the same stage (same p), added
+// back without re-forming it; null forms it from p.
+ebv_status nodal_projection(Ctx *c, double *ut, double *p, ebv_step_stats *st, int slot, const double *gpa = nullptr)
 {
-    TRY(launch_add_gradp(c, ut, p, +1.0));
+    if (gpa) TRY(launch_add_stored(c, ut, gpa));
+    else TRY(launch_add_gradp(c, ut, p, +1.0));
     TRY(launch_nodal_rhs(c, ut, c->rhs_n));
     int it = 0;
     double res = 0.0;
@@ -239,12 +242,12 @@ ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f
     // Predictor
     ph.mark(1, "ebv: predictor derived quantities");
     TRY(derived(c, u, c->Cm, c->em, c->Vm, &loc.iters[0], &loc.res[0], 0));
-    TRY(launch_psi(c, u, c->Cm, c->Vm, p, f, c->psi));
+    TRY(launch_psi(c, u, c->Cm, c->Vm, p, f, c->psi, c->gpa));
     ph.mark(2, "ebv: predictor viscous solves");
     TRY(viscous_update(c, c->em, c->psi, c->ut, &loc, 1));
     ph.mark(3, "ebv: predictor nodal projection");
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->ps, p, NN * 8, cudaMemcpyDeviceToDevice, c->stream));
-    TRY(nodal_projection(c, c->ut, c->ps, &loc, 4));
+    TRY(nodal_projection(c, c->ut, c->ps, &loc, 4, c->gpa));   // c->ps holds p here
     EBV_CUDA_TRY(c, cudaMemcpyAsync(c->us, c->ut, 3 * N3 * 8, cudaMemcpyDeviceToDevice, c->stream));
     // Corrector
     ph.mark(4, "ebv: corrector derived quantities");
@@ -252,12 +255,12 @@ ebv_status advance_impl(Ctx *c, double *u, double *p, double dt, const double *f
     TRY(launch_average(c, c->Cm, c->Cs, (int)(3 * N3)));
     TRY(launch_average(c, c->Vm, c->Vs, (int)(3 * N3)));
     TRY(launch_average(c, c->em, c->es, (int)N3));
-    TRY(launch_psi(c, u, c->Cm, c->Vm, c->ps, f, c->psi));
+    TRY(launch_psi(c, u, c->Cm, c->Vm, c->ps, f, c->psi, c->gpa));
     ph.mark(5, "ebv: corrector viscous solves");
     TRY(viscous_update(c, c->em, c->psi, c->ut, &loc, 6));
     ph.mark(6, "ebv: corrector nodal projection");
     EBV_CUDA_TRY(c, cudaMemcpyAsync(p, c->ps, NN * 8, cudaMemcpyDeviceToDevice, c->stream));
-    TRY(nodal_projection(c, c->ut, p, &loc, 9));
+    TRY(nodal_projection(c, c->ut, p, &loc, 9, c->gpa));      // p holds c->ps here
     EBV_CUDA_TRY(c, cudaMemcpyAsync(u, c->ut, 3 * N3 * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (st) {
         ph.mark(7, "ebv: drag");
@@ -532,7 +535,7 @@ ebv_status ebv_create(const ebv_grid *grid, const ebv_params *params, void *stre
     ok &= alloc(&c->Cm, 3 * N3, as) && alloc(&c->Vm, 3 * N3, as) && alloc(&c->Cs, 3 * N3, as) &&
           alloc(&c->Vs, 3 * N3, as);
     ok &= alloc(&c->em, N3, as) && alloc(&c->es, N3, as) && alloc(&c->psi, 3 * N3, as) &&
-          alloc(&c->ut, 3 * N3, as) && alloc(&c->us, 3 * N3, as);
+          alloc(&c->ut, 3 * N3, as) && alloc(&c->us, 3 * N3, as) && alloc(&c->gpa, 3 * N3, as);
     ok &= alloc(&c->ps, NN, as) && alloc(&c->uf, NF, as) && alloc(&c->phi, N3, as) && alloc(&c->G, 9 * N3, as) &&
           alloc(&c->DC, 3 * N3, as) && alloc(&c->dD, 3 * N3, as) && alloc(&c->Dh, 3 * N3, as) &&
           alloc(&c->wts, N3, as) && alloc(&c->srate, N3, as) && alloc(&c->rhs_c, std::max(N3, (size_t)1), as) &&
@@ -889,7 +892,7 @@ void ebv_destroy(ebv_ctx *c)
                     c->Cs, c->Vs, c->em, c->es, c->psi, c->ut, c->us, c->ps, c->uf, c->phi, c->G, c->DC,
                     c->dD, c->Dh, c->wts, c->dudn, c->srate, c->rhs_c, c->rhs_n, c->u_host_dev, c->p_host_dev,
                     c->dt_dev, c->cfl_max, c->kr, c->kz, c->kp, c->kq, c->part, c->scal, c->nearm,
-                    c->nearl, c->ff, c->kr32, c->kz32, c->kp32, c->kq32, c->ke32};
+                    c->nearl, c->ff, c->kr32, c->kz32, c->kp32, c->kq32, c->ke32, c->gpa};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     CcHier *hs[2] = {&c->mac, &c->visc};

@@ -277,6 +277,7 @@ struct Ctx {
     double *Cm = nullptr, *Vm = nullptr, *Cs = nullptr, *Vs = nullptr;
     double *em = nullptr, *es = nullptr, *psi = nullptr, *ut = nullptr, *us = nullptr;
     double *ps = nullptr, *uf = nullptr, *phi = nullptr, *G = nullptr, *DC = nullptr;
+    double *gpa = nullptr;       // (dt/rho) grad p of the stage's old pressure, for the projection's add-back
     double *dD = nullptr, *Dh = nullptr, *wts = nullptr, *dudn = nullptr, *srate = nullptr;
     double *ff = nullptr;        // face fluxes: 3 components x face triple
     double *rhs_c = nullptr;     // cell rhs scratch
@@ -427,7 +428,8 @@ ebv_status launch_viscous_explicit(Ctx *c, const double *u, const double *eta, c
                                    double *V);
 ebv_status launch_redistribute_into(Ctx *c, const double *DC, double sign, double div, double *out);
 ebv_status launch_psi(Ctx *c, const double *u, const double *C, const double *V, const double *p,
-                      const double *f, double *psi);
+                      const double *f, double *psi, double *gpa = nullptr);
+ebv_status launch_add_stored(Ctx *c, double *u, const double *gpa);
 ebv_status launch_add_gradp(Ctx *c, double *u, const double *p, double coef_sign);
 ebv_status launch_nodal_rhs(Ctx *c, const double *ut, double *b);
 ebv_status launch_timestep(Ctx *c, const double *u, const double *f, double dt_fixed);

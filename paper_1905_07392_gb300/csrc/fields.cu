@@ -590,25 +590,46 @@ __device__ inline void grad_p3(const GridD &g, const double *p, int i, int j, in
     gr[2] = ((P3 + P4) - (P1 + P2)) * q4h;
 }
 
-// psi = rho u + dt (rho C + V - grad p + f)
+// psi = rho u + dt (rho C + V - grad p + f).  With gpa, also (dt/rho) grad p
+// (covered cells 0): the term the nodal projection adds back to the solved
+// velocity, from the same node sums (the values k_add_gradp would form).
 __global__ void k_psi(GridD g, const uint8_t *__restrict__ flag, const double *__restrict__ u,
                       const double *__restrict__ C, const double *__restrict__ V,
                       const double *__restrict__ p, const double *__restrict__ f,
-                      const double *__restrict__ dtp, double rho, double *__restrict__ psi)
+                      const double *__restrict__ dtp, double rho, double *__restrict__ psi,
+                      double *__restrict__ gpa)
 {
     CELL_INDEX
     const int N3 = ncell(g);
     const double dt = *dtp;
     if (flag[c] == 0) {
         for (int q = 0; q < 3; q++) psi[q * N3 + c] = 0.0;
+        if (gpa)
+            for (int q = 0; q < 3; q++) gpa[q * N3 + c] = 0.0;
         return;
     }
-    double gr[3];
-    grad_p3(g, p, i, j, k, 0.25 * g.ih, gr);
+    double sums[3];
+    grad_p3(g, p, i, j, k, 1.0, sums);
+    const double q4h = 0.25 * g.ih, q4a = dtp[DT_DT_RHO] * (0.25 * g.ih);
     for (int q = 0; q < 3; q++) {
         int s = q * N3 + c;
         double fq = f ? f[s] : 0.0;
-        psi[s] = rho * u[s] + dt * (rho * C[s] + V[s] - gr[q] + fq);
+        psi[s] = rho * u[s] + dt * (rho * C[s] + V[s] - sums[q] * q4h + fq);
+        if (gpa) gpa[s] = sums[q] * q4a;
+    }
+}
+
+// u += gpa (the stored (dt/rho) grad p of k_psi) on fluid cells, 0 on covered
+// cells: k_add_gradp(sgn = +1) without re-forming the gradient.
+__global__ void k_add_stored(GridD g, const uint8_t *__restrict__ flag, double *__restrict__ u,
+                             const double *__restrict__ gpa)
+{
+    CELL_INDEX
+    const int N3 = ncell(g);
+    const bool fl = flag[c] != 0;
+    for (int q = 0; q < 3; q++) {
+        const int s = q * N3 + c;
+        u[s] = fl ? u[s] + gpa[s] : 0.0;
     }
 }
 
@@ -642,9 +663,30 @@ __device__ inline bool node_dirichlet(const GridD &g, int i, int j, int k)
     return false;
 }
 
+// Per fluid cell, the four weighted signed sums of its velocity that its 8
+// nodes take (alpha h^2/4 times (ux + uy) + uz, (ux + uy) - uz, (ux - uy) + uz,
+// (ux - uy) - uz): every corner's sum is one of these or its exact negation
+// (IEEE rounding is symmetric), so k_nodal_rhs adds or subtracts them in its
+// corner order with half the FP64 operations of forming each corner's sum
+// itself (each product is rounded before it is added).
+__global__ void k_nodal_cellsums(GridD g, GeomD geo, const double *__restrict__ ut, double *__restrict__ P)
+{
+    CELL_INDEX
+    if (geo.flag[c] == 0) return;
+    const int N3 = ncell(g);
+    const double hq = g.h * g.h * 0.25, w = geo.alpha[c] * hq;
+    const double ux = ut[c], uy = ut[N3 + c], uz = ut[2 * N3 + c];
+    const double pxy = ux + uy, mxy = ux - uy;
+    P[c] = w * (pxy + uz);
+    P[N3 + c] = w * (pxy - uz);
+    P[2 * N3 + c] = w * (mxy + uz);
+    P[3 * N3 + c] = w * (mxy - uz);
+}
+
 // Nodal right-hand side (weak divergence of ut plus the inflow boundary
 // integral), times rho/dt so the solve uses the unit-coefficient operator.
-__global__ void k_nodal_rhs(GridD g, GeomD geo, const double *__restrict__ ut,
+// P: the cell sums of k_nodal_cellsums.
+__global__ void k_nodal_rhs(GridD g, GeomD geo, const double *__restrict__ P,
                             const double *__restrict__ dtp, double *__restrict__ b)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -662,18 +704,20 @@ __global__ void k_nodal_rhs(GridD g, GeomD geo, const double *__restrict__ ut,
         act = any;
     }
     if (!act) { b[n] = 0.0; return; }
-    // per cell: alpha h^2/4 times the signed sum of its three components
-    // (FP64 operations are this GPU's scarce resource: 4 per cell)
-    const double hq = h * h * 0.25;
+    // per cell: alpha h^2/4 times the signed sum of its three components,
+    // (ux + uy) + uz for the corner (i - ci, j - cj, k - ck) = (1, 1, 1) and
+    // so on: sums 0..3 of k_nodal_cellsums, negated for the opposite corners
     double v = 0.0;
     for (int oc = 0; oc < 8; oc++) {
         int ci = i - 1 + (oc & 1), cj = j - 1 + ((oc >> 1) & 1), ck = k - 1 + ((oc >> 2) & 1);
         if (!avail(g, geo.flag, ci, cj, ck)) continue;
-        int c = cidx(g, ci, cj, ck);
-        const double ux = ut[c], uy = ut[N3 + c], uz = ut[2 * N3 + c];
-        const double sxy = (i - ci) ? (j - cj ? ux + uy : ux - uy) : (j - cj ? uy - ux : -ux - uy);
-        const double sc = (k - ck) ? sxy + uz : sxy - uz;
-        v += (geo.alpha[c] * hq) * sc;
+        const int c = cidx(g, ci, cj, ck);
+        const int di = i - ci, dj = j - cj, dk = k - ck;
+        // (di,dj,dk) -> sum: (1,1,1) 0, (1,1,0) 1, (1,0,1) 2, (1,0,0) 3; with di = 0 the
+        // negation of the sum of (1, 1-dj, 1-dk)
+        const int q = di ? (dj ? 0 : 2) + (dk ? 0 : 1) : (dj ? 2 : 0) + (dk ? 1 : 0);
+        const double pc = P[q * N3 + c];
+        v = di ? v + pc : v - pc;
     }
     int id[3] = {i, j, k};
     const double *A[3] = {geo.ax, geo.ay, geo.az};
@@ -949,11 +993,18 @@ ebv_status launch_viscous_explicit(Ctx *c, const double *u, const double *eta, c
 }
 
 ebv_status launch_psi(Ctx *c, const double *u, const double *C, const double *V, const double *p,
-                      const double *f, double *psi)
+                      const double *f, double *psi, double *gpa)
 {
     const GridD &g = c->g;
     EBV_LAUNCH(c, k_psi, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, C, V, p, f, c->dt_dev,
-               c->prm.rho, psi);
+               c->prm.rho, psi, gpa);
+    return EBV_OK;
+}
+
+ebv_status launch_add_stored(Ctx *c, double *u, const double *gpa)
+{
+    const GridD &g = c->g;
+    EBV_LAUNCH(c, k_add_stored, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, gpa);
     return EBV_OK;
 }
 
@@ -967,7 +1018,9 @@ ebv_status launch_add_gradp(Ctx *c, double *u, const double *p, double sgn)
 ebv_status launch_nodal_rhs(Ctx *c, const double *ut, double *b)
 {
     const GridD &g = c->g;
-    EBV_LAUNCH(c, k_nodal_rhs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), ut,
+    double *P = c->G;   // scratch: the velocity gradient is not needed again before the next stage forms it
+    EBV_LAUNCH(c, k_nodal_cellsums, grid3(g.nx, g.ny, g.nz), block3(), 0, g, geomd(c), ut, P);
+    EBV_LAUNCH(c, k_nodal_rhs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), P,
                c->dt_dev, b);
     return EBV_OK;
 }

@@ -357,10 +357,13 @@ __device__ inline void load4(const F *p, float v[4])
 
 // kPz = 1 asks for 5 resident blocks per SM (at most 51 registers), kPz = 2
 // for 4: one plane per thread and more warps, or two and more loads per warp.
-template <int kPz>
+// kCorr: the pass after the coarse-grid correction, as in k_cc_gs (each
+// neighbour value plus its parent's coarse correction xc, level gc).
+template <int kPz, bool kCorr = false>
 __global__ void __launch_bounds__(256, kPz == 1 ? 5 : 4) k_cc_gs4(VOp<float> A, float *__restrict__ x,
                                                                  const float *__restrict__ b, int color,
-                                                                 int zero_start)
+                                                                 int zero_start, const float *__restrict__ xc = nullptr,
+                                                                 GridD gc = GridD())
 {
     using F = typename VFace<float>::type;
     const GridD &g = A.g;
@@ -405,15 +408,25 @@ __global__ void __launch_bounds__(256, kPz == 1 ? 5 : 4) k_cc_gs4(VOp<float> A, 
                 const int t = t0 + m, i = 2 * t + par;
                 const float bxl = float(A.bx[rf + (par ? hf + t : t)]);
                 const float bxh = float(A.bx[rf + (par ? t + 1 : hf + t)]);
-                const float xw = par ? xo[m] : (m ? xo[m - 1] : xb);
-                const float xe = par ? (m < 3 ? xo[m + 1] : xb) : xo[m];
+                float xw = par ? xo[m] : (m ? xo[m - 1] : xb);
+                float xe = par ? (m < 3 ? xo[m + 1] : xb) : xo[m];
+                float ys = xs[m], yn = xn[m], zd = xd[m], zu = xu[m];
+                if constexpr (kCorr) {
+                    auto cor = [&](int ii, int jj, int kq) { return xc[cix<float>(gc, ii >> 1, jj >> 1, kq >> 1)]; };
+                    if (i > 0) xw = xw + cor(i - 1, j, k);
+                    if (i < g.nx - 1) xe = xe + cor(i + 1, j, k);
+                    if (j > 0) ys = ys + cor(i, j - 1, k);
+                    if (j < g.ny - 1) yn = yn + cor(i, j + 1, k);
+                    if (k > 0) zd = zd + cor(i, j, k - 1);
+                    if (k < g.nz - 1) zu = zu + cor(i, j, k + 1);
+                }
                 float s = 0.f;
                 if (i > 0) s += bxl * xw;
                 if (i < g.nx - 1) s += bxh * xe;
-                if (j > 0) s += fy0[m] * xs[m];
-                if (j < g.ny - 1) s += fy1[m] * xn[m];
-                if (k > 0) s += fz0[m] * xd[m];
-                if (k < g.nz - 1) s += fz1[m] * xu[m];
+                if (j > 0) s += fy0[m] * ys;
+                if (j < g.ny - 1) s += fy1[m] * yn;
+                if (k > 0) s += fz0[m] * zd;
+                if (k < g.nz - 1) s += fz1[m] * zu;
                 off[m] = s;
             }
         }
@@ -472,7 +485,7 @@ inline void launch_gs4(cudaStream_t st, dim3 bk, int pz, const VOp<float> &A, fl
 // x_in + the coarse correction of the neighbour's parent (prolongation
 // folded in, as in k_cc_gs).  kDot: also the partial b.x_out of every
 // (plane, tile), part[plane * ntiles + tile], summed over the same cells in
-// the same order as k_cc_dot_tiles, which forms them after colour passes.
+// the same order as k_cc_gs2_dot, which forms them with the colour passes.
 constexpr int RB_TX = 64;                 // tile cells along x
 constexpr int RB_HW = RB_TX / 2;          // half-row positions per tile
 constexpr int RB_TY = 16;                 // tile rows
@@ -846,27 +859,68 @@ __global__ void k_xface_pad(GridD g, const float *__restrict__ bf, F *__restrict
 // The fused sweep's face type: the V-cycle's.
 using RbF = typename VFace<float>::type;
 
-// The (plane, tile) partials of b.x of k_cc_rb_sweep<kDot>, after two colour
-// passes: the same threads, cells, order and sums.  Grid (tiles x, tiles y,
-// nz), RB_THREADS threads.
-__global__ void __launch_bounds__(RB_THREADS) k_cc_dot_tiles(GridD g, const float *__restrict__ b,
-                                                              const float *__restrict__ x, double *__restrict__ part)
+// The second colour pass of a sweep (colour c1, plain) together with the
+// (plane, tile) partials of b.x that k_cc_rb_sweep<kDot> forms: the same
+// threads (positions pq, pq+1 of both halves of a tile row), cells, order
+// and sums, so the colour passes end with the fused sweep's r.z bit for bit.
+// Each c1 cell is formed by the operations of gs_cell; the other colour is
+// read (unchanged by this pass) for the partial.  Grid (tiles x, tiles y, nz).
+__global__ void __launch_bounds__(RB_THREADS) k_cc_gs2_dot(VOp<float> A, float *__restrict__ x,
+                                                            const float *__restrict__ b, int c1,
+                                                            double *__restrict__ part)
 {
     __shared__ double wsum[RB_THREADS / 32];
-    const int tid = threadIdx.x, hx = g.nx >> 1;
+    const GridD &g = A.g;
+    const int tid = threadIdx.x, hx = g.nx >> 1, hf = (g.nx + 2) >> 1;
     const int r = tid >> 4;
     const int j = blockIdx.y * RB_TY + r, pq = blockIdx.x * RB_HW + 2 * (tid & 15), k = blockIdx.z;
     double dsum = 0.0;
     if (j < g.ny && pq < hx) {
-        const size_t o = (size_t)(k * g.ny + j) * g.nx + pq;
-        float d = 0.f;
+        const int h2 = (c1 + j + k) & 1, sy = g.nx, sz = g.nx * g.ny;
+        const int rc = (k * g.ny + j) * g.nx;
+        const int c = rc + (h2 ? hx : 0) + pq, o = rc + (h2 ? 0 : hx) + pq;
+        const float2 bb = *reinterpret_cast<const float2 *>(b + c);
+        const float2 bo = *reinterpret_cast<const float2 *>(b + o);
+        const float2 di = *reinterpret_cast<const float2 *>(A.dinv + c);
+        const float2 xo = *reinterpret_cast<const float2 *>(x + o);
+        const float xb = h2 ? (pq + 2 < hx ? x[o + 2] : 0.f) : (pq > 0 ? x[o - 1] : 0.f);
+        float2 xs = make_float2(0.f, 0.f), xn = xs, xd = xs, xu = xs;
+        if (j > 0) xs = *reinterpret_cast<const float2 *>(x + c - sy);
+        if (j < g.ny - 1) xn = *reinterpret_cast<const float2 *>(x + c + sy);
+        if (k > 0) xd = *reinterpret_cast<const float2 *>(x + c - sz);
+        if (k < g.nz - 1) xu = *reinterpret_cast<const float2 *>(x + c + sz);
+        const float2 fy0 = ld2f(A.by + c + k * g.nx), fy1 = ld2f(A.by + c + k * g.nx + g.nx);
+        const float2 fz0 = ld2f(A.bz + c), fz1 = ld2f(A.bz + c + sz);
+        const float xw2[2] = {h2 ? xo.x : xb, h2 ? xo.y : xo.x};
+        const float xe2[2] = {h2 ? xo.y : xo.x, h2 ? xb : xo.y};
+        const float ys0[2] = {fy0.x, fy0.y}, ys1[2] = {fy1.x, fy1.y}, zs0[2] = {fz0.x, fz0.y}, zs1[2] = {fz1.x, fz1.y};
+        const float vs[2] = {xs.x, xs.y}, vn[2] = {xn.x, xn.y}, vd[2] = {xd.x, xd.y}, vu[2] = {xu.x, xu.y};
+        const float bv[2] = {bb.x, bb.y}, dv[2] = {di.x, di.y};
+        const int rf = rc + k * g.ny + j;
+        float s2[2];
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const float2 bv = *reinterpret_cast<const float2 *>(b + o + h * hx);
-            const float2 xv = *reinterpret_cast<const float2 *>(x + o + h * hx);
-            d += bv.x * xv.x;
-            d += bv.y * xv.y;
+        for (int e = 0; e < 2; e++) {
+            const int t = pq + e, i = 2 * t + h2;
+            const float bxl = float(A.bx[rf + (h2 ? hf + t : t)]);
+            const float bxh = float(A.bx[rf + (h2 ? t + 1 : hf + t)]);
+            float off = 0.f;
+            if (i > 0) off += bxl * xw2[e];
+            if (i < g.nx - 1) off += bxh * xe2[e];
+            if (j > 0) off += ys0[e] * vs[e];
+            if (j < g.ny - 1) off += ys1[e] * vn[e];
+            if (k > 0) off += zs0[e] * vd[e];
+            if (k < g.nz - 1) off += zs1[e] * vu[e];
+            s2[e] = (bv[e] + off) * dv[e];
         }
+        *reinterpret_cast<float2 *>(x + c) = make_float2(s2[0], s2[1]);
+        // b.x over the 4 cells, half 0 then half 1, as k_cc_rb_sweep<kDot>
+        const float b0[2] = {h2 ? bo.x : bb.x, h2 ? bo.y : bb.y}, b1[2] = {h2 ? bb.x : bo.x, h2 ? bb.y : bo.y};
+        const float v0[2] = {h2 ? xo.x : s2[0], h2 ? xo.y : s2[1]}, v1[2] = {h2 ? s2[0] : xo.x, h2 ? s2[1] : xo.y};
+        float d = 0.f;
+        d += b0[0] * v0[0];
+        d += b0[1] * v0[1];
+        d += b1[0] * v1[0];
+        d += b1[1] * v1[1];
         dsum = (double)d;
     }
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
@@ -923,6 +977,71 @@ __global__ void __launch_bounds__(256) k_cc_resid_restrict(VOp<T> A, const T *__
     const int K = blockIdx.z * blockDim.z + threadIdx.z;
     if (I >= gc.nx || J >= gc.ny || K >= gc.nz) return;
     bc[cix<T>(gc, I, J, K)] = rr_cell<T>(A, x, b, I, J, K);
+}
+
+// k_cc_resid_restrict for FP32 levels with nx a multiple of 8: a thread
+// forms coarse cells I0 .. I0+3 (I0 = 4t) of coarse row (J, K).  Their red
+// children lie in one half of each of the 4 fine rows (2J+jj, 2K+kk) -- the
+// half of parity (j + k) & 1 -- at the consecutive positions I0 .. I0+3, so
+// x, b, the diagonal, the y and z neighbours and faces are 16-byte (8-byte
+// BF16) vectors, as in k_cc_gs4.  Children and operations in the order of
+// rr_cell (rows (2J,2K), (2J+1,2K), (2J,2K+1), (2J+1,2K+1)), so the results
+// are the same bits; the coarse values go out as two 8-byte pairs (even and
+// odd coarse cells are the two halves of the coarse row).
+__global__ void __launch_bounds__(256) k_cc_rr4(VOp<float> A, const float *__restrict__ x,
+                                               const float *__restrict__ b, GridD gc, float *__restrict__ bc)
+{
+    const GridD &g = A.g;
+    const int hx = g.nx >> 1, hf = (g.nx + 2) >> 1;
+    const int I0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    if (I0 >= gc.nx || J >= gc.ny || K >= gc.nz) return;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 2; kk++)
+#pragma unroll
+        for (int jj = 0; jj < 2; jj++) {
+            const int j = 2 * J + jj, k = 2 * K + kk, h = (j + k) & 1;
+            const int rc = (k * g.ny + j) * g.nx;
+            const int c = rc + (h ? hx : 0) + I0, o = rc + (h ? 0 : hx) + I0;
+            float xc4[4], bb[4], dg[4], xo[4], xs[4], xn[4], xd[4], xu[4], fy0[4], fy1[4], fz0[4], fz1[4];
+            load4(x + c, xc4);
+            load4(b + c, bb);
+            load4(A.diag + c, dg);
+            load4(x + o, xo);
+            const float xb = h ? (I0 + 4 < hx ? x[o + 4] : 0.f) : (I0 > 0 ? x[o - 1] : 0.f);
+            if (j > 0) load4(x + c - sy, xs);
+            if (j < g.ny - 1) load4(x + c + sy, xn);
+            if (k > 0) load4(x + c - sz, xd);
+            if (k < g.nz - 1) load4(x + c + sz, xu);
+            load4(A.by + c + k * g.nx, fy0);
+            load4(A.by + c + k * g.nx + g.nx, fy1);
+            load4(A.bz + c, fz0);
+            load4(A.bz + c + sz, fz1);
+            const int rf = rc + k * g.ny + j;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int t = I0 + e, i = 2 * t + h;
+                const float bxl = float(A.bx[rf + (h ? hf + t : t)]);
+                const float bxh = float(A.bx[rf + (h ? t + 1 : hf + t)]);
+                const float xw = h ? xo[e] : (e ? xo[e - 1] : xb);
+                const float xe = h ? (e < 3 ? xo[e + 1] : xb) : xo[e];
+                float off = 0.f;
+                if (i > 0) off += bxl * xw;
+                if (i < g.nx - 1) off += bxh * xe;
+                if (j > 0) off += fy0[e] * xs[e];
+                if (j < g.ny - 1) off += fy1[e] * xn[e];
+                if (k > 0) off += fz0[e] * xd[e];
+                if (k < g.nz - 1) off += fz1[e] * xu[e];
+                acc[e] += bb[e] - (dg[e] * xc4[e] - off);
+            }
+        }
+    const int hxc = gc.nx >> 1;
+    float *row = bc + (K * gc.ny + J) * gc.nx;
+    *reinterpret_cast<float2 *>(row + (I0 >> 1)) = make_float2(acc[0] * 0.125f, acc[2] * 0.125f);
+    *reinterpret_cast<float2 *>(row + hxc + (I0 >> 1)) = make_float2(acc[1] * 0.125f, acc[3] * 0.125f);
 }
 
 // Rediscretised coarse operator: face coefficient = (sum of the 4 fine faces) / 16,
@@ -1233,6 +1352,74 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
     }
     const double vs = kRes ? block_sum3_t<float>(vr) : block_sum3_t<T>(v);
     if (thread_linear() == 0) part[block_linear()] = vs;
+}
+
+// k_cc_apply_dot<float> for levels with nx a multiple of 8: a thread forms
+// q = A p at 4 consecutive cells of one half-row (half h = tx / nq) in each of
+// two planes, with 16-byte loads as in k_cc_gs4 (the x faces, rows of nx + 1,
+// as scalars), and adds p.q of its 8 cells to its block's partial.  Each q is
+// formed as in cc_row; the partial sums are grouped by this kernel's fixed
+// block shape (kApply4Blk).
+constexpr int kApply4X = 16, kApply4Y = 8, kApply4Z = 2;
+__global__ void __launch_bounds__(256) k_cc_apply4(CcOp<float> A, const float *__restrict__ p, float *__restrict__ q,
+                                                  double *__restrict__ part)
+{
+    const GridD &g = A.g;
+    const int hx = g.nx >> 1, hf = (g.nx + 2) >> 1, nq = hx >> 2;
+    const int tx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int kk = blockIdx.z * blockDim.z + threadIdx.z;
+    const int sy = g.nx, sz = g.nx * g.ny;
+    float v = 0.f;
+    if (tx < 2 * nq && j < g.ny) {
+        const int h = tx / nq, t0 = 4 * (tx - h * nq);
+#pragma unroll
+        for (int hp = 0; hp < 2; hp++) {
+            const int k = 2 * kk + hp;
+            if (k >= g.nz) continue;
+            const int rc = (k * g.ny + j) * g.nx;
+            const int c = rc + (h ? hx : 0) + t0, o = rc + (h ? 0 : hx) + t0;
+            float pc[4], dg[4], xo[4], xs[4], xn[4], xd[4], xu[4], fy0[4], fy1[4], fz0[4], fz1[4], y[4];
+            load4(p + c, pc);
+            load4(A.diag + c, dg);
+            load4(p + o, xo);
+            const float xb = h ? (t0 + 4 < hx ? p[o + 4] : 0.f) : (t0 > 0 ? p[o - 1] : 0.f);
+            if (j > 0) load4(p + c - sy, xs);
+            if (j < g.ny - 1) load4(p + c + sy, xn);
+            if (k > 0) load4(p + c - sz, xd);
+            if (k < g.nz - 1) load4(p + c + sz, xu);
+            load4(A.by + c + k * g.nx, fy0);
+            load4(A.by + c + k * g.nx + g.nx, fy1);
+            load4(A.bz + c, fz0);
+            load4(A.bz + c + sz, fz1);
+            const int rf = rc + k * g.ny + j;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int t = t0 + e, i = 2 * t + h;
+                const float bxl = A.bx[rf + (h ? hf + t : t)];
+                const float bxh = A.bx[rf + (h ? t + 1 : hf + t)];
+                const float xw = h ? xo[e] : (e ? xo[e - 1] : xb);
+                const float xe = h ? (e < 3 ? xo[e + 1] : xb) : xo[e];
+                float off = 0.f;
+                if (i > 0) off += bxl * xw;
+                if (i < g.nx - 1) off += bxh * xe;
+                if (j > 0) off += fy0[e] * xs[e];
+                if (j < g.ny - 1) off += fy1[e] * xn[e];
+                if (k > 0) off += fz0[e] * xd[e];
+                if (k < g.nz - 1) off += fz1[e] * xu[e];
+                y[e] = dg[e] * pc[e] - off;
+                v += pc[e] * y[e];
+            }
+            *reinterpret_cast<float4 *>(q + c) = make_float4(y[0], y[1], y[2], y[3]);
+        }
+    }
+    const double vs = block_sum3_t<float>(v);
+    if (thread_linear() == 0) part[block_linear()] = vs;
+}
+inline dim3 apply4_grid(const GridD &g)
+{
+    const int nq2 = 2 * ((g.nx >> 1) >> 2), nzh = (g.nz + 1) / 2;
+    return dim3((nq2 + kApply4X - 1) / kApply4X, (g.ny + kApply4Y - 1) / kApply4Y, (nzh + kApply4Z - 1) / kApply4Z);
 }
 
 // ===========================================================================
@@ -2354,13 +2541,24 @@ NdOp<T> ndop(const NdLevel &L)
 
 // Profiler names of the colour sweeps, by precision and level (level 0 is
 // HBM-bound; the coarse levels are latency- and launch-bound).
+// Profiling labels of the colour passes per precision and level: plain
+// passes (from zero or not), the pass after the coarse correction, and the
+// pass that also forms r.z.
 static const char *const kGsName[2][8] = {
-    {"cc_gs_colour_sweep<double> L0", "cc_gs_colour_sweep<double> L1", "cc_gs_colour_sweep<double> L2",
-     "cc_gs_colour_sweep<double> L3", "cc_gs_colour_sweep<double> L4", "cc_gs_colour_sweep<double> L5",
-     "cc_gs_colour_sweep<double> L6", "cc_gs_colour_sweep<double> L7+"},
-    {"cc_gs_colour_sweep<float> L0", "cc_gs_colour_sweep<float> L1", "cc_gs_colour_sweep<float> L2",
-     "cc_gs_colour_sweep<float> L3", "cc_gs_colour_sweep<float> L4", "cc_gs_colour_sweep<float> L5",
-     "cc_gs_colour_sweep<float> L6", "cc_gs_colour_sweep<float> L7+"}};
+    {"cc_gs_colour_pass<double> L0", "cc_gs_colour_pass<double> L1", "cc_gs_colour_pass<double> L2",
+     "cc_gs_colour_pass<double> L3", "cc_gs_colour_pass<double> L4", "cc_gs_colour_pass<double> L5",
+     "cc_gs_colour_pass<double> L6", "cc_gs_colour_pass<double> L7+"},
+    {"cc_gs_colour_pass<float> L0", "cc_gs_colour_pass<float> L1", "cc_gs_colour_pass<float> L2",
+     "cc_gs_colour_pass<float> L3", "cc_gs_colour_pass<float> L4", "cc_gs_colour_pass<float> L5",
+     "cc_gs_colour_pass<float> L6", "cc_gs_colour_pass<float> L7+"}};
+static const char *const kGsCorrName[2][8] = {
+    {"cc_gs_correction_pass<double> L0", "cc_gs_correction_pass<double> L1", "cc_gs_correction_pass<double> L2",
+     "cc_gs_correction_pass<double> L3", "cc_gs_correction_pass<double> L4", "cc_gs_correction_pass<double> L5",
+     "cc_gs_correction_pass<double> L6", "cc_gs_correction_pass<double> L7+"},
+    {"cc_gs_correction_pass<float> L0", "cc_gs_correction_pass<float> L1", "cc_gs_correction_pass<float> L2",
+     "cc_gs_correction_pass<float> L3", "cc_gs_correction_pass<float> L4", "cc_gs_correction_pass<float> L5",
+     "cc_gs_correction_pass<float> L6", "cc_gs_correction_pass<float> L7+"}};
+static const char *const kGsDotName[2] = {"cc_gs_rz_pass<double> L0", "cc_gs_rz_pass<float> L0"};
 
 // Two red-black Gauss-Seidel sweeps in place (the first from x = 0 when
 // zero_start), each as two colour passes.
@@ -2513,7 +2711,7 @@ const char *const kRbName[8] = {"cc_rb_sweep<float> L0", "cc_rb_sweep<float> L1"
 // pair as the V-cycle uses it: sweep 1 (from zero, or after the coarse
 // correction) then sweep 2 (plain, or with r.z partials).
 // dot_part: the last pass also writes partials of b.x -- per (plane, tile)
-// (k_cc_rb_sweep<kDot> or k_cc_dot_tiles) on levels the fused sweep applies
+// (k_cc_rb_sweep<kDot> or k_cc_gs2_dot) on levels the fused sweep applies
 // to, else per block of k_cc_gs<kDot>; returns their number (0 without
 // dot_part).  FP32 levels with nx a multiple of 16 can run each sweep as one
 // fused pass (x -> t -> x) or as two colour passes, with the same results bit
@@ -2576,28 +2774,42 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
             }
             EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false>), gr, bk, 0, A, x, b, color, zs, nullptr, GridD());
         };
-        if (s == 0 && xc)  // the first pass after the coarse-grid correction (+ the coarse array)
-            EBV_LAUNCH_P(c, name, nb + 0.125 * sizeof(T) * (double)ncell(g), (k_cc_gs<T, true>), gr, bk, 0, A, x, b,
-                         c0, z, xc, *gc);
+        if (s == 0 && xc) {  // the first pass after the coarse-grid correction (+ the coarse array)
+            const char *nmc = kGsCorrName[sizeof(T) == 4][l < 7 ? l : 7];
+            const double nbc = nb + 0.125 * sizeof(T) * (double)ncell(g);
+            bool done = false;
+            if constexpr (sizeof(T) == 4) {
+                if (gs4_ok(g)) {   // vectorised, same results
+                    if (L.gs4_pz == 1)
+                        EBV_LAUNCH_P(c, nmc, nbc, (k_cc_gs4<1, true>), gs4_grid(g, L.gs4_blk, 1), L.gs4_blk, 0, A, x, b,
+                                     c0, z, xc, *gc);
+                    else
+                        EBV_LAUNCH_P(c, nmc, nbc, (k_cc_gs4<2, true>), gs4_grid(g, L.gs4_blk, 2), L.gs4_blk, 0, A, x, b,
+                                     c0, z, xc, *gc);
+                    done = true;
+                }
+            }
+            if (!done) EBV_LAUNCH_P(c, nmc, nbc, (k_cc_gs<T, true>), gr, bk, 0, A, x, b, c0, z, xc, *gc);
+        }
         else
             plain(c0, z);
-        if (s == 1 && dot_part && !tiles)
+        if (s == 1 && dot_part && tiles) {
+            // the fused sweep's r.z partials, per (plane, tile), with the last pass
+            if constexpr (sizeof(T) == 4) {
+                const dim3 gt((g.nx / 2 + RB_HW - 1) / RB_HW, (g.ny + RB_TY - 1) / RB_TY, g.nz);
+                EBV_LAUNCH_P(c, kGsDotName[1], nb, k_cc_gs2_dot, gt, dim3(RB_THREADS), 0, A, x, b, 1 - c0, dot_part);
+                return (int)(gt.x * gt.y * gt.z);
+            }
+        } else if (s == 1 && dot_part) {
             // fixed block shape: the grouping of its partial sums must not
             // follow the autotuned shape, or results would depend on timing
-            EBV_LAUNCH_P(c, name, nb, (k_cc_gs<T, false, true>), gs_grid(g, block3()), block3(), 0, A, x, b, 1 - c0,
-                         0, nullptr, GridD(), dot_part);
-        else
+            EBV_LAUNCH_P(c, kGsDotName[sizeof(T) == 4], nb, (k_cc_gs<T, false, true>), gs_grid(g, block3()), block3(),
+                         0, A, x, b, 1 - c0, 0, nullptr, GridD(), dot_part);
+        } else {
             plain(1 - c0, 0);
-    }
-    if (!dot_part) return 0;
-    if constexpr (sizeof(T) == 4) {
-        if (tiles) {
-            const dim3 gt((g.nx / 2 + RB_HW - 1) / RB_HW, (g.ny + RB_TY - 1) / RB_TY, g.nz);
-            EBV_LAUNCH_P(c, "cc_dot_tiles", 8.0 * (double)ncell(g), k_cc_dot_tiles, gt, dim3(RB_THREADS), 0, g,
-                         (const float *)b, (const float *)x, dot_part);
-            return (int)(gt.x * gt.y * gt.z);
         }
     }
+    if (!dot_part) return 0;
     const dim3 gd = gs_grid(g, block3());
     return (int)(gd.x * gd.y * gd.z);
 }
@@ -2619,10 +2831,20 @@ int cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0, double *dot_part = nullptr)
         cc_smooth2<T>(c, L, l, x, (T *)c->lt[l], b, true, true);
         const CcLevel &Lc = H.lv[l + 1];
         // x, b, diagonal, 3 faces (storage type) read, 1/8 word written
-        EBV_LAUNCH_P(c, sizeof(T) == 4 ? "cc_residual_restrict<float>" : "cc_residual_restrict<double>",
-                     ((3.0 + 1.0 / 8.0) * sizeof(T) + 3.0 * sizeof(typename VFace<T>::type)) * (double)ncell(L.g),
-                     k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, vop<T>(L), x, b, Lc.g,
-                     (T *)c->lb[l + 1]);
+        const double nbr = ((3.0 + 1.0 / 8.0) * sizeof(T) + 3.0 * sizeof(typename VFace<T>::type)) * (double)ncell(L.g);
+        const char *nmr = sizeof(T) == 4 ? "cc_residual_restrict<float>" : "cc_residual_restrict<double>";
+        bool vec = false;
+        if constexpr (sizeof(T) == 4) {
+            if (gs4_ok(L.g)) {   // four coarse cells per thread, vector loads (same results)
+                const dim3 bk(8, 8, 4), gr((Lc.g.nx / 4 + bk.x - 1) / bk.x, (Lc.g.ny + bk.y - 1) / bk.y,
+                                            (Lc.g.nz + bk.z - 1) / bk.z);
+                EBV_LAUNCH_P(c, nmr, nbr, k_cc_rr4, gr, bk, 0, vop<float>(L), x, b, Lc.g, (float *)c->lb[l + 1]);
+                vec = true;
+            }
+        }
+        if (!vec)
+            EBV_LAUNCH_P(c, nmr, nbr, k_cc_resid_restrict<T>, cgrid(Lc.g), block3(), 0, vop<T>(L), x, b, Lc.g,
+                         (T *)c->lb[l + 1]);
     }
     if (l0 < Lb) {
         CoarseVC<T> D;
@@ -3040,10 +3262,17 @@ struct CcProblem : Problem {
         EBV_LAUNCH_P(c, "cc_apply_fp64", 48.0 * n(), k_cc_apply_dot<double>, agrid(), block3(), 0,
                      ccop<double>(H->lv[0]), p, q, c->part);
     }
+    // FP32 levels with nx a multiple of 8: the vectorised apply (its own partials)
+    bool vec32() const { return gs4_ok(H->lv[0].g); }
+    int apply_blocks32() const override { return vec32() ? nblocks3(apply4_grid(H->lv[0].g)) : apply_blocks(); }
     void apply_dot32(Ctx *c, const float *p, float *q) override
     {
-        EBV_LAUNCH_P(c, "cc_apply_fp32", 24.0 * n(), k_cc_apply_dot<float>, agrid(), block3(), 0,
-                     ccop<float>(H->lv[0]), p, q, c->part);
+        if (vec32())
+            EBV_LAUNCH_P(c, "cc_apply_fp32", 24.0 * n(), k_cc_apply4, apply4_grid(H->lv[0].g),
+                         dim3(kApply4X, kApply4Y, kApply4Z), 0, ccop<float>(H->lv[0]), p, q, c->part);
+        else
+            EBV_LAUNCH_P(c, "cc_apply_fp32", 24.0 * n(), k_cc_apply_dot<float>, agrid(), block3(), 0,
+                         ccop<float>(H->lv[0]), p, q, c->part);
     }
     void precond(Ctx *c, const double *r, double *z) override { cc_vcycle<double>(c, *H, r, z); }
     void precond32(Ctx *c, const float *r, float *z) override { cc_vcycle<float>(c, *H, r, z); }
@@ -3442,12 +3671,16 @@ ebv_status autotune_shapes_t(Ctx *c)
                                   kind == RB_DOT ? c->part : nullptr, L.rb_kz);
                     });
                     const float ms_p = time_it([&]() {
-                        if (kind == RB_CORR)
-                            k_cc_gs<T, true><<<grc, bk, 0, c->stream>>>(A, x, b, 0, 0, d, gc);
+                        if (kind == RB_CORR) {
+                            if (L.gs4_pz == 1)
+                                k_cc_gs4<1, true><<<gs4_grid(L.g, L.gs4_blk, 1), L.gs4_blk, 0, c->stream>>>(A, x, b, 0, 0, d, gc);
+                            else
+                                k_cc_gs4<2, true><<<gs4_grid(L.g, L.gs4_blk, 2), L.gs4_blk, 0, c->stream>>>(A, x, b, 0, 0, d, gc);
+                        }
                         else
                             launch_gs4(c->stream, L.gs4_blk, L.gs4_pz, A, x, b, 0, kind == RB_ZERO ? 1 : 0);
-                        launch_gs4(c->stream, L.gs4_blk, L.gs4_pz, A, x, b, 1, 0);
-                        if (kind == RB_DOT) k_cc_dot_tiles<<<gt, RB_THREADS, 0, c->stream>>>(L.g, b, x, c->part);
+                        if (kind == RB_DOT) k_cc_gs2_dot<<<gt, RB_THREADS, 0, c->stream>>>(A, x, b, 1, c->part);
+                        else launch_gs4(c->stream, L.gs4_blk, L.gs4_pz, A, x, b, 1, 0);
                     });
                     L.rb_ms[kind][0] = ms_f;
                     L.rb_ms[kind][1] = ms_p;
