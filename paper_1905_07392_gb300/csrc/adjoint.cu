@@ -2,8 +2,12 @@
 // convective term): for each forward kernel of the step, a kernel that takes
 // the adjoint of its outputs and adds the adjoint of its inputs.  Each mirrors its forward
 // kernel's stencil (same branches, same weights); where the forward kernel
-// gathers from several cells the reverse one scatters with FP64 atomics, or
-// gathers the transposed stencil where that is as simple.
+// gathers from several cells the reverse one gathers the transposed stencil
+// where that is as simple, or scatters with plain additions in launches that
+// no two threads' targets overlap in: faces of one position parity, cells of
+// one colour of a map that is one-to-one on the stencil's offsets, cut cells
+// of one colour of a greedy colouring by shared stencil cells.  No atomics,
+// so the gradients are bitwise reproducible.
 //
 // Forward kernel            reverse kernel here
 //   k_strain_eta              k_se_adj            (eta(||gamma||) and G = grad u)
@@ -20,6 +24,7 @@
 //   k_mac_rhs / k_mac_correct k_mac_rhs_adj / k_mac_correct_adj (with one MAC solve)
 //   k_conv_flux               k_conv_flux_adj
 #include <algorithm>
+#include <unordered_map>
 
 #include "ebv_internal.cuh"
 
@@ -143,19 +148,25 @@ __device__ inline double block_sum_lin(double v)
 
 // ---- strain rate + viscosity -------------------------------------------------
 // In: eta_bar (per cell), G_bar (9 per cell, or NULL).  Adds the adjoint of u
-// to u_bar (atomics); block partial sums of eta_bar d eta/d tau0 and
-// eta_bar d eta/d mu to part[b], part[nblocks + b].
+// to u_bar; block partial sums of eta_bar d eta/d tau0 and eta_bar d eta/d mu
+// to part[b], part[nblocks + b].  One launch per colour (i + 3j + 4k) mod 13:
+// a cell scatters to itself and to its neighbours at distance 1 and 2 along
+// each axis, and that map is one-to-one on those 13 offsets mod 13, so cells
+// of one colour never share a target and plain additions, in launch order,
+// make the result bitwise reproducible.
+constexpr int kSeColours = 13;
+__device__ inline int se_colour(int i, int j, int k) { return (i + 3 * j + 4 * k) % kSeColours; }
 __global__ void __launch_bounds__(256) k_se_adj(GridD g, const uint8_t *__restrict__ flag,
                                                 const double *__restrict__ u, ParamsD p,
                                                 const double *__restrict__ eta_bar,
                                                 const double *__restrict__ G_bar, double *__restrict__ u_bar,
-                                                double *__restrict__ part)
+                                                double *__restrict__ part, int colour)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     double vt = 0.0, vm = 0.0;
-    if (i < g.nx && j < g.ny && k < g.nz) {
+    if (i < g.nx && j < g.ny && k < g.nz && se_colour(i, j, k) == colour) {
         const int c = cidx(g, i, j, k);
         const int N3 = ncell(g);
         if (flag[c] != 0) {
@@ -211,7 +222,7 @@ __global__ void __launch_bounds__(256) k_se_adj(GridD g, const uint8_t *__restri
                     double gb = sb * (Gm[d][q] + Gm[q][d]);
                     if (G_bar) gb += G_bar[(3 * d + q) * N3 + c];
                     if (gb == 0.0) continue;
-                    for (int r = 0; r < cnt[d]; r++) atomicAdd(&u_bar[q * N3 + idx[d][r]], w[d][r] * gb);
+                    for (int r = 0; r < cnt[d]; r++) u_bar[q * N3 + idx[d][r]] += w[d][r] * gb;
                 }
         }
     }
@@ -226,70 +237,117 @@ __global__ void __launch_bounds__(256) k_se_adj(GridD g, const uint8_t *__restri
 }
 
 // ---- wall-normal derivative (Eq. dudn) -----------------------------------------
-__global__ void k_wall_dudn_adj(GridD g, GeomD geo, const double *__restrict__ dudn_bar, double *__restrict__ u_bar)
+// The stencil of cut cell t (the entries of geo.cut) for the wall-normal
+// derivative, as k_wall_dudn forms it: with ok, 18 cells (two 3 x 3 planes
+// along the normal's dominant axis); else, with near_ok, the one cell near.
+struct WallSten {
+    int kax, k1, k2, si, cc1[2], cc2[2], near[3], ci[3];
+    double dist[2], L1[2][3], L2[2][3];
+    bool ok, near_ok;
+};
+__device__ inline WallSten wall_stencil(const GridD &g, const GeomD &geo, int c)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= geo.ncut) return;
+    WallSten w;
     const int N3 = geo.ncell;
-    const int c = geo.cut[t];
-    int ci[3] = {c % g.nx, (c / g.nx) % g.ny, c / (g.nx * g.ny)};
+    w.ci[0] = c % g.nx; w.ci[1] = (c / g.nx) % g.ny; w.ci[2] = c / (g.nx * g.ny);
     double n[3], b[3];
     for (int e = 0; e < 3; e++) { n[e] = geo.nrm[e * N3 + c]; b[e] = geo.bcen[e * N3 + c]; }
     int kax = 0;
     if (fabs(n[1]) > fabs(n[kax])) kax = 1;
     if (fabs(n[2]) > fabs(n[kax])) kax = 2;
-    const int k1 = (kax == 0) ? 1 : 0, k2 = (kax == 2) ? 1 : 2;
+    w.kax = kax;
+    w.k1 = (kax == 0) ? 1 : 0;
+    w.k2 = (kax == 2) ? 1 : 2;
     const double s = n[kax] > 0.0 ? 1.0 : -1.0;
-    const int si = n[kax] > 0.0 ? 1 : -1;
-    const double dist[2] = {(s - b[kax]) / n[kax], (2.0 * s - b[kax]) / n[kax]};
-    int cc1[2], cc2[2];
-    double L1[2][3], L2[2][3];
-    bool ok = true;
+    w.si = n[kax] > 0.0 ? 1 : -1;
+    w.dist[0] = (s - b[kax]) / n[kax];
+    w.dist[1] = (2.0 * s - b[kax]) / n[kax];
+    w.ok = true;
     for (int m = 0; m < 2; m++) {
-        double P1 = b[k1] + dist[m] * n[k1], P2 = b[k2] + dist[m] * n[k2];
-        cc1[m] = (int)floor(P1 + 0.5);
-        cc2[m] = (int)floor(P2 + 0.5);
-        double x1 = P1 - cc1[m], x2 = P2 - cc2[m];
-        L1[m][0] = 0.5 * x1 * (x1 - 1.0); L1[m][1] = 1.0 - x1 * x1; L1[m][2] = 0.5 * x1 * (x1 + 1.0);
-        L2[m][0] = 0.5 * x2 * (x2 - 1.0); L2[m][1] = 1.0 - x2 * x2; L2[m][2] = 0.5 * x2 * (x2 + 1.0);
-        for (int q1 = -1; q1 <= 1 && ok; q1++)
+        double P1 = b[w.k1] + w.dist[m] * n[w.k1], P2 = b[w.k2] + w.dist[m] * n[w.k2];
+        w.cc1[m] = (int)floor(P1 + 0.5);
+        w.cc2[m] = (int)floor(P2 + 0.5);
+        double x1 = P1 - w.cc1[m], x2 = P2 - w.cc2[m];
+        w.L1[m][0] = 0.5 * x1 * (x1 - 1.0); w.L1[m][1] = 1.0 - x1 * x1; w.L1[m][2] = 0.5 * x1 * (x1 + 1.0);
+        w.L2[m][0] = 0.5 * x2 * (x2 - 1.0); w.L2[m][1] = 1.0 - x2 * x2; w.L2[m][2] = 0.5 * x2 * (x2 + 1.0);
+        if (!w.ok) continue;
+        for (int q1 = -1; q1 <= 1 && w.ok; q1++)
             for (int q2 = -1; q2 <= 1; q2++) {
                 int id[3];
-                id[kax] = ci[kax] + (m + 1) * si;
-                id[k1] = ci[k1] + cc1[m] + q1;
-                id[k2] = ci[k2] + cc2[m] + q2;
-                if (!avail(g, geo.flag, id[0], id[1], id[2])) { ok = false; break; }
+                id[kax] = w.ci[kax] + (m + 1) * w.si;
+                id[w.k1] = w.ci[w.k1] + w.cc1[m] + q1;
+                id[w.k2] = w.ci[w.k2] + w.cc2[m] + q2;
+                if (!avail(g, geo.flag, id[0], id[1], id[2])) { w.ok = false; break; }
             }
-        if (!ok) break;
     }
-    int near[3];
-    near[kax] = ci[kax] + si;
+    w.near[kax] = w.ci[kax] + w.si;
     {
-        double P1 = b[k1] + dist[0] * n[k1], P2 = b[k2] + dist[0] * n[k2];
-        near[k1] = ci[k1] + (int)floor(P1 + 0.5);
-        near[k2] = ci[k2] + (int)floor(P2 + 0.5);
+        double P1 = b[w.k1] + w.dist[0] * n[w.k1], P2 = b[w.k2] + w.dist[0] * n[w.k2];
+        w.near[w.k1] = w.ci[w.k1] + (int)floor(P1 + 0.5);
+        w.near[w.k2] = w.ci[w.k2] + (int)floor(P2 + 0.5);
     }
-    const bool near_ok = avail(g, geo.flag, near[0], near[1], near[2]);
-    const double d1 = dist[0], d2 = dist[1];
+    w.near_ok = avail(g, geo.flag, w.near[0], w.near[1], w.near[2]);
+    return w;
+}
+__device__ inline int wall_cell(const GridD &g, const WallSten &w, int m, int q1, int q2)
+{
+    int id[3];
+    id[w.kax] = w.ci[w.kax] + (m + 1) * w.si;
+    id[w.k1] = w.ci[w.k1] + w.cc1[m] + q1;
+    id[w.k2] = w.ci[w.k2] + w.cc2[m] + q2;
+    return cidx(g, id[0], id[1], id[2]);
+}
+
+// The cells each cut cell's stencil touches (kWallTargets per cut cell, -1
+// unused): the host colours the cut cells so that no two of one colour share
+// a target.
+constexpr int kWallTargets = 18;
+__global__ void k_wall_targets(GridD g, GeomD geo, int *__restrict__ tgt)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= geo.ncut) return;
+    int *o = tgt + (size_t)t * kWallTargets;
+    for (int r = 0; r < kWallTargets; r++) o[r] = -1;
+    const int c = geo.cut[t];
+    if (c < 0 || c >= geo.ncell) return;
+    const WallSten w = wall_stencil(g, geo, c);
+    if (w.ok) {
+        int r = 0;
+        for (int m = 0; m < 2; m++)
+            for (int q1 = -1; q1 <= 1; q1++)
+                for (int q2 = -1; q2 <= 1; q2++) o[r++] = wall_cell(g, w, m, q1, q2);
+    } else if (w.near_ok) {
+        o[0] = cidx(g, w.near[0], w.near[1], w.near[2]);
+    }
+}
+
+// One colour of cut cells (list[0 .. n)): no two share a target, so plain
+// additions, colour after colour, make u_bar bitwise reproducible.
+__global__ void k_wall_dudn_adj(GridD g, GeomD geo, const int *__restrict__ list, int n,
+                                const double *__restrict__ dudn_bar, double *__restrict__ u_bar)
+{
+    const int s_ = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s_ >= n) return;
+    const int t = list[s_];
+    const int N3 = geo.ncell;
+    const int c = geo.cut[t];
+    if (c < 0 || c >= N3) return;
+    const WallSten w = wall_stencil(g, geo, c);
+    const double d1 = w.dist[0], d2 = w.dist[1];
     for (int q = 0; q < 3; q++) {
         const double rb = dudn_bar[q * geo.ncut + t];
         if (rb == 0.0) continue;
         double *ubq = u_bar + q * N3;
-        if (ok) {
+        if (w.ok) {
             // r = (d2^2 uv0 - d1^2 uv1) / (d1 d2 (d2 - d1)) / h
             const double den = d1 * d2 * (d2 - d1);
             const double cm[2] = {d2 * d2 / den / g.h, -d1 * d1 / den / g.h};
             for (int m = 0; m < 2; m++)
                 for (int q1 = -1; q1 <= 1; q1++)
-                    for (int q2 = -1; q2 <= 1; q2++) {
-                        int id[3];
-                        id[kax] = ci[kax] + (m + 1) * si;
-                        id[k1] = ci[k1] + cc1[m] + q1;
-                        id[k2] = ci[k2] + cc2[m] + q2;
-                        atomicAdd(&ubq[cidx(g, id[0], id[1], id[2])], cm[m] * L1[m][q1 + 1] * L2[m][q2 + 1] * rb);
-                    }
-        } else if (near_ok) {
-            atomicAdd(&ubq[cidx(g, near[0], near[1], near[2])], rb / (dist[0] * g.h));
+                    for (int q2 = -1; q2 <= 1; q2++)
+                        ubq[wall_cell(g, w, m, q1, q2)] += cm[m] * w.L1[m][q1 + 1] * w.L2[m][q2 + 1] * rb;
+        } else if (w.near_ok) {
+            ubq[cidx(g, w.near[0], w.near[1], w.near[2])] += rb / (d1 * g.h);
         }
     }
 }
@@ -301,13 +359,15 @@ __global__ void __launch_bounds__(256) k_visc_flux_adj(GridD g, int d, const dou
                                                        const double *__restrict__ G,
                                                        const double *__restrict__ Fb, int nft, int off,
                                                        double *__restrict__ u_bar, double *__restrict__ eta_bar,
-                                                       double *__restrict__ G_bar)
+                                                       double *__restrict__ G_bar, int colour)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
     if (i >= mx || j >= my || k >= mz) return;
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    if ((pos & 1) != colour) return;   // faces of one parity share no cell: plain additions
     const int f = fidx(g, d, i, j, k);
     const int N3 = ncell(g);
     const double a = ap[f];
@@ -315,7 +375,6 @@ __global__ void __launch_bounds__(256) k_visc_flux_adj(GridD g, int d, const dou
     double fb[3];
     for (int jj = 0; jj < 3; jj++) fb[jj] = Fb[jj * nft + off + f];
     if (fb[0] == 0.0 && fb[1] == 0.0 && fb[2] == 0.0) return;
-    const int pos = d == 0 ? i : (d == 1 ? j : k);
     int3 e = unit3(d);
     const double ih = g.ih;
     if (pos == 0 || pos == dimn(g, d)) {
@@ -327,17 +386,17 @@ __global__ void __launch_bounds__(256) k_visc_flux_adj(GridD g, int d, const dou
             // F_d = a eta_c (hs ? val - u_d : u_d - val) 2 / h
             const double ud = u[d * N3 + c];
             const double T = (hs ? (val - ud) : (ud - val)) * (2.0 * ih);
-            atomicAdd(&eta_bar[c], a * fb[d] * T);
-            atomicAdd(&u_bar[d * N3 + c], a * fb[d] * eta[c] * (hs ? -1.0 : 1.0) * (2.0 * ih));
+            eta_bar[c] += a * fb[d] * T;
+            u_bar[d * N3 + c] += a * fb[d] * eta[c] * (hs ? -1.0 : 1.0) * (2.0 * ih);
         } else {
             // F_jj = a eta_c G[(3 jj + d)] for jj != d
             double eb = 0.0;
             for (int jj = 0; jj < 3; jj++) {
                 if (jj == d) continue;
                 eb += fb[jj] * G[(3 * jj + d) * N3 + c];
-                atomicAdd(&G_bar[(3 * jj + d) * N3 + c], a * eta[c] * fb[jj]);
+                G_bar[(3 * jj + d) * N3 + c] += a * eta[c] * fb[jj];
             }
-            atomicAdd(&eta_bar[c], a * eb);
+            eta_bar[c] += a * eb;
         }
         return;
     }
@@ -350,15 +409,15 @@ __global__ void __launch_bounds__(256) k_visc_flux_adj(GridD g, int d, const dou
         efb += a * fb[jj] * der;
         const double derb = a * ef * fb[jj];
         if (jj == d) {
-            atomicAdd(&u_bar[d * N3 + cR], derb * ih);
-            atomicAdd(&u_bar[d * N3 + cL], -derb * ih);
+            u_bar[d * N3 + cR] += derb * ih;
+            u_bar[d * N3 + cL] += -derb * ih;
         } else {
-            atomicAdd(&G_bar[(3 * jj + d) * N3 + cL], 0.5 * derb);
-            atomicAdd(&G_bar[(3 * jj + d) * N3 + cR], 0.5 * derb);
+            G_bar[(3 * jj + d) * N3 + cL] += 0.5 * derb;
+            G_bar[(3 * jj + d) * N3 + cR] += 0.5 * derb;
         }
     }
-    atomicAdd(&eta_bar[cL], 0.5 * efb);
-    atomicAdd(&eta_bar[cR], 0.5 * efb);
+    eta_bar[cL] += 0.5 * efb;
+    eta_bar[cR] += 0.5 * efb;
 }
 
 // ---- conservative divergence of a face flux triple ------------------------
@@ -584,15 +643,19 @@ __global__ void k_nodal_rhs_t(GridD g, GeomD geo, const uint8_t *__restrict__ ac
 }
 
 // ---- drag (Eq. drag-force): adjoints of eta, du/dn and p, times wJ ---------------
+// One launch per parity colour of the cut cell ((i & 1) + 2 (j & 1) + 4 (k & 1)):
+// cells of one parity share no node, so the pressure adjoint takes plain
+// additions (each cut cell's own entries are its alone).
 __global__ void k_drag_adj(GridD g, GeomD geo, const double *__restrict__ eta, const double *__restrict__ dudn,
                            double wJ, double *__restrict__ eta_bar, double *__restrict__ dudn_bar,
-                           double *__restrict__ p_bar)
+                           double *__restrict__ p_bar, int colour)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= geo.ncut) return;
     const int N3 = geo.ncell;
     const int c = geo.cut[t];
     const int i = c % g.nx, j = (c / g.nx) % g.ny, k = c / (g.nx * g.ny);
+    if ((i & 1) + 2 * (j & 1) + 4 * (k & 1) != colour) return;
     double n[3], b[3], gq[3];
     for (int e = 0; e < 3; e++) {
         n[e] = geo.nrm[e * N3 + c];
@@ -607,7 +670,7 @@ __global__ void k_drag_adj(GridD g, GeomD geo, const double *__restrict__ eta, c
         const int oi = o & 1, oj = (o >> 1) & 1, ok = (o >> 2) & 1;
         const double w = (oi ? b[0] + 0.5 : 0.5 - b[0]) * (oj ? b[1] + 0.5 : 0.5 - b[1]) *
                          (ok ? b[2] + 0.5 : 0.5 - b[2]);
-        atomicAdd(&p_bar[nidx(g, i + oi, j + oj, k + ok)], -F * n[2] * w);
+        p_bar[nidx(g, i + oi, j + oj, k + ok)] += -F * n[2] * w;
     }
 }
 
@@ -643,11 +706,16 @@ __device__ inline void mc_slope_w(const GridD &g, const uint8_t *flag, const dou
     else { w[2] = 2.0; w[1] = -2.0; }
 }
 
+// One launch per colour (i + 2j + 3k) mod 7: a cell's slopes read itself and
+// its two neighbours along each axis, and that map is one-to-one on those 7
+// offsets mod 7, so cells of one colour share no target (plain additions).
+constexpr int kSlopeColours = 7;
 __global__ void __launch_bounds__(256) k_slopes_adj(GridD g, const uint8_t *__restrict__ flag,
                                                     const double *__restrict__ u, const double *__restrict__ Sb,
-                                                    double *__restrict__ ub)
+                                                    double *__restrict__ ub, int colour)
 {
     ADJ_CELL
+    if ((i + 2 * j + 3 * k) % kSlopeColours != colour) return;
     if (!flag[c]) return;
     const int N3 = ncell(g);
     for (int d = 0; d < 3; d++)
@@ -658,7 +726,7 @@ __global__ void __launch_bounds__(256) k_slopes_adj(GridD g, const uint8_t *__re
             double w[3];
             mc_slope_w(g, flag, u + q * N3, i, j, k, d, idx, w);
             for (int r = 0; r < 3; r++)
-                if (w[r] != 0.0) atomicAdd(&ub[q * N3 + idx[r]], w[r] * sb);
+                if (w[r] != 0.0) ub[q * N3 + idx[r]] += w[r] * sb;
         }
 }
 
@@ -668,19 +736,20 @@ __global__ void __launch_bounds__(256) k_conv_flux_adj(GridD g, int d, const dou
                                                        const double *__restrict__ uFd,
                                                        const double *__restrict__ Fb, int nft, int off,
                                                        double *__restrict__ ub, double *__restrict__ Sb,
-                                                       double *__restrict__ uFbd)
+                                                       double *__restrict__ uFbd, int colour)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
     if (i >= mx || j >= my || k >= mz) return;
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    if ((pos & 1) != colour) return;   // faces of one parity share no cell: plain additions
     const int f = fidx(g, d, i, j, k);
     const int N3 = ncell(g);
     const double a = ap[f];
     if (a <= 0.0) { uFbd[f] = 0.0; return; }
     const double w = uFd[f];
-    const int pos = d == 0 ? i : (d == 1 ? j : k);
     int3 e = unit3(d);
     double wb = 0.0;
     if (pos == 0 || pos == dimn(g, d)) {
@@ -691,7 +760,7 @@ __global__ void __launch_bounds__(256) k_conv_flux_adj(GridD g, int d, const dou
             const double fb = Fb[q * nft + off + f];
             const double state = in ? g.u_in[q] : u[q * N3 + c];
             wb += a * state * fb;
-            if (!in) atomicAdd(&ub[q * N3 + c], a * w * fb);
+            if (!in) ub[q * N3 + c] += a * w * fb;
         }
         uFbd[f] = wb;
         return;
@@ -706,12 +775,12 @@ __global__ void __launch_bounds__(256) k_conv_flux_adj(GridD g, int d, const dou
         const double stb = a * w * fb;
         const double wl = w > 0.0 ? 1.0 : (w < 0.0 ? 0.0 : 0.5), wr = 1.0 - wl;
         if (wl != 0.0 && stb != 0.0) {
-            atomicAdd(&ub[q * N3 + cL], wl * stb);
-            atomicAdd(&Sb[(3 * d + q) * N3 + cL], 0.5 * wl * stb);
+            ub[q * N3 + cL] += wl * stb;
+            Sb[(3 * d + q) * N3 + cL] += 0.5 * wl * stb;
         }
         if (wr != 0.0 && stb != 0.0) {
-            atomicAdd(&ub[q * N3 + cR], wr * stb);
-            atomicAdd(&Sb[(3 * d + q) * N3 + cR], -0.5 * wr * stb);
+            ub[q * N3 + cR] += wr * stb;
+            Sb[(3 * d + q) * N3 + cR] += -0.5 * wr * stb;
         }
     }
     uFbd[f] = wb;
@@ -777,35 +846,36 @@ __global__ void k_mac_rhs_adj(GridD g, int d, const uint8_t *__restrict__ flag, 
 __global__ void __launch_bounds__(256) k_face_states_adj(GridD g, int d, const double *__restrict__ ap,
                                                          const double *__restrict__ u, const double *__restrict__ S,
                                                          const double *__restrict__ ufbd, double *__restrict__ ub,
-                                                         double *__restrict__ Sb)
+                                                         double *__restrict__ Sb, int colour)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
     const int mx = g.nx + (d == 0), my = g.ny + (d == 1), mz = g.nz + (d == 2);
     if (i >= mx || j >= my || k >= mz) return;
+    const int pos = d == 0 ? i : (d == 1 ? j : k);
+    if ((pos & 1) != colour) return;   // faces of one parity share no cell: plain additions
     const int f = fidx(g, d, i, j, k);
     if (!(ap[f] > 0.0)) return;
     const double fb = ufbd[f];
     if (fb == 0.0) return;
     const int N3 = ncell(g);
-    const int pos = d == 0 ? i : (d == 1 ? j : k);
     int3 e = unit3(d);
     if (pos == 0 || pos == dimn(g, d)) {
         const int hs = pos != 0;
         if (g.bc[2 * d + hs] == EBV_OUTFLOW)
-            atomicAdd(&ub[d * N3 + cidx(g, i - hs * e.x, j - hs * e.y, k - hs * e.z)], fb);
+            ub[d * N3 + cidx(g, i - hs * e.x, j - hs * e.y, k - hs * e.z)] += fb;
         return;
     }
     const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
     const double uL = u[d * N3 + cL] + 0.5 * S[(3 * d + d) * N3 + cL];
     const double uR = u[d * N3 + cR] - 0.5 * S[(3 * d + d) * N3 + cR];
     if (uL > 0.0 && uL + uR > 0.0) {
-        atomicAdd(&ub[d * N3 + cL], fb);
-        atomicAdd(&Sb[(3 * d + d) * N3 + cL], 0.5 * fb);
+        ub[d * N3 + cL] += fb;
+        Sb[(3 * d + d) * N3 + cL] += 0.5 * fb;
     } else if (uR < 0.0 && uL + uR < 0.0) {
-        atomicAdd(&ub[d * N3 + cR], fb);
-        atomicAdd(&Sb[(3 * d + d) * N3 + cR], -0.5 * fb);
+        ub[d * N3 + cR] += fb;
+        Sb[(3 * d + d) * N3 + cR] += -0.5 * fb;
     }
 }
 
@@ -896,15 +966,80 @@ ebv_status adj_strain_eta(Ctx *c, const double *u, const double *eta_bar, const 
     const dim3 gr = grid3(g.nx, g.ny, g.nz);
     const int nb = gr.x * gr.y * gr.z;
     if (2 * (size_t)nb > ((size_t)1 << 20)) return c->fail(EBV_ERR_INVALID, "grid too large for the partial sums");
-    EBV_LAUNCH(c, k_se_adj, gr, block3(), 0, g, c->flag, u, paramsd(c->prm), eta_bar, G_bar, u_bar, c->part);
-    EBV_LAUNCH(c, k_sum2, dim3(1), dim3(1024), 0, c->part, nb, grads_dev);
+    for (int q = 0; q < kSeColours; q++) {   // colour by colour, each reduced in turn (fixed order)
+        EBV_LAUNCH(c, k_se_adj, gr, block3(), 0, g, c->flag, u, paramsd(c->prm), eta_bar, G_bar, u_bar, c->part,
+                   q);
+        EBV_LAUNCH(c, k_sum2, dim3(1), dim3(1024), 0, c->part, nb, grads_dev);
+    }
+    return EBV_OK;
+}
+
+// Colours of the cut cells for the wall-gradient adjoint, once per geometry:
+// greedy in cut-list order, a cell takes the first colour no earlier cell
+// sharing one of its stencil cells has; the lists hold each colour's cut
+// indices in ascending order.
+ebv_status wall_colouring(Ctx *c)
+{
+    if (c->wall_col_ok) return EBV_OK;
+    const int n = c->ncut;
+    c->wall_col_off.assign(1, 0);
+    if (c->wall_col) cudaFree(c->wall_col);
+    c->wall_col = nullptr;
+    if (n) {
+        int *tgt_dev = nullptr;
+        EBV_CUDA_TRY(c, dev_malloc((void **)&tgt_dev, (size_t)n * kWallTargets * sizeof(int)));
+        EBV_LAUNCH(c, k_wall_targets, dim3((n + 127) / 128), dim3(128), 0, c->g, geomd(c), tgt_dev);
+        std::vector<int> tgt((size_t)n * kWallTargets);
+        cudaError_t e = cudaMemcpyAsync(tgt.data(), tgt_dev, tgt.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(tgt_dev);
+        EBV_CUDA_TRY(c, e);
+        std::unordered_map<int, std::vector<int>> used;   // stencil cell -> colours of the cut cells touching it
+        std::vector<int> col(n);
+        int ncol = 0;
+        std::vector<char> taken;
+        for (int t = 0; t < n; t++) {
+            taken.assign(ncol + 1, 0);
+            for (int r = 0; r < kWallTargets; r++) {
+                const int x = tgt[(size_t)t * kWallTargets + r];
+                if (x < 0) continue;
+                auto it = used.find(x);
+                if (it != used.end())
+                    for (int q : it->second) taken[q] = 1;
+            }
+            int q = 0;
+            while (taken[q]) q++;
+            col[t] = q;
+            ncol = std::max(ncol, q + 1);
+            for (int r = 0; r < kWallTargets; r++) {
+                const int x = tgt[(size_t)t * kWallTargets + r];
+                if (x >= 0) used[x].push_back(q);
+            }
+        }
+        c->wall_col_off.assign(ncol + 1, 0);
+        for (int t = 0; t < n; t++) c->wall_col_off[col[t] + 1]++;
+        for (int q = 0; q < ncol; q++) c->wall_col_off[q + 1] += c->wall_col_off[q];
+        std::vector<int> list(n), pos(c->wall_col_off.begin(), c->wall_col_off.end() - 1);
+        for (int t = 0; t < n; t++) list[pos[col[t]]++] = t;
+        EBV_CUDA_TRY(c, dev_malloc((void **)&c->wall_col, (size_t)n * sizeof(int)));
+        EBV_CUDA_TRY(c, cudaMemcpy(c->wall_col, list.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    c->wall_col_ok = true;
     return EBV_OK;
 }
 
 ebv_status adj_wall_dudn(Ctx *c, const double *dudn_bar, double *u_bar)
 {
-    if (c->ncut)
-        EBV_LAUNCH(c, k_wall_dudn_adj, dim3((c->ncut + 127) / 128), dim3(128), 0, c->g, geomd(c), dudn_bar, u_bar);
+    if (!c->ncut) return EBV_OK;
+    const ebv_status st = wall_colouring(c);
+    if (st != EBV_OK) return st;
+    const int nc = (int)c->wall_col_off.size() - 1;
+    for (int q = 0; q < nc; q++) {
+        const int n = c->wall_col_off[q + 1] - c->wall_col_off[q];
+        EBV_LAUNCH(c, k_wall_dudn_adj, dim3((n + 127) / 128), dim3(128), 0, c->g, geomd(c),
+                   c->wall_col + c->wall_col_off[q], n, dudn_bar, u_bar);
+    }
     return EBV_OK;
 }
 
@@ -951,8 +1086,9 @@ ebv_status adj_viscous_explicit(Ctx *c, const double *u, const double *eta, cons
     // face fluxes
     off = 0;
     for (int d = 0; d < 3; d++) {
-        EBV_LAUNCH(c, k_visc_flux_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
-                   A[d], u, eta, G, Fb, nft, off, u_bar, eta_bar, G_bar);
+        for (int q = 0; q < 2; q++)   // even, then odd face positions
+            EBV_LAUNCH(c, k_visc_flux_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g,
+                       d, A[d], u, eta, G, Fb, nft, off, u_bar, eta_bar, G_bar, q);
         off += nface(g, d);
     }
     return EBV_OK;
@@ -984,8 +1120,9 @@ ebv_status adj_convective(Ctx *c, const double *u, const double *S, const double
     // fluxes: to u, S and the projected face velocities
     EBV_CUDA_TRY(c, cudaMemsetAsync(Sb, 0, 9 * (size_t)N3 * sizeof(double), c->stream));
     for (int d = 0; d < 3; d++)
-        EBV_LAUNCH(c, k_conv_flux_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
-                   A[d], u, S, uF + offs[d], Fb, nft, offs[d], ub, Sb, uFb + offs[d]);
+        for (int q = 0; q < 2; q++)   // even, then odd face positions
+            EBV_LAUNCH(c, k_conv_flux_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g,
+                       d, A[d], u, S, uF + offs[d], Fb, nft, offs[d], ub, Sb, uFb + offs[d], q);
     // MAC projection: phi_bar, the adjoint solve, then the face divergence
     EBV_LAUNCH(c, k_mac_correct_adj, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->ax, c->ay, c->az, uFb, phib);
     int it = 0;
@@ -998,9 +1135,11 @@ ebv_status adj_convective(Ctx *c, const double *u, const double *S, const double
                    c->flag, A[d], bb, uFb + offs[d]);
     // face states and slopes
     for (int d = 0; d < 3; d++)
-        EBV_LAUNCH(c, k_face_states_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0, g, d,
-                   A[d], u, S, uFb + offs[d], ub, Sb);
-    EBV_LAUNCH(c, k_slopes_adj, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, Sb, ub);
+        for (int q = 0; q < 2; q++)   // even, then odd face positions
+            EBV_LAUNCH(c, k_face_states_adj, grid3(g.nx + (d == 0), g.ny + (d == 1), g.nz + (d == 2)), block3(), 0,
+                       g, d, A[d], u, S, uFb + offs[d], ub, Sb, q);
+    for (int q = 0; q < kSlopeColours; q++)
+        EBV_LAUNCH(c, k_slopes_adj, grid3(g.nx, g.ny, g.nz), block3(), 0, g, c->flag, u, Sb, ub, q);
     return EBV_OK;
 }
 
@@ -1031,8 +1170,9 @@ ebv_status adj_nodal_rhs_t(Ctx *c, const double *rb, double *ub)
 ebv_status adj_drag(Ctx *c, const double *eta, double wJ, double *eta_bar, double *dudn_bar, double *p_bar)
 {
     if (c->ncut)
-        EBV_LAUNCH(c, k_drag_adj, dim3((c->ncut + 127) / 128), dim3(128), 0, c->g, geomd(c), eta, c->dudn, wJ,
-                   eta_bar, dudn_bar, p_bar);
+        for (int q = 0; q < 8; q++)   // parity colours of the cut cells
+            EBV_LAUNCH(c, k_drag_adj, dim3((c->ncut + 127) / 128), dim3(128), 0, c->g, geomd(c), eta, c->dudn, wJ,
+                       eta_bar, dudn_bar, p_bar, q);
     return EBV_OK;
 }
 

@@ -892,7 +892,7 @@ void ebv_destroy(ebv_ctx *c)
                     c->Cs, c->Vs, c->em, c->es, c->psi, c->ut, c->us, c->ps, c->uf, c->phi, c->G, c->DC,
                     c->dD, c->Dh, c->wts, c->dudn, c->srate, c->rhs_c, c->rhs_n, c->u_host_dev, c->p_host_dev,
                     c->dt_dev, c->cfl_max, c->kr, c->kz, c->kp, c->kq, c->part, c->scal, c->nearm,
-                    c->nearl, c->ff, c->kr32, c->kz32, c->kp32, c->kq32, c->ke32, c->gpa};
+                    c->nearl, c->ff, c->kr32, c->kz32, c->kp32, c->kq32, c->ke32, c->gpa, c->wall_col};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     CcHier *hs[2] = {&c->mac, &c->visc};

@@ -320,6 +320,11 @@ struct Ctx {
     // adjoint workspace (allocated by the first adjoint call)
     double *adj = nullptr;
     size_t adj_len = 0;
+    // the cut cells by colour for the wall-gradient adjoint (built on first
+    // use per geometry): wall_col[wall_col_off[q] .. wall_col_off[q+1]) colour q
+    int *wall_col = nullptr;
+    std::vector<int> wall_col_off;
+    bool wall_col_ok = false;
     // the captured step (one graph launch = one step)
     cudaGraphExec_t step_exec = nullptr;
     const void *gkey_u = nullptr, *gkey_p = nullptr, *gkey_f = nullptr;

@@ -521,6 +521,7 @@ ebv_status install_geometry(Ctx *c, HostGeom &H)
     }
     EBV_CUDA_TRY(c, cudaStreamSynchronize(s));
     c->have_geom = true;
+    c->wall_col_ok = false;   // the wall-gradient adjoint's colouring follows the geometry
     return EBV_OK;
 }
 

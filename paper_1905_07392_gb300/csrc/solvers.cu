@@ -1361,6 +1361,9 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
 // formed as in cc_row; the partial sums are grouped by this kernel's fixed
 // block shape (kApply4Blk).
 constexpr int kApply4X = 16, kApply4Y = 8, kApply4Z = 2;
+// The vectorised apply and restriction serve grids where they launch at least
+// this many blocks (two per SM of 152); smaller grids keep one cell per thread.
+constexpr long long kVecMinBlocks = 304;
 __global__ void __launch_bounds__(256) k_cc_apply4(CcOp<float> A, const float *__restrict__ p, float *__restrict__ q,
                                                   double *__restrict__ part)
 {
@@ -2835,9 +2838,11 @@ int cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0, double *dot_part = nullptr)
         const char *nmr = sizeof(T) == 4 ? "cc_residual_restrict<float>" : "cc_residual_restrict<double>";
         bool vec = false;
         if constexpr (sizeof(T) == 4) {
-            if (gs4_ok(L.g)) {   // four coarse cells per thread, vector loads (same results)
-                const dim3 bk(8, 8, 4), gr((Lc.g.nx / 4 + bk.x - 1) / bk.x, (Lc.g.ny + bk.y - 1) / bk.y,
-                                            (Lc.g.nz + bk.z - 1) / bk.z);
+            const dim3 bk(8, 8, 4), gr((Lc.g.nx / 4 + bk.x - 1) / bk.x, (Lc.g.ny + bk.y - 1) / bk.y,
+                                        (Lc.g.nz + bk.z - 1) / bk.z);
+            // four coarse cells per thread, vector loads (same results), where
+            // that still gives two blocks per SM (small levels keep the scalar kernel)
+            if (gs4_ok(L.g) && (long long)gr.x * gr.y * gr.z >= kVecMinBlocks) {
                 EBV_LAUNCH_P(c, nmr, nbr, k_cc_rr4, gr, bk, 0, vop<float>(L), x, b, Lc.g, (float *)c->lb[l + 1]);
                 vec = true;
             }
@@ -3262,8 +3267,12 @@ struct CcProblem : Problem {
         EBV_LAUNCH_P(c, "cc_apply_fp64", 48.0 * n(), k_cc_apply_dot<double>, agrid(), block3(), 0,
                      ccop<double>(H->lv[0]), p, q, c->part);
     }
-    // FP32 levels with nx a multiple of 8: the vectorised apply (its own partials)
-    bool vec32() const { return gs4_ok(H->lv[0].g); }
+    // FP32 levels with nx a multiple of 8 large enough for two blocks per SM:
+    // the vectorised apply (its own partials; the choice follows the grid only)
+    bool vec32() const
+    {
+        return gs4_ok(H->lv[0].g) && nblocks3(apply4_grid(H->lv[0].g)) >= kVecMinBlocks;
+    }
     int apply_blocks32() const override { return vec32() ? nblocks3(apply4_grid(H->lv[0].g)) : apply_blocks(); }
     void apply_dot32(Ctx *c, const float *p, float *q) override
     {

@@ -10,7 +10,8 @@ initial state, checkpointing every 2 steps.  With the convective term the
 limiter and the upwinding are piecewise linear: the seeded noise of the
 initial state keeps their decisions away from ties (a uniform flow would sit
 on the limiter's kink in every cell), so no kink lies within a difference
-step."""
+step.  The reverse kernels scatter with plain additions in a fixed order (no
+atomics), so the gradients of two runs agree bit for bit."""
 import numpy as np
 import pytest
 
@@ -223,3 +224,13 @@ def test_drag_gradient_matches_dual_oracle(E, dual_case, precision):
     assert gm == pytest.approx(ref["mu"], rel=1e-8), (gm, ref["mu"])
     gf = float(torch.dot(fb, _t(df)))
     assert gf == pytest.approx(ref["f"], rel=1e-8), (gf, ref["f"])
+
+
+@pytest.mark.parametrize("advect", [0, 1])
+def test_gradients_bitwise_reproducible(E, advect):
+    w, s, u0, p0, f, dt, fluid = _setup(E, 0, advect=advect)
+    runs = [s.drag_gradient(u0, p0, dt, STEPS, EVERY, f=f) for _ in range(2)]
+    (J1, gt1, gm1, fb1), (J2, gt2, gm2, fb2) = runs
+    assert J1 == J2 and gt1 == gt2 and gm1 == gm2
+    assert torch.equal(fb1, fb2)
+    s.close()
