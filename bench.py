@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-fp32-faces", action="store_true")
+    ap.add_argument("--skip-mixed", action="store_true")
     ap.add_argument("--skip-config2", action="store_true")
     ap.add_argument("--skip-paper", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=CPU_SAMPLE_N,
@@ -309,6 +310,9 @@ def run_ours(args, rank, world, local):
            "yield_frac": st["yield_frac"]}
     s.close()
 
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    ref64 = None   # (u, p, stats) of the FP64 path after the timed steps, for the other forms
     if not args.skip_fp64:
         s64 = make_solver(w, ebvisc.FP64)
         u64, p64 = initial_state(s64, w, dev)
@@ -320,8 +324,7 @@ def run_ours(args, rank, world, local):
                        "solve_iters_last_step": st64["iters"]}
         # error of the FP32-smoother path against FP64 after the same steps
         # from the same seeded state
-        def rel(a, b):
-            return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        ref64 = (u64, p64, st64)
         out["fp32_vs_fp64"] = {"steps": args.warmup + args.steps, "u_rel_l2": rel(u, u64),
                                "p_rel_l2": rel(p, p64),
                                "drag_rel": abs(st["drag"] - st64["drag"]) / abs(st64["drag"])}
@@ -344,6 +347,35 @@ def run_ours(args, rank, world, local):
                                      "(library build variant EBV_VCYCLE_FP32_FACES); headline uses BF16"}
         sf.close()
         del uf, pf
+
+    if not args.skip_mixed:
+        # FP32_MIXED: the same path with the strain rate and viscosity of the
+        # cells away from the EB in FP32; its error against FP64 after the same
+        # steps, and the strain-rate kernel's achieved bandwidth (eager profile)
+        sm = make_solver(w, ebvisc.FP32_MIXED)
+        um, pm = initial_state(sm, w, dev)
+        secm, _, _ = time_steps(sm, um, pm, args.steps, args.warmup, world, graph=True)
+        secm = max_over_ranks(secm, world)
+        stm = sm.advance(um.clone(), pm.clone(), stats=True)
+        ue, pe = initial_state(sm, w, dev)
+        _, _, profm = time_steps(sm, ue, pe, 2, 1, world, profile=True)
+        del ue, pe
+        mix = {"value": round(job_value(cells, args.steps, world, secm), 3), "unit": UNIT,
+               "ms_per_step": round(1e3 * secm / args.steps, 3), "solve_iters_last_step": stm["iters"]}
+        k5 = profm.get("strain_rate_viscosity")
+        if k5 and k5["launches"] > 0:
+            gbs = k5["bytes"] / (k5["ms"] * 1e-3) / 1e9
+            mix["strain_rate_viscosity"] = {"ms_per_launch": round(k5["ms"] / k5["launches"], 4),
+                                            "GB/s": round(gbs, 1), "frac": round(gbs / measured_peaks()[0], 4)}
+        if ref64 is not None:
+            u64, p64, st64 = ref64
+            mix["vs_fp64"] = {"steps": args.warmup + args.steps, "u_rel_l2": rel(um, u64), "p_rel_l2": rel(pm, p64),
+                              "drag_rel": abs(stm["drag"] - st64["drag"]) / abs(st64["drag"])}
+        mix["note"] = ("precision EBV_FP32_MIXED: as the headline, with the strain rate and apparent viscosity "
+                       "of cells away from the EB formed in FP32 from FP64 velocity differences")
+        out["fp32_mixed"] = mix
+        sm.close()
+        del um, pm
 
     if not args.skip_config2:
         out["config2"] = run_config2(dev)
@@ -429,15 +461,19 @@ def steady_creeping(s, u, p, dt_mult=100.0, max_steps=300, rtol=1e-7):
     """Creeping-flow steps (advect = 0) at dt_mult times the CFL step of the
     initial state until the drag changes by less than rtol; the viscous
     update is implicit, so the large step only speeds up the approach to the
-    steady state, which is the same at any step size.  Returns (stats, steps)."""
+    steady state, which is the same at any step size.  Returns (stats, steps,
+    the last step's relative drag change): steps == max_steps with a change
+    above rtol means the cap ended the run."""
     dt = s.timestep(u) * dt_mult
-    prev = None
+    prev, rel = None, float("nan")
     for k in range(max_steps):
         st = s.advance(u, p, dt=dt)
-        if prev is not None and abs(st["drag"] - prev) <= rtol * abs(st["drag"]):
-            return st, k + 1
+        if prev is not None:
+            rel = abs(st["drag"] - prev) / abs(st["drag"])
+            if rel <= rtol:
+                return st, k + 1, rel
         prev = st["drag"]
-    return st, max_steps
+    return st, max_steps, rel
 
 
 def run_paper_workloads(dev, cells_per_d=16):
@@ -470,27 +506,28 @@ def run_paper_workloads(dev, cells_per_d=16):
     n = (4 * npd, npd // 2, 6 * npd)
     s, u, p = make(n, (W.INFLOW, W.INFLOW, W.SLIP, W.SLIP, W.INFLOW, W.INFLOW),
                    [(E.BODY_CYLINDER, (1, 2 * D, 3 * D, D / 2))])
-    st, k = steady_creeping(s, u, p)
+    st, k, rel = steady_creeping(s, u, p)
     cd = st["drag"] / (1.0 * 1.0 * n[1] * h)
     out["cylinder_newtonian"] = {"C_D": cd, "faxen_C_D": faxen_cd(0.25), "rel_diff": cd / faxen_cd(0.25) - 1.0,
-                                 "steps": k, "cells": n[0] * n[1] * n[2]}
+                                 "steps": k, "last_rel_change": rel, "cells": n[0] * n[1] * n[2]}
     s.close()
     n, hh = W.sphere_box_grid(npd, D)
     for bi in (0.0, 10.0):
         tau0 = W.tau0_for_bingham(bi, D / 2)
         s, u, p = make(n, (W.INFLOW,) * 6, [(E.BODY_SPHERE, (2 * D, 2 * D, 3 * D, D / 2))], tau0,
                        E.BINGHAM if bi > 0 else E.NEWTONIAN)
-        st, k = steady_creeping(s, u, p)
+        st, k, rel = steady_creeping(s, u, p)
         out[f"sphere_box_bi{bi:g}"] = {"C_S": st["drag"] / (6.0 * math.pi * 1.0 * 1.0 * D / 2),
-                                      "yield_frac": st["yield_frac"], "steps": k, "cells": n[0] * n[1] * n[2]}
+                                      "yield_frac": st["yield_frac"], "steps": k, "last_rel_change": rel,
+                                      "cells": n[0] * n[1] * n[2]}
         s.close()
     sph, cube = W.sphere_cube_bodies(D)
     s, u, p = make(n, (W.INFLOW,) * 6, [(E.BODY_SPHERE, sph), (E.BODY_BOX, cube)], W.tau0_for_bingham(10.0, D / 2),
                    E.BINGHAM)
-    st, k = steady_creeping(s, u, p)
+    st, k, rel = steady_creeping(s, u, p)
     lam, dev_ = s.flow_diagnostics(u)
     fluid = s.geometry()["alpha"] > 0
-    out["sphere_cube_bi10"] = {"F_D": st["drag"], "yield_frac": st["yield_frac"], "steps": k,
+    out["sphere_cube_bi10"] = {"F_D": st["drag"], "yield_frac": st["yield_frac"], "steps": k, "last_rel_change": rel,
                                "lambda_mean": float(lam[fluid].mean()),
                                "unyielded_by_stress_dev": float((dev_[fluid] <= 1e-3).double().mean())}
     s.close()

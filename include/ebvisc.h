@@ -68,7 +68,15 @@ enum { EBV_NEWTONIAN = 0, EBV_BINGHAM = 1, EBV_HERSCHEL_BULKLEY = 2, EBV_POWER_L
  * conjugate gradients with an FP32 multigrid preconditioner whose V-cycle
  * stores its cell-centred face coefficients in BF16; both converge to
  * ebv_params.tol.  Geometry and every field are FP64 in both. */
-enum { EBV_FP64 = 0, EBV_FP32_REFINE = 1 };
+/* Precision forms.  EBV_FP32_REFINE: every linear solve is iterative
+ * refinement, FP64 residual and solution around FP32 conjugate gradients and
+ * an FP32 multigrid V-cycle; everything else FP64.  EBV_FP32_MIXED: the same,
+ * and the strain rate and apparent viscosity of fluid cells away from the EB
+ * (neither cut nor next to a cut cell, all six neighbours fluid) are formed in
+ * FP32 from FP64 velocity differences, the near-wall ones in FP64 (results
+ * within about 1e-7 of FP64 rather than 1e-10; the adjoint differentiates the
+ * FP64 formula). */
+enum { EBV_FP64 = 0, EBV_FP32_REFINE = 1, EBV_FP32_MIXED = 2 };
 
 typedef struct {
     int n[3];        /* cells per direction; each even down to the multigrid bottom */
@@ -94,7 +102,7 @@ typedef struct {
                          a cell centre behind the EB plane counts as this close to the wall
                          (0.01 in the bindings; larger values under-enforce no-slip in small
                          cut cells and raise the drag) */
-    int precision;    /* EBV_FP64 or EBV_FP32_REFINE */
+    int precision;    /* EBV_FP64, EBV_FP32_REFINE or EBV_FP32_MIXED */
     int advect;       /* 1: Algorithm 1 as printed; 0: creeping flow, the convective term C = 0
                          (the paper's evaluation runs at Re = 1e-3, Sec. "Cylinder moving through
                          Bingham fluid"); the adjoint (ebv_adjoint_step) follows either */
@@ -293,7 +301,9 @@ void ebv_set_spin_limit(long long cycles);
 /* How FP32 multigrid levels whose x size is a multiple of 16 run a red-black
  * sweep: 0 as two colour passes, 1 (default) as whichever of the two colour
  * passes and the fused one-pass sweep was faster when the context's solvers
- * were set up, 2 always as the fused sweep.  All give the same results bit
+ * were set up (instances of an ebv_batch keep the colour passes: their steps
+ * run side by side, where a lone kernel's time does not decide), 2 always as
+ * the fused sweep.  All give the same results bit
  * for bit; the switch exists to show that and to measure the difference.
  * Process-wide; read when a step is issued or captured. */
 void ebv_set_fused_sweep(int mode);

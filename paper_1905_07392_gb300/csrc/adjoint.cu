@@ -162,9 +162,11 @@ __global__ void __launch_bounds__(256) k_se_adj(GridD g, const uint8_t *__restri
                                                 const double *__restrict__ G_bar, double *__restrict__ u_bar,
                                                 double *__restrict__ part, int colour)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // thread x index t covers the cell of this colour i = i0 + 13 t of row (j, k)
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z * blockDim.z + threadIdx.z;
+    const int i0 = ((colour - 3 * j - 4 * k) % kSeColours + kSeColours) % kSeColours;
+    const int i = i0 + kSeColours * (int)(blockIdx.x * blockDim.x + threadIdx.x);
     double vt = 0.0, vm = 0.0;
     if (i < g.nx && j < g.ny && k < g.nz && se_colour(i, j, k) == colour) {
         const int c = cidx(g, i, j, k);
@@ -963,7 +965,7 @@ ebv_status adj_strain_eta(Ctx *c, const double *u, const double *eta_bar, const 
                           double *grads_dev)
 {
     const GridD &g = c->g;
-    const dim3 gr = grid3(g.nx, g.ny, g.nz);
+    const dim3 gr = grid3((g.nx + kSeColours - 1) / kSeColours, g.ny, g.nz);   // one colour's cells per launch
     const int nb = gr.x * gr.y * gr.z;
     if (2 * (size_t)nb > ((size_t)1 << 20)) return c->fail(EBV_ERR_INVALID, "grid too large for the partial sums");
     for (int q = 0; q < kSeColours; q++) {   // colour by colour, each reduced in turn (fixed order)

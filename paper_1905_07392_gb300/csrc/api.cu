@@ -55,7 +55,10 @@ ebv_status check_params(const ebv_params *p, std::string &why)
     if (!(p->tol > 0.0) || p->max_iters < 1) { why = "tol > 0 and max_iters >= 1 required"; return EBV_ERR_INVALID; }
     if (!(p->cfl > 0.0)) { why = "cfl must be > 0"; return EBV_ERR_INVALID; }
     if (!(p->delta_min > 0.0)) { why = "delta_min must be > 0"; return EBV_ERR_INVALID; }
-    if (p->precision != EBV_FP64 && p->precision != EBV_FP32_REFINE) { why = "unknown precision"; return EBV_ERR_INVALID; }
+    if (p->precision != EBV_FP64 && p->precision != EBV_FP32_REFINE && p->precision != EBV_FP32_MIXED) {
+        why = "unknown precision";
+        return EBV_ERR_INVALID;
+    }
     if (p->advect != 0 && p->advect != 1) { why = "advect must be 0 or 1"; return EBV_ERR_INVALID; }
     return EBV_OK;
 }
@@ -1375,6 +1378,7 @@ ebv_status ebv_batch_create(int n, const ebv_grid *grids, const ebv_params *para
             ebv_batch_destroy(b);
             return st;
         }
+        c->batched = true;
         b->ctx.push_back(c);
     }
     *out = b;

@@ -263,6 +263,11 @@ struct Ctx {
     ProfEvents prof;
 
     bool have_geom = false;
+    // an instance of a batch: its steps run beside the other instances', so
+    // the smoother keeps the colour passes in switch mode 1 (the fused sweep
+    // wins a lone timing on small grids but takes two blocks' shared memory
+    // per SM; the batch measured 7 % slower with it)
+    bool batched = false;
     // geometry (device)
     double *alpha = nullptr, *ax = nullptr, *ay = nullptr, *az = nullptr, *area = nullptr;
     double *nrm = nullptr, *bcen = nullptr;

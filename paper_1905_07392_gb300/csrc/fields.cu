@@ -90,13 +90,40 @@ __device__ inline double d_robust(const GridD &g, const uint8_t *flag, const dou
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;       \
     const int c = cidx(g, i, j, k);
 
+// The apparent viscosity of eta_of in FP32 (EBV_FP32_MIXED, cells away from
+// the EB): the same laws and branches, FP32 arithmetic and math functions.
+__device__ inline float eta_of_f(const ParamsD &p, float sr, float rsr)
+{
+    const float m = (float)p.m, mu = (float)p.mu, tau0 = (float)p.tau0, nf = (float)p.n_flow;
+    const float msr = m * sr;
+    const float yield = (sr > 0.f) ? (msr > 20.f ? 1.f : -expm1f(-msr)) * rsr : m;
+    const float srf = sr > (float)p.inv_m ? sr : (float)p.inv_m;
+    switch (p.model) {
+    case EBV_NEWTONIAN: return mu;
+    case EBV_BINGHAM: return mu + tau0 * yield;
+    case EBV_HERSCHEL_BULKLEY: return mu * powf(srf, nf - 1.f) + tau0 * yield;
+    case EBV_POWER_LAW: return mu * powf(srf, nf - 1.f);
+    case EBV_SOUZA_MENDES_DUTRA: {
+        const float y2 = (sr > 0.f) ? -expm1f(-(float)p.eta0 * sr / tau0) * rsr : (float)p.eta0 / tau0;
+        return mu * powf(srf, nf - 1.f) + tau0 * y2;
+    }
+    }
+    return mu;
+}
+
 // ---- fused strain rate + apparent viscosity (optionally the gradient) -----
-template <bool kWriteG>
+// kMixed (EBV_FP32_MIXED): cells whose six neighbours are fluid and that are
+// neither cut nor next to a cut cell (nearm) form the central differences of
+// u in FP64 (they cancel: u is O(1), its differences small) and the rest --
+// the scaling by 1/(2h), the strain-rate norm, its reciprocal square root and
+// the viscosity law -- in FP32; every other cell takes the FP64 path.
+template <bool kWriteG, bool kMixed = false>
 __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__restrict__ flag,
                                                     const double *__restrict__ u, ParamsD p,
                                                     double *__restrict__ eta,
                                                     double *__restrict__ srate,
-                                                    double *__restrict__ G)
+                                                    double *__restrict__ G,
+                                                    const uint8_t *__restrict__ nearm = nullptr)
 {
     CELL_INDEX
     const int N3 = ncell(g);
@@ -106,6 +133,35 @@ __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__re
         if (kWriteG)
             for (int q = 0; q < 9; q++) G[q * N3 + c] = 0.0;
         return;
+    }
+    if constexpr (kMixed) {
+        const int sy = g.nx, sz = g.nx * g.ny;
+        if (!nearm[c] && i > 0 && i < g.nx - 1 && j > 0 && j < g.ny - 1 && k > 0 && k < g.nz - 1 &&
+            flag[c - 1] && flag[c + 1] && flag[c - sy] && flag[c + sy] && flag[c - sz] && flag[c + sz]) {
+            const int st[3] = {1, sy, sz};
+            const float hf = (float)(0.5 * g.ih);
+            float Gf[3][3];
+#pragma unroll
+            for (int d = 0; d < 3; d++)
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    const double *uq = u + q * N3;
+                    Gf[d][q] = (float)(uq[c + st[d]] - uq[c - st[d]]) * hf;
+                }
+            const float xy = Gf[0][1] + Gf[1][0], xz = Gf[0][2] + Gf[2][0], yz = Gf[1][2] + Gf[2][1];
+            const float s = 2.f * (Gf[0][0] * Gf[0][0] + Gf[1][1] * Gf[1][1] + Gf[2][2] * Gf[2][2]) +
+                            (xy * xy + xz * xz + yz * yz);
+            const float rsr = s > 0.f ? rsqrtf(s) : 0.f;
+            const float sr = s * rsr;
+            eta[c] = (double)eta_of_f(p, sr, rsr);
+            if (srate) srate[c] = (double)sr;
+            if (kWriteG)
+#pragma unroll
+                for (int d = 0; d < 3; d++)
+#pragma unroll
+                    for (int q = 0; q < 3; q++) G[(3 * d + q) * N3 + c] = (double)Gf[d][q];
+            return;
+        }
     }
     double Gm[3][3];
     const double ih = g.ih;
@@ -870,12 +926,22 @@ ebv_status launch_strain_eta(Ctx *c, const double *u, double *eta, double *srate
     const GridD &g = c->g;
     // u (3 words), flag (1 byte), eta (+ ||gamma||) (+ 9 gradient words)
     const double nb = (double)ncell(g) * (8.0 * (4 + (srate ? 1 : 0) + (G ? 9 : 0)) + 1.0);
+    const dim3 gr = grid3(g.nx, g.ny, g.nz);
+    if (c->prm.precision == EBV_FP32_MIXED) {   // FP32 away from the EB (plus the near-cell mask)
+        if (G)
+            EBV_LAUNCH_P(c, "strain_rate_viscosity", nb + ncell(g), (k_strain_eta<true, true>), gr, block3(), 0, g,
+                         c->flag, u, paramsd(c->prm), eta, srate, G, c->nearm);
+        else
+            EBV_LAUNCH_P(c, "strain_rate_viscosity", nb + ncell(g), (k_strain_eta<false, true>), gr, block3(), 0, g,
+                         c->flag, u, paramsd(c->prm), eta, srate, nullptr, c->nearm);
+        return EBV_OK;
+    }
     if (G)
-        EBV_LAUNCH_P(c, "strain_rate_viscosity", nb, k_strain_eta<true>, grid3(g.nx, g.ny, g.nz), block3(), 0, g,
-                     c->flag, u, paramsd(c->prm), eta, srate, G);
+        EBV_LAUNCH_P(c, "strain_rate_viscosity", nb, k_strain_eta<true>, gr, block3(), 0, g, c->flag, u,
+                     paramsd(c->prm), eta, srate, G);
     else
-        EBV_LAUNCH_P(c, "strain_rate_viscosity", nb, k_strain_eta<false>, grid3(g.nx, g.ny, g.nz), block3(), 0, g,
-                     c->flag, u, paramsd(c->prm), eta, srate, nullptr);
+        EBV_LAUNCH_P(c, "strain_rate_viscosity", nb, k_strain_eta<false>, gr, block3(), 0, g, c->flag, u,
+                     paramsd(c->prm), eta, srate, nullptr);
     return EBV_OK;
 }
 

@@ -3339,7 +3339,7 @@ struct NdProblem : Problem {
 // operator application)
 ebv_status solve(Ctx *c, Problem &P, const double *b, double *x, int *iters, double *res, bool x_zero = false)
 {
-    if (c->prm.precision == EBV_FP32_REFINE) return pcg_refine(c, P, b, x, iters, res, x_zero);
+    if (c->prm.precision != EBV_FP64) return pcg_refine(c, P, b, x, iters, res, x_zero);
     return pcg(c, P, b, x, iters, res);
 }
 
@@ -3545,7 +3545,7 @@ ebv_status setup_geometry_solvers(Ctx *c)
     // both precisions of the projection hierarchy are kept
     ebv_status s = cc_finish_hierarchy(c, c->mac, false);
     if (s != EBV_OK) return s;
-    if (c->prm.precision == EBV_FP32_REFINE) {
+    if (c->prm.precision != EBV_FP64) {
         // FP32 levels derived from FP64 fine coefficients; the bottom inverse
         // from the FP32 coarse operator
         s = cc_finish_hierarchy(c, c->mac, true);
@@ -3652,7 +3652,7 @@ ebv_status autotune_shapes_t(Ctx *c)
             // results), per kind of sweep: the faster serves it in switch mode 1
             RbMaps m;
             for (int q = 0; q < 4; q++) L.rb_ms[q][0] = 1e30f, L.rb_ms[q][1] = 0.f;
-            if (rb_fusable(L.g) && gs4_ok(L.g) && rb_map(c, x, 0, L.g, &m.x) && rb_map(c, b, 1, L.g, &m.b) &&
+            if (!c->batched && rb_fusable(L.g) && gs4_ok(L.g) && rb_map(c, x, 0, L.g, &m.x) && rb_map(c, b, 1, L.g, &m.b) &&
                 rb_map(c, A.dinv, 1, L.g, &m.d) && rb_map(c, L.bxp, 4, L.g, &m.fx) && rb_map(c, A.by, 2, L.g, &m.fy) &&
                 rb_map(c, A.bz, 3, L.g, &m.fz)) {
                 const long long nl = c->launches;
@@ -3721,7 +3721,7 @@ ebv_status autotune_shapes_t(Ctx *c)
 
 ebv_status autotune_shapes(Ctx *c)
 {
-    return c->prm.precision == EBV_FP32_REFINE ? autotune_shapes_t<float>(c) : autotune_shapes_t<double>(c);
+    return c->prm.precision != EBV_FP64 ? autotune_shapes_t<float>(c) : autotune_shapes_t<double>(c);
 }
 
 ebv_status mac_solve(Ctx *c, const double *b, double *x, int *iters, double *res)
@@ -3738,7 +3738,7 @@ ebv_status visc_build(Ctx *c, const double *eta)
     CcLevel &V0 = c->visc.lv[0];
     EBV_LAUNCH(c, k_visc_coeffs, grid3(g.nx + 1, g.ny + 1, g.nz + 1), block3(), 0, g, geomd(c), paramsd(c->prm), eta,
                c->dt_dev, V0.extra_d, V0.bf_d[0], V0.bf_d[1], V0.bf_d[2]);
-    return cc_finish_hierarchy(c, c->visc, c->prm.precision == EBV_FP32_REFINE);
+    return cc_finish_hierarchy(c, c->visc, c->prm.precision != EBV_FP64);
 }
 
 ebv_status visc_solve(Ctx *c, const double *psi_comp, int comp, double *x, int *iters, double *res)

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libebvisc.so")
 
 INFLOW, OUTFLOW, SLIP, NOSLIP = 0, 1, 2, 3
 NEWTONIAN, BINGHAM, HERSCHEL_BULKLEY, POWER_LAW, SOUZA_MENDES_DUTRA = 0, 1, 2, 3, 4
-FP64, FP32_REFINE = 0, 1
+FP64, FP32_REFINE, FP32_MIXED = 0, 1, 2
 STATUS = {0: "EBV_OK", -1: "EBV_ERR_INVALID", -2: "EBV_ERR_CUDA", -3: "EBV_ERR_NOT_CONVERGED",
           -4: "EBV_ERR_TIMEOUT", -5: "EBV_ERR_NAN", -6: "EBV_ERR_GEOMETRY", -8: "EBV_ERR_OOM"}
 
