@@ -116,7 +116,9 @@ __device__ inline float eta_of_f(const ParamsD &p, float sr, float rsr)
 // neither cut nor next to a cut cell (nearm) form the central differences of
 // u in FP64 (they cancel: u is O(1), its differences small) and the rest --
 // the scaling by 1/(2h), the strain-rate norm, its reciprocal square root and
-// the viscosity law -- in FP32; every other cell takes the FP64 path.
+// the viscosity law -- in FP32; every other cell takes the FP64 path.  (The
+// conversions between the two cost about what the FP64 arithmetic they
+// replace did, here and with integer bit-field conversions, measured.)
 template <bool kWriteG, bool kMixed = false>
 __global__ void __launch_bounds__(256) k_strain_eta(GridD g, const uint8_t *__restrict__ flag,
                                                     const double *__restrict__ u, ParamsD p,

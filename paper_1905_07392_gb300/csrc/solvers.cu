@@ -17,6 +17,7 @@
 
 #include "ebv_internal.cuh"
 #include "tma.cuh"
+#include "fpbits.cuh"
 
 namespace ebv {
 
@@ -864,19 +865,28 @@ using RbF = typename VFace<float>::type;
 // threads (positions pq, pq+1 of both halves of a tile row), cells, order
 // and sums, so the colour passes end with the fused sweep's r.z bit for bit.
 // Each c1 cell is formed by the operations of gs_cell; the other colour is
-// read (unchanged by this pass) for the partial.  Grid (tiles x, tiles y, nz).
+// read (unchanged by this pass) for the partial.  A block covers
+// kGs2Planes planes of its tile (the loads of all of them in flight
+// together), each plane's partial reduced on its own.  Grid (tiles x,
+// tiles y, ceil(nz / kGs2Planes)).
+constexpr int kGs2Planes = 4;
 __global__ void __launch_bounds__(RB_THREADS) k_cc_gs2_dot(VOp<float> A, float *__restrict__ x,
                                                             const float *__restrict__ b, int c1,
                                                             double *__restrict__ part)
 {
-    __shared__ double wsum[RB_THREADS / 32];
+    __shared__ double wsum[kGs2Planes][RB_THREADS / 32];
     const GridD &g = A.g;
     const int tid = threadIdx.x, hx = g.nx >> 1, hf = (g.nx + 2) >> 1;
     const int r = tid >> 4;
-    const int j = blockIdx.y * RB_TY + r, pq = blockIdx.x * RB_HW + 2 * (tid & 15), k = blockIdx.z;
-    double dsum = 0.0;
-    if (j < g.ny && pq < hx) {
-        const int h2 = (c1 + j + k) & 1, sy = g.nx, sz = g.nx * g.ny;
+    const int j = blockIdx.y * RB_TY + r, pq = blockIdx.x * RB_HW + 2 * (tid & 15);
+    const int sy = g.nx, sz = g.nx * g.ny;
+    double dsum[kGs2Planes];
+#pragma unroll
+    for (int pl = 0; pl < kGs2Planes; pl++) {
+        const int k = blockIdx.z * kGs2Planes + pl;
+        dsum[pl] = 0.0;
+        if (j >= g.ny || pq >= hx || k >= g.nz) continue;
+        const int h2 = (c1 + j + k) & 1;
         const int rc = (k * g.ny + j) * g.nx;
         const int c = rc + (h2 ? hx : 0) + pq, o = rc + (h2 ? 0 : hx) + pq;
         const float2 bb = *reinterpret_cast<const float2 *>(b + c);
@@ -921,15 +931,22 @@ __global__ void __launch_bounds__(RB_THREADS) k_cc_gs2_dot(VOp<float> A, float *
         d += b0[1] * v0[1];
         d += b1[0] * v1[0];
         d += b1[1] * v1[1];
-        dsum = (double)d;
+        dsum[pl] = (double)d;
     }
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-    if ((tid & 31) == 0) wsum[tid >> 5] = dsum;
+#pragma unroll
+    for (int pl = 0; pl < kGs2Planes; pl++) {
+        double v = dsum[pl];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) wsum[pl][tid >> 5] = v;
+    }
     __syncthreads();
-    if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < RB_THREADS / 32; w++) s += wsum[w];
-        part[(size_t)k * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = s;
+    if (tid < kGs2Planes) {
+        const int k = blockIdx.z * kGs2Planes + tid;
+        if (k < g.nz) {
+            double s = 0.0;
+            for (int w = 0; w < RB_THREADS / 32; w++) s += wsum[tid][w];
+            part[(size_t)k * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = s;
+        }
     }
 }
 
@@ -1167,7 +1184,7 @@ __global__ void k_to_split(GridD g, int d, const double *__restrict__ a, float *
     const double sc = sig ? *sig : 1.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const int i = s % mx, j = (s / mx) % my, k = s / (mx * my);
-        b[d < 0 ? cix<float>(g, i, j, k) : fidxT<float>(g, d, i, j, k)] = (float)(a[s] * sc);
+        b[d < 0 ? cix<float>(g, i, j, k) : fidxT<float>(g, d, i, j, k)] = f64_to_f32_pow2(a[s], sc);
     }
 }
 
@@ -1176,7 +1193,8 @@ __global__ void k_to32_scaled(const double *__restrict__ a, float *__restrict__ 
                               const double *__restrict__ sig)
 {
     const double sc = *sig;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) b[s] = (float)(a[s] * sc);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        b[s] = f64_to_f32_pow2(a[s], sc);
 }
 
 // FP32 face coefficients -> the V-cycle's BF16 copy (same layout)
@@ -1341,7 +1359,7 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
         for (int h = 0; h < 2; h++)
             if (cc[h] >= 0) {
                 if constexpr (kRes) {
-                    const float r = (float)((b[cc[h]] - y[h]) * sc);
+                    const float r = f64_to_f32_pow2(b[cc[h]] - y[h], sc);
                     r32[cix<float>(A.g, i, j, 2 * kk + h)] = r;
                     vr += r * r;
                 } else {
@@ -1672,7 +1690,7 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 if (kMode == ND_RESID) out[n] = T(0);
                 if (kMode == ND_APPLY) { out[n] = X0; v += X0 * X0; }
                 if (kMode == ND_RES32) {
-                    const float r = (float)((b_c - X0) * sc);
+                    const float r = f64_to_f32_pow2(b_c - X0, sc);
                     out32[n] = r;
                     vr += r * r;
                 }
@@ -1686,7 +1704,7 @@ __global__ void __launch_bounds__(NT_X * NT_Y) k_nd_tile(NdOp<T> A, const T *__r
                 if (kMode == ND_RESID) out[n] = b_c - ax;
                 if (kMode == ND_APPLY) { out[n] = ax; v += X0 * ax; }
                 if (kMode == ND_RES32) {
-                    const float r = (float)((b_c - ax) * sc);
+                    const float r = f64_to_f32_pow2(b_c - ax, sc);
                     out32[n] = r;
                     vr += r * r;
                 }
@@ -1727,7 +1745,7 @@ __global__ void __launch_bounds__(256) k_nd_irr(NdOp<T> A, const int *__restrict
         if (kMode == ND_RESID) out[n] = b[n] - ax;
         if (kMode == ND_APPLY) { out[n] = ax; v = xin[n] * ax; }
         if (kMode == ND_RES32) {
-            const float r = (float)((b[n] - ax) * sc);
+            const float r = f64_to_f32_pow2(b[n] - ax, sc);
             out32[n] = r;
             v = T(r) * T(r);
         }
@@ -2799,9 +2817,10 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
         if (s == 1 && dot_part && tiles) {
             // the fused sweep's r.z partials, per (plane, tile), with the last pass
             if constexpr (sizeof(T) == 4) {
-                const dim3 gt((g.nx / 2 + RB_HW - 1) / RB_HW, (g.ny + RB_TY - 1) / RB_TY, g.nz);
+                const dim3 gt((g.nx / 2 + RB_HW - 1) / RB_HW, (g.ny + RB_TY - 1) / RB_TY,
+                              (g.nz + kGs2Planes - 1) / kGs2Planes);
                 EBV_LAUNCH_P(c, kGsDotName[1], nb, k_cc_gs2_dot, gt, dim3(RB_THREADS), 0, A, x, b, 1 - c0, dot_part);
-                return (int)(gt.x * gt.y * gt.z);
+                return rb_ntiles(g) * g.nz;
             }
         } else if (s == 1 && dot_part) {
             // fixed block shape: the grouping of its partial sums must not
@@ -3670,7 +3689,8 @@ ebv_status autotune_shapes_t(Ctx *c)
                 // the correction sweep reads a coarse array: a zeroed vector with the next level's dims
                 const bool has_c = l + 1 < c->mac.L;
                 const GridD gc = has_c ? c->mac.lv[l + 1].g : GridD();
-                const dim3 gt((L.g.nx / 2 + RB_HW - 1) / RB_HW, (L.g.ny + RB_TY - 1) / RB_TY, L.g.nz);
+                const dim3 gt((L.g.nx / 2 + RB_HW - 1) / RB_HW, (L.g.ny + RB_TY - 1) / RB_TY,
+                              (L.g.nz + kGs2Planes - 1) / kGs2Planes);
                 const dim3 bk = L.gs_blk, grc = gs_grid(L.g, bk);
                 for (int kind = 0; kind < 4; kind++) {
                     if (kind == RB_CORR && !has_c) continue;   // (no correction sweep on the last level)
