@@ -359,9 +359,10 @@ __device__ inline void load4(const F *p, float v[4])
 // kPz = 1 asks for 5 resident blocks per SM (at most 51 registers), kPz = 2
 // for 4: one plane per thread and more warps, or two and more loads per warp.
 // kCorr: the pass after the coarse-grid correction, as in k_cc_gs (each
-// neighbour value plus its parent's coarse correction xc, level gc).
+// neighbour value plus its parent's coarse correction xc, level gc); its
+// coarse rows in registers ask for 3 resident blocks per SM.
 template <int kPz, bool kCorr = false>
-__global__ void __launch_bounds__(256, kPz == 1 ? 5 : 4) k_cc_gs4(VOp<float> A, float *__restrict__ x,
+__global__ void __launch_bounds__(256, kCorr ? 3 : (kPz == 1 ? 5 : 4)) k_cc_gs4(VOp<float> A, float *__restrict__ x,
                                                                  const float *__restrict__ b, int color,
                                                                  int zero_start, const float *__restrict__ xc = nullptr,
                                                                  GridD gc = GridD())
@@ -404,6 +405,28 @@ __global__ void __launch_bounds__(256, kPz == 1 ? 5 : 4) k_cc_gs4(VOp<float> A, 
             load4(A.bz + c, fz0);
             load4(A.bz + c + sz, fz1);
             const int rf = rc + k * g.ny + j, hf = (g.nx + 2) >> 1;
+            // kCorr: the parents of the 4 cells' neighbours are the coarse cells
+            // t0-1 .. t0+4 of the parent row and t0 .. t0+3 of the rows of the y
+            // and z neighbours' parents; in the coarse row-split layout the even
+            // and odd ones of t0 .. t0+3 are two 8-byte pairs of each row
+            float cw[6] = {}, cs[4] = {}, cn[4] = {}, cd[4] = {}, cu[4] = {};
+            if constexpr (kCorr) {
+                const int hxc = gc.nx >> 1, tc = t0 >> 1;
+                auto row4 = [&](int J, int K, float *o) {
+                    const float *r0 = xc + (K * gc.ny + J) * gc.nx;
+                    const float2 ev = *reinterpret_cast<const float2 *>(r0 + tc);
+                    const float2 od = *reinterpret_cast<const float2 *>(r0 + hxc + tc);
+                    o[0] = ev.x; o[1] = od.x; o[2] = ev.y; o[3] = od.y;
+                };
+                row4(j >> 1, k >> 1, cw + 1);
+                const float *r0 = xc + ((k >> 1) * gc.ny + (j >> 1)) * gc.nx;
+                cw[0] = t0 > 0 ? r0[hxc + tc - 1] : 0.f;          // coarse t0 - 1 (odd)
+                cw[5] = t0 + 4 < gc.nx ? r0[tc + 2] : 0.f;         // coarse t0 + 4 (even)
+                if (j > 0) row4((j - 1) >> 1, k >> 1, cs);
+                if (j < g.ny - 1) row4((j + 1) >> 1, k >> 1, cn);
+                if (k > 0) row4(j >> 1, (k - 1) >> 1, cd);
+                if (k < g.nz - 1) row4(j >> 1, (k + 1) >> 1, cu);
+            }
 #pragma unroll
             for (int m = 0; m < 4; m++) {
                 const int t = t0 + m, i = 2 * t + par;
@@ -413,13 +436,13 @@ __global__ void __launch_bounds__(256, kPz == 1 ? 5 : 4) k_cc_gs4(VOp<float> A, 
                 float xe = par ? (m < 3 ? xo[m + 1] : xb) : xo[m];
                 float ys = xs[m], yn = xn[m], zd = xd[m], zu = xu[m];
                 if constexpr (kCorr) {
-                    auto cor = [&](int ii, int jj, int kq) { return xc[cix<float>(gc, ii >> 1, jj >> 1, kq >> 1)]; };
-                    if (i > 0) xw = xw + cor(i - 1, j, k);
-                    if (i < g.nx - 1) xe = xe + cor(i + 1, j, k);
-                    if (j > 0) ys = ys + cor(i, j - 1, k);
-                    if (j < g.ny - 1) yn = yn + cor(i, j + 1, k);
-                    if (k > 0) zd = zd + cor(i, j, k - 1);
-                    if (k < g.nz - 1) zu = zu + cor(i, j, k + 1);
+                    // parent of i - 1 is coarse t - 1 + par, of i + 1 coarse t + par
+                    if (i > 0) xw = xw + (par ? cw[m + 1] : cw[m]);
+                    if (i < g.nx - 1) xe = xe + (par ? cw[m + 2] : cw[m + 1]);
+                    if (j > 0) ys = ys + cs[m];
+                    if (j < g.ny - 1) yn = yn + cn[m];
+                    if (k > 0) zd = zd + cd[m];
+                    if (k < g.nz - 1) zu = zu + cu[m];
                 }
                 float s = 0.f;
                 if (i > 0) s += bxl * xw;
