@@ -288,6 +288,17 @@ def run_ours(args, rank, world, local):
     del ue, pe
     value = job_value(cells, args.steps, world, sec)
     roof, kernels = roofline(prof, cells)
+    # the timings that chose each MAC level's sweep form (fused, passes; ms
+    # of four launches) for the kinds from zero, plain, corrected, with r.z
+    sweeps = {}
+    for lv in range(8):
+        try:
+            t = [s.sweep_timing(lv, k) for k in range(4)]
+        except Exception:
+            break
+        if any(f < 1e29 for f, _ in t):
+            sweeps[f"L{lv}"] = {n: [round(f, 4), round(q, 4)]
+                                for n, (f, q) in zip(("zero", "plain", "corr", "dot"), t) if f < 1e29}
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sec / args.steps, 3),
@@ -298,7 +309,7 @@ def run_ours(args, rank, world, local):
                       "precision": PRECISION,
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (each cell field 134 MB at 256^3)"},
-           "roofline": roof, "kernels": kernels,
+           "roofline": roof, "kernels": kernels, "sweep_forms_ms": sweeps,
            "step_launch": ("kernel by kernel" if args.eager else
                            "one CUDA graph launch per step (solver loops as conditional nodes)"),
            "eager": {"value": round(job_value(cells, args.steps, world, sec_e), 3), "unit": UNIT,

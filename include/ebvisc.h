@@ -308,6 +308,18 @@ void ebv_set_spin_limit(long long cycles);
  * Process-wide; read when a step is issued or captured. */
 void ebv_set_fused_sweep(int mode);
 
+/* Measurement hook: the times (ms, four launches each) that chose the form
+ * of one kind of red-black sweep on level `level` of the MAC hierarchy when
+ * the context's solvers were set up (ebv_set_fused_sweep mode 1): kind 0 the
+ * sweep from zero, 1 the plain sweep, 2 the sweep after the coarse
+ * correction, 3 the sweep that also forms the r.z partials; *fused_ms the
+ * one-pass sweep, *passes_ms its two colour passes.  A form that was not
+ * timed (the level does not fuse, an FP64 context, no correction on the
+ * coarsest level, a batch instance) reads 1e30 and 0.  EBV_ERR_INVALID for a
+ * null argument or a level or kind out of range; the values are only
+ * meaningful after the first step. */
+ebv_status ebv_sweep_timing(const ebv_ctx *ctx, int level, int kind, float *fused_ms, float *passes_ms);
+
 /* Counters for the measurement harness: kernel launches queued since the
  * context was created (host counter). */
 long long ebv_launch_count(const ebv_ctx *ctx);

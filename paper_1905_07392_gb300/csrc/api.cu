@@ -883,6 +883,15 @@ ebv_status ebv_drag(ebv_ctx *c, const double *u, const double *p, double *fz, do
 
 long long ebv_launch_count(const ebv_ctx *c) { return c ? c->launches : 0; }
 
+ebv_status ebv_sweep_timing(const ebv_ctx *c, int level, int kind, float *fused_ms, float *passes_ms)
+{
+    if (!c || !fused_ms || !passes_ms || level < 0 || level >= c->mac.L || kind < 0 || kind > 3)
+        return EBV_ERR_INVALID;
+    *fused_ms = c->mac.lv[level].rb_ms[kind][0];
+    *passes_ms = c->mac.lv[level].rb_ms[kind][1];
+    return EBV_OK;
+}
+
 const char *ebv_last_error(const ebv_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 void ebv_destroy(ebv_ctx *c)

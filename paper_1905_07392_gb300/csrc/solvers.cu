@@ -509,7 +509,10 @@ inline void launch_gs4(cudaStream_t st, dim3 bk, int pz, const VOp<float> &A, fl
 // x_in + the coarse correction of the neighbour's parent (prolongation
 // folded in, as in k_cc_gs).  kDot: also the partial b.x_out of every
 // (plane, tile), part[plane * ntiles + tile], summed over the same cells in
-// the same order as k_cc_gs2_dot, which forms them with the colour passes.
+// the same order as k_cc_gs2_dot, which forms them with the colour passes:
+// in FP32 over a thread's cells and within the warp, in FP64 over the warps
+// (FP64 arithmetic is scarce on this GPU: FP64 warp sums made each plane's
+// partial cost more than the plane's loads).
 constexpr int RB_TX = 64;                 // tile cells along x
 constexpr int RB_HW = RB_TX / 2;          // half-row positions per tile
 constexpr int RB_TY = 16;                 // tile rows
@@ -520,6 +523,8 @@ constexpr int RB_XR = RB_TY + 4;          // rows of the x box
 constexpr int RB_CR = RB_TY + 2;          // rows of the cell boxes (b, 1/diag, x and z faces, results)
 constexpr int RB_YR = RB_TY + 3;          // rows of the y-face box
 constexpr int RB_NBAR = 3;                // mbarriers (steps in flight + 1)
+constexpr int RB_KW = 24;                 // coarse box width (half-row positions of the coarse level)
+constexpr int RB_KR = RB_TY / 2 + 2;      // coarse box rows
 static_assert(RB_THREADS == 256, "one thread per 2 positions of each tile row");
 // half-row length of the padded x-face copy: nx/2 + 1 even faces, rounded up to 8
 __host__ __device__ inline int rb_hxp(int nx) { return ((nx / 2 + 1) + 7) / 8 * 8; }
@@ -529,19 +534,22 @@ template <class F>
 struct RbSmem {
     static constexpr int bX = RB_XW * 2 * RB_XR * 4, bC = RB_XW * 2 * RB_CR * 4;
     static constexpr int bY = RB_FW * 2 * RB_YR * (int)sizeof(F), bZ = RB_FW * 2 * RB_CR * (int)sizeof(F);
+    static constexpr int bR = RB_XW * RB_CR * 4, bK = RB_KW * 2 * RB_KR * 4;
     static constexpr int kX = al128(bX), kC = al128(bC), kY = al128(bY), kZ = al128(bZ);
+    static constexpr int kR = al128(bR), kK = al128(bK);
     // x: planes m-1, m, m+1 and one ahead; b, 1/diag, x and y faces: m-1, m
     // and one ahead; z faces: face planes m-1 .. m+1 and one ahead; results
-    // of the first colour: planes m-2 .. m
+    // of the first colour (only its half of each row): planes m-2 .. m;
+    // coarse correction (kCorr): coarse planes (m-1)/2 .. (m+1)/2 and one ahead
     static constexpr int oX = 0, oB = oX + 4 * kX, oD = oB + 3 * kC, oY = oD + 3 * kC, oZ = oY + 3 * kY;
-    static constexpr int oXF = oZ + 4 * kZ, oR = oXF + 3 * kZ, oBar = oR + 3 * kC, oMisc = oBar + 64;
+    static constexpr int oXF = oZ + 4 * kZ, oR = oXF + 3 * kZ, oK = oR + 3 * kR, oBar = oK + 3 * kK;
+    static constexpr int oMisc = oBar + 64;
     static constexpr int bytes = oMisc + 128;
 };
 
 template <class F>
 struct RbArgs {
-    GridD g, gc;            // this level; the coarse level (kCorr)
-    const float *xc;        // coarse correction (kCorr)
+    GridD g;                // this level
     float *xout;
     double *part;           // kDot partials
     int *ctl;
@@ -550,12 +558,18 @@ struct RbArgs {
 };
 
 struct RbMaps {
-    CUtensorMap x, b, d, fx, fy, fz;
+    CUtensorMap x, b, d, fx, fy, fz, xc;   // xc: the coarse correction (kCorr)
 };
+
+// Coarse planes step q loads (kCorr): step m needs coarse planes (m-1)/2 ..
+// (m+1)/2 (floor division); the first step loads both of its, every later
+// step the plane (m+1)/2 when it is new (m+1 even).  With three ring slots a
+// load never lands on a slot a step in flight still reads.
+__device__ inline int rb_coarse_count(int q, int m) { return q == 0 ? 2 : (((m + 1) & 1) == 0 ? 1 : 0); }
 
 template <class F>
 __device__ inline void rb_issue(unsigned char *sm, uint64_t *bar, int q, int m0, int p0, int y0, bool zero,
-                                const RbMaps &tm)
+                                bool corr, const RbMaps &tm)
 {
     using S = RbSmem<F>;
     const int m = m0 + q;
@@ -563,7 +577,15 @@ __device__ inline void rb_issue(unsigned char *sm, uint64_t *bar, int q, int m0,
     uint32_t bytes = 2 * S::bC + S::bY + 2 * S::bZ;
     if (!zero) bytes += (q == 0 ? 3 : 1) * S::bX;
     if (q == 0) bytes += S::bZ;
+    if (corr) bytes += rb_coarse_count(q, m) * S::bK;
     mbar_arrive_expect_tx(b, bytes);
+    if (corr) {
+        const int nk = rb_coarse_count(q, m), cfirst = q == 0 ? ((m - 1) >> 1) : ((m + 1) >> 1);
+        for (int t = 0; t < nk; t++) {
+            const int C = cfirst + t;
+            tma_load_4d(sm + S::oK + ((C + 3) % 3) * S::kK, &tm.xc, p0 / 2 - 4, 0, y0 / 2 - 1, C, b);
+        }
+    }
     if (!zero) {
         if (q == 0) {
             tma_load_4d(sm + S::oX + ((m - 1 + 8) & 3) * S::kX, &tm.x, p0 - 4, 0, y0 - 2, m - 1, b);
@@ -614,10 +636,13 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
     auto FX = [&](int pl) { return reinterpret_cast<const F *>(sm + S::oXF + ((pl + 3) % 3) * S::kZ); };
     auto FY = [&](int pl) { return reinterpret_cast<const F *>(sm + S::oY + ((pl + 3) % 3) * S::kY); };
     auto FZ = [&](int pl) { return reinterpret_cast<const F *>(sm + S::oZ + ((pl + 8) & 3) * S::kZ); };
-    auto R = [&](int pl) { return reinterpret_cast<float *>(sm + S::oR + ((pl + 3) % 3) * S::kC); };
-    auto cor = [&](int i, int j, int k) -> float {
-        return kCorr ? a.xc[cix<float>(a.gc, i >> 1, j >> 1, k >> 1)] : 0.f;
-    };
+    // results of the first colour: row r, position q of that row's first-colour half
+    auto R = [&](int pl) { return reinterpret_cast<float *>(sm + S::oR + ((pl + 3) % 3) * S::kR); };
+    // the staged coarse correction (kCorr): coarse plane K, the entry of
+    // coarse cell I in box row rw (a row offset from cor_row)
+    auto Kpl = [&](int K) { return reinterpret_cast<const float *>(sm + S::oK + ((K + 3) % 3) * S::kK); };
+    auto cor_row = [&](int J) { return (J - (y0 / 2 - 1)) * 2 * RB_KW; };
+    auto cor_col = [&](int I) { return (I & 1) * RB_KW + (I >> 1) - (p0 / 2 - 4); };
     if (smem_u32(sm) & 127) {   // tile destinations must be 128-byte aligned: report, load nothing
         if (tid == 0) atomicCAS(a.ctl + C_ERR, 0, E_SMEM);
         return;
@@ -629,8 +654,8 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
     }
     __syncthreads();
     if (tid == 0) {
-        rb_issue<F>(sm, bar, 0, m0, p0, y0, kZero, tm);
-        rb_issue<F>(sm, bar, 1, m0, p0, y0, kZero, tm);
+        rb_issue<F>(sm, bar, 0, m0, p0, y0, kZero, kCorr, tm);
+        rb_issue<F>(sm, bar, 1, m0, p0, y0, kZero, kCorr, tm);
     }
     // second colour and output: thread -> positions pq, pq+1 of both halves of tile row r
     const int r = tid >> 4, pq = p0 + 2 * (tid & 15);
@@ -646,6 +671,12 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
             const F *Fx = FX(m), *Fy = FY(m), *Fz0 = FZ(m), *Fz1 = FZ(m + 1);
             float *Rm = R(m);
             const int k = m;
+            // coarse planes of the parents (k >> 1) and of the other z neighbour
+            const float *Kk = nullptr, *Ko = nullptr;
+            if (kCorr) {
+                Kk = Kpl(k >> 1);
+                Ko = Kpl((k >> 1) - 1 + 2 * (k & 1));
+            }
             auto XI = [&](const float *Xp, int rr, int h2, int qq) { return Xp[(rr * 2 + h2) * RB_XW + qq]; };
             // one cell (i = 2p + h, j) of box row r1: the operations of gs_cell
             auto cell = [&](int r1, int j, int h, int p) {
@@ -666,12 +697,17 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
                     float xs = XI(X1, rx - 1, h, qx), xn = XI(X1, rx + 1, h, qx);
                     float xd = XI(X0, rx, h, qx), xu = XI(X2, rx, h, qx);
                     if (kCorr) {
-                        if (i > 0) xw = xw + cor(i - 1, j, k);
-                        if (i < g.nx - 1) xe = xe + cor(i + 1, j, k);
-                        if (j > 0) xs = xs + cor(i, j - 1, k);
-                        if (j < g.ny - 1) xn = xn + cor(i, j + 1, k);
-                        if (k > 0) xd = xd + cor(i, j, k - 1);
-                        if (k < g.nz - 1) xu = xu + cor(i, j, k + 1);
+                        // the neighbours' parents: this cell's (I = p, J, K) or, one
+                        // per axis, the next coarse cell on the neighbour's side
+                        const int rj = cor_row(j >> 1), ro = cor_row((j >> 1) - 1 + 2 * (j & 1));
+                        const float co = Kk[rj + cor_col(p)], cx = Kk[rj + cor_col(h ? p + 1 : p - 1)];
+                        const float cy = Kk[ro + cor_col(p)], cz = Ko[rj + cor_col(p)];
+                        if (i > 0) xw = xw + (h ? co : cx);
+                        if (i < g.nx - 1) xe = xe + (h ? cx : co);
+                        if (j > 0) xs = xs + ((j & 1) ? co : cy);
+                        if (j < g.ny - 1) xn = xn + ((j & 1) ? cy : co);
+                        if (k > 0) xd = xd + ((k & 1) ? co : cz);
+                        if (k < g.nz - 1) xu = xu + ((k & 1) ? cz : co);
                     }
                     if (i > 0) off += bxl * xw;
                     if (i < g.nx - 1) off += bxh * xe;
@@ -680,7 +716,7 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
                     if (k > 0) off += fz0 * xd;
                     if (k < g.nz - 1) off += fz1 * xu;
                 }
-                Rm[cc] = (Bm[cc] + off) * Dm[cc];
+                Rm[r1 * RB_XW + qx] = (Bm[cc] + off) * Dm[cc];
             };
             {   // the tile: positions p, p + 1 of row y0 + r, paired shared-memory loads
                 const int j = y0 + r, h = (a.c0 + j + m) & 1, p = pq;
@@ -713,17 +749,33 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
                         const float zs0[2] = {fz0.x, fz0.y}, zs1[2] = {fz1.x, fz1.y};
                         const float vs[2] = {xs.x, xs.y}, vn[2] = {xn.x, xn.y}, vd[2] = {xd.x, xd.y};
                         const float vu[2] = {xu.x, xu.y}, bv[2] = {bb.x, bb.y}, dv[2] = {dd.x, dd.y};
+                        // the parents of the neighbours of cells 2(p+e)+h: coarse cells
+                        // p+e (co) and, per axis, the next one on the neighbour's side
+                        float co[2] = {0.f, 0.f}, cx[2] = {0.f, 0.f}, cy[2] = {0.f, 0.f}, cz[2] = {0.f, 0.f};
+                        if (kCorr) {
+                            const int rj = cor_row(j >> 1), ro = cor_row((j >> 1) - 1 + 2 * (j & 1));
+                            const int i0 = cor_col(p), i1 = cor_col(p + 1);
+                            co[0] = Kk[rj + i0];
+                            co[1] = Kk[rj + i1];
+                            const float ce = Kk[rj + cor_col(h ? p + 2 : p - 1)];
+                            cx[0] = h ? co[1] : ce;
+                            cx[1] = h ? ce : co[0];
+                            cy[0] = Kk[ro + i0];
+                            cy[1] = Kk[ro + i1];
+                            cz[0] = Ko[rj + i0];
+                            cz[1] = Ko[rj + i1];
+                        }
 #pragma unroll
                         for (int e = 0; e < 2; e++) {
                             const int i = 2 * (p + e) + h;
                             float xw = xw2[e], xe = xe2[e], xs_ = vs[e], xn_ = vn[e], xd_ = vd[e], xu_ = vu[e];
                             if (kCorr) {
-                                if (i > 0) xw = xw + cor(i - 1, j, k);
-                                if (i < g.nx - 1) xe = xe + cor(i + 1, j, k);
-                                if (j > 0) xs_ = xs_ + cor(i, j - 1, k);
-                                if (j < g.ny - 1) xn_ = xn_ + cor(i, j + 1, k);
-                                if (k > 0) xd_ = xd_ + cor(i, j, k - 1);
-                                if (k < g.nz - 1) xu_ = xu_ + cor(i, j, k + 1);
+                                if (i > 0) xw = xw + (h ? co[e] : cx[e]);
+                                if (i < g.nx - 1) xe = xe + (h ? cx[e] : co[e]);
+                                if (j > 0) xs_ = xs_ + ((j & 1) ? co[e] : cy[e]);
+                                if (j < g.ny - 1) xn_ = xn_ + ((j & 1) ? cy[e] : co[e]);
+                                if (k > 0) xd_ = xd_ + ((k & 1) ? co[e] : cz[e]);
+                                if (k < g.nz - 1) xu_ = xu_ + ((k & 1) ? cz[e] : co[e]);
                             }
                             float off = 0.f;
                             if (i > 0) off += bxl[e] * xw;
@@ -738,7 +790,7 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
                         v[0] = (bb.x + 0.f) * dd.x;
                         v[1] = (bb.y + 0.f) * dd.y;
                     }
-                    *reinterpret_cast<float2 *>(Rm + ch) = make_float2(v[0], v[1]);
+                    *reinterpret_cast<float2 *>(Rm + r1 * RB_XW + qx) = make_float2(v[0], v[1]);
                 }
             }
             // the ring: item t = tid / 3 of every third thread, spread over all warps
@@ -773,7 +825,7 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
         // second colour on plane mm = m - 1, and the plane's output
         const int mm = m - 1;
         if (q >= 2) {
-            double dsum = 0.0;
+            float dsum = 0.f;   // (a thread's 4 cells, then the warp: FP32; the 8 warps: FP64)
             if (own) {
                 const float *Rc = R(mm), *Bm = Bv(mm);
                 const int rc = r + 1, qx = pq - p0 + 4, h2 = (c1 + j2 + mm) & 1;
@@ -782,16 +834,18 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
                     const float *Rl = R(mm - 1), *Rh = R(mm + 1), *Dm = Dv(mm);
                     const F *Fx = FX(mm), *Fy = FY(mm), *Fz0 = FZ(mm), *Fz1 = FZ(mm + 1);
                     const int k = mm, j = j2, hh = h2, qf = qx + 4;
-                    const int ch = (rc * 2 + hh) * RB_XW + qx, co = (rc * 2 + 1 - hh) * RB_XW + qx;
-                    // paired loads: own half (b, 1/diag, y and z neighbours), the other half (x neighbours)
+                    const int ch = (rc * 2 + hh) * RB_XW + qx, cr = rc * RB_XW + qx;
+                    // paired loads: own half (b, 1/diag), and the first colour's results:
+                    // the y and z neighbours (rows rc -+ 1, planes mm -+ 1) and the x
+                    // neighbours (row rc) -- each row's first-colour half
                     const float2 bb = *reinterpret_cast<const float2 *>(Bm + ch);
                     const float2 dd = *reinterpret_cast<const float2 *>(Dm + ch);
-                    const float2 xs = *reinterpret_cast<const float2 *>(Rc + ch - 2 * RB_XW);
-                    const float2 xn = *reinterpret_cast<const float2 *>(Rc + ch + 2 * RB_XW);
-                    const float2 xd = *reinterpret_cast<const float2 *>(Rl + ch);
-                    const float2 xu = *reinterpret_cast<const float2 *>(Rh + ch);
-                    const float2 xo = *reinterpret_cast<const float2 *>(Rc + co);
-                    const float xb = hh ? Rc[co + 2] : Rc[co - 1];
+                    const float2 xs = *reinterpret_cast<const float2 *>(Rc + cr - RB_XW);
+                    const float2 xn = *reinterpret_cast<const float2 *>(Rc + cr + RB_XW);
+                    const float2 xd = *reinterpret_cast<const float2 *>(Rl + cr);
+                    const float2 xu = *reinterpret_cast<const float2 *>(Rh + cr);
+                    const float2 xo = *reinterpret_cast<const float2 *>(Rc + cr);
+                    const float xb = hh ? Rc[cr + 2] : Rc[cr - 1];
                     const float xw2[2] = {hh ? xo.x : xb, hh ? xo.y : xo.x};
                     const float xe2[2] = {hh ? xo.y : xo.x, hh ? xb : xo.y};
                     const float2 fxl = ld2f(Fx + (rc * 2 + hh) * RB_FW + qf);
@@ -835,12 +889,12 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
                     for (int h = 0; h < 2; h++)
 #pragma unroll
                         for (int e = 0; e < 2; e++) d += Bm[(rc * 2 + h) * RB_XW + qx + e] * v[h][e];
-                    dsum = (double)d;
+                    dsum = d;
                 }
             }
             if constexpr (kDot) {
                 for (int o = 16; o > 0; o >>= 1) dsum += __shfl_down_sync(0xffffffffu, dsum, o);
-                if ((tid & 31) == 0) wsum[tid >> 5] = dsum;
+                if ((tid & 31) == 0) wsum[tid >> 5] = (double)dsum;
             }
         }
         __syncthreads();
@@ -852,7 +906,7 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
             }
             if (q + 2 < nstep) {
                 fence_proxy_async();
-                rb_issue<F>(sm, bar, q + 2, m0, p0, y0, kZero, tm);
+                rb_issue<F>(sm, bar, q + 2, m0, p0, y0, kZero, kCorr, tm);
             }
         }
     }
@@ -903,11 +957,11 @@ __global__ void __launch_bounds__(RB_THREADS) k_cc_gs2_dot(VOp<float> A, float *
     const int r = tid >> 4;
     const int j = blockIdx.y * RB_TY + r, pq = blockIdx.x * RB_HW + 2 * (tid & 15);
     const int sy = g.nx, sz = g.nx * g.ny;
-    double dsum[kGs2Planes];
+    float dsum[kGs2Planes];
 #pragma unroll
     for (int pl = 0; pl < kGs2Planes; pl++) {
         const int k = blockIdx.z * kGs2Planes + pl;
-        dsum[pl] = 0.0;
+        dsum[pl] = 0.f;
         if (j >= g.ny || pq >= hx || k >= g.nz) continue;
         const int h2 = (c1 + j + k) & 1;
         const int rc = (k * g.ny + j) * g.nx;
@@ -954,13 +1008,14 @@ __global__ void __launch_bounds__(RB_THREADS) k_cc_gs2_dot(VOp<float> A, float *
         d += b0[1] * v0[1];
         d += b1[0] * v1[0];
         d += b1[1] * v1[1];
-        dsum[pl] = (double)d;
+        dsum[pl] = d;
     }
+    // per warp in FP32, across the 8 warps in FP64 (as k_cc_rb_sweep<kDot>)
 #pragma unroll
     for (int pl = 0; pl < kGs2Planes; pl++) {
-        double v = dsum[pl];
+        float v = dsum[pl];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0) wsum[pl][tid >> 5] = v;
+        if ((tid & 31) == 0) wsum[pl][tid >> 5] = (double)v;
     }
     __syncthreads();
     if (tid < kGs2Planes) {
@@ -2583,11 +2638,10 @@ NdOp<T> ndop(const NdLevel &L)
 // V-cycles
 // ---------------------------------------------------------------------------
 
-// Profiler names of the colour sweeps, by precision and level (level 0 is
-// HBM-bound; the coarse levels are latency- and launch-bound).
-// Profiling labels of the colour passes per precision and level: plain
-// passes (from zero or not), the pass after the coarse correction, and the
-// pass that also forms r.z.
+// Profiling labels of the colour passes per precision and level (level 0 is
+// HBM-bound; the coarse levels are latency- and launch-bound): plain passes
+// (from zero or not), the pass after the coarse correction, and the pass
+// that also forms r.z; and of the residual-restriction per level.
 static const char *const kGsName[2][8] = {
     {"cc_gs_colour_pass<double> L0", "cc_gs_colour_pass<double> L1", "cc_gs_colour_pass<double> L2",
      "cc_gs_colour_pass<double> L3", "cc_gs_colour_pass<double> L4", "cc_gs_colour_pass<double> L5",
@@ -2603,6 +2657,11 @@ static const char *const kGsCorrName[2][8] = {
      "cc_gs_correction_pass<float> L3", "cc_gs_correction_pass<float> L4", "cc_gs_correction_pass<float> L5",
      "cc_gs_correction_pass<float> L6", "cc_gs_correction_pass<float> L7+"}};
 static const char *const kGsDotName[2] = {"cc_gs_rz_pass<double> L0", "cc_gs_rz_pass<float> L0"};
+static const char *const kRrName[2][4] = {
+    {"cc_residual_restrict<double> L0", "cc_residual_restrict<double> L1", "cc_residual_restrict<double> L2",
+     "cc_residual_restrict<double> L3+"},
+    {"cc_residual_restrict<float> L0", "cc_residual_restrict<float> L1", "cc_residual_restrict<float> L2",
+     "cc_residual_restrict<float> L3+"}};
 
 // Two red-black Gauss-Seidel sweeps in place (the first from x = 0 when
 // zero_start), each as two colour passes.
@@ -2632,7 +2691,9 @@ inline bool rb_fusable(const GridD &g)
 
 // Tensor map of one array of the level, by box kind: 0 x (FP32 cells, tile +
 // 2 rows each side), 1 FP32 cells (tile + 1 row), 2 y faces, 3 z faces, 4 the
-// padded x faces; the array viewed as (half-row position, half, row, plane).
+// padded x faces, 5 the coarse correction (g the coarse level: the parents
+// of the tile and its ring); the array viewed as (half-row position, half,
+// row, plane).
 bool rb_map(Ctx *c, const void *p, int kind, const GridD &g, CUtensorMap *out)
 {
     if (!p) return false;
@@ -2641,14 +2702,14 @@ bool rb_map(Ctx *c, const void *p, int kind, const GridD &g, CUtensorMap *out)
             *out = e.m;
             return true;
         }
-    const bool face = kind >= 2;
+    const bool face = kind >= 2 && kind <= 4;
     const uint64_t es = face ? sizeof(RbF) : 4;
     const uint64_t hx = kind == 4 ? (uint64_t)rb_hxp(g.nx) : (uint64_t)g.nx / 2;
     const uint64_t rows = kind == 2 ? g.ny + 1 : g.ny, planes = kind == 3 ? g.nz + 1 : g.nz;
     const uint64_t dims[4] = {hx, 2, rows, planes};
     const uint64_t st[3] = {hx * es, 2 * hx * es, rows * 2 * hx * es};
-    const uint32_t box[4] = {(uint32_t)(face ? RB_FW : RB_XW), 2u,
-                             (uint32_t)(kind == 0 ? RB_XR : (kind == 2 ? RB_YR : RB_CR)), 1u};
+    const uint32_t box[4] = {(uint32_t)(kind == 5 ? RB_KW : (face ? RB_FW : RB_XW)), 2u,
+                             (uint32_t)(kind == 0 ? RB_XR : (kind == 2 ? RB_YR : (kind == 5 ? RB_KR : RB_CR))), 1u};
     const CUtensorMapDataType ty = (face && sizeof(RbF) == 2) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     Ctx::TmaEntry e;
@@ -2710,12 +2771,10 @@ int rb_kz(const GridD &g)
 
 // One fused sweep (maps already encoded by rb_maps).
 void rb_launch(Ctx *c, const char *name, const GridD &g, const RbMaps &tm, float *xout, int c0, int mode,
-               const float *xc, const GridD *gc, double *part, int kz = 0)
+               double *part, int kz = 0)
 {
     RbArgs<RbF> a;
     a.g = g;
-    a.gc = gc ? *gc : GridD();
-    a.xc = xc;
     a.xout = xout;
     a.part = part;
     a.ctl = c->ctl;
@@ -2779,17 +2838,23 @@ int cc_smooth2(Ctx *c, const CcLevel &L, int l, T *x, T *t, const T *b, bool red
             const int k1 = zero_start ? RB_ZERO : (xc ? RB_CORR : RB_PLAIN), k2 = dot_part ? RB_DOT : RB_PLAIN;
             // (the pair runs x -> t -> x fused, or in place as passes: one form for both)
             const bool faster = L.rb_ms[k1][0] + L.rb_ms[k2][0] < L.rb_ms[k1][1] + L.rb_ms[k2][1];
-            if ((mode == 2 || (mode == 1 && faster)) && rb_map(c, x, 0, g, &m1.x) && rb_map(c, t, 0, g, &m2.x) &&
-                rb_map(c, b, 1, g, &m1.b) && rb_map(c, A.dinv, 1, g, &m1.d) && rb_map(c, L.bxp, 4, g, &m1.fx) &&
-                rb_map(c, A.by, 2, g, &m1.fy) && rb_map(c, A.bz, 3, g, &m1.fz)) {
+            bool use = (mode == 2 || (mode == 1 && faster)) && rb_map(c, x, 0, g, &m1.x) &&
+                       rb_map(c, t, 0, g, &m2.x) && rb_map(c, b, 1, g, &m1.b) && rb_map(c, A.dinv, 1, g, &m1.d) &&
+                       rb_map(c, L.bxp, 4, g, &m1.fx) && rb_map(c, A.by, 2, g, &m1.fy) &&
+                       rb_map(c, A.bz, 3, g, &m1.fz);
+            if (use) {
                 m2.b = m1.b;
                 m2.d = m1.d;
                 m2.fx = m1.fx;
                 m2.fy = m1.fy;
                 m2.fz = m1.fz;
+                m1.xc = m2.xc = m1.b;   // (read by the correction sweep only)
+                if (k1 == RB_CORR) use = rb_map(c, xc, 5, *gc, &m1.xc);
+            }
+            if (use) {
                 const char *nm = kRbName[l < 7 ? l : 7];
-                rb_launch(c, nm, g, m1, t, c0, k1, xc, gc, nullptr, L.rb_kz);
-                rb_launch(c, nm, g, m2, x, c0, k2, nullptr, nullptr, dot_part, L.rb_kz);
+                rb_launch(c, nm, g, m1, t, c0, k1, nullptr, L.rb_kz);
+                rb_launch(c, nm, g, m2, x, c0, k2, dot_part, L.rb_kz);
                 return dot_part ? rb_ntiles(g) * g.nz : 0;
             }
         }
@@ -3706,7 +3771,7 @@ ebv_status autotune_shapes_t(Ctx *c)
                 float best = 1e30f;
                 for (int kz : kzc) {
                     const float ms = time_it(
-                        [&]() { rb_launch(c, "autotune", L.g, m, y, 0, RB_PLAIN, nullptr, nullptr, nullptr, kz); });
+                        [&]() { rb_launch(c, "autotune", L.g, m, y, 0, RB_PLAIN, nullptr, kz); });
                     if (ms < best) { best = ms; L.rb_kz = kz; }
                 }
                 // the correction sweep reads a coarse array: a zeroed vector with the next level's dims
@@ -3717,10 +3782,11 @@ ebv_status autotune_shapes_t(Ctx *c)
                 const dim3 bk = L.gs_blk, grc = gs_grid(L.g, bk);
                 for (int kind = 0; kind < 4; kind++) {
                     if (kind == RB_CORR && !has_c) continue;   // (no correction sweep on the last level)
-                    const float *xcv = kind == RB_CORR ? d : nullptr;
+                    RbMaps mk = m;
+                    mk.xc = m.b;
+                    if (kind == RB_CORR && !rb_map(c, d, 5, gc, &mk.xc)) continue;
                     const float ms_f = time_it([&]() {
-                        rb_launch(c, "autotune", L.g, m, y, 0, kind, xcv, kind == RB_CORR ? &gc : nullptr,
-                                  kind == RB_DOT ? c->part : nullptr, L.rb_kz);
+                        rb_launch(c, "autotune", L.g, mk, y, 0, kind, kind == RB_DOT ? c->part : nullptr, L.rb_kz);
                     });
                     const float ms_p = time_it([&]() {
                         if (kind == RB_CORR) {
