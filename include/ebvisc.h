@@ -62,20 +62,17 @@ enum { EBV_INFLOW = 0, EBV_OUTFLOW = 1, EBV_SLIP = 2, EBV_NOSLIP = 3 };
 /* Rheology (paper Table "Generalised Newtonian fluid models"). */
 enum { EBV_NEWTONIAN = 0, EBV_BINGHAM = 1, EBV_HERSCHEL_BULKLEY = 2, EBV_POWER_LAW = 3,
        EBV_SOUZA_MENDES_DUTRA = 4 };
-/* Precision of the linear solves.  EBV_FP64: conjugate gradients and
- * multigrid in FP64.  EBV_FP32_REFINE: FP64 iterative refinement (FP64
- * operator, residual and solution) around corrections solved by FP32
- * conjugate gradients with an FP32 multigrid preconditioner whose V-cycle
- * stores its cell-centred face coefficients in BF16; both converge to
- * ebv_params.tol.  Geometry and every field are FP64 in both. */
-/* Precision forms.  EBV_FP32_REFINE: every linear solve is iterative
- * refinement, FP64 residual and solution around FP32 conjugate gradients and
- * an FP32 multigrid V-cycle; everything else FP64.  EBV_FP32_MIXED: the same,
- * and the strain rate and apparent viscosity of fluid cells away from the EB
- * (neither cut nor next to a cut cell, all six neighbours fluid) are formed in
- * FP32 from FP64 velocity differences, the near-wall ones in FP64 (results
- * within about 1e-7 of FP64 rather than 1e-10; the adjoint differentiates the
- * FP64 formula). */
+/* Precision forms; every one converges each linear solve to ebv_params.tol.
+ * EBV_FP64: conjugate gradients and multigrid in FP64.  EBV_FP32_REFINE:
+ * every linear solve is FP64 iterative refinement (FP64 operator, residual
+ * and solution) around corrections solved by FP32 conjugate gradients with an
+ * FP32 multigrid preconditioner whose cell-centred V-cycle stores its face
+ * coefficients in BF16; geometry and every field FP64.  EBV_FP32_MIXED: the
+ * same, and the strain rate and apparent viscosity of fluid cells away from
+ * the EB (neither cut nor next to a cut cell, all six neighbours fluid) are
+ * formed in FP32 from FP64 velocity differences, the near-wall ones in FP64
+ * (results within about 1e-7 of FP64 rather than 1e-10; the adjoint
+ * differentiates the FP64 formula). */
 enum { EBV_FP64 = 0, EBV_FP32_REFINE = 1, EBV_FP32_MIXED = 2 };
 
 typedef struct {

@@ -2480,8 +2480,26 @@ __global__ void __launch_bounds__(256) k_cg_update32(float *__restrict__ r, cons
 {
     const float a = (float)(scal[S_RZ] / scal[S_PQ]);
     float v = 0.0f;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        float rs = r[s] - a * q[s];
+    // 16-byte vectors (the arrays come from cudaMalloc), then the n % 4 tail:
+    // four independent loads per thread keep enough bytes in flight
+    const int n4 = n >> 2, t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    float4 *r4 = reinterpret_cast<float4 *>(r);
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    for (int s = t0; s < n4; s += st) {
+        float4 rs = r4[s];
+        const float4 qs = q4[s];
+        rs.x = rs.x - a * qs.x;
+        rs.y = rs.y - a * qs.y;
+        rs.z = rs.z - a * qs.z;
+        rs.w = rs.w - a * qs.w;
+        r4[s] = rs;
+        v += rs.x * rs.x;
+        v += rs.y * rs.y;
+        v += rs.z * rs.z;
+        v += rs.w * rs.w;
+    }
+    for (int s = 4 * n4 + t0; s < n; s += st) {
+        const float rs = r[s] - a * q[s];
         r[s] = rs;
         v += rs * rs;
     }
@@ -2942,7 +2960,7 @@ int cc_vcycle(Ctx *c, CcHier &H, const T *b0, T *x0, double *dot_part = nullptr)
         const CcLevel &Lc = H.lv[l + 1];
         // x, b, diagonal, 3 faces (storage type) read, 1/8 word written
         const double nbr = ((3.0 + 1.0 / 8.0) * sizeof(T) + 3.0 * sizeof(typename VFace<T>::type)) * (double)ncell(L.g);
-        const char *nmr = sizeof(T) == 4 ? "cc_residual_restrict<float>" : "cc_residual_restrict<double>";
+        const char *nmr = kRrName[sizeof(T) == 4][l < 3 ? l : 3];
         bool vec = false;
         if constexpr (sizeof(T) == 4) {
             const dim3 bk(8, 8, 4), gr((Lc.g.nx / 4 + bk.x - 1) / bk.x, (Lc.g.ny + bk.y - 1) / bk.y,
