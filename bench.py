@@ -59,6 +59,8 @@ def parse():
                     help="also time the oracle on the 128^3 sphere channel (minutes)")
     ap.add_argument("--eager", action="store_true",
                     help="issue every step kernel by kernel (no step graph), e.g. under a profiler")
+    ap.add_argument("--inner-drop", type=float, default=1e-4,
+                    help="residual drop of each FP32 correction solve of the refinement (ebv_set_inner_drop)")
     ap.add_argument("--fused-sweep", type=int, default=1, choices=[0, 1, 2],
                     help="smoother sweeps of FP32 levels: 0 colour passes, 1 the faster form per level "
                          "(timed at set-up, default), 2 the fused one-pass sweep (same results)")
@@ -266,6 +268,7 @@ def run_ours(args, rank, world, local):
     from paper_1905_07392_gb300 import build_lib, ebvisc
     build_lib.build()
     ebvisc.load().ebv_set_fused_sweep(args.fused_sweep)
+    ebvisc.load().ebv_set_inner_drop(args.inner_drop)
     dev = torch.device("cuda", local)
     w = workload(args.n)
     cells = w.n ** 3

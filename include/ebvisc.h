@@ -305,6 +305,15 @@ void ebv_set_spin_limit(long long cycles);
  * Process-wide; read when a step is issued or captured. */
 void ebv_set_fused_sweep(int mode);
 
+/* EBV_FP32_REFINE / EBV_FP32_MIXED: the factor by which each FP32 correction
+ * solve of the iterative refinement reduces its residual before the FP64
+ * residual is formed again (default 1e-4; the last correction of a solve aims
+ * only for what the tolerance still needs).  Values outside (0, 1) restore
+ * the default.  Changes the number of corrections and inner iterations, not
+ * the tolerance the solves meet.  Process-wide; read when a step is issued or
+ * captured. */
+void ebv_set_inner_drop(double drop);
+
 /* Measurement hook: the times (ms, four launches each) that chose the form
  * of one kind of red-black sweep on level `level` of the MAC hierarchy when
  * the context's solvers were set up (ebv_set_fused_sweep mode 1): kind 0 the

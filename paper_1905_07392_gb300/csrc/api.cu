@@ -42,6 +42,7 @@ cudaError_t dev_malloc(void **p, size_t bytes)
 extern "C" void ebv_set_alloc_limit(long long bytes) { g_alloc_budget.store(bytes < 0 ? -1 : bytes); }
 extern "C" void ebv_set_spin_limit(long long cycles) { ebv::set_spin_limit(cycles); }
 extern "C" void ebv_set_fused_sweep(int mode) { ebv::set_fused_sweep(mode); }
+extern "C" void ebv_set_inner_drop(double drop) { ebv::set_inner_drop(drop); }
 
 namespace {
 

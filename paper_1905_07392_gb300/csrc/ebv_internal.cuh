@@ -365,6 +365,11 @@ long long spin_limit();
 int fused_sweep_mode();
 void set_spin_limit(long long cycles);
 void set_fused_sweep(int mode);
+// The drop of the residual each FP32 correction solve of the refinement aims
+// for (ebv_set_inner_drop), read when a solve is issued or captured.
+double refine_inner_drop();
+void set_inner_drop(double drop);
+constexpr double kInnerDropDefault = 1e-4;
 constexpr long long kSpinDefault = 2000000000LL;   // about 1 s at the maximum SM clock
 constexpr long long kRbDrainCycles = 4000000000LL; // waiting for loads in flight after a timeout
 

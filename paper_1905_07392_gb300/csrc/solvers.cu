@@ -2516,14 +2516,36 @@ __global__ void k_cg_pupdate32(float *__restrict__ p, float *__restrict__ e, con
     const int k = ctl[C_K];
     const float beta = k == 0 ? 0.0f : (float)(scal[S_RZ] / scal[S_RZOLD]);
     const float a = k == 0 ? 0.0f : (float)(scal[S_RZOLD] / scal[S_PQ]);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    // one element: the same operations as before, for each lane of a vector
+    auto upd = [&](float &pv, float &ev, float zv) {
         if (k == 0) {
-            p[s] = z[s];
+            pv = zv;
         } else {
-            const float po = p[s];
-            e[s] = k == 1 ? a * po : e[s] + a * po;
-            p[s] = z[s] + beta * po;
+            const float po = pv;
+            ev = k == 1 ? a * po : ev + a * po;
+            pv = zv + beta * po;
         }
+    };
+    // 16-byte vectors (cudaMalloc'd arrays), then the n % 4 tail
+    const int n4 = n >> 2, t0 = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    float4 *p4 = reinterpret_cast<float4 *>(p), *e4 = reinterpret_cast<float4 *>(e);
+    const float4 *z4 = reinterpret_cast<const float4 *>(z);
+    for (int s = t0; s < n4; s += st) {
+        const float4 zv = z4[s];
+        float4 pv = k == 0 ? zv : p4[s];
+        float4 ev = k >= 2 ? e4[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        upd(pv.x, ev.x, zv.x);
+        upd(pv.y, ev.y, zv.y);
+        upd(pv.z, ev.z, zv.z);
+        upd(pv.w, ev.w, zv.w);
+        p4[s] = pv;
+        if (k >= 1) e4[s] = ev;
+    }
+    for (int s = 4 * n4 + t0; s < n; s += st) {
+        float pv = k == 0 ? z[s] : p[s], ev = k >= 2 ? e[s] : 0.f;
+        upd(pv, ev, z[s]);
+        p[s] = pv;
+        if (k >= 1) e[s] = ev;
     }
 }
 
@@ -3332,7 +3354,7 @@ ebv_status pcg_refine(Ctx *c, Problem &P, const double *b, double *x, int *iters
     const int n = P.n();
     const double tol = c->prm.tol;
     const int maxit = c->prm.max_iters;
-    const double inner_drop = 1e-4;
+    const double inner_drop = refine_inner_drop();
     float *r = c->kr32, *z = c->kz32, *p = c->kp32, *q = c->kq32, *e = c->ke32;
     // x_zero: the first residual is b itself (its norm is |b|^2, reduced below)
     bool first_is_b = x_zero;
@@ -3905,6 +3927,7 @@ ebv_status nodal_solve(Ctx *c, const double *b, double *x, int *iters, double *r
 namespace {
 long long g_spin = kSpinDefault;
 int g_fused = 1;
+double g_inner_drop = kInnerDropDefault;
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -3913,6 +3936,8 @@ long long spin_limit() { return g_spin; }
 int fused_sweep_mode() { return g_fused; }
 void set_spin_limit(long long cycles) { g_spin = cycles < 0 ? kSpinDefault : cycles; }
 void set_fused_sweep(int mode) { g_fused = mode < 0 ? 0 : (mode > 2 ? 2 : mode); }
+double refine_inner_drop() { return g_inner_drop; }
+void set_inner_drop(double drop) { g_inner_drop = (drop > 0.0 && drop < 1.0) ? drop : kInnerDropDefault; }
 
 bool tma_encode_4d(CUtensorMap *tm, CUtensorMapDataType type, void *base, const uint64_t dims[4],
                    const uint64_t strides[3], const uint32_t box[4])

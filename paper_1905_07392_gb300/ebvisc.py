@@ -73,7 +73,7 @@ EXPORTS = ["ebv_create", "ebv_set_params", "ebv_build_geometry", "ebv_build_geom
            "ebv_batch_instance", "ebv_batch_advance", "ebv_batch_launch_count",
            "ebv_batch_last_error", "ebv_batch_destroy", "ebv_adjoint_step", "ebv_drag_adjoint",
            "ebv_drag_gradient_workspace", "ebv_drag_gradient", "ebv_set_alloc_limit",
-           "ebv_set_spin_limit", "ebv_set_fused_sweep", "ebv_sweep_timing",
+           "ebv_set_spin_limit", "ebv_set_fused_sweep", "ebv_set_inner_drop", "ebv_sweep_timing",
            "ebv_save_state", "ebv_load_state", "ebv_build_geometry_spheres",
            "ebv_build_geometry_bodies"]
 
@@ -149,6 +149,7 @@ def _open(path):
         "ebv_set_alloc_limit": ([C.c_longlong], None),
         "ebv_set_spin_limit": ([C.c_longlong], None),
         "ebv_set_fused_sweep": ([C.c_int], None),
+        "ebv_set_inner_drop": ([C.c_double], None),
         "ebv_sweep_timing": ([vp, C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
         "ebv_save_state": ([vp, vp, vp, C.c_char_p], C.c_int),
         "ebv_build_geometry_spheres": ([vp, C.c_int, dp], C.c_int),
