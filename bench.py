@@ -231,7 +231,9 @@ def measured_peaks():
 # DRAM bytes (read + write) per algorithmic byte, from one ncu capture of the
 # current kernel on a smaller grid (192^3, traffic grows with the cells);
 # the reported traffic is this ratio times the algorithmic bytes per launch.
-NCU_TRAFFIC_RATIO = {"cc_gs_colour_pass<float> L0": 1.16, "cc_rb_sweep<float> L0": 1.00}
+# The fused sweep's figure is over its four kinds (from zero, plain, after the
+# coarse correction, with r.z), which share the L0 label.
+NCU_TRAFFIC_RATIO = {"cc_gs_colour_pass<float> L0": 1.16, "cc_rb_sweep<float> L0": 0.97}
 
 
 def roofline(prof, cells):
