@@ -19,7 +19,7 @@
 //   grad_p (k_psi, k_add_gradp)  k_gradp_t
 //   k_nodal_rhs (in ut)       k_nodal_rhs_t
 //   k_drag_terms              k_drag_adj
-//   k_slopes                  k_slopes_adj        (MC limiter)
+//   k_slopes_march            k_slopes_adj        (MC limiter)
 //   k_face_states             k_face_states_adj   (Godunov upwinding)
 //   k_mac_rhs / k_mac_correct k_mac_rhs_adj / k_mac_correct_adj (with one MAC solve)
 //   k_conv_flux               k_conv_flux_adj

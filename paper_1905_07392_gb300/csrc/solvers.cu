@@ -15,6 +15,8 @@
 #include <math.h>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "ebv_internal.cuh"
 #include "tma.cuh"
 #include "fpbits.cuh"
@@ -86,12 +88,33 @@ __device__ inline double block_sum3_t(T v)
     }
 }
 
-__global__ void __launch_bounds__(1024) k_reduce_final(const double *part, int n, double *out)
+// Sum of n block partials in a fixed order, over a cluster of kRedCtas
+// blocks: block q sums the slice [q n / kRedCtas, (q + 1) n / kRedCtas)
+// (strided over its threads, then its block sum) and stores that sum in
+// block 0's shared memory; after the cluster barrier block 0 adds the
+// kRedCtas sums in rank order.  FP64 additions issue at about one per SM and
+// cycle on this GPU, so a single block spent up to 16 us on the 32,768
+// partials of a 256^3 refinement residual; the cluster spreads them over
+// kRedCtas SMs.  The barrier is the hardware cluster barrier (no spin).
+constexpr int kRedCtas = 8, kRedThreads = 512;
+__global__ void __cluster_dims__(kRedCtas, 1, 1) __launch_bounds__(kRedThreads)
+    k_reduce_final(const double *part, int n, double *out)
 {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double csum[kRedCtas];
+    const int q = (int)cl.block_rank();
+    const int lo = (int)((long long)n * q / kRedCtas), hi = (int)((long long)n * (q + 1) / kRedCtas);
     double v = 0.0;
-    for (int s = threadIdx.x; s < n; s += 1024) v += part[s];
-    v = block_sum<1024>(v);
-    if (threadIdx.x == 0) *out = v;
+    for (int s = lo + threadIdx.x; s < hi; s += kRedThreads) v += part[s];
+    v = block_sum<kRedThreads>(v);
+    if (threadIdx.x == 0) *cl.map_shared_rank(&csum[q], 0) = v;
+    cl.sync();
+    if (q == 0 && threadIdx.x == 0) {
+        double t = 0.0;
+        for (int r = 0; r < kRedCtas; r++) t += csum[r];
+        *out = t;
+    }
 }
 
 __global__ void __launch_bounds__(256) k_dot(const double *__restrict__ a, const double *__restrict__ b,
@@ -108,7 +131,7 @@ __global__ void __launch_bounds__(256) k_dot(const double *__restrict__ a, const
 
 ebv_status reduce_sum(Ctx *c, const double *part, int nblocks, double *out_dev)
 {
-    EBV_LAUNCH(c, k_reduce_final, dim3(1), dim3(1024), 0, part, nblocks, out_dev);
+    EBV_LAUNCH(c, k_reduce_final, dim3(kRedCtas), dim3(kRedThreads), 0, part, nblocks, out_dev);
     return EBV_OK;
 }
 
