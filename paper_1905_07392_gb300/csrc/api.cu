@@ -143,18 +143,29 @@ ebv_status derived(Ctx *c, const double *u, double *C, double *eta, double *V, i
     return EBV_OK;
 }
 
-__global__ void k_init_guess(int n3, const uint8_t *flag, const double *psi, double rho, double *ut)
+// ut = psi / rho on fluid cells (0 on covered ones), the viscous solves'
+// initial guess.  An FP64 division is about fifteen FP64-pipe instructions on
+// this GPU, so when rho is a power of two (rho = 1 in the usual scaling) the
+// kernel multiplies by the exact reciprocal instead: the same bits.
+__global__ void k_init_guess(int n3, const uint8_t *flag, const double *psi, double rho, double inv_rho,
+                             int exact_inv, double *ut)
 {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < 3 * n3; s += gridDim.x * blockDim.x) {
-        int c = s % n3;
-        ut[s] = flag[c] ? psi[s] / rho : 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += gridDim.x * blockDim.x) {
+        const bool fl = flag[c] != 0;
+        for (int q = 0; q < 3; q++) {
+            const int s = q * n3 + c;
+            ut[s] = fl ? (exact_inv ? psi[s] * inv_rho : psi[s] / rho) : 0.0;
+        }
     }
 }
 
 ebv_status viscous_update(Ctx *c, const double *eta, const double *psi, double *ut, ebv_step_stats *st, int slot)
 {
     const int N3 = ncell(c->g);
-    EBV_LAUNCH(c, k_init_guess, dim3(kReduceBlocks), dim3(256), 0, N3, c->flag, psi, c->prm.rho, ut);
+    int e2 = 0;
+    const bool pow2 = frexp(c->prm.rho, &e2) == 0.5;   // rho = 2^(e2 - 1): 1/rho exact
+    EBV_LAUNCH(c, k_init_guess, dim3(kReduceBlocks), dim3(256), 0, N3, c->flag, psi, c->prm.rho, 1.0 / c->prm.rho,
+               pow2 ? 1 : 0, ut);
     TRY(visc_build(c, eta));
     for (int q = 0; q < 3; q++) {
         int it = 0;

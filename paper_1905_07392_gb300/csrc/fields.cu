@@ -400,15 +400,22 @@ __global__ void __launch_bounds__(256) k_conv_flux(GridD g, int d, const double 
         return;
     }
     const int cL = cidx(g, i - e.x, j - e.y, k - e.z), cR = cidx(g, i, j, k);
-    // only the upwind side's state is formed (fewer FP64 operations)
+    // only the upwind side's state is formed (fewer FP64 operations), and the
+    // side is chosen before the arithmetic: faces of either sign in one warp
+    // run the same instructions (u_L + S_L/2 or u_R - S_R/2, one FMA each, as
+    // before).  Across the flow the sign of w alternates between neighbouring
+    // faces, and branching on it ran both halves in most warps.
     const double aw = a * w;
-    for (int q = 0; q < 3; q++) {
-        double state;
-        if (w > 0.0) state = u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL];
-        else if (w < 0.0) state = u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR];
-        else state = 0.5 * ((u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL]) +
-                            (u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR]));
-        F[q * nft + off + f] = aw * state;
+    if (w != 0.0) {
+        const int cs = w > 0.0 ? cL : cR;
+        const double hs = w > 0.0 ? 0.5 : -0.5;
+        for (int q = 0; q < 3; q++) F[q * nft + off + f] = aw * (u[q * N3 + cs] + hs * S[(3 * d + q) * N3 + cs]);
+    } else {
+        for (int q = 0; q < 3; q++) {
+            const double state = 0.5 * ((u[q * N3 + cL] + 0.5 * S[(3 * d + q) * N3 + cL]) +
+                                        (u[q * N3 + cR] - 0.5 * S[(3 * d + q) * N3 + cR]));
+            F[q * nft + off + f] = aw * state;
+        }
     }
 }
 

@@ -921,16 +921,16 @@ __global__ void __launch_bounds__(RB_THREADS, 2)
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            if (kDot && q >= 2) {
-                double s = 0.0;
-                for (int w = 0; w < RB_THREADS / 32; w++) s += wsum[w];
-                a.part[(size_t)mm * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = s;
-            }
-            if (q + 2 < nstep) {
-                fence_proxy_async();
-                rb_issue<F>(sm, bar, q + 2, m0, p0, y0, kZero, kCorr, tm);
-            }
+        // the plane's partial from the warp sums (FP64) in warp 1, so that
+        // thread 0 issues the next loads at once
+        if (kDot && q >= 2 && tid == 32) {
+            double s = 0.0;
+            for (int w = 0; w < RB_THREADS / 32; w++) s += wsum[w];
+            a.part[(size_t)mm * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = s;
+        }
+        if (tid == 0 && q + 2 < nstep) {
+            fence_proxy_async();
+            rb_issue<F>(sm, bar, q + 2, m0, p0, y0, kZero, kCorr, tm);
         }
     }
 }
