@@ -1105,8 +1105,10 @@ __global__ void __launch_bounds__(256) k_cc_resid_restrict(VOp<T> A, const T *__
 // BF16) vectors, as in k_cc_gs4.  Children and operations in the order of
 // rr_cell (rows (2J,2K), (2J+1,2K), (2J,2K+1), (2J+1,2K+1)), so the results
 // are the same bits; the coarse values go out as two 8-byte pairs (even and
-// odd coarse cells are the two halves of the coarse row).
-__global__ void __launch_bounds__(256) k_cc_rr4(VOp<float> A, const float *__restrict__ x,
+// odd coarse cells are the two halves of the coarse row).  Bound by load
+// latency: capped at 64 registers (from 75) for four blocks per SM, 16 %
+// faster at 256^3.
+__global__ void __launch_bounds__(256, 4) k_cc_rr4(VOp<float> A, const float *__restrict__ x,
                                                const float *__restrict__ b, GridD gc, float *__restrict__ bc)
 {
     const GridD &g = A.g;
@@ -1478,7 +1480,8 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
 // two planes, with 16-byte loads as in k_cc_gs4 (the x faces, rows of nx + 1,
 // as scalars), and adds p.q of its 8 cells to its block's partial.  Each q is
 // formed as in cc_row; the partial sums are grouped by this kernel's fixed
-// block shape (kApply4Blk).
+// block shape (kApply4Blk).  (Capped at 48 registers for five blocks per SM
+// it measured no faster than at 64 registers and four.)
 constexpr int kApply4X = 16, kApply4Y = 8, kApply4Z = 2;
 // The vectorised apply and restriction serve grids where they launch at least
 // this many blocks (two per SM of 152); smaller grids keep one cell per thread.
