@@ -1,4 +1,4 @@
-"""CPU models of the index and bit-level logic of three CUDA kernels (no GPU).
+"""CPU models of the index and bit-level logic of five CUDA kernels (no GPU).
 
 Each model repeats in Python, step by step, what one kernel does with its
 data -- which boxes it stages into which ring slot, which lane or row hands a
@@ -17,7 +17,11 @@ and is compared with the plain definition of the same result:
 * k_slopes_march (fields.cu): the face differences handed on by lane shuffle,
   shared row and register, against the direct differences, bit for bit;
 * mc_limit (fields.cu): the monotonised-central limiter on the 32-bit words of
-  the IEEE patterns, against the same limiter on 64-bit patterns.
+  the IEEE patterns, against the same limiter on 64-bit patterns;
+* k_cc_rr4 (solvers.cu): residual and restriction with 4-wide vectors,
+  against the residuals of the first-colour children averaged one by one;
+* k_cc_gs2_dot (solvers.cu): the last colour pass forming the fused sweep's
+  (plane, tile) partials of b.x, against the fused sweep's own.
 
 These are models of the kernels' logic, not the kernels; the GPU tests
 compare the kernels with the oracle.
@@ -426,3 +430,174 @@ def test_limiter_words_match_64bit_patterns():
         if a[0] == "bits":
             a = ("bits", a[1] & 0xFFFFFFFFFFFFFFFF)
         assert a == b, (dl, dr, dd, a, b)
+
+
+# ---- k_cc_rr4: residual and restriction, four coarse cells per thread -----
+def _split_pos(m, i):
+    return ((m + 1) >> 1) + (i >> 1) if i & 1 else i >> 1
+
+
+@pytest.mark.parametrize("shape", [(16, 4, 6), (24, 6, 2), (8, 2, 2), (32, 10, 4)])
+def test_rr4_model_matches_residual_restriction(shape):
+    """k_cc_rr4: the coarse value is the mean of the residuals of the fine
+    cells of the first colour (i + j + k even) among its 8 children; the
+    kernel's thread forms coarse cells I0 .. I0+3 of a coarse row from
+    4-wide vectors of the half-rows that hold those children, and writes
+    them as two pairs (even and odd coarse cells)."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(0)
+    N = nx * ny * nz
+    x, b, dg = rng.standard_normal(N), rng.standard_normal(N), rng.uniform(1, 2, N)
+    bx = rng.uniform(0, 1, (nx + 1) * ny * nz)
+    by = rng.uniform(0, 1, nx * (ny + 1) * nz)
+    bz = rng.uniform(0, 1, nx * ny * (nz + 1))
+    cix = lambda i, j, k: (k * ny + j) * nx + _split_pos(nx, i)
+
+    def face(d, i, j, k):
+        if d == 0: return (k * ny + j) * (nx + 1) + _split_pos(nx + 1, i)
+        if d == 1: return (k * (ny + 1) + j) * nx + _split_pos(nx, i)
+        return (k * ny + j) * nx + _split_pos(nx, i)
+    gnx, gny, gnz = nx // 2, ny // 2, nz // 2
+    ref = np.zeros(gnx * gny * gnz)
+    for K, J, I in itertools.product(range(gnz), range(gny), range(gnx)):
+        s = 0.0
+        for o in range(8):
+            if bin(o).count("1") & 1:
+                continue
+            i, j, k = 2 * I + (o & 1), 2 * J + ((o >> 1) & 1), 2 * K + ((o >> 2) & 1)
+            c, off = cix(i, j, k), 0.0
+            if i > 0: off += bx[face(0, i, j, k)] * x[cix(i - 1, j, k)]
+            if i < nx - 1: off += bx[face(0, i + 1, j, k)] * x[cix(i + 1, j, k)]
+            if j > 0: off += by[face(1, i, j, k)] * x[c - nx]
+            if j < ny - 1: off += by[face(1, i, j + 1, k)] * x[c + nx]
+            if k > 0: off += bz[face(2, i, j, k)] * x[c - nx * ny]
+            if k < nz - 1: off += bz[face(2, i, j, k + 1)] * x[c + nx * ny]
+            s += b[c] - (dg[c] * x[c] - off)
+        ref[(K * gny + J) * gnx + _split_pos(gnx, I)] = s * 0.125
+    out = np.full(gnx * gny * gnz, np.nan)
+    hx, hf, sy, sz = nx >> 1, (nx + 2) >> 1, nx, nx * ny
+    for K, J, I0 in itertools.product(range(gnz), range(gny), range(0, gnx, 4)):
+        acc = [0.0] * 4
+        for kk, jj in itertools.product(range(2), range(2)):
+            j, k = 2 * J + jj, 2 * K + kk
+            h = (j + k) & 1                       # the half holding the first colour's children
+            rc = (k * ny + j) * nx
+            c, o = rc + (hx if h else 0) + I0, rc + (0 if h else hx) + I0
+            assert c % 4 == 0 and o % 4 == 0      # 16-byte vectors
+            xc4, bb, d4, xo = x[c:c + 4], b[c:c + 4], dg[c:c + 4], x[o:o + 4]
+            xb = (x[o + 4] if I0 + 4 < hx else 0.0) if h else (x[o - 1] if I0 > 0 else 0.0)
+            xs = x[c - sy:c - sy + 4] if j > 0 else None
+            xn = x[c + sy:c + sy + 4] if j < ny - 1 else None
+            xd = x[c - sz:c - sz + 4] if k > 0 else None
+            xu = x[c + sz:c + sz + 4] if k < nz - 1 else None
+            fy0, fy1 = by[c + k * nx:c + k * nx + 4], by[c + k * nx + nx:c + k * nx + nx + 4]
+            fz0, fz1 = bz[c:c + 4], bz[c + sz:c + sz + 4]
+            rf = rc + k * ny + j
+            for e in range(4):
+                t = I0 + e
+                i = 2 * t + h
+                bxl, bxh = bx[rf + (hf + t if h else t)], bx[rf + (t + 1 if h else hf + t)]
+                xw = xo[e] if h else (xo[e - 1] if e else xb)
+                xe = (xo[e + 1] if e < 3 else xb) if h else xo[e]
+                off = 0.0
+                if i > 0: off += bxl * xw
+                if i < nx - 1: off += bxh * xe
+                if j > 0: off += fy0[e] * xs[e]
+                if j < ny - 1: off += fy1[e] * xn[e]
+                if k > 0: off += fz0[e] * xd[e]
+                if k < nz - 1: off += fz1[e] * xu[e]
+                acc[e] += bb[e] - (d4[e] * xc4[e] - off)
+        hxc, row = gnx >> 1, (K * gny + J) * gnx
+        out[row + (I0 >> 1)], out[row + (I0 >> 1) + 1] = acc[0] * 0.125, acc[2] * 0.125
+        out[row + hxc + (I0 >> 1)], out[row + hxc + (I0 >> 1) + 1] = acc[1] * 0.125, acc[3] * 0.125
+    assert not np.isnan(out).any()
+    assert np.array_equal(out, ref)
+
+
+# ---- k_cc_gs2_dot: the last colour pass with the fused sweep's partials ---
+def _one_colour(g, b, dinv, x, bx, by, bz, col):
+    x = x.copy()
+    hf = (g.nx + 2) >> 1
+    new = {}
+    for k, j, i in itertools.product(range(g.nz), range(g.ny), range(g.nx)):
+        if (i + j + k) & 1 != col:
+            continue
+        c, t, odd = cix(g, i, j, k), i >> 1, i & 1
+        rf = (k * g.ny + j) * (g.nx + 1)
+        s = 0.0
+        if i > 0: s += bx[rf + (hf + t if odd else t)] * x[cix(g, i - 1, j, k)]
+        if i < g.nx - 1: s += bx[rf + (t + 1 if odd else hf + t)] * x[cix(g, i + 1, j, k)]
+        if j > 0: s += by[c + k * g.nx] * x[c - g.nx]
+        if j < g.ny - 1: s += by[c + k * g.nx + g.nx] * x[c + g.nx]
+        if k > 0: s += bz[c] * x[c - g.nx * g.ny]
+        if k < g.nz - 1: s += bz[c + g.nx * g.ny] * x[c + g.nx * g.ny]
+        new[c] = (b[c] + s) * dinv[c]
+    for c, v in new.items():
+        x[c] = v
+    return x
+
+
+def _gs2_dot(g, b, dinv, x, bx, by, bz, c1):
+    """k_cc_gs2_dot: colour c1 by the fused sweep's threads (positions pq,
+    pq + 1 of both halves of a tile row), with the b.x partial of every
+    (plane, tile) over the same cells."""
+    x = x.copy()
+    hx, hf, sy, sz = g.nx >> 1, (g.nx + 2) >> 1, g.nx, g.nx * g.ny
+    part, upd = {}, {}
+    for k, ty_, tx_ in itertools.product(range(g.nz), range((g.ny + TY - 1) // TY), range((hx + HW - 1) // HW)):
+        for tid in range(THREADS):
+            j, pq = ty_ * TY + (tid >> 4), tx_ * HW + 2 * (tid & 15)
+            if not (j < g.ny and pq < hx):
+                continue
+            h2 = (c1 + j + k) & 1
+            rc = (k * g.ny + j) * g.nx
+            c, o = rc + (hx if h2 else 0) + pq, rc + (0 if h2 else hx) + pq
+            bb, bo, di, xo = b[c:c + 2], b[o:o + 2], dinv[c:c + 2], x[o:o + 2]
+            xb = (x[o + 2] if pq + 2 < hx else 0.0) if h2 else (x[o - 1] if pq > 0 else 0.0)
+            xs = x[c - sy:c - sy + 2] if j > 0 else [0, 0]
+            xn = x[c + sy:c + sy + 2] if j < g.ny - 1 else [0, 0]
+            xd = x[c - sz:c - sz + 2] if k > 0 else [0, 0]
+            xu = x[c + sz:c + sz + 2] if k < g.nz - 1 else [0, 0]
+            xw2 = [xo[0] if h2 else xb, xo[1] if h2 else xo[0]]
+            xe2 = [xo[1] if h2 else xo[0], xb if h2 else xo[1]]
+            rf = rc + k * g.ny + j
+            s2 = [0.0, 0.0]
+            for e in range(2):
+                t = pq + e
+                i = 2 * t + h2
+                off = 0.0
+                if i > 0: off += bx[rf + (hf + t if h2 else t)] * xw2[e]
+                if i < g.nx - 1: off += bx[rf + (t + 1 if h2 else hf + t)] * xe2[e]
+                if j > 0: off += by[c + k * g.nx + e] * xs[e]
+                if j < g.ny - 1: off += by[c + k * g.nx + g.nx + e] * xn[e]
+                if k > 0: off += bz[c + e] * xd[e]
+                if k < g.nz - 1: off += bz[c + sz + e] * xu[e]
+                s2[e] = (bb[e] + off) * di[e]
+            upd[c], upd[c + 1] = s2
+            b0, b1 = (bo, bb) if h2 else (bb, bo)
+            v0, v1 = (xo, s2) if h2 else (s2, xo)
+            key = (k, ty_, tx_)
+            part[key] = part.get(key, 0.0) + b0[0] * v0[0] + b0[1] * v0[1] + b1[0] * v1[0] + b1[1] * v1[1]
+    for c, v in upd.items():
+        x[c] = v
+    return x, part
+
+
+@pytest.mark.parametrize("shape", [(16, 5, 3), (80, 20, 4), (48, 18, 7)])
+def test_gs2_dot_model_matches_fused_partials(shape):
+    """The colour passes end with k_cc_gs2_dot, which forms the same (plane,
+    tile) partials of b.x over the same cells as the fused sweep with r.z."""
+    g = Grid(*shape)
+    rng = np.random.default_rng(3)
+    n = g.nx * g.ny * g.nz
+    b, dinv, x = rng.standard_normal(n), rng.uniform(0.1, 0.3, n), rng.standard_normal(n)
+    bx = rng.uniform(0, 1, (g.nx + 1) * g.ny * g.nz)
+    by = rng.uniform(0, 1, g.nx * (g.ny + 1) * g.nz)
+    bz = rng.uniform(0, 1, g.nx * g.ny * (g.nz + 1))
+    for c0 in (0, 1):
+        ref = colour_passes(g, b, dinv, x, bx, by, bz, c0, False)
+        out, part = _gs2_dot(g, b, dinv, _one_colour(g, b, dinv, x, bx, by, bz, c0), bx, by, bz, 1 - c0)
+        assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+        _, fused_part = fused_sweep(g, b, dinv, x, bx, by, bz, c0, 3)
+        assert set(part) == set(fused_part)
+        assert max(abs(part[key] - fused_part[key]) for key in part) <= 1e-12
