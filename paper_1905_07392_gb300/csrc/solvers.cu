@@ -530,7 +530,12 @@ inline void launch_gs4(cudaStream_t st, dim3 bk, int pz, const VOp<float> &A, fl
 // instead of hanging.
 // kZero: x_in is zero (not read).  kCorr: the first colour reads
 // x_in + the coarse correction of the neighbour's parent (prolongation
-// folded in, as in k_cc_gs).  kDot: also the partial b.x_out of every
+// folded in, as in k_cc_gs); the coarse planes of the tile's parents come by
+// TMA too (a RB_KW x 2 x RB_KR box per coarse plane, a three-slot ring, one
+// new plane every other step), and each cell reads its four distinct parent
+// values (its own parent and, per axis, the next coarse cell on the
+// neighbour's side) once.  The first colour's results keep only that
+// colour's half of each row.  kDot: also the partial b.x_out of every
 // (plane, tile), part[plane * ntiles + tile], summed over the same cells in
 // the same order as k_cc_gs2_dot, which forms them with the colour passes:
 // in FP32 over a thread's cells and within the warp, in FP64 over the warps
