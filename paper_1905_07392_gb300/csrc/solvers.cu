@@ -1485,8 +1485,8 @@ __global__ void __launch_bounds__(256) k_cc_apply_dot(CcOp<T> A, const T *__rest
 // two planes, with 16-byte loads as in k_cc_gs4 (the x faces, rows of nx + 1,
 // as scalars), and adds p.q of its 8 cells to its block's partial.  Each q is
 // formed as in cc_row; the partial sums are grouped by this kernel's fixed
-// block shape (kApply4Blk).  (Capped at 48 registers for five blocks per SM
-// it measured no faster than at 64 registers and four.)
+// block shape (kApply4Blk).  (A cap of 48 registers, for five blocks per SM,
+// measures no faster than 64 registers and four blocks.)
 constexpr int kApply4X = 16, kApply4Y = 8, kApply4Z = 2;
 // The vectorised apply and restriction serve grids where they launch at least
 // this many blocks (two per SM of 152); smaller grids keep one cell per thread.
@@ -2547,7 +2547,7 @@ __global__ void k_cg_pupdate32(float *__restrict__ p, float *__restrict__ e, con
     const int k = ctl[C_K];
     const float beta = k == 0 ? 0.0f : (float)(scal[S_RZ] / scal[S_RZOLD]);
     const float a = k == 0 ? 0.0f : (float)(scal[S_RZOLD] / scal[S_PQ]);
-    // one element: the same operations as before, for each lane of a vector
+    // one element (each lane of a vector, and the tail)
     auto upd = [&](float &pv, float &ev, float zv) {
         if (k == 0) {
             pv = zv;
